@@ -1,0 +1,234 @@
+"""FP64 CPU oracle for the Nexels image formation.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke``
+and by the benchmark's CPU-baseline leg.  The product package never imports
+it, and it imports nothing from the product package's compute path (inputs
+come from the shared seeded generator, which holds no rendering arithmetic).
+
+The compiled part (``nexel_oracle.cpp``) is the brute-force definition: every
+pixel walks all surfels in centre-depth order.  This module only marshals
+float64 arrays through ctypes.
+
+Functions and the passages they follow:
+  render / render_bwd   Sec. 3 (Eq. 1, centre-depth order), Sec. 4.1 (kernel,
+                        Eqs. 3-4), Sec. 4.2 (collection pass, Eqs. 5-6)
+  field_features        Sec. 3 (Instant-NGP hash grid), Eq. 3, supp. Sec. 7.1
+  mlp, texture          Sec. 3 (G), Eq. 4, supp. Sec. 7.1 (no bias, G(0) = 0)
+  map_positive, hash    supp. Sec. 7.1 (MapPositive) and the spatial hash
+  depth_order           Sec. 3 (sorted by the depth of the centres)
+  storage_bytes         supp. Sec. 7.1, last paragraph (2 B per Instant-NGP
+                        parameter, 4 B otherwise)
+Parity unpinned: the shared conventions alpha_min / alpha_max / T_min, the
+near plane and the level scales s_l are parameters, not facts of the paper.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nexel_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OCam(C.Structure):
+    _fields_ = [("W", C.c_int), ("H", C.c_int), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("Rt", C.c_double * 12),
+                ("near", C.c_double)]
+
+
+class OSet(C.Structure):
+    _fields_ = [("K", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
+                ("T_min", C.c_double), ("bg", C.c_double * 3), ("tie_tol", C.c_double)]
+
+
+class OField(C.Structure):
+    _fields_ = [("L", C.c_int), ("T", C.c_int), ("F", C.c_int),
+                ("scale", C.POINTER(C.c_double)), ("table", C.POINTER(C.c_double)),
+                ("n_layers", C.c_int), ("widths", C.POINTER(C.c_int)),
+                ("weights", C.POINTER(C.c_double))]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.oracle_map_positive.restype = C.c_uint64
+        _lib.oracle_map_positive.argtypes = [C.c_int64]
+        _lib.oracle_hash.restype = C.c_uint32
+        _lib.oracle_hash.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_uint32]
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _cam(cam) -> OCam:
+    c = OCam()
+    c.W, c.H = cam.width, cam.height
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    m = np.asarray(cam.world_to_cam, np.float64).ravel()
+    for i in range(12):
+        c.Rt[i] = float(m[i])
+    c.near = float(cam.near)
+    return c
+
+
+def _set(st, tie_tol) -> OSet:
+    s = OSet()
+    s.K = int(st.K)
+    s.alpha_min, s.alpha_max, s.T_min = float(st.alpha_min), float(st.alpha_max), float(st.T_min)
+    for i in range(3):
+        s.bg[i] = float(st.bg[i])
+    s.tie_tol = float(tie_tol)
+    return s
+
+
+class _FieldRef:
+    """Keeps the float64 copies alive while the C struct points at them."""
+
+    def __init__(self, field, table=None):
+        self.scale = _d(field.level_scale)
+        self.table = _d(field.table if table is None else table)
+        self.widths = np.ascontiguousarray(np.asarray(field.widths, np.int32))
+        self.weights = _d(np.concatenate([np.asarray(w, np.float64).ravel() for w in field.weights]))
+        self.n_mlp = self.weights.size
+        self.s = OField()
+        self.s.L, self.s.T, self.s.F = int(field.L), int(field.T), int(field.F)
+        self.s.scale = self.scale.ctypes.data_as(C.POINTER(C.c_double))
+        self.s.table = self.table.ctypes.data_as(C.POINTER(C.c_double))
+        self.s.n_layers = len(field.weights)
+        self.s.widths = self.widths.ctypes.data_as(C.POINTER(C.c_int))
+        self.s.weights = self.weights.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _surfels(scene):
+    return [_d(scene.mu), _d(scene.quat), _d(scene.scale), _d(scene.opacity),
+            _d(scene.gamma), _d(scene.color)]
+
+
+def all_pixels(cam) -> np.ndarray:
+    return np.arange(cam.width * cam.height, dtype=np.int32)
+
+
+def render(scene, cam, settings, field=None, pixels=None, tie_tol: float = 1e-6,
+           table=None) -> dict:
+    """Forward of the listed pixels.  ``table`` overrides field.table (e.g.
+    the fp16-rounded copy the reduced-precision path reads)."""
+    L = lib()
+    pix = all_pixels(cam) if pixels is None else np.ascontiguousarray(pixels, np.int32)
+    n, K = pix.size, settings.K
+    out = dict(image=np.zeros((n, 3)), notex=np.zeros((n, 3)), weights=np.zeros((n, K)),
+               ids=np.zeros((n, K), np.int32), depths=np.zeros((n, K)),
+               textures=np.zeros((n, K, 3)), T_final=np.zeros(n),
+               n_contrib=np.zeros(n, np.int32), tie=np.zeros(n, np.int32))
+    fr = _FieldRef(field, table) if field is not None else None
+    sv = _surfels(scene)
+    c, s = _cam(cam), _set(settings, tie_tol)
+    rc = L.oracle_render(C.byref(c), C.byref(s), C.byref(fr.s) if fr else None,
+                         C.c_int(scene.n), *[_p(a) for a in sv], C.c_int(n), _p(pix),
+                         *[_p(out[k]) for k in ("image", "notex", "weights", "ids", "depths",
+                                                "textures", "T_final", "n_contrib", "tie")])
+    if rc != 0:
+        raise ValueError(f"oracle_render failed ({rc})")
+    out["pixels"] = pix
+    return out
+
+
+def render_bwd(scene, cam, settings, field, pixels, d_image, d_weights=None,
+               d_textures=None, table=None) -> dict:
+    L = lib()
+    pix = np.ascontiguousarray(pixels, np.int32)
+    n, N = pix.size, scene.n
+    fr = _FieldRef(field, table) if field is not None else None
+    sv = _surfels(scene)
+    g = dict(mu=np.zeros((N, 3)), quat=np.zeros((N, 4)), scale=np.zeros((N, 2)),
+             opacity=np.zeros(N), gamma=np.zeros((N, 2)), color=np.zeros((N, 3)))
+    if fr:
+        g["table"] = np.zeros((field.L, field.T, field.F))
+        g["mlp"] = np.zeros(fr.n_mlp)
+    dI = _d(d_image).reshape(n, 3)
+    dW = None if d_weights is None else _d(d_weights).reshape(n, settings.K)
+    dT = None if d_textures is None else _d(d_textures).reshape(n, settings.K, 3)
+    c, s = _cam(cam), _set(settings, 0.0)
+    rc = L.oracle_render_bwd(C.byref(c), C.byref(s), C.byref(fr.s) if fr else None,
+                             C.c_int(N), *[_p(a) for a in sv], C.c_int(n), _p(pix),
+                             _p(dI), _p(dW), _p(dT),
+                             *[_p(g[k]) for k in ("mu", "quat", "scale", "opacity", "gamma",
+                                                  "color")],
+                             _p(g.get("table")), _p(g.get("mlp")))
+    if rc != 0:
+        raise ValueError(f"oracle_render_bwd failed ({rc})")
+    if fr:
+        offs = np.cumsum([0] + [w.size for w in field.weights])
+        g["mlp_layers"] = [g["mlp"][offs[i]:offs[i + 1]].reshape(field.weights[i].shape)
+                           for i in range(len(field.weights))]
+    return g
+
+
+def field_features(field, focal, x, t, table=None) -> np.ndarray:
+    fr = _FieldRef(field, table)
+    x, t = _d(x).reshape(-1, 3), _d(t).ravel()
+    out = np.zeros((t.size, field.L * field.F))
+    lib().oracle_field_features(C.byref(fr.s), C.c_double(focal), C.c_int(t.size), _p(x), _p(t),
+                                _p(out))
+    return out
+
+
+def mlp(field, inp) -> np.ndarray:
+    fr = _FieldRef(field)
+    inp = _d(inp).reshape(-1, field.widths[0])
+    out = np.zeros((inp.shape[0], field.widths[-1]))
+    lib().oracle_mlp(C.byref(fr.s), C.c_int(inp.shape[0]), _p(inp), _p(out))
+    return out
+
+
+def texture(field, focal, x, t, table=None) -> np.ndarray:
+    fr = _FieldRef(field, table)
+    x, t = _d(x).reshape(-1, 3), _d(t).ravel()
+    out = np.zeros((t.size, field.widths[-1]))
+    lib().oracle_texture(C.byref(fr.s), C.c_double(focal), C.c_int(t.size), _p(x), _p(t), _p(out))
+    return out
+
+
+def map_positive(k: int) -> int:
+    return int(lib().oracle_map_positive(int(k)))
+
+
+def hash_index(kx: int, ky: int, kz: int, T: int) -> int:
+    return int(lib().oracle_hash(int(kx), int(ky), int(kz), int(T)))
+
+
+def depth_order(cam, mu) -> np.ndarray:
+    mu = _d(mu).reshape(-1, 3)
+    order = np.zeros(mu.shape[0], np.int32)
+    c = _cam(cam)
+    n = lib().oracle_depth_order(C.byref(c), C.c_int(mu.shape[0]), _p(mu), _p(order))
+    return order[:n]
+
+
+def storage_bytes(n_prims: int, floats_per_prim: int, L: int, T: int, F: int,
+                  mlp_params: int) -> int:
+    """Model size as the paper reports it: 2 bytes per Instant-NGP parameter
+    (hash table and MLP), 4 bytes per other parameter (supp. Sec. 7.1)."""
+    return 4 * n_prims * floats_per_prim + 2 * (L * T * F + mlp_params)
