@@ -1,0 +1,412 @@
+"""Benchmark of the Nexels hot path on one GB300 (and N replicas).
+
+A step is one pass of the whole differentiable image formation over one
+view: preprocess + binning + sort, collection pass, texturing pass (hash
+gather + MLP + composite), and the full backward (MLP and hash-grid
+backward, collection backward, preprocess backward), with the inputs
+resident in HBM.  The loss and the optimizer are outside the step.
+
+Workload: 300k surfels (box room + facades), 1280x720, K = 4, hash grid
+16 levels x 2^19 x 2, MLP 32 -> 64 -> 64 -> 3; the BF16 form (FP16 table,
+BF16 tensor-core MLP, FP32 accumulation) is the headline and the FP32 form
+is reported beside it, together with render FPS (forward only) for both.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "train-step Mpix/s and render FPS, 300k surfels 720p K=4, BF16 vs FP32 path"
+WORKLOAD = "config2: 300k surfels (box room + facades), 1280x720, K=4, hash 16x2^19x2, MLP 32-64-64-3"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region (read only)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.idx}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- workload
+class Job:
+    """Device-resident inputs and workspaces of one form (bf16 or f32)."""
+
+    def __init__(self, w, dev, precision: str):
+        import torch
+        from paper_2512_13796_gb300 import render as R
+        self.R = R
+        self.precision = precision
+        grid, mlp = ("f16", "bf16") if precision == "bf16" else ("f32", "f32")
+        self.cam, self.st = w.cameras[0], w.settings
+        self.cam_s = R.camera_struct(self.cam)
+        self.st_s = R.settings_struct(self.st, grid, mlp)
+        self.p = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).to(dev)
+                  for k in ("mu", "quat", "scale", "opacity", "gamma", "color")}
+        self.field = R.DeviceField.from_synth(w.field, dev, grid, mlp)
+        self.ts = self.field.storage_table()
+        self.wts = self.field.weights
+        self.ws = R.Workspace(dev, cap_hint=32 << 20)
+        H, W = self.cam.height, self.cam.width
+        g = torch.Generator(device="cpu").manual_seed(123)
+        self.d_image = (torch.randn(H, W, 3, generator=g) * 1e-3).to(dev)
+        self.N = w.scene.n
+        self.grads = None
+        self.fwd_out = None
+
+    def forward(self):
+        p = self.p
+        self.fwd_out = self.R.forward(self.ws, self.cam_s, self.st_s, self.field, self.ts, self.wts,
+                                      p["mu"], p["quat"], p["scale"], p["opacity"], p["gamma"],
+                                      p["color"])
+        return self.fwd_out
+
+    def step(self):
+        out = self.forward()
+        p = self.p
+        self.grads = self.R.backward(self.ws, self.cam_s, self.st_s, self.field, self.ts, self.wts,
+                                     p["mu"], p["quat"], p["scale"], p["opacity"], p["gamma"], out,
+                                     self.d_image, grads=self.grads)
+        return out
+
+
+def timed(fn, steps, flush, stream):
+    """Per-step CUDA-event times (ms) with an L2 flush before each step."""
+    import torch
+    times = []
+    for _ in range(steps):
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        times.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, hbm_traffic=None):
+    """Roofline entry of the dominant kernel from live per-kernel events."""
+    name, (ms_tot, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    ms = ms_tot / max(launches, 1)
+    w = job
+    P = w.cam.width * w.cam.height
+    K = w.st.K
+    L, F = w.field.L, w.field.F
+    b_entry = 2 if w.precision == "bf16" else 4
+    out = {"kernel": name, "ms_per_launch": ms, "launches": launches}
+    samples = int((w.fwd_out["ids"] >= 0).sum().item()) if w.fwd_out is not None else P * K
+    if name.startswith("texture_fwd") or name.startswith("texture_bwd"):
+        # algorithmic bytes: the table entries the gather reads (8 corners x
+        # L levels x F features), plus, in the backward, an FP32 read-modify-
+        # write of the same entries in the table gradient
+        per = L * 8 * F * b_entry + (L * 8 * F * 4 * 2 if "bwd" in name else 0)
+        A = samples * per / (ms * 1e-3) / 1e9
+        out.update(bound="hbm", achieved=A, peak=peaks["hbm_gbs"], unit="GB/s",
+                   peak_source=f"hbm_gbs ({peak_kind})", units_per_launch=samples,
+                   bytes_per_unit=per)
+        out["frac"] = A / out["peak"]
+    elif name.startswith("mlp_wgrad"):
+        widths = w.field.widths
+        macs = sum(widths[i] * widths[i + 1] for i in range(len(widths) - 1))
+        rows = ((P * (1 << (K - 1).bit_length()) + 15) // 16) * 16
+        flop = rows * 2 * macs * 3  # forward recompute, input-side deltas, weight gradient
+        A = flop / (ms * 1e-3) / 1e12
+        pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        out.update(bound="tensor", achieved=A, peak=pk, unit="TFLOP/s",
+                   peak_source=f"bf16_tflops_sustained ({peak_kind})", units_per_launch=rows,
+                   flop_per_unit=2 * macs * 3)
+        out["frac"] = A / pk
+    else:
+        # sort / scan / collection kernels: report bytes moved per launch
+        # against the HBM peak (algorithmic bytes set by the caller)
+        out.update(bound="hbm", achieved=None, peak=peaks["hbm_gbs"], unit="GB/s", frac=None)
+    out["traffic"] = hbm_traffic
+    return out
+
+
+def cpu_baseline(w, seconds_target: float = 15.0) -> dict:
+    """The FP64 oracle as it stands, forward + backward on a pixel sample of
+    the same view, on this host's cores."""
+    import oracle
+    from paper_2512_13796_gb300 import synth
+    cam, st = w.cameras[0], w.settings
+    n = 256
+    t_used = 0.0
+    done = 0
+    rng_seed = 0
+    while t_used < seconds_target and n <= 65536:
+        pix = synth.pixel_sample(cam, n, 0, seed=rng_seed)
+        t0 = time.perf_counter()
+        oracle.render(w.scene, cam, st, w.field, pix)
+        dI = np.ones((pix.size, 3)) * 1e-3
+        oracle.render_bwd(w.scene, cam, st, w.field, pix, dI)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        done += pix.size
+        rng_seed += 1
+        if dt < seconds_target / 4:
+            n *= 2
+    return {"value": done / t_used / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{done} random pixels of the 1280x720 view, forward + backward, FP64 "
+                      f"brute force over all 300k surfels ({t_used:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="nexels", choices=["nexels", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-json", default=None, help="write per-kernel times here")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2512_13796_gb300 import synth
+
+    if args.impl == "reference":
+        # the oracle, timed on the host: rank 0 only
+        if rank != 0:
+            return
+        w = synth.workload(2)
+        import oracle
+        cam, st = w.cameras[0], w.settings
+        per_step = 512
+        for k in range(args.warmup):
+            pix = synth.pixel_sample(cam, 64, 0, seed=1000 + k)
+            oracle.render(w.scene, cam, st, w.field, pix)
+        t = []
+        for k in range(args.steps):
+            pix = synth.pixel_sample(cam, per_step, 0, seed=k)
+            t0 = time.perf_counter()
+            oracle.render(w.scene, cam, st, w.field, pix)
+            oracle.render_bwd(w.scene, cam, st, w.field, pix, np.ones((pix.size, 3)) * 1e-3)
+            t.append(time.perf_counter() - t0)
+        v = per_step * args.steps / sum(t) / 1e6
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "sample": f"{per_step} pixels per step"},
+                "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": os.cpu_count(),
+                                 "kind": "oracle",
+                                 "sample": f"{per_step} random pixels per step, forward + "
+                                           "backward, FP64 brute force"},
+                "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2512_13796_gb300 import _native
+    _native.build()
+    _native.lib()
+    stream = torch.cuda.current_stream()
+    peaks, peak_kind = load_peaks()
+    w = synth.workload(2)
+    jobs = {"bf16": Job(w, dev, "bf16"), "f32": Job(w, dev, "f32")}
+    P = w.cameras[0].width * w.cameras[0].height
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.zero_()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for j in jobs.values():
+        for _ in range(max(args.warmup, 3)):
+            j.step()
+    barrier()
+
+    results = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = _native.nexel_launch_count()
+    t_train = timed(jobs["bf16"].step, args.steps, flush, stream)
+    launches = (_native.nexel_launch_count() - launches0) // args.steps
+    barrier()
+    clk = clocks.stop()
+    results["bf16_train"] = t_train
+    results["f32_train"] = timed(jobs["f32"].step, args.steps, flush, stream)
+    results["bf16_fwd"] = timed(jobs["bf16"].forward, args.steps, flush, stream)
+    results["f32_fwd"] = timed(jobs["f32"].forward, args.steps, flush, stream)
+    barrier()
+    # per-kernel CUDA events on the launch stream, same steps again
+    _native.nexel_profile_enable(True)
+    results["bf16_train_profiled"] = timed(jobs["bf16"].step, args.steps, flush, stream)
+    prof = _native.nexel_profile_read()
+    _native.nexel_profile_enable(True)
+    results["f32_train_profiled"] = timed(jobs["f32"].step, args.steps, flush, stream)
+    prof_f32 = _native.nexel_profile_read()
+    _native.nexel_profile_enable(False)
+
+    def agg(ts):
+        t = torch.tensor([float(np.mean(ts))], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = {k: agg(v) for k, v in results.items()}
+
+    # end to end through the public API: target image H2D from pinned memory,
+    # autograd render, L1 loss, backward, loss D2H
+    from paper_2512_13796_gb300 import render as R
+    jb = jobs["bf16"]
+    params = {k: v.clone().requires_grad_(True) for k, v in jb.p.items()}
+    fld = R.DeviceField.from_synth(w.field, dev, "f16", "bf16")
+    fld.table.requires_grad_(True)
+    fld.weights.requires_grad_(True)
+    H, W = w.cameras[0].height, w.cameras[0].width
+    target_host = torch.rand(H, W, 3).pin_memory()
+    loss_host = torch.empty(1).pin_memory()
+    ws_e2e = R.Workspace(dev, cap_hint=32 << 20)
+
+    def e2e_step():
+        tgt = target_host.to(dev, non_blocking=True)
+        img, _, _ = R.render(params, fld, w.cameras[0], w.settings, ws_e2e)
+        loss = (img - tgt).abs().mean()
+        loss.backward()
+        loss_host.copy_(loss.detach().reshape(1), non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = agg([e2e_ms])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if args.profile_json and rank == 0:
+        with open(args.profile_json, "w") as f:
+            json.dump({"bf16_train": prof, "f32_train": prof_f32, "steps": args.steps}, f, indent=1)
+
+    rl = roofline(prof, jobs["bf16"], peaks, peak_kind, args.steps)
+    n_inst = jobs["bf16"].fwd_out["n_instances"]
+    mpix = lambda m: world * P / (m * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": mpix(ms["bf16_train"]), "unit": "Mpix/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms["bf16_train"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "surfels": w.scene.n, "width": W, "height": H,
+                   "K": w.settings.K, "n_instances": int(n_inst),
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "forms": {
+            "bf16": {"train_mpix_s": mpix(ms["bf16_train"]), "train_ms": ms["bf16_train"],
+                     "render_fps": 1e3 / ms["bf16_fwd"], "render_ms": ms["bf16_fwd"]},
+            "f32": {"train_mpix_s": mpix(ms["f32_train"]), "train_ms": ms["f32_train"],
+                    "render_fps": 1e3 / ms["f32_fwd"], "render_ms": ms["f32_fwd"]},
+        },
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items(),
+                                                                        key=lambda kv: -kv[1][0])},
+        "kernels_ms_per_step_f32": {k: v[0] / args.steps for k, v in
+                                    sorted(prof_f32.items(), key=lambda kv: -kv[1][0])},
+        "profiled_ms_per_step": {"bf16": ms["bf16_train_profiled"], "f32": ms["f32_train_profiled"]},
+        "roofline": rl,
+        "cpu_baseline": cpu,
+        "e2e": {"value": mpix(e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches),
+        "gpu_launches_note": "kernels of libnexel per timed step (library launch counter)",
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * nexel.h — C ABI of the Nexels image-formation library (libnexel.so).
+ *
+ * The library renders neurally-textured surfels ("nexels") on one CUDA
+ * device and differentiates the result:
+ *   nexel_preprocess  per-surfel projection, tile binning and the
+ *                     (tile, centre-depth) ordering of Sec. 3 ("Preliminaries":
+ *                     surfels are sorted by the depth of their centres and
+ *                     alpha-composited by a tile-based rasterizer);
+ *   nexel_render_fwd  the collection pass (Sec. 4.2: alpha, transmittance,
+ *                     the non-textured render N of Eq. 5 and the per-pixel
+ *                     top-K buffers I, W, D) followed by the texturing pass
+ *                     (Sec. 4.2 and Eqs. 3-4: x = o + D d, down-weighted
+ *                     hash-grid features, MLP G) and the composite of Eq. 6;
+ *   nexel_render_bwd  the gradient of those outputs with respect to every
+ *                     surfel parameter, the hash table and the MLP weights.
+ *
+ * Conventions shared by every entry point
+ *   - All array pointers are DEVICE pointers to caller-owned memory unless a
+ *     comment says "host".  The library never allocates or frees device
+ *     memory; scratch lives in the caller's workspace (nexel_workspace_size).
+ *   - Arrays are dense, C order, float32 unless stated: mu [N][3],
+ *     quat [N][4] as (w, x, y, z) (need not be unit: it is normalised
+ *     inside, with the gradient taken through the normalisation),
+ *     scale [N][2] (sigma_1, sigma_2 > 0), opacity [N], gamma [N][2] (>= 1),
+ *     color [N][3].  Per-pixel outputs are [H][W][...] with pixel
+ *     (x, y) at index y * W + x.  Parameters are passed activated.
+ *   - Camera: pinhole, pixel centres at (x + 0.5, y + 0.5), world_to_cam is
+ *     a row-major 3x4 [R | t] with x_cam = R x_world + t, +z forward and +y
+ *     down.  The ray of pixel (x, y) is o + t d with o the camera centre and
+ *     d = R^T ((x + .5 - cx) / fx, (y + .5 - cy) / fy, 1), NOT normalised, so
+ *     t equals view depth.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) except nexel_preprocess, which synchronises the
+ *     stream once to read the instance count back to the host.
+ *   - Return value: NEXEL_OK (0) or a negative NEXEL_ERR_* code; nothing is
+ *     launched when an argument check fails.  nexel_status_string names it.
+ */
+#ifndef NEXEL_H_
+#define NEXEL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NEXEL_OK 0
+#define NEXEL_ERR_INVALID_ARG (-1)
+#define NEXEL_ERR_CUDA (-2)
+#define NEXEL_ERR_CAPACITY (-3)
+#define NEXEL_ERR_UNSUPPORTED (-4)
+#define NEXEL_ERR_TIMEOUT (-5)
+#define NEXEL_ERR_NUMERIC (-6)
+
+#define NEXEL_F32 0
+#define NEXEL_F16 1
+#define NEXEL_BF16 2
+
+#define NEXEL_MAX_K 8
+#define NEXEL_MAX_LEVELS 32
+#define NEXEL_MAX_LAYERS 4
+#define NEXEL_TILE 16
+
+typedef void* nexel_stream_t; /* a cudaStream_t */
+
+typedef struct {
+  int width, height;
+  float fx, fy, cx, cy;
+  float world_to_cam[12];
+  float near_plane; /* surfel centres and ray hits at depth <= near are dropped */
+} nexel_camera;
+
+/* Render settings.  alpha_min / alpha_max / T_min are the compositing
+ * thresholds the paper inherits from 3DGS without stating them (defaults
+ * 1/255, 0.99, 1e-4): a surfel with alpha < alpha_min is skipped, alpha is
+ * clamped to alpha_max, and compositing stops before the surfel that would
+ * take the transmittance below T_min.  K in 0..NEXEL_MAX_K is the number of
+ * textured primitives per pixel (Sec. 4.2).  grid_dtype is the storage type
+ * of the hash table (NEXEL_F32 or NEXEL_F16); mlp_dtype the arithmetic of
+ * the MLP (NEXEL_F32: FP32 SIMT; NEXEL_BF16: BF16 tensor-core MMA with FP32
+ * accumulation). */
+typedef struct {
+  int K;
+  float alpha_min, alpha_max, T_min;
+  float bg[3];
+  int grid_dtype, mlp_dtype;
+} nexel_settings;
+
+/* Neural field of Sec. 3 ("Instant-NGP") and Eq. 4: L hash tables of T
+ * entries (T a power of two) with F features (F = 2), level scales s_l, and
+ * an MLP without bias: widths[0] = L * F -> hidden ... -> widths[n_layers]
+ * = 3, ReLU on hidden layers, linear output.  weights are float32 packed
+ * layer after layer, layer l row-major [widths[l+1]][widths[l]].  Hidden
+ * widths must be multiples of 16 and at most 64; L * F a multiple of 8 and at
+ * most 64. */
+typedef struct {
+  int L, T, F;
+  float level_scale[NEXEL_MAX_LEVELS]; /* host values, s_l per world unit */
+  const void* table;                   /* device [L][T][F], grid_dtype */
+  int n_layers;
+  int widths[NEXEL_MAX_LAYERS + 1];
+  const float* weights; /* device, float32 */
+} nexel_field;
+
+/* Bytes of device workspace needed for N surfels and up to max_instances
+ * (tile, surfel) pairs on this camera.  Writes *bytes (host).  The same
+ * workspace must be passed, with the same ws_bytes, to nexel_preprocess and
+ * to the nexel_render_fwd / nexel_render_bwd calls that follow it; its
+ * instance capacity is derived from ws_bytes. */
+int nexel_workspace_size(const nexel_camera* cam, int N, long long max_instances, size_t* bytes);
+
+/* Bytes of the separate backward scratch (per-sample texture gradients and
+ * field features) for this camera, K and field.  Writes *bytes (host). */
+int nexel_bwd_workspace_size(const nexel_camera* cam, const nexel_settings* settings,
+                             const nexel_field* field, size_t* bytes);
+
+/* Geometry preprocess and binning (Sec. 3, "Preliminaries", and Sec. 4.1,
+ * the generalised-Gaussian kernel alpha = o exp(-|u|^(2 g1)/2) exp(-|v|^(2 g2)/2)):
+ * per surfel the camera-space frame, the exact screen footprint of the
+ * region where alpha >= alpha_min, the tiles it touches; then a stable radix
+ * sort of surfels by centre depth (culled: centre depth <= near or
+ * opacity < alpha_min) and a stable radix sort of (tile, depth-rank)
+ * instances by tile, bit-exact.  Results stay in `ws`.  Writes the number of
+ * instances to *n_instances_out (host); returns NEXEL_ERR_CAPACITY, without
+ * binning, if it exceeds the capacity `ws` was sized for. */
+int nexel_preprocess(const nexel_camera* cam, const nexel_settings* settings, int N,
+                     const float* mu, const float* quat, const float* scale,
+                     const float* opacity, const float* gamma, const float* color, void* ws,
+                     size_t ws_bytes, long long* n_instances_out, nexel_stream_t stream);
+
+/* Forward render, after nexel_preprocess on the same ws.  Outputs (device,
+ * caller-owned, fully overwritten):
+ *   image    [H][W][3]  C = N + sum_j W_j T_j + T_final bg     (Eq. 6)
+ *   notex    [H][W][3]  N, non-textured render without the K  (Eq. 5)
+ *   weights  [H][W][K]  W, blending weights w = alpha T, descending
+ *   ids      [H][W][K]  I, surfel index, -1 for an empty slot (int32)
+ *   depths   [H][W][K]  D, ray parameter t* of the intersection, 0 if empty
+ *   textures [H][W][K][3] T_j = G(Delta * H(o + D_j d)), 0 if empty (Eq. 4)
+ *   T_final  [H][W]     transmittance after the last composited surfel
+ * Ties in weight keep the front-most surfel. */
+int nexel_render_fwd(const nexel_camera* cam, const nexel_settings* settings,
+                     const nexel_field* field, int N, void* ws, size_t ws_bytes, float* image,
+                     float* notex, float* weights, int* ids, float* depths, float* textures,
+                     float* T_final, nexel_stream_t stream);
+
+/* Backward of nexel_render_fwd (same ws, same saved outputs).  Upstream
+ * gradients: d_image [H][W][3] (required); d_weights [H][W][K] and
+ * d_textures [H][W][K][3] may be NULL.  The discrete choices (order,
+ * skips, early stop, top-K) are held fixed.  Gradient outputs (device,
+ * float32, shaped like their parameters; d_table is [L][T][F] float32 and
+ * d_mlp is packed like field->weights) are overwritten, or added to when
+ * accumulate != 0.  Any gradient pointer may be NULL to skip it.  bwd_ws is
+ * scratch of nexel_bwd_workspace_size bytes.  Requires alpha_max < 1 (the
+ * replay divides by 1 - alpha).  The colour gradient flows only to surfels
+ * composited untextured (Eq. 5). */
+int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
+                     const nexel_field* field, int N, const float* mu, const float* quat,
+                     const float* scale, const float* opacity, const float* gamma, void* ws,
+                     size_t ws_bytes, void* bwd_ws, size_t bwd_ws_bytes, const float* weights,
+                     const int* ids, const float* depths, const float* T_final,
+                     const float* d_image, const float* d_weights, const float* d_textures,
+                     int accumulate, float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
+                     float* d_gamma, float* d_color, float* d_table, float* d_mlp,
+                     nexel_stream_t stream);
+
+/* Inspection of the binning done by the last nexel_preprocess on ws: the
+ * n_instances (tile, surfel) pairs in the order the collection pass walks
+ * them, i.e. by tile, then by centre view depth (Sec. 3, "Preliminaries"),
+ * then by surfel index.  Writes tile index (ty * tiles_x + tx), surfel index
+ * and the float32 centre depth used as the sort key; any output may be NULL.
+ * Device outputs of n_instances elements each. */
+int nexel_instance_list(const nexel_camera* cam, int N, const void* ws, size_t ws_bytes,
+                        long long n_instances, int* tile_out, int* id_out, float* depth_out,
+                        nexel_stream_t stream);
+
+/* Instrumentation (no counterpart in the paper).  nexel_launch_count: the
+ * number of kernels this library has launched in the process.
+ * nexel_profile_enable(1) starts recording a CUDA event pair on the launch
+ * stream around every kernel launch (0 stops and discards);
+ * nexel_profile_read synchronises those events and reports, per kernel
+ * name, the summed device time in ms and the launch count: up to
+ * max_entries rows into names (32 chars each, host), total_ms and launches
+ * (host arrays), and the number of distinct kernels into *n_out. */
+long long nexel_launch_count(void);
+int nexel_profile_enable(int on);
+int nexel_profile_read(int max_entries, char* names, float* total_ms, int* launches, int* n_out);
+
+/* Human-readable name of a status code (static string). */
+const char* nexel_status_string(int status);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int nexel_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEXEL_H_ */

@@ -46,7 +46,8 @@ struct OSet {
   int K;
   double alpha_min, alpha_max, T_min;
   double bg[3];
-  double tie_tol;  // relative width used to flag tie pixels
+  double tie_tol;    // relative width used to flag threshold / top-K ties
+  double order_tol;  // relative width used to flag centre-depth order ties
 };
 
 struct OField {
@@ -302,7 +303,8 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
     e.id = i; e.pos = (int)pos; e.alpha = ac; e.alpha_raw = a; e.clamped = a > st.alpha_max;
     e.T = T; e.w = ac * T; e.t = t; e.u = u; e.v = v;
     for (int k = 0; k < 3; ++k) e.x[k] = x[k];
-    if (!r.list.empty() && near_rel(s.zc[r.list.back().id], s.zc[i], tol)) r.tie |= TIE_ORDER;
+    if (!r.list.empty() && near_rel(s.zc[r.list.back().id], s.zc[i], st.order_tol))
+      r.tie |= TIE_ORDER;
     r.list.push_back(e);
     T = test;
   }

@@ -1,0 +1,233 @@
+"""Build and ctypes binding of libnexel.so (the C ABI in include/nexel.h).
+
+Argument marshalling only: every function here forwards plain pointers and
+sizes to the library, which does all the work in its CUDA kernels.  There
+is no fallback: if the library is missing or fails to load, calls raise.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import ctypes as C
+import glob
+import os
+import subprocess
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+_CSRC = os.path.join(_PKG, "csrc")
+_INC = os.path.join(_ROOT, "include")
+_BUILD = os.path.join(_PKG, "_build")
+LIB_PATH = os.path.join(_PKG, "libnexel.so")
+
+ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", _INC]
+
+NEXEL_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "instance capacity exceeded",
+          -4: "unsupported configuration", -5: "device wait timed out", -6: "numeric check failed"}
+F32, F16, BF16 = 0, 1, 2
+MAX_LEVELS, MAX_LAYERS = 32, 4
+
+EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess",
+           "nexel_render_fwd", "nexel_render_bwd", "nexel_instance_list", "nexel_status_string",
+           "nexel_version", "nexel_launch_count", "nexel_profile_enable", "nexel_profile_read"]
+
+
+def _nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def _sources():
+    return sorted(glob.glob(os.path.join(_CSRC, "*.cu")))
+
+
+def _headers():
+    return sorted(glob.glob(os.path.join(_CSRC, "*.cuh")) + glob.glob(os.path.join(_INC, "*.h")))
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit (in parallel) and link libnexel.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    hdr_t = max((os.path.getmtime(h) for h in _headers()), default=0.0)
+    nvcc = _nvcc()
+    jobs = []
+    for src in _sources():
+        obj = os.path.join(_BUILD, os.path.basename(src)[:-3] + ".o")
+        if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_t):
+            jobs.append((src, obj))
+
+    def compile_one(job):
+        src, obj = job
+        tmp = obj + f".{os.getpid()}.tmp.o"
+        cmd = [nvcc, *ARCH_FLAGS, *NVCC_FLAGS, "-c", src, "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr[-4000:]}")
+        os.replace(tmp, obj)
+        if verbose:
+            print("compiled", os.path.basename(src))
+
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+            list(ex.map(compile_one, jobs))
+    objs = [os.path.join(_BUILD, os.path.basename(s)[:-3] + ".o") for s in _sources()]
+    if force or jobs or not os.path.exists(LIB_PATH) or \
+            os.path.getmtime(LIB_PATH) < max(os.path.getmtime(o) for o in objs):
+        tmp = LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = [nvcc, *ARCH_FLAGS, "-shared", "-o", tmp, *objs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ------------------------------------------------------------- C structs
+class Camera(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("world_to_cam", C.c_float * 12),
+                ("near_plane", C.c_float)]
+
+
+class Settings(C.Structure):
+    _fields_ = [("K", C.c_int), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
+                ("T_min", C.c_float), ("bg", C.c_float * 3), ("grid_dtype", C.c_int),
+                ("mlp_dtype", C.c_int)]
+
+
+class Field(C.Structure):
+    _fields_ = [("L", C.c_int), ("T", C.c_int), ("F", C.c_int),
+                ("level_scale", C.c_float * MAX_LEVELS), ("table", C.c_void_p),
+                ("n_layers", C.c_int), ("widths", C.c_int * (MAX_LAYERS + 1)),
+                ("weights", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib(auto_build: bool = False):
+    """The loaded library.  Raises if it is missing (no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not auto_build:
+            raise RuntimeError(f"libnexel.so is not built ({LIB_PATH}); run build() first")
+        build()
+    L = C.CDLL(LIB_PATH)
+    vp, i, sz, ll = C.c_void_p, C.c_int, C.c_size_t, C.c_longlong
+    L.nexel_workspace_size.argtypes = [vp, i, ll, C.POINTER(sz)]
+    L.nexel_bwd_workspace_size.argtypes = [vp, vp, vp, C.POINTER(sz)]
+    L.nexel_preprocess.argtypes = [vp, vp, i] + [vp] * 7 + [sz, C.POINTER(ll), vp]
+    L.nexel_render_fwd.argtypes = [vp, vp, vp, i, vp, sz] + [vp] * 7 + [vp]
+    L.nexel_render_bwd.argtypes = ([vp, vp, vp, i] + [vp] * 5 + [vp, sz, vp, sz] + [vp] * 4 +
+                                   [vp] * 3 + [i] + [vp] * 8 + [vp])
+    L.nexel_instance_list.argtypes = [vp, i, vp, sz, ll, vp, vp, vp, vp]
+    L.nexel_launch_count.restype = C.c_longlong
+    L.nexel_launch_count.argtypes = []
+    L.nexel_profile_enable.argtypes = [i]
+    L.nexel_profile_read.argtypes = [i, vp, vp, vp, C.POINTER(i)]
+    L.nexel_status_string.restype = C.c_char_p
+    L.nexel_status_string.argtypes = [i]
+    L.nexel_version.restype = i
+    for name in EXPORTS:
+        getattr(L, name).restype = getattr(L, name).restype or i
+    _lib = L
+    return L
+
+
+class NexelError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+def check(fn: str, code: int) -> int:
+    if code != NEXEL_OK:
+        raise NexelError(fn, code)
+    return code
+
+
+# Thin wrappers with the ABI's names: pointers are ints (tensor.data_ptr()),
+# structs are the ctypes classes above.
+def nexel_workspace_size(cam: Camera, N: int, max_instances: int) -> int:
+    out = C.c_size_t(0)
+    check("nexel_workspace_size", lib().nexel_workspace_size(C.byref(cam), N, max_instances,
+                                                            C.byref(out)))
+    return out.value
+
+
+def nexel_bwd_workspace_size(cam: Camera, st: Settings, field: Field | None) -> int:
+    out = C.c_size_t(0)
+    check("nexel_bwd_workspace_size",
+          lib().nexel_bwd_workspace_size(C.byref(cam), C.byref(st),
+                                         C.byref(field) if field is not None else None,
+                                         C.byref(out)))
+    return out.value
+
+
+def nexel_preprocess(cam, st, N, mu, quat, scale, opacity, gamma, color, ws, ws_bytes,
+                     stream) -> tuple[int, int]:
+    """Returns (status, n_instances); status NEXEL_ERR_CAPACITY is returned,
+    not raised, so the caller can grow the workspace."""
+    n = C.c_longlong(0)
+    rc = lib().nexel_preprocess(C.byref(cam), C.byref(st), N, mu, quat, scale, opacity, gamma,
+                                color, ws, ws_bytes, C.byref(n), stream)
+    return rc, n.value
+
+
+def nexel_render_fwd(cam, st, field, N, ws, ws_bytes, image, notex, weights, ids, depths,
+                     textures, T_final, stream) -> int:
+    return check("nexel_render_fwd", lib().nexel_render_fwd(
+        C.byref(cam), C.byref(st), C.byref(field) if field is not None else None, N, ws, ws_bytes,
+        image, notex, weights, ids, depths, textures, T_final, stream))
+
+
+def nexel_render_bwd(cam, st, field, N, mu, quat, scale, opacity, gamma, ws, ws_bytes, bws,
+                     bws_bytes, weights, ids, depths, T_final, d_image, d_weights, d_textures,
+                     accumulate, d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color, d_table,
+                     d_mlp, stream) -> int:
+    return check("nexel_render_bwd", lib().nexel_render_bwd(
+        C.byref(cam), C.byref(st), C.byref(field) if field is not None else None, N, mu, quat,
+        scale, opacity, gamma, ws, ws_bytes, bws, bws_bytes, weights, ids, depths, T_final,
+        d_image, d_weights, d_textures, int(accumulate), d_mu, d_quat, d_scale, d_opacity,
+        d_gamma, d_color, d_table, d_mlp, stream))
+
+
+def nexel_instance_list(cam, N, ws, ws_bytes, n_instances, tile_out, id_out, depth_out,
+                        stream) -> int:
+    return check("nexel_instance_list", lib().nexel_instance_list(
+        C.byref(cam), N, ws, ws_bytes, n_instances, tile_out, id_out, depth_out, stream))
+
+
+def nexel_launch_count() -> int:
+    return lib().nexel_launch_count()
+
+
+def nexel_profile_enable(on: bool) -> int:
+    return check("nexel_profile_enable", lib().nexel_profile_enable(1 if on else 0))
+
+
+def nexel_profile_read(max_entries: int = 64) -> dict:
+    """{kernel name: (total ms, launches)} of the events recorded so far."""
+    names = C.create_string_buffer(32 * max_entries)
+    ms = (C.c_float * max_entries)()
+    cnt = (C.c_int * max_entries)()
+    n = C.c_int(0)
+    check("nexel_profile_read", lib().nexel_profile_read(max_entries, names, ms, cnt, C.byref(n)))
+    out = {}
+    for k in range(min(n.value, max_entries)):
+        nm = names.raw[32 * k:32 * k + 32].split(b"\0")[0].decode()
+        out[nm] = (float(ms[k]), int(cnt[k]))
+    return out
+
+
+def nexel_status_string(code: int) -> str:
+    return lib().nexel_status_string(code).decode()
+
+
+def nexel_version() -> int:
+    return lib().nexel_version()

@@ -1,0 +1,365 @@
+// C ABI of libnexel: argument checks, workspace layout and the launch
+// sequence of each entry point.
+#include "common.cuh"
+#include "texture_common.cuh"
+
+#include <cmath>
+#include <cstring>
+
+namespace nexel {
+
+static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+static int ceil_log2(long long n) {
+  int b = 0;
+  while ((1LL << b) < n) ++b;
+  return b;
+}
+
+static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
+  L.N = N;
+  L.P = cam.width * cam.height;
+  L.K = 0;
+  int tx = (cam.width + kTile - 1) / kTile, ty = (cam.height + kTile - 1) / kTile;
+  L.n_tiles = tx * ty;
+  L.tile_bits = ceil_log2(L.n_tiles);
+  L.rank_bits = std::max(1, ceil_log2(std::max(N, 2)));
+  L.key64 = (L.tile_bits + L.rank_bits > 32) ? 1 : 0;
+  L.tile_passes = (L.tile_bits + 7) / 8;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += align_up(bytes);
+    return at;
+  };
+  size_t n = (size_t)std::max(N, 1);
+  L.geom_orig = take(n * kRecF4 * 16);
+  L.geom_sorted = take(n * kRecF4 * 16);
+  L.dkey0 = take(n * 4);
+  L.dkey1 = take(n * 4);
+  L.did0 = take(n * 4);
+  L.did1 = take(n * 4);
+  L.rect = take(n * 8);
+  L.count = take(n * 4);
+  L.offs = take((n + 1) * 4);
+  L.ranges = take((size_t)L.n_tiles * 8);
+  L.n_contrib = take((size_t)std::max(L.P, 1) * 4);
+  L.grad_sorted = take(n * kGradStride * 4);
+  L.counters = take(256);
+  L.fixed_end = o;
+}
+
+static void ws_cap(WsLayout& L, long long cap) {
+  L.cap = cap;
+  size_t o = L.fixed_end;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += align_up(bytes);
+    return at;
+  };
+  size_t kb = L.key64 ? 8 : 4;
+  size_t c = (size_t)std::max(cap, 1LL);
+  L.inst0 = take(c * kb);
+  L.inst1 = take(c * kb);
+  long long nb = std::max((c + kSortTile - 1) / kSortTile, ((size_t)L.N + kSortTile - 1) / kSortTile);
+  L.hist = take((size_t)256 * nb * 4);
+  long long scan_n = std::max(256LL * nb, (long long)L.N + 1);
+  L.scan_sums = take(((size_t)(scan_n + kScanTile - 1) / kScanTile + 1) * 4);
+  L.total = o;
+}
+
+WsLayout ws_layout(const nexel_camera& cam, int K, int N, long long cap) {
+  WsLayout L;
+  ws_fixed(cam, N, L);
+  L.K = K;
+  ws_cap(L, cap);
+  return L;
+}
+
+WsLayout ws_layout_for_bytes(const nexel_camera& cam, int K, int N, size_t ws_bytes) {
+  WsLayout L;
+  ws_fixed(cam, N, L);
+  L.K = K;
+  ws_cap(L, 1);
+  if (L.total > ws_bytes) {
+    L.cap = -1;
+    return L;
+  }
+  size_t kb = L.key64 ? 8 : 4;
+  long long cap = (long long)((ws_bytes - L.fixed_end) / (2 * kb + 1));
+  ws_cap(L, cap);
+  while (L.total > ws_bytes && cap > 1) {
+    cap -= std::max(1LL, cap / 1024);
+    ws_cap(L, cap);
+  }
+  if (L.total > ws_bytes) L.cap = -1;
+  return L;
+}
+
+BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim) {
+  // per-sample gradients are indexed p * K + j; the features and texture
+  // gradients by padded row (pixel-major, next power of two >= K rows per
+  // pixel, rounded up to 16-row MMA tiles)
+  BwdLayout B;
+  const size_t P = (size_t)cam.width * cam.height;
+  int KP = 1;
+  while (KP < K) KP <<= 1;
+  const size_t S = P * (size_t)std::max(K, 0);
+  const size_t rows = ((P * (size_t)KP + 15) / 16) * 16;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += align_up(bytes);
+    return at;
+  };
+  B.dweff = take(std::max<size_t>(S, 1) * 4);
+  B.ddepth = take(std::max<size_t>(S, 1) * 4);
+  B.feat = take(std::max<size_t>(rows, 1) * (size_t)std::max(feat_dim, 1) * 4);
+  B.gtex = take(std::max<size_t>(rows, 1) * 16);
+  B.total = o;
+  return B;
+}
+
+DevCam make_devcam(const nexel_camera& cam) {
+  DevCam c;
+  c.W = cam.width;
+  c.H = cam.height;
+  c.tiles_x = (cam.width + kTile - 1) / kTile;
+  c.tiles_y = (cam.height + kTile - 1) / kTile;
+  c.fx = cam.fx; c.fy = cam.fy; c.cx = cam.cx; c.cy = cam.cy;
+  const float* m = cam.world_to_cam;
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) c.R[3 * r + k] = m[4 * r + k];
+    c.t[r] = m[4 * r + 3];
+  }
+  for (int a = 0; a < 3; ++a)
+    c.o[a] = (float)-((double)c.R[a] * c.t[0] + (double)c.R[3 + a] * c.t[1] +
+                      (double)c.R[6 + a] * c.t[2]);
+  c.near_ = cam.near_plane;
+  return c;
+}
+
+// Composite without textures (K = 0): C = N + T_final bg.
+__global__ void k_composite_notex(long long P, float bg0, float bg1, float bg2,
+                                  const float* __restrict__ notex, const float* __restrict__ Tf,
+                                  float* __restrict__ image) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float t = Tf[p];
+  image[3 * p] = notex[3 * p] + t * bg0;
+  image[3 * p + 1] = notex[3 * p + 1] + t * bg1;
+  image[3 * p + 2] = notex[3 * p + 2] + t * bg2;
+}
+
+static bool cam_ok(const nexel_camera* c) {
+  return c && c->width > 0 && c->height > 0 && c->width <= 16384 && c->height <= 16384 &&
+         std::isfinite(c->fx) && std::isfinite(c->fy) && c->fx > 0 && c->fy > 0 &&
+         c->near_plane > 0 && std::isfinite(c->near_plane) &&
+         (long long)((c->width + kTile - 1) / kTile) * ((c->height + kTile - 1) / kTile) < (1 << 24);
+}
+
+static bool settings_ok(const nexel_settings* s) {
+  return s && s->K >= 0 && s->K <= NEXEL_MAX_K && s->alpha_min > 0.f && s->alpha_max > 0.f &&
+         s->alpha_max <= 1.f && s->alpha_min <= s->alpha_max && s->T_min >= 0.f &&
+         s->T_min < 1.f && (s->grid_dtype == NEXEL_F32 || s->grid_dtype == NEXEL_F16) &&
+         (s->mlp_dtype == NEXEL_F32 || s->mlp_dtype == NEXEL_BF16);
+}
+
+static bool field_ok(const nexel_field* f) {
+  if (!f || !f->table || !f->weights) return false;
+  if (f->L <= 0 || f->L > NEXEL_MAX_LEVELS || f->F != 2 || f->T <= 0) return false;
+  if ((f->T & (f->T - 1)) != 0) return false;
+  if (f->n_layers < 2 || f->n_layers > NEXEL_MAX_LAYERS) return false;
+  for (int l = 0; l < f->L; ++l)
+    if (!(f->level_scale[l] > 0.f) || !std::isfinite(f->level_scale[l])) return false;
+  return true;
+}
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? NEXEL_OK : NEXEL_ERR_CUDA; }
+
+template <typename KeyT>
+__global__ void k_instance_list(long long n, int rank_bits, uint32_t rmask,
+                                const KeyT* __restrict__ keys, const uint32_t* __restrict__ did,
+                                const uint32_t* __restrict__ dkey, int* __restrict__ tile_out,
+                                int* __restrict__ id_out, float* __restrict__ depth_out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  KeyT k = keys[i];
+  uint32_t r = (uint32_t)k & rmask;
+  if (tile_out) tile_out[i] = (int)(k >> rank_bits);
+  if (id_out) id_out[i] = (int)did[r];
+  if (depth_out) depth_out[i] = __uint_as_float(dkey[r]);
+}
+
+}  // namespace nexel
+
+using namespace nexel;
+
+extern "C" {
+
+int nexel_version(void) { return 100; }
+
+const char* nexel_status_string(int status) {
+  switch (status) {
+    case NEXEL_OK: return "ok";
+    case NEXEL_ERR_INVALID_ARG: return "invalid argument";
+    case NEXEL_ERR_CUDA: return "CUDA error";
+    case NEXEL_ERR_CAPACITY: return "instance capacity exceeded";
+    case NEXEL_ERR_UNSUPPORTED: return "unsupported configuration";
+    case NEXEL_ERR_TIMEOUT: return "device wait timed out";
+    case NEXEL_ERR_NUMERIC: return "numeric check failed";
+    default: return "unknown status";
+  }
+}
+
+int nexel_workspace_size(const nexel_camera* cam, int N, long long max_instances, size_t* bytes) {
+  if (!cam_ok(cam) || N < 0 || max_instances < 0 || !bytes) return NEXEL_ERR_INVALID_ARG;
+  if (max_instances >= (1LL << 32) - 1) return NEXEL_ERR_UNSUPPORTED;
+  WsLayout L = ws_layout(*cam, 0, N, max_instances);
+  *bytes = L.total;
+  return NEXEL_OK;
+}
+
+int nexel_bwd_workspace_size(const nexel_camera* cam, const nexel_settings* settings,
+                             const nexel_field* field, size_t* bytes) {
+  if (!cam_ok(cam) || !settings_ok(settings) || !bytes) return NEXEL_ERR_INVALID_ARG;
+  int fd = (settings->K > 0 && field) ? field->L * field->F : 0;
+  *bytes = bwd_layout(*cam, settings->K, fd).total;
+  return NEXEL_OK;
+}
+
+int nexel_preprocess(const nexel_camera* cam, const nexel_settings* settings, int N,
+                     const float* mu, const float* quat, const float* scale,
+                     const float* opacity, const float* gamma, const float* color, void* ws,
+                     size_t ws_bytes, long long* n_instances_out, nexel_stream_t stream) {
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !n_instances_out)
+    return NEXEL_ERR_INVALID_ARG;
+  if (N > 0 && (!mu || !quat || !scale || !opacity || !gamma || !color))
+    return NEXEL_ERR_INVALID_ARG;
+  WsLayout L = ws_layout_for_bytes(*cam, settings->K, N, ws_bytes);
+  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevCam c = make_devcam(*cam);
+  char* w = (char*)ws;
+  cudaError_t e = cudaMemsetAsync(w + L.counters, 0, 256, st);
+  if (e == cudaSuccess)
+    e = launch_preprocess(c, *settings, N, mu, quat, scale, opacity, gamma, color, w, L, st);
+  if (e == cudaSuccess) e = launch_depth_sort(N, w, L, st);
+  if (e == cudaSuccess) e = launch_count_scan(N, w, L, st);
+  uint32_t n_inst = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&n_inst, w + L.counters + 4, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
+  *n_instances_out = (long long)n_inst;
+  if ((long long)n_inst > L.cap) return NEXEL_ERR_CAPACITY;
+  return cuda_status(launch_binning(c, N, (long long)n_inst, w, L, st));
+}
+
+int nexel_render_fwd(const nexel_camera* cam, const nexel_settings* settings,
+                     const nexel_field* field, int N, void* ws, size_t ws_bytes, float* image,
+                     float* notex, float* weights, int* ids, float* depths, float* textures,
+                     float* T_final, nexel_stream_t stream) {
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !image || !notex || !T_final)
+    return NEXEL_ERR_INVALID_ARG;
+  const int K = settings->K;
+  if (K > 0 && (!weights || !ids || !depths || !textures)) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !field_ok(field)) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !texture_arch_supported(*settings, *field)) return NEXEL_ERR_UNSUPPORTED;
+  WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
+  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevCam c = make_devcam(*cam);
+  char* w = (char*)ws;
+  cudaError_t e = launch_collect_fwd(c, *settings, w, L, notex, weights, ids, depths, T_final, st);
+  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
+  if (K == 0) {
+    long long P = (long long)cam->width * cam->height;
+    {
+      NEXEL_PROF("composite_notex", st);
+      k_composite_notex<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(
+          P, settings->bg[0], settings->bg[1], settings->bg[2], notex, T_final, image);
+    }
+    return cuda_status(cudaGetLastError());
+  }
+  e = launch_texture_fwd(c, *settings, *field, notex, weights, ids, depths, T_final, image,
+                         textures, st);
+  return cuda_status(e);
+}
+
+int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
+                     const nexel_field* field, int N, const float* mu, const float* quat,
+                     const float* scale, const float* opacity, const float* gamma, void* ws,
+                     size_t ws_bytes, void* bwd_ws, size_t bwd_ws_bytes, const float* weights,
+                     const int* ids, const float* depths, const float* T_final,
+                     const float* d_image, const float* d_weights, const float* d_textures,
+                     int accumulate, float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
+                     float* d_gamma, float* d_color, float* d_table, float* d_mlp,
+                     nexel_stream_t stream) {
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !T_final || !d_image)
+    return NEXEL_ERR_INVALID_ARG;
+  if (!(settings->alpha_max < 1.f)) return NEXEL_ERR_INVALID_ARG;
+  if (N > 0 && (!mu || !quat || !scale || !opacity || !gamma)) return NEXEL_ERR_INVALID_ARG;
+  const int K = settings->K;
+  if (K > 0 && (!weights || !ids || !depths || !bwd_ws)) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !field_ok(field)) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !texture_arch_supported(*settings, *field)) return NEXEL_ERR_UNSUPPORTED;
+  WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
+  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
+  BwdLayout B = bwd_layout(*cam, K, K > 0 ? field->L * field->F : 0);
+  if (K > 0 && bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevCam c = make_devcam(*cam);
+  char* w = (char*)ws;
+  char* bw = (char*)bwd_ws;
+  cudaError_t e = cudaSuccess;
+  if (K > 0) {
+    if (!accumulate) {
+      if (d_table)
+        e = cudaMemsetAsync(d_table, 0, sizeof(float) * (size_t)field->L * field->T * field->F, st);
+      size_t nw = 0;
+      for (int l = 0; l < field->n_layers; ++l) nw += (size_t)field->widths[l] * field->widths[l + 1];
+      if (e == cudaSuccess && d_mlp) e = cudaMemsetAsync(d_mlp, 0, sizeof(float) * nw, st);
+    }
+    if (e == cudaSuccess)
+      e = launch_texture_bwd(c, *settings, *field, bw, B, weights, ids, depths, d_image, d_weights,
+                             d_textures, d_table, d_mlp, st);
+  }
+  if (e == cudaSuccess) e = launch_collect_bwd(c, *settings, w, L, bw, B, ids, T_final, d_image, st);
+  if (e == cudaSuccess)
+    e = launch_preprocess_bwd(c, *settings, N, mu, quat, scale, opacity, gamma, w, L, accumulate,
+                              d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color, st);
+  return cuda_status(e);
+}
+
+int nexel_instance_list(const nexel_camera* cam, int N, const void* ws, size_t ws_bytes,
+                        long long n_instances, int* tile_out, int* id_out, float* depth_out,
+                        nexel_stream_t stream) {
+  if (!cam_ok(cam) || N < 0 || !ws || n_instances < 0) return NEXEL_ERR_INVALID_ARG;
+  WsLayout L = ws_layout_for_bytes(*cam, 0, N, ws_bytes);
+  if (L.cap < 0 || n_instances > L.cap) return NEXEL_ERR_INVALID_ARG;
+  if (n_instances == 0) return NEXEL_OK;
+  const char* w = (const char*)ws;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned grid = (unsigned)((n_instances + 255) / 256);
+  const uint32_t* did = (const uint32_t*)(w + L.did0);
+  const uint32_t* dk = (const uint32_t*)(w + L.dkey0);
+  if (L.key64)
+    {
+      NEXEL_PROF("instance_list", st);
+      k_instance_list<unsigned long long><<<grid, 256, 0, st>>>(
+          n_instances, 32, 0xFFFFFFFFu, (const unsigned long long*)(w + L.inst0), did, dk, tile_out,
+          id_out, depth_out);
+    }
+  else
+    {
+      NEXEL_PROF("instance_list", st);
+      k_instance_list<uint32_t><<<grid, 256, 0, st>>>(n_instances, L.rank_bits,
+                                                      (1u << L.rank_bits) - 1u,
+                                                      (const uint32_t*)(w + L.inst0), did, dk,
+                                                      tile_out, id_out, depth_out);
+    }
+  return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,669 @@
+// Surfel preprocess, tile binning and the two stable radix sorts (centre
+// depth, then tile), plus the preprocess backward.
+//
+// Ordering (Sec. 3, "Preliminaries"): surfels are sorted by the view depth of
+// their centres and composited per tile.  Instead of sorting 64-bit
+// (tile, depth) keys of every (tile, surfel) instance, the N surfels are
+// first sorted by depth (32-bit float keys, index order on ties), the
+// instances are then emitted in depth-rank order, and a stable sort on the
+// tile bits alone finishes the job.  The resulting per-tile lists are
+// identical, bit for bit, to a stable sort of (tile << 32 | depth bits) keys,
+// at a fraction of the key traffic: a key is (tile << rank_bits | rank) in
+// 32 bits whenever tile_bits + rank_bits <= 32.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace nexel {
+
+// ----------------------------------------------------------- float-float
+struct ff { float hi, lo; };
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  ff p = two_prod(a.hi, b);
+  return fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  float q1 = a.hi / b.hi;
+  ff qb = ff_mul_f(b, q1);
+  ff r = ff_add(a, {-qb.hi, -qb.lo});
+  float q2 = r.hi / b.hi;
+  return fast_two_sum(q1, q2);
+}
+
+// Rotation of a (normalised) quaternion (w, x, y, z): columns v1, v2, n.
+__device__ __forceinline__ void quat_cols(float w, float x, float y, float z, float3& v1, float3& v2,
+                                          float3& n) {
+  v1 = make_float3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+  v2 = make_float3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+  n = make_float3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+}
+
+__device__ __forceinline__ float3 rot(const float* R, float3 v) {
+  return make_float3(R[0] * v.x + R[1] * v.y + R[2] * v.z, R[3] * v.x + R[4] * v.y + R[5] * v.z,
+                     R[6] * v.x + R[7] * v.y + R[8] * v.z);
+}
+__device__ __forceinline__ float3 rotT(const float* R, float3 v) {
+  return make_float3(R[0] * v.x + R[3] * v.y + R[6] * v.z, R[1] * v.x + R[4] * v.y + R[7] * v.z,
+                     R[2] * v.x + R[5] * v.y + R[8] * v.z);
+}
+
+// ------------------------------------------------------------ preprocess
+// One thread per surfel.  Builds the packed record (see common.cuh), the
+// depth key and the tile rectangle of the region where alpha >= alpha_min:
+// |u| <= (2 ln(o / alpha_min))^(1 / (2 gamma_1)) and likewise for v, i.e. a
+// rectangle on the surfel plane, clipped to view depth >= near (hits at
+// t* <= near are dropped) and projected; its image is the convex hull of the
+// projected vertices.
+__global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __restrict__ mu,
+                             const float* __restrict__ quat, const float* __restrict__ scale,
+                             const float* __restrict__ opac, const float* __restrict__ gam,
+                             const float* __restrict__ color, float4* __restrict__ geom,
+                             uint32_t* __restrict__ dkey, uint32_t* __restrict__ did,
+                             uint2* __restrict__ rect, uint32_t* __restrict__ count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  did[i] = (uint32_t)i;
+  float m[3] = {mu[3 * i], mu[3 * i + 1], mu[3 * i + 2]};
+  float qw = quat[4 * i], qx = quat[4 * i + 1], qy = quat[4 * i + 2], qz = quat[4 * i + 3];
+  float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  qw *= qn; qx *= qn; qy *= qn; qz *= qn;
+  float3 v1, v2, n;
+  quat_cols(qw, qx, qy, qz, v1, v2, n);
+  float s1 = scale[2 * i], s2 = scale[2 * i + 1];
+  float o = opac[i];
+  float g1 = gam[2 * i], g2 = gam[2 * i + 1];
+  // camera-space centre in float-float (the projected centre is the one
+  // quantity whose absolute error enters every pixel's offset)
+  ff mc[3];
+  for (int a = 0; a < 3; ++a) {
+    ff acc = two_prod(c.R[3 * a], m[0]);
+    acc = ff_add(acc, two_prod(c.R[3 * a + 1], m[1]));
+    acc = ff_add(acc, two_prod(c.R[3 * a + 2], m[2]));
+    mc[a] = ff_add(acc, {c.t[a], 0.f});
+  }
+  float z = mc[2].hi;
+  float3 v1c = rot(c.R, v1), v2c = rot(c.R, v2), nc = rot(c.R, n);
+  bool ok = (z > c.near_) && (o >= alpha_min) && (s1 > 0.f) && (s2 > 0.f) && (g1 >= 1.f) &&
+            (g2 >= 1.f);
+  float dmx = 0.f, dmy = 0.f, dn0 = 0.f;
+  if (ok) {
+    dmx = mc[0].hi / z;
+    dmy = mc[1].hi / z;
+    dn0 = dmx * nc.x + dmy * nc.y + nc.z;
+    ok = fabsf(dn0) >= 1e-7f;  // edge-on to its own centre ray: a line, dropped
+  }
+  uint2 rc = make_uint2(0, 0);
+  uint32_t cnt = 0;
+  if (ok) {
+    // support rectangle, slightly inflated
+    float lr = 2.f * logf(o / alpha_min);
+    float ru = (lr > 0.f ? powf(lr, 0.5f / g1) : 0.f) * 1.001f + 1e-6f;
+    float rv = (lr > 0.f ? powf(lr, 0.5f / g2) : 0.f) * 1.001f + 1e-6f;
+    float3 eu = make_float3(ru * s1 * v1c.x, ru * s1 * v1c.y, ru * s1 * v1c.z);
+    float3 ev = make_float3(rv * s2 * v2c.x, rv * s2 * v2c.y, rv * s2 * v2c.z);
+    float3 ctr = make_float3(mc[0].hi, mc[1].hi, z);
+    float3 P[4];
+    const float su[4] = {-1.f, 1.f, 1.f, -1.f}, sv[4] = {-1.f, -1.f, 1.f, 1.f};
+    for (int k = 0; k < 4; ++k)
+      P[k] = make_float3(ctr.x + su[k] * eu.x + sv[k] * ev.x, ctr.y + su[k] * eu.y + sv[k] * ev.y,
+                         ctr.z + su[k] * eu.z + sv[k] * ev.z);
+    float xmin = 3e38f, xmax = -3e38f, ymin = 3e38f, ymax = -3e38f;
+    int nv = 0;
+    auto take = [&](float3 p) {
+      float iz = 1.f / p.z;
+      float px = c.fx * p.x * iz + c.cx, py = c.fy * p.y * iz + c.cy;
+      xmin = fminf(xmin, px); xmax = fmaxf(xmax, px);
+      ymin = fminf(ymin, py); ymax = fmaxf(ymax, py);
+      ++nv;
+    };
+    for (int k = 0; k < 4; ++k) {
+      float3 A = P[k], B = P[(k + 1) & 3];
+      bool ia = A.z >= c.near_, ib = B.z >= c.near_;
+      if (ia) take(A);
+      if (ia != ib) {
+        float s = (c.near_ - A.z) / (B.z - A.z);
+        float3 X = make_float3(A.x + s * (B.x - A.x), A.y + s * (B.y - A.y), c.near_);
+        take(X);
+      }
+    }
+    if (nv > 0) {
+      // pixel centres (x + .5) inside [xmin, xmax], one pixel of margin
+      float fx0 = fmaxf(xmin - 1.5f, -1e7f), fx1 = fminf(xmax + 0.5f, 1e7f);
+      float fy0 = fmaxf(ymin - 1.5f, -1e7f), fy1 = fminf(ymax + 0.5f, 1e7f);
+      int px0 = max((int)ceilf(fx0), 0), px1 = min((int)floorf(fx1), c.W - 1);
+      int py0 = max((int)ceilf(fy0), 0), py1 = min((int)floorf(fy1), c.H - 1);
+      if (px0 <= px1 && py0 <= py1) {
+        int tx0 = px0 / kTile, tx1 = px1 / kTile, ty0 = py0 / kTile, ty1 = py1 / kTile;
+        rc = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+        cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+      }
+    }
+  }
+  if (cnt == 0) ok = false;
+  rect[i] = rc;
+  count[i] = cnt;
+  dkey[i] = ok ? __float_as_uint(z) : 0xFFFFFFFFu;
+  float4* g = geom + (size_t)i * kRecF4;
+  if (!ok) {
+    for (int k = 0; k < kRecF4; ++k) g[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  // projected centre in float-float: cp = f * (mc / z) + c
+  ff zz = mc[2];
+  ff dx = ff_div(mc[0], zz), dy = ff_div(mc[1], zz);
+  ff cpx = ff_add(ff_mul_f(dx, c.fx), {c.cx, 0.f});
+  ff cpy = ff_add(ff_mul_f(dy, c.fy), {c.cy, 0.f});
+  // per-pixel-unit plane tilt and in-plane gradients (derivation in the
+  // backward kernel below)
+  float ax = v1c.x / s1, ay = v1c.y / s1, az = v1c.z / s1;
+  float bx = v2c.x / s2, by = v2c.y / s2, bz = v2c.z / s2;
+  float ad = dmx * ax + dmy * ay + az;
+  float bd = dmx * bx + dmy * by + bz;
+  float ra = ad / dn0, rb = bd / dn0;
+  float Ax = (ax - nc.x * ra) / c.fx, Ay = (ay - nc.y * ra) / c.fy;
+  float Bx = (bx - nc.x * rb) / c.fx, By = (by - nc.y * rb) / c.fy;
+  float nx = nc.x / (c.fx * dn0), ny = nc.y / (c.fy * dn0);
+  g[0] = make_float4(cpx.hi, cpy.hi, cpx.lo, cpy.lo);
+  g[1] = make_float4(z, o, g1, g2);
+  g[2] = make_float4(nx, ny, Ax, Ay);
+  g[3] = make_float4(Bx, By, 0.f, 0.f);
+  g[4] = make_float4(color[3 * i], color[3 * i + 1], color[3 * i + 2], __uint_as_float((uint32_t)i));
+}
+
+// ------------------------------------------------------- scan (exclusive)
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_w, uint32_t& total) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int nw = blockDim.x >> 5;
+    uint32_t y = lane < nw ? s_w[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t z = __shfl_up_sync(0xffffffffu, y, d);
+      if (lane >= d) y += z;
+    }
+    if (lane < nw) s_w[lane] = y;
+  }
+  __syncthreads();
+  uint32_t pre = warp > 0 ? s_w[warp - 1] : 0;
+  total = s_w[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return pre + x - v;
+}
+
+// Each block scans kScanTile consecutive elements in place.
+__global__ void __launch_bounds__(256) k_scan_partial(uint32_t* __restrict__ a, long long n,
+                                                      uint32_t* __restrict__ sums) {
+  __shared__ uint32_t s_w[8];
+  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t loc = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? a[base + k] : 0u;
+    loc += v[k];
+  }
+  uint32_t tot;
+  uint32_t pre = block_excl_scan(loc, s_w, tot);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) a[base + k] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(uint32_t* __restrict__ sums, int nb,
+                                                    uint32_t* __restrict__ total_out) {
+  __shared__ uint32_t s_w[32];
+  uint32_t carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += 1024) {
+    int i = b0 + threadIdx.x;
+    uint32_t v = i < nb ? sums[i] : 0u;
+    uint32_t tot;
+    uint32_t pre = block_excl_scan(v, s_w, tot);
+    if (i < nb) sums[i] = carry + pre;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(uint32_t* __restrict__ a, long long n,
+                                                  const uint32_t* __restrict__ sums) {
+  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  uint32_t add = sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) a[base + k] += add;
+}
+
+static cudaError_t excl_scan(uint32_t* a, long long n, uint32_t* sums, uint32_t* total,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int nb = (int)((n + kScanTile - 1) / kScanTile);
+  {
+    NEXEL_PROF("scan_partial", st);
+    k_scan_partial<<<nb, 256, 0, st>>>(a, n, sums);
+  }
+  {
+    NEXEL_PROF("scan_sums", st);
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, nb, total);
+  }
+  {
+    NEXEL_PROF("scan_add", st);
+    k_scan_add<<<nb, 256, 0, st>>>(a, n, sums);
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- radix sort
+// Stable LSD radix sort, reduce-then-scan: per pass a per-block digit
+// histogram, one exclusive scan over (digit, block), and a scatter that ranks
+// keys stably inside the block (warp match + per-warp digit counts), stages
+// them in shared memory in digit order and writes runs out coalesced.
+template <typename KeyT>
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const KeyT* __restrict__ keys,
+                                                             long long n, int shift, int bits,
+                                                             uint32_t* __restrict__ hist,
+                                                             int nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t mask = (1u << bits) - 1u;
+  long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int k = 0; k < kSortItems; ++k) {
+    long long i = base + (long long)k * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & mask], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < (1 << bits)) hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename KeyT, bool kVal>
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const KeyT* __restrict__ kin, KeyT* __restrict__ kout, const uint32_t* __restrict__ vin,
+    uint32_t* __restrict__ vout, long long n, int shift, int bits,
+    const uint32_t* __restrict__ offs, int nblocks) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  KeyT* s_key = reinterpret_cast<KeyT*>(smem);
+  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);
+  __shared__ uint32_t s_start[256], s_run[256], s_w[8];
+  __shared__ uint32_t s_wc[kSortThreads / 32][256];
+  const int nbins = 1 << bits;
+  const uint32_t mask = (uint32_t)nbins - 1u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long base = (long long)blockIdx.x * kSortTile;
+  const int nloc = (int)min((long long)kSortTile, n - base);
+  for (int b = threadIdx.x; b < 256 * (kSortThreads / 32); b += kSortThreads)
+    (&s_wc[0][0])[b] = 0;
+  s_run[threadIdx.x] = 0;
+  __syncthreads();
+  KeyT key[kSortItems];
+  uint32_t val[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    int li = k * kSortThreads + threadIdx.x;
+    if (li < nloc) {
+      key[k] = kin[base + li];
+      if (kVal) val[k] = vin[base + li];
+      atomicAdd(&s_run[(uint32_t)(key[k] >> shift) & mask], 1u);
+    }
+  }
+  __syncthreads();
+  uint32_t tot;
+  uint32_t st0 = block_excl_scan(s_run[threadIdx.x], s_w, tot);
+  s_start[threadIdx.x] = st0;
+  s_run[threadIdx.x] = st0;
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    int li = k * kSortThreads + threadIdx.x;
+    bool valid = li < nloc;
+    uint32_t d = valid ? ((uint32_t)(key[k] >> shift) & mask) : 0xFFFFFFFFu;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t r = __popc(peers & lt);
+    if (valid && (peers & lt) == 0) s_wc[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = s_run[d] + r;
+      for (int w = 0; w < warp; ++w) pos += s_wc[w][d];
+      s_key[pos] = key[k];
+      if (kVal) s_val[pos] = val[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < nbins) {
+      uint32_t t2 = 0;
+#pragma unroll
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        t2 += s_wc[w][threadIdx.x];
+        s_wc[w][threadIdx.x] = 0;
+      }
+      s_run[threadIdx.x] += t2;
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < nloc; j += kSortThreads) {
+    KeyT kk = s_key[j];
+    uint32_t d = (uint32_t)(kk >> shift) & mask;
+    size_t g = (size_t)offs[(size_t)d * nblocks + blockIdx.x] + (j - s_start[d]);
+    kout[g] = kk;
+    if (kVal) vout[g] = s_val[j];
+  }
+}
+
+// Sorts n keys (and values when vin != nullptr) on bits [lo, lo + nbits).
+// Returns the index (0 or 1) of the buffer pair that holds the result.
+template <typename KeyT>
+static cudaError_t radix_sort(KeyT* k0, KeyT* k1, uint32_t* v0, uint32_t* v1, long long n, int lo,
+                              int nbits, uint32_t* hist, uint32_t* sums, cudaStream_t st,
+                              int* which) {
+  *which = 0;
+  if (n <= 1 || nbits <= 0) return cudaSuccess;
+  int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+  KeyT* kin = k0; KeyT* kout = k1;
+  uint32_t* vin = v0; uint32_t* vout = v1;
+  size_t smem = (size_t)kSortTile * (sizeof(KeyT) + (v0 ? sizeof(uint32_t) : 0));
+  for (int b = 0; b < nbits; b += 8) {
+    int bits = std::min(8, nbits - b);
+    int shift = lo + b;
+    {
+      NEXEL_PROF("radix_hist", st);
+      k_radix_hist<KeyT><<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, bits, hist, nblocks);
+    }
+    cudaError_t e = excl_scan(hist, (long long)(1 << bits) * nblocks, sums, nullptr, st);
+    if (e != cudaSuccess) return e;
+    if (v0) {
+      {
+        NEXEL_PROF("radix_scatter", st);
+        k_radix_scatter<KeyT, true><<<nblocks, kSortThreads, smem, st>>>(kin, kout, vin, vout, n,
+                                                                          shift, bits, hist, nblocks);
+      }
+    } else {
+      {
+        NEXEL_PROF("radix_scatter", st);
+        k_radix_scatter<KeyT, false><<<nblocks, kSortThreads, smem, st>>>(
+            kin, kout, nullptr, nullptr, n, shift, bits, hist, nblocks);
+      }
+    }
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+    *which ^= 1;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- permutation, duplicate, ranges
+__global__ void k_permute(int N, const uint32_t* __restrict__ did, const float4* __restrict__ geom,
+                          float4* __restrict__ geom_sorted, const uint32_t* __restrict__ count,
+                          uint32_t* __restrict__ offs) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  uint32_t id = did[r];
+  const float4* s = geom + (size_t)id * kRecF4;
+  float4* d = geom_sorted + (size_t)r * kRecF4;
+#pragma unroll
+  for (int k = 0; k < kRecF4; ++k) d[k] = s[k];
+  offs[r] = count[id];
+}
+
+template <typename KeyT>
+__global__ void k_duplicate(int N, int tiles_x, int rank_bits, const uint32_t* __restrict__ did,
+                            const uint2* __restrict__ rect, const uint32_t* __restrict__ offs,
+                            const uint32_t* __restrict__ count, KeyT* __restrict__ keys) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  uint32_t id = did[r];
+  if (count[id] == 0) return;
+  uint2 rc = rect[id];
+  int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  size_t o = offs[r];
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      KeyT tile = (KeyT)(ty * tiles_x + tx);
+      keys[o++] = (tile << rank_bits) | (KeyT)r;
+    }
+}
+
+template <typename KeyT>
+__global__ void k_ranges(long long n, int rank_bits, const KeyT* __restrict__ keys,
+                         uint2* __restrict__ ranges) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t t = (uint32_t)(keys[i] >> rank_bits);
+  if (i == 0 || (uint32_t)(keys[i - 1] >> rank_bits) != t) ranges[t].x = (uint32_t)i;
+  if (i == n - 1 || (uint32_t)(keys[i + 1] >> rank_bits) != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+// ------------------------------------------------------------- launchers
+cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, const float* mu,
+                              const float* quat, const float* scale, const float* opacity,
+                              const float* gamma, const float* color, char* ws,
+                              const WsLayout& L, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  {
+    NEXEL_PROF("preprocess", st);
+    k_preprocess<<<(N + 255) / 256, 256, 0, st>>>(
+        c, s.alpha_min, N, mu, quat, scale, opacity, gamma, color, (float4*)(ws + L.geom_orig),
+        (uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.did0), (uint2*)(ws + L.rect),
+        (uint32_t*)(ws + L.count));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_depth_sort(int N, char* ws, const WsLayout& L, cudaStream_t st) {
+  int which = 0;
+  cudaError_t e = radix_sort<uint32_t>((uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.dkey1),
+                                       (uint32_t*)(ws + L.did0), (uint32_t*)(ws + L.did1), N, 0,
+                                       32, (uint32_t*)(ws + L.hist), (uint32_t*)(ws + L.scan_sums),
+                                       st, &which);
+  // 4 passes: the result is back in buffer 0
+  (void)which;
+  return e;
+}
+
+cudaError_t launch_count_scan(int N, char* ws, const WsLayout& L, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  {
+    NEXEL_PROF("permute", st);
+    k_permute<<<(N + 255) / 256, 256, 0, st>>>(N, (uint32_t*)(ws + L.did0),
+                                               (float4*)(ws + L.geom_orig),
+                                               (float4*)(ws + L.geom_sorted),
+                                               (uint32_t*)(ws + L.count), (uint32_t*)(ws + L.offs));
+  }
+  uint32_t* counters = (uint32_t*)(ws + L.counters);
+  return excl_scan((uint32_t*)(ws + L.offs), N, (uint32_t*)(ws + L.scan_sums), counters + 1, st);
+}
+
+template <typename KeyT>
+static cudaError_t binning_t(const DevCam& c, int N, long long n_inst, char* ws, const WsLayout& L,
+                             cudaStream_t st) {
+  // The duplicate step writes into the buffer that makes the last sort pass
+  // land in inst0, which is where the collection kernels read.
+  int passes = (n_inst > 1) ? L.tile_passes : 0;
+  KeyT* k0 = (KeyT*)(ws + ((passes & 1) ? L.inst1 : L.inst0));
+  KeyT* k1 = (KeyT*)(ws + ((passes & 1) ? L.inst0 : L.inst1));
+  int rb = L.key64 ? 32 : L.rank_bits;
+  {
+    NEXEL_PROF("duplicate", st);
+    k_duplicate<KeyT><<<(N + 255) / 256, 256, 0, st>>>(
+        N, c.tiles_x, rb, (uint32_t*)(ws + L.did0), (uint2*)(ws + L.rect),
+        (uint32_t*)(ws + L.offs), (uint32_t*)(ws + L.count), k0);
+  }
+  int which = 0;
+  cudaError_t e = radix_sort<KeyT>(k0, k1, nullptr, nullptr, n_inst, rb, L.tile_bits,
+                                   (uint32_t*)(ws + L.hist), (uint32_t*)(ws + L.scan_sums), st,
+                                   &which);
+  if (e != cudaSuccess) return e;
+  KeyT* res = which ? k1 : k0;
+  if ((char*)res != ws + L.inst0) return cudaErrorUnknown;
+  e = cudaMemsetAsync(ws + L.ranges, 0, sizeof(uint2) * (size_t)L.n_tiles, st);
+  if (e != cudaSuccess) return e;
+  if (n_inst > 0)
+    {
+      NEXEL_PROF("tile_ranges", st);
+      k_ranges<KeyT><<<(unsigned)((n_inst + 255) / 256), 256, 0, st>>>(n_inst, rb, res,
+                                                                      (uint2*)(ws + L.ranges));
+    }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_binning(const DevCam& c, int N, long long n_inst, char* ws, const WsLayout& L,
+                           cudaStream_t st) {
+  if (L.key64) return binning_t<unsigned long long>(c, N, n_inst, ws, L, st);
+  return binning_t<uint32_t>(c, N, n_inst, ws, L, st);
+}
+
+// ------------------------------------------------------ preprocess backward
+// Chain rule from the packed-record gradients (rank order, written by the
+// collection backward) to mu, q (through the normalisation), sigma, o,
+// gamma and colour.  Forward relations, per surfel (camera space):
+//   mc = Rc mu + t, (v1c, v2c, nc) = Rc (v1, v2, n), z = mc.z,
+//   dm = (mc.x / z, mc.y / z, 1), cp = (fx dm.x + cx, fy dm.y + cy),
+//   dn0 = dm . nc, nx = nc.x / (fx dn0), ny = nc.y / (fy dn0),
+//   a = v1c / s1, ra = (dm . a) / dn0, A = ((a.x - nc.x ra) / fx, (a.y - nc.y ra) / fy),
+//   likewise B with v2c / s2.
+__global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ mu,
+                                 const float* __restrict__ quat, const float* __restrict__ scale,
+                                 const float* __restrict__ opac, const float* __restrict__ gam,
+                                 const uint32_t* __restrict__ did, const uint32_t* __restrict__ dkey,
+                                 const float* __restrict__ gs, float* __restrict__ d_mu,
+                                 float* __restrict__ d_quat, float* __restrict__ d_scale,
+                                 float* __restrict__ d_opac, float* __restrict__ d_gamma,
+                                 float* __restrict__ d_color) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  if (dkey[r] == 0xFFFFFFFFu) return;  // culled: no gradient
+  uint32_t i = did[r];
+  const float* g = gs + (size_t)r * kGradStride;
+  float g_cpx = g[0], g_cpy = g[1], g_z = g[2], g_o = g[3], g_g1 = g[4], g_g2 = g[5];
+  float g_nx = g[6], g_ny = g[7], g_Ax = g[8], g_Ay = g[9], g_Bx = g[10], g_By = g[11];
+  float m[3] = {mu[3 * i], mu[3 * i + 1], mu[3 * i + 2]};
+  float q0 = quat[4 * i], q1 = quat[4 * i + 1], q2 = quat[4 * i + 2], q3 = quat[4 * i + 3];
+  float qn = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  float w = q0 * qn, x = q1 * qn, y = q2 * qn, zq = q3 * qn;
+  float3 v1, v2, n;
+  quat_cols(w, x, y, zq, v1, v2, n);
+  float s1 = scale[2 * i], s2 = scale[2 * i + 1];
+  float3 mcv = rot(c.R, make_float3(m[0], m[1], m[2]));
+  mcv.x += c.t[0]; mcv.y += c.t[1]; mcv.z += c.t[2];
+  float3 v1c = rot(c.R, v1), v2c = rot(c.R, v2), nc = rot(c.R, n);
+  float z = mcv.z;
+  float dmx = mcv.x / z, dmy = mcv.y / z;
+  float dn0 = dmx * nc.x + dmy * nc.y + nc.z;
+  float3 a = make_float3(v1c.x / s1, v1c.y / s1, v1c.z / s1);
+  float3 b = make_float3(v2c.x / s2, v2c.y / s2, v2c.z / s2);
+  float ad = dmx * a.x + dmy * a.y + a.z, bd = dmx * b.x + dmy * b.y + b.z;
+  float ra = ad / dn0, rb = bd / dn0;
+  float nxv = nc.x / (c.fx * dn0), nyv = nc.y / (c.fy * dn0);
+  // backward
+  float gApx = g_Ax / c.fx, gApy = g_Ay / c.fy, gBpx = g_Bx / c.fx, gBpy = g_By / c.fy;
+  float3 g_a = make_float3(gApx, gApy, 0.f), g_b = make_float3(gBpx, gBpy, 0.f);
+  float3 g_nc = make_float3(-gApx * ra - gBpx * rb, -gApy * ra - gBpy * rb, 0.f);
+  float g_ra = -(gApx * nc.x + gApy * nc.y), g_rb = -(gBpx * nc.x + gBpy * nc.y);
+  float g_ad = g_ra / dn0, g_bd = g_rb / dn0;
+  float g_dn0 = -(g_ra * ra + g_rb * rb) / dn0;
+  g_a.x += g_ad * dmx; g_a.y += g_ad * dmy; g_a.z += g_ad;
+  g_b.x += g_bd * dmx; g_b.y += g_bd * dmy; g_b.z += g_bd;
+  float g_dmx = g_ad * a.x + g_bd * b.x, g_dmy = g_ad * a.y + g_bd * b.y;
+  // nx = nc.x / (fx dn0)
+  g_nc.x += g_nx / (c.fx * dn0);
+  g_nc.y += g_ny / (c.fy * dn0);
+  g_dn0 += -(g_nx * nxv + g_ny * nyv) / dn0;
+  // dn0 = dm . nc
+  g_dmx += g_dn0 * nc.x; g_dmy += g_dn0 * nc.y;
+  g_nc.x += g_dn0 * dmx; g_nc.y += g_dn0 * dmy; g_nc.z += g_dn0;
+  // cp
+  g_dmx += c.fx * g_cpx;
+  g_dmy += c.fy * g_cpy;
+  // dm = mc.xy / z, z = mc.z
+  float3 g_mc = make_float3(g_dmx / z, g_dmy / z, g_z - (g_dmx * mcv.x + g_dmy * mcv.y) / (z * z));
+  // a = v1c / s1
+  float3 g_v1c = make_float3(g_a.x / s1, g_a.y / s1, g_a.z / s1);
+  float3 g_v2c = make_float3(g_b.x / s2, g_b.y / s2, g_b.z / s2);
+  float g_s1 = -(g_a.x * a.x + g_a.y * a.y + g_a.z * a.z) / s1;
+  float g_s2 = -(g_b.x * b.x + g_b.y * b.y + g_b.z * b.z) / s2;
+  float3 g_m = rotT(c.R, g_mc);
+  float3 g_v1 = rotT(c.R, g_v1c), g_v2 = rotT(c.R, g_v2c), g_n = rotT(c.R, g_nc);
+  // rotation of the unit quaternion: G[row][col] with columns v1, v2, n
+  float G[9] = {g_v1.x, g_v2.x, g_n.x, g_v1.y, g_v2.y, g_n.y, g_v1.z, g_v2.z, g_n.z};
+  float gw = G[1] * (-2 * zq) + G[2] * (2 * y) + G[3] * (2 * zq) + G[5] * (-2 * x) +
+             G[6] * (-2 * y) + G[7] * (2 * x);
+  float gx = G[1] * (2 * y) + G[2] * (2 * zq) + G[3] * (2 * y) + G[4] * (-4 * x) +
+             G[5] * (-2 * w) + G[6] * (2 * zq) + G[7] * (2 * w) + G[8] * (-4 * x);
+  float gy = G[0] * (-4 * y) + G[1] * (2 * x) + G[2] * (2 * w) + G[3] * (2 * x) + G[5] * (2 * zq) +
+             G[6] * (-2 * w) + G[7] * (2 * zq) + G[8] * (-4 * y);
+  float gz = G[0] * (-4 * zq) + G[1] * (-2 * w) + G[2] * (2 * x) + G[3] * (2 * w) +
+             G[4] * (-4 * zq) + G[5] * (2 * y) + G[6] * (2 * x) + G[7] * (2 * y);
+  float dot = w * gw + x * gx + y * gy + zq * gz;
+  if (d_mu) {
+    d_mu[3 * i] += g_m.x; d_mu[3 * i + 1] += g_m.y; d_mu[3 * i + 2] += g_m.z;
+  }
+  if (d_quat) {
+    d_quat[4 * i] += (gw - w * dot) * qn;
+    d_quat[4 * i + 1] += (gx - x * dot) * qn;
+    d_quat[4 * i + 2] += (gy - y * dot) * qn;
+    d_quat[4 * i + 3] += (gz - zq * dot) * qn;
+  }
+  if (d_scale) { d_scale[2 * i] += g_s1; d_scale[2 * i + 1] += g_s2; }
+  if (d_opac) d_opac[i] += g_o;
+  if (d_gamma) { d_gamma[2 * i] += g_g1; d_gamma[2 * i + 1] += g_g2; }
+  if (d_color) {
+    d_color[3 * i] += g[12]; d_color[3 * i + 1] += g[13]; d_color[3 * i + 2] += g[14];
+  }
+  (void)opac; (void)gam;
+}
+
+cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int N, const float* mu,
+                                  const float* quat, const float* scale, const float* opacity,
+                                  const float* gamma, char* ws, const WsLayout& L, int accumulate,
+                                  float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
+                                  float* d_gamma, float* d_color, cudaStream_t st) {
+  (void)s;
+  if (N <= 0) return cudaSuccess;
+  if (!accumulate) {
+    cudaError_t e = cudaSuccess;
+    if (d_mu) e = cudaMemsetAsync(d_mu, 0, sizeof(float) * 3 * (size_t)N, st);
+    if (e == cudaSuccess && d_quat) e = cudaMemsetAsync(d_quat, 0, sizeof(float) * 4 * (size_t)N, st);
+    if (e == cudaSuccess && d_scale) e = cudaMemsetAsync(d_scale, 0, sizeof(float) * 2 * (size_t)N, st);
+    if (e == cudaSuccess && d_opacity) e = cudaMemsetAsync(d_opacity, 0, sizeof(float) * (size_t)N, st);
+    if (e == cudaSuccess && d_gamma) e = cudaMemsetAsync(d_gamma, 0, sizeof(float) * 2 * (size_t)N, st);
+    if (e == cudaSuccess && d_color) e = cudaMemsetAsync(d_color, 0, sizeof(float) * 3 * (size_t)N, st);
+    if (e != cudaSuccess) return e;
+  }
+  {
+    NEXEL_PROF("preprocess_bwd", st);
+    k_preprocess_bwd<<<(N + 255) / 256, 256, 0, st>>>(
+        c, N, mu, quat, scale, opacity, gamma, (uint32_t*)(ws + L.did0), (uint32_t*)(ws + L.dkey0),
+        (float*)(ws + L.grad_sorted), d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nexel

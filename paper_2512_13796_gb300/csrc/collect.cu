@@ -1,0 +1,332 @@
+// Collection pass (Sec. 4.2) forward and backward.
+//
+// One CTA per 16x16 tile, one thread per pixel.  The tile's surfel list (in
+// centre-depth order) is streamed through shared memory in batches of 256
+// packed records; every thread walks the batch front to back, evaluates the
+// ray-surfel intersection and the generalised-Gaussian opacity, composites
+// (Eq. 1) and keeps a register-resident top-K buffer of (weight, rank, depth)
+// sorted by descending weight.  A surfel that is not (or no longer) among
+// the K goes into the non-textured render N (Eq. 5).
+//
+// The backward replays each pixel's list back to front from its last
+// composited surfel, restoring T_i = T_{i+1} / (1 - alpha_i), and carries the
+// weighted colour of everything behind (R) so that
+// dL/dalpha_i = T_i (e_i - R_i), where e_i is the colour-side gradient of
+// surfel i: c_i . dL/dC if it is not textured, dL/dW_j if it fills slot j.
+// Per-surfel gradients are pre-reduced across the warp with shuffles and
+// added to the rank-ordered gradient records with one atomic per value.
+#include "common.cuh"
+
+namespace nexel {
+
+template <typename KeyT>
+__device__ __forceinline__ uint32_t rank_of(KeyT k, uint32_t mask) {
+  return (uint32_t)k & mask;
+}
+
+template <int K, typename KeyT>
+__global__ void __launch_bounds__(kTilePix) k_collect_fwd(
+    DevCam c, float alpha_min, float alpha_max, float T_min, uint32_t rmask,
+    const uint2* __restrict__ ranges, const KeyT* __restrict__ keys,
+    const float4* __restrict__ recs, float* __restrict__ notex, float* __restrict__ weights,
+    int* __restrict__ ids, float* __restrict__ depths, float* __restrict__ T_final,
+    int* __restrict__ n_contrib) {
+  __shared__ float4 s_rec[kRecF4][kTilePix];
+  __shared__ uint32_t s_rank[kTilePix];
+  const int tile = blockIdx.x;
+  const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
+  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+  const int py = ty * kTile + (threadIdx.x / kTile);
+  const bool inside = px < c.W && py < c.H;
+  const float fpx = px + 0.5f, fpy = py + 0.5f;
+  const uint2 rg = ranges[tile];
+  float T = 1.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+  float Wk[K > 0 ? K : 1], Dk[K > 0 ? K : 1];
+  int Rk[K > 0 ? K : 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { Wk[k] = 0.f; Dk[k] = 0.f; Rk[k] = -1; }
+  int last = 0;
+  bool done = !inside;
+  for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kTilePix) {
+    if (__syncthreads_count(done) == kTilePix) break;
+    uint32_t i = b0 + threadIdx.x;
+    if (i < rg.y) {
+      uint32_t r = rank_of(keys[i], rmask);
+      s_rank[threadIdx.x] = r;
+      const float4* src = recs + (size_t)r * kRecF4;
+#pragma unroll
+      for (int k = 0; k < kRecF4; ++k) s_rec[k][threadIdx.x] = __ldg(src + k);
+    }
+    __syncthreads();
+    const int nb = (int)min((uint32_t)kTilePix, rg.y - b0);
+    if (!done) {
+      for (int j = 0; j < nb; ++j) {
+        const float4 q0 = s_rec[0][j], q1 = s_rec[1][j], q2 = s_rec[2][j], q3 = s_rec[3][j];
+        Hit h;
+        if (!eval_surfel(q0, q1, q2, q3, fpx, fpy, c.near_, alpha_min, h)) continue;
+        const float a = fminf(h.alpha, alpha_max);
+        const float test = T * (1.f - a);
+        if (test < T_min) { done = true; break; }
+        const float w = a * T;
+        if constexpr (K > 0) {
+          if (w > Wk[K - 1]) {
+            if (Rk[K - 1] >= 0) {  // evicted: back into N
+              float4 ce = __ldg(recs + (size_t)Rk[K - 1] * kRecF4 + 4);
+              n0 = fmaf(Wk[K - 1], ce.x, n0); n1 = fmaf(Wk[K - 1], ce.y, n1); n2 = fmaf(Wk[K - 1], ce.z, n2);
+            }
+            Wk[K - 1] = w; Rk[K - 1] = (int)s_rank[j]; Dk[K - 1] = h.t;
+#pragma unroll
+            for (int k = K - 1; k > 0; --k) {
+              if (Wk[k] > Wk[k - 1]) {
+                float tw = Wk[k]; Wk[k] = Wk[k - 1]; Wk[k - 1] = tw;
+                float td = Dk[k]; Dk[k] = Dk[k - 1]; Dk[k - 1] = td;
+                int tr = Rk[k]; Rk[k] = Rk[k - 1]; Rk[k - 1] = tr;
+              }
+            }
+          } else {
+            const float4 q4 = s_rec[4][j];
+            n0 = fmaf(w, q4.x, n0); n1 = fmaf(w, q4.y, n1); n2 = fmaf(w, q4.z, n2);
+          }
+        } else {
+          const float4 q4 = s_rec[4][j];
+          n0 = fmaf(w, q4.x, n0); n1 = fmaf(w, q4.y, n1); n2 = fmaf(w, q4.z, n2);
+        }
+        T = test;
+        last = (int)(b0 - rg.x) + j + 1;
+      }
+    }
+  }
+  if (!inside) return;
+  const size_t p = (size_t)py * c.W + px;
+  notex[3 * p] = n0; notex[3 * p + 1] = n1; notex[3 * p + 2] = n2;
+  T_final[p] = T;
+  n_contrib[p] = last;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int id = -1;
+    if (Rk[k] >= 0) id = (int)__float_as_uint(__ldg(recs + (size_t)Rk[k] * kRecF4 + 4).w);
+    weights[p * K + k] = Wk[k];
+    ids[p * K + k] = id;
+    depths[p * K + k] = Dk[k];
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+template <int K, typename KeyT>
+__global__ void __launch_bounds__(kTilePix) k_collect_bwd(
+    DevCam c, float alpha_min, float alpha_max, float bg0, float bg1, float bg2, uint32_t rmask,
+    const uint2* __restrict__ ranges, const KeyT* __restrict__ keys,
+    const float4* __restrict__ recs, const int* __restrict__ ids, const float* __restrict__ T_final,
+    const int* __restrict__ n_contrib, const float* __restrict__ d_image,
+    const float* __restrict__ dweff, const float* __restrict__ ddepth,
+    float* __restrict__ grad) {
+  __shared__ float4 s_rec[kRecF4][kTilePix];
+  __shared__ uint32_t s_rank[kTilePix];
+  __shared__ int s_max;
+  const int tile = blockIdx.x;
+  const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
+  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+  const int py = ty * kTile + (threadIdx.x / kTile);
+  const bool inside = px < c.W && py < c.H;
+  const float fpx = px + 0.5f, fpy = py + 0.5f;
+  const uint2 rg = ranges[tile];
+  const size_t p = inside ? (size_t)py * c.W + px : 0;
+  float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
+  int last = 0;
+  int Ik[K > 0 ? K : 1];
+  float dWe[K > 0 ? K : 1], dDk[K > 0 ? K : 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) { Ik[k] = -1; dWe[k] = 0.f; dDk[k] = 0.f; }
+  if (inside) {
+    T = T_final[p];
+    last = n_contrib[p];
+    dC0 = d_image[3 * p]; dC1 = d_image[3 * p + 1]; dC2 = d_image[3 * p + 2];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      Ik[k] = ids[p * K + k];
+      dWe[k] = dweff[p * K + k];
+      dDk[k] = ddepth[p * K + k];
+    }
+  }
+  float R = bg0 * dC0 + bg1 * dC1 + bg2 * dC2;  // background behind everything
+  if (threadIdx.x == 0) s_max = 0;
+  __syncthreads();
+  atomicMax(&s_max, last);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t list_end = rg.x + (uint32_t)s_max;
+  for (uint32_t bend = list_end; bend > rg.x;) {
+    const uint32_t bstart = (bend - rg.x > (uint32_t)kTilePix) ? bend - kTilePix : rg.x;
+    __syncthreads();
+    uint32_t i = bstart + threadIdx.x;
+    if (i < bend) {
+      uint32_t r = rank_of(keys[i], rmask);
+      s_rank[threadIdx.x] = r;
+      const float4* src = recs + (size_t)r * kRecF4;
+#pragma unroll
+      for (int k = 0; k < kRecF4; ++k) s_rec[k][threadIdx.x] = __ldg(src + k);
+    }
+    __syncthreads();
+    for (int j = (int)(bend - bstart) - 1; j >= 0; --j) {
+      const int pos = (int)(bstart - rg.x) + j;
+      const float4 q0 = s_rec[0][j], q1 = s_rec[1][j], q2 = s_rec[2][j], q3 = s_rec[3][j];
+      Hit h;
+      bool ok = pos < last && eval_surfel(q0, q1, q2, q3, fpx, fpy, c.near_, alpha_min, h);
+      if (!__any_sync(0xffffffffu, ok)) continue;
+      float g[15];
+#pragma unroll
+      for (int k = 0; k < 15; ++k) g[k] = 0.f;
+      if (ok) {
+        const float4 q4 = s_rec[4][j];
+        const float a = fminf(h.alpha, alpha_max);
+        const bool clamped = h.alpha > alpha_max;
+        T = T / (1.f - a);
+        const int id = (int)__float_as_uint(q4.w);
+        int slot = -1;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (Ik[k] == id) slot = k;
+        float e, dt = 0.f;
+        if (slot >= 0) {
+          float ew = 0.f, ed = 0.f;
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            if (k == slot) { ew = dWe[k]; ed = dDk[k]; }
+          e = ew;
+          dt = ed;
+        } else {
+          e = q4.x * dC0 + q4.y * dC1 + q4.z * dC2;
+          const float w = a * T;
+          g[12] = w * dC0; g[13] = w * dC1; g[14] = w * dC2;
+        }
+        const float da = T * (e - R);
+        R = a * e + (1.f - a) * R;
+        float du = 0.f, dv = 0.f;
+        if (!clamped) {
+          const float al = h.alpha;
+          g[3] = da * al / q1.y;
+          const float cpa = -da * al;  // dL/d(pu) * 2 = -dalpha * alpha
+          if (h.u != 0.f) {
+            du = cpa * q1.z * h.pu / h.u;
+            g[4] = cpa * h.pu * logf(fabsf(h.u));
+          }
+          if (h.v != 0.f) {
+            dv = cpa * q1.w * h.pv / h.v;
+            g[5] = cpa * h.pv * logf(fabsf(h.v));
+          }
+        }
+        dt += du * h.ut + dv * h.vt;
+        const float dut = du * h.t, dvt = dv * h.t;
+        g[8] = dut * h.dx; g[9] = dut * h.dy;
+        g[10] = dvt * h.dx; g[11] = dvt * h.dy;
+        float ddx = dut * q2.z + dvt * q3.x, ddy = dut * q2.w + dvt * q3.y;
+        g[2] = dt / h.den;
+        const float dden = -dt * h.t / h.den;
+        g[6] = dden * h.dx; g[7] = dden * h.dy;
+        ddx += dden * q2.x; ddy += dden * q2.y;
+        g[0] = -ddx; g[1] = -ddy;
+      }
+#pragma unroll
+      for (int k = 0; k < 15; ++k) g[k] = warp_sum(g[k]);
+      if (lane == 0) {
+        float* dst = grad + (size_t)s_rank[j] * kGradStride;
+#pragma unroll
+        for (int k = 0; k < 15; ++k)
+          if (g[k] != 0.f) atomicAdd(dst + k, g[k]);
+      }
+    }
+    bend = bstart;
+  }
+}
+
+template <typename KeyT>
+static cudaError_t collect_fwd_t(const DevCam& c, const nexel_settings& s, char* ws,
+                                 const WsLayout& L, float* notex, float* weights, int* ids,
+                                 float* depths, float* T_final, cudaStream_t st) {
+  uint32_t rmask = L.key64 ? 0xFFFFFFFFu : ((1u << L.rank_bits) - 1u);
+  dim3 grid(L.n_tiles), block(kTilePix);
+  auto* rg = (const uint2*)(ws + L.ranges);
+  auto* keys = (const KeyT*)(ws + L.inst0);
+  auto* recs = (const float4*)(ws + L.geom_sorted);
+  int* nc = (int*)(ws + L.n_contrib);
+  NEXEL_PROF("collect_fwd", st);
+#define NEXEL_CF(KK)                                                                              \
+  k_collect_fwd<KK, KeyT><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.T_min, rmask, rg, \
+                                                  keys, recs, notex, weights, ids, depths,       \
+                                                  T_final, nc)
+  switch (s.K) {
+    case 0: NEXEL_CF(0); break;
+    case 1: NEXEL_CF(1); break;
+    case 2: NEXEL_CF(2); break;
+    case 3: NEXEL_CF(3); break;
+    case 4: NEXEL_CF(4); break;
+    case 5: NEXEL_CF(5); break;
+    case 6: NEXEL_CF(6); break;
+    case 7: NEXEL_CF(7); break;
+    case 8: NEXEL_CF(8); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef NEXEL_CF
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collect_fwd(const DevCam& c, const nexel_settings& s, char* ws,
+                               const WsLayout& L, float* notex, float* weights, int* ids,
+                               float* depths, float* T_final, cudaStream_t st) {
+  if (L.key64)
+    return collect_fwd_t<unsigned long long>(c, s, ws, L, notex, weights, ids, depths, T_final, st);
+  return collect_fwd_t<uint32_t>(c, s, ws, L, notex, weights, ids, depths, T_final, st);
+}
+
+template <typename KeyT>
+static cudaError_t collect_bwd_t(const DevCam& c, const nexel_settings& s, char* ws,
+                                 const WsLayout& L, const char* bws, const BwdLayout& B,
+                                 const int* ids, const float* T_final, const float* d_image,
+                                 cudaStream_t st) {
+  uint32_t rmask = L.key64 ? 0xFFFFFFFFu : ((1u << L.rank_bits) - 1u);
+  dim3 grid(L.n_tiles), block(kTilePix);
+  auto* rg = (const uint2*)(ws + L.ranges);
+  auto* keys = (const KeyT*)(ws + L.inst0);
+  auto* recs = (const float4*)(ws + L.geom_sorted);
+  auto* nc = (const int*)(ws + L.n_contrib);
+  auto* dwe = (const float*)(bws + B.dweff);
+  auto* ddp = (const float*)(bws + B.ddepth);
+  float* grad = (float*)(ws + L.grad_sorted);
+  cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * kGradStride * (size_t)L.N, st);
+  if (e != cudaSuccess) return e;
+  NEXEL_PROF("collect_bwd", st);
+#define NEXEL_CB(KK)                                                                               \
+  k_collect_bwd<KK, KeyT><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.bg[0], s.bg[1],  \
+                                                  s.bg[2], rmask, rg, keys, recs, ids, T_final,  \
+                                                  nc, d_image, dwe, ddp, grad)
+  switch (s.K) {
+    case 0: NEXEL_CB(0); break;
+    case 1: NEXEL_CB(1); break;
+    case 2: NEXEL_CB(2); break;
+    case 3: NEXEL_CB(3); break;
+    case 4: NEXEL_CB(4); break;
+    case 5: NEXEL_CB(5); break;
+    case 6: NEXEL_CB(6); break;
+    case 7: NEXEL_CB(7); break;
+    case 8: NEXEL_CB(8); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef NEXEL_CB
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collect_bwd(const DevCam& c, const nexel_settings& s, char* ws,
+                               const WsLayout& L, const char* bws, const BwdLayout& B,
+                               const int* ids, const float* T_final, const float* d_image,
+                               cudaStream_t st) {
+  if (L.key64)
+    return collect_bwd_t<unsigned long long>(c, s, ws, L, bws, B, ids, T_final, d_image, st);
+  return collect_bwd_t<uint32_t>(c, s, ws, L, bws, B, ids, T_final, d_image, st);
+}
+
+}  // namespace nexel

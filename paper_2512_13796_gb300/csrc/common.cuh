@@ -1,0 +1,176 @@
+// Internal declarations shared by the CUDA translation units of libnexel.
+// Device helpers here are the single definition of the per-pixel surfel
+// evaluation used by both the forward and the backward collection kernels,
+// so that both take bit-identical discrete decisions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/nexel.h"
+
+namespace nexel {
+
+constexpr int kTile = NEXEL_TILE;            // 16 x 16 pixel tiles
+constexpr int kTilePix = kTile * kTile;      // one thread per pixel
+constexpr int kRecF4 = 5;                    // packed surfel record: 5 float4
+constexpr int kGradStride = 16;              // per-surfel gradient record (floats)
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort block
+constexpr int kScanItems = 8;
+constexpr int kScanTile = 256 * kScanItems;
+
+// Camera as the kernels see it (float32, with derived fields).
+struct DevCam {
+  int W, H, tiles_x, tiles_y;
+  float fx, fy, cx, cy;
+  float R[9];   // world -> camera rotation, row-major
+  float t[3];
+  float o[3];   // camera centre in world space
+  float near_;
+};
+
+// Packed per-surfel record (rank order), see the preprocess kernel:
+//  q0 = (cpx_hi, cpy_hi, cpx_lo, cpy_lo)  projected centre, pixels, as a
+//        float-float pair (hi + lo)
+//  q1 = (z, o, gamma1, gamma2)             centre view depth, opacity, gamma
+//  q2 = (nx, ny, Ax, Ay)                   plane tilt and u-gradient per pixel
+//  q3 = (Bx, By, 0, 0)                     v-gradient per pixel
+//  q4 = (c0, c1, c2, id)                   colour and original index (bits)
+// For a pixel centre p: dp = p - cp, den = 1 + dp . n, t* = z / den,
+// u = t* (dp . A), v = t* (dp . B).
+
+struct Hit {
+  float dx, dy, den, t, ut, vt, u, v, pu, pv, alpha;  // alpha before clamping
+};
+
+// |a|^(2 g); exact square for g == 1.
+__device__ __forceinline__ float pow2g(float a, float g) {
+  if (g == 1.0f) return a * a;
+  return exp2f(2.0f * g * __log2f(fabsf(a)));
+}
+
+// Ray-surfel intersection and the generalised-Gaussian opacity (Sec. 4.1).
+// Returns false when the surfel does not contribute (behind the near plane,
+// alpha below alpha_min, or non-finite).
+__device__ __forceinline__ bool eval_surfel(const float4& q0, const float4& q1, const float4& q2,
+                                            const float4& q3, float fpx, float fpy, float near_,
+                                            float alpha_min, Hit& h) {
+  h.dx = (fpx - q0.x) - q0.z;
+  h.dy = (fpy - q0.y) - q0.w;
+  h.den = fmaf(h.dx, q2.x, fmaf(h.dy, q2.y, 1.0f));
+  h.t = q1.x / h.den;
+  if (!(h.t > near_)) return false;
+  h.ut = fmaf(h.dx, q2.z, h.dy * q2.w);
+  h.vt = fmaf(h.dx, q3.x, h.dy * q3.y);
+  h.u = h.t * h.ut;
+  h.v = h.t * h.vt;
+  h.pu = pow2g(h.u, q1.z);
+  h.pv = pow2g(h.v, q1.w);
+  h.alpha = q1.y * expf(-0.5f * (h.pu + h.pv));
+  if (!(h.alpha >= alpha_min) || h.alpha == 0.0f) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------- hash grid
+// MapPositive of the supplementary material (x > 0 -> 2x - 1, else -2x) on
+// the integer lattice coordinate, then the Instant-NGP spatial hash.
+__device__ __forceinline__ uint32_t map_pos(int k) {
+  return k > 0 ? (uint32_t)(2 * k - 1) : (uint32_t)(-2 * k);
+}
+__device__ __forceinline__ uint32_t hash3(int kx, int ky, int kz, uint32_t mask) {
+  return (map_pos(kx) ^ (map_pos(ky) * 2654435761u) ^ (map_pos(kz) * 805459861u)) & mask;
+}
+
+template <typename TT>
+__device__ __forceinline__ float2 load_entry(const TT* tab, uint32_t idx);
+template <>
+__device__ __forceinline__ float2 load_entry<float>(const float* tab, uint32_t idx) {
+  return __ldg(reinterpret_cast<const float2*>(tab) + idx);
+}
+template <>
+__device__ __forceinline__ float2 load_entry<__half>(const __half* tab, uint32_t idx) {
+  __half2 h = __ldg(reinterpret_cast<const __half2*>(tab) + idx);
+  return __half22float2(h);
+}
+
+// Eq. 3: Delta = 1 - exp(-(f / (s t))^2 / (2 pi)).
+__device__ __forceinline__ float downweight(float focal, float s, float t) {
+  float r = focal / (s * t);
+  return -expm1f(-r * r * 0.15915494309189535f);
+}
+
+// ------------------------------------------------------------ workspace
+// Main workspace (binning results and per-pixel replay data).  Regions that
+// depend only on (camera, K, N) come first; the instance buffers and the
+// sort scratch, whose size follows the instance capacity, come last, so
+// every call re-derives the same layout from (camera, K, N, ws_bytes).
+struct WsLayout {
+  size_t geom_orig, geom_sorted, dkey0, dkey1, did0, did1, rect, count, offs, ranges, n_contrib,
+      grad_sorted, counters, fixed_end, inst0, inst1, hist, scan_sums, total;
+  int N, P, K, n_tiles, tile_bits, rank_bits, key64, tile_passes;
+  long long cap;
+};
+// Backward scratch (per sample): dL/dW_j, dL/dD_j, the field features and
+// the texture gradient.
+struct BwdLayout {
+  size_t dweff, ddepth, feat, gtex, total;
+};
+
+WsLayout ws_layout(const nexel_camera& cam, int K, int N, long long cap);
+// Largest capacity whose layout fits in ws_bytes (cap < 0 if none).
+WsLayout ws_layout_for_bytes(const nexel_camera& cam, int K, int N, size_t ws_bytes);
+BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim);
+DevCam make_devcam(const nexel_camera& cam);
+
+// Launch accounting: construct one before each kernel launch (see prof.cu).
+class ProfScope {
+ public:
+  ProfScope(const char* name, cudaStream_t st);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t st_;
+  void* a_;
+};
+#define NEXEL_PROF(name, st) ::nexel::ProfScope _nexel_prof_scope_(name, st)
+
+// Launchers (host side).  They return a cudaError_t.
+cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, const float* mu,
+                              const float* quat, const float* scale, const float* opacity,
+                              const float* gamma, const float* color, char* ws,
+                              const WsLayout& L, cudaStream_t st);
+cudaError_t launch_depth_sort(int N, char* ws, const WsLayout& L, cudaStream_t st);
+cudaError_t launch_count_scan(int N, char* ws, const WsLayout& L, cudaStream_t st);
+cudaError_t launch_binning(const DevCam& c, int N, long long n_inst, char* ws, const WsLayout& L,
+                           cudaStream_t st);
+cudaError_t launch_collect_fwd(const DevCam& c, const nexel_settings& s, char* ws,
+                               const WsLayout& L, float* notex, float* weights, int* ids,
+                               float* depths, float* T_final, cudaStream_t st);
+cudaError_t launch_collect_bwd(const DevCam& c, const nexel_settings& s, char* ws,
+                               const WsLayout& L, const char* bws, const BwdLayout& B,
+                               const int* ids, const float* T_final, const float* d_image,
+                               cudaStream_t st);
+cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int N, const float* mu,
+                                  const float* quat, const float* scale, const float* opacity,
+                                  const float* gamma, char* ws, const WsLayout& L, int accumulate,
+                                  float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
+                                  float* d_gamma, float* d_color, cudaStream_t st);
+cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
+                               const float* notex, const float* weights, const int* ids,
+                               const float* depths, const float* T_final, float* image,
+                               float* textures, cudaStream_t st);
+cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
+                               char* bws, const BwdLayout& B, const float* weights, const int* ids,
+                               const float* depths, const float* d_image, const float* d_weights,
+                               const float* d_textures, float* d_table, float* d_mlp,
+                               cudaStream_t st);
+bool texture_arch_supported(const nexel_settings& s, const nexel_field& f);
+
+}  // namespace nexel

@@ -1,0 +1,249 @@
+// Device helpers of the texturing pass shared by its FP32 and BF16 kernels:
+// the neural-field description, the hashed trilinear gather (forward and
+// backward) and the FP32 MLP.
+#pragma once
+
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace nexel {
+
+struct FieldDev {
+  int L;
+  uint32_t mask;  // T - 1
+  float focal;    // f of Eq. 3 (fx)
+  float s[NEXEL_MAX_LEVELS];
+  const void* table;
+  const float* w;
+};
+
+inline FieldDev make_fielddev(const DevCam& c, const nexel_field& f) {
+  FieldDev d;
+  d.L = f.L;
+  d.mask = (uint32_t)f.T - 1u;
+  d.focal = c.fx;
+  for (int l = 0; l < NEXEL_MAX_LEVELS; ++l) d.s[l] = l < f.L ? f.level_scale[l] : 0.f;
+  d.table = f.table;
+  d.w = f.weights;
+  return d;
+}
+
+template <int IN, int H1, int H2>
+struct MlpArch {
+  static constexpr int HL = H2 > 0 ? H2 : H1;
+  static constexpr int kOffLast = IN * H1 + (H2 > 0 ? H1 * H2 : 0);
+  static constexpr int kWeights = kOffLast + 3 * HL;
+};
+
+// World-space direction of pixel (px, py), not normalised (z_cam = 1).
+__device__ __forceinline__ float3 pixel_dir(const DevCam& c, int px, int py) {
+  float dx = (px + 0.5f - c.cx) / c.fx, dy = (py + 0.5f - c.cy) / c.fy;
+  return make_float3(c.R[0] * dx + c.R[3] * dy + c.R[6], c.R[1] * dx + c.R[4] * dy + c.R[7],
+                     c.R[2] * dx + c.R[5] * dy + c.R[8]);
+}
+
+// Down-weighted hashed trilinear features of one point (level-major, F = 2).
+template <int IN, typename TT>
+__device__ __forceinline__ void hash_features(const FieldDev& f, float3 x, float t, float* feat) {
+  const TT* tab = reinterpret_cast<const TT*>(f.table);
+  const size_t T = (size_t)f.mask + 1;
+#pragma unroll
+  for (int l = 0; l < IN / 2; ++l) {
+    const float s = f.s[l];
+    const float gx = s * x.x, gy = s * x.y, gz = s * x.z;
+    const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+    const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
+    const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
+    const TT* tl = tab + (size_t)l * T * 2;
+    float ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+      const float w = (dx ? rx : 1.f - rx) * (dy ? ry : 1.f - ry) * (dz ? rz : 1.f - rz);
+      const float2 e = load_entry<TT>(tl, hash3(cx + dx, cy + dy, cz + dz, f.mask));
+      ax = fmaf(w, e.x, ax);
+      ay = fmaf(w, e.y, ay);
+    }
+    const float dw = downweight(f.focal, s, t);
+    feat[2 * l] = dw * ax;
+    feat[2 * l + 1] = dw * ay;
+  }
+}
+
+// Scatter of the feature gradient gin into the float32 table gradient and
+// the positional / depth gradient; returns dL/dt for x = o + t d.
+template <int IN, typename TT>
+__device__ __forceinline__ float hash_backward(const FieldDev& f, float3 x, float t, float3 d,
+                                               const float* gin, float* d_table) {
+  const TT* tab = reinterpret_cast<const TT*>(f.table);
+  const size_t T = (size_t)f.mask + 1;
+  float dt = 0.f, gxx = 0.f, gxy = 0.f, gxz = 0.f;
+#pragma unroll
+  for (int l = 0; l < IN / 2; ++l) {
+    const float s = f.s[l];
+    const float gx = s * x.x, gy = s * x.y, gz = s * x.z;
+    const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+    const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
+    const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
+    const TT* tl = tab + (size_t)l * T * 2;
+    float* dl = d_table ? d_table + (size_t)l * T * 2 : nullptr;
+    const float r = f.focal / (s * t);
+    const float dw = downweight(f.focal, s, t);
+    const float g0 = gin[2 * l], g1 = gin[2 * l + 1];
+    float ax = 0.f, ay = 0.f, px = 0.f, py = 0.f, pz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+      const float wx = dx ? rx : 1.f - rx, wy = dy ? ry : 1.f - ry, wz = dz ? rz : 1.f - rz;
+      const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f, sz = dz ? 1.f : -1.f;
+      const uint32_t idx = hash3(cx + dx, cy + dy, cz + dz, f.mask);
+      const float2 e = load_entry<TT>(tl, idx);
+      const float w = wx * wy * wz;
+      ax = fmaf(w, e.x, ax);
+      ay = fmaf(w, e.y, ay);
+      const float ge = g0 * e.x + g1 * e.y;
+      px = fmaf(ge, sx * wy * wz, px);
+      py = fmaf(ge, wx * sy * wz, py);
+      pz = fmaf(ge, wx * wy * sz, pz);
+      if (dl) {
+        const float sc = dw * w;
+        atomicAdd(reinterpret_cast<float2*>(dl) + idx, make_float2(sc * g0, sc * g1));
+      }
+    }
+    // Delta = 1 - exp(-r^2 / 2pi), r = f / (s t): dDelta/dt = -(1 - Delta) r^2 / (pi t)
+    const float ddw = -(1.f - dw) * r * r * 0.3183098861837907f / t;
+    dt = fmaf(g0 * ax + g1 * ay, ddw, dt);
+    gxx = fmaf(dw * s, px, gxx);
+    gxy = fmaf(dw * s, py, gxy);
+    gxz = fmaf(dw * s, pz, gxz);
+  }
+  return dt + gxx * d.x + gxy * d.y + gxz * d.z;
+}
+
+// FP32 MLP forward; keeps the hidden activations when asked.
+template <int IN, int H1, int H2>
+__device__ __forceinline__ void mlp_fwd_f32(const float* __restrict__ sW, const float* in,
+                                            float* out, float* keep1, float* keep2) {
+  using A = MlpArch<IN, H1, H2>;
+  float h1[H1];
+#pragma unroll
+  for (int o = 0; o < H1; ++o) {
+    const float4* wr = reinterpret_cast<const float4*>(sW + o * IN);
+    float v = 0.f;
+#pragma unroll
+    for (int i = 0; i < IN / 4; ++i) {
+      float4 w4 = wr[i];
+      v = fmaf(w4.x, in[4 * i], v);
+      v = fmaf(w4.y, in[4 * i + 1], v);
+      v = fmaf(w4.z, in[4 * i + 2], v);
+      v = fmaf(w4.w, in[4 * i + 3], v);
+    }
+    h1[o] = fmaxf(v, 0.f);
+    if (keep1) keep1[o] = h1[o];
+  }
+  const float* hl = h1;
+  float h2[H2 > 0 ? H2 : 1];
+  if constexpr (H2 > 0) {
+#pragma unroll
+    for (int o = 0; o < H2; ++o) {
+      const float4* wr = reinterpret_cast<const float4*>(sW + IN * H1 + o * H1);
+      float v = 0.f;
+#pragma unroll
+      for (int i = 0; i < H1 / 4; ++i) {
+        float4 w4 = wr[i];
+        v = fmaf(w4.x, h1[4 * i], v);
+        v = fmaf(w4.y, h1[4 * i + 1], v);
+        v = fmaf(w4.z, h1[4 * i + 2], v);
+        v = fmaf(w4.w, h1[4 * i + 3], v);
+      }
+      h2[o] = fmaxf(v, 0.f);
+      if (keep2) keep2[o] = h2[o];
+    }
+    hl = h2;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4* wr = reinterpret_cast<const float4*>(sW + A::kOffLast + k * A::HL);
+    float v = 0.f;
+#pragma unroll
+    for (int i = 0; i < A::HL / 4; ++i) {
+      float4 w4 = wr[i];
+      v = fmaf(w4.x, hl[4 * i], v);
+      v = fmaf(w4.y, hl[4 * i + 1], v);
+      v = fmaf(w4.z, hl[4 * i + 2], v);
+      v = fmaf(w4.w, hl[4 * i + 3], v);
+    }
+    out[k] = v;
+  }
+}
+
+// FP32 MLP backward to the input (ReLU masks from the kept activations).
+template <int IN, int H1, int H2>
+__device__ __forceinline__ void mlp_bwd_input_f32(const float* __restrict__ sW, const float* gT,
+                                                  const float* h1, const float* h2, float* gin) {
+  using A = MlpArch<IN, H1, H2>;
+  constexpr int HL = A::HL;
+  const float* W3 = sW + A::kOffLast;
+  const float* hl = (H2 > 0) ? h2 : h1;
+  float dl[HL];
+#pragma unroll
+  for (int i = 0; i < HL; ++i) {
+    float v = W3[i] * gT[0] + W3[HL + i] * gT[1] + W3[2 * HL + i] * gT[2];
+    dl[i] = hl[i] > 0.f ? v : 0.f;
+  }
+  float d1[H1];
+  if constexpr (H2 > 0) {
+    const float* W2 = sW + IN * H1;
+#pragma unroll
+    for (int i = 0; i < H1; ++i) d1[i] = 0.f;
+#pragma unroll
+    for (int o = 0; o < H2; ++o) {
+      const float g = dl[o];
+      const float4* wr = reinterpret_cast<const float4*>(W2 + o * H1);
+#pragma unroll
+      for (int i = 0; i < H1 / 4; ++i) {
+        float4 w4 = wr[i];
+        d1[4 * i] = fmaf(w4.x, g, d1[4 * i]);
+        d1[4 * i + 1] = fmaf(w4.y, g, d1[4 * i + 1]);
+        d1[4 * i + 2] = fmaf(w4.z, g, d1[4 * i + 2]);
+        d1[4 * i + 3] = fmaf(w4.w, g, d1[4 * i + 3]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < H1; ++i) d1[i] = h1[i] > 0.f ? d1[i] : 0.f;
+  } else {
+#pragma unroll
+    for (int i = 0; i < H1; ++i) d1[i] = dl[i];
+  }
+#pragma unroll
+  for (int i = 0; i < IN; ++i) gin[i] = 0.f;
+#pragma unroll
+  for (int o = 0; o < H1; ++o) {
+    const float g = d1[o];
+    const float4* wr = reinterpret_cast<const float4*>(sW + o * IN);
+#pragma unroll
+    for (int i = 0; i < IN / 4; ++i) {
+      float4 w4 = wr[i];
+      gin[4 * i] = fmaf(w4.x, g, gin[4 * i]);
+      gin[4 * i + 1] = fmaf(w4.y, g, gin[4 * i + 1]);
+      gin[4 * i + 2] = fmaf(w4.z, g, gin[4 * i + 2]);
+      gin[4 * i + 3] = fmaf(w4.w, g, gin[4 * i + 3]);
+    }
+  }
+}
+
+// BF16 tensor-core texturing (texture_bf16.cu).
+bool bf16_arch_supported(const nexel_field& f);
+cudaError_t launch_texture_fwd_bf16(const DevCam& c, const nexel_settings& s, const nexel_field& f,
+                                    const FieldDev& fd, const float* notex, const float* weights,
+                                    const int* ids, const float* depths, const float* T_final,
+                                    float* image, float* textures, cudaStream_t st);
+cudaError_t launch_texture_bwd_bf16(const DevCam& c, const nexel_settings& s, const nexel_field& f,
+                                    const FieldDev& fd, char* bws, const BwdLayout& B,
+                                    const float* weights, const int* ids, const float* depths,
+                                    const float* d_image, const float* d_weights,
+                                    const float* d_textures, float* d_table, float* d_mlp,
+                                    cudaStream_t st);
+
+}  // namespace nexel

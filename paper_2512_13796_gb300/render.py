@@ -1,0 +1,222 @@
+"""PyTorch-facing API: device buffers, streams and autograd around libnexel.
+
+Everything here is argument marshalling.  PyTorch provides device memory and
+the current CUDA stream; the three library calls (preprocess, forward,
+backward) do all of the rendering arithmetic in CUDA kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _native as N_
+
+
+def camera_struct(cam) -> N_.Camera:
+    c = N_.Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    m = np.asarray(cam.world_to_cam, np.float32).ravel()
+    for i in range(12):
+        c.world_to_cam[i] = float(m[i])
+    c.near_plane = float(cam.near)
+    return c
+
+
+def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32") -> N_.Settings:
+    s = N_.Settings()
+    s.K = int(st.K)
+    s.alpha_min, s.alpha_max, s.T_min = float(st.alpha_min), float(st.alpha_max), float(st.T_min)
+    for i in range(3):
+        s.bg[i] = float(st.bg[i])
+    s.grid_dtype = {"f32": N_.F32, "f16": N_.F16}[grid_dtype]
+    s.mlp_dtype = {"f32": N_.F32, "bf16": N_.BF16}[mlp_dtype]
+    return s
+
+
+@dataclasses.dataclass
+class DeviceField:
+    """Neural field on the device: FP32 master table and weights, plus the
+    storage copy of the table the kernels read (FP16 in the precision form)."""
+    L: int
+    T: int
+    F: int
+    level_scale: tuple
+    widths: tuple
+    table: torch.Tensor        # (L, T, F) float32 master
+    weights: torch.Tensor      # flat float32, layer after layer, (out, in) row-major
+    grid_dtype: str = "f32"
+    mlp_dtype: str = "f32"
+
+    @staticmethod
+    def from_synth(f, device, grid_dtype="f32", mlp_dtype="f32") -> "DeviceField":
+        w = torch.from_numpy(np.concatenate([x.ravel() for x in f.weights]).astype(np.float32))
+        return DeviceField(f.L, f.T, f.F, tuple(float(s) for s in f.level_scale), tuple(f.widths),
+                           torch.from_numpy(f.table).to(device).contiguous(),
+                           w.to(device).contiguous(), grid_dtype, mlp_dtype)
+
+    def storage_table(self, table: torch.Tensor | None = None) -> torch.Tensor:
+        t = self.table if table is None else table
+        return t.detach().to(torch.float16).contiguous() if self.grid_dtype == "f16" else \
+            t.detach().contiguous()
+
+    def struct(self, table_store: torch.Tensor, weights: torch.Tensor) -> N_.Field:
+        f = N_.Field()
+        f.L, f.T, f.F = self.L, self.T, self.F
+        for l in range(self.L):
+            f.level_scale[l] = float(self.level_scale[l])
+        f.table = table_store.data_ptr()
+        f.n_layers = len(self.widths) - 1
+        for i, w in enumerate(self.widths):
+            f.widths[i] = int(w)
+        f.weights = weights.data_ptr()
+        return f
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Workspace:
+    """Device scratch for one camera and surfel count; grows on demand."""
+
+    def __init__(self, device, cap_hint: int = 1 << 20):
+        self.device = torch.device(device)
+        self.cap = int(cap_hint)
+        self.ws = None
+        self.ws_key = None
+        self.bws = None
+        self.bws_key = None
+
+    def main(self, cam_s: N_.Camera, N: int):
+        key = (cam_s.width, cam_s.height, N, self.cap)
+        if self.ws_key != key:
+            nbytes = N_.nexel_workspace_size(cam_s, N, self.cap)
+            self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.ws_key = key
+        return self.ws
+
+    def bwd(self, cam_s, st_s, field_s):
+        nbytes = N_.nexel_bwd_workspace_size(cam_s, st_s, field_s)
+        if self.bws is None or self.bws.numel() < nbytes:
+            self.bws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self.bws
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def preprocess(ws: Workspace, cam_s, st_s, mu, quat, scale, opacity, gamma, color) -> int:
+    N = mu.shape[0]
+    while True:
+        buf = ws.main(cam_s, N)
+        rc, n_inst = N_.nexel_preprocess(cam_s, st_s, N, mu.data_ptr(), quat.data_ptr(),
+                                         scale.data_ptr(), opacity.data_ptr(), gamma.data_ptr(),
+                                         color.data_ptr(), buf.data_ptr(), buf.numel(), _stream())
+        if rc == -3:  # capacity: grow and redo
+            ws.cap = int(n_inst * 1.25) + 1024
+            continue
+        N_.check("nexel_preprocess", rc)
+        return n_inst
+
+
+def forward(ws: Workspace, cam_s, st_s, field: DeviceField | None, table_store, weights, mu,
+            quat, scale, opacity, gamma, color) -> dict:
+    """Preprocess + forward render; returns the output tensors."""
+    dev = mu.device
+    H, W, K = cam_s.height, cam_s.width, st_s.K
+    n_inst = preprocess(ws, cam_s, st_s, mu, quat, scale, opacity, gamma, color)
+    out = dict(image=torch.empty(H, W, 3, device=dev), notex=torch.empty(H, W, 3, device=dev),
+               weights=torch.empty(H, W, K, device=dev),
+               ids=torch.empty(H, W, K, dtype=torch.int32, device=dev),
+               depths=torch.empty(H, W, K, device=dev),
+               textures=torch.empty(H, W, K, 3, device=dev), T_final=torch.empty(H, W, device=dev))
+    fs = field.struct(table_store, weights) if (field is not None and K > 0) else None
+    buf = ws.ws
+    N_.nexel_render_fwd(cam_s, st_s, fs, mu.shape[0], buf.data_ptr(), buf.numel(),
+                        out["image"].data_ptr(), out["notex"].data_ptr(),
+                        _ptr(out["weights"]) if K else None, _ptr(out["ids"]) if K else None,
+                        _ptr(out["depths"]) if K else None, _ptr(out["textures"]) if K else None,
+                        out["T_final"].data_ptr(), _stream())
+    out["n_instances"] = n_inst
+    return out
+
+
+def backward(ws: Workspace, cam_s, st_s, field, table_store, weights, mu, quat, scale, opacity,
+             gamma, fwd: dict, d_image, d_weights=None, d_textures=None, accumulate=False,
+             grads: dict | None = None) -> dict:
+    dev = mu.device
+    N = mu.shape[0]
+    K = st_s.K
+    g = grads if grads is not None else {}
+    for k, shape in (("mu", (N, 3)), ("quat", (N, 4)), ("scale", (N, 2)), ("opacity", (N,)),
+                     ("gamma", (N, 2)), ("color", (N, 3))):
+        if k not in g:
+            g[k] = torch.zeros(shape, device=dev)
+    fs = None
+    if field is not None and K > 0:
+        fs = field.struct(table_store, weights)
+        if "table" not in g:
+            g["table"] = torch.zeros_like(field.table)
+        if "mlp" not in g:
+            g["mlp"] = torch.zeros_like(field.weights)
+    bws = ws.bwd(cam_s, st_s, fs)
+    buf = ws.ws
+    N_.nexel_render_bwd(cam_s, st_s, fs, N, mu.data_ptr(), quat.data_ptr(), scale.data_ptr(),
+                        opacity.data_ptr(), gamma.data_ptr(), buf.data_ptr(), buf.numel(),
+                        bws.data_ptr(), bws.numel(),
+                        _ptr(fwd["weights"]) if K else None, _ptr(fwd["ids"]) if K else None,
+                        _ptr(fwd["depths"]) if K else None, fwd["T_final"].data_ptr(),
+                        d_image.contiguous().data_ptr(),
+                        _ptr(d_weights.contiguous()) if d_weights is not None else None,
+                        _ptr(d_textures.contiguous()) if d_textures is not None else None,
+                        accumulate, g["mu"].data_ptr(), g["quat"].data_ptr(),
+                        g["scale"].data_ptr(), g["opacity"].data_ptr(), g["gamma"].data_ptr(),
+                        g["color"].data_ptr(), _ptr(g.get("table")), _ptr(g.get("mlp")),
+                        _stream())
+    return g
+
+
+class NexelRender(torch.autograd.Function):
+    """Differentiable render: inputs are the activated surfel parameters and
+    the field's FP32 master table and weights; outputs image, W and T."""
+
+    @staticmethod
+    def forward(ctx, mu, quat, scale, opacity, gamma, color, table, weights, cfg):
+        ws, cam_s, st_s, field = cfg["ws"], cfg["cam"], cfg["settings"], cfg["field"]
+        args = [t.detach().contiguous() for t in (mu, quat, scale, opacity, gamma, color)]
+        ts = field.storage_table(table) if field is not None else None
+        w = weights.detach().contiguous() if weights is not None else None
+        out = forward(ws, cam_s, st_s, field, ts, w, *args)
+        ctx.cfg = cfg
+        ctx.args, ctx.ts, ctx.w = args, ts, w
+        ctx.out = out
+        return out["image"], out["weights"], out["textures"]
+
+    @staticmethod
+    def backward(ctx, d_image, d_weights, d_textures):
+        cfg = ctx.cfg
+        mu, quat, scale, opacity, gamma, color = ctx.args
+        g = backward(cfg["ws"], cfg["cam"], cfg["settings"], cfg["field"], ctx.ts, ctx.w, mu, quat,
+                     scale, opacity, gamma, ctx.out, d_image, d_weights, d_textures)
+        return (g["mu"], g["quat"], g["scale"], g["opacity"], g["gamma"], g["color"],
+                g.get("table"), g.get("mlp"), None)
+
+
+def render(params: dict, field: DeviceField | None, cam, settings, ws: Workspace | None = None):
+    """Differentiable render of one view.  ``params`` holds activated
+    surfel tensors mu, quat, scale, opacity, gamma, color (float32, cuda).
+    Returns (image [H,W,3], weights [H,W,K], textures [H,W,K,3])."""
+    dev = params["mu"].device
+    ws = ws or Workspace(dev)
+    cfg = dict(ws=ws, cam=camera_struct(cam),
+               settings=settings_struct(settings, field.grid_dtype if field else "f32",
+                                        field.mlp_dtype if field else "f32"),
+               field=field)
+    tab = field.table if field is not None else None
+    w = field.weights if field is not None else None
+    return NexelRender.apply(params["mu"], params["quat"], params["scale"], params["opacity"],
+                             params["gamma"], params["color"], tab, w, cfg)

@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/*.h; host-side argument checks answer without touching a GPU."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2512_13796_gb300 import _native as N_
+from paper_2512_13796_gb300 import render as R
+from paper_2512_13796_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"^[A-Za-z_][\w \t\*]*?\b(nexel_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    N_.build()
+    return N_.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert {"nexel_preprocess", "nexel_render_fwd", "nexel_render_bwd"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(N_.EXPORTS) <= names
+
+
+def test_status_strings(lib):
+    assert N_.nexel_status_string(0) == "ok"
+    assert N_.nexel_status_string(-3) == "instance capacity exceeded"
+    assert N_.nexel_version() >= 100
+
+
+def test_workspace_sizes_are_host_only(lib):
+    cam = R.camera_struct(synth.front_camera(1280, 720))
+    a = N_.nexel_workspace_size(cam, 300_000, 10_000_000)
+    b = N_.nexel_workspace_size(cam, 300_000, 20_000_000)
+    assert b > a > 300_000 * 80
+    st = R.settings_struct(synth.Settings(K=4))
+    f = N_.Field()
+    f.L, f.T, f.F = 16, 1 << 19, 2
+    assert N_.nexel_bwd_workspace_size(cam, st, f) >= 1280 * 720 * 4 * (8 + 32 * 4 + 16)
+
+
+def test_invalid_arguments_rejected_before_launch(lib):
+    cam = R.camera_struct(synth.front_camera(64, 64))
+    bad = R.camera_struct(synth.front_camera(64, 64))
+    bad.width = 0
+    st = R.settings_struct(synth.Settings(K=2))
+    n = C.c_longlong(0)
+    assert lib.nexel_preprocess(C.byref(bad), C.byref(st), 1, *([None] * 7), 0, C.byref(n), None) == -1
+    assert lib.nexel_preprocess(C.byref(cam), C.byref(st), 5, *([None] * 7), 0, C.byref(n), None) == -1
+    st9 = R.settings_struct(synth.Settings(K=9))
+    assert lib.nexel_preprocess(C.byref(cam), C.byref(st9), 0, *([None] * 7), 0, C.byref(n), None) == -1
+    out = C.c_size_t(0)
+    assert lib.nexel_workspace_size(C.byref(bad), 10, 10, C.byref(out)) == -1
+    assert lib.nexel_workspace_size(C.byref(cam), -1, 10, C.byref(out)) == -1

@@ -1,0 +1,244 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element
+on the same seeded inputs.  FP32 form: colours within 1e-5 absolute,
+gradients within 1e-3 relative, top-K ids and sort keys bit-exact; pixels
+whose discrete choices lie within 1e-5 (relative) of a threshold or a tie
+are excluded and counted."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_13796_gb300 import synth
+
+from helpers import compare_forward, compare_grads, masked_upstream, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TIE = 1e-5
+TOL_F32 = 1e-5
+GRAD_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    assert torch.cuda.is_available(), "GPU test without a CUDA device"
+    from paper_2512_13796_gb300 import _native
+    _native.build()
+    _native.lib()
+    return torch.device("cuda:0")
+
+
+def _report(name, stats):
+    print(f"\n[{name}] " + " ".join(f"{k}={v:.3g}" if isinstance(v, float) else f"{k}={v}"
+                                    for k, v in stats.items()))
+
+
+@pytest.mark.parametrize("gamma", ["one", "var"])
+def test_config0_forward(dev, gamma):
+    w = synth.workload(0, gamma=gamma)
+    cam, st = w.cameras[0], w.settings
+    fw, _, _ = run_gpu(w.scene, cam, st, w.field, dev)
+    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE)
+    s = compare_forward(fw, ref, st.K, TOL_F32)
+    _report(f"config0 fwd gamma={gamma}", s)
+    assert s["n_tie"] < 0.25 * s["n_pix"]
+
+
+@pytest.mark.parametrize("gamma", ["one", "var"])
+def test_config0_backward(dev, gamma):
+    w = synth.workload(0, gamma=gamma)
+    cam, st = w.cameras[0], w.settings
+    P, K = cam.width * cam.height, st.K
+    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE)
+    pix = ref["pixels"]
+    ok = ref["tie"] == 0
+    dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=5)
+    _, gg, _ = run_gpu(w.scene, cam, st, w.field, dev, d_image=dI, d_weights=dW, d_textures=dT)
+    sel = pix[ok]
+    gr = oracle.render_bwd(w.scene, cam, st, w.field, sel, dI[sel], dW[sel], dT[sel])
+    s = compare_grads(gg, gr, GRAD_RTOL)
+    _report(f"config0 bwd gamma={gamma}", s)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    w = synth.workload(1)
+    cam = w.cameras[0]
+    pix = synth.pixel_sample(cam, 4096, 4, seed=1)
+    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE)
+    return w, pix, ref
+
+
+def test_config1_forward_sampled(dev, cfg1):
+    w, pix, ref = cfg1
+    fw, _, _ = run_gpu(w.scene, w.cameras[0], w.settings, w.field, dev)
+    s = compare_forward(fw, ref, w.settings.K, TOL_F32)
+    _report("config1 fwd", s)
+    assert s["n_tie"] < 0.25 * s["n_pix"]
+
+
+def test_config1_backward_sampled(dev, cfg1):
+    w, pix, ref = cfg1
+    cam, st = w.cameras[0], w.settings
+    P, K = cam.width * cam.height, st.K
+    ok = ref["tie"] == 0
+    dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=6)
+    _, gg, _ = run_gpu(w.scene, cam, st, w.field, dev, d_image=dI, d_weights=dW, d_textures=dT)
+    sel = pix[ok]
+    gr = oracle.render_bwd(w.scene, cam, st, w.field, sel, dI[sel], dW[sel], dT[sel])
+    s = compare_grads(gg, gr, GRAD_RTOL)
+    _report("config1 bwd", s)
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    w = synth.workload(2, precision="f32")
+    cam = w.cameras[0]
+    pix = synth.pixel_sample(cam, 2048, 3, seed=2)
+    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE)
+    return w, pix, ref
+
+
+def test_config2_fp32_forward_sampled(dev, cfg2):
+    w, pix, ref = cfg2
+    fw, _, _ = run_gpu(w.scene, w.cameras[0], w.settings, w.field, dev)
+    s = compare_forward(fw, ref, w.settings.K, TOL_F32)
+    _report("config2 fp32 fwd", s)
+    assert s["n_tie"] < 0.25 * s["n_pix"]
+
+
+def test_config2_fp32_backward_sampled(dev, cfg2):
+    w, pix, ref = cfg2
+    cam, st = w.cameras[0], w.settings
+    P, K = cam.width * cam.height, st.K
+    ok = ref["tie"] == 0
+    dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=7)
+    _, gg, _ = run_gpu(w.scene, cam, st, w.field, dev, d_image=dI, d_weights=dW, d_textures=dT)
+    sel = pix[ok]
+    gr = oracle.render_bwd(w.scene, cam, st, w.field, sel, dI[sel], dW[sel], dT[sel])
+    s = compare_grads(gg, gr, GRAD_RTOL)
+    _report("config2 fp32 bwd", s)
+
+
+# Reduced-precision form: FP16 table, BF16 MLP on tensor cores with FP32
+# accumulation.  Colours within 2e-3 per channel of the FP64 oracle (which
+# reads the FP32 table); gradients within 3e-2 of the class scale: a BF16
+# operand carries a relative rounding error of 2^-9 and the input gradient
+# passes three BF16 products, so 1e-2-level relative error is expected.
+TOL_BF16 = 2e-3
+GRAD_RTOL_BF16 = 3e-2
+
+
+@pytest.mark.parametrize("cfg", ["cfg1", "cfg2"])
+def test_bf16_forward_sampled(dev, cfg, request):
+    w, pix, ref = request.getfixturevalue(cfg)
+    fw, _, _ = run_gpu(w.scene, w.cameras[0], w.settings, w.field, dev, grid="f16", mlp="bf16")
+    s = compare_forward(fw, ref, w.settings.K, TOL_BF16)
+    _report(f"{cfg} bf16 fwd", s)
+
+
+@pytest.mark.parametrize("cfg", ["cfg1", "cfg2"])
+def test_bf16_backward_sampled(dev, cfg, request):
+    w, pix, ref = request.getfixturevalue(cfg)
+    cam, st = w.cameras[0], w.settings
+    P, K = cam.width * cam.height, st.K
+    ok = ref["tie"] == 0
+    dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=8)
+    _, gg, _ = run_gpu(w.scene, cam, st, w.field, dev, grid="f16", mlp="bf16", d_image=dI,
+                       d_weights=dW, d_textures=dT)
+    sel = pix[ok]
+    gr = oracle.render_bwd(w.scene, cam, st, w.field, sel, dI[sel], dW[sel], dT[sel])
+    s = compare_grads(gg, gr, GRAD_RTOL_BF16)
+    _report(f"{cfg} bf16 bwd", s)
+
+
+@pytest.mark.parametrize("idx", [1, 2])
+def test_binning_order_bit_exact(dev, idx):
+    """The per-tile lists are a stable sort of (tile, centre depth, index):
+    bit-exact against a CPU sort of the same float32 keys; depths match the
+    FP64 centre depth, and near-equal depths (key ties) are counted."""
+    import torch
+    from paper_2512_13796_gb300 import _native as N_
+    from paper_2512_13796_gb300 import render as R
+    w = synth.workload(idx, precision="f32")
+    cam = w.cameras[0]
+    fw, _, ws = run_gpu(w.scene, cam, w.settings, w.field, dev)
+    n = fw["n_instances"]
+    tiles = torch.empty(n, dtype=torch.int32, device=dev)
+    ids = torch.empty(n, dtype=torch.int32, device=dev)
+    dep = torch.empty(n, dtype=torch.float32, device=dev)
+    N_.nexel_instance_list(R.camera_struct(cam), w.scene.n, ws.ws.data_ptr(), ws.ws.numel(), n,
+                           tiles.data_ptr(), ids.data_ptr(), dep.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    t, i, d = tiles.cpu().numpy(), ids.cpu().numpy(), dep.cpu().numpy()
+    order = np.lexsort((i, d.view(np.uint32), t))
+    assert np.array_equal(order, np.arange(n)), "instance list is not (tile, depth, id) sorted"
+    M = cam.world_to_cam.astype(np.float64)
+    z = w.scene.mu.astype(np.float64) @ M[2, :3] + M[2, 3]
+    rel = np.abs(d - z[i]) / z[i]
+    assert rel.max() < 1e-6
+    zs = np.sort(z[z > cam.near])
+    ties = int(np.sum(np.diff(zs) < 1e-6 * zs[1:]))
+    print(f"\n[binning config{idx}] n_instances={n} mean tiles/surfel={n / w.scene.n:.2f} "
+          f"max depth rel err={rel.max():.2e} key ties(1e-6)={ties}")
+    # every surfel appears at most once per tile
+    key = t.astype(np.int64) * (w.scene.n + 1) + i
+    assert np.unique(key).size == n
+
+
+def test_ragged_image_all_K(dev):
+    """Image sizes that are not multiples of the 16x16 tile, every K."""
+    sc = synth.make_scene(400, 3, 21, gamma="var")
+    sc.scale *= 2.0
+    fld = synth.make_field(4, 12, 2, (16,), 21, table_std=0.3)
+    cam = synth.front_camera(37, 29)
+    for K in range(0, 9):
+        st = synth.Settings(K=K)
+        fw, _, _ = run_gpu(sc, cam, st, fld if K else None, dev)
+        ref = oracle.render(sc, cam, st, fld if K else None, tie_tol=TIE)
+        if K == 0:
+            ok = ref["tie"] == 0
+            e = np.abs(fw["image"].reshape(-1, 3)[ok] - ref["image"][ok]).max()
+            assert e <= TOL_F32
+        else:
+            compare_forward(fw, ref, K, TOL_F32)
+
+
+def test_empty_and_culled_scenes(dev):
+    """N = 0, and surfels all behind the camera: image = T_final bg = bg."""
+    cam = synth.front_camera(40, 24)
+    st = synth.Settings(K=2, bg=(0.25, 0.5, 0.75))
+    fld = synth.make_field(4, 12, 2, (16,), 0)
+    empty = synth.make_scene(1, 1, 0)
+    empty = synth.Scene(*(getattr(empty, k)[:0] for k in ("mu", "quat", "scale", "opacity",
+                                                          "gamma", "color")))
+    fw, _, _ = run_gpu(empty, cam, st, fld, dev)
+    np.testing.assert_array_equal(fw["image"], np.broadcast_to(np.float32(st.bg), fw["image"].shape))
+    assert np.all(fw["ids"] == -1) and np.all(fw["T_final"] == 1.0)
+    behind = synth.make_scene(50, 1, 3)
+    behind.mu[:, 2] = -5.0  # camera at z = -3 looking along +z
+    fw, _, _ = run_gpu(behind, cam, st, fld, dev)
+    assert fw["n_instances"] == 0
+    np.testing.assert_array_equal(fw["image"], np.broadcast_to(np.float32(st.bg), fw["image"].shape))
+
+
+def test_capacity_growth(dev):
+    """A workspace sized for too few instances returns the capacity error,
+    the wrapper grows it and the result matches a large workspace."""
+    from paper_2512_13796_gb300 import render as R
+    w = synth.workload(0)
+    ws = R.Workspace(dev, cap_hint=16)
+    fw, _, _ = run_gpu(w.scene, w.cameras[0], w.settings, w.field, dev, ws=ws)
+    assert ws.cap >= fw["n_instances"]
+    fw2, _, _ = run_gpu(w.scene, w.cameras[0], w.settings, w.field, dev)
+    for k in ("image", "ids", "weights"):
+        np.testing.assert_array_equal(fw[k], fw2[k])
+
+
+def test_deterministic_forward(dev):
+    w = synth.workload(1)
+    a, _, _ = run_gpu(w.scene, w.cameras[0], w.settings, w.field, dev)
+    b, _, _ = run_gpu(w.scene, w.cameras[0], w.settings, w.field, dev)
+    for k in ("image", "ids", "weights", "depths", "textures", "T_final"):
+        np.testing.assert_array_equal(a[k], b[k])
