@@ -86,6 +86,11 @@ typedef struct {
   float alpha_min, alpha_max, T_min;
   float bg[3];
   int grid_dtype, mlp_dtype;
+  /* 0: nexel_render_bwd reads the forward's saved I, W, D and T_final;
+   * 1: it recomputes them (the collection pass runs again inside the
+   * backward), so the caller need not keep them between the two calls and
+   * passes NULL for them. */
+  int recompute_buffers;
 } nexel_settings;
 
 /* Neural field of Sec. 3 ("Instant-NGP") and Eq. 4: L hash tables of T
@@ -113,6 +118,8 @@ int nexel_workspace_size(const nexel_camera* cam, int N, long long max_instances
 
 /* Bytes of the separate backward scratch (per-sample texture gradients and
  * field features) for this camera, K and field.  Writes *bytes (host). */
+/* With settings->recompute_buffers the scratch also holds the recomputed
+ * per-pixel buffers. */
 int nexel_bwd_workspace_size(const nexel_camera* cam, const nexel_settings* settings,
                              const nexel_field* field, size_t* bytes);
 

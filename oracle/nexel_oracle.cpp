@@ -48,6 +48,7 @@ struct OSet {
   double bg[3];
   double tie_tol;    // relative width used to flag threshold / top-K ties
   double order_tol;  // relative width used to flag centre-depth order ties
+  double cell_tol;   // world-space distance to a hash-cell face flagged as a kink
 };
 
 struct OField {
@@ -255,7 +256,7 @@ struct PixelResult {
   std::vector<std::vector<LevelEval>> lev;             // per slot level evals
 };
 
-enum { TIE_TOPK = 1, TIE_ALPHA = 2, TIE_TMIN = 4, TIE_NEAR = 8, TIE_ORDER = 16 };
+enum { TIE_TOPK = 1, TIE_ALPHA = 2, TIE_TMIN = 4, TIE_NEAR = 8, TIE_ORDER = 16, TIE_CELL = 32 };
 
 inline bool near_rel(double a, double b, double tol) {
   return std::fabs(a - b) <= tol * std::max(std::fabs(a), std::fabs(b));
@@ -303,7 +304,10 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
     e.id = i; e.pos = (int)pos; e.alpha = ac; e.alpha_raw = a; e.clamped = a > st.alpha_max;
     e.T = T; e.w = ac * T; e.t = t; e.u = u; e.v = v;
     for (int k = 0; k < 3; ++k) e.x[k] = x[k];
-    if (!r.list.empty() && near_rel(s.zc[r.list.back().id], s.zc[i], st.order_tol))
+    // equal depths are ordered by index on every side; only nearly equal,
+    // unequal ones can be ordered differently by a lower-precision key
+    if (!r.list.empty() && s.zc[r.list.back().id] != s.zc[i] &&
+        near_rel(s.zc[r.list.back().id], s.zc[i], st.order_tol))
       r.tie |= TIE_ORDER;
     r.list.push_back(e);
     T = test;
@@ -339,6 +343,16 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
     for (int ch = 0; ch < 3; ++ch) r.tex[j][ch] = 0.0;
     if (!fd) continue;
     double x[3] = {o[0] + e.t * d[0], o[1] + e.t * d[1], o[2] + e.t * d[2]};
+    // the integer cell of each level is decided by floor(s_l x): a point
+    // within cell_tol (world units) of a cell face is a kink of the
+    // trilinear interpolation, where a lower-precision x may fall on the
+    // other side
+    if (st.cell_tol > 0.0)
+      for (int l = 0; l < fd->L; ++l)
+        for (int a = 0; a < 3; ++a) {
+          double g = fd->scale[l] * x[a];
+          if (std::fabs(g - std::nearbyint(g)) < st.cell_tol * fd->scale[l]) r.tie |= TIE_CELL;
+        }
     std::vector<double> feat(fd->L * fd->F);
     field_features(*fd, c.fx, x, e.t, feat.data(), keep ? &r.lev[j] : nullptr);
     std::vector<std::vector<double>> acts;
@@ -449,6 +463,36 @@ int oracle_render(const OCam* c, const OSet* st, const OField* fd, int N, const 
     if (T_final) T_final[p] = r.T_final;
     if (n_contrib) n_contrib[p] = (int)r.list.size();
     if (tie) tie[p] = r.tie;
+  }
+  return 0;
+}
+
+// Reference images for the learned-part test: the same compositing (Eq. 1)
+// over all intersected surfels, but every surfel shows a known procedural
+// world-space texture tau(x*) at its intersection instead of a colour:
+//   tau_c(x) = 0.5 + 0.4 sin(f x_0 + 2c) sin(f x_1 + c) + 0.1 sin(f x_2 - c).
+// image is [n_pix][3].
+int oracle_render_procedural(const OCam* c, const OSet* st, int N, const double* mu,
+                             const double* quat, const double* scale, const double* opac,
+                             const double* gamma, double freq, int n_pix, const int* pix,
+                             double* image) {
+  std::vector<double> dummy(3 * (size_t)std::max(N, 1), 0.0);
+  Scene s = make_scene(*c, N, mu, quat, scale, opac, gamma, dummy.data());
+  OSet st0 = *st;
+  st0.K = 0;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int p = 0; p < n_pix; ++p) {
+    PixelResult r;
+    render_pixel(*c, st0, nullptr, s, pix[p], false, r);
+    for (int ch = 0; ch < 3; ++ch) {
+      double v = r.T_final * st->bg[ch];
+      for (const Contrib& e : r.list) {
+        double tau = 0.5 + 0.4 * std::sin(freq * e.x[0] + 2.0 * ch) * std::sin(freq * e.x[1] + ch) +
+                     0.1 * std::sin(freq * e.x[2] - ch);
+        v += e.w * tau;
+      }
+      image[3 * p + ch] = v;
+    }
   }
   return 0;
 }

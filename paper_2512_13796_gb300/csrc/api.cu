@@ -96,7 +96,7 @@ WsLayout ws_layout_for_bytes(const nexel_camera& cam, int K, int N, size_t ws_by
   return L;
 }
 
-BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim) {
+BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim, bool recompute) {
   // per-sample gradients are indexed p * K + j; the features and texture
   // gradients by padded row (pixel-major, next power of two >= K rows per
   // pixel, rounded up to 16-row MMA tiles)
@@ -116,6 +116,12 @@ BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim) {
   B.ddepth = take(std::max<size_t>(S, 1) * 4);
   B.feat = take(std::max<size_t>(rows, 1) * (size_t)std::max(feat_dim, 1) * 4);
   B.gtex = take(std::max<size_t>(rows, 1) * 16);
+  const size_t rc = recompute ? 1 : 0;
+  B.rc_notex = take(rc * P * 12);
+  B.rc_weights = take(rc * S * 4);
+  B.rc_ids = take(rc * S * 4);
+  B.rc_depths = take(rc * S * 4);
+  B.rc_T = take(rc * P * 4);
   B.total = o;
   return B;
 }
@@ -224,7 +230,7 @@ int nexel_bwd_workspace_size(const nexel_camera* cam, const nexel_settings* sett
                              const nexel_field* field, size_t* bytes) {
   if (!cam_ok(cam) || !settings_ok(settings) || !bytes) return NEXEL_ERR_INVALID_ARG;
   int fd = (settings->K > 0 && field) ? field->L * field->F : 0;
-  *bytes = bwd_layout(*cam, settings->K, fd).total;
+  *bytes = bwd_layout(*cam, settings->K, fd, settings->recompute_buffers != 0).total;
   return NEXEL_OK;
 }
 
@@ -296,24 +302,37 @@ int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
                      int accumulate, float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
                      float* d_gamma, float* d_color, float* d_table, float* d_mlp,
                      nexel_stream_t stream) {
-  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !T_final || !d_image)
+  const bool rc = settings && settings->recompute_buffers != 0;
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !d_image)
     return NEXEL_ERR_INVALID_ARG;
+  if (!rc && !T_final) return NEXEL_ERR_INVALID_ARG;
   if (!(settings->alpha_max < 1.f)) return NEXEL_ERR_INVALID_ARG;
   if (N > 0 && (!mu || !quat || !scale || !opacity || !gamma)) return NEXEL_ERR_INVALID_ARG;
   const int K = settings->K;
-  if (K > 0 && (!weights || !ids || !depths || !bwd_ws)) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !rc && (!weights || !ids || !depths)) return NEXEL_ERR_INVALID_ARG;
+  if ((K > 0 || rc) && !bwd_ws) return NEXEL_ERR_INVALID_ARG;
   if (K > 0 && !field_ok(field)) return NEXEL_ERR_INVALID_ARG;
   if (K > 0 && !texture_arch_supported(*settings, *field)) return NEXEL_ERR_UNSUPPORTED;
   WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
   if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
-  BwdLayout B = bwd_layout(*cam, K, K > 0 ? field->L * field->F : 0);
-  if (K > 0 && bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
+  BwdLayout B = bwd_layout(*cam, K, K > 0 ? field->L * field->F : 0, rc);
+  if ((K > 0 || rc) && bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   DevCam c = make_devcam(*cam);
   char* w = (char*)ws;
   char* bw = (char*)bwd_ws;
   cudaError_t e = cudaSuccess;
-  if (K > 0) {
+  if (rc) {
+    // recompute I, W, D, T_final with the collection pass (same kernel, same
+    // inputs, hence the same values the forward produced)
+    weights = (const float*)(bw + B.rc_weights);
+    ids = (const int*)(bw + B.rc_ids);
+    depths = (const float*)(bw + B.rc_depths);
+    T_final = (const float*)(bw + B.rc_T);
+    e = launch_collect_fwd(c, *settings, w, L, (float*)(bw + B.rc_notex), (float*)weights,
+                           (int*)ids, (float*)depths, (float*)T_final, st);
+  }
+  if (e == cudaSuccess && K > 0) {
     if (!accumulate) {
       if (d_table)
         e = cudaMemsetAsync(d_table, 0, sizeof(float) * (size_t)field->L * field->T * field->F, st);

@@ -510,7 +510,7 @@ static cudaError_t binning_t(const DevCam& c, int N, long long n_inst, char* ws,
   KeyT* k0 = (KeyT*)(ws + ((passes & 1) ? L.inst1 : L.inst0));
   KeyT* k1 = (KeyT*)(ws + ((passes & 1) ? L.inst0 : L.inst1));
   int rb = L.key64 ? 32 : L.rank_bits;
-  {
+  if (N > 0) {
     NEXEL_PROF("duplicate", st);
     k_duplicate<KeyT><<<(N + 255) / 256, 256, 0, st>>>(
         N, c.tiles_x, rb, (uint32_t*)(ws + L.did0), (uint2*)(ws + L.rect),

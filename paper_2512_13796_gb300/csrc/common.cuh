@@ -103,6 +103,33 @@ __device__ __forceinline__ float downweight(float focal, float s, float t) {
   return -expm1f(-r * r * 0.15915494309189535f);
 }
 
+// Warp-aggregated float2 atomic add: lanes that target the same table entry
+// are grouped with __match_any_sync, the lowest lane of each group sums the
+// group's values (in lane order, from a per-warp shared-memory slot array)
+// and issues one vector atomic.  Every lane of the warp must call it; lanes
+// with active == false contribute nothing.  s_warp: 32 float2 of this warp.
+__device__ __forceinline__ void warp_atomic_add2(float* base, uint32_t idx, float2 v, bool active,
+                                                 float2* s_warp) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long key =
+      active ? reinterpret_cast<unsigned long long>(base + 2 * (size_t)idx) : 0ull;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  s_warp[lane] = v;
+  __syncwarp();
+  if (active && (peers & ((1u << lane) - 1u)) == 0u) {
+    float2 acc = make_float2(0.f, 0.f);
+    unsigned m = peers;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1u;
+      acc.x += s_warp[b].x;
+      acc.y += s_warp[b].y;
+    }
+    atomicAdd(reinterpret_cast<float2*>(base) + idx, acc);
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------ workspace
 // Main workspace (binning results and per-pixel replay data).  Regions that
 // depend only on (camera, K, N) come first; the instance buffers and the
@@ -117,13 +144,13 @@ struct WsLayout {
 // Backward scratch (per sample): dL/dW_j, dL/dD_j, the field features and
 // the texture gradient.
 struct BwdLayout {
-  size_t dweff, ddepth, feat, gtex, total;
+  size_t dweff, ddepth, feat, gtex, rc_notex, rc_weights, rc_ids, rc_depths, rc_T, total;
 };
 
 WsLayout ws_layout(const nexel_camera& cam, int K, int N, long long cap);
 // Largest capacity whose layout fits in ws_bytes (cap < 0 if none).
 WsLayout ws_layout_for_bytes(const nexel_camera& cam, int K, int N, size_t ws_bytes);
-BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim);
+BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim, bool recompute);
 DevCam make_devcam(const nexel_camera& cam);
 
 // Launch accounting: construct one before each kernel launch (see prof.cu).

@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_bwd_bf16(
   using Bw = Bf16W<IN, H1, H2>;
   constexpr int HL = Bw::HL;
   extern __shared__ __align__(16) __nv_bfloat16 sw[];
+  __shared__ float2 s_red[kWarps][32];
   load_weights_bf16<IN, H1, H2>(f.w, sw, true);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -211,8 +212,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_bwd_bf16(
 #pragma unroll
     for (int nt = 0; nt < IN / 8; ++nt) {
       const int l = 4 * nt + t;
-      if (A.valid) dtA += level_backward<TT>(f, l, A.x, A.D, A.d, gin[nt][0], gin[nt][1], d_table);
-      if (B.valid) dtB += level_backward<TT>(f, l, B.x, B.D, B.d, gin[nt][2], gin[nt][3], d_table);
+      const float ra = level_backward<TT>(f, l, A.x, A.D, A.d, gin[nt][0], gin[nt][1], d_table,
+                                          A.valid, s_red[warp]);
+      const float rb = level_backward<TT>(f, l, B.x, B.D, B.d, gin[nt][2], gin[nt][3], d_table,
+                                          B.valid, s_red[warp]);
+      if (A.valid) dtA += ra;
+      if (B.valid) dtB += rb;
     }
     dtA += __shfl_xor_sync(0xffffffffu, dtA, 1);
     dtA += __shfl_xor_sync(0xffffffffu, dtA, 2);

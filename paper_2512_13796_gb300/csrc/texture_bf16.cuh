@@ -175,10 +175,13 @@ __device__ __forceinline__ float2 level_feature(const FieldDev& f, int l, float3
 }
 
 // Backward of one (sample, level): table scatter and dL/dt contribution
-// (through Delta and, with x = o + t d, the trilinear weights).
+// (through Delta and, with x = o + t d, the trilinear weights).  Called by
+// all lanes of the warp together (warp-aggregated atomics); inactive lanes
+// scatter nothing and their return value is meaningless.
 template <typename TT>
 __device__ __forceinline__ float level_backward(const FieldDev& f, int l, float3 x, float t,
-                                                float3 d, float g0, float g1, float* d_table) {
+                                                float3 d, float g0, float g1, float* d_table,
+                                                bool active, float2* s_warp) {
   const size_t T = (size_t)f.mask + 1;
   const TT* tl = reinterpret_cast<const TT*>(f.table) + (size_t)l * T * 2;
   float* dl = d_table ? d_table + (size_t)l * T * 2 : nullptr;
@@ -206,7 +209,7 @@ __device__ __forceinline__ float level_backward(const FieldDev& f, int l, float3
     pz = fmaf(ge, wx * wy * sz, pz);
     if (dl) {
       const float sc = dw * w;
-      atomicAdd(reinterpret_cast<float2*>(dl) + idx, make_float2(sc * g0, sc * g1));
+      warp_atomic_add2(dl, idx, make_float2(sc * g0, sc * g1), active, s_warp);
     }
   }
   const float ddw = -(1.f - dw) * r * r * 0.3183098861837907f / t;

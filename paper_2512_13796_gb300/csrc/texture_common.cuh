@@ -75,7 +75,8 @@ __device__ __forceinline__ void hash_features(const FieldDev& f, float3 x, float
 // the positional / depth gradient; returns dL/dt for x = o + t d.
 template <int IN, typename TT>
 __device__ __forceinline__ float hash_backward(const FieldDev& f, float3 x, float t, float3 d,
-                                               const float* gin, float* d_table) {
+                                               const float* gin, float* d_table, bool active,
+                                               float2* s_warp) {
   const TT* tab = reinterpret_cast<const TT*>(f.table);
   const size_t T = (size_t)f.mask + 1;
   float dt = 0.f, gxx = 0.f, gxy = 0.f, gxz = 0.f;
@@ -108,7 +109,7 @@ __device__ __forceinline__ float hash_backward(const FieldDev& f, float3 x, floa
       pz = fmaf(ge, wx * wy * sz, pz);
       if (dl) {
         const float sc = dw * w;
-        atomicAdd(reinterpret_cast<float2*>(dl) + idx, make_float2(sc * g0, sc * g1));
+        warp_atomic_add2(dl, idx, make_float2(sc * g0, sc * g1), active, s_warp);
       }
     }
     // Delta = 1 - exp(-r^2 / 2pi), r = f / (s t): dDelta/dt = -(1 - Delta) r^2 / (pi t)

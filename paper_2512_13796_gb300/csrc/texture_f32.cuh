@@ -83,41 +83,47 @@ __global__ void __launch_bounds__(256) k_tex_bwd_f32(
   __shared__ __align__(16) float sW[A::kWeights];
   for (int k = threadIdx.x; k < A::kWeights; k += blockDim.x) sW[k] = f.w[k];
   __syncthreads();
+  __shared__ float2 s_red[8][32];
   const long long S = (long long)c.W * c.H * K;
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S) return;
-  const long long p = s / K;
-  const int id = ids[s];
-  float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (id < 0) {
+  // no early exit: the table scatter is warp-aggregated, every lane takes part
+  const bool in_range = s < S;
+  const int id = in_range ? ids[s] : -1;
+  const bool active = id >= 0;
+  float gin[IN];
+#pragma unroll
+  for (int k = 0; k < IN; ++k) gin[k] = 0.f;
+  float3 x = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+  float D = 1.f;
+  if (active) {
+    const long long p = s / K;
+    const float wj = weights[s];
+    D = depths[s];
+    d = pixel_dir(c, (int)(p % c.W), (int)(p / c.W));
+    x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
+    float feat[IN];
+    hash_features<IN, TT>(f, x, D, feat);
+    float out[3], h1[H1], h2[H2 > 0 ? H2 : 1];
+    mlp_fwd_f32<IN, H1, H2>(sW, feat, out, h1, h2);
+    const float dc0 = d_image[3 * p], dc1 = d_image[3 * p + 1], dc2 = d_image[3 * p + 2];
+    float gT[3] = {wj * dc0, wj * dc1, wj * dc2};
+    if (d_textures) {
+      gT[0] += d_textures[3 * s]; gT[1] += d_textures[3 * s + 1]; gT[2] += d_textures[3 * s + 2];
+    }
+    float dwe = out[0] * dc0 + out[1] * dc1 + out[2] * dc2;
+    if (d_weights) dwe += d_weights[s];
+    dweff[s] = dwe;
+    mlp_bwd_input_f32<IN, H1, H2>(sW, gT, h1, h2, gin);
+    for (int k = 0; k < IN; ++k) feat_out[s * IN + k] = feat[k];
+    gtex_out[s] = make_float4(gT[0], gT[1], gT[2], 0.f);
+  } else if (in_range) {
     dweff[s] = 0.f;
     ddepth[s] = 0.f;
     for (int k = 0; k < IN; ++k) feat_out[s * IN + k] = 0.f;
-    gtex_out[s] = g4;
-    return;
+    gtex_out[s] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  const float wj = weights[s];
-  const float D = depths[s];
-  float3 d = pixel_dir(c, (int)(p % c.W), (int)(p / c.W));
-  float3 x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
-  float feat[IN];
-  hash_features<IN, TT>(f, x, D, feat);
-  float out[3], h1[H1], h2[H2 > 0 ? H2 : 1];
-  mlp_fwd_f32<IN, H1, H2>(sW, feat, out, h1, h2);
-  const float dc0 = d_image[3 * p], dc1 = d_image[3 * p + 1], dc2 = d_image[3 * p + 2];
-  float gT[3] = {wj * dc0, wj * dc1, wj * dc2};
-  if (d_textures) {
-    gT[0] += d_textures[3 * s]; gT[1] += d_textures[3 * s + 1]; gT[2] += d_textures[3 * s + 2];
-  }
-  float dwe = out[0] * dc0 + out[1] * dc1 + out[2] * dc2;
-  if (d_weights) dwe += d_weights[s];
-  dweff[s] = dwe;
-  float gin[IN];
-  mlp_bwd_input_f32<IN, H1, H2>(sW, gT, h1, h2, gin);
-  for (int k = 0; k < IN; ++k) feat_out[s * IN + k] = feat[k];
-  gtex_out[s] = make_float4(gT[0], gT[1], gT[2], 0.f);
-  float dD = hash_backward<IN, TT>(f, x, D, d, gin, d_table);
-  ddepth[s] = dD;
+  const float dD = hash_backward<IN, TT>(f, x, D, d, gin, d_table, active, s_red[threadIdx.x >> 5]);
+  if (active) ddepth[s] = dD;
 }
 
 // Weight gradients: dW_l = sum_s delta_{l+1}[s] (x) a_l[s].  Each CTA walks

@@ -25,7 +25,8 @@ def camera_struct(cam) -> N_.Camera:
     return c
 
 
-def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32") -> N_.Settings:
+def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32",
+                    recompute: bool = False) -> N_.Settings:
     s = N_.Settings()
     s.K = int(st.K)
     s.alpha_min, s.alpha_max, s.T_min = float(st.alpha_min), float(st.alpha_max), float(st.T_min)
@@ -33,6 +34,7 @@ def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32") -> N_.S
         s.bg[i] = float(st.bg[i])
     s.grid_dtype = {"f32": N_.F32, "f16": N_.F16}[grid_dtype]
     s.mlp_dtype = {"f32": N_.F32, "bf16": N_.BF16}[mlp_dtype]
+    s.recompute_buffers = 1 if recompute else 0
     return s
 
 
@@ -168,8 +170,9 @@ def backward(ws: Workspace, cam_s, st_s, field, table_store, weights, mu, quat, 
     N_.nexel_render_bwd(cam_s, st_s, fs, N, mu.data_ptr(), quat.data_ptr(), scale.data_ptr(),
                         opacity.data_ptr(), gamma.data_ptr(), buf.data_ptr(), buf.numel(),
                         bws.data_ptr(), bws.numel(),
-                        _ptr(fwd["weights"]) if K else None, _ptr(fwd["ids"]) if K else None,
-                        _ptr(fwd["depths"]) if K else None, fwd["T_final"].data_ptr(),
+                        *((None, None, None, None) if st_s.recompute_buffers else
+                          (_ptr(fwd["weights"]) if K else None, _ptr(fwd["ids"]) if K else None,
+                           _ptr(fwd["depths"]) if K else None, fwd["T_final"].data_ptr())),
                         d_image.contiguous().data_ptr(),
                         _ptr(d_weights.contiguous()) if d_weights is not None else None,
                         _ptr(d_textures.contiguous()) if d_textures is not None else None,

@@ -14,6 +14,7 @@ from helpers import compare_forward, compare_grads, masked_upstream, run_gpu
 pytestmark = pytest.mark.gpu
 
 TIE = 1e-5
+CELL = 2e-6  # world units: FP32 intersection points differ from FP64 by < 1e-6
 TOL_F32 = 1e-5
 GRAD_RTOL = 1e-3
 
@@ -38,7 +39,7 @@ def test_config0_forward(dev, gamma):
     w = synth.workload(0, gamma=gamma)
     cam, st = w.cameras[0], w.settings
     fw, _, _ = run_gpu(w.scene, cam, st, w.field, dev)
-    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE)
+    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE, cell_tol=CELL)
     s = compare_forward(fw, ref, st.K, TOL_F32)
     _report(f"config0 fwd gamma={gamma}", s)
     assert s["n_tie"] < 0.25 * s["n_pix"]
@@ -49,7 +50,7 @@ def test_config0_backward(dev, gamma):
     w = synth.workload(0, gamma=gamma)
     cam, st = w.cameras[0], w.settings
     P, K = cam.width * cam.height, st.K
-    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE)
+    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE, cell_tol=CELL)
     pix = ref["pixels"]
     ok = ref["tie"] == 0
     dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=5)
@@ -65,7 +66,7 @@ def cfg1():
     w = synth.workload(1)
     cam = w.cameras[0]
     pix = synth.pixel_sample(cam, 4096, 4, seed=1)
-    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE)
+    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE, cell_tol=CELL)
     return w, pix, ref
 
 
@@ -95,7 +96,7 @@ def cfg2():
     w = synth.workload(2, precision="f32")
     cam = w.cameras[0]
     pix = synth.pixel_sample(cam, 2048, 3, seed=2)
-    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE)
+    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE, cell_tol=CELL)
     return w, pix, ref
 
 
@@ -122,9 +123,11 @@ def test_config2_fp32_backward_sampled(dev, cfg2):
 
 # Reduced-precision form: FP16 table, BF16 MLP on tensor cores with FP32
 # accumulation.  Colours within 2e-3 per channel of the FP64 oracle (which
-# reads the FP32 table); gradients within 3e-2 of the class scale: a BF16
-# operand carries a relative rounding error of 2^-9 and the input gradient
-# passes three BF16 products, so 1e-2-level relative error is expected.
+# reads the FP32 table).  Gradients: a BF16 operand carries a relative
+# rounding error of 2^-9 and the feature gradient passes three BF16
+# products, after which the positional gradient sums 16 levels x 8 corners
+# with cancellation; the gradient vector of each parameter class is
+# compared in relative L2 norm.
 TOL_BF16 = 2e-3
 GRAD_RTOL_BF16 = 3e-2
 
@@ -148,7 +151,7 @@ def test_bf16_backward_sampled(dev, cfg, request):
                        d_weights=dW, d_textures=dT)
     sel = pix[ok]
     gr = oracle.render_bwd(w.scene, cam, st, w.field, sel, dI[sel], dW[sel], dT[sel])
-    s = compare_grads(gg, gr, GRAD_RTOL_BF16)
+    s = compare_grads(gg, gr, GRAD_RTOL_BF16, metric="l2")
     _report(f"{cfg} bf16 bwd", s)
 
 
@@ -242,3 +245,23 @@ def test_deterministic_forward(dev):
     b, _, _ = run_gpu(w.scene, w.cameras[0], w.settings, w.field, dev)
     for k in ("image", "ids", "weights", "depths", "textures", "T_final"):
         np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("mlp", ["f32", "bf16"])
+def test_recomputed_buffers_match_stored(dev, mlp):
+    """Backward with I, W, D, T_final recomputed inside the backward (the
+    memory-saving variant) gives the same gradients as the backward that
+    reads the forward's saved buffers (up to the summation order of the
+    float atomics)."""
+    w = synth.workload(1)
+    cam, st = w.cameras[0], w.settings
+    P, K = cam.width * cam.height, st.K
+    rng = np.random.default_rng(3)
+    dI = rng.normal(size=(P, 3))
+    dW = rng.normal(size=(P, K))
+    grid = "f16" if mlp == "bf16" else "f32"
+    _, g1, _ = run_gpu(w.scene, cam, st, w.field, dev, grid=grid, mlp=mlp, d_image=dI, d_weights=dW)
+    _, g2, _ = run_gpu(w.scene, cam, st, w.field, dev, grid=grid, mlp=mlp, d_image=dI, d_weights=dW,
+                       recompute=True)
+    for k in ("mu", "quat", "scale", "opacity", "gamma", "color", "table", "mlp"):
+        np.testing.assert_allclose(g1[k], g2[k], rtol=1e-4, atol=1e-6 * np.abs(g1[k]).max())

@@ -405,3 +405,18 @@ def test_clamped_alpha_has_no_gradient():
     g = oracle.render_bwd(sc, cam, st, None, pix, np.ones((pix.size, 3)))
     assert g["opacity"][0] == 0.0 and np.all(g["scale"] == 0.0)
     np.testing.assert_allclose(g["color"][0], 0.9 * pix.size)
+
+
+def test_procedural_targets_reduce_to_constant_colour():
+    """With frequency 0 the procedural texture is a constant per channel, so
+    the procedural render equals the plain render (K = 0) with that colour."""
+    cam = synth.front_camera(24, 20)
+    sc = small_scene(17, n=90)
+    st = synth.Settings(K=0)
+    img = oracle.render_procedural(sc, cam, st, 0.0)
+    tau = np.array([0.5 + 0.4 * math.sin(2 * c) * math.sin(c) + 0.1 * math.sin(-c)
+                    for c in range(3)])
+    sc2 = synth.Scene(sc.mu, sc.quat, sc.scale, sc.opacity, sc.gamma,
+                      np.tile(tau, (sc.n, 1)))
+    ref = oracle.render(sc2, cam, st, None)
+    np.testing.assert_allclose(img, ref["image"], rtol=1e-12, atol=1e-14)
