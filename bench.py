@@ -233,6 +233,8 @@ def main():
     ap.add_argument("--impl", default="nexels", choices=["nexels", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default=None, help="write per-kernel times here")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2],
+                    help="2: the headline workload; 1: the 50k-surfel 800x800 case (profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -285,7 +287,7 @@ def main():
     _native.lib()
     stream = torch.cuda.current_stream()
     peaks, peak_kind = load_peaks()
-    w = synth.workload(2)
+    w = synth.workload(args.config)
     jobs = {"bf16": Job(w, dev, "bf16"), "f32": Job(w, dev, "f32")}
     P = w.cameras[0].width * w.cameras[0].height
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -379,7 +381,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms["bf16_train"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "surfels": w.scene.n, "width": W, "height": H,
+        "config": {"workload": WORKLOAD if args.config == 2 else "config1: 50k surfels, 800x800, K=4, hash 8x2^16x2, MLP 16-64-3", "surfels": w.scene.n, "width": W, "height": H,
                    "K": w.settings.K, "n_instances": int(n_inst),
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
