@@ -55,7 +55,8 @@ class OCam(C.Structure):
 class OSet(C.Structure):
     _fields_ = [("K", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
                 ("T_min", C.c_double), ("bg", C.c_double * 3), ("tie_tol", C.c_double),
-                ("order_tol", C.c_double), ("cell_tol", C.c_double)]
+                ("order_tol", C.c_double), ("cell_tol", C.c_double),
+                ("relu_tol", C.c_double)]
 
 
 class OField(C.Structure):
@@ -95,7 +96,7 @@ def _cam(cam) -> OCam:
     return c
 
 
-def _set(st, tie_tol, order_tol=1e-6, cell_tol=0.0) -> OSet:
+def _set(st, tie_tol, order_tol=1e-6, cell_tol=0.0, relu_tol=0.0) -> OSet:
     s = OSet()
     s.K = int(st.K)
     s.alpha_min, s.alpha_max, s.T_min = float(st.alpha_min), float(st.alpha_max), float(st.T_min)
@@ -104,6 +105,7 @@ def _set(st, tie_tol, order_tol=1e-6, cell_tol=0.0) -> OSet:
     s.tie_tol = float(tie_tol)
     s.order_tol = float(min(order_tol, tie_tol)) if tie_tol > 0 else 0.0
     s.cell_tol = float(cell_tol)
+    s.relu_tol = float(relu_tol)
     return s
 
 
@@ -134,11 +136,12 @@ def all_pixels(cam) -> np.ndarray:
     return np.arange(cam.width * cam.height, dtype=np.int32)
 
 
-TIE_BITS = {1: "topk", 2: "alpha", 4: "T_min", 8: "near", 16: "order", 32: "cell"}
+TIE_BITS = {1: "topk", 2: "alpha", 4: "T_min", 8: "near", 16: "order", 32: "cell", 64: "relu"}
 
 
 def render(scene, cam, settings, field=None, pixels=None, tie_tol: float = 1e-6,
-           table=None, order_tol: float = 1e-6, cell_tol: float = 0.0) -> dict:
+           table=None, order_tol: float = 1e-6, cell_tol: float = 0.0,
+           relu_tol: float = 0.0) -> dict:
     """Forward of the listed pixels.  ``table`` overrides field.table (e.g.
     the fp16-rounded copy the reduced-precision path reads).  A pixel is
     flagged in ``tie`` when one of its discrete choices lies within tie_tol
@@ -147,7 +150,9 @@ def render(scene, cam, settings, field=None, pixels=None, tie_tol: float = 1e-6,
     within order_tol, two consecutive composited surfels with equal centre
     depth (16); and, when cell_tol > 0, a textured intersection within
     cell_tol (world units) of a hash-cell face of some level (32), where the
-    trilinear interpolation has a kink."""
+    trilinear interpolation has a kink; and, when relu_tol > 0, a textured
+    sample with a hidden MLP pre-activation within relu_tol (relative to the
+    sum of the magnitudes of its terms) of zero (64), a ReLU kink."""
     L = lib()
     pix = all_pixels(cam) if pixels is None else np.ascontiguousarray(pixels, np.int32)
     n, K = pix.size, settings.K
@@ -157,7 +162,7 @@ def render(scene, cam, settings, field=None, pixels=None, tie_tol: float = 1e-6,
                n_contrib=np.zeros(n, np.int32), tie=np.zeros(n, np.int32))
     fr = _FieldRef(field, table) if field is not None else None
     sv = _surfels(scene)
-    c, s = _cam(cam), _set(settings, tie_tol, order_tol, cell_tol)
+    c, s = _cam(cam), _set(settings, tie_tol, order_tol, cell_tol, relu_tol)
     rc = L.oracle_render(C.byref(c), C.byref(s), C.byref(fr.s) if fr else None,
                          C.c_int(scene.n), *[_p(a) for a in sv], C.c_int(n), _p(pix),
                          *[_p(out[k]) for k in ("image", "notex", "weights", "ids", "depths",

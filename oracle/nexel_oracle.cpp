@@ -49,6 +49,7 @@ struct OSet {
   double tie_tol;    // relative width used to flag threshold / top-K ties
   double order_tol;  // relative width used to flag centre-depth order ties
   double cell_tol;   // world-space distance to a hash-cell face flagged as a kink
+  double relu_tol;   // relative width used to flag hidden pre-activations near 0
 };
 
 struct OField {
@@ -256,7 +257,10 @@ struct PixelResult {
   std::vector<std::vector<LevelEval>> lev;             // per slot level evals
 };
 
-enum { TIE_TOPK = 1, TIE_ALPHA = 2, TIE_TMIN = 4, TIE_NEAR = 8, TIE_ORDER = 16, TIE_CELL = 32 };
+enum {
+  TIE_TOPK = 1, TIE_ALPHA = 2, TIE_TMIN = 4, TIE_NEAR = 8, TIE_ORDER = 16, TIE_CELL = 32,
+  TIE_RELU = 64
+};
 
 inline bool near_rel(double a, double b, double tol) {
   return std::fabs(a - b) <= tol * std::max(std::fabs(a), std::fabs(b));
@@ -359,6 +363,25 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
     mlp_forward(*fd, feat.data(), acts);
     for (int ch = 0; ch < 3; ++ch) r.tex[j][ch] = acts[fd->n_layers][ch];
     for (int ch = 0; ch < 3; ++ch) r.image[ch] += e.w * r.tex[j][ch];
+    // a hidden pre-activation within relu_tol of zero (relative to the sum
+    // of the magnitudes of its terms) is a ReLU decision that a
+    // lower-precision evaluation may take the other way
+    if (st.relu_tol > 0.0) {
+      const double* W = fd->weights;
+      for (int l = 0; l + 1 < fd->n_layers; ++l) {
+        int ni = fd->widths[l], no = fd->widths[l + 1];
+        for (int o2 = 0; o2 < no; ++o2) {
+          double a = 0.0, mag = 0.0;
+          for (int i = 0; i < ni; ++i) {
+            double term = W[(size_t)o2 * ni + i] * acts[l][i];
+            a += term;
+            mag += std::fabs(term);
+          }
+          if (std::fabs(a) <= st.relu_tol * mag && mag > 0.0) r.tie |= TIE_RELU;
+        }
+        W += (size_t)no * ni;
+      }
+    }
     if (keep) r.acts[j] = std::move(acts);
   }
 }

@@ -35,6 +35,8 @@ static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
   size_t n = (size_t)std::max(N, 1);
   L.geom_orig = take(n * kRecF4 * 16);
   L.geom_sorted = take(n * kRecF4 * 16);
+  L.aux_orig = take(n * kAuxF4 * 16);
+  L.aux_sorted = take(n * kAuxF4 * 16);
   L.dkey0 = take(n * 4);
   L.dkey1 = take(n * 4);
   L.did0 = take(n * 4);
@@ -116,6 +118,9 @@ BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim, bool recomput
   B.ddepth = take(std::max<size_t>(S, 1) * 4);
   B.feat = take(std::max<size_t>(rows, 1) * (size_t)std::max(feat_dim, 1) * 4);
   B.gtex = take(std::max<size_t>(rows, 1) * 16);
+  // level-major (row stride rounded up to 32 rows)
+  B.gin = take((std::max<size_t>(rows, 1) + 32) * (size_t)std::max(feat_dim, 1) * 4);
+  B.dtl = take((std::max<size_t>(rows, 1) + 32) * (size_t)std::max(feat_dim / 2, 1) * 4);
   const size_t rc = recompute ? 1 : 0;
   B.rc_notex = take(rc * P * 12);
   B.rc_weights = take(rc * S * 4);

@@ -76,8 +76,9 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __re
                              const float* __restrict__ quat, const float* __restrict__ scale,
                              const float* __restrict__ opac, const float* __restrict__ gam,
                              const float* __restrict__ color, float4* __restrict__ geom,
-                             uint32_t* __restrict__ dkey, uint32_t* __restrict__ did,
-                             uint2* __restrict__ rect, uint32_t* __restrict__ count) {
+                             float4* __restrict__ aux, uint32_t* __restrict__ dkey,
+                             uint32_t* __restrict__ did, uint2* __restrict__ rect,
+                             uint32_t* __restrict__ count) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   did[i] = (uint32_t)i;
@@ -164,6 +165,7 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __re
   float4* g = geom + (size_t)i * kRecF4;
   if (!ok) {
     for (int k = 0; k < kRecF4; ++k) g[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < kAuxF4; ++k) aux[(size_t)i * kAuxF4 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
   // projected centre in float-float: cp = f * (mc / z) + c
@@ -171,21 +173,21 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __re
   ff dx = ff_div(mc[0], zz), dy = ff_div(mc[1], zz);
   ff cpx = ff_add(ff_mul_f(dx, c.fx), {c.cx, 0.f});
   ff cpy = ff_add(ff_mul_f(dy, c.fy), {c.cy, 0.f});
-  // per-pixel-unit plane tilt and in-plane gradients (derivation in the
-  // backward kernel below)
-  float ax = v1c.x / s1, ay = v1c.y / s1, az = v1c.z / s1;
-  float bx = v2c.x / s2, by = v2c.y / s2, bz = v2c.z / s2;
-  float ad = dmx * ax + dmy * ay + az;
-  float bd = dmx * bx + dmy * by + bz;
-  float ra = ad / dn0, rb = bd / dn0;
-  float Ax = (ax - nc.x * ra) / c.fx, Ay = (ay - nc.y * ra) / c.fy;
-  float Bx = (bx - nc.x * rb) / c.fx, By = (by - nc.y * rb) / c.fy;
-  float nx = nc.x / (c.fx * dn0), ny = nc.y / (c.fy * dn0);
+  // u and v numerators (common.cuh): Cu = -z (d_mu x v2) / s1 and
+  // Cv = z (d_mu x v1) / s2, x and y components, with z d_mu = mu_c
+  const float mx = mc[0].hi, my = mc[1].hi;
+  const float Cux = -(my * v2c.z - z * v2c.y) / s1, Cuy = -(z * v2c.x - mx * v2c.z) / s1;
+  const float Cvx = (my * v1c.z - z * v1c.y) / s2, Cvy = (z * v1c.x - mx * v1c.z) / s2;
   g[0] = make_float4(cpx.hi, cpy.hi, cpx.lo, cpy.lo);
   g[1] = make_float4(z, o, g1, g2);
-  g[2] = make_float4(nx, ny, Ax, Ay);
-  g[3] = make_float4(Bx, By, 0.f, 0.f);
+  g[2] = make_float4(nc.x / c.fx, nc.y / c.fy, Cux / c.fx, Cuy / c.fy);
+  g[3] = make_float4(Cvx / c.fx, Cvy / c.fy, dn0, 0.f);
   g[4] = make_float4(color[3 * i], color[3 * i + 1], color[3 * i + 2], __uint_as_float((uint32_t)i));
+  float4* a = aux + (size_t)i * kAuxF4;
+  a[0] = make_float4(mx, my, z, s1);
+  a[1] = make_float4(v1c.x, v1c.y, v1c.z, s2);
+  a[2] = make_float4(v2c.x, v2c.y, v2c.z, 0.f);
+  a[3] = make_float4(nc.x, nc.y, nc.z, 0.f);
 }
 
 // ------------------------------------------------------- scan (exclusive)
@@ -421,7 +423,8 @@ static cudaError_t radix_sort(KeyT* k0, KeyT* k1, uint32_t* v0, uint32_t* v1, lo
 
 // ------------------------------------------- permutation, duplicate, ranges
 __global__ void k_permute(int N, const uint32_t* __restrict__ did, const float4* __restrict__ geom,
-                          float4* __restrict__ geom_sorted, const uint32_t* __restrict__ count,
+                          float4* __restrict__ geom_sorted, const float4* __restrict__ aux,
+                          float4* __restrict__ aux_sorted, const uint32_t* __restrict__ count,
                           uint32_t* __restrict__ offs) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
@@ -430,6 +433,10 @@ __global__ void k_permute(int N, const uint32_t* __restrict__ did, const float4*
   float4* d = geom_sorted + (size_t)r * kRecF4;
 #pragma unroll
   for (int k = 0; k < kRecF4; ++k) d[k] = s[k];
+  const float4* sa = aux + (size_t)id * kAuxF4;
+  float4* da = aux_sorted + (size_t)r * kAuxF4;
+#pragma unroll
+  for (int k = 0; k < kAuxF4; ++k) da[k] = sa[k];
   offs[r] = count[id];
 }
 
@@ -471,7 +478,8 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
     NEXEL_PROF("preprocess", st);
     k_preprocess<<<(N + 255) / 256, 256, 0, st>>>(
         c, s.alpha_min, N, mu, quat, scale, opacity, gamma, color, (float4*)(ws + L.geom_orig),
-        (uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.did0), (uint2*)(ws + L.rect),
+        (float4*)(ws + L.aux_orig), (uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.did0),
+        (uint2*)(ws + L.rect),
         (uint32_t*)(ws + L.count));
   }
   return cudaGetLastError();
@@ -495,6 +503,8 @@ cudaError_t launch_count_scan(int N, char* ws, const WsLayout& L, cudaStream_t s
     k_permute<<<(N + 255) / 256, 256, 0, st>>>(N, (uint32_t*)(ws + L.did0),
                                                (float4*)(ws + L.geom_orig),
                                                (float4*)(ws + L.geom_sorted),
+                                               (float4*)(ws + L.aux_orig),
+                                               (float4*)(ws + L.aux_sorted),
                                                (uint32_t*)(ws + L.count), (uint32_t*)(ws + L.offs));
   }
   uint32_t* counters = (uint32_t*)(ws + L.counters);
@@ -541,17 +551,13 @@ cudaError_t launch_binning(const DevCam& c, int N, long long n_inst, char* ws, c
 }
 
 // ------------------------------------------------------ preprocess backward
-// Chain rule from the packed-record gradients (rank order, written by the
-// collection backward) to mu, q (through the normalisation), sigma, o,
-// gamma and colour.  Forward relations, per surfel (camera space):
-//   mc = Rc mu + t, (v1c, v2c, nc) = Rc (v1, v2, n), z = mc.z,
-//   dm = (mc.x / z, mc.y / z, 1), cp = (fx dm.x + cx, fy dm.y + cy),
-//   dn0 = dm . nc, nx = nc.x / (fx dn0), ny = nc.y / (fy dn0),
-//   a = v1c / s1, ra = (dm . a) / dn0, A = ((a.x - nc.x ra) / fx, (a.y - nc.y ra) / fy),
-//   likewise B with v2c / s2.
-__global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ mu,
-                                 const float* __restrict__ quat, const float* __restrict__ scale,
-                                 const float* __restrict__ opac, const float* __restrict__ gam,
+// The collection backward accumulates, per surfel (rank order), the
+// gradient with respect to its camera-space frame: mu_c, v1_c, v2_c, n_c,
+// sigma, opacity, gamma and colour.  Here those are rotated back to world
+// space (x_c = R x + t, so dL/dx = R^T dL/dx_c) and the three frame columns
+// are taken through the rotation of the normalised quaternion and the
+// normalisation itself.
+__global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ quat,
                                  const uint32_t* __restrict__ did, const uint32_t* __restrict__ dkey,
                                  const float* __restrict__ gs, float* __restrict__ d_mu,
                                  float* __restrict__ d_quat, float* __restrict__ d_scale,
@@ -562,56 +568,14 @@ __global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ mu,
   if (dkey[r] == 0xFFFFFFFFu) return;  // culled: no gradient
   uint32_t i = did[r];
   const float* g = gs + (size_t)r * kGradStride;
-  float g_cpx = g[0], g_cpy = g[1], g_z = g[2], g_o = g[3], g_g1 = g[4], g_g2 = g[5];
-  float g_nx = g[6], g_ny = g[7], g_Ax = g[8], g_Ay = g[9], g_Bx = g[10], g_By = g[11];
-  float m[3] = {mu[3 * i], mu[3 * i + 1], mu[3 * i + 2]};
+  const float3 g_m = rotT(c.R, make_float3(g[0], g[1], g[2]));
+  const float3 g_v1 = rotT(c.R, make_float3(g[3], g[4], g[5]));
+  const float3 g_v2 = rotT(c.R, make_float3(g[6], g[7], g[8]));
+  const float3 g_n = rotT(c.R, make_float3(g[9], g[10], g[11]));
   float q0 = quat[4 * i], q1 = quat[4 * i + 1], q2 = quat[4 * i + 2], q3 = quat[4 * i + 3];
   float qn = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
   float w = q0 * qn, x = q1 * qn, y = q2 * qn, zq = q3 * qn;
-  float3 v1, v2, n;
-  quat_cols(w, x, y, zq, v1, v2, n);
-  float s1 = scale[2 * i], s2 = scale[2 * i + 1];
-  float3 mcv = rot(c.R, make_float3(m[0], m[1], m[2]));
-  mcv.x += c.t[0]; mcv.y += c.t[1]; mcv.z += c.t[2];
-  float3 v1c = rot(c.R, v1), v2c = rot(c.R, v2), nc = rot(c.R, n);
-  float z = mcv.z;
-  float dmx = mcv.x / z, dmy = mcv.y / z;
-  float dn0 = dmx * nc.x + dmy * nc.y + nc.z;
-  float3 a = make_float3(v1c.x / s1, v1c.y / s1, v1c.z / s1);
-  float3 b = make_float3(v2c.x / s2, v2c.y / s2, v2c.z / s2);
-  float ad = dmx * a.x + dmy * a.y + a.z, bd = dmx * b.x + dmy * b.y + b.z;
-  float ra = ad / dn0, rb = bd / dn0;
-  float nxv = nc.x / (c.fx * dn0), nyv = nc.y / (c.fy * dn0);
-  // backward
-  float gApx = g_Ax / c.fx, gApy = g_Ay / c.fy, gBpx = g_Bx / c.fx, gBpy = g_By / c.fy;
-  float3 g_a = make_float3(gApx, gApy, 0.f), g_b = make_float3(gBpx, gBpy, 0.f);
-  float3 g_nc = make_float3(-gApx * ra - gBpx * rb, -gApy * ra - gBpy * rb, 0.f);
-  float g_ra = -(gApx * nc.x + gApy * nc.y), g_rb = -(gBpx * nc.x + gBpy * nc.y);
-  float g_ad = g_ra / dn0, g_bd = g_rb / dn0;
-  float g_dn0 = -(g_ra * ra + g_rb * rb) / dn0;
-  g_a.x += g_ad * dmx; g_a.y += g_ad * dmy; g_a.z += g_ad;
-  g_b.x += g_bd * dmx; g_b.y += g_bd * dmy; g_b.z += g_bd;
-  float g_dmx = g_ad * a.x + g_bd * b.x, g_dmy = g_ad * a.y + g_bd * b.y;
-  // nx = nc.x / (fx dn0)
-  g_nc.x += g_nx / (c.fx * dn0);
-  g_nc.y += g_ny / (c.fy * dn0);
-  g_dn0 += -(g_nx * nxv + g_ny * nyv) / dn0;
-  // dn0 = dm . nc
-  g_dmx += g_dn0 * nc.x; g_dmy += g_dn0 * nc.y;
-  g_nc.x += g_dn0 * dmx; g_nc.y += g_dn0 * dmy; g_nc.z += g_dn0;
-  // cp
-  g_dmx += c.fx * g_cpx;
-  g_dmy += c.fy * g_cpy;
-  // dm = mc.xy / z, z = mc.z
-  float3 g_mc = make_float3(g_dmx / z, g_dmy / z, g_z - (g_dmx * mcv.x + g_dmy * mcv.y) / (z * z));
-  // a = v1c / s1
-  float3 g_v1c = make_float3(g_a.x / s1, g_a.y / s1, g_a.z / s1);
-  float3 g_v2c = make_float3(g_b.x / s2, g_b.y / s2, g_b.z / s2);
-  float g_s1 = -(g_a.x * a.x + g_a.y * a.y + g_a.z * a.z) / s1;
-  float g_s2 = -(g_b.x * b.x + g_b.y * b.y + g_b.z * b.z) / s2;
-  float3 g_m = rotT(c.R, g_mc);
-  float3 g_v1 = rotT(c.R, g_v1c), g_v2 = rotT(c.R, g_v2c), g_n = rotT(c.R, g_nc);
-  // rotation of the unit quaternion: G[row][col] with columns v1, v2, n
+  // dL/dR with R = [v1 v2 n] (row-major: G[row][col])
   float G[9] = {g_v1.x, g_v2.x, g_n.x, g_v1.y, g_v2.y, g_n.y, g_v1.z, g_v2.z, g_n.z};
   float gw = G[1] * (-2 * zq) + G[2] * (2 * y) + G[3] * (2 * zq) + G[5] * (-2 * x) +
              G[6] * (-2 * y) + G[7] * (2 * x);
@@ -631,13 +595,12 @@ __global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ mu,
     d_quat[4 * i + 2] += (gy - y * dot) * qn;
     d_quat[4 * i + 3] += (gz - zq * dot) * qn;
   }
-  if (d_scale) { d_scale[2 * i] += g_s1; d_scale[2 * i + 1] += g_s2; }
-  if (d_opac) d_opac[i] += g_o;
-  if (d_gamma) { d_gamma[2 * i] += g_g1; d_gamma[2 * i + 1] += g_g2; }
+  if (d_scale) { d_scale[2 * i] += g[12]; d_scale[2 * i + 1] += g[13]; }
+  if (d_opac) d_opac[i] += g[14];
+  if (d_gamma) { d_gamma[2 * i] += g[15]; d_gamma[2 * i + 1] += g[16]; }
   if (d_color) {
-    d_color[3 * i] += g[12]; d_color[3 * i + 1] += g[13]; d_color[3 * i + 2] += g[14];
+    d_color[3 * i] += g[17]; d_color[3 * i + 1] += g[18]; d_color[3 * i + 2] += g[19];
   }
-  (void)opac; (void)gam;
 }
 
 cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int N, const float* mu,
@@ -660,7 +623,7 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
   {
     NEXEL_PROF("preprocess_bwd", st);
     k_preprocess_bwd<<<(N + 255) / 256, 256, 0, st>>>(
-        c, N, mu, quat, scale, opacity, gamma, (uint32_t*)(ws + L.did0), (uint32_t*)(ws + L.dkey0),
+        c, N, quat, (uint32_t*)(ws + L.did0), (uint32_t*)(ws + L.dkey0),
         (float*)(ws + L.grad_sorted), d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color);
   }
   return cudaGetLastError();

@@ -124,8 +124,9 @@ __global__ void __launch_bounds__(kTilePix) k_collect_bwd(
     const float4* __restrict__ recs, const int* __restrict__ ids, const float* __restrict__ T_final,
     const int* __restrict__ n_contrib, const float* __restrict__ d_image,
     const float* __restrict__ dweff, const float* __restrict__ ddepth,
-    float* __restrict__ grad) {
+    const float4* __restrict__ aux, float* __restrict__ grad) {
   __shared__ float4 s_rec[kRecF4][kTilePix];
+  __shared__ float4 s_aux[kAuxF4][kTilePix];
   __shared__ uint32_t s_rank[kTilePix];
   __shared__ int s_max;
   const int tile = blockIdx.x;
@@ -134,6 +135,8 @@ __global__ void __launch_bounds__(kTilePix) k_collect_bwd(
   const int py = ty * kTile + (threadIdx.x / kTile);
   const bool inside = px < c.W && py < c.H;
   const float fpx = px + 0.5f, fpy = py + 0.5f;
+  // camera-space ray direction of this pixel (z component 1)
+  const float rdx = (fpx - c.cx) / c.fx, rdy = (fpy - c.cy) / c.fy;
   const uint2 rg = ranges[tile];
   const size_t p = inside ? (size_t)py * c.W + px : 0;
   float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
@@ -170,6 +173,9 @@ __global__ void __launch_bounds__(kTilePix) k_collect_bwd(
       const float4* src = recs + (size_t)r * kRecF4;
 #pragma unroll
       for (int k = 0; k < kRecF4; ++k) s_rec[k][threadIdx.x] = __ldg(src + k);
+      const float4* asrc = aux + (size_t)r * kAuxF4;
+#pragma unroll
+      for (int k = 0; k < kAuxF4; ++k) s_aux[k][threadIdx.x] = __ldg(asrc + k);
     }
     __syncthreads();
     for (int j = (int)(bend - bstart) - 1; j >= 0; --j) {
@@ -178,9 +184,11 @@ __global__ void __launch_bounds__(kTilePix) k_collect_bwd(
       Hit h;
       bool ok = pos < last && eval_surfel(q0, q1, q2, q3, fpx, fpy, c.near_, alpha_min, h);
       if (!__any_sync(0xffffffffu, ok)) continue;
-      float g[15];
+      // per-surfel gradient record: mu_c (0-2), v1_c (3-5), v2_c (6-8),
+      // n_c (9-11), sigma (12-13), opacity (14), gamma (15-16), colour (17-19)
+      float g[kGradStride];
 #pragma unroll
-      for (int k = 0; k < 15; ++k) g[k] = 0.f;
+      for (int k = 0; k < kGradStride; ++k) g[k] = 0.f;
       if (ok) {
         const float4 q4 = s_rec[4][j];
         const float a = fminf(h.alpha, alpha_max);
@@ -202,41 +210,50 @@ __global__ void __launch_bounds__(kTilePix) k_collect_bwd(
         } else {
           e = q4.x * dC0 + q4.y * dC1 + q4.z * dC2;
           const float w = a * T;
-          g[12] = w * dC0; g[13] = w * dC1; g[14] = w * dC2;
+          g[17] = w * dC0; g[18] = w * dC1; g[19] = w * dC2;
         }
         const float da = T * (e - R);
         R = a * e + (1.f - a) * R;
         float du = 0.f, dv = 0.f;
         if (!clamped) {
           const float al = h.alpha;
-          g[3] = da * al / q1.y;
+          g[14] = da * al / q1.y;
           const float cpa = -da * al;  // dL/d(pu) * 2 = -dalpha * alpha
           if (h.u != 0.f) {
             du = cpa * q1.z * h.pu / h.u;
-            g[4] = cpa * h.pu * logf(fabsf(h.u));
+            g[15] = cpa * h.pu * logf(fabsf(h.u));
           }
           if (h.v != 0.f) {
             dv = cpa * q1.w * h.pv / h.v;
-            g[5] = cpa * h.pv * logf(fabsf(h.v));
+            g[16] = cpa * h.pv * logf(fabsf(h.v));
           }
         }
-        dt += du * h.ut + dv * h.vt;
-        const float dut = du * h.t, dvt = dv * h.t;
-        g[8] = dut * h.dx; g[9] = dut * h.dy;
-        g[10] = dvt * h.dx; g[11] = dvt * h.dy;
-        float ddx = dut * q2.z + dvt * q3.x, ddy = dut * q2.w + dvt * q3.y;
-        g[2] = dt / h.den;
-        const float dden = -dt * h.t / h.den;
-        g[6] = dden * h.dx; g[7] = dden * h.dy;
-        ddx += dden * q2.x; ddy += dden * q2.y;
-        g[0] = -ddx; g[1] = -ddy;
+        // camera-space chain (the hit x = t d lies on the plane, so
+        // x - mu = u s1 v1 + v s2 v2 exactly): u = (x - mu) . v1 / s1 with
+        // t = (mu . n) / (d . n)
+        const float4 a0 = s_aux[0][j], a1 = s_aux[1][j], a2 = s_aux[2][j], a3 = s_aux[3][j];
+        const float s1 = a0.w, s2 = a1.w;
+        const float us = h.u * s1, vs = h.v * s2;
+        const float rx = us * a1.x + vs * a2.x, ry = us * a1.y + vs * a2.y,
+                    rz = us * a1.z + vs * a2.z;
+        const float du1 = du / s1, dv2 = dv / s2;
+        const float grx = du1 * a1.x + dv2 * a2.x, gry = du1 * a1.y + dv2 * a2.y,
+                    grz = du1 * a1.z + dv2 * a2.z;
+        const float gtt = dt + grx * rdx + gry * rdy + grz;
+        const float gd = gtt / h.den;
+        g[0] = -grx + gd * a3.x; g[1] = -gry + gd * a3.y; g[2] = -grz + gd * a3.z;
+        g[3] = du1 * rx; g[4] = du1 * ry; g[5] = du1 * rz;
+        g[6] = dv2 * rx; g[7] = dv2 * ry; g[8] = dv2 * rz;
+        g[9] = -gd * rx; g[10] = -gd * ry; g[11] = -gd * rz;
+        g[12] = -du1 * h.u;
+        g[13] = -dv2 * h.v;
       }
 #pragma unroll
-      for (int k = 0; k < 15; ++k) g[k] = warp_sum(g[k]);
+      for (int k = 0; k < kGradStride; ++k) g[k] = warp_sum(g[k]);
       if (lane == 0) {
         float* dst = grad + (size_t)s_rank[j] * kGradStride;
 #pragma unroll
-        for (int k = 0; k < 15; ++k)
+        for (int k = 0; k < kGradStride; ++k)
           if (g[k] != 0.f) atomicAdd(dst + k, g[k]);
       }
     }
@@ -296,6 +313,7 @@ static cudaError_t collect_bwd_t(const DevCam& c, const nexel_settings& s, char*
   auto* nc = (const int*)(ws + L.n_contrib);
   auto* dwe = (const float*)(bws + B.dweff);
   auto* ddp = (const float*)(bws + B.ddepth);
+  auto* aux = (const float4*)(ws + L.aux_sorted);
   float* grad = (float*)(ws + L.grad_sorted);
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * kGradStride * (size_t)L.N, st);
   if (e != cudaSuccess) return e;
@@ -303,7 +321,7 @@ static cudaError_t collect_bwd_t(const DevCam& c, const nexel_settings& s, char*
 #define NEXEL_CB(KK)                                                                               \
   k_collect_bwd<KK, KeyT><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.bg[0], s.bg[1],  \
                                                   s.bg[2], rmask, rg, keys, recs, ids, T_final,  \
-                                                  nc, d_image, dwe, ddp, grad)
+                                                  nc, d_image, dwe, ddp, aux, grad)
   switch (s.K) {
     case 0: NEXEL_CB(0); break;
     case 1: NEXEL_CB(1); break;

@@ -16,7 +16,8 @@ namespace nexel {
 constexpr int kTile = NEXEL_TILE;            // 16 x 16 pixel tiles
 constexpr int kTilePix = kTile * kTile;      // one thread per pixel
 constexpr int kRecF4 = 5;                    // packed surfel record: 5 float4
-constexpr int kGradStride = 16;              // per-surfel gradient record (floats)
+constexpr int kAuxF4 = 4;                    // camera-space frame for the backward
+constexpr int kGradStride = 20;              // per-surfel gradient record (floats)
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort block
@@ -37,14 +38,24 @@ struct DevCam {
 //  q0 = (cpx_hi, cpy_hi, cpx_lo, cpy_lo)  projected centre, pixels, as a
 //        float-float pair (hi + lo)
 //  q1 = (z, o, gamma1, gamma2)             centre view depth, opacity, gamma
-//  q2 = (nx, ny, Ax, Ay)                   plane tilt and u-gradient per pixel
-//  q3 = (Bx, By, 0, 0)                     v-gradient per pixel
+//  q2 = (nx, ny, Cux, Cuy)                 normal and u-numerator per pixel
+//  q3 = (Cvx, Cvy, dn0, 0)                 v-numerator, d_mu . n
 //  q4 = (c0, c1, c2, id)                   colour and original index (bits)
-// For a pixel centre p: dp = p - cp, den = 1 + dp . n, t* = z / den,
-// u = t* (dp . A), v = t* (dp . B).
+// With d_mu = mu_c / z the ray through the centre and delta = d - d_mu the
+// offset of a pixel's ray (z component 0), the hit of the ray o + t d with
+// the surfel plane is t* = (mu_c . n) / (d . n) = z dn0 / (d . n) and, by
+// a (d_mu . n) - n (d_mu . a) = d_mu x (a x n),
+//   u = delta . Cu / (d . n),  Cu = -z (d_mu x v2) / sigma1,
+//   v = delta . Cv / (d . n),  Cv =  z (d_mu x v1) / sigma2,
+// with d . n = dn0 + delta . n.  No per-surfel constant divides by
+// d_mu . n, so nearly edge-on surfels keep FP32 accuracy.  The x and y
+// components are stored divided by fx and fy, so delta is in pixels.
+//
+// Auxiliary camera-space record for the backward (rank order):
+//  a0 = (mu_c, sigma1), a1 = (v1_c, sigma2), a2 = (v2_c, 0), a3 = (n_c, 0).
 
 struct Hit {
-  float dx, dy, den, t, ut, vt, u, v, pu, pv, alpha;  // alpha before clamping
+  float dx, dy, den, t, u, v, pu, pv, alpha;  // alpha before clamping
 };
 
 // |a|^(2 g); exact square for g == 1.
@@ -61,13 +72,12 @@ __device__ __forceinline__ bool eval_surfel(const float4& q0, const float4& q1, 
                                             float alpha_min, Hit& h) {
   h.dx = (fpx - q0.x) - q0.z;
   h.dy = (fpy - q0.y) - q0.w;
-  h.den = fmaf(h.dx, q2.x, fmaf(h.dy, q2.y, 1.0f));
-  h.t = q1.x / h.den;
+  h.den = fmaf(h.dx, q2.x, fmaf(h.dy, q2.y, q3.z));
+  const float inv = 1.0f / h.den;
+  h.t = q1.x * q3.z * inv;  // z dn0 / den: exactly z on the centre ray
   if (!(h.t > near_)) return false;
-  h.ut = fmaf(h.dx, q2.z, h.dy * q2.w);
-  h.vt = fmaf(h.dx, q3.x, h.dy * q3.y);
-  h.u = h.t * h.ut;
-  h.v = h.t * h.vt;
+  h.u = fmaf(h.dx, q2.z, h.dy * q2.w) * inv;
+  h.v = fmaf(h.dx, q3.x, h.dy * q3.y) * inv;
   h.pu = pow2g(h.u, q1.z);
   h.pv = pow2g(h.v, q1.w);
   h.alpha = q1.y * expf(-0.5f * (h.pu + h.pv));
@@ -103,40 +113,14 @@ __device__ __forceinline__ float downweight(float focal, float s, float t) {
   return -expm1f(-r * r * 0.15915494309189535f);
 }
 
-// Warp-aggregated float2 atomic add: lanes that target the same table entry
-// are grouped with __match_any_sync, the lowest lane of each group sums the
-// group's values (in lane order, from a per-warp shared-memory slot array)
-// and issues one vector atomic.  Every lane of the warp must call it; lanes
-// with active == false contribute nothing.  s_warp: 32 float2 of this warp.
-__device__ __forceinline__ void warp_atomic_add2(float* base, uint32_t idx, float2 v, bool active,
-                                                 float2* s_warp) {
-  const int lane = threadIdx.x & 31;
-  const unsigned long long key =
-      active ? reinterpret_cast<unsigned long long>(base + 2 * (size_t)idx) : 0ull;
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  s_warp[lane] = v;
-  __syncwarp();
-  if (active && (peers & ((1u << lane) - 1u)) == 0u) {
-    float2 acc = make_float2(0.f, 0.f);
-    unsigned m = peers;
-    while (m) {
-      const int b = __ffs(m) - 1;
-      m &= m - 1u;
-      acc.x += s_warp[b].x;
-      acc.y += s_warp[b].y;
-    }
-    atomicAdd(reinterpret_cast<float2*>(base) + idx, acc);
-  }
-  __syncwarp();
-}
-
 // ------------------------------------------------------------ workspace
 // Main workspace (binning results and per-pixel replay data).  Regions that
 // depend only on (camera, K, N) come first; the instance buffers and the
 // sort scratch, whose size follows the instance capacity, come last, so
 // every call re-derives the same layout from (camera, K, N, ws_bytes).
 struct WsLayout {
-  size_t geom_orig, geom_sorted, dkey0, dkey1, did0, did1, rect, count, offs, ranges, n_contrib,
+  size_t geom_orig, geom_sorted, aux_orig, aux_sorted, dkey0, dkey1, did0, did1, rect, count, offs,
+      ranges, n_contrib,
       grad_sorted, counters, fixed_end, inst0, inst1, hist, scan_sums, total;
   int N, P, K, n_tiles, tile_bits, rank_bits, key64, tile_passes;
   long long cap;
@@ -144,7 +128,8 @@ struct WsLayout {
 // Backward scratch (per sample): dL/dW_j, dL/dD_j, the field features and
 // the texture gradient.
 struct BwdLayout {
-  size_t dweff, ddepth, feat, gtex, rc_notex, rc_weights, rc_ids, rc_depths, rc_T, total;
+  size_t dweff, ddepth, feat, gtex, gin, dtl, rc_notex, rc_weights, rc_ids, rc_depths, rc_T,
+      total;
 };
 
 WsLayout ws_layout(const nexel_camera& cam, int K, int N, long long cap);

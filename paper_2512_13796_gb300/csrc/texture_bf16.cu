@@ -3,6 +3,8 @@
 // FP32 accumulation everywhere; the table is read as FP16 or FP32.
 #include "texture_bf16.cuh"
 
+#include <type_traits>
+
 namespace nexel {
 
 constexpr int kWarps = 4;  // warps per CTA, one 16-row tile each
@@ -142,11 +144,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_bwd_bf16(
     const int* __restrict__ ids, const float* __restrict__ depths,
     const float* __restrict__ d_image, const float* __restrict__ d_weights,
     const float* __restrict__ d_textures, float* __restrict__ dweff, float* __restrict__ ddepth,
-    uint32_t* __restrict__ feat_out, float4* __restrict__ gtex_out, float* __restrict__ d_table) {
+    uint32_t* __restrict__ feat_out, float4* __restrict__ gtex_out, float* __restrict__ gin_out) {
   using Bw = Bf16W<IN, H1, H2>;
   constexpr int HL = Bw::HL;
   extern __shared__ __align__(16) __nv_bfloat16 sw[];
-  __shared__ float2 s_red[kWarps][32];
   load_weights_bf16<IN, H1, H2>(f.w, sw, true);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -208,28 +209,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_bwd_bf16(
       layer<H1, IN>(dl, sw + Bw::p1, Bw::t1, g, t, gin);
     }
     // table scatter and depth gradient: n-tile nt, columns 8 nt + 2t -> level 4 nt + t
-    float dtA = 0.f, dtB = 0.f;
+    // feature gradient by row (FP32): n-tile nt holds columns 8 nt + 2t, +1;
+    // the hash-grid backward (k_hash_bwd) scatters it and writes ddepth of
+    // textured samples
+    // level-major: level 4 nt + t of row r at gin_out[l * R + r]
+    {
+      float2* g2 = reinterpret_cast<float2*>(gin_out);
+      const long long R = gin_stride(n_tiles * 16);
 #pragma unroll
-    for (int nt = 0; nt < IN / 8; ++nt) {
-      const int l = 4 * nt + t;
-      const float ra = level_backward<TT>(f, l, A.x, A.D, A.d, gin[nt][0], gin[nt][1], d_table,
-                                          A.valid, s_red[warp]);
-      const float rb = level_backward<TT>(f, l, B.x, B.D, B.d, gin[nt][2], gin[nt][3], d_table,
-                                          B.valid, s_red[warp]);
-      if (A.valid) dtA += ra;
-      if (B.valid) dtB += rb;
+      for (int nt = 0; nt < IN / 8; ++nt) {
+        const long long l = 4 * nt + t;
+        g2[l * R + rA] = make_float2(gin[nt][0], gin[nt][1]);
+        g2[l * R + rB] = make_float2(gin[nt][2], gin[nt][3]);
+      }
     }
-    dtA += __shfl_xor_sync(0xffffffffu, dtA, 1);
-    dtA += __shfl_xor_sync(0xffffffffu, dtA, 2);
-    dtB += __shfl_xor_sync(0xffffffffu, dtB, 1);
-    dtB += __shfl_xor_sync(0xffffffffu, dtB, 2);
     if (t == 0) {
       if (A.in_pix) {
-        ddepth[A.s] = A.valid ? dtA : 0.f;
+        if (!A.valid) ddepth[A.s] = 0.f;
         dweff[A.s] = A.valid ? pwA + (d_weights ? d_weights[A.s] : 0.f) : 0.f;
       }
       if (B.in_pix) {
-        ddepth[B.s] = B.valid ? dtB : 0.f;
+        if (!B.valid) ddepth[B.s] = 0.f;
         dweff[B.s] = B.valid ? pwB + (d_weights ? d_weights[B.s] : 0.f) : 0.f;
       }
       gtex_out[rA] = make_float4(gA[0], gA[1], gA[2], 0.f);
@@ -509,9 +509,13 @@ static cudaError_t bwd_bf16(const DevCam& c, const nexel_settings& s, const Fiel
   kern<<<grid, kWarps * 32, smem, st>>>(c, fd, s.K, KP, n_tiles, weights, ids, depths, d_image,
                                         d_weights, d_textures, (float*)(bws + B.dweff),
                                         (float*)(bws + B.ddepth), (uint32_t*)(bws + B.feat),
-                                        (float4*)(bws + B.gtex), d_table);
+                                        (float4*)(bws + B.gtex), (float*)(bws + B.gin));
   }
   e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_hash_bwd(c, fd, s.K, KP, n_tiles * 16, std::is_same<TT, __half>::value, ids, depths,
+                      (const float2*)(bws + B.gin), (float*)(bws + B.dtl),
+                      (float*)(bws + B.ddepth), d_table, st);
   if (e != cudaSuccess || !d_mlp) return e;
   const size_t smem2 = sizeof(__nv_bfloat16) * WgSmem<IN, H1, H2>::total;
   auto kw = k_mlp_wgrad_bf16<IN, H1, H2>;

