@@ -194,6 +194,30 @@ long long nexel_launch_count(void);
 int nexel_profile_enable(int on);
 int nexel_profile_read(int max_entries, char* names, float* total_ms, int* launches, int* n_out);
 
+/* Allocation-free forward render (the paper has no counterpart: this is a
+ * deployment variant).  For callers that cannot allocate device memory --
+ * e.g. a plugin inside a host application that owns all device
+ * allocations, or a frame callback on a fixed memory budget where an
+ * allocation could synchronise the device -- this runs nexel_preprocess and
+ * nexel_render_fwd with a workspace that is a file-scope device array of the
+ * library (12 MiB on each device that uses it, held until the process
+ * exits) instead of caller memory; it allocates nothing.  Inputs and outputs
+ * are as for nexel_preprocess / nexel_render_fwd.  Limits: N <= 16384
+ * surfels and width * height <= 65536 pixels (else NEXEL_ERR_INVALID_ARG,
+ * nothing launched); more (tile, surfel) instances than the array holds
+ * returns NEXEL_ERR_CAPACITY with the count in *n_instances_out.  The first
+ * call on a device resolves the array's device address (once per device,
+ * with that device current), so make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race,
+ * so serialise them; it keeps the previous call's contents, and the
+ * pipeline clears what must start at zero itself. */
+int nexel_render_fwd_static(const nexel_camera* cam, const nexel_settings* settings,
+                            const nexel_field* field, int N, const float* mu, const float* quat,
+                            const float* scale, const float* opacity, const float* gamma,
+                            const float* color, float* image, float* notex, float* weights,
+                            int* ids, float* depths, float* textures, float* T_final,
+                            long long* n_instances_out, nexel_stream_t stream);
+
 /* Human-readable name of a status code (static string). */
 const char* nexel_status_string(int status);
 

@@ -30,7 +30,8 @@ MAX_LEVELS, MAX_LAYERS = 32, 4
 
 EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess",
            "nexel_render_fwd", "nexel_render_bwd", "nexel_instance_list", "nexel_status_string",
-           "nexel_version", "nexel_launch_count", "nexel_profile_enable", "nexel_profile_read"]
+           "nexel_version", "nexel_launch_count", "nexel_profile_enable", "nexel_profile_read",
+           "nexel_render_fwd_static"]
 
 
 def _nvcc() -> str:
@@ -126,6 +127,8 @@ def lib(auto_build: bool = False):
     L.nexel_render_bwd.argtypes = ([vp, vp, vp, i] + [vp] * 5 + [vp, sz, vp, sz] + [vp] * 4 +
                                    [vp] * 3 + [i] + [vp] * 8 + [vp])
     L.nexel_instance_list.argtypes = [vp, i, vp, sz, ll, vp, vp, vp, vp]
+    L.nexel_render_fwd_static.argtypes = [vp, vp, vp, i] + [vp] * 6 + [vp] * 7 + [
+        C.POINTER(ll), vp]
     L.nexel_launch_count.restype = C.c_longlong
     L.nexel_launch_count.argtypes = []
     L.nexel_profile_enable.argtypes = [i]
@@ -201,6 +204,17 @@ def nexel_instance_list(cam, N, ws, ws_bytes, n_instances, tile_out, id_out, dep
                         stream) -> int:
     return check("nexel_instance_list", lib().nexel_instance_list(
         C.byref(cam), N, ws, ws_bytes, n_instances, tile_out, id_out, depth_out, stream))
+
+
+def nexel_render_fwd_static(cam, st, field, N, mu, quat, scale, opacity, gamma, color, image,
+                            notex, weights, ids, depths, textures, T_final, stream) -> tuple:
+    """Allocation-free forward render; returns (status, n_instances)."""
+    n = C.c_longlong(0)
+    rc = lib().nexel_render_fwd_static(
+        C.byref(cam), C.byref(st), C.byref(field) if field is not None else None, N, mu, quat,
+        scale, opacity, gamma, color, image, notex, weights, ids, depths, textures, T_final,
+        C.byref(n), stream)
+    return rc, n.value
 
 
 def nexel_launch_count() -> int:
