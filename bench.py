@@ -112,6 +112,8 @@ class Job:
         self.cam, self.st = w.cameras[0], w.settings
         self.cam_s = R.camera_struct(self.cam)
         self.st_s = R.settings_struct(self.st, grid, mlp)
+        # a training step: the forward leaves the field features for the backward
+        self.st_train = R.settings_struct(self.st, grid, mlp, cache_features=True)
         self.p = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).to(dev)
                   for k in ("mu", "quat", "scale", "opacity", "gamma", "color")}
         self.field = R.DeviceField.from_synth(w.field, dev, grid, mlp)
@@ -125,17 +127,18 @@ class Job:
         self.grads = None
         self.fwd_out = None
 
-    def forward(self):
+    def forward(self, st_s=None):
         p = self.p
-        self.fwd_out = self.R.forward(self.ws, self.cam_s, self.st_s, self.field, self.ts, self.wts,
-                                      p["mu"], p["quat"], p["scale"], p["opacity"], p["gamma"],
-                                      p["color"])
+        self.fwd_out = self.R.forward(self.ws, self.cam_s, st_s or self.st_s, self.field, self.ts,
+                                      self.wts, p["mu"], p["quat"], p["scale"], p["opacity"],
+                                      p["gamma"], p["color"])
         return self.fwd_out
 
     def step(self):
-        out = self.forward()
+        out = self.forward(self.st_train)
         p = self.p
-        self.grads = self.R.backward(self.ws, self.cam_s, self.st_s, self.field, self.ts, self.wts,
+        self.grads = self.R.backward(self.ws, self.cam_s, self.st_train, self.field, self.ts,
+                                     self.wts,
                                      p["mu"], p["quat"], p["scale"], p["opacity"], p["gamma"], out,
                                      self.d_image, grads=self.grads)
         return out

@@ -91,6 +91,12 @@ typedef struct {
    * backward), so the caller need not keep them between the two calls and
    * passes NULL for them. */
   int recompute_buffers;
+  /* 0: nexel_render_bwd gathers the hash-grid features of every textured
+   * sample again; 1 (a training step): nexel_render_fwd leaves them in the
+   * bwd_ws it is given, and the nexel_render_bwd that follows reads them
+   * there instead.  Both calls must then get the same bwd_ws, with no other
+   * call on it in between. */
+  int cache_features;
 } nexel_settings;
 
 /* Neural field of Sec. 3 ("Instant-NGP") and Eq. 4: L hash tables of T
@@ -146,11 +152,14 @@ int nexel_preprocess(const nexel_camera* cam, const nexel_settings* settings, in
  *   depths   [H][W][K]  D, ray parameter t* of the intersection, 0 if empty
  *   textures [H][W][K][3] T_j = G(Delta * H(o + D_j d)), 0 if empty (Eq. 4)
  *   T_final  [H][W]     transmittance after the last composited surfel
- * Ties in weight keep the front-most surfel. */
+ * Ties in weight keep the front-most surfel.  bwd_ws / bwd_ws_bytes: the
+ * backward scratch (nexel_bwd_workspace_size) when settings->cache_features
+ * is set and K > 0 (else NEXEL_ERR_INVALID_ARG); otherwise unused and may be
+ * NULL / 0. */
 int nexel_render_fwd(const nexel_camera* cam, const nexel_settings* settings,
-                     const nexel_field* field, int N, void* ws, size_t ws_bytes, float* image,
-                     float* notex, float* weights, int* ids, float* depths, float* textures,
-                     float* T_final, nexel_stream_t stream);
+                     const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
+                     size_t bwd_ws_bytes, float* image, float* notex, float* weights, int* ids,
+                     float* depths, float* textures, float* T_final, nexel_stream_t stream);
 
 /* Backward of nexel_render_fwd (same ws, same saved outputs).  Upstream
  * gradients: d_image [H][W][3] (required); d_weights [H][W][K] and

@@ -96,7 +96,8 @@ class Camera(C.Structure):
 class Settings(C.Structure):
     _fields_ = [("K", C.c_int), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("T_min", C.c_float), ("bg", C.c_float * 3), ("grid_dtype", C.c_int),
-                ("mlp_dtype", C.c_int), ("recompute_buffers", C.c_int)]
+                ("mlp_dtype", C.c_int), ("recompute_buffers", C.c_int),
+                ("cache_features", C.c_int)]
 
 
 class Field(C.Structure):
@@ -123,7 +124,7 @@ def lib(auto_build: bool = False):
     L.nexel_workspace_size.argtypes = [vp, i, ll, C.POINTER(sz)]
     L.nexel_bwd_workspace_size.argtypes = [vp, vp, vp, C.POINTER(sz)]
     L.nexel_preprocess.argtypes = [vp, vp, i] + [vp] * 7 + [sz, C.POINTER(ll), vp]
-    L.nexel_render_fwd.argtypes = [vp, vp, vp, i, vp, sz] + [vp] * 7 + [vp]
+    L.nexel_render_fwd.argtypes = [vp, vp, vp, i, vp, sz, vp, sz] + [vp] * 7 + [vp]
     L.nexel_render_bwd.argtypes = ([vp, vp, vp, i] + [vp] * 5 + [vp, sz, vp, sz] + [vp] * 4 +
                                    [vp] * 3 + [i] + [vp] * 8 + [vp])
     L.nexel_instance_list.argtypes = [vp, i, vp, sz, ll, vp, vp, vp, vp]
@@ -182,11 +183,11 @@ def nexel_preprocess(cam, st, N, mu, quat, scale, opacity, gamma, color, ws, ws_
     return rc, n.value
 
 
-def nexel_render_fwd(cam, st, field, N, ws, ws_bytes, image, notex, weights, ids, depths,
-                     textures, T_final, stream) -> int:
+def nexel_render_fwd(cam, st, field, N, ws, ws_bytes, bws, bws_bytes, image, notex, weights,
+                     ids, depths, textures, T_final, stream) -> int:
     return check("nexel_render_fwd", lib().nexel_render_fwd(
         C.byref(cam), C.byref(st), C.byref(field) if field is not None else None, N, ws, ws_bytes,
-        image, notex, weights, ids, depths, textures, T_final, stream))
+        bws, bws_bytes, image, notex, weights, ids, depths, textures, T_final, stream))
 
 
 def nexel_render_bwd(cam, st, field, N, mu, quat, scale, opacity, gamma, ws, ws_bytes, bws,

@@ -268,15 +268,22 @@ int nexel_preprocess(const nexel_camera* cam, const nexel_settings* settings, in
 }
 
 int nexel_render_fwd(const nexel_camera* cam, const nexel_settings* settings,
-                     const nexel_field* field, int N, void* ws, size_t ws_bytes, float* image,
-                     float* notex, float* weights, int* ids, float* depths, float* textures,
-                     float* T_final, nexel_stream_t stream) {
+                     const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
+                     size_t bwd_ws_bytes, float* image, float* notex, float* weights, int* ids,
+                     float* depths, float* textures, float* T_final, nexel_stream_t stream) {
   if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !image || !notex || !T_final)
     return NEXEL_ERR_INVALID_ARG;
   const int K = settings->K;
   if (K > 0 && (!weights || !ids || !depths || !textures)) return NEXEL_ERR_INVALID_ARG;
   if (K > 0 && !field_ok(field)) return NEXEL_ERR_INVALID_ARG;
   if (K > 0 && !texture_arch_supported(*settings, *field)) return NEXEL_ERR_UNSUPPORTED;
+  const bool cache = K > 0 && settings->cache_features != 0;
+  void* feat_cache = nullptr;
+  if (cache) {
+    BwdLayout B = bwd_layout(*cam, K, field->L * field->F, settings->recompute_buffers != 0);
+    if (!bwd_ws || bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
+    feat_cache = (char*)bwd_ws + B.feat;
+  }
   WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
   if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -294,7 +301,7 @@ int nexel_render_fwd(const nexel_camera* cam, const nexel_settings* settings,
     return cuda_status(cudaGetLastError());
   }
   e = launch_texture_fwd(c, *settings, *field, notex, weights, ids, depths, T_final, image,
-                         textures, st);
+                         textures, feat_cache, st);
   return cuda_status(e);
 }
 
@@ -347,7 +354,7 @@ int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
     }
     if (e == cudaSuccess)
       e = launch_texture_bwd(c, *settings, *field, bw, B, weights, ids, depths, d_image, d_weights,
-                             d_textures, d_table, d_mlp, st);
+                             d_textures, d_table, d_mlp, settings->cache_features != 0, st);
   }
   if (e == cudaSuccess) e = launch_collect_bwd(c, *settings, w, L, bw, B, ids, T_final, d_image, st);
   if (e == cudaSuccess)

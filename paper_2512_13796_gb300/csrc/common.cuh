@@ -174,15 +174,18 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
                                   const float* gamma, char* ws, const WsLayout& L, int accumulate,
                                   float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
                                   float* d_gamma, float* d_color, cudaStream_t st);
+// feat_cache (may be null): where a training forward leaves the per-sample
+// field features for the backward (the backward's feature buffer).
 cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                const float* notex, const float* weights, const int* ids,
                                const float* depths, const float* T_final, float* image,
-                               float* textures, cudaStream_t st);
+                               float* textures, void* feat_cache, cudaStream_t st);
+// feat_cached: the forward left the features in bws (no gather here).
 cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                char* bws, const BwdLayout& B, const float* weights, const int* ids,
                                const float* depths, const float* d_image, const float* d_weights,
                                const float* d_textures, float* d_table, float* d_mlp,
-                               cudaStream_t st);
+                               bool feat_cached, cudaStream_t st);
 bool texture_arch_supported(const nexel_settings& s, const nexel_field& f);
 
 }  // namespace nexel

@@ -74,6 +74,6 @@ extern "C" int nexel_render_fwd_static(const nexel_camera* cam, const nexel_sett
   rc = nexel_preprocess(cam, settings, N, mu, quat, scale, opacity, gamma, color, ws,
                         kStaticBytes, n_instances_out, stream);
   if (rc != NEXEL_OK) return rc;
-  return nexel_render_fwd(cam, settings, field, N, ws, kStaticBytes, image, notex, weights, ids,
-                          depths, textures, T_final, stream);
+  return nexel_render_fwd(cam, settings, field, N, ws, kStaticBytes, nullptr, 0, image, notex,
+                          weights, ids, depths, textures, T_final, stream);
 }

@@ -43,8 +43,10 @@ bool texture_arch_supported(const nexel_settings& s, const nexel_field& f) {
 cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                const float* notex, const float* weights, const int* ids,
                                const float* depths, const float* T_final, float* image,
-                               float* textures, cudaStream_t st) {
+                               float* textures, void* feat_cache, cudaStream_t st) {
   FieldDev fd = make_fielddev(c, f);
+  fd.feat = feat_cache;
+  fd.feat_mode = feat_cache ? 1 : 0;
   if (s.mlp_dtype == NEXEL_BF16)
     return launch_texture_fwd_bf16(c, s, f, fd, notex, weights, ids, depths, T_final, image,
                                    textures, st);
@@ -61,8 +63,10 @@ cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const n
                                char* bws, const BwdLayout& B, const float* weights, const int* ids,
                                const float* depths, const float* d_image, const float* d_weights,
                                const float* d_textures, float* d_table, float* d_mlp,
-                               cudaStream_t st) {
+                               bool feat_cached, cudaStream_t st) {
   FieldDev fd = make_fielddev(c, f);
+  fd.feat = bws + B.feat;
+  fd.feat_mode = feat_cached ? 2 : 0;
   if (s.mlp_dtype == NEXEL_BF16)
     return launch_texture_bwd_bf16(c, s, f, fd, bws, B, weights, ids, depths, d_image, d_weights,
                                    d_textures, d_table, d_mlp, st);

@@ -96,10 +96,21 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_fwd_bf16(
   const float bg[3] = {bg0, bg1, bg2};
   for (long long mt = (long long)blockIdx.x * kWarps + warp; mt < n_tiles;
        mt += (long long)gridDim.x * kWarps) {
-    const RowInfo A = row_info(c, P, K, KP, mt * 16 + g, ids, weights, depths);
-    const RowInfo B = row_info(c, P, K, KP, mt * 16 + g + 8, ids, weights, depths);
+    const long long rA = mt * 16 + g, rB = rA + 8;
+    const RowInfo A = row_info(c, P, K, KP, rA, ids, weights, depths);
+    const RowInfo B = row_info(c, P, K, KP, rB, ids, weights, depths);
     uint32_t a1[IN / 16][4];
     gather_frags<IN, TT>(f, A, B, t, a1);
+    if (f.feat_mode == 1) {  // training step: leave the features for the backward
+      uint32_t* fo = reinterpret_cast<uint32_t*>(f.feat);
+#pragma unroll
+      for (int kt = 0; kt < IN / 16; ++kt) {
+        fo[(rA * IN + 16 * kt + 2 * t) / 2] = a1[kt][0];
+        fo[(rB * IN + 16 * kt + 2 * t) / 2] = a1[kt][1];
+        fo[(rA * IN + 16 * kt + 8 + 2 * t) / 2] = a1[kt][2];
+        fo[(rB * IN + 16 * kt + 8 + 2 * t) / 2] = a1[kt][3];
+      }
+    }
     uint32_t a2[H1 / 16][4], a3[(H2 > 0 ? H2 : 16) / 16][4];
     float out[1][4];
     mlp_fwd_bf16<IN, H1, H2>(sw, g, t, a1, a2, a3, out);
@@ -158,7 +169,17 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_bwd_bf16(
     const RowInfo A = row_info(c, P, K, KP, rA, ids, weights, depths);
     const RowInfo B = row_info(c, P, K, KP, rB, ids, weights, depths);
     uint32_t a1[IN / 16][4];
-    gather_frags<IN, TT>(f, A, B, t, a1);
+    if (f.feat_mode == 2) {  // the forward of this step left the features
+#pragma unroll
+      for (int kt = 0; kt < IN / 16; ++kt) {
+        a1[kt][0] = feat_out[(rA * IN + 16 * kt + 2 * t) / 2];
+        a1[kt][1] = feat_out[(rB * IN + 16 * kt + 2 * t) / 2];
+        a1[kt][2] = feat_out[(rA * IN + 16 * kt + 8 + 2 * t) / 2];
+        a1[kt][3] = feat_out[(rB * IN + 16 * kt + 8 + 2 * t) / 2];
+      }
+    } else {
+      gather_frags<IN, TT>(f, A, B, t, a1);
+    }
     uint32_t a2[H1 / 16][4], a3[(H2 > 0 ? H2 : 16) / 16][4];
     float out[1][4];
     mlp_fwd_bf16<IN, H1, H2>(sw, g, t, a1, a2, a3, out);
@@ -235,13 +256,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_bwd_bf16(
       gtex_out[rA] = make_float4(gA[0], gA[1], gA[2], 0.f);
       gtex_out[rB] = make_float4(gB[0], gB[1], gB[2], 0.f);
     }
-    // features by row, BF16 pairs
+    // features by row, BF16 pairs (for the weight-gradient kernel)
+    if (f.feat_mode != 2) {
 #pragma unroll
-    for (int kt = 0; kt < IN / 16; ++kt) {
-      feat_out[(rA * IN + 16 * kt + 2 * t) / 2] = a1[kt][0];
-      feat_out[(rB * IN + 16 * kt + 2 * t) / 2] = a1[kt][1];
-      feat_out[(rA * IN + 16 * kt + 8 + 2 * t) / 2] = a1[kt][2];
-      feat_out[(rB * IN + 16 * kt + 8 + 2 * t) / 2] = a1[kt][3];
+      for (int kt = 0; kt < IN / 16; ++kt) {
+        feat_out[(rA * IN + 16 * kt + 2 * t) / 2] = a1[kt][0];
+        feat_out[(rB * IN + 16 * kt + 2 * t) / 2] = a1[kt][1];
+        feat_out[(rA * IN + 16 * kt + 8 + 2 * t) / 2] = a1[kt][2];
+        feat_out[(rB * IN + 16 * kt + 8 + 2 * t) / 2] = a1[kt][3];
+      }
     }
   }
 }

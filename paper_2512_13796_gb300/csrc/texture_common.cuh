@@ -16,10 +16,17 @@ struct FieldDev {
   float s[NEXEL_MAX_LEVELS];
   const void* table;
   const float* w;
+  // per-sample feature buffer of a training step: feat_mode 1 = the forward
+  // writes the features there, 2 = the backward reads them instead of
+  // gathering, 0 = unused
+  void* feat;
+  int feat_mode;
 };
 
 inline FieldDev make_fielddev(const DevCam& c, const nexel_field& f) {
   FieldDev d;
+  d.feat = nullptr;
+  d.feat_mode = 0;
   d.L = f.L;
   d.mask = (uint32_t)f.T - 1u;
   d.focal = c.fx;

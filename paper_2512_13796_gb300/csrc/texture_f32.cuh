@@ -49,9 +49,18 @@ __global__ void __launch_bounds__(256) k_tex_fwd_f32(DevCam c, FieldDev f, int K
       float3 x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
       float feat[IN];
       hash_features<IN, TT>(f, x, D, feat);
+      if (f.feat_mode == 1) {
+        float* fo = reinterpret_cast<float*>(f.feat) + (p * K + j) * IN;
+#pragma unroll
+        for (int k = 0; k < IN; ++k) fo[k] = feat[k];
+      }
       float out[3];
       mlp_fwd_f32<IN, H1, H2>(sW, feat, out, nullptr, nullptr);
       t0 = out[0]; t1 = out[1]; t2 = out[2];
+    } else if (f.feat_mode == 1) {
+      float* fo = reinterpret_cast<float*>(f.feat) + (p * K + j) * IN;
+#pragma unroll
+      for (int k = 0; k < IN; ++k) fo[k] = 0.f;
     }
     float* dst = textures + (p * K + j) * 3;
     dst[0] = t0; dst[1] = t1; dst[2] = t2;
@@ -101,7 +110,12 @@ __global__ void __launch_bounds__(256) k_tex_bwd_f32(
     d = pixel_dir(c, (int)(p % c.W), (int)(p / c.W));
     x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
     float feat[IN];
-    hash_features<IN, TT>(f, x, D, feat);
+    if (f.feat_mode == 2) {  // left by the forward of this step
+#pragma unroll
+      for (int k = 0; k < IN; ++k) feat[k] = feat_out[s * IN + k];
+    } else {
+      hash_features<IN, TT>(f, x, D, feat);
+    }
     float out[3], h1[H1], h2[H2 > 0 ? H2 : 1];
     mlp_fwd_f32<IN, H1, H2>(sW, feat, out, h1, h2);
     const float dc0 = d_image[3 * p], dc1 = d_image[3 * p + 1], dc2 = d_image[3 * p + 2];
@@ -113,12 +127,14 @@ __global__ void __launch_bounds__(256) k_tex_bwd_f32(
     if (d_weights) dwe += d_weights[s];
     dweff[s] = dwe;
     mlp_bwd_input_f32<IN, H1, H2>(sW, gT, h1, h2, gin);
-    for (int k = 0; k < IN; ++k) feat_out[s * IN + k] = feat[k];
+    if (f.feat_mode != 2)
+      for (int k = 0; k < IN; ++k) feat_out[s * IN + k] = feat[k];
     gtex_out[s] = make_float4(gT[0], gT[1], gT[2], 0.f);
   } else if (in_range) {
     dweff[s] = 0.f;
     ddepth[s] = 0.f;
-    for (int k = 0; k < IN; ++k) feat_out[s * IN + k] = 0.f;
+    if (f.feat_mode != 2)
+      for (int k = 0; k < IN; ++k) feat_out[s * IN + k] = 0.f;
     gtex_out[s] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   // the hash-grid backward (k_hash_bwd) reads gin and writes ddepth of

@@ -26,7 +26,7 @@ def camera_struct(cam) -> N_.Camera:
 
 
 def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32",
-                    recompute: bool = False) -> N_.Settings:
+                    recompute: bool = False, cache_features: bool = False) -> N_.Settings:
     s = N_.Settings()
     s.K = int(st.K)
     s.alpha_min, s.alpha_max, s.T_min = float(st.alpha_min), float(st.alpha_max), float(st.T_min)
@@ -35,6 +35,7 @@ def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32",
     s.grid_dtype = {"f32": N_.F32, "f16": N_.F16}[grid_dtype]
     s.mlp_dtype = {"f32": N_.F32, "bf16": N_.BF16}[mlp_dtype]
     s.recompute_buffers = 1 if recompute else 0
+    s.cache_features = 1 if cache_features else 0
     return s
 
 
@@ -138,7 +139,10 @@ def forward(ws: Workspace, cam_s, st_s, field: DeviceField | None, table_store, 
                textures=torch.empty(H, W, K, 3, device=dev), T_final=torch.empty(H, W, device=dev))
     fs = field.struct(table_store, weights) if (field is not None and K > 0) else None
     buf = ws.ws
+    # a training step leaves the field features in the backward scratch
+    bws = ws.bwd(cam_s, st_s, fs) if (st_s.cache_features and K > 0) else None
     N_.nexel_render_fwd(cam_s, st_s, fs, mu.shape[0], buf.data_ptr(), buf.numel(),
+                        _ptr(bws), bws.numel() if bws is not None else 0,
                         out["image"].data_ptr(), out["notex"].data_ptr(),
                         _ptr(out["weights"]) if K else None, _ptr(out["ids"]) if K else None,
                         _ptr(out["depths"]) if K else None, _ptr(out["textures"]) if K else None,
@@ -215,9 +219,14 @@ def render(params: dict, field: DeviceField | None, cam, settings, ws: Workspace
     Returns (image [H,W,3], weights [H,W,K], textures [H,W,K,3])."""
     dev = params["mu"].device
     ws = ws or Workspace(dev)
+    # when a backward will follow, the forward leaves the field features for it
+    train = torch.is_grad_enabled() and (
+        any(t.requires_grad for t in params.values()) or
+        (field is not None and (field.table.requires_grad or field.weights.requires_grad)))
     cfg = dict(ws=ws, cam=camera_struct(cam),
                settings=settings_struct(settings, field.grid_dtype if field else "f32",
-                                        field.mlp_dtype if field else "f32"),
+                                        field.mlp_dtype if field else "f32",
+                                        cache_features=train),
                field=field)
     tab = field.table if field is not None else None
     w = field.weights if field is not None else None

@@ -271,3 +271,28 @@ def test_recomputed_buffers_match_stored(dev, mlp):
     _, g2, _ = run_gpu(w.scene, cam, st, w.field, dev, grid=grid, mlp=mlp, d_image=dI, d_weights=dW,
                        recompute=True)
     compare_grads(g2, g1, 1e-4)
+
+
+@pytest.mark.parametrize("mlp", ["f32", "bf16"])
+@pytest.mark.parametrize("recompute", [False, True])
+def test_cached_features_match_gathered(dev, mlp, recompute):
+    """A training step whose forward leaves the field features for the
+    backward (cache_features) gives the same outputs and gradients as one
+    whose backward gathers them again: the cached features are the very
+    values the gather produces, so only the summation order of the float
+    atomics differs."""
+    w = synth.workload(1)
+    cam, st = w.cameras[0], w.settings
+    P, K = cam.width * cam.height, st.K
+    rng = np.random.default_rng(5)
+    dI = rng.normal(size=(P, 3))
+    dW = rng.normal(size=(P, K))
+    dT = rng.normal(size=(P, K, 3))
+    grid = "f16" if mlp == "bf16" else "f32"
+    f1, g1, _ = run_gpu(w.scene, cam, st, w.field, dev, grid=grid, mlp=mlp, d_image=dI,
+                        d_weights=dW, d_textures=dT, recompute=recompute)
+    f2, g2, _ = run_gpu(w.scene, cam, st, w.field, dev, grid=grid, mlp=mlp, d_image=dI,
+                        d_weights=dW, d_textures=dT, recompute=recompute, cache_features=True)
+    for k in ("image", "weights", "ids", "textures", "T_final"):
+        assert np.array_equal(f1[k], f2[k]), k
+    compare_grads(g2, g1, 1e-4)
