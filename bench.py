@@ -65,10 +65,18 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: wait (at most 5 s) for its
+        # first sample so that the samples cover the timed region
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self) -> dict | None:
         if self.proc is None:
@@ -160,7 +168,28 @@ def timed(fn, steps, flush, stream):
     return [a.elapsed_time(b) for a, b in times]
 
 
-def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, hbm_traffic=None):
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the ncu capture
+    recorded in profiles/dram_traffic.txt, or None when there is none or the
+    kernel's source file has changed since (its SHA-1 no longer matches)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) < 5 or line.startswith("#") or f[0] != kernel or f[1] != workload:
+            continue
+        src = os.path.join(ROOT, f[3])
+        if not os.path.exists(src):
+            return None
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() != f[4]:
+            return None
+        return int(f[2])
+    return None
+
+
+def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, workload: str):
     """Roofline entry of the dominant kernel from live per-kernel events."""
     name, (ms_tot, launches) = max(prof.items(), key=lambda kv: kv[1][0])
     ms = ms_tot / max(launches, 1)
@@ -181,6 +210,16 @@ def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, hb
                    peak_source=f"hbm_gbs ({peak_kind})", units_per_launch=samples,
                    bytes_per_unit=per)
         out["frac"] = A / out["peak"]
+    elif name.startswith("hash_bwd"):
+        # algorithmic bytes per textured sample, as for the gather: the table
+        # entries read for dL/dD (L levels x 8 corners x F in the storage
+        # type) plus the same entries of the FP32 table gradient added to
+        per = L * 8 * F * (b_entry + 4)
+        A = samples * per / (ms * 1e-3) / 1e9
+        out.update(bound="hbm", achieved=A, peak=peaks["hbm_gbs"], unit="GB/s",
+                   peak_source=f"hbm_gbs ({peak_kind})", units_per_launch=samples,
+                   bytes_per_unit=per)
+        out["frac"] = A / out["peak"]
     elif name.startswith("mlp_wgrad"):
         widths = w.field.widths
         macs = sum(widths[i] * widths[i + 1] for i in range(len(widths) - 1))
@@ -196,7 +235,7 @@ def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, hb
         # sort / scan / collection kernels: report bytes moved per launch
         # against the HBM peak (algorithmic bytes set by the caller)
         out.update(bound="hbm", achieved=None, peak=peaks["hbm_gbs"], unit="GB/s", frac=None)
-    out["traffic"] = hbm_traffic
+    out["traffic"] = measured_traffic(name, workload)
     return out
 
 
@@ -231,7 +270,7 @@ def cpu_baseline(w, seconds_target: float = 15.0) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="nexels", choices=["nexels", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -315,12 +354,12 @@ def main():
     t_train = timed(jobs["bf16"].step, args.steps, flush, stream)
     launches = (_native.nexel_launch_count() - launches0) // args.steps
     barrier()
-    clk = clocks.stop()
     results["bf16_train"] = t_train
     results["f32_train"] = timed(jobs["f32"].step, args.steps, flush, stream)
     results["bf16_fwd"] = timed(jobs["bf16"].forward, args.steps, flush, stream)
     results["f32_fwd"] = timed(jobs["f32"].forward, args.steps, flush, stream)
     barrier()
+    clk = clocks.stop()  # samples over all four timed regions
     # per-kernel CUDA events on the launch stream, same steps again
     _native.nexel_profile_enable(True)
     results["bf16_train_profiled"] = timed(jobs["bf16"].step, args.steps, flush, stream)
@@ -376,7 +415,7 @@ def main():
         with open(args.profile_json, "w") as f:
             json.dump({"bf16_train": prof, "f32_train": prof_f32, "steps": args.steps}, f, indent=1)
 
-    rl = roofline(prof, jobs["bf16"], peaks, peak_kind, args.steps)
+    rl = roofline(prof, jobs["bf16"], peaks, peak_kind, args.steps, f"config{args.config}")
     n_inst = jobs["bf16"].fwd_out["n_instances"]
     mpix = lambda m: world * P / (m * 1e-3) / 1e6
     line = {

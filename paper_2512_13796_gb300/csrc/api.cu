@@ -42,6 +42,7 @@ static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
   L.did0 = take(n * 4);
   L.did1 = take(n * 4);
   L.rect = take(n * 8);
+  L.conic = take(n * 32);
   L.count = take(n * 4);
   L.offs = take((n + 1) * 4);
   L.ranges = take((size_t)L.n_tiles * 8);
@@ -120,7 +121,6 @@ BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim, bool recomput
   B.gtex = take(std::max<size_t>(rows, 1) * 16);
   // level-major (row stride rounded up to 32 rows)
   B.gin = take((std::max<size_t>(rows, 1) + 32) * (size_t)std::max(feat_dim, 1) * 4);
-  B.dtl = take((std::max<size_t>(rows, 1) + 32) * (size_t)std::max(feat_dim / 2, 1) * 4);
   const size_t rc = recompute ? 1 : 0;
   B.rc_notex = take(rc * P * 12);
   B.rc_weights = take(rc * S * 4);

@@ -72,13 +72,59 @@ __device__ __forceinline__ float3 rotT(const float* R, float3 v) {
 // rectangle on the surfel plane, clipped to view depth >= near (hits at
 // t* <= near are dropped) and projected; its image is the convex hull of the
 // projected vertices.
+// Conservative tile test.  With the conic of the support written by
+// k_preprocess, Q(delta) = delta^T M delta + 2 b . delta - 1 <= 0 holds at
+// every pixel where alpha >= alpha_min.  The tile is kept unless Q > 0 on
+// the whole rectangle of its pixel centres grown by one pixel (and a small
+// tolerance), so dropping it removes only (pixel, surfel) pairs that the
+// collection pass would skip anyway.  The minimum of a quadratic over a
+// rectangle lies at a corner, at the critical point of an edge, or (when M
+// is positive definite) at the interior critical point.
+//
+// One out-of-line body with explicitly rounded operations: the counting and
+// the emitting kernels must take identical decisions.
+__device__ __noinline__ bool tile_may_hit(const float4 q0, const float4 q1, int tx, int ty, int W,
+                                          int H) {
+  const float m00 = q0.x, m01 = q0.y, m11 = q0.z, bx = q0.w, by = q1.x;
+  const float X0 = tx * kTile + 0.5f - 1.f - q1.y, X1 = min(tx * kTile + kTile - 1, W - 1) + 1.5f - q1.y;
+  const float Y0 = ty * kTile + 0.5f - 1.f - q1.z, Y1 = min(ty * kTile + kTile - 1, H - 1) + 1.5f - q1.z;
+  auto Q = [&](float x, float y) {
+    return __fsub_rn(fmaf(x, fmaf(m00, x, 2.f * fmaf(m01, y, bx)), __fmul_rn(y, fmaf(m11, y, 2.f * by))),
+                     1.f);
+  };
+  float q = fminf(fminf(Q(X0, Y0), Q(X1, Y0)), fminf(Q(X0, Y1), Q(X1, Y1)));
+  if (m00 > 0.f) {
+    const float ya[2] = {Y0, Y1};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float x = fminf(fmaxf(__fdiv_rn(-fmaf(m01, ya[e], bx), m00), X0), X1);
+      q = fminf(q, Q(x, ya[e]));
+    }
+  }
+  if (m11 > 0.f) {
+    const float xa[2] = {X0, X1};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float y = fminf(fmaxf(__fdiv_rn(-fmaf(m01, xa[e], by), m11), Y0), Y1);
+      q = fminf(q, Q(xa[e], y));
+    }
+  }
+  const float det = __fsub_rn(__fmul_rn(m00, m11), __fmul_rn(m01, m01));
+  if (m00 > 0.f && det > 0.f) {
+    const float xs = __fdiv_rn(__fsub_rn(__fmul_rn(m01, by), __fmul_rn(m11, bx)), det);
+    const float ys = __fdiv_rn(__fsub_rn(__fmul_rn(m01, bx), __fmul_rn(m00, by)), det);
+    if (xs >= X0 && xs <= X1 && ys >= Y0 && ys <= Y1) q = fminf(q, Q(xs, ys));
+  }
+  return !(q > 1e-3f);  // NaN keeps the tile
+}
+
 __global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __restrict__ mu,
                              const float* __restrict__ quat, const float* __restrict__ scale,
                              const float* __restrict__ opac, const float* __restrict__ gam,
                              const float* __restrict__ color, float4* __restrict__ geom,
                              float4* __restrict__ aux, uint32_t* __restrict__ dkey,
                              uint32_t* __restrict__ did, uint2* __restrict__ rect,
-                             uint32_t* __restrict__ count) {
+                             float4* __restrict__ conic, uint32_t* __restrict__ count) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   did[i] = (uint32_t)i;
@@ -178,6 +224,27 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __re
   const float mx = mc[0].hi, my = mc[1].hi;
   const float Cux = -(my * v2c.z - z * v2c.y) / s1, Cuy = -(z * v2c.x - mx * v2c.z) / s1;
   const float Cvx = (my * v1c.z - z * v1c.y) / s2, Cvy = (z * v1c.x - mx * v1c.z) / s2;
+  {
+    // support conic for the tile test (tile_may_hit): with delta the pixel
+    // offset from the projected centre and den = dn0 + delta . n', the
+    // support |u|^(2 g1) + |v|^(2 g2) <= 2 ln(o / alpha_min) lies inside
+    // (u / ru)^2 + (v / rv)^2 <= kappa (kappa = 1 when g1 = g2 = 1, else 2),
+    // i.e. Q(delta) = (delta . A)^2 + (delta . B)^2 - kappa den^2 <= 0 with
+    // A = Cu' / ru, B = Cv' / rv; stored divided by kappa dn0^2, so that
+    // Q = delta^T M delta + 2 b . delta - 1.
+    const float lr = 2.f * logf(o / alpha_min);
+    const float ru = powf(lr, 0.5f / g1) * 1.001f + 1e-6f, rv = powf(lr, 0.5f / g2) * 1.001f + 1e-6f;
+    const float kap = (g1 == 1.f && g2 == 1.f) ? 1.f : 2.f;
+    const float Ax = Cux / (c.fx * ru), Ay = Cuy / (c.fy * ru);
+    const float Bx = Cvx / (c.fx * rv), By = Cvy / (c.fy * rv);
+    const float nx = nc.x / c.fx, ny = nc.y / c.fy;
+    const float is = 1.f / (kap * dn0 * dn0), in2 = 1.f / (dn0 * dn0);
+    const float m00 = (Ax * Ax + Bx * Bx) * is - nx * nx * in2;
+    const float m01 = (Ax * Ay + Bx * By) * is - nx * ny * in2;
+    const float m11 = (Ay * Ay + By * By) * is - ny * ny * in2;
+    conic[2 * i] = make_float4(m00, m01, m11, -nx / dn0);
+    conic[2 * i + 1] = make_float4(-ny / dn0, cpx.hi, cpy.hi, 0.f);
+  }
   g[0] = make_float4(cpx.hi, cpy.hi, cpx.lo, cpy.lo);
   g[1] = make_float4(z, o, g1, g2);
   g[2] = make_float4(nc.x / c.fx, nc.y / c.fy, Cux / c.fx, Cuy / c.fy);
@@ -441,21 +508,57 @@ __global__ void k_permute(int N, const uint32_t* __restrict__ did, const float4*
 }
 
 template <typename KeyT>
-__global__ void k_duplicate(int N, int tiles_x, int rank_bits, const uint32_t* __restrict__ did,
-                            const uint2* __restrict__ rect, const uint32_t* __restrict__ offs,
-                            const uint32_t* __restrict__ count, KeyT* __restrict__ keys) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int rank_bits,
+                                                   const uint32_t* __restrict__ did,
+                                                   const uint2* __restrict__ rect,
+                                                   const float4* __restrict__ conic,
+                                                   const uint32_t* __restrict__ offs,
+                                                   const uint32_t* __restrict__ count,
+                                                   KeyT* __restrict__ keys) {
+  // one warp per surfel (rank order): the lanes test 32 tiles of the
+  // rectangle at a time and the passing ones are written in tile order
+  const int lane = threadIdx.x & 31;
+  const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (r >= N) return;
-  uint32_t id = did[r];
+  const uint32_t id = did[r];
   if (count[id] == 0) return;
-  uint2 rc = rect[id];
-  int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  const uint2 rc = rect[id];
+  const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
+  const float4 q0 = conic[2 * id], q1 = conic[2 * id + 1];
   size_t o = offs[r];
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      KeyT tile = (KeyT)(ty * tiles_x + tx);
-      keys[o++] = (tile << rank_bits) | (KeyT)r;
+  for (int b = 0; b < nt; b += 32) {
+    const int k = b + lane;
+    const int tx = tx0 + k % nx, ty = ty0 + k / nx;
+    const bool hit = k < nt && tile_may_hit(q0, q1, tx, ty, c.W, c.H);
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      const KeyT tile = (KeyT)(ty * c.tiles_x + tx);
+      keys[o + __popc(m & ((1u << lane) - 1u))] = (tile << rank_bits) | (KeyT)r;
     }
+    o += __popc(m);
+  }
+}
+
+// Exact instance count of each surfel: the tiles of its rectangle that pass
+// tile_may_hit (one warp per surfel, original order).
+__global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
+                                                    const uint2* __restrict__ rect,
+                                                    const float4* __restrict__ conic,
+                                                    uint32_t* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= N || count[i] == 0) return;  // warp-uniform
+  const uint2 rc = rect[i];
+  const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
+  const float4 q0 = conic[2 * i], q1 = conic[2 * i + 1];
+  uint32_t n = 0;
+  for (int k = lane; k < nt; k += 32)
+    n += tile_may_hit(q0, q1, tx0 + k % nx, ty0 + k / nx, c.W, c.H) ? 1u : 0u;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) n += __shfl_xor_sync(0xffffffffu, n, d);
+  if (lane == 0) count[i] = n;
 }
 
 template <typename KeyT>
@@ -479,8 +582,14 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
     k_preprocess<<<(N + 255) / 256, 256, 0, st>>>(
         c, s.alpha_min, N, mu, quat, scale, opacity, gamma, color, (float4*)(ws + L.geom_orig),
         (float4*)(ws + L.aux_orig), (uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.did0),
-        (uint2*)(ws + L.rect),
-        (uint32_t*)(ws + L.count));
+        (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint32_t*)(ws + L.count));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  {
+    NEXEL_PROF("tile_count", st);
+    k_tile_count<<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, st>>>(
+        c, N, (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint32_t*)(ws + L.count));
   }
   return cudaGetLastError();
 }
@@ -522,8 +631,8 @@ static cudaError_t binning_t(const DevCam& c, int N, long long n_inst, char* ws,
   int rb = L.key64 ? 32 : L.rank_bits;
   if (N > 0) {
     NEXEL_PROF("duplicate", st);
-    k_duplicate<KeyT><<<(N + 255) / 256, 256, 0, st>>>(
-        N, c.tiles_x, rb, (uint32_t*)(ws + L.did0), (uint2*)(ws + L.rect),
+    k_duplicate<KeyT><<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, st>>>(
+        c, N, rb, (uint32_t*)(ws + L.did0), (uint2*)(ws + L.rect), (float4*)(ws + L.conic),
         (uint32_t*)(ws + L.offs), (uint32_t*)(ws + L.count), k0);
   }
   int which = 0;

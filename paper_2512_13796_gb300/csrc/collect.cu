@@ -13,8 +13,9 @@
 // weighted colour of everything behind (R) so that
 // dL/dalpha_i = T_i (e_i - R_i), where e_i is the colour-side gradient of
 // surfel i: c_i . dL/dC if it is not textured, dL/dW_j if it fills slot j.
-// Per-surfel gradients are pre-reduced across the warp with shuffles and
-// added to the rank-ordered gradient records with one atomic per value.
+// Per-surfel gradients are pre-reduced across the warp with a transposing
+// shuffle butterfly and added to the rank-ordered gradient records with one
+// atomic per value, issued by 20 lanes at once.
 #include "common.cuh"
 
 namespace nexel {
@@ -111,10 +112,48 @@ __global__ void __launch_bounds__(kTilePix) k_collect_fwd(
   }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Warp sum of the 20 per-lane gradient values, added to dst[0..19] with one
+// atomic per value.  A transposing butterfly: at each xor step a lane keeps
+// one half of its partial sums and sends the other half to its partner
+// (20 -> 10 -> 5 -> 3 -> 2 -> 1 values, 21 shuffles instead of 5 x 20), so
+// that in the end 20 distinct lanes each hold the total of one value, at
+// index 10 b4 + 5 b3 + 3 b2 + 2 b1 + b0 (b = lane bits), and issue their
+// atomics in the same instruction.
+__device__ __forceinline__ void warp_sum20_add(const float (&g)[kGradStride], float* dst) {
+  static_assert(kGradStride == 20, "the butterfly below is laid out for 20 values");
+  const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+  float u[10];
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-  return v;
+  for (int i = 0; i < 10; ++i) {
+    const float keep = b4 ? g[10 + i] : g[i], send = b4 ? g[i] : g[10 + i];
+    u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float w[6];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float keep = b3 ? u[5 + i] : u[i], send = b3 ? u[i] : u[5 + i];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  w[5] = 0.f;
+  float x[4];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float keep = b2 ? w[3 + i] : w[i], send = b2 ? w[i] : w[3 + i];
+    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  x[3] = 0.f;
+  float y[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b1 ? x[2 + i] : x[i], send = b1 ? x[i] : x[2 + i];
+    y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  const float keep = b0 ? y[1] : y[0], send = b0 ? y[0] : y[1];
+  const float z = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+  const int lo = 2 * (int)b1 + (int)b0;      // index within the 3-value group
+  const int mid = 3 * (int)b2 + lo;          // index within the 5-value group
+  if (lo <= 2 && mid <= 4 && z != 0.f) atomicAdd(dst + 10 * (int)b4 + 5 * (int)b3 + mid, z);
 }
 
 template <int K, typename KeyT>
@@ -161,7 +200,6 @@ __global__ void __launch_bounds__(kTilePix) k_collect_bwd(
   __syncthreads();
   atomicMax(&s_max, last);
   __syncthreads();
-  const int lane = threadIdx.x & 31;
   const uint32_t list_end = rg.x + (uint32_t)s_max;
   for (uint32_t bend = list_end; bend > rg.x;) {
     const uint32_t bstart = (bend - rg.x > (uint32_t)kTilePix) ? bend - kTilePix : rg.x;
@@ -248,14 +286,7 @@ __global__ void __launch_bounds__(kTilePix) k_collect_bwd(
         g[12] = -du1 * h.u;
         g[13] = -dv2 * h.v;
       }
-#pragma unroll
-      for (int k = 0; k < kGradStride; ++k) g[k] = warp_sum(g[k]);
-      if (lane == 0) {
-        float* dst = grad + (size_t)s_rank[j] * kGradStride;
-#pragma unroll
-        for (int k = 0; k < kGradStride; ++k)
-          if (g[k] != 0.f) atomicAdd(dst + k, g[k]);
-      }
+      warp_sum20_add(g, grad + (size_t)s_rank[j] * kGradStride);
     }
     bend = bstart;
   }

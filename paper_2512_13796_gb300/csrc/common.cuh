@@ -119,7 +119,8 @@ __device__ __forceinline__ float downweight(float focal, float s, float t) {
 // sort scratch, whose size follows the instance capacity, come last, so
 // every call re-derives the same layout from (camera, K, N, ws_bytes).
 struct WsLayout {
-  size_t geom_orig, geom_sorted, aux_orig, aux_sorted, dkey0, dkey1, did0, did1, rect, count, offs,
+  size_t geom_orig, geom_sorted, aux_orig, aux_sorted, dkey0, dkey1, did0, did1, rect, conic, count,
+      offs,
       ranges, n_contrib,
       grad_sorted, counters, fixed_end, inst0, inst1, hist, scan_sums, total;
   int N, P, K, n_tiles, tile_bits, rank_bits, key64, tile_passes;
@@ -128,7 +129,7 @@ struct WsLayout {
 // Backward scratch (per sample): dL/dW_j, dL/dD_j, the field features and
 // the texture gradient.
 struct BwdLayout {
-  size_t dweff, ddepth, feat, gtex, gin, dtl, rc_notex, rc_weights, rc_ids, rc_depths, rc_T,
+  size_t dweff, ddepth, feat, gtex, gin, rc_notex, rc_weights, rc_ids, rc_depths, rc_T,
       total;
 };
 

@@ -1,5 +1,6 @@
 // BF16 tensor-core form of the texturing pass: forward, input-gradient
-// backward with the hash-table scatter, and the MLP weight-gradient GEMMs.
+// backward (the hash-table scatter follows in hash_bwd.cu), and the MLP
+// weight-gradient GEMMs.
 // FP32 accumulation everywhere; the table is read as FP16 or FP32.
 #include "texture_bf16.cuh"
 
@@ -146,9 +147,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_fwd_bf16(
   }
 }
 
-// Backward, per 16-row tile: recompute, input gradient through the MLP on
-// tensor cores, table scatter, dL/dD and dL/dW; saves the BF16 features and
-// the FP32 texture gradient (by row) for the weight-gradient kernel.
+// Backward, per 16-row tile: recompute (or read the cached features), input
+// gradient through the MLP on tensor cores, dL/dW; saves the feature
+// gradient (level-major, for hash_bwd.cu), the BF16 features and the FP32
+// texture gradient (by row) for the weight-gradient kernel.
 template <int IN, int H1, int H2, typename TT>
 __global__ void __launch_bounds__(kWarps * 32) k_tex_bwd_bf16(
     DevCam c, FieldDev f, int K, int KP, long long n_tiles, const float* __restrict__ weights,
@@ -229,7 +231,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_tex_bwd_bf16(
     } else {
       layer<H1, IN>(dl, sw + Bw::p1, Bw::t1, g, t, gin);
     }
-    // table scatter and depth gradient: n-tile nt, columns 8 nt + 2t -> level 4 nt + t
     // feature gradient by row (FP32): n-tile nt holds columns 8 nt + 2t, +1;
     // the hash-grid backward (k_hash_bwd) scatters it and writes ddepth of
     // textured samples
@@ -537,8 +538,7 @@ static cudaError_t bwd_bf16(const DevCam& c, const nexel_settings& s, const Fiel
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_hash_bwd(c, fd, s.K, KP, n_tiles * 16, std::is_same<TT, __half>::value, ids, depths,
-                      (const float2*)(bws + B.gin), (float*)(bws + B.dtl),
-                      (float*)(bws + B.ddepth), d_table, st);
+                      (const float2*)(bws + B.gin), (float*)(bws + B.ddepth), d_table, st);
   if (e != cudaSuccess || !d_mlp) return e;
   const size_t smem2 = sizeof(__nv_bfloat16) * WgSmem<IN, H1, H2>::total;
   auto kw = k_mlp_wgrad_bf16<IN, H1, H2>;

@@ -83,12 +83,11 @@ __host__ __device__ inline long long gin_stride(long long n_rows) { return (n_ro
 
 // Hash-grid backward (hash_bwd.cu): table scatter and dL/dD from the feature
 // gradient, level-major gin[l * gin_stride(n_rows) + r] = (dL/dh_l0, dL/dh_l1)
-// of row r (row r is pixel r / KP, slot r % KP); dtl is scratch of the same
-// shape (one float per entry).
+// of row r = p * KP + j (pixel p, slot j; KP the power of two >= K).  Writes
+// ddepth[p * K + j] of every textured sample.
 cudaError_t launch_hash_bwd(const DevCam& c, const FieldDev& fd, int K, int KP, long long n_rows,
                             bool half_table, const int* ids, const float* depths,
-                            const float2* gin, float* dtl, float* ddepth, float* d_table,
-                            cudaStream_t st);
+                            const float2* gin, float* ddepth, float* d_table, cudaStream_t st);
 
 // FP32 MLP forward; keeps the hidden activations when asked.
 template <int IN, int H1, int H2>

@@ -6,10 +6,11 @@
 // shared memory, then the composite C = N + sum_j W_j T_j + T_final bg of
 // Eq. 6 reduced over the slot lanes of the pixel with shuffles.
 //
-// Backward: the sample kernel recomputes the forward, runs the MLP backward
-// for the input gradient, scatters the hash-table gradient (float2 atomics)
-// and forms dL/dD (through the trilinear weights, Delta and x = o + D d) and
-// dL/dW; it leaves the features and the texture gradient in the workspace,
+// Backward: the sample kernel recomputes the forward (or reads the features
+// the forward of a training step left), runs the MLP backward for the
+// feature gradient and forms dL/dW; it leaves the feature gradient (for the
+// hash-grid backward, hash_bwd.cu, which scatters it into the table gradient
+// and forms dL/dD), the features and the texture gradient in the workspace,
 // from which a second kernel forms the MLP weight gradients (a reduction
 // over all samples) with per-thread register accumulators.
 #pragma once
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(256) k_tex_fwd_f32(DevCam c, FieldDev f, int K
 // ------------------------------------------------------------ backward
 template <int IN, int H1, int H2, typename TT>
 __global__ void __launch_bounds__(256) k_tex_bwd_f32(
-    DevCam c, FieldDev f, int K, const float* __restrict__ weights, const int* __restrict__ ids,
+    DevCam c, FieldDev f, int K, int KP, const float* __restrict__ weights, const int* __restrict__ ids,
     const float* __restrict__ depths, const float* __restrict__ d_image,
     const float* __restrict__ d_weights, const float* __restrict__ d_textures,
     float* __restrict__ dweff, float* __restrict__ ddepth, float* __restrict__ feat_out,
@@ -94,7 +95,6 @@ __global__ void __launch_bounds__(256) k_tex_bwd_f32(
   __syncthreads();
   const long long S = (long long)c.W * c.H * K;
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  // no early exit: the table scatter is warp-aggregated, every lane takes part
   const bool in_range = s < S;
   const int id = in_range ? ids[s] : -1;
   const bool active = id >= 0;
@@ -140,11 +140,13 @@ __global__ void __launch_bounds__(256) k_tex_bwd_f32(
   // the hash-grid backward (k_hash_bwd) reads gin and writes ddepth of
   // textured samples
   if (in_range) {
-    // level-major: (dL/dh_l0, dL/dh_l1) of level l at gin_out[l * R + s]
-    const long long R = gin_stride(S);
+    // level-major: (dL/dh_l0, dL/dh_l1) of level l at gin_out[l * R + row],
+    // row = p * KP + j
+    const long long R = gin_stride(S / K * KP);
+    const long long row = (s / K) * KP + s % K;
     float2* g2 = reinterpret_cast<float2*>(gin_out);
 #pragma unroll
-    for (int l = 0; l < IN / 2; ++l) g2[l * R + s] = make_float2(gin[2 * l], gin[2 * l + 1]);
+    for (int l = 0; l < IN / 2; ++l) g2[l * R + row] = make_float2(gin[2 * l], gin[2 * l + 1]);
   }
   (void)x;
   (void)d;
@@ -294,17 +296,20 @@ cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
                                cudaStream_t st) {
   long long S = (long long)c.W * c.H * s.K;
   if (S == 0) return cudaSuccess;
+  int KP = 1;
+  while (KP < s.K) KP <<= 1;
   {
     NEXEL_PROF("texture_bwd_f32", st);
     k_tex_bwd_f32<IN, H1, H2, TT><<<(unsigned)((S + 255) / 256), 256, 0, st>>>(
-        c, fd, s.K, weights, ids, depths, d_image, d_weights, d_textures, (float*)(bws + B.dweff),
+        c, fd, s.K, KP, weights, ids, depths, d_image, d_weights, d_textures, (float*)(bws + B.dweff),
         (float*)(bws + B.ddepth), (float*)(bws + B.feat), (float4*)(bws + B.gtex),
         (float*)(bws + B.gin), d_table);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_hash_bwd(c, fd, s.K, s.K, S, false, ids, depths, (const float2*)(bws + B.gin),
-                      (float*)(bws + B.dtl), (float*)(bws + B.ddepth), d_table, st);
+  e = launch_hash_bwd(c, fd, s.K, KP, (long long)c.W * c.H * KP, false, ids, depths,
+                      (const float2*)(bws + B.gin),
+                      (float*)(bws + B.ddepth), d_table, st);
   if (e != cudaSuccess || !d_mlp) return e;
   size_t smem = wgrad_smem_f32<IN, H1, H2>();
   e = cudaFuncSetAttribute(k_mlp_wgrad_f32<IN, H1, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

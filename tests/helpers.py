@@ -51,12 +51,20 @@ def flat(out, K):
                 T_final=out["T_final"].reshape(P))
 
 
+# Tie bits that can change a forward output discontinuously: the top-K
+# choice, the alpha_min skip, the T_min stop, the near-plane cut and the
+# depth order.  Near a hash-cell face (32) or a ReLU kink (64) the texture is
+# continuous -- only its derivative jumps -- so those pixels stay in the
+# forward comparison and are excluded from the gradient comparisons only.
+FWD_TIE_MASK = 1 | 2 | 4 | 8 | 16
+
+
 def compare_forward(gpu, ref, K, tol_color, tol_rel=1e-4, check_textures=True):
-    """Element-by-element comparison on the oracle's pixels that are not tie
-    pixels.  Returns a dict of error statistics."""
+    """Element-by-element comparison on the oracle's pixels that are not
+    forward tie pixels.  Returns a dict of error statistics."""
     pix = ref["pixels"]
     g = {k: v[pix] for k, v in flat(gpu, K).items()}
-    ok = ref["tie"] == 0
+    ok = (ref["tie"] & FWD_TIE_MASK) == 0
     stats = dict(n_pix=int(pix.size), n_tie=int((~ok).sum()))
     for bit, name in oracle.TIE_BITS.items():
         stats["tie_" + name] = int(((ref["tie"] & bit) != 0).sum())
