@@ -77,43 +77,63 @@ __device__ __forceinline__ float3 rotT(const float* R, float3 v) {
 // every pixel where alpha >= alpha_min.  The tile is kept unless Q > 0 on
 // the whole rectangle of its pixel centres grown by one pixel (and a small
 // tolerance), so dropping it removes only (pixel, surfel) pairs that the
-// collection pass would skip anyway.  The minimum of a quadratic over a
-// rectangle lies at a corner, at the critical point of an edge, or (when M
-// is positive definite) at the interior critical point.
+// collection pass would skip anyway.
 //
-// One out-of-line body with explicitly rounded operations: the counting and
-// the emitting kernels must take identical decisions.
-__device__ __noinline__ bool tile_may_hit(const float4 q0, const float4 q1, int tx, int ty, int W,
-                                          int H) {
-  const float m00 = q0.x, m01 = q0.y, m11 = q0.z, bx = q0.w, by = q1.x;
-  const float X0 = tx * kTile + 0.5f - 1.f - q1.y, X1 = min(tx * kTile + kTile - 1, W - 1) + 1.5f - q1.y;
-  const float Y0 = ty * kTile + 0.5f - 1.f - q1.z, Y1 = min(ty * kTile + kTile - 1, H - 1) + 1.5f - q1.z;
-  auto Q = [&](float x, float y) {
-    return __fsub_rn(fmaf(x, fmaf(m00, x, 2.f * fmaf(m01, y, bx)), __fmul_rn(y, fmaf(m11, y, 2.f * by))),
-                     1.f);
-  };
-  float q = fminf(fminf(Q(X0, Y0), Q(X1, Y0)), fminf(Q(X0, Y1), Q(X1, Y1)));
-  if (m00 > 0.f) {
-    const float ya[2] = {Y0, Y1};
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const float x = fminf(fmaxf(__fdiv_rn(-fmaf(m01, ya[e], bx), m00), X0), X1);
-      q = fminf(q, Q(x, ya[e]));
-    }
-  }
-  if (m11 > 0.f) {
-    const float xa[2] = {X0, X1};
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const float y = fminf(fmaxf(__fdiv_rn(-fmaf(m01, xa[e], by), m11), Y0), Y1);
-      q = fminf(q, Q(xa[e], y));
-    }
-  }
-  const float det = __fsub_rn(__fmul_rn(m00, m11), __fmul_rn(m01, m01));
-  if (m00 > 0.f && det > 0.f) {
-    const float xs = __fdiv_rn(__fsub_rn(__fmul_rn(m01, by), __fmul_rn(m11, bx)), det);
-    const float ys = __fdiv_rn(__fsub_rn(__fmul_rn(m01, bx), __fmul_rn(m00, by)), det);
-    if (xs >= X0 && xs <= X1 && ys >= Y0 && ys <= Y1) q = fminf(q, Q(xs, ys));
+// Minimum of Q over the rectangle.  When M is positive definite (the
+// common case: the support is an ellipse) Q is convex with its minimum at
+// delta*: if delta* lies in the rectangle the tile is kept; otherwise the
+// constrained minimum lies on an edge that faces delta* (from the minimiser
+// Q decreases towards delta*, which must leave the rectangle), so only the
+// one or two facing edges are searched.  Otherwise (an oblique surfel whose
+// support reaches the horizon) the minimum lies at a corner, at the
+// critical point of an edge or at the interior critical point.
+//
+// Every operation is explicitly rounded (no contraction left to the
+// compiler), so the counting and the emitting kernels take identical
+// decisions.
+struct TileConic {
+  float m00, m01, m11, bx, by, cpx, cpy, inv00, inv11, dsx, dsy, pd;
+};
+
+__device__ __forceinline__ TileConic load_conic(const float4* __restrict__ conic, uint32_t i) {
+  const float4 a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
+  return {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+}
+
+__device__ __forceinline__ float conic_q(const TileConic& k, float x, float y) {
+  // x (m00 x + 2 (m01 y + bx)) + y (m11 y + 2 by) - 1
+  const float lx = __fmaf_rn(k.m00, x, __fmul_rn(2.f, __fmaf_rn(k.m01, y, k.bx)));
+  const float ly = __fmaf_rn(k.m11, y, __fmul_rn(2.f, k.by));
+  return __fadd_rn(__fmaf_rn(x, lx, __fmul_rn(y, ly)), -1.f);
+}
+
+// min of Q on the edge x = xe, y in [y0, y1] (m11 > 0)
+__device__ __forceinline__ float edge_min_x(const TileConic& k, float xe, float y0, float y1) {
+  const float y = fminf(fmaxf(__fmul_rn(-__fmaf_rn(k.m01, xe, k.by), k.inv11), y0), y1);
+  return conic_q(k, xe, y);
+}
+// min of Q on the edge y = ye, x in [x0, x1] (m00 > 0)
+__device__ __forceinline__ float edge_min_y(const TileConic& k, float ye, float x0, float x1) {
+  const float x = fminf(fmaxf(__fmul_rn(-__fmaf_rn(k.m01, ye, k.bx), k.inv00), x0), x1);
+  return conic_q(k, x, ye);
+}
+
+__device__ __forceinline__ bool tile_may_hit(const TileConic& k, int tx, int ty, int W, int H) {
+  const float X0 = __fadd_rn((float)(tx * kTile) - 0.5f, -k.cpx);
+  const float X1 = __fadd_rn((float)min(tx * kTile + kTile - 1, W - 1) + 1.5f, -k.cpx);
+  const float Y0 = __fadd_rn((float)(ty * kTile) - 0.5f, -k.cpy);
+  const float Y1 = __fadd_rn((float)min(ty * kTile + kTile - 1, H - 1) + 1.5f, -k.cpy);
+  float q = 3.0e38f;
+  if (k.pd != 0.f) {
+    const bool in_x = k.dsx >= X0 && k.dsx <= X1, in_y = k.dsy >= Y0 && k.dsy <= Y1;
+    if (in_x && in_y) return true;
+    if (!in_x) q = edge_min_x(k, k.dsx < X0 ? X0 : X1, Y0, Y1);
+    if (!in_y) q = fminf(q, edge_min_y(k, k.dsy < Y0 ? Y0 : Y1, X0, X1));
+  } else {
+    q = fminf(fminf(conic_q(k, X0, Y0), conic_q(k, X1, Y0)),
+              fminf(conic_q(k, X0, Y1), conic_q(k, X1, Y1)));
+    if (k.m00 > 0.f) q = fminf(q, fminf(edge_min_y(k, Y0, X0, X1), edge_min_y(k, Y1, X0, X1)));
+    if (k.m11 > 0.f) q = fminf(q, fminf(edge_min_x(k, X0, Y0, Y1), edge_min_x(k, X1, Y0, Y1)));
   }
   return !(q > 1e-3f);  // NaN keeps the tile
 }
@@ -242,8 +262,15 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __re
     const float m00 = (Ax * Ax + Bx * Bx) * is - nx * nx * in2;
     const float m01 = (Ax * Ay + Bx * By) * is - nx * ny * in2;
     const float m11 = (Ay * Ay + By * By) * is - ny * ny * in2;
-    conic[2 * i] = make_float4(m00, m01, m11, -nx / dn0);
-    conic[2 * i + 1] = make_float4(-ny / dn0, cpx.hi, cpy.hi, 0.f);
+    const float bx = -nx / dn0, by = -ny / dn0;
+    const float det = m00 * m11 - m01 * m01;
+    const bool pd = m00 > 0.f && m11 > 0.f && det > 0.f;
+    // minimiser delta* = -M^-1 b of the convex case
+    const float dsx = pd ? (m01 * by - m11 * bx) / det : 0.f;
+    const float dsy = pd ? (m01 * bx - m00 * by) / det : 0.f;
+    conic[3 * i] = make_float4(m00, m01, m11, bx);
+    conic[3 * i + 1] = make_float4(by, cpx.hi, cpy.hi, m00 > 0.f ? 1.f / m00 : 0.f);
+    conic[3 * i + 2] = make_float4(m11 > 0.f ? 1.f / m11 : 0.f, dsx, dsy, pd ? 1.f : 0.f);
   }
   g[0] = make_float4(cpx.hi, cpy.hi, cpx.lo, cpy.lo);
   g[1] = make_float4(z, o, g1, g2);
@@ -525,12 +552,12 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
   const uint2 rc = rect[id];
   const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
   const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
-  const float4 q0 = conic[2 * id], q1 = conic[2 * id + 1];
+  const TileConic kc = load_conic(conic, id);
   size_t o = offs[r];
   for (int b = 0; b < nt; b += 32) {
     const int k = b + lane;
     const int tx = tx0 + k % nx, ty = ty0 + k / nx;
-    const bool hit = k < nt && tile_may_hit(q0, q1, tx, ty, c.W, c.H);
+    const bool hit = k < nt && tile_may_hit(kc, tx, ty, c.W, c.H);
     const unsigned m = __ballot_sync(0xffffffffu, hit);
     if (hit) {
       const KeyT tile = (KeyT)(ty * c.tiles_x + tx);
@@ -552,10 +579,10 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
   const uint2 rc = rect[i];
   const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
   const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
-  const float4 q0 = conic[2 * i], q1 = conic[2 * i + 1];
+  const TileConic kc = load_conic(conic, (uint32_t)i);
   uint32_t n = 0;
   for (int k = lane; k < nt; k += 32)
-    n += tile_may_hit(q0, q1, tx0 + k % nx, ty0 + k / nx, c.W, c.H) ? 1u : 0u;
+    n += tile_may_hit(kc, tx0 + k % nx, ty0 + k / nx, c.W, c.H) ? 1u : 0u;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) n += __shfl_xor_sync(0xffffffffu, n, d);
   if (lane == 0) count[i] = n;

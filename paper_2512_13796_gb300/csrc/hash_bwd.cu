@@ -25,21 +25,12 @@ namespace nexel {
 
 namespace {
 
-constexpr uint32_t kNoKey = 0xFFFFFFFFu;
 constexpr int kHbThreads = 256;
-constexpr int kHbMinBlocks = 6;
+constexpr int kHbMinBlocks = 5;
 
-__device__ __forceinline__ void run_add2(float2* base, uint32_t idx, float vx, float vy,
-                                         bool valid, int lane) {
-  const uint32_t key = valid ? idx : kNoKey;
-  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
-  if (__popc(heads) > 16) {  // many distinct entries: plain atomics
-    if (valid) atomicAdd(base + idx, make_float2(vx, vy));
-    return;
-  }
-  // inclusive segmented scan: a lane accumulates the lanes of its run below it
-  const int seg_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+// Inclusive segmented scan of (vx, vy) over the lanes; seg_start is the
+// first lane of the calling lane's segment.
+__device__ __forceinline__ void seg_scan2(float& vx, float& vy, int lane, int seg_start) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const float ox = __shfl_up_sync(0xffffffffu, vx, d);
@@ -49,8 +40,6 @@ __device__ __forceinline__ void run_add2(float2* base, uint32_t idx, float vx, f
       vy += oy;
     }
   }
-  const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-  if (valid && tail) atomicAdd(base + idx, make_float2(vx, vy));
 }
 
 }  // namespace
@@ -102,8 +91,24 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     const float wx[2] = {1.f - rx, rx}, wy[2] = {1.f - ry, ry}, wz[2] = {1.f - rz, rz};
     const TT* tl = reinterpret_cast<const TT*>(f.table) + (size_t)l * T * 2;
     float2* dl = d_table ? reinterpret_cast<float2*>(d_table + (size_t)l * T * 2) : nullptr;
-    // runs of equal entries need cells of about two pixels or more
-    const bool share = __any_sync(0xffffffffu, valid && rr >= 2.f);
+    // neighbour structure along the warp (consecutive pixels of one slot):
+    // a lane whose successor lies in the same cell shares all 8 entries
+    // with it; one whose successor lies in the next cell along x shares its
+    // 4 entries at x + 1 with the successor's entries at x
+    const int ncx = __shfl_down_sync(0xffffffffu, cx, 1);
+    const int ncy = __shfl_down_sync(0xffffffffu, cy, 1);
+    const int ncz = __shfl_down_sync(0xffffffffu, cz, 1);
+    const bool nvalid = __shfl_down_sync(0xffffffffu, valid, 1) && lane < 31;
+    const bool yz_next = valid && nvalid && ncy == cy && ncz == cz;
+    const bool same_next = yz_next && ncx == cx, adj_next = yz_next && ncx == cx + 1;
+    const bool same_prev = __shfl_up_sync(0xffffffffu, same_next, 1) && lane > 0;
+    const bool adj_prev = __shfl_up_sync(0xffffffffu, adj_next, 1) && lane > 0;
+    const unsigned heads = __ballot_sync(0xffffffffu, !same_prev);
+    // runs of one cell are summed with a segmented scan when there are few
+    // of them; otherwise every lane adds its own values
+    const bool scan = __popc(heads) <= 16;
+    const int seg_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const bool tail = !scan || !same_next;
     const float gsx = dw * g.x, gsy = dw * g.y;
     float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
 #pragma unroll
@@ -121,11 +126,28 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
         qy = fmaf(ge, dy ? wxz : -wxz, qy);
         qz = fmaf(ge, dz ? wxy : -wxy, qz);
       }
-      if (dl) {
-        if (share)
-          run_add2(dl, idx, w * gsx, w * gsy, valid, lane);
-        else if (valid)
-          atomicAdd(dl + idx, make_float2(w * gsx, w * gsy));
+    }
+    if (dl) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {  // (dy, dz) pairs: entries at x and x + 1
+        const int dy = kk & 1, dz = kk >> 1;
+        const uint32_t hyz = hy[dy] ^ hz[dz];
+        const float wyz = wy[dy] * wz[dz];
+        float v0x = wx[0] * wyz * gsx, v0y = wx[0] * wyz * gsy;
+        float v1x = wx[1] * wyz * gsx, v1y = wx[1] * wyz * gsy;
+        if (scan) seg_scan2(v1x, v1y, lane, seg_start);
+        // the run ending here hands its x + 1 sums to the next run's x entry
+        const float px = __shfl_up_sync(0xffffffffu, (tail && adj_next) ? v1x : 0.f, 1);
+        const float py = __shfl_up_sync(0xffffffffu, (tail && adj_next) ? v1y : 0.f, 1);
+        if (adj_prev && lane > 0) {
+          v0x += px;
+          v0y += py;
+        }
+        if (scan) seg_scan2(v0x, v0y, lane, seg_start);
+        if (valid && tail) {
+          atomicAdd(dl + ((hx[0] ^ hyz) & f.mask), make_float2(v0x, v0y));
+          if (!adj_next) atomicAdd(dl + ((hx[1] ^ hyz) & f.mask), make_float2(v1x, v1y));
+        }
       }
     }
     // Delta = 1 - exp(-r^2 / 2pi), r = f / (s D): dDelta/dD = -(1 - Delta) r^2 / (pi D)
