@@ -127,6 +127,7 @@ BwdLayout bwd_layout(const nexel_camera& cam, int K, int feat_dim, bool recomput
   B.rc_ids = take(rc * S * 4);
   B.rc_depths = take(rc * S * 4);
   B.rc_T = take(rc * P * 4);
+  B.status = take(256);
   B.total = o;
   return B;
 }

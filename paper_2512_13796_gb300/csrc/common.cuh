@@ -130,6 +130,7 @@ struct WsLayout {
 // the texture gradient.
 struct BwdLayout {
   size_t dweff, ddepth, feat, gtex, gin, rc_notex, rc_weights, rc_ids, rc_depths, rc_T,
+      status,  // kernel status words (a bounded wait that ran out sets one)
       total;
 };
 

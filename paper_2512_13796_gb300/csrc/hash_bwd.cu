@@ -29,10 +29,11 @@ constexpr int kHbThreads = 256;
 constexpr int kHbMinBlocks = 5;
 
 // Inclusive segmented scan of (vx, vy) over the lanes; seg_start is the
-// first lane of the calling lane's segment.
-__device__ __forceinline__ void seg_scan2(float& vx, float& vy, int lane, int seg_start) {
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
+// first lane of the calling lane's segment, max_len (warp-uniform) the
+// longest segment.
+__device__ __forceinline__ void seg_scan2(float& vx, float& vy, int lane, int seg_start,
+                                          int max_len) {
+  for (int d = 1; d < max_len; d <<= 1) {
     const float ox = __shfl_up_sync(0xffffffffu, vx, d);
     const float oy = __shfl_up_sync(0xffffffffu, vy, d);
     if (lane - d >= seg_start) {
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     D = depths[s];
     d = pixel_dir(c, (int)(p % (uint32_t)c.W), (int)(p / (uint32_t)c.W));
   }
+  const float iD = 1.f / D, fD = f.focal * iD;
   const float3 x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
   const size_t T = (size_t)f.mask + 1;
   const int L = f.L;
@@ -82,8 +84,9 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
     const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
     const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
-    const float rr = f.focal / (sl * D);  // cell size in pixels at depth D
-    const float dw = downweight(f.focal, sl, D);
+    const float rr = fD * f.inv_s[l];  // cell size in pixels at depth D
+    // Eq. 3: Delta = 1 - exp(-r^2 / 2pi), r = f / (s D)
+    const float dw = -expm1f(-rr * rr * 0.15915494309189535f);
     // per-axis parts of the spatial hash (MapPositive, times the primes)
     const uint32_t hx[2] = {map_pos(cx), map_pos(cx + 1)};
     const uint32_t hy[2] = {map_pos(cy) * 2654435761u, map_pos(cy + 1) * 2654435761u};
@@ -108,6 +111,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     // of them; otherwise every lane adds its own values
     const bool scan = __popc(heads) <= 16;
     const int seg_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const int max_len = (int)__reduce_max_sync(0xffffffffu, (unsigned)(lane - seg_start)) + 1;
     const bool tail = !scan || !same_next;
     const float gsx = dw * g.x, gsy = dw * g.y;
     float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
         const float wyz = wy[dy] * wz[dz];
         float v0x = wx[0] * wyz * gsx, v0y = wx[0] * wyz * gsy;
         float v1x = wx[1] * wyz * gsx, v1y = wx[1] * wyz * gsy;
-        if (scan) seg_scan2(v1x, v1y, lane, seg_start);
+        if (scan) seg_scan2(v1x, v1y, lane, seg_start, max_len);
         // the run ending here hands its x + 1 sums to the next run's x entry
         const float px = __shfl_up_sync(0xffffffffu, (tail && adj_next) ? v1x : 0.f, 1);
         const float py = __shfl_up_sync(0xffffffffu, (tail && adj_next) ? v1y : 0.f, 1);
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
           v0x += px;
           v0y += py;
         }
-        if (scan) seg_scan2(v0x, v0y, lane, seg_start);
+        if (scan) seg_scan2(v0x, v0y, lane, seg_start, max_len);
         if (valid && tail) {
           atomicAdd(dl + ((hx[0] ^ hyz) & f.mask), make_float2(v0x, v0y));
           if (!adj_next) atomicAdd(dl + ((hx[1] ^ hyz) & f.mask), make_float2(v1x, v1y));
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
       }
     }
     // Delta = 1 - exp(-r^2 / 2pi), r = f / (s D): dDelta/dD = -(1 - Delta) r^2 / (pi D)
-    const float ddw = -(1.f - dw) * rr * rr * 0.3183098861837907f / D;
+    const float ddw = -(1.f - dw) * rr * rr * 0.3183098861837907f * iD;
     dt += (g.x * ax + g.y * ay) * ddw + dw * sl * (qx * d.x + qy * d.y + qz * d.z);
   }
   if (valid) ddepth[s] = dt;

@@ -521,6 +521,18 @@ static cudaError_t bwd_bf16(const DevCam& c, const nexel_settings& s, const Fiel
   while (KP < s.K) KP <<= 1;
   const long long rows = (long long)c.W * c.H * KP;
   const long long n_tiles = (rows + 15) / 16;
+  if (fd.feat_mode == 2 && tc_arch_supported(IN, H1, H2)) {
+    // the forward cached the features: MLP backward and weight gradients on
+    // tcgen05, then the hash-grid backward
+    cudaError_t e = launch_texture_bwd_tc(
+        c, s.K, KP, n_tiles * 16, IN, H1, H2, fd.w, (const uint32_t*)(bws + B.feat), weights, ids,
+        d_image, d_weights, d_textures, (float*)(bws + B.dweff), (float2*)(bws + B.gin), d_mlp,
+        (int*)(bws + B.status), st);
+    if (e != cudaSuccess) return e;
+    return launch_hash_bwd(c, fd, s.K, KP, n_tiles * 16, std::is_same<TT, __half>::value, ids,
+                           depths, (const float2*)(bws + B.gin), (float*)(bws + B.ddepth), d_table,
+                           st);
+  }
   const size_t smem = sizeof(__nv_bfloat16) * Bf16W<IN, H1, H2>::all_elems;
   auto kern = k_tex_bwd_bf16<IN, H1, H2, TT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

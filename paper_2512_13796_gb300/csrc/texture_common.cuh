@@ -14,6 +14,7 @@ struct FieldDev {
   uint32_t mask;  // T - 1
   float focal;    // f of Eq. 3 (fx)
   float s[NEXEL_MAX_LEVELS];
+  float inv_s[NEXEL_MAX_LEVELS];  // 1 / s
   const void* table;
   const float* w;
   // per-sample feature buffer of a training step: feat_mode 1 = the forward
@@ -30,7 +31,10 @@ inline FieldDev make_fielddev(const DevCam& c, const nexel_field& f) {
   d.L = f.L;
   d.mask = (uint32_t)f.T - 1u;
   d.focal = c.fx;
-  for (int l = 0; l < NEXEL_MAX_LEVELS; ++l) d.s[l] = l < f.L ? f.level_scale[l] : 0.f;
+  for (int l = 0; l < NEXEL_MAX_LEVELS; ++l) {
+    d.s[l] = l < f.L ? f.level_scale[l] : 0.f;
+    d.inv_s[l] = l < f.L ? 1.f / f.level_scale[l] : 0.f;
+  }
   d.table = f.table;
   d.w = f.weights;
   return d;
@@ -200,6 +204,16 @@ __device__ __forceinline__ void mlp_bwd_input_f32(const float* __restrict__ sW, 
     }
   }
 }
+
+// tcgen05 texture-MLP backward from cached features (texture_tc.cu):
+// writes dweff, the level-major feature gradient and adds the MLP weight
+// gradients to d_mlp (may be null).
+bool tc_arch_supported(int in, int h1, int h2);
+cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
+                                  int h2, const float* w, const uint32_t* feat,
+                                  const float* weights, const int* ids, const float* d_image,
+                                  const float* d_weights, const float* d_textures, float* dweff,
+                                  float2* gin, float* d_mlp, int* status, cudaStream_t st);
 
 // BF16 tensor-core texturing (texture_bf16.cu).
 bool bf16_arch_supported(const nexel_field& f);

@@ -1,0 +1,464 @@
+// Texture-MLP backward on the 5th-generation tensor cores (tcgen05, TMEM
+// accumulators), for a training step whose forward cached the features:
+// Sec. 4.2 / Eq. 4 backward through G (no bias, ReLU hidden layers, linear
+// output) for every textured sample, and the MLP weight gradients summed
+// over all samples.
+//
+// One CTA of 128 threads owns 128-row tiles (row = (pixel, slot) pair,
+// pixel-major with KP rows per pixel; thread t = row t of the tile = TMEM
+// lane t).  Per tile, four rounds of MMAs (M = 128, BF16 operands in shared
+// memory, FP32 accumulators in TMEM), each followed by an epilogue in which
+// every thread reads its row back (tcgen05.ld), applies ReLU or its mask and
+// writes the next operand to shared memory:
+//   R1  h1 = X W1^T                      (X = cached features)
+//   R2  h2 = h1 W2^T                     (two hidden layers only)
+//       T = h_last W3^T, dL/dW_j = T . dL/dC + dL/dW_j (upstream), d3 = the
+//       texture gradient, d_last = (d3 W3) * [h_last > 0]   (CUDA cores)
+//   R3  d1 = (d2 W2) * [h1 > 0]           (two hidden layers only)
+//   R4  feature gradient X' = d1 W1 (to the hash-grid backward), and the
+//       weight gradients, accumulated in TMEM over all tiles of the CTA:
+//         Da += [h1 | h2]^T [d_last | d3]  -> dW2 (or dummy) and dW3 blocks
+//         Db += [X | ...]^T d1             -> dW1 block
+//       (the row-major activation tiles are read MN-major, K = rows, so no
+//       transposed copies are made).
+// Shared-memory operands use the no-swizzle core-matrix layout (8 rows x
+// 16 bytes per core matrix); a descriptor's leading byte offset is the
+// stride between core matrices along K and its stride byte offset the stride
+// along M/N, for K-major and MN-major operands alike.
+#include "texture_common.cuh"
+
+#include <algorithm>
+
+namespace nexel {
+
+namespace {
+
+constexpr int kTcRows = 128;
+constexpr int kTcThreads = 128;
+constexpr int kTcCols = 256;  // TMEM columns per CTA (two CTAs per SM)
+constexpr int kTcWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor, kind::f16: BF16 x BF16 -> F32, M x N
+__host__ __device__ constexpr uint32_t idesc(int m, int n, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                    bool acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(id), "r"((uint32_t)acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(bar)));
+}
+
+// Bounded wait for the mbarrier phase `parity`; false when the limit ran out.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < kTcWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Thread-to-MMA hand-over: generic-proxy shared stores and TMEM reads of all
+// threads happen before the MMAs thread 0 issues next.
+__device__ __forceinline__ void sync_to_mma() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// byte offset of element (row r, feature f) in a core-matrix tile whose
+// 8-row groups are sg bytes apart
+__host__ __device__ constexpr uint32_t cm_off(int r, int f, int sg) {
+  return (uint32_t)((r >> 3) * sg + (f >> 3) * 128 + (r & 7) * 16 + (f & 7) * 2);
+}
+
+// Stores 8 consecutive features f0..f0+7 (f0 % 8 == 0) of row r.
+__device__ __forceinline__ void st8(unsigned char* base, int r, int f0, int sg, const float* v) {
+  uint4 q = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+  *reinterpret_cast<uint4*>(base + cm_off(r, f0, sg)) = q;
+}
+
+template <int IN, int H1, int H2>
+struct TcLayout {
+  static constexpr int HL = H2 > 0 ? H2 : H1;
+  static constexpr int FA = IN + H1 + H2;                  // activation features per row
+  static constexpr int FD = HL + 16 + (H2 > 0 ? H1 : 0);  // delta features per row
+  static constexpr int SA = FA / 8 * 128, SD = FD / 8 * 128;
+  static constexpr int D1 = H2 > 0 ? HL + 16 : 0;         // first feature of d1 in the delta tile
+  // bytes
+  static constexpr int act = 0;
+  static constexpr int act_bytes = kTcRows / 8 * SA + 2048;  // MN-major reads run up to 128 features
+  static constexpr int del = act + act_bytes;
+  static constexpr int del_bytes = kTcRows / 8 * SD + 2048;
+  static constexpr int w1 = del + del_bytes;                 // [H1][IN]   K-major, B of R1
+  static constexpr int w2 = w1 + H1 * IN * 2;                // [H2][H1]   B of R2
+  static constexpr int w2t = w2 + H2 * H1 * 2;               // [H1][H2]   B of R3
+  static constexpr int w1t = w2t + H2 * H1 * 2;              // [IN][H1]   B of the feature gradient
+  static constexpr int w3 = w1t + IN * H1 * 2;               // FP32 [3][HL]
+  static constexpr int total = w3 + 3 * HL * 4;
+  static_assert(IN % 16 == 0 && H1 == 64 && (H2 == 0 || H2 == 64), "supported MLP shapes");
+  static_assert(HL + 16 <= 256 && FA <= 256, "MMA N limits");
+};
+
+template <int IN, int H1, int H2>
+__global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
+    DevCam c, int K, int log2KP, long long n_rows, long long n_tiles, const float* __restrict__ wts,
+    const uint32_t* __restrict__ feat, const float* __restrict__ weights,
+    const int* __restrict__ ids, const float* __restrict__ d_image,
+    const float* __restrict__ d_weights, const float* __restrict__ d_textures,
+    float* __restrict__ dweff, float2* __restrict__ gin, float* __restrict__ d_mlp,
+    int* __restrict__ status) {
+  using Lt = TcLayout<IN, H1, H2>;
+  constexpr int HL = Lt::HL;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* act = tc_smem + Lt::act;
+  unsigned char* del = tc_smem + Lt::del;
+  float* w3s = reinterpret_cast<float*>(tc_smem + Lt::w3);
+
+  // weights -> shared: BF16 K-major core-matrix tiles (B operands), W3 FP32
+  {
+    const float* W1 = wts;               // [H1][IN]
+    const float* W2 = wts + H1 * IN;     // [H2][H1]
+    const float* W3 = W2 + H2 * H1;      // [3][HL]
+    for (int i = tid; i < H1 * IN; i += kTcThreads) {
+      const int o = i / IN, k = i % IN;
+      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w1 + cm_off(o, k, IN / 8 * 128)) =
+          __float2bfloat16_rn(W1[i]);
+      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w1t + cm_off(k, o, H1 / 8 * 128)) =
+          __float2bfloat16_rn(W1[i]);
+    }
+    for (int i = tid; i < H2 * H1; i += kTcThreads) {
+      const int o = i / H1, k = i % H1;
+      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w2 + cm_off(o, k, H1 / 8 * 128)) =
+          __float2bfloat16_rn(W2[i]);
+      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w2t + cm_off(k, o, (H2 > 0 ? H2 : 8) / 8 * 128)) =
+          __float2bfloat16_rn(W2[i]);
+    }
+    for (int i = tid; i < 3 * HL; i += kTcThreads) w3s[i] = W3[i];
+    // zero the delta tile once: the padding columns of d3 stay zero
+    for (int i = tid; i < Lt::del_bytes / 16; i += kTcThreads)
+      reinterpret_cast<uint4*>(del)[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  sync_to_mma();
+  const uint32_t tmem = s_tmem;
+  const uint32_t t0 = tmem, t_da = tmem + 64, t_db = tmem + 64 + 80;  // columns
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t sb = smem_u32(tc_smem);
+  uint32_t phase = 0;
+  bool ok = true;
+  bool first = true;
+  const long long P = (long long)c.W * c.H;
+  const int KP = 1 << log2KP;
+
+  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const long long r = tile * kTcRows + tid;
+    const long long p = r >> log2KP;
+    const int j = (int)(r & (KP - 1));
+    const long long s = p * K + j;
+    const bool in_pix = r < n_rows && p < P && j < K;
+    const bool valid = in_pix && ids[s] >= 0;
+    float gT[3] = {0.f, 0.f, 0.f}, dC[3] = {0.f, 0.f, 0.f}, dWx = 0.f;
+    if (valid) {
+      const float w = weights[s];
+      dC[0] = d_image[3 * p]; dC[1] = d_image[3 * p + 1]; dC[2] = d_image[3 * p + 2];
+      gT[0] = w * dC[0]; gT[1] = w * dC[1]; gT[2] = w * dC[2];
+      if (d_textures) {
+        gT[0] += d_textures[3 * s]; gT[1] += d_textures[3 * s + 1]; gT[2] += d_textures[3 * s + 2];
+      }
+      if (d_weights) dWx = d_weights[s];
+    }
+    // stage X (cached BF16 features of this row; zero beyond the rows) and d3
+#pragma unroll
+    for (int c8 = 0; c8 < IN / 8; ++c8) {
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (r < n_rows) q = reinterpret_cast<const uint4*>(feat + (size_t)r * (IN / 2))[c8];
+      *reinterpret_cast<uint4*>(act + cm_off(tid, 8 * c8, Lt::SA)) = q;
+    }
+    {
+      const float d3[8] = {gT[0], gT[1], gT[2], 0.f, 0.f, 0.f, 0.f, 0.f};
+      st8(del, tid, HL, Lt::SD, d3);
+    }
+    sync_to_mma();
+    // R1: h1 = X W1^T -> t0
+    if (tid == 0) {
+#pragma unroll
+      for (int kk = 0; kk < IN / 16; ++kk)
+        mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
+            sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0), kk > 0);
+      commit(&s_bar);
+    }
+    ok = wait_bar(&s_bar, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint64_t m1 = 0, m2 = 0;  // ReLU masks of h1, h2
+    float hl[HL];             // last hidden layer (FP32), for T
+#pragma unroll
+    for (int c16 = 0; c16 < H1 / 16; ++c16) {
+      float v[16];
+      tmem_ld16(t0 + lane_base + 16 * c16, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (v[i] > 0.f) m1 |= 1ull << (16 * c16 + i);
+        v[i] = fmaxf(v[i], 0.f);
+        if (H2 == 0) hl[16 * c16 + i] = v[i];
+      }
+      st8(act, tid, IN + 16 * c16, Lt::SA, v);
+      st8(act, tid, IN + 16 * c16 + 8, Lt::SA, v + 8);
+    }
+    if constexpr (H2 > 0) {
+      sync_to_mma();
+      // R2: h2 = h1 W2^T -> t0
+      if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < H1 / 16; ++kk)
+          mma(t0, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
+              sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0), kk > 0);
+        commit(&s_bar);
+      }
+      ok = ok && wait_bar(&s_bar, phase);
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c16 = 0; c16 < H2 / 16; ++c16) {
+        float v[16];
+        tmem_ld16(t0 + lane_base + 16 * c16, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          if (v[i] > 0.f) m2 |= 1ull << (16 * c16 + i);
+          v[i] = fmaxf(v[i], 0.f);
+          hl[16 * c16 + i] = v[i];
+        }
+        st8(act, tid, IN + H1 + 16 * c16, Lt::SA, v);
+        st8(act, tid, IN + H1 + 16 * c16 + 8, Lt::SA, v + 8);
+      }
+    }
+    // texture T = W3 h_last, dL/dW_j, and d_last = (W3^T d3) * [h_last > 0]
+    {
+      const uint64_t ml = H2 > 0 ? m2 : m1;
+      float T0 = 0.f, T1 = 0.f, T2 = 0.f;
+#pragma unroll
+      for (int i = 0; i < HL; ++i) {
+        T0 = fmaf(w3s[i], hl[i], T0);
+        T1 = fmaf(w3s[HL + i], hl[i], T1);
+        T2 = fmaf(w3s[2 * HL + i], hl[i], T2);
+      }
+      if (in_pix) dweff[s] = valid ? T0 * dC[0] + T1 * dC[1] + T2 * dC[2] + dWx : 0.f;
+#pragma unroll
+      for (int c8 = 0; c8 < HL / 8; ++c8) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int q = 8 * c8 + i;
+          const float g = gT[0] * w3s[q] + gT[1] * w3s[HL + q] + gT[2] * w3s[2 * HL + q];
+          v[i] = ((ml >> q) & 1ull) ? g : 0.f;
+        }
+        st8(del, tid, 8 * c8, Lt::SD, v);
+      }
+    }
+    if constexpr (H2 > 0) {
+      sync_to_mma();
+      // R3: d1 = (d2 W2) * [h1 > 0]; d2 is the delta tile's first H2 features
+      if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < H2 / 16; ++kk)
+          mma(t0, sdesc(sb + Lt::del + kk * 256, 128, Lt::SD),
+              sdesc(sb + Lt::w2t + kk * 256, 128, H2 / 8 * 128), idesc(128, H1, 0, 0), kk > 0);
+        commit(&s_bar);
+      }
+      ok = ok && wait_bar(&s_bar, phase);
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c16 = 0; c16 < H1 / 16; ++c16) {
+        float v[16];
+        tmem_ld16(t0 + lane_base + 16 * c16, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = ((m1 >> (16 * c16 + i)) & 1ull) ? v[i] : 0.f;
+        st8(del, tid, Lt::D1 + 16 * c16, Lt::SD, v);
+        st8(del, tid, Lt::D1 + 16 * c16 + 8, Lt::SD, v + 8);
+      }
+    }
+    sync_to_mma();
+    // R4: feature gradient d1 W1 -> t0; weight gradients into Da, Db
+    if (tid == 0) {
+#pragma unroll
+      for (int kk = 0; kk < H1 / 16; ++kk)
+        mma(t0, sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 256, 128, Lt::SD),
+            sdesc(sb + Lt::w1t + kk * 256, 128, H1 / 8 * 128), idesc(128, IN, 0, 0), kk > 0);
+      // K = rows: 16 rows = two 8-row groups per MMA
+#pragma unroll
+      for (int kk = 0; kk < kTcRows / 16; ++kk) {
+        const bool acc = !(first && kk == 0);
+        mma(t_da, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 2 * Lt::SA, Lt::SA, 128),
+            sdesc(sb + Lt::del + kk * 2 * Lt::SD, Lt::SD, 128), idesc(128, HL + 16, 1, 1), acc);
+        mma(t_db, sdesc(sb + Lt::act + kk * 2 * Lt::SA, Lt::SA, 128),
+            sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 2 * Lt::SD, Lt::SD, 128),
+            idesc(128, H1, 1, 1), acc);
+      }
+      commit(&s_bar);
+    }
+    ok = ok && wait_bar(&s_bar, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    first = false;
+    {
+      // feature gradient, level-major float2 per level
+      const long long R = gin_stride(n_rows);
+#pragma unroll
+      for (int c16 = 0; c16 < IN / 16; ++c16) {
+        float v[16];
+        tmem_ld16(t0 + lane_base + 16 * c16, v);
+        if (r < n_rows) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) gin[(long long)(8 * c16 + i) * R + r] = make_float2(v[2 * i], v[2 * i + 1]);
+        }
+      }
+    }
+    // the next tile's staging overwrites the operand tiles: the MMAs that
+    // read them have completed (the wait above).  A wait that ran out on any
+    // thread ends the loop for the whole CTA.
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok) != 0;
+  }
+  // weight gradients of this CTA: Da lane m = activation feature IN + m,
+  // column n = delta feature n; Db lane m = activation feature m, column
+  // n = d1 feature n
+  if (!first && ok && d_mlp) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float* dW1 = d_mlp;
+    float* dW2 = d_mlp + H1 * IN;
+    float* dW3 = dW2 + H2 * H1;
+    for (int c16 = 0; c16 < (HL + 16) / 16; ++c16) {
+      float v[16];
+      tmem_ld16(t_da + lane_base + 16 * c16, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int n = 16 * c16 + i, m = tid;
+        if (H2 > 0) {
+          if (m < H1 && n < H2) atomicAdd(dW2 + n * H1 + m, v[i]);              // dW2[o=n][i=m]
+          if (m >= H1 && m < H1 + H2 && n >= HL && n < HL + 3)
+            atomicAdd(dW3 + (n - HL) * HL + (m - H1), v[i]);                     // dW3[o][i]
+        } else {
+          if (m < H1 && n >= HL && n < HL + 3) atomicAdd(dW3 + (n - HL) * HL + m, v[i]);
+        }
+      }
+    }
+    for (int c16 = 0; c16 < H1 / 16; ++c16) {
+      float v[16];
+      tmem_ld16(t_db + lane_base + 16 * c16, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (tid < IN) atomicAdd(dW1 + (16 * c16 + i) * IN + tid, v[i]);         // dW1[o][i]
+    }
+  }
+  if (!ok && tid == 0 && status) atomicExch(status, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
+template <int IN, int H1, int H2>
+cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const float* w,
+                       const uint32_t* feat, const float* weights, const int* ids,
+                       const float* d_image, const float* d_weights, const float* d_textures,
+                       float* dweff, float2* gin, float* d_mlp, int* status, cudaStream_t st) {
+  using Lt = TcLayout<IN, H1, H2>;
+  int log2KP = 0;
+  while ((1 << log2KP) < KP) ++log2KP;
+  const long long n_tiles = (n_rows + kTcRows - 1) / kTcRows;
+  if (n_tiles == 0) return cudaSuccess;
+  auto kern = k_tex_bwd_tc<IN, H1, H2>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::total);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<long long>(n_tiles, 2LL * nsm);
+  NEXEL_PROF("texture_bwd_tc", st);
+  kern<<<grid, kTcThreads, Lt::total, st>>>(c, K, log2KP, n_rows, n_tiles, w, feat, weights, ids,
+                                            d_image, d_weights, d_textures, dweff, gin, d_mlp,
+                                            status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_arch_supported(int in, int h1, int h2) {
+  return (in == 16 && h1 == 64 && h2 == 0) || (in == 32 && h1 == 64 && h2 == 64);
+}
+
+cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
+                                  int h2, const float* w, const uint32_t* feat,
+                                  const float* weights, const int* ids, const float* d_image,
+                                  const float* d_weights, const float* d_textures, float* dweff,
+                                  float2* gin, float* d_mlp, int* status, cudaStream_t st) {
+  if (in == 16 && h1 == 64 && h2 == 0)
+    return tex_bwd_tc<16, 64, 0>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights,
+                                 d_textures, dweff, gin, d_mlp, status, st);
+  if (in == 32 && h1 == 64 && h2 == 64)
+    return tex_bwd_tc<32, 64, 64>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights,
+                                  d_textures, dweff, gin, d_mlp, status, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nexel
