@@ -302,7 +302,7 @@ int nexel_render_fwd(const nexel_camera* cam, const nexel_settings* settings,
     return cuda_status(cudaGetLastError());
   }
   e = launch_texture_fwd(c, *settings, *field, notex, weights, ids, depths, T_final, image,
-                         textures, feat_cache, st);
+                         textures, feat_cache, (int*)(w + L.counters + 32), st);
   return cuda_status(e);
 }
 

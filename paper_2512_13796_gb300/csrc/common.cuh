@@ -181,7 +181,7 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
 cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                const float* notex, const float* weights, const int* ids,
                                const float* depths, const float* T_final, float* image,
-                               float* textures, void* feat_cache, cudaStream_t st);
+                               float* textures, void* feat_cache, int* status, cudaStream_t st);
 // feat_cached: the forward left the features in bws (no gather here).
 cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                char* bws, const BwdLayout& B, const float* weights, const int* ids,

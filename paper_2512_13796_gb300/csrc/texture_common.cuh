@@ -215,6 +215,13 @@ cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_ro
                                   const float* d_weights, const float* d_textures, float* dweff,
                                   float2* gin, float* d_mlp, int* status, cudaStream_t st);
 
+// tcgen05 texturing forward (texture_tc.cu); writes the features to fd.feat
+// when fd.feat_mode == 1.
+cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, const nexel_field& f,
+                                  const FieldDev& fd, const float* notex, const float* weights,
+                                  const int* ids, const float* depths, const float* T_final,
+                                  float* image, float* textures, int* status, cudaStream_t st);
+
 // BF16 tensor-core texturing (texture_bf16.cu).
 bool bf16_arch_supported(const nexel_field& f);
 cudaError_t launch_texture_fwd_bf16(const DevCam& c, const nexel_settings& s, const nexel_field& f,

@@ -125,6 +125,28 @@ __device__ __forceinline__ void st8(unsigned char* base, int r, int f0, int sg, 
   *reinterpret_cast<uint4*>(base + cm_off(r, f0, sg)) = q;
 }
 
+// Down-weighted trilinear hash-grid feature pair of level l at x (Eqs. 3-4).
+template <typename TT>
+__device__ __forceinline__ float2 level_feature_tc(const FieldDev& f, int l, float3 x, float t) {
+  const TT* tl = reinterpret_cast<const TT*>(f.table) + (size_t)l * ((size_t)f.mask + 1) * 2;
+  const float s = f.s[l];
+  const float gx = s * x.x, gy = s * x.y, gz = s * x.z;
+  const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+  const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
+  const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
+  float ax = 0.f, ay = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+    const float w = (dx ? rx : 1.f - rx) * (dy ? ry : 1.f - ry) * (dz ? rz : 1.f - rz);
+    const float2 e = load_entry<TT>(tl, hash3(cx + dx, cy + dy, cz + dz, f.mask));
+    ax = fmaf(w, e.x, ax);
+    ay = fmaf(w, e.y, ay);
+  }
+  const float dw = downweight(f.focal, s, t);
+  return make_float2(dw * ax, dw * ay);
+}
+
 template <int IN, int H1, int H2>
 struct TcLayout {
   static constexpr int HL = H2 > 0 ? H2 : H1;
@@ -227,11 +249,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       }
       if (d_weights) dWx = d_weights[s];
     }
-    // stage X (cached BF16 features of this row; zero beyond the rows) and d3
+    // stage X (cached BF16 features of this row; zero beyond the pixels) and d3
 #pragma unroll
     for (int c8 = 0; c8 < IN / 8; ++c8) {
       uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (r < n_rows) q = reinterpret_cast<const uint4*>(feat + (size_t)r * (IN / 2))[c8];
+      if (r < n_rows && p < P) q = reinterpret_cast<const uint4*>(feat + (size_t)r * (IN / 2))[c8];
       *reinterpret_cast<uint4*>(act + cm_off(tid, 8 * c8, Lt::SA)) = q;
     }
     {
@@ -441,6 +463,237 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- forward
+// Texturing forward on tcgen05 (Eqs. 3-4 and the composite of Eq. 6).  A
+// CTA of 256 threads owns 128-row tiles (128 / KP pixels x KP slots).
+// Gather: thread t handles half t / 128 of the levels of one row; within a
+// warp the lanes are consecutive pixels of one slot, so at coarse levels
+// neighbouring lanes read the same table entries.  The down-weighted
+// features go to shared memory as the BF16 A operand (and, in a training
+// step, to the feature cache); then up to three MMA rounds (X W1^T,
+// h1 W2^T, h_last W3^T) with ReLU epilogues, the last one writing the
+// textures and the composite.  Epilogues split the columns between warps w
+// and w + 4 (which share TMEM lanes).
+template <int IN, int H1, int H2>
+struct TcFwdLayout {
+  static constexpr int HL = H2 > 0 ? H2 : H1;
+  static constexpr int FA = IN + H1 + H2;
+  static constexpr int SA = FA / 8 * 128;
+  static constexpr int act = 0;
+  static constexpr int w1 = act + kTcRows / 8 * SA;   // [H1][IN]
+  static constexpr int w2 = w1 + H1 * IN * 2;         // [H2][H1]
+  static constexpr int w3 = w2 + H2 * H1 * 2;         // [16][HL], rows 3.. zero
+  static constexpr int total = w3 + 16 * HL * 2;
+};
+
+constexpr int kTcFwdThreads = 256;
+constexpr int kTcFwdCols = 128;
+
+template <int IN, int H1, int H2, typename TT>
+__global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
+    DevCam c, FieldDev f, int K, int log2KP, long long n_tiles, float bg0, float bg1, float bg2,
+    const float* __restrict__ notex, const float* __restrict__ weights,
+    const int* __restrict__ ids, const float* __restrict__ depths,
+    const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures,
+    uint32_t* __restrict__ feat_cache, int* __restrict__ status) {
+  using Lt = TcFwdLayout<IN, H1, H2>;
+  constexpr int HL = Lt::HL;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* act = tc_smem + Lt::act;
+  {
+    const float* W1 = f.w;
+    const float* W2 = f.w + H1 * IN;
+    const float* W3 = W2 + H2 * H1;
+    for (int i = tid; i < H1 * IN; i += kTcFwdThreads)
+      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w1 + cm_off(i / IN, i % IN, IN / 8 * 128)) =
+          __float2bfloat16_rn(W1[i]);
+    for (int i = tid; i < H2 * H1; i += kTcFwdThreads)
+      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w2 + cm_off(i / H1, i % H1, H1 / 8 * 128)) =
+          __float2bfloat16_rn(W2[i]);
+    for (int i = tid; i < 16 * HL; i += kTcFwdThreads) {
+      const int o = i / HL, k = i % HL;
+      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w3 + cm_off(o, k, HL / 8 * 128)) =
+          __float2bfloat16_rn(o < 3 ? W3[o * HL + k] : 0.f);
+    }
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(kTcFwdCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  sync_to_mma();
+  const uint32_t tmem = s_tmem;
+  const uint32_t t0 = tmem, t1 = tmem + 64;
+  const uint32_t sb = smem_u32(tc_smem);
+  const int KP = 1 << log2KP, PPT = kTcRows >> log2KP;
+  const long long P = (long long)c.W * c.H;
+  // epilogue role: TMEM lanes 32 (warp % 4) .., column half warp / 4
+  const int erow = 32 * (warp & 3) + lane, ehalf = warp >> 2;
+  const uint32_t elane = (uint32_t)(32 * (warp & 3)) << 16;
+  // gather role: row (pixel tt % PPT, slot tt / PPT), levels of half gh
+  const int tt = tid & (kTcRows - 1), gh = tid >> 7;
+  const int grow = (tt % PPT) * KP + tt / PPT;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    {
+      const long long p = tile * PPT + tt % PPT;
+      const int j = tt / PPT;
+      const bool in_pix = p < P && j < K;
+      const long long s = p * K + j;
+      const bool valid = in_pix && ids[s] >= 0;
+      float3 x = make_float3(0.f, 0.f, 0.f);
+      float D = 1.f;
+      if (valid) {
+        D = depths[s];
+        const float3 d = pixel_dir(c, (int)(p % c.W), (int)(p / c.W));
+        x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
+      }
+      constexpr int LH = IN / 4;  // levels per half (F = 2)
+#pragma unroll
+      for (int g8 = 0; g8 < LH / 4; ++g8) {  // 4 levels = 8 features per store
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float2 e = make_float2(0.f, 0.f);
+          if (valid) e = level_feature_tc<TT>(f, gh * LH + 4 * g8 + q, x, D);
+          v[2 * q] = e.x;
+          v[2 * q + 1] = e.y;
+        }
+        const int f0 = gh * (IN / 2) + 8 * g8;
+        st8(act, grow, f0, Lt::SA, v);
+        if (feat_cache && p < P) {
+          const uint4 q4 = *reinterpret_cast<const uint4*>(act + cm_off(grow, f0, Lt::SA));
+          reinterpret_cast<uint4*>(feat_cache + (size_t)(tile * kTcRows + grow) * (IN / 2))[f0 / 8] = q4;
+        }
+      }
+    }
+    sync_to_mma();
+    if (tid == 0) {
+#pragma unroll
+      for (int kk = 0; kk < IN / 16; ++kk)
+        mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
+            sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0), kk > 0);
+      commit(&s_bar);
+    }
+    ok = wait_bar(&s_bar, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int c16 = 0; c16 < H1 / 32; ++c16) {
+      float v[16];
+      const int col = ehalf * (H1 / 2) + 16 * c16;
+      tmem_ld16(t0 + elane + col, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+      st8(act, erow, IN + col, Lt::SA, v);
+      st8(act, erow, IN + col + 8, Lt::SA, v + 8);
+    }
+    if constexpr (H2 > 0) {
+      sync_to_mma();
+      if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < H1 / 16; ++kk)
+          mma(t0, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
+              sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0), kk > 0);
+        commit(&s_bar);
+      }
+      ok = ok && wait_bar(&s_bar, phase);
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c16 = 0; c16 < H2 / 32; ++c16) {
+        float v[16];
+        const int col = ehalf * (H2 / 2) + 16 * c16;
+        tmem_ld16(t0 + elane + col, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+        st8(act, erow, IN + H1 + col, Lt::SA, v);
+        st8(act, erow, IN + H1 + col + 8, Lt::SA, v + 8);
+      }
+    }
+    sync_to_mma();
+    if (tid == 0) {
+#pragma unroll
+      for (int kk = 0; kk < HL / 16; ++kk)
+        mma(t1, sdesc(sb + Lt::act + ((IN + H1 + H2 - HL) / 8) * 128 + kk * 256, 128, Lt::SA),
+            sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, 16, 0, 0), kk > 0);
+      commit(&s_bar);
+    }
+    ok = ok && wait_bar(&s_bar, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ehalf == 0) {
+      float v[16];
+      tmem_ld16(t1 + elane, v);
+      const long long p = tile * PPT + erow / KP;
+      const int j = erow & (KP - 1);
+      const bool in_pix = p < P && j < K;
+      const long long s = p * K + j;
+      float wj = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
+      if (in_pix) {
+        if (ids[s] >= 0) {
+          wj = weights[s];
+          T0 = v[0]; T1 = v[1]; T2 = v[2];
+        }
+        textures[3 * s] = T0; textures[3 * s + 1] = T1; textures[3 * s + 2] = T2;
+      }
+      float c0 = wj * T0, c1 = wj * T1, c2 = wj * T2;
+      for (int dd = 1; dd < KP; dd <<= 1) {
+        c0 += __shfl_xor_sync(0xffffffffu, c0, dd);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, dd);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, dd);
+      }
+      if (j == 0 && p < P) {
+        const float Tf = T_final[p];
+        image[3 * p] = notex[3 * p] + c0 + Tf * bg0;
+        image[3 * p + 1] = notex[3 * p + 1] + c1 + Tf * bg1;
+        image[3 * p + 2] = notex[3 * p + 2] + c2 + Tf * bg2;
+      }
+    }
+    // the next tile's gather overwrites the operand tile
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok) != 0;
+  }
+  if (!ok && tid == 0 && status) atomicExch(status, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcFwdCols));
+}
+
+template <int IN, int H1, int H2, typename TT>
+cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev& fd,
+                       const float* notex, const float* weights, const int* ids,
+                       const float* depths, const float* T_final, float* image, float* textures,
+                       int* status, cudaStream_t st) {
+  using Lt = TcFwdLayout<IN, H1, H2>;
+  int log2KP = 0;
+  while ((1 << log2KP) < s.K) ++log2KP;
+  const long long rows = (long long)c.W * c.H << log2KP;
+  const long long n_tiles = (rows + kTcRows - 1) / kTcRows;
+  if (n_tiles == 0) return cudaSuccess;
+  auto kern = k_tex_fwd_tc<IN, H1, H2, TT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::total);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<long long>(n_tiles, 3LL * nsm);
+  NEXEL_PROF("texture_fwd_tc", st);
+  kern<<<grid, kTcFwdThreads, Lt::total, st>>>(
+      c, fd, s.K, log2KP, n_tiles, s.bg[0], s.bg[1], s.bg[2], notex, weights, ids, depths, T_final,
+      image, textures, fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool tc_arch_supported(int in, int h1, int h2) {
@@ -458,6 +711,25 @@ cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_ro
   if (in == 32 && h1 == 64 && h2 == 64)
     return tex_bwd_tc<32, 64, 64>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights,
                                   d_textures, dweff, gin, d_mlp, status, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, const nexel_field& f,
+                                  const FieldDev& fd, const float* notex, const float* weights,
+                                  const int* ids, const float* depths, const float* T_final,
+                                  float* image, float* textures, int* status, cudaStream_t st) {
+  const bool h = s.grid_dtype == NEXEL_F16;
+  const int in = f.widths[0], h1 = f.widths[1], h2 = f.n_layers == 3 ? f.widths[2] : 0;
+  if (in == 16 && h1 == 64 && h2 == 0)
+    return h ? tex_fwd_tc<16, 64, 0, __half>(c, s, fd, notex, weights, ids, depths, T_final, image,
+                                             textures, status, st)
+             : tex_fwd_tc<16, 64, 0, float>(c, s, fd, notex, weights, ids, depths, T_final, image,
+                                            textures, status, st);
+  if (in == 32 && h1 == 64 && h2 == 64)
+    return h ? tex_fwd_tc<32, 64, 64, __half>(c, s, fd, notex, weights, ids, depths, T_final,
+                                              image, textures, status, st)
+             : tex_fwd_tc<32, 64, 64, float>(c, s, fd, notex, weights, ids, depths, T_final, image,
+                                             textures, status, st);
   return cudaErrorInvalidValue;
 }
 
