@@ -54,6 +54,31 @@ __device__ __forceinline__ float3 pixel_dir(const DevCam& c, int px, int py) {
                      c.R[2] * dx + c.R[5] * dy + c.R[8]);
 }
 
+// Raw table entry (the FP16 pair as its 32-bit pattern, or the FP32 pair)
+// and its conversion, so that many gathers can be in flight at once.
+template <typename TT>
+struct RawEntry;
+template <>
+struct RawEntry<__half> {
+  using T = uint32_t;
+  __device__ static T load(const __half* tl, uint32_t idx) {
+    return __ldg(reinterpret_cast<const unsigned int*>(tl) + idx);
+  }
+  __device__ static float2 to2(T v) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&v));
+  }
+  __device__ static T zero() { return 0u; }
+};
+template <>
+struct RawEntry<float> {
+  using T = float2;
+  __device__ static T load(const float* tl, uint32_t idx) {
+    return __ldg(reinterpret_cast<const float2*>(tl) + idx);
+  }
+  __device__ static float2 to2(T v) { return v; }
+  __device__ static T zero() { return make_float2(0.f, 0.f); }
+};
+
 // Down-weighted hashed trilinear features of one point (level-major, F = 2).
 template <int IN, typename TT>
 __device__ __forceinline__ void hash_features(const FieldDev& f, float3 x, float t, float* feat) {

@@ -125,6 +125,46 @@ __device__ __forceinline__ void st8(unsigned char* base, int r, int f0, int sg, 
   *reinterpret_cast<uint4*>(base + cm_off(r, f0, sg)) = q;
 }
 
+// Features of levels l0 .. l0 + 3 at x (Eqs. 3-4): all 32 corner loads are
+// issued before any is used.
+template <typename TT>
+__device__ __forceinline__ void gather4_tc(const FieldDev& f, int l0, float3 x, float t, bool valid,
+                                           float (&v)[8]) {
+  using R = RawEntry<TT>;
+  typename R::T e[4][8];
+  float fr[4][3], dw[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int l = l0 + q;
+    const TT* tl = reinterpret_cast<const TT*>(f.table) + (size_t)l * ((size_t)f.mask + 1) * 2;
+    const float s = f.s[l];
+    const float gx = s * x.x, gy = s * x.y, gz = s * x.z;
+    const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+    const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
+    fr[q][0] = gx - fx0; fr[q][1] = gy - fy0; fr[q][2] = gz - fz0;
+    dw[q] = downweight(f.focal, s, t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      e[q][k] = valid ? R::load(tl, hash3(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1), f.mask))
+                      : R::zero();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float rx = fr[q][0], ry = fr[q][1], rz = fr[q][2];
+    float ax = 0.f, ay = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+      const float w = (dx ? rx : 1.f - rx) * (dy ? ry : 1.f - ry) * (dz ? rz : 1.f - rz);
+      const float2 ee = R::to2(e[q][k]);
+      ax = fmaf(w, ee.x, ax);
+      ay = fmaf(w, ee.y, ay);
+    }
+    v[2 * q] = valid ? dw[q] * ax : 0.f;
+    v[2 * q + 1] = valid ? dw[q] * ay : 0.f;
+  }
+}
+
 // Down-weighted trilinear hash-grid feature pair of level l at x (Eqs. 3-4).
 template <typename TT>
 __device__ __forceinline__ float2 level_feature_tc(const FieldDev& f, int l, float3 x, float t) {
@@ -232,30 +272,55 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   const long long P = (long long)c.W * c.H;
   const int KP = 1 << log2KP;
 
-  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+  // per-row inputs of a tile; the next tile's are loaded while this one's
+  // MMA rounds run
+  struct RowIn {
+    uint4 x[IN / 8];
+    float gT[3], dC[3], dWx;
+    long long s;
+    bool valid, in_pix;
+  };
+  auto load_row = [&](long long tile, RowIn& in) {
     const long long r = tile * kTcRows + tid;
     const long long p = r >> log2KP;
     const int j = (int)(r & (KP - 1));
-    const long long s = p * K + j;
-    const bool in_pix = r < n_rows && p < P && j < K;
-    const bool valid = in_pix && ids[s] >= 0;
-    float gT[3] = {0.f, 0.f, 0.f}, dC[3] = {0.f, 0.f, 0.f}, dWx = 0.f;
-    if (valid) {
-      const float w = weights[s];
-      dC[0] = d_image[3 * p]; dC[1] = d_image[3 * p + 1]; dC[2] = d_image[3 * p + 2];
-      gT[0] = w * dC[0]; gT[1] = w * dC[1]; gT[2] = w * dC[2];
+    in.s = p * K + j;
+    in.in_pix = tile < n_tiles && r < n_rows && p < P && j < K;
+    in.valid = in.in_pix && ids[in.s] >= 0;
+    in.gT[0] = in.gT[1] = in.gT[2] = in.dC[0] = in.dC[1] = in.dC[2] = in.dWx = 0.f;
+    if (in.valid) {
+      const float w = weights[in.s];
+      in.dC[0] = d_image[3 * p]; in.dC[1] = d_image[3 * p + 1]; in.dC[2] = d_image[3 * p + 2];
+      in.gT[0] = w * in.dC[0]; in.gT[1] = w * in.dC[1]; in.gT[2] = w * in.dC[2];
       if (d_textures) {
-        gT[0] += d_textures[3 * s]; gT[1] += d_textures[3 * s + 1]; gT[2] += d_textures[3 * s + 2];
+        in.gT[0] += d_textures[3 * in.s];
+        in.gT[1] += d_textures[3 * in.s + 1];
+        in.gT[2] += d_textures[3 * in.s + 2];
       }
-      if (d_weights) dWx = d_weights[s];
+      if (d_weights) in.dWx = d_weights[in.s];
     }
-    // stage X (cached BF16 features of this row; zero beyond the pixels) and d3
+    // cached BF16 features of this row; zero beyond the pixels
 #pragma unroll
     for (int c8 = 0; c8 < IN / 8; ++c8) {
-      uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (r < n_rows && p < P) q = reinterpret_cast<const uint4*>(feat + (size_t)r * (IN / 2))[c8];
-      *reinterpret_cast<uint4*>(act + cm_off(tid, 8 * c8, Lt::SA)) = q;
+      in.x[c8] = make_uint4(0u, 0u, 0u, 0u);
+      if (tile < n_tiles && r < n_rows && p < P)
+        in.x[c8] = reinterpret_cast<const uint4*>(feat + (size_t)r * (IN / 2))[c8];
     }
+  };
+  RowIn nxt;
+  load_row(blockIdx.x, nxt);
+  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const long long r = tile * kTcRows + tid;
+    const RowIn cur = nxt;
+    const long long s = cur.s;
+    const bool in_pix = cur.in_pix, valid = cur.valid;
+    const float gT[3] = {cur.gT[0], cur.gT[1], cur.gT[2]};
+    const float dC[3] = {cur.dC[0], cur.dC[1], cur.dC[2]};
+    const float dWx = cur.dWx;
+    // stage X and d3
+#pragma unroll
+    for (int c8 = 0; c8 < IN / 8; ++c8)
+      *reinterpret_cast<uint4*>(act + cm_off(tid, 8 * c8, Lt::SA)) = cur.x[c8];
     {
       const float d3[8] = {gT[0], gT[1], gT[2], 0.f, 0.f, 0.f, 0.f, 0.f};
       st8(del, tid, HL, Lt::SD, d3);
@@ -269,11 +334,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
             sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0), kk > 0);
       commit(&s_bar);
     }
+    load_row(tile + gridDim.x, nxt);
     ok = wait_bar(&s_bar, phase);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     uint64_t m1 = 0, m2 = 0;  // ReLU masks of h1, h2
-    float hl[HL];             // last hidden layer (FP32), for T
 #pragma unroll
     for (int c16 = 0; c16 < H1 / 16; ++c16) {
       float v[16];
@@ -282,7 +347,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       for (int i = 0; i < 16; ++i) {
         if (v[i] > 0.f) m1 |= 1ull << (16 * c16 + i);
         v[i] = fmaxf(v[i], 0.f);
-        if (H2 == 0) hl[16 * c16 + i] = v[i];
       }
       st8(act, tid, IN + 16 * c16, Lt::SA, v);
       st8(act, tid, IN + 16 * c16 + 8, Lt::SA, v + 8);
@@ -308,7 +372,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         for (int i = 0; i < 16; ++i) {
           if (v[i] > 0.f) m2 |= 1ull << (16 * c16 + i);
           v[i] = fmaxf(v[i], 0.f);
-          hl[16 * c16 + i] = v[i];
         }
         st8(act, tid, IN + H1 + 16 * c16, Lt::SA, v);
         st8(act, tid, IN + H1 + 16 * c16 + 8, Lt::SA, v + 8);
@@ -317,25 +380,41 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     // texture T = W3 h_last, dL/dW_j, and d_last = (W3^T d3) * [h_last > 0]
     {
       const uint64_t ml = H2 > 0 ? m2 : m1;
+      const float4* w34 = reinterpret_cast<const float4*>(w3s);
       float T0 = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < HL; ++i) {
-        T0 = fmaf(w3s[i], hl[i], T0);
-        T1 = fmaf(w3s[HL + i], hl[i], T1);
-        T2 = fmaf(w3s[2 * HL + i], hl[i], T2);
-      }
-      if (in_pix) dweff[s] = valid ? T0 * dC[0] + T1 * dC[1] + T2 * dC[2] + dWx : 0.f;
-#pragma unroll
       for (int c8 = 0; c8 < HL / 8; ++c8) {
+        float wr[3][8];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          const float4 a = w34[(o * HL + 8 * c8) / 4], b = w34[(o * HL + 8 * c8) / 4 + 1];
+          wr[o][0] = a.x; wr[o][1] = a.y; wr[o][2] = a.z; wr[o][3] = a.w;
+          wr[o][4] = b.x; wr[o][5] = b.y; wr[o][6] = b.z; wr[o][7] = b.w;
+        }
+        // the last hidden layer of this row, as stored (BF16)
+        const uint4 hq = *reinterpret_cast<const uint4*>(act + cm_off(tid, IN + H1 + H2 - HL + 8 * c8, Lt::SA));
+        const uint32_t hw[4] = {hq.x, hq.y, hq.z, hq.w};
+        float hv[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float2 h2v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hw[i]));
+          hv[2 * i] = h2v.x;
+          hv[2 * i + 1] = h2v.y;
+        }
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int q = 8 * c8 + i;
-          const float g = gT[0] * w3s[q] + gT[1] * w3s[HL + q] + gT[2] * w3s[2 * HL + q];
+          const float hlq = hv[i];
+          T0 = fmaf(wr[0][i], hlq, T0);
+          T1 = fmaf(wr[1][i], hlq, T1);
+          T2 = fmaf(wr[2][i], hlq, T2);
+          const float g = fmaf(gT[0], wr[0][i], fmaf(gT[1], wr[1][i], gT[2] * wr[2][i]));
           v[i] = ((ml >> q) & 1ull) ? g : 0.f;
         }
         st8(del, tid, 8 * c8, Lt::SD, v);
       }
+      if (in_pix) dweff[s] = valid ? T0 * dC[0] + T1 * dC[1] + T2 * dC[2] + dWx : 0.f;
     }
     if constexpr (H2 > 0) {
       sync_to_mma();
@@ -368,7 +447,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         mma(t0, sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 256, 128, Lt::SD),
             sdesc(sb + Lt::w1t + kk * 256, 128, H1 / 8 * 128), idesc(128, IN, 0, 0), kk > 0);
       // K = rows: 16 rows = two 8-row groups per MMA
-#pragma unroll
+#pragma unroll 1
       for (int kk = 0; kk < kTcRows / 16; ++kk) {
         const bool acc = !(first && kk == 0);
         mma(t_da, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 2 * Lt::SA, Lt::SA, 128),
@@ -561,13 +640,7 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
 #pragma unroll
       for (int g8 = 0; g8 < LH / 4; ++g8) {  // 4 levels = 8 features per store
         float v[8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float2 e = make_float2(0.f, 0.f);
-          if (valid) e = level_feature_tc<TT>(f, gh * LH + 4 * g8 + q, x, D);
-          v[2 * q] = e.x;
-          v[2 * q + 1] = e.y;
-        }
+        gather4_tc<TT>(f, gh * LH + 4 * g8, x, D, valid, v);
         const int f0 = gh * (IN / 2) + 8 * g8;
         st8(act, grow, f0, Lt::SA, v);
         if (feat_cache && p < P) {
