@@ -26,7 +26,7 @@ namespace nexel {
 namespace {
 
 constexpr int kHbThreads = 256;
-constexpr int kHbMinBlocks = 4;
+constexpr int kHbMinBlocks = 5;
 
 // Inclusive segmented scan of (vx, vy) over the lanes; seg_start is the
 // first lane of the calling lane's segment, max_len (warp-uniform) the
@@ -77,14 +77,8 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
   // pixel groups start at successive levels; the KP warps of a group move
   // together
   int l = (int)((gw >> log2KP) % (uint32_t)L);
-  using Raw = RawEntry<TT>;
-  float2 g_next = valid ? gin[(size_t)l * R + r] : make_float2(0.f, 0.f);
   for (int it = 0; it < L; ++it, l = (l + 1 == L) ? 0 : l + 1) {
-    const float2 g = g_next;
-    {  // the next level's feature gradient, in flight during this level
-      const int ln = (l + 1 == L) ? 0 : l + 1;
-      if (valid && it + 1 < L) g_next = gin[(size_t)ln * R + r];
-    }
+    const float2 g = valid ? gin[(size_t)l * R + r] : make_float2(0.f, 0.f);
     const float sl = f.s[l];
     const float gx = sl * x.x, gy = sl * x.y, gz = sl * x.z;
     const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
@@ -120,12 +114,23 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     const int max_len = (int)__reduce_max_sync(0xffffffffu, (unsigned)(lane - seg_start)) + 1;
     const bool tail = !scan || !same_next;
     const float gsx = dw * g.x, gsy = dw * g.y;
-    // the 8 corner entries (for dL/dD), in flight during the table scatter
-    typename Raw::T ev[8];
+    float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-      ev[k] = valid ? Raw::load(tl, (hx[k & 1] ^ hy[(k >> 1) & 1] ^ hz[(k >> 2) & 1]) & f.mask)
-                    : Raw::zero();
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+      const uint32_t idx = (hx[dx] ^ hy[dy] ^ hz[dz]) & f.mask;
+      const float wyz = wy[dy] * wz[dz], wxz = wx[dx] * wz[dz], wxy = wx[dx] * wy[dy];
+      const float w = wxy * wz[dz];
+      if (valid) {
+        const float2 e = load_entry<TT>(tl, idx);
+        ax = fmaf(w, e.x, ax);
+        ay = fmaf(w, e.y, ay);
+        const float ge = fmaf(g.x, e.x, g.y * e.y);
+        qx = fmaf(ge, dx ? wyz : -wyz, qx);
+        qy = fmaf(ge, dy ? wxz : -wxz, qy);
+        qz = fmaf(ge, dz ? wxy : -wxy, qz);
+      }
+    }
     if (dl) {
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {  // (dy, dz) pairs: entries at x and x + 1
@@ -148,20 +153,6 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
           if (!adj_next) atomicAdd(dl + ((hx[1] ^ hyz) & f.mask), make_float2(v1x, v1y));
         }
       }
-    }
-    float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-      const float wyz = wy[dy] * wz[dz], wxz = wx[dx] * wz[dz], wxy = wx[dx] * wy[dy];
-      const float w = wxy * wz[dz];
-      const float2 e = Raw::to2(ev[k]);
-      ax = fmaf(w, e.x, ax);
-      ay = fmaf(w, e.y, ay);
-      const float ge = fmaf(g.x, e.x, g.y * e.y);
-      qx = fmaf(ge, dx ? wyz : -wyz, qx);
-      qy = fmaf(ge, dy ? wxz : -wxz, qy);
-      qz = fmaf(ge, dz ? wxy : -wxy, qz);
     }
     // Delta = 1 - exp(-r^2 / 2pi), r = f / (s D): dDelta/dD = -(1 - Delta) r^2 / (pi D)
     const float ddw = -(1.f - dw) * rr * rr * 0.3183098861837907f * iD;

@@ -47,14 +47,9 @@ cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const n
   FieldDev fd = make_fielddev(c, f);
   fd.feat = feat_cache;
   fd.feat_mode = feat_cache ? 1 : 0;
-  if (s.mlp_dtype == NEXEL_BF16) {
-    const int h2 = f.n_layers == 3 ? f.widths[2] : 0;
-    if (tc_arch_supported(f.widths[0], f.widths[1], h2))
-      return launch_texture_fwd_tc(c, s, f, fd, notex, weights, ids, depths, T_final, image,
-                                   textures, status, st);
-    return launch_texture_fwd_bf16(c, s, f, fd, notex, weights, ids, depths, T_final, image,
-                                   textures, st);
-  }
+  if (s.mlp_dtype == NEXEL_BF16)
+    return launch_texture_fwd_tc(c, s, f, fd, notex, weights, ids, depths, T_final, image,
+                                 textures, status, st);
 #define X(a, b, cc)                                                                                \
   if (arch_match(f, a, b, cc))                                                                     \
     return tex_fwd_f32<a, b, cc, float>(c, s, fd, notex, weights, ids, depths, T_final, image, \

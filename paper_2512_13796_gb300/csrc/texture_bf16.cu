@@ -1,6 +1,7 @@
-// BF16 tensor-core form of the texturing pass: forward, input-gradient
-// backward (the hash-table scatter follows in hash_bwd.cu), and the MLP
-// weight-gradient GEMMs.
+// BF16 mma.sync form of the texturing backward for a step without cached
+// features: input-gradient backward with a fresh gather (the hash-table
+// scatter follows in hash_bwd.cu) and the MLP weight-gradient GEMMs.  The
+// forward and the cached-feature backward run on tcgen05 (texture_tc.cu).
 // FP32 accumulation everywhere; the table is read as FP16 or FP32.
 #include "texture_bf16.cuh"
 
@@ -80,70 +81,6 @@ __device__ __forceinline__ void mlp_fwd_bf16(const __nv_bfloat16* sw, int g, int
     layer<H2, 8>(a3, sw + B::o3, B::s3, g, t, out);
   } else {
     layer<H1, 8>(a2, sw + B::o3, B::s3, g, t, out);
-  }
-}
-
-template <int IN, int H1, int H2, typename TT>
-__global__ void __launch_bounds__(kWarps * 32) k_tex_fwd_bf16(
-    DevCam c, FieldDev f, int K, int KP, long long n_tiles, float bg0, float bg1, float bg2,
-    const float* __restrict__ notex, const float* __restrict__ weights,
-    const int* __restrict__ ids, const float* __restrict__ depths,
-    const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures) {
-  extern __shared__ __align__(16) __nv_bfloat16 sw[];
-  load_weights_bf16<IN, H1, H2>(f.w, sw, false);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const long long P = (long long)c.W * c.H;
-  const float bg[3] = {bg0, bg1, bg2};
-  for (long long mt = (long long)blockIdx.x * kWarps + warp; mt < n_tiles;
-       mt += (long long)gridDim.x * kWarps) {
-    const long long rA = mt * 16 + g, rB = rA + 8;
-    const RowInfo A = row_info(c, P, K, KP, rA, ids, weights, depths);
-    const RowInfo B = row_info(c, P, K, KP, rB, ids, weights, depths);
-    uint32_t a1[IN / 16][4];
-    gather_frags<IN, TT>(f, A, B, t, a1);
-    if (f.feat_mode == 1) {  // training step: leave the features for the backward
-      uint32_t* fo = reinterpret_cast<uint32_t*>(f.feat);
-#pragma unroll
-      for (int kt = 0; kt < IN / 16; ++kt) {
-        fo[(rA * IN + 16 * kt + 2 * t) / 2] = a1[kt][0];
-        fo[(rB * IN + 16 * kt + 2 * t) / 2] = a1[kt][1];
-        fo[(rA * IN + 16 * kt + 8 + 2 * t) / 2] = a1[kt][2];
-        fo[(rB * IN + 16 * kt + 8 + 2 * t) / 2] = a1[kt][3];
-      }
-    }
-    uint32_t a2[H1 / 16][4], a3[(H2 > 0 ? H2 : 16) / 16][4];
-    float out[1][4];
-    mlp_fwd_bf16<IN, H1, H2>(sw, g, t, a1, a2, a3, out);
-    // lane t holds output columns 2t, 2t + 1 (channels 0..2 live in t = 0, 1)
-    if (t == 0) {
-      if (A.in_pix) { textures[3 * A.s] = out[0][0]; textures[3 * A.s + 1] = out[0][1]; }
-      if (B.in_pix) { textures[3 * B.s] = out[0][2]; textures[3 * B.s + 1] = out[0][3]; }
-    } else if (t == 1) {
-      if (A.in_pix) textures[3 * A.s + 2] = out[0][0];
-      if (B.in_pix) textures[3 * B.s + 2] = out[0][2];
-    }
-    float cA0 = A.w * out[0][0], cA1 = A.w * out[0][1];
-    float cB0 = B.w * out[0][2], cB1 = B.w * out[0][3];
-    for (int d = 1; d < KP; d <<= 1) {
-      cA0 += __shfl_xor_sync(0xffffffffu, cA0, 4 * d);
-      cA1 += __shfl_xor_sync(0xffffffffu, cA1, 4 * d);
-      cB0 += __shfl_xor_sync(0xffffffffu, cB0, 4 * d);
-      cB1 += __shfl_xor_sync(0xffffffffu, cB1, 4 * d);
-    }
-    if ((g % KP) == 0 && t < 2) {
-      const int ch0 = 2 * t;
-      if (A.p < P) {
-        const float Tf = T_final[A.p];
-        image[3 * A.p + ch0] = notex[3 * A.p + ch0] + cA0 + Tf * bg[ch0];
-        if (t == 0) image[3 * A.p + 1] = notex[3 * A.p + 1] + cA1 + Tf * bg[1];
-      }
-      if (B.p < P) {
-        const float Tf = T_final[B.p];
-        image[3 * B.p + ch0] = notex[3 * B.p + ch0] + cB0 + Tf * bg[ch0];
-        if (t == 0) image[3 * B.p + 1] = notex[3 * B.p + 1] + cB1 + Tf * bg[1];
-      }
-    }
   }
 }
 
@@ -491,27 +428,6 @@ static int sm_count() {
 }
 
 template <int IN, int H1, int H2, typename TT>
-static cudaError_t fwd_bf16(const DevCam& c, const nexel_settings& s, const FieldDev& fd,
-                            const float* notex, const float* weights, const int* ids,
-                            const float* depths, const float* T_final, float* image,
-                            float* textures, cudaStream_t st) {
-  int KP = 1;
-  while (KP < s.K) KP <<= 1;
-  const long long rows = (long long)c.W * c.H * KP;
-  const long long n_tiles = (rows + 15) / 16;
-  const size_t smem = sizeof(__nv_bfloat16) * Bf16W<IN, H1, H2>::fwd_elems;
-  auto kern = k_tex_fwd_bf16<IN, H1, H2, TT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const long long want = (n_tiles + kWarps - 1) / kWarps;
-  const unsigned grid = (unsigned)std::min<long long>(want, (long long)sm_count() * 16);
-  NEXEL_PROF("texture_fwd_bf16", st);
-  kern<<<grid, kWarps * 32, smem, st>>>(c, fd, s.K, KP, n_tiles, s.bg[0], s.bg[1], s.bg[2], notex,
-                                        weights, ids, depths, T_final, image, textures);
-  return cudaGetLastError();
-}
-
-template <int IN, int H1, int H2, typename TT>
 static cudaError_t bwd_bf16(const DevCam& c, const nexel_settings& s, const FieldDev& fd,
                             char* bws, const BwdLayout& B, const float* weights, const int* ids,
                             const float* depths, const float* d_image, const float* d_weights,
@@ -580,22 +496,6 @@ bool bf16_arch_supported(const nexel_field& f) {
   NEXEL_BF16_ARCHS(X)
 #undef X
   return false;
-}
-
-cudaError_t launch_texture_fwd_bf16(const DevCam& c, const nexel_settings& s, const nexel_field& f,
-                                    const FieldDev& fd, const float* notex, const float* weights,
-                                    const int* ids, const float* depths, const float* T_final,
-                                    float* image, float* textures, cudaStream_t st) {
-  const bool h = s.grid_dtype == NEXEL_F16;
-#define X(a, b, cc)                                                                            \
-  if (match(f, a, b, cc))                                                                      \
-    return h ? fwd_bf16<a, b, cc, __half>(c, s, fd, notex, weights, ids, depths, T_final,       \
-                                          image, textures, st)                                  \
-             : fwd_bf16<a, b, cc, float>(c, s, fd, notex, weights, ids, depths, T_final, image, \
-                                         textures, st);
-  NEXEL_BF16_ARCHS(X)
-#undef X
-  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_texture_bwd_bf16(const DevCam& c, const nexel_settings& s, const nexel_field& f,

@@ -249,10 +249,6 @@ cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, cons
 
 // BF16 tensor-core texturing (texture_bf16.cu).
 bool bf16_arch_supported(const nexel_field& f);
-cudaError_t launch_texture_fwd_bf16(const DevCam& c, const nexel_settings& s, const nexel_field& f,
-                                    const FieldDev& fd, const float* notex, const float* weights,
-                                    const int* ids, const float* depths, const float* T_final,
-                                    float* image, float* textures, cudaStream_t st);
 cudaError_t launch_texture_bwd_bf16(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                     const FieldDev& fd, char* bws, const BwdLayout& B,
                                     const float* weights, const int* ids, const float* depths,
