@@ -116,7 +116,8 @@ class Job:
         from paper_2512_13796_gb300 import render as R
         self.R = R
         self.precision = precision
-        grid, mlp = ("f16", "bf16") if precision == "bf16" else ("f32", "f32")
+        grid, mlp = {"bf16": ("f16", "bf16"), "f16": ("f16", "f16"),
+                     "f32": ("f32", "f32")}[precision]
         self.cam, self.st = w.cameras[0], w.settings
         self.cam_s = R.camera_struct(self.cam)
         self.st_s = R.settings_struct(self.st, grid, mlp)
@@ -330,7 +331,7 @@ def main():
     stream = torch.cuda.current_stream()
     peaks, peak_kind = load_peaks()
     w = synth.workload(args.config)
-    jobs = {"bf16": Job(w, dev, "bf16"), "f32": Job(w, dev, "f32")}
+    jobs = {"bf16": Job(w, dev, "bf16"), "f32": Job(w, dev, "f32"), "f16": Job(w, dev, "f16")}
     P = w.cameras[0].width * w.cameras[0].height
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -358,6 +359,8 @@ def main():
     results["f32_train"] = timed(jobs["f32"].step, args.steps, flush, stream)
     results["bf16_fwd"] = timed(jobs["bf16"].forward, args.steps, flush, stream)
     results["f32_fwd"] = timed(jobs["f32"].forward, args.steps, flush, stream)
+    results["f16_train"] = timed(jobs["f16"].step, args.steps, flush, stream)
+    results["f16_fwd"] = timed(jobs["f16"].forward, args.steps, flush, stream)
     barrier()
     clk = clocks.stop()  # samples over all four timed regions
     # per-kernel CUDA events on the launch stream, same steps again
@@ -432,6 +435,10 @@ def main():
                      "render_fps": 1e3 / ms["bf16_fwd"], "render_ms": ms["bf16_fwd"]},
             "f32": {"train_mpix_s": mpix(ms["f32_train"]), "train_ms": ms["f32_train"],
                     "render_fps": 1e3 / ms["f32_fwd"], "render_ms": ms["f32_fwd"]},
+            "f16_mlp_loss_scaled": {"train_mpix_s": mpix(ms["f16_train"]),
+                                    "train_ms": ms["f16_train"],
+                                    "render_fps": 1e3 / ms["f16_fwd"],
+                                    "render_ms": ms["f16_fwd"]},
         },
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items(),
                                                                         key=lambda kv: -kv[1][0])},

@@ -79,8 +79,11 @@ typedef struct {
  * take the transmittance below T_min.  K in 0..NEXEL_MAX_K is the number of
  * textured primitives per pixel (Sec. 4.2).  grid_dtype is the storage type
  * of the hash table (NEXEL_F32 or NEXEL_F16); mlp_dtype the arithmetic of
- * the MLP (NEXEL_F32: FP32 SIMT; NEXEL_BF16: BF16 tensor-core MMA with FP32
- * accumulation). */
+ * the MLP (NEXEL_F32: FP32 SIMT; NEXEL_BF16: BF16 operands on the tensor
+ * cores with FP32 accumulation; NEXEL_F16: FP16 operands with FP32
+ * accumulation, the backward scaling the gradient that enters the MLP by
+ * 128 and unscaling the results, as the paper trains).  The tensor-core
+ * forms support the MLPs 16 -> 64 -> 3 and 32 -> 64 -> 64 -> 3. */
 typedef struct {
   int K;
   float alpha_min, alpha_max, T_min;

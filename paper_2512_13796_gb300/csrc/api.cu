@@ -174,7 +174,7 @@ static bool settings_ok(const nexel_settings* s) {
   return s && s->K >= 0 && s->K <= NEXEL_MAX_K && s->alpha_min > 0.f && s->alpha_max > 0.f &&
          s->alpha_max <= 1.f && s->alpha_min <= s->alpha_max && s->T_min >= 0.f &&
          s->T_min < 1.f && (s->grid_dtype == NEXEL_F32 || s->grid_dtype == NEXEL_F16) &&
-         (s->mlp_dtype == NEXEL_F32 || s->mlp_dtype == NEXEL_BF16);
+         (s->mlp_dtype == NEXEL_F32 || s->mlp_dtype == NEXEL_BF16 || s->mlp_dtype == NEXEL_F16);
 }
 
 static bool field_ok(const nexel_field* f) {

@@ -1,6 +1,6 @@
 // Dispatch of the texturing pass over the supported MLP shapes and storage
-// types.  The FP32 kernels are in texture_f32.cuh, the BF16 tensor-core ones
-// in texture_bf16.cu.
+// types.  The FP32 kernels are in texture_f32.cuh, the BF16 / FP16
+// tensor-core (tcgen05) ones in texture_tc.cu.
 #include "texture_f32.cuh"
 
 namespace nexel {
@@ -32,7 +32,10 @@ static bool arch_match(const nexel_field& f, int in, int h1, int h2) {
 
 bool texture_arch_supported(const nexel_settings& s, const nexel_field& f) {
   if (f.F != 2 || f.L * f.F != f.widths[0]) return false;
-  if (s.mlp_dtype == NEXEL_BF16) return bf16_arch_supported(f);
+  if (s.mlp_dtype == NEXEL_BF16 || s.mlp_dtype == NEXEL_F16) {
+    const int h2 = f.n_layers == 3 ? f.widths[2] : 0;
+    return f.widths[f.n_layers] == 3 && tc_arch_supported(f.widths[0], f.widths[1], h2);
+  }
   if (s.grid_dtype != NEXEL_F32) return false;  // the FP32 form reads an FP32 table
 #define X(a, b, c) if (arch_match(f, a, b, c)) return true;
   NEXEL_ARCH_LIST(X)
@@ -47,7 +50,7 @@ cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const n
   FieldDev fd = make_fielddev(c, f);
   fd.feat = feat_cache;
   fd.feat_mode = feat_cache ? 1 : 0;
-  if (s.mlp_dtype == NEXEL_BF16)
+  if (s.mlp_dtype == NEXEL_BF16 || s.mlp_dtype == NEXEL_F16)
     return launch_texture_fwd_tc(c, s, f, fd, notex, weights, ids, depths, T_final, image,
                                  textures, status, st);
 #define X(a, b, cc)                                                                                \
@@ -67,9 +70,26 @@ cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const n
   FieldDev fd = make_fielddev(c, f);
   fd.feat = bws + B.feat;
   fd.feat_mode = feat_cached ? 2 : 0;
-  if (s.mlp_dtype == NEXEL_BF16)
-    return launch_texture_bwd_bf16(c, s, f, fd, bws, B, weights, ids, depths, d_image, d_weights,
-                                   d_textures, d_table, d_mlp, st);
+  if (s.mlp_dtype == NEXEL_BF16 || s.mlp_dtype == NEXEL_F16) {
+    // tcgen05 backward from the features (cached by the forward of a
+    // training step, else gathered again here), then the hash-grid backward
+    int KP = 1;
+    while (KP < s.K) KP <<= 1;
+    const long long n_rows = ((long long)c.W * c.H * KP + 15) / 16 * 16;
+    cudaError_t e = cudaSuccess;
+    if (!feat_cached)
+      e = launch_texture_gather_tc(c, s, f, fd, ids, depths, (uint32_t*)(bws + B.feat), st);
+    const int h2 = f.n_layers == 3 ? f.widths[2] : 0;
+    if (e == cudaSuccess)
+      e = launch_texture_bwd_tc(c, s.K, KP, n_rows, f.widths[0], f.widths[1], h2,
+                                s.mlp_dtype == NEXEL_F16, f.weights, (const uint32_t*)(bws + B.feat),
+                                weights, ids, d_image, d_weights, d_textures,
+                                (float*)(bws + B.dweff), (float2*)(bws + B.gin), d_mlp,
+                                (int*)(bws + B.status), st);
+    if (e != cudaSuccess) return e;
+    return launch_hash_bwd(c, fd, s.K, KP, n_rows, s.grid_dtype == NEXEL_F16, ids, depths,
+                           (const float2*)(bws + B.gin), (float*)(bws + B.ddepth), d_table, st);
+  }
 #define X(a, b, cc)                                                                          \
   if (arch_match(f, a, b, cc))                                                               \
     return tex_bwd_f32<a, b, cc, float>(c, s, fd, bws, B, weights, ids, depths, d_image,      \

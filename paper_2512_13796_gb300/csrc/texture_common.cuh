@@ -230,30 +230,23 @@ __device__ __forceinline__ void mlp_bwd_input_f32(const float* __restrict__ sW, 
   }
 }
 
-// tcgen05 texture-MLP backward from cached features (texture_tc.cu):
-// writes dweff, the level-major feature gradient and adds the MLP weight
-// gradients to d_mlp (may be null).
+// Texturing on tcgen05 (texture_tc.cu), BF16 or FP16 MMA operands
+// (s.mlp_dtype).  The forward writes the features to fd.feat when
+// fd.feat_mode == 1; the gather pass writes them for a backward without
+// cached features; the backward writes dweff and the level-major feature
+// gradient and adds the MLP weight gradients to d_mlp (may be null).
 bool tc_arch_supported(int in, int h1, int h2);
-cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
-                                  int h2, const float* w, const uint32_t* feat,
-                                  const float* weights, const int* ids, const float* d_image,
-                                  const float* d_weights, const float* d_textures, float* dweff,
-                                  float2* gin, float* d_mlp, int* status, cudaStream_t st);
-
-// tcgen05 texturing forward (texture_tc.cu); writes the features to fd.feat
-// when fd.feat_mode == 1.
 cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                   const FieldDev& fd, const float* notex, const float* weights,
                                   const int* ids, const float* depths, const float* T_final,
                                   float* image, float* textures, int* status, cudaStream_t st);
-
-// BF16 tensor-core texturing (texture_bf16.cu).
-bool bf16_arch_supported(const nexel_field& f);
-cudaError_t launch_texture_bwd_bf16(const DevCam& c, const nexel_settings& s, const nexel_field& f,
-                                    const FieldDev& fd, char* bws, const BwdLayout& B,
-                                    const float* weights, const int* ids, const float* depths,
-                                    const float* d_image, const float* d_weights,
-                                    const float* d_textures, float* d_table, float* d_mlp,
-                                    cudaStream_t st);
+cudaError_t launch_texture_gather_tc(const DevCam& c, const nexel_settings& s,
+                                     const nexel_field& f, const FieldDev& fd, const int* ids,
+                                     const float* depths, uint32_t* feat, cudaStream_t st);
+cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
+                                  int h2, bool f16, const float* w, const uint32_t* feat,
+                                  const float* weights, const int* ids, const float* d_image,
+                                  const float* d_weights, const float* d_textures, float* dweff,
+                                  float2* gin, float* d_mlp, int* status, cudaStream_t st);
 
 }  // namespace nexel

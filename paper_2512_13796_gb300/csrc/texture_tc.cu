@@ -51,9 +51,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
   return d;
 }
 
-// instruction descriptor, kind::f16: BF16 x BF16 -> F32, M x N
-__host__ __device__ constexpr uint32_t idesc(int m, int n, int a_mn, int b_mn) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+// instruction descriptor, kind::f16: A and B of format fmt (0 = F16,
+// 1 = BF16), F32 accumulator, M x N
+__host__ __device__ constexpr uint32_t idesc(int m, int n, int a_mn, int b_mn, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
          ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
@@ -108,10 +109,39 @@ __device__ __forceinline__ void sync_to_mma() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
+// MMA operand type.  BF16; or FP16, where the backward scales the gradient
+// entering the MLP by 128 and unscales the feature and weight gradients (the
+// paper trains the MLP in FP16 with a loss scale of 128).
+struct OpBf16 {
+  static constexpr uint32_t kFmt = 1;
+  static constexpr float kScale = 1.f;
+  __device__ static uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+  }
+  __device__ static float2 unpack2(uint32_t w) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+  }
+  __device__ static uint16_t cvt(float x) {
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    return *reinterpret_cast<uint16_t*>(&b);
+  }
+};
+struct OpF16 {
+  static constexpr uint32_t kFmt = 0;
+  static constexpr float kScale = 128.f;
+  __device__ static uint32_t pack2(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+  }
+  __device__ static float2 unpack2(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  }
+  __device__ static uint16_t cvt(float x) {
+    __half h = __float2half_rn(x);
+    return *reinterpret_cast<uint16_t*>(&h);
+  }
+};
 
 // byte offset of element (row r, feature f) in a core-matrix tile whose
 // 8-row groups are sg bytes apart
@@ -120,8 +150,10 @@ __host__ __device__ constexpr uint32_t cm_off(int r, int f, int sg) {
 }
 
 // Stores 8 consecutive features f0..f0+7 (f0 % 8 == 0) of row r.
+template <typename OP>
 __device__ __forceinline__ void st8(unsigned char* base, int r, int f0, int sg, const float* v) {
-  uint4 q = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+  uint4 q = make_uint4(OP::pack2(v[0], v[1]), OP::pack2(v[2], v[3]), OP::pack2(v[4], v[5]),
+                       OP::pack2(v[6], v[7]));
   *reinterpret_cast<uint4*>(base + cm_off(r, f0, sg)) = q;
 }
 
@@ -209,7 +241,7 @@ struct TcLayout {
   static_assert(HL + 16 <= 256 && FA <= 256, "MMA N limits");
 };
 
-template <int IN, int H1, int H2>
+template <int IN, int H1, int H2, typename OP>
 __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     DevCam c, int K, int log2KP, long long n_rows, long long n_tiles, const float* __restrict__ wts,
     const uint32_t* __restrict__ feat, const float* __restrict__ weights,
@@ -234,17 +266,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     const float* W3 = W2 + H2 * H1;      // [3][HL]
     for (int i = tid; i < H1 * IN; i += kTcThreads) {
       const int o = i / IN, k = i % IN;
-      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w1 + cm_off(o, k, IN / 8 * 128)) =
-          __float2bfloat16_rn(W1[i]);
-      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w1t + cm_off(k, o, H1 / 8 * 128)) =
-          __float2bfloat16_rn(W1[i]);
+      *reinterpret_cast<uint16_t*>(tc_smem + Lt::w1 + cm_off(o, k, IN / 8 * 128)) =
+          OP::cvt(W1[i]);
+      *reinterpret_cast<uint16_t*>(tc_smem + Lt::w1t + cm_off(k, o, H1 / 8 * 128)) =
+          OP::cvt(W1[i]);
     }
     for (int i = tid; i < H2 * H1; i += kTcThreads) {
       const int o = i / H1, k = i % H1;
-      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w2 + cm_off(o, k, H1 / 8 * 128)) =
-          __float2bfloat16_rn(W2[i]);
-      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w2t + cm_off(k, o, (H2 > 0 ? H2 : 8) / 8 * 128)) =
-          __float2bfloat16_rn(W2[i]);
+      *reinterpret_cast<uint16_t*>(tc_smem + Lt::w2 + cm_off(o, k, H1 / 8 * 128)) =
+          OP::cvt(W2[i]);
+      *reinterpret_cast<uint16_t*>(tc_smem + Lt::w2t + cm_off(k, o, (H2 > 0 ? H2 : 8) / 8 * 128)) =
+          OP::cvt(W2[i]);
     }
     for (int i = tid; i < 3 * HL; i += kTcThreads) w3s[i] = W3[i];
     // zero the delta tile once: the padding columns of d3 stay zero
@@ -322,8 +354,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     for (int c8 = 0; c8 < IN / 8; ++c8)
       *reinterpret_cast<uint4*>(act + cm_off(tid, 8 * c8, Lt::SA)) = cur.x[c8];
     {
-      const float d3[8] = {gT[0], gT[1], gT[2], 0.f, 0.f, 0.f, 0.f, 0.f};
-      st8(del, tid, HL, Lt::SD, d3);
+      const float d3[8] = {OP::kScale * gT[0], OP::kScale * gT[1], OP::kScale * gT[2], 0.f, 0.f, 0.f, 0.f, 0.f};
+      st8<OP>(del, tid, HL, Lt::SD, d3);
     }
     sync_to_mma();
     // R1: h1 = X W1^T -> t0
@@ -331,7 +363,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
 #pragma unroll
       for (int kk = 0; kk < IN / 16; ++kk)
         mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
-            sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0), kk > 0);
+            sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
       commit(&s_bar);
     }
     load_row(tile + gridDim.x, nxt);
@@ -348,8 +380,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         if (v[i] > 0.f) m1 |= 1ull << (16 * c16 + i);
         v[i] = fmaxf(v[i], 0.f);
       }
-      st8(act, tid, IN + 16 * c16, Lt::SA, v);
-      st8(act, tid, IN + 16 * c16 + 8, Lt::SA, v + 8);
+      st8<OP>(act, tid, IN + 16 * c16, Lt::SA, v);
+      st8<OP>(act, tid, IN + 16 * c16 + 8, Lt::SA, v + 8);
     }
     if constexpr (H2 > 0) {
       sync_to_mma();
@@ -358,7 +390,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
 #pragma unroll
         for (int kk = 0; kk < H1 / 16; ++kk)
           mma(t0, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
-              sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0), kk > 0);
+              sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0, OP::kFmt), kk > 0);
         commit(&s_bar);
       }
       ok = ok && wait_bar(&s_bar, phase);
@@ -373,8 +405,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
           if (v[i] > 0.f) m2 |= 1ull << (16 * c16 + i);
           v[i] = fmaxf(v[i], 0.f);
         }
-        st8(act, tid, IN + H1 + 16 * c16, Lt::SA, v);
-        st8(act, tid, IN + H1 + 16 * c16 + 8, Lt::SA, v + 8);
+        st8<OP>(act, tid, IN + H1 + 16 * c16, Lt::SA, v);
+        st8<OP>(act, tid, IN + H1 + 16 * c16 + 8, Lt::SA, v + 8);
       }
     }
     // texture T = W3 h_last, dL/dW_j, and d_last = (W3^T d3) * [h_last > 0]
@@ -397,7 +429,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         float hv[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const float2 h2v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&hw[i]));
+          const float2 h2v = OP::unpack2(hw[i]);
           hv[2 * i] = h2v.x;
           hv[2 * i + 1] = h2v.y;
         }
@@ -409,10 +441,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
           T0 = fmaf(wr[0][i], hlq, T0);
           T1 = fmaf(wr[1][i], hlq, T1);
           T2 = fmaf(wr[2][i], hlq, T2);
-          const float g = fmaf(gT[0], wr[0][i], fmaf(gT[1], wr[1][i], gT[2] * wr[2][i]));
+          const float g = OP::kScale * fmaf(gT[0], wr[0][i], fmaf(gT[1], wr[1][i], gT[2] * wr[2][i]));
           v[i] = ((ml >> q) & 1ull) ? g : 0.f;
         }
-        st8(del, tid, 8 * c8, Lt::SD, v);
+        st8<OP>(del, tid, 8 * c8, Lt::SD, v);
       }
       if (in_pix) dweff[s] = valid ? T0 * dC[0] + T1 * dC[1] + T2 * dC[2] + dWx : 0.f;
     }
@@ -423,7 +455,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
 #pragma unroll
         for (int kk = 0; kk < H2 / 16; ++kk)
           mma(t0, sdesc(sb + Lt::del + kk * 256, 128, Lt::SD),
-              sdesc(sb + Lt::w2t + kk * 256, 128, H2 / 8 * 128), idesc(128, H1, 0, 0), kk > 0);
+              sdesc(sb + Lt::w2t + kk * 256, 128, H2 / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
         commit(&s_bar);
       }
       ok = ok && wait_bar(&s_bar, phase);
@@ -435,8 +467,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         tmem_ld16(t0 + lane_base + 16 * c16, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = ((m1 >> (16 * c16 + i)) & 1ull) ? v[i] : 0.f;
-        st8(del, tid, Lt::D1 + 16 * c16, Lt::SD, v);
-        st8(del, tid, Lt::D1 + 16 * c16 + 8, Lt::SD, v + 8);
+        st8<OP>(del, tid, Lt::D1 + 16 * c16, Lt::SD, v);
+        st8<OP>(del, tid, Lt::D1 + 16 * c16 + 8, Lt::SD, v + 8);
       }
     }
     sync_to_mma();
@@ -445,16 +477,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
 #pragma unroll
       for (int kk = 0; kk < H1 / 16; ++kk)
         mma(t0, sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 256, 128, Lt::SD),
-            sdesc(sb + Lt::w1t + kk * 256, 128, H1 / 8 * 128), idesc(128, IN, 0, 0), kk > 0);
+            sdesc(sb + Lt::w1t + kk * 256, 128, H1 / 8 * 128), idesc(128, IN, 0, 0, OP::kFmt), kk > 0);
       // K = rows: 16 rows = two 8-row groups per MMA
 #pragma unroll 1
       for (int kk = 0; kk < kTcRows / 16; ++kk) {
         const bool acc = !(first && kk == 0);
         mma(t_da, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 2 * Lt::SA, Lt::SA, 128),
-            sdesc(sb + Lt::del + kk * 2 * Lt::SD, Lt::SD, 128), idesc(128, HL + 16, 1, 1), acc);
+            sdesc(sb + Lt::del + kk * 2 * Lt::SD, Lt::SD, 128), idesc(128, HL + 16, 1, 1, OP::kFmt), acc);
         mma(t_db, sdesc(sb + Lt::act + kk * 2 * Lt::SA, Lt::SA, 128),
             sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 2 * Lt::SD, Lt::SD, 128),
-            idesc(128, H1, 1, 1), acc);
+            idesc(128, H1, 1, 1, OP::kFmt), acc);
       }
       commit(&s_bar);
     }
@@ -471,7 +503,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         tmem_ld16(t0 + lane_base + 16 * c16, v);
         if (r < n_rows) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) gin[(long long)(8 * c16 + i) * R + r] = make_float2(v[2 * i], v[2 * i + 1]);
+          for (int i = 0; i < 8; ++i)
+            gin[(long long)(8 * c16 + i) * R + r] =
+                make_float2(v[2 * i] * (1.f / OP::kScale), v[2 * i + 1] * (1.f / OP::kScale));
         }
       }
     }
@@ -496,11 +530,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       for (int i = 0; i < 16; ++i) {
         const int n = 16 * c16 + i, m = tid;
         if (H2 > 0) {
-          if (m < H1 && n < H2) atomicAdd(dW2 + n * H1 + m, v[i]);              // dW2[o=n][i=m]
+          if (m < H1 && n < H2) atomicAdd(dW2 + n * H1 + m, v[i] * (1.f / OP::kScale));  // dW2[o=n][i=m]
           if (m >= H1 && m < H1 + H2 && n >= HL && n < HL + 3)
-            atomicAdd(dW3 + (n - HL) * HL + (m - H1), v[i]);                     // dW3[o][i]
+            atomicAdd(dW3 + (n - HL) * HL + (m - H1), v[i] * (1.f / OP::kScale));         // dW3[o][i]
         } else {
-          if (m < H1 && n >= HL && n < HL + 3) atomicAdd(dW3 + (n - HL) * HL + m, v[i]);
+          if (m < H1 && n >= HL && n < HL + 3)
+            atomicAdd(dW3 + (n - HL) * HL + m, v[i] * (1.f / OP::kScale));
         }
       }
     }
@@ -509,7 +544,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       tmem_ld16(t_db + lane_base + 16 * c16, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        if (tid < IN) atomicAdd(dW1 + (16 * c16 + i) * IN + tid, v[i]);         // dW1[o][i]
+        if (tid < IN) atomicAdd(dW1 + (16 * c16 + i) * IN + tid, v[i] * (1.f / OP::kScale));  // dW1[o][i]
     }
   }
   if (!ok && tid == 0 && status) atomicExch(status, 1);
@@ -518,7 +553,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
-template <int IN, int H1, int H2>
+template <int IN, int H1, int H2, typename OP>
 cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const float* w,
                        const uint32_t* feat, const float* weights, const int* ids,
                        const float* d_image, const float* d_weights, const float* d_textures,
@@ -528,7 +563,7 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
   while ((1 << log2KP) < KP) ++log2KP;
   const long long n_tiles = (n_rows + kTcRows - 1) / kTcRows;
   if (n_tiles == 0) return cudaSuccess;
-  auto kern = k_tex_bwd_tc<IN, H1, H2>;
+  auto kern = k_tex_bwd_tc<IN, H1, H2, OP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::total);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 152;
@@ -568,7 +603,7 @@ struct TcFwdLayout {
 constexpr int kTcFwdThreads = 256;
 constexpr int kTcFwdCols = 128;
 
-template <int IN, int H1, int H2, typename TT>
+template <int IN, int H1, int H2, typename TT, typename OP>
 __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
     DevCam c, FieldDev f, int K, int log2KP, long long n_tiles, float bg0, float bg1, float bg2,
     const float* __restrict__ notex, const float* __restrict__ weights,
@@ -587,15 +622,15 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
     const float* W2 = f.w + H1 * IN;
     const float* W3 = W2 + H2 * H1;
     for (int i = tid; i < H1 * IN; i += kTcFwdThreads)
-      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w1 + cm_off(i / IN, i % IN, IN / 8 * 128)) =
-          __float2bfloat16_rn(W1[i]);
+      *reinterpret_cast<uint16_t*>(tc_smem + Lt::w1 + cm_off(i / IN, i % IN, IN / 8 * 128)) =
+          OP::cvt(W1[i]);
     for (int i = tid; i < H2 * H1; i += kTcFwdThreads)
-      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w2 + cm_off(i / H1, i % H1, H1 / 8 * 128)) =
-          __float2bfloat16_rn(W2[i]);
+      *reinterpret_cast<uint16_t*>(tc_smem + Lt::w2 + cm_off(i / H1, i % H1, H1 / 8 * 128)) =
+          OP::cvt(W2[i]);
     for (int i = tid; i < 16 * HL; i += kTcFwdThreads) {
       const int o = i / HL, k = i % HL;
-      *reinterpret_cast<__nv_bfloat16*>(tc_smem + Lt::w3 + cm_off(o, k, HL / 8 * 128)) =
-          __float2bfloat16_rn(o < 3 ? W3[o * HL + k] : 0.f);
+      *reinterpret_cast<uint16_t*>(tc_smem + Lt::w3 + cm_off(o, k, HL / 8 * 128)) =
+          OP::cvt(o < 3 ? W3[o * HL + k] : 0.f);
     }
   }
   if (tid == 0) {
@@ -642,7 +677,7 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
         float v[8];
         gather4_tc<TT>(f, gh * LH + 4 * g8, x, D, valid, v);
         const int f0 = gh * (IN / 2) + 8 * g8;
-        st8(act, grow, f0, Lt::SA, v);
+        st8<OP>(act, grow, f0, Lt::SA, v);
         if (feat_cache && p < P) {
           const uint4 q4 = *reinterpret_cast<const uint4*>(act + cm_off(grow, f0, Lt::SA));
           reinterpret_cast<uint4*>(feat_cache + (size_t)(tile * kTcRows + grow) * (IN / 2))[f0 / 8] = q4;
@@ -654,7 +689,7 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
 #pragma unroll
       for (int kk = 0; kk < IN / 16; ++kk)
         mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
-            sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0), kk > 0);
+            sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
       commit(&s_bar);
     }
     ok = wait_bar(&s_bar, phase);
@@ -667,8 +702,8 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
       tmem_ld16(t0 + elane + col, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-      st8(act, erow, IN + col, Lt::SA, v);
-      st8(act, erow, IN + col + 8, Lt::SA, v + 8);
+      st8<OP>(act, erow, IN + col, Lt::SA, v);
+      st8<OP>(act, erow, IN + col + 8, Lt::SA, v + 8);
     }
     if constexpr (H2 > 0) {
       sync_to_mma();
@@ -676,7 +711,7 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
 #pragma unroll
         for (int kk = 0; kk < H1 / 16; ++kk)
           mma(t0, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
-              sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0), kk > 0);
+              sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0, OP::kFmt), kk > 0);
         commit(&s_bar);
       }
       ok = ok && wait_bar(&s_bar, phase);
@@ -689,8 +724,8 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
         tmem_ld16(t0 + elane + col, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-        st8(act, erow, IN + H1 + col, Lt::SA, v);
-        st8(act, erow, IN + H1 + col + 8, Lt::SA, v + 8);
+        st8<OP>(act, erow, IN + H1 + col, Lt::SA, v);
+        st8<OP>(act, erow, IN + H1 + col + 8, Lt::SA, v + 8);
       }
     }
     sync_to_mma();
@@ -698,7 +733,7 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
 #pragma unroll
       for (int kk = 0; kk < HL / 16; ++kk)
         mma(t1, sdesc(sb + Lt::act + ((IN + H1 + H2 - HL) / 8) * 128 + kk * 256, 128, Lt::SA),
-            sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, 16, 0, 0), kk > 0);
+            sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, 16, 0, 0, OP::kFmt), kk > 0);
       commit(&s_bar);
     }
     ok = ok && wait_bar(&s_bar, phase);
@@ -742,7 +777,7 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcFwdCols));
 }
 
-template <int IN, int H1, int H2, typename TT>
+template <int IN, int H1, int H2, typename TT, typename OP>
 cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev& fd,
                        const float* notex, const float* weights, const int* ids,
                        const float* depths, const float* T_final, float* image, float* textures,
@@ -753,7 +788,7 @@ cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev&
   const long long rows = (long long)c.W * c.H << log2KP;
   const long long n_tiles = (rows + kTcRows - 1) / kTcRows;
   if (n_tiles == 0) return cudaSuccess;
-  auto kern = k_tex_fwd_tc<IN, H1, H2, TT>;
+  auto kern = k_tex_fwd_tc<IN, H1, H2, TT, OP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::total);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 152;
@@ -767,6 +802,56 @@ cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev&
   return cudaGetLastError();
 }
 
+// Feature pass of a backward without cached features: the gather of the
+// forward (same lane layout and arithmetic), written to the feature buffer.
+template <int IN, typename TT, typename OP>
+__global__ void __launch_bounds__(kTcFwdThreads) k_gather_tc(DevCam c, FieldDev f, int K, int log2KP,
+                                                           long long n_tiles, const int* __restrict__ ids,
+                                                           const float* __restrict__ depths,
+                                                           uint32_t* __restrict__ feat) {
+  const long long tile = blockIdx.x;
+  const int tid = threadIdx.x, tt = tid & (kTcRows - 1), gh = tid >> 7;
+  const int KP = 1 << log2KP, PPT = kTcRows >> log2KP;
+  const long long P = (long long)c.W * c.H;
+  const long long p = tile * PPT + tt % PPT;
+  const int j = tt / PPT;
+  if (tile >= n_tiles || p >= P) return;
+  const long long s = p * K + j;
+  const bool valid = j < K && ids[s] >= 0;
+  float3 x = make_float3(0.f, 0.f, 0.f);
+  float D = 1.f;
+  if (valid) {
+    D = depths[s];
+    const float3 d = pixel_dir(c, (int)(p % c.W), (int)(p / c.W));
+    x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
+  }
+  const size_t row = (size_t)p * KP + j;
+  constexpr int LH = IN / 4;
+#pragma unroll
+  for (int g8 = 0; g8 < LH / 4; ++g8) {
+    float v[8];
+    gather4_tc<TT>(f, gh * LH + 4 * g8, x, D, valid, v);
+    const int f0 = gh * (IN / 2) + 8 * g8;
+    reinterpret_cast<uint4*>(feat + row * (IN / 2))[f0 / 8] =
+        make_uint4(OP::pack2(v[0], v[1]), OP::pack2(v[2], v[3]), OP::pack2(v[4], v[5]),
+                   OP::pack2(v[6], v[7]));
+  }
+}
+
+template <int IN, typename TT, typename OP>
+cudaError_t gather_tc(const DevCam& c, const nexel_settings& s, const FieldDev& fd, const int* ids,
+                      const float* depths, uint32_t* feat, cudaStream_t st) {
+  int log2KP = 0;
+  while ((1 << log2KP) < s.K) ++log2KP;
+  const long long rows = (long long)c.W * c.H << log2KP;
+  const long long n_tiles = (rows + kTcRows - 1) / kTcRows;
+  if (n_tiles == 0) return cudaSuccess;
+  NEXEL_PROF("texture_gather_tc", st);
+  k_gather_tc<IN, TT, OP><<<(unsigned)n_tiles, kTcFwdThreads, 0, st>>>(c, fd, s.K, log2KP, n_tiles,
+                                                                      ids, depths, feat);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool tc_arch_supported(int in, int h1, int h2) {
@@ -774,16 +859,22 @@ bool tc_arch_supported(int in, int h1, int h2) {
 }
 
 cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
-                                  int h2, const float* w, const uint32_t* feat,
+                                  int h2, bool f16, const float* w, const uint32_t* feat,
                                   const float* weights, const int* ids, const float* d_image,
                                   const float* d_weights, const float* d_textures, float* dweff,
                                   float2* gin, float* d_mlp, int* status, cudaStream_t st) {
-  if (in == 16 && h1 == 64 && h2 == 0)
-    return tex_bwd_tc<16, 64, 0>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights,
-                                 d_textures, dweff, gin, d_mlp, status, st);
-  if (in == 32 && h1 == 64 && h2 == 64)
-    return tex_bwd_tc<32, 64, 64>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights,
-                                  d_textures, dweff, gin, d_mlp, status, st);
+#define NEXEL_TCB(A, B, C, OPT)                                                                   \
+  return tex_bwd_tc<A, B, C, OPT>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights, \
+                                  d_textures, dweff, gin, d_mlp, status, st)
+  if (in == 16 && h1 == 64 && h2 == 0) {
+    if (f16) NEXEL_TCB(16, 64, 0, OpF16);
+    NEXEL_TCB(16, 64, 0, OpBf16);
+  }
+  if (in == 32 && h1 == 64 && h2 == 64) {
+    if (f16) NEXEL_TCB(32, 64, 64, OpF16);
+    NEXEL_TCB(32, 64, 64, OpBf16);
+  }
+#undef NEXEL_TCB
   return cudaErrorInvalidValue;
 }
 
@@ -791,18 +882,42 @@ cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, cons
                                   const FieldDev& fd, const float* notex, const float* weights,
                                   const int* ids, const float* depths, const float* T_final,
                                   float* image, float* textures, int* status, cudaStream_t st) {
-  const bool h = s.grid_dtype == NEXEL_F16;
+  const bool h = s.grid_dtype == NEXEL_F16, f16 = s.mlp_dtype == NEXEL_F16;
   const int in = f.widths[0], h1 = f.widths[1], h2 = f.n_layers == 3 ? f.widths[2] : 0;
-  if (in == 16 && h1 == 64 && h2 == 0)
-    return h ? tex_fwd_tc<16, 64, 0, __half>(c, s, fd, notex, weights, ids, depths, T_final, image,
-                                             textures, status, st)
-             : tex_fwd_tc<16, 64, 0, float>(c, s, fd, notex, weights, ids, depths, T_final, image,
-                                            textures, status, st);
-  if (in == 32 && h1 == 64 && h2 == 64)
-    return h ? tex_fwd_tc<32, 64, 64, __half>(c, s, fd, notex, weights, ids, depths, T_final,
-                                              image, textures, status, st)
-             : tex_fwd_tc<32, 64, 64, float>(c, s, fd, notex, weights, ids, depths, T_final, image,
-                                             textures, status, st);
+#define NEXEL_TCF(A, B, C, TT, OPT)                                                            \
+  return tex_fwd_tc<A, B, C, TT, OPT>(c, s, fd, notex, weights, ids, depths, T_final, image, \
+                                      textures, status, st)
+#define NEXEL_TCF2(A, B, C)                                \
+  if (h) {                                                 \
+    if (f16) NEXEL_TCF(A, B, C, __half, OpF16);            \
+    NEXEL_TCF(A, B, C, __half, OpBf16);                    \
+  }                                                        \
+  if (f16) NEXEL_TCF(A, B, C, float, OpF16);               \
+  NEXEL_TCF(A, B, C, float, OpBf16);
+  if (in == 16 && h1 == 64 && h2 == 0) { NEXEL_TCF2(16, 64, 0) }
+  if (in == 32 && h1 == 64 && h2 == 64) { NEXEL_TCF2(32, 64, 64) }
+#undef NEXEL_TCF2
+#undef NEXEL_TCF
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_texture_gather_tc(const DevCam& c, const nexel_settings& s,
+                                     const nexel_field& f, const FieldDev& fd, const int* ids,
+                                     const float* depths, uint32_t* feat, cudaStream_t st) {
+  const bool h = s.grid_dtype == NEXEL_F16, f16 = s.mlp_dtype == NEXEL_F16;
+  const int in = f.widths[0];
+#define NEXEL_TCG(A, TT, OPT) return gather_tc<A, TT, OPT>(c, s, fd, ids, depths, feat, st)
+#define NEXEL_TCG2(A)                                              \
+  if (h) {                                                         \
+    if (f16) NEXEL_TCG(A, __half, OpF16);                          \
+    NEXEL_TCG(A, __half, OpBf16);                                  \
+  }                                                                \
+  if (f16) NEXEL_TCG(A, float, OpF16);                             \
+  NEXEL_TCG(A, float, OpBf16);
+  if (in == 16) { NEXEL_TCG2(16) }
+  if (in == 32) { NEXEL_TCG2(32) }
+#undef NEXEL_TCG2
+#undef NEXEL_TCG
   return cudaErrorInvalidValue;
 }
 

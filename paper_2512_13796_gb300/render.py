@@ -33,7 +33,7 @@ def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32",
     for i in range(3):
         s.bg[i] = float(st.bg[i])
     s.grid_dtype = {"f32": N_.F32, "f16": N_.F16}[grid_dtype]
-    s.mlp_dtype = {"f32": N_.F32, "bf16": N_.BF16}[mlp_dtype]
+    s.mlp_dtype = {"f32": N_.F32, "bf16": N_.BF16, "f16": N_.F16}[mlp_dtype]
     s.recompute_buffers = 1 if recompute else 0
     s.cache_features = 1 if cache_features else 0
     return s

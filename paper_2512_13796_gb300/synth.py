@@ -202,13 +202,14 @@ class Workload:
     settings: Settings
     field: Field
     grid_dtype: str   # "f32" | "f16"
-    mlp_dtype: str    # "f32" | "bf16"
+    mlp_dtype: str    # "f32" | "bf16" | "f16"
 
 
 def workload(idx: int, *, gamma: str | None = None, seed: int | None = None,
              precision: str | None = None) -> Workload:
     """Config 0..4 of the measurement plan.  ``precision`` overrides the
-    grid/MLP storage: "f32" or "bf16" (fp16 table + bf16 MLP)."""
+    grid/MLP storage: "f32", "bf16" (fp16 table + bf16 MLP) or "f16" (fp16
+    table + fp16 MLP with loss scaling)."""
     s = idx if seed is None else seed
     if idx == 0:
         sc = make_scene(256, 3, s, gamma=gamma or "one")
@@ -242,8 +243,8 @@ def workload(idx: int, *, gamma: str | None = None, seed: int | None = None,
         raise ValueError(idx)
     prec = precision or prec
     return Workload(f"config{idx}", sc, cams, st, fld,
-                    "f16" if prec == "bf16" else "f32",
-                    "bf16" if prec == "bf16" else "f32")
+                    "f32" if prec == "f32" else "f16",
+                    prec)
 
 
 def pixel_sample(cam: Camera, n_random: int, n_tiles: int, seed: int,
