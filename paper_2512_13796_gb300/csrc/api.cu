@@ -43,6 +43,7 @@ static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
   L.did1 = take(n * 4);
   L.rect = take(n * 8);
   L.conic = take(n * 48);
+  L.tmask = take(n * 16);
   L.count = take(n * 4);
   L.offs = take((n + 1) * 4);
   L.ranges = take((size_t)L.n_tiles * 8);

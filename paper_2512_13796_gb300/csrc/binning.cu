@@ -406,65 +406,69 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const KeyT* __restrict__ kin, KeyT* __restrict__ kout, const uint32_t* __restrict__ vin,
     uint32_t* __restrict__ vout, long long n, int shift, int bits,
     const uint32_t* __restrict__ offs, int nblocks) {
+  // Warp w ranks the block's keys [512 w, 512 w + 512) in order (item k,
+  // lane l -> key 512 w + 32 k + l) with warp-private digit counters (match
+  // + leader update, no block barrier per item); one block-wide scan over
+  // (digit, warp) then gives every key its place in digit order.
   extern __shared__ __align__(16) unsigned char smem[];
   KeyT* s_key = reinterpret_cast<KeyT*>(smem);
   uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);
-  __shared__ uint32_t s_start[256], s_run[256], s_w[8];
-  __shared__ uint32_t s_wc[kSortThreads / 32][256];
+  constexpr int kW = kSortThreads / 32;
+  __shared__ uint32_t s_start[256], s_w[8];
+  __shared__ uint32_t s_wc[kW][256];
   const int nbins = 1 << bits;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long base = (long long)blockIdx.x * kSortTile;
   const int nloc = (int)min((long long)kSortTile, n - base);
-  for (int b = threadIdx.x; b < 256 * (kSortThreads / 32); b += kSortThreads)
-    (&s_wc[0][0])[b] = 0;
-  s_run[threadIdx.x] = 0;
+  for (int b = threadIdx.x; b < 256 * kW; b += kSortThreads) (&s_wc[0][0])[b] = 0;
   __syncthreads();
   KeyT key[kSortItems];
-  uint32_t val[kSortItems];
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    int li = k * kSortThreads + threadIdx.x;
-    if (li < nloc) {
-      key[k] = kin[base + li];
-      if (kVal) val[k] = vin[base + li];
-      atomicAdd(&s_run[(uint32_t)(key[k] >> shift) & mask], 1u);
-    }
-  }
-  __syncthreads();
-  uint32_t tot;
-  uint32_t st0 = block_excl_scan(s_run[threadIdx.x], s_w, tot);
-  s_start[threadIdx.x] = st0;
-  s_run[threadIdx.x] = st0;
-  __syncthreads();
+  uint32_t val[kSortItems], rank[kSortItems];
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    int li = k * kSortThreads + threadIdx.x;
-    bool valid = li < nloc;
-    uint32_t d = valid ? ((uint32_t)(key[k] >> shift) & mask) : 0xFFFFFFFFu;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    uint32_t r = __popc(peers & lt);
-    if (valid && (peers & lt) == 0) s_wc[warp][d] = __popc(peers);
-    __syncthreads();
+    const int li = warp * (32 * kSortItems) + k * 32 + lane;
+    const bool valid = li < nloc;
     if (valid) {
-      uint32_t pos = s_run[d] + r;
-      for (int w = 0; w < warp; ++w) pos += s_wc[w][d];
+      key[k] = kin[base + li];
+      if (kVal) val[k] = vin[base + li];
+    }
+    const uint32_t d = valid ? ((uint32_t)(key[k] >> shift) & mask) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = 0;
+    if (valid) before = s_wc[warp][d];
+    __syncwarp();
+    rank[k] = before + __popc(peers & lt);
+    if (valid && (peers & lt) == 0) s_wc[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive prefix over warps (in place) and the block total
+  uint32_t tot_d = 0;
+  if (threadIdx.x < 256) {
+#pragma unroll
+    for (int w = 0; w < kW; ++w) {
+      const uint32_t c = s_wc[w][threadIdx.x];
+      s_wc[w][threadIdx.x] = tot_d;
+      tot_d += c;
+    }
+  }
+  uint32_t tot;
+  const uint32_t st0 = block_excl_scan(tot_d, s_w, tot);
+  s_start[threadIdx.x] = st0;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int li = warp * (32 * kSortItems) + k * 32 + lane;
+    if (li < nloc) {
+      const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
+      const uint32_t pos = s_start[d] + s_wc[warp][d] + rank[k];
       s_key[pos] = key[k];
       if (kVal) s_val[pos] = val[k];
     }
-    __syncthreads();
-    if (threadIdx.x < nbins) {
-      uint32_t t2 = 0;
-#pragma unroll
-      for (int w = 0; w < kSortThreads / 32; ++w) {
-        t2 += s_wc[w][threadIdx.x];
-        s_wc[w][threadIdx.x] = 0;
-      }
-      s_run[threadIdx.x] += t2;
-    }
-    __syncthreads();
   }
+  __syncthreads();
   for (int j = threadIdx.x; j < nloc; j += kSortThreads) {
     KeyT kk = s_key[j];
     uint32_t d = (uint32_t)(kk >> shift) & mask;
@@ -539,11 +543,14 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
                                                    const uint32_t* __restrict__ did,
                                                    const uint2* __restrict__ rect,
                                                    const float4* __restrict__ conic,
+                                                   const uint4* __restrict__ tmask,
                                                    const uint32_t* __restrict__ offs,
                                                    const uint32_t* __restrict__ count,
                                                    KeyT* __restrict__ keys) {
-  // one warp per surfel (rank order): the lanes test 32 tiles of the
-  // rectangle at a time and the passing ones are written in tile order
+  // one warp per surfel (rank order): the lanes take 32 tiles of the
+  // rectangle at a time and the passing ones are written in tile order; the
+  // decisions come from the counting pass's mask when the rectangle has at
+  // most 128 tiles, else the test runs again
   const int lane = threadIdx.x & 31;
   const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (r >= N) return;
@@ -552,8 +559,24 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
   const uint2 rc = rect[id];
   const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
   const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
-  const TileConic kc = load_conic(conic, id);
   size_t o = offs[r];
+  if (nt <= 128) {
+    const uint4 mq = tmask[id];
+    const uint32_t mw[4] = {mq.x, mq.y, mq.z, mq.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (32 * i >= nt) break;
+      const unsigned m = mw[i];
+      if ((m >> lane) & 1u) {
+        const int k = 32 * i + lane;
+        const KeyT tile = (KeyT)((ty0 + k / nx) * c.tiles_x + tx0 + k % nx);
+        keys[o + __popc(m & ((1u << lane) - 1u))] = (tile << rank_bits) | (KeyT)r;
+      }
+      o += __popc(m);
+    }
+    return;
+  }
+  const TileConic kc = load_conic(conic, id);
   for (int b = 0; b < nt; b += 32) {
     const int k = b + lane;
     const int tx = tx0 + k % nx, ty = ty0 + k / nx;
@@ -568,10 +591,12 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
 }
 
 // Exact instance count of each surfel: the tiles of its rectangle that pass
-// tile_may_hit (one warp per surfel, original order).
+// tile_may_hit (one warp per surfel, original order), and, for rectangles of
+// at most 128 tiles, the pass/fail bits in rectangle order for k_duplicate.
 __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
                                                     const uint2* __restrict__ rect,
                                                     const float4* __restrict__ conic,
+                                                    uint4* __restrict__ tmask,
                                                     uint32_t* __restrict__ count) {
   const int lane = threadIdx.x & 31;
   const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -581,6 +606,21 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
   const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
   const TileConic kc = load_conic(conic, (uint32_t)i);
   uint32_t n = 0;
+  if (nt <= 128) {
+    uint32_t mw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int k = 32 * w + lane;
+      const bool hit = k < nt && tile_may_hit(kc, tx0 + k % nx, ty0 + k / nx, c.W, c.H);
+      mw[w] = __ballot_sync(0xffffffffu, hit);
+      n += __popc(mw[w]);
+    }
+    if (lane == 0) {
+      tmask[i] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+      count[i] = n;
+    }
+    return;
+  }
   for (int k = lane; k < nt; k += 32)
     n += tile_may_hit(kc, tx0 + k % nx, ty0 + k / nx, c.W, c.H) ? 1u : 0u;
 #pragma unroll
@@ -616,7 +656,8 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
   {
     NEXEL_PROF("tile_count", st);
     k_tile_count<<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, st>>>(
-        c, N, (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint32_t*)(ws + L.count));
+        c, N, (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint4*)(ws + L.tmask),
+        (uint32_t*)(ws + L.count));
   }
   return cudaGetLastError();
 }
@@ -660,7 +701,7 @@ static cudaError_t binning_t(const DevCam& c, int N, long long n_inst, char* ws,
     NEXEL_PROF("duplicate", st);
     k_duplicate<KeyT><<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, st>>>(
         c, N, rb, (uint32_t*)(ws + L.did0), (uint2*)(ws + L.rect), (float4*)(ws + L.conic),
-        (uint32_t*)(ws + L.offs), (uint32_t*)(ws + L.count), k0);
+        (const uint4*)(ws + L.tmask), (uint32_t*)(ws + L.offs), (uint32_t*)(ws + L.count), k0);
   }
   int which = 0;
   cudaError_t e = radix_sort<KeyT>(k0, k1, nullptr, nullptr, n_inst, rb, L.tile_bits,

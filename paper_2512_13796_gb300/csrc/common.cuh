@@ -119,7 +119,7 @@ __device__ __forceinline__ float downweight(float focal, float s, float t) {
 // sort scratch, whose size follows the instance capacity, come last, so
 // every call re-derives the same layout from (camera, K, N, ws_bytes).
 struct WsLayout {
-  size_t geom_orig, geom_sorted, aux_orig, aux_sorted, dkey0, dkey1, did0, did1, rect, conic, count,
+  size_t geom_orig, geom_sorted, aux_orig, aux_sorted, dkey0, dkey1, did0, did1, rect, conic, tmask, count,
       offs,
       ranges, n_contrib,
       grad_sorted, counters, fixed_end, inst0, inst1, hist, scan_sums, total;
