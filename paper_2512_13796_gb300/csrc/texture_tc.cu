@@ -591,7 +591,8 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
 template <int IN, int H1, int H2>
 struct TcFwdLayout {
   static constexpr int HL = H2 > 0 ? H2 : H1;
-  static constexpr int FA = IN + H1 + H2;
+  // features X, then the hidden layer (h2 overwrites h1 once R2 has read it)
+  static constexpr int FA = IN + (H1 > H2 ? H1 : H2);
   static constexpr int SA = FA / 8 * 128;
   static constexpr int act = 0;
   static constexpr int w1 = act + kTcRows / 8 * SA;   // [H1][IN]
@@ -724,15 +725,15 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
         tmem_ld16(t0 + elane + col, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-        st8<OP>(act, erow, IN + H1 + col, Lt::SA, v);
-        st8<OP>(act, erow, IN + H1 + col + 8, Lt::SA, v + 8);
+        st8<OP>(act, erow, IN + col, Lt::SA, v);
+        st8<OP>(act, erow, IN + col + 8, Lt::SA, v + 8);
       }
     }
     sync_to_mma();
     if (tid == 0) {
 #pragma unroll
       for (int kk = 0; kk < HL / 16; ++kk)
-        mma(t1, sdesc(sb + Lt::act + ((IN + H1 + H2 - HL) / 8) * 128 + kk * 256, 128, Lt::SA),
+        mma(t1, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
             sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, 16, 0, 0, OP::kFmt), kk > 0);
       commit(&s_bar);
     }
