@@ -65,7 +65,8 @@ static void ws_cap(WsLayout& L, long long cap) {
   size_t c = (size_t)std::max(cap, 1LL);
   L.inst0 = take(c * kb);
   L.inst1 = take(c * kb);
-  long long nb = std::max((c + kSortTile - 1) / kSortTile, ((size_t)L.N + kSortTile - 1) / kSortTile);
+  const size_t depth_tile = (size_t)kSortThreads * kSortItemsDepth;
+  long long nb = std::max((c + kSortTile - 1) / kSortTile, ((size_t)L.N + depth_tile - 1) / depth_tile);
   L.hist = take((size_t)256 * nb * 4);
   long long scan_n = std::max(256LL * nb, (long long)L.N + 1);
   L.scan_sums = take(((size_t)(scan_n + kScanTile - 1) / kScanTile + 1) * 4);

@@ -312,11 +312,47 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_w, u
   return pre + x - v;
 }
 
-// Each block scans kScanTile consecutive elements in place.
-__global__ void __launch_bounds__(256) k_scan_partial(uint32_t* __restrict__ a, long long n,
-                                                      uint32_t* __restrict__ sums) {
+// Exclusive scan in two launches: the block sums of kScanTile-element
+// tiles, then every block adds the sum of the tiles before it (a block
+// reduction over at most a few thousand sums) to its own in-place scan.
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict__ a, long long n,
+                                                     uint32_t* __restrict__ sums) {
   __shared__ uint32_t s_w[8];
-  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  uint32_t loc = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) loc += (base + k < n) ? a[base + k] : 0u;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, d);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = loc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scan_final(uint32_t* __restrict__ a, long long n,
+                                                    const uint32_t* __restrict__ sums,
+                                                    uint32_t* __restrict__ total_out) {
+  __shared__ uint32_t s_w[8];
+  __shared__ uint32_t s_carry;
+  // carry = sum of the sums of the tiles before this one
+  uint32_t c = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += 256) c += sums[b];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    s_carry = t;
+  }
+  __syncthreads();
+  const uint32_t carry = s_carry;
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
   uint32_t loc = 0;
 #pragma unroll
@@ -325,37 +361,13 @@ __global__ void __launch_bounds__(256) k_scan_partial(uint32_t* __restrict__ a, 
     loc += v[k];
   }
   uint32_t tot;
-  uint32_t pre = block_excl_scan(loc, s_w, tot);
+  uint32_t pre = block_excl_scan(loc, s_w, tot) + carry;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     if (base + k < n) a[base + k] = pre;
     pre += v[k];
   }
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) k_scan_sums(uint32_t* __restrict__ sums, int nb,
-                                                    uint32_t* __restrict__ total_out) {
-  __shared__ uint32_t s_w[32];
-  uint32_t carry = 0;
-  for (int b0 = 0; b0 < nb; b0 += 1024) {
-    int i = b0 + threadIdx.x;
-    uint32_t v = i < nb ? sums[i] : 0u;
-    uint32_t tot;
-    uint32_t pre = block_excl_scan(v, s_w, tot);
-    if (i < nb) sums[i] = carry + pre;
-    carry += tot;
-  }
-  if (threadIdx.x == 0 && total_out) *total_out = carry;
-}
-
-__global__ void __launch_bounds__(256) k_scan_add(uint32_t* __restrict__ a, long long n,
-                                                  const uint32_t* __restrict__ sums) {
-  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
-  uint32_t add = sums[blockIdx.x];
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k)
-    if (base + k < n) a[base + k] += add;
+  if (total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total_out = carry + tot;
 }
 
 static cudaError_t excl_scan(uint32_t* a, long long n, uint32_t* sums, uint32_t* total,
@@ -363,16 +375,12 @@ static cudaError_t excl_scan(uint32_t* a, long long n, uint32_t* sums, uint32_t*
   if (n <= 0) return cudaSuccess;
   int nb = (int)((n + kScanTile - 1) / kScanTile);
   {
-    NEXEL_PROF("scan_partial", st);
-    k_scan_partial<<<nb, 256, 0, st>>>(a, n, sums);
+    NEXEL_PROF("scan_reduce", st);
+    k_scan_reduce<<<nb, 256, 0, st>>>(a, n, sums);
   }
   {
-    NEXEL_PROF("scan_sums", st);
-    k_scan_sums<<<1, 1024, 0, st>>>(sums, nb, total);
-  }
-  {
-    NEXEL_PROF("scan_add", st);
-    k_scan_add<<<nb, 256, 0, st>>>(a, n, sums);
+    NEXEL_PROF("scan_final", st);
+    k_scan_final<<<nb, 256, 0, st>>>(a, n, sums, total);
   }
   return cudaGetLastError();
 }
@@ -382,7 +390,7 @@ static cudaError_t excl_scan(uint32_t* a, long long n, uint32_t* sums, uint32_t*
 // histogram, one exclusive scan over (digit, block), and a scatter that ranks
 // keys stably inside the block (warp match + per-warp digit counts), stages
 // them in shared memory in digit order and writes runs out coalesced.
-template <typename KeyT>
+template <typename KeyT, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const KeyT* __restrict__ keys,
                                                              long long n, int shift, int bits,
                                                              uint32_t* __restrict__ hist,
@@ -391,9 +399,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const KeyT* __restr
   h[threadIdx.x] = 0;
   __syncthreads();
   uint32_t mask = (1u << bits) - 1u;
-  long long base = (long long)blockIdx.x * kSortTile;
+  long long base = (long long)blockIdx.x * (kSortThreads * ITEMS);
 #pragma unroll 4
-  for (int k = 0; k < kSortItems; ++k) {
+  for (int k = 0; k < ITEMS; ++k) {
     long long i = base + (long long)k * kSortThreads + threadIdx.x;
     if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & mask], 1u);
   }
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const KeyT* __restr
   if (threadIdx.x < (1 << bits)) hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-template <typename KeyT, bool kVal>
+template <typename KeyT, bool kVal, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const KeyT* __restrict__ kin, KeyT* __restrict__ kout, const uint32_t* __restrict__ vin,
     uint32_t* __restrict__ vout, long long n, int shift, int bits,
@@ -412,23 +420,23 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   // (digit, warp) then gives every key its place in digit order.
   extern __shared__ __align__(16) unsigned char smem[];
   KeyT* s_key = reinterpret_cast<KeyT*>(smem);
-  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + kSortTile);
+  uint32_t* s_val = reinterpret_cast<uint32_t*>(s_key + (kSortThreads * ITEMS));
   constexpr int kW = kSortThreads / 32;
   __shared__ uint32_t s_start[256], s_w[8];
   __shared__ uint32_t s_wc[kW][256];
   const int nbins = 1 << bits;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long base = (long long)blockIdx.x * kSortTile;
-  const int nloc = (int)min((long long)kSortTile, n - base);
+  const long long base = (long long)blockIdx.x * (kSortThreads * ITEMS);
+  const int nloc = (int)min((long long)(kSortThreads * ITEMS), n - base);
   for (int b = threadIdx.x; b < 256 * kW; b += kSortThreads) (&s_wc[0][0])[b] = 0;
   __syncthreads();
-  KeyT key[kSortItems];
-  uint32_t val[kSortItems], rank[kSortItems];
+  KeyT key[ITEMS];
+  uint32_t val[ITEMS], rank[ITEMS];
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const int li = warp * (32 * kSortItems) + k * 32 + lane;
+  for (int k = 0; k < ITEMS; ++k) {
+    const int li = warp * (32 * ITEMS) + k * 32 + lane;
     const bool valid = li < nloc;
     if (valid) {
       key[k] = kin[base + li];
@@ -459,8 +467,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   s_start[threadIdx.x] = st0;
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const int li = warp * (32 * kSortItems) + k * 32 + lane;
+  for (int k = 0; k < ITEMS; ++k) {
+    const int li = warp * (32 * ITEMS) + k * 32 + lane;
     if (li < nloc) {
       const uint32_t d = (uint32_t)(key[k] >> shift) & mask;
       const uint32_t pos = s_start[d] + s_wc[warp][d] + rank[k];
@@ -480,35 +488,35 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 
 // Sorts n keys (and values when vin != nullptr) on bits [lo, lo + nbits).
 // Returns the index (0 or 1) of the buffer pair that holds the result.
-template <typename KeyT>
+template <typename KeyT, int ITEMS>
 static cudaError_t radix_sort(KeyT* k0, KeyT* k1, uint32_t* v0, uint32_t* v1, long long n, int lo,
                               int nbits, uint32_t* hist, uint32_t* sums, cudaStream_t st,
                               int* which) {
   *which = 0;
   if (n <= 1 || nbits <= 0) return cudaSuccess;
-  int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+  int nblocks = (int)((n + (kSortThreads * ITEMS) - 1) / (kSortThreads * ITEMS));
   KeyT* kin = k0; KeyT* kout = k1;
   uint32_t* vin = v0; uint32_t* vout = v1;
-  size_t smem = (size_t)kSortTile * (sizeof(KeyT) + (v0 ? sizeof(uint32_t) : 0));
+  size_t smem = (size_t)(kSortThreads * ITEMS) * (sizeof(KeyT) + (v0 ? sizeof(uint32_t) : 0));
   for (int b = 0; b < nbits; b += 8) {
     int bits = std::min(8, nbits - b);
     int shift = lo + b;
     {
       NEXEL_PROF("radix_hist", st);
-      k_radix_hist<KeyT><<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, bits, hist, nblocks);
+      k_radix_hist<KeyT, ITEMS><<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, bits, hist, nblocks);
     }
     cudaError_t e = excl_scan(hist, (long long)(1 << bits) * nblocks, sums, nullptr, st);
     if (e != cudaSuccess) return e;
     if (v0) {
       {
         NEXEL_PROF("radix_scatter", st);
-        k_radix_scatter<KeyT, true><<<nblocks, kSortThreads, smem, st>>>(kin, kout, vin, vout, n,
+        k_radix_scatter<KeyT, true, ITEMS><<<nblocks, kSortThreads, smem, st>>>(kin, kout, vin, vout, n,
                                                                           shift, bits, hist, nblocks);
       }
     } else {
       {
         NEXEL_PROF("radix_scatter", st);
-        k_radix_scatter<KeyT, false><<<nblocks, kSortThreads, smem, st>>>(
+        k_radix_scatter<KeyT, false, ITEMS><<<nblocks, kSortThreads, smem, st>>>(
             kin, kout, nullptr, nullptr, n, shift, bits, hist, nblocks);
       }
     }
@@ -538,6 +546,14 @@ __global__ void k_permute(int N, const uint32_t* __restrict__ did, const float4*
   offs[r] = count[id];
 }
 
+// (k / nx, k % nx) for the small tile counts of one rectangle (k < 2^22),
+// exact through the float reciprocal: (k + 1/2) / nx stays at least
+// 1 / (2 nx) from an integer.
+__device__ __forceinline__ int2 rect_tile(int k, int nx, float inv_nx) {
+  const int q = __float2int_rz(((float)k + 0.5f) * inv_nx);
+  return make_int2(k - q * nx, q);
+}
+
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int rank_bits,
                                                    const uint32_t* __restrict__ did,
@@ -559,6 +575,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
   const uint2 rc = rect[id];
   const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
   const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
+  const float inv_nx = 1.f / (float)nx;
   size_t o = offs[r];
   if (nt <= 128) {
     const uint4 mq = tmask[id];
@@ -568,8 +585,8 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
       if (32 * i >= nt) break;
       const unsigned m = mw[i];
       if ((m >> lane) & 1u) {
-        const int k = 32 * i + lane;
-        const KeyT tile = (KeyT)((ty0 + k / nx) * c.tiles_x + tx0 + k % nx);
+        const int2 t2 = rect_tile(32 * i + lane, nx, inv_nx);
+        const KeyT tile = (KeyT)((ty0 + t2.y) * c.tiles_x + tx0 + t2.x);
         keys[o + __popc(m & ((1u << lane) - 1u))] = (tile << rank_bits) | (KeyT)r;
       }
       o += __popc(m);
@@ -579,7 +596,8 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
   const TileConic kc = load_conic(conic, id);
   for (int b = 0; b < nt; b += 32) {
     const int k = b + lane;
-    const int tx = tx0 + k % nx, ty = ty0 + k / nx;
+    const int2 t2 = rect_tile(k, nx, inv_nx);
+    const int tx = tx0 + t2.x, ty = ty0 + t2.y;
     const bool hit = k < nt && tile_may_hit(kc, tx, ty, c.W, c.H);
     const unsigned m = __ballot_sync(0xffffffffu, hit);
     if (hit) {
@@ -604,6 +622,7 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
   const uint2 rc = rect[i];
   const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
   const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
+  const float inv_nx = 1.f / (float)nx;
   const TileConic kc = load_conic(conic, (uint32_t)i);
   uint32_t n = 0;
   if (nt <= 128) {
@@ -611,7 +630,8 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const int k = 32 * w + lane;
-      const bool hit = k < nt && tile_may_hit(kc, tx0 + k % nx, ty0 + k / nx, c.W, c.H);
+      const int2 t2 = rect_tile(k, nx, inv_nx);
+      const bool hit = k < nt && tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H);
       mw[w] = __ballot_sync(0xffffffffu, hit);
       n += __popc(mw[w]);
     }
@@ -621,8 +641,10 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
     }
     return;
   }
-  for (int k = lane; k < nt; k += 32)
-    n += tile_may_hit(kc, tx0 + k % nx, ty0 + k / nx, c.W, c.H) ? 1u : 0u;
+  for (int k = lane; k < nt; k += 32) {
+    const int2 t2 = rect_tile(k, nx, inv_nx);
+    n += tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H) ? 1u : 0u;
+  }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) n += __shfl_xor_sync(0xffffffffu, n, d);
   if (lane == 0) count[i] = n;
@@ -664,7 +686,9 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
 
 cudaError_t launch_depth_sort(int N, char* ws, const WsLayout& L, cudaStream_t st) {
   int which = 0;
-  cudaError_t e = radix_sort<uint32_t>((uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.dkey1),
+  // the depth sort (N keys) uses 1024-key tiles, for parallelism at a few
+  // hundred thousand surfels
+  cudaError_t e = radix_sort<uint32_t, kSortItemsDepth>((uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.dkey1),
                                        (uint32_t*)(ws + L.did0), (uint32_t*)(ws + L.did1), N, 0,
                                        32, (uint32_t*)(ws + L.hist), (uint32_t*)(ws + L.scan_sums),
                                        st, &which);
@@ -704,7 +728,7 @@ static cudaError_t binning_t(const DevCam& c, int N, long long n_inst, char* ws,
         (const uint4*)(ws + L.tmask), (uint32_t*)(ws + L.offs), (uint32_t*)(ws + L.count), k0);
   }
   int which = 0;
-  cudaError_t e = radix_sort<KeyT>(k0, k1, nullptr, nullptr, n_inst, rb, L.tile_bits,
+  cudaError_t e = radix_sort<KeyT, kSortItems>(k0, k1, nullptr, nullptr, n_inst, rb, L.tile_bits,
                                    (uint32_t*)(ws + L.hist), (uint32_t*)(ws + L.scan_sums), st,
                                    &which);
   if (e != cudaSuccess) return e;

@@ -19,7 +19,8 @@ constexpr int kRecF4 = 5;                    // packed surfel record: 5 float4
 constexpr int kAuxF4 = 4;                    // camera-space frame for the backward
 constexpr int kGradStride = 20;              // per-surfel gradient record (floats)
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 16;                        // instance (tile) sort
+constexpr int kSortItemsDepth = 4;                    // depth sort of the surfels
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort block
 constexpr int kScanItems = 8;
 constexpr int kScanTile = 256 * kScanItems;
