@@ -261,6 +261,181 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad_f32(long long S, const float*
   }
 }
 
+// Register-tiled form for H1 = 64 (the 16-64-3 and 32-64-64-3 MLPs): chunks
+// of 64 samples; every GEMM of the chunk (forward recompute, deltas, weight
+// gradients) gives each of the 256 threads a 4 x (N / 16) tile of outputs,
+// so one k step costs 4 + N / 16 shared loads for 4 N / 16 FMAs.  The
+// weight-gradient tiles stay in registers across all chunks of the CTA.
+namespace wg {
+constexpr int kR = 64;  // samples per chunk
+// C[m][n] = sum_k A(m, k) B(n, k), M = 64, thread (ty, tx) = (t / 16, t % 16)
+// owns rows 4 ty .. 4 ty + 3 and columns TN tx .. TN tx + TN - 1.
+template <int N, int K, typename FA, typename FB>
+__device__ __forceinline__ void gemm(FA a, FB b, float (&acc)[4][N / 16]) {
+  constexpr int TN = N / 16;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    float av[4], bv[TN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) av[i] = a(4 * ty + i, k);
+#pragma unroll
+    for (int j = 0; j < TN; ++j) bv[j] = b(TN * tx + j, k);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+template <int N>
+__device__ __forceinline__ void zero(float (&acc)[4][N / 16]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < N / 16; ++j) acc[i][j] = 0.f;
+}
+}  // namespace wg
+
+template <int IN, int H1, int H2>
+__global__ void __launch_bounds__(256, 2) k_mlp_wgrad_f32_tiled(long long S,
+                                                                 const float* __restrict__ w,
+                                                                 const float* __restrict__ feat,
+                                                                 const float4* __restrict__ gtex,
+                                                                 float* __restrict__ d_mlp) {
+  static_assert(H1 == 64 && (H2 == 0 || H2 == 64) && IN % 16 == 0, "tiled shapes");
+  using A = MlpArch<IN, H1, H2>;
+  constexpr int HL = (H2 > 0) ? H2 : H1;
+  constexpr int R = wg::kR;
+  constexpr int PX = IN + 1, PH = 64 + 1;  // padded row strides
+  constexpr int PW1 = IN + 1, PW2 = H1 + 1;  // padded weight rows (no bank conflicts)
+  constexpr int kWs = H1 * PW1 + H2 * PW2 + 3 * HL;
+  extern __shared__ __align__(16) float sm[];
+  float* sW = sm;                       // weights, rows padded
+  float* sX = sW + kWs;                 // R x PX
+  float* sH1 = sX + R * PX;             // R x PH
+  float* sH2 = sH1 + R * PH;            // R x PH (two hidden layers)
+  float* sD3 = sH2 + R * PH;            // R x 4
+  float* sDL = sD3 + R * 4;             // R x PH: delta of the last hidden layer
+  float* sD1 = sDL + R * PH;            // R x PH: delta of h1 (two hidden layers)
+  for (int k = threadIdx.x; k < H1 * IN; k += blockDim.x) sW[(k / IN) * PW1 + k % IN] = w[k];
+  for (int k = threadIdx.x; k < H2 * H1; k += blockDim.x)
+    sW[H1 * PW1 + (k / H1) * PW2 + k % H1] = w[H1 * IN + k];
+  for (int k = threadIdx.x; k < 3 * HL; k += blockDim.x)
+    sW[H1 * PW1 + H2 * PW2 + k] = w[A::kOffLast + k];
+  const float* W1 = sW;                          // [H1][PW1]
+  const float* W2 = sW + H1 * PW1;               // [H2][PW2]
+  const float* W3 = sW + H1 * PW1 + H2 * PW2;    // [3][HL]
+  const float* sHL = (H2 > 0) ? sH2 : sH1;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  // weight-gradient tiles: dW2 (or dW1 when one hidden layer) as 64 x 64,
+  // dW1 as 64 x IN (two hidden layers), dW3 entry per thread
+  float g2[4][64 / 16], g1[4][IN / 16];
+  wg::zero<64>(g2);
+  wg::zero<IN>(g1);
+  float g3 = 0.f;
+  const long long n_chunks = (S + R - 1) / R;
+  for (long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    const long long s0 = ch * R;
+    __syncthreads();
+    for (int k = threadIdx.x; k < R * IN; k += 256) {
+      const int r = k / IN, i = k % IN;
+      sX[r * PX + i] = (s0 + r < S) ? feat[s0 * IN + k] : 0.f;
+    }
+    for (int r = threadIdx.x; r < R; r += 256) {
+      const float4 g = (s0 + r < S) ? gtex[s0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sD3[4 * r] = g.x; sD3[4 * r + 1] = g.y; sD3[4 * r + 2] = g.z; sD3[4 * r + 3] = 0.f;
+    }
+    __syncthreads();
+    {  // h1 = relu(X W1^T)
+      float acc[4][64 / 16];
+      wg::zero<64>(acc);
+      wg::gemm<64, IN>([&](int m, int k) { return sX[m * PX + k]; },
+                       [&](int n, int k) { return W1[n * PW1 + k]; }, acc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sH1[(4 * ty + i) * PH + 4 * tx + j] = fmaxf(acc[i][j], 0.f);
+    }
+    __syncthreads();
+    if constexpr (H2 > 0) {  // h2 = relu(h1 W2^T)
+      float acc[4][64 / 16];
+      wg::zero<64>(acc);
+      wg::gemm<64, H1>([&](int m, int k) { return sH1[m * PH + k]; },
+                       [&](int n, int k) { return W2[n * PW2 + k]; }, acc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sH2[(4 * ty + i) * PH + 4 * tx + j] = fmaxf(acc[i][j], 0.f);
+      __syncthreads();
+    }
+    // delta of the last hidden layer: (W3^T d3) * [h > 0]
+    for (int k = threadIdx.x; k < R * HL; k += 256) {
+      const int r = k / HL, c = k % HL;
+      const float v = W3[c] * sD3[4 * r] + W3[HL + c] * sD3[4 * r + 1] + W3[2 * HL + c] * sD3[4 * r + 2];
+      sDL[r * PH + c] = sHL[r * PH + c] > 0.f ? v : 0.f;
+    }
+    __syncthreads();
+    const float* sDH1 = sDL;  // delta of h1
+    if constexpr (H2 > 0) {  // d1 = (d2 W2) * [h1 > 0]
+      float acc[4][64 / 16];
+      wg::zero<64>(acc);
+      wg::gemm<64, H2>([&](int m, int k) { return sDL[m * PH + k]; },
+                       [&](int n, int k) { return W2[k * PW2 + n]; }, acc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m = 4 * ty + i, n = 4 * tx + j;
+          sD1[m * PH + n] = sH1[m * PH + n] > 0.f ? acc[i][j] : 0.f;
+        }
+      __syncthreads();
+      sDH1 = sD1;
+      // dW2[o][i] += sum_r d2[r][o] h1[r][i]
+      wg::gemm<64, R>([&](int m, int k) { return sDL[k * PH + m]; },
+                      [&](int n, int k) { return sH1[k * PH + n]; }, g2);
+    }
+    // dW1[o][i] += sum_r d1[r][o] x[r][i]
+    if constexpr (H2 > 0) {
+      wg::gemm<IN, R>([&](int m, int k) { return sDH1[k * PH + m]; },
+                      [&](int n, int k) { return sX[k * PX + n]; }, g1);
+    } else {
+      wg::gemm<IN, R>([&](int m, int k) { return sDL[k * PH + m]; },
+                      [&](int n, int k) { return sX[k * PX + n]; }, g1);
+    }
+    // dW3[o][i] += sum_r d3[r][o] h_last[r][i]
+    if (threadIdx.x < 3 * HL) {
+      const int o = threadIdx.x / HL, i = threadIdx.x % HL;
+      float v = g3;
+#pragma unroll 8
+      for (int r = 0; r < R; ++r) v = fmaf(sD3[4 * r + o], sHL[r * PH + i], v);
+      g3 = v;
+    }
+  }
+  // one atomic per owned entry
+  if constexpr (H2 > 0) {
+    float* dW2 = d_mlp + H1 * IN;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) atomicAdd(dW2 + (4 * ty + i) * H1 + 4 * tx + j, g2[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < IN / 16; ++j)
+      atomicAdd(d_mlp + (4 * ty + i) * IN + (IN / 16) * tx + j, g1[i][j]);
+  if (threadIdx.x < 3 * HL) atomicAdd(d_mlp + A::kOffLast + threadIdx.x, g3);
+}
+
+template <int IN, int H1, int H2>
+size_t wgrad_smem_f32_tiled() {
+  using A = MlpArch<IN, H1, H2>;
+  constexpr int R = wg::kR;
+  constexpr int HL = (H2 > 0) ? H2 : H1;
+  (void)sizeof(A);
+  return sizeof(float) * (H1 * (IN + 1) + H2 * (H1 + 1) + 3 * HL + R * (IN + 1) + 4 * R * 65 + R * 4);
+}
+
 template <int IN, int H1, int H2>
 size_t wgrad_smem_f32() {
   using A = MlpArch<IN, H1, H2>;
@@ -311,6 +486,21 @@ cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
                       (const float2*)(bws + B.gin),
                       (float*)(bws + B.ddepth), d_table, st);
   if (e != cudaSuccess || !d_mlp) return e;
+  if constexpr (H1 == 64) {
+    const size_t smem = wgrad_smem_f32_tiled<IN, H1, H2>();
+    e = cudaFuncSetAttribute(k_mlp_wgrad_f32_tiled<IN, H1, H2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long chunks = (S + wg::kR - 1) / wg::kR;
+    const unsigned grid = (unsigned)std::min<long long>(chunks, 2LL * nsm);
+    NEXEL_PROF("mlp_wgrad_f32", st);
+    k_mlp_wgrad_f32_tiled<IN, H1, H2><<<grid, 256, smem, st>>>(
+        S, fd.w, (float*)(bws + B.feat), (float4*)(bws + B.gtex), d_mlp);
+    return cudaGetLastError();
+  }
   size_t smem = wgrad_smem_f32<IN, H1, H2>();
   e = cudaFuncSetAttribute(k_mlp_wgrad_f32<IN, H1, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
