@@ -13,6 +13,11 @@
 // and forms dL/dD), the features and the texture gradient in the workspace,
 // from which a second kernel forms the MLP weight gradients (a reduction
 // over all samples) with per-thread register accumulators.
+//
+// The MLPs with 64-wide hidden layers use the chunked forms further below
+// instead (register-tiled SIMT GEMMs over 64-row chunks, the weight
+// gradients formed in the same backward kernel); the per-sample kernels
+// serve the 8-16-3 MLP.
 #pragma once
 
 #include "common.cuh"
@@ -261,11 +266,9 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad_f32(long long S, const float*
   }
 }
 
-// Register-tiled form for H1 = 64 (the 16-64-3 and 32-64-64-3 MLPs): chunks
-// of 64 samples; every GEMM of the chunk (forward recompute, deltas, weight
-// gradients) gives each of the 256 threads a 4 x (N / 16) tile of outputs,
-// so one k step costs 4 + N / 16 shared loads for 4 N / 16 FMAs.  The
-// weight-gradient tiles stay in registers across all chunks of the CTA.
+// Register-tiled SIMT GEMM for the chunked forms below: every GEMM of a
+// 64-row chunk gives each of the 256 threads a 4 x (N / 16) tile of
+// outputs, so one k step costs 4 + N / 16 shared loads for 4 N / 16 FMAs.
 namespace wg {
 constexpr int kR = 64;  // samples per chunk
 // C[m][n] = sum_k A(m, k) B(n, k), M = 64, thread (ty, tx) = (t / 16, t % 16)
@@ -297,90 +300,269 @@ __device__ __forceinline__ void zero(float (&acc)[4][N / 16]) {
 }  // namespace wg
 
 template <int IN, int H1, int H2>
-__global__ void __launch_bounds__(256, 2) k_mlp_wgrad_f32_tiled(long long S,
-                                                                 const float* __restrict__ w,
-                                                                 const float* __restrict__ feat,
-                                                                 const float4* __restrict__ gtex,
-                                                                 float* __restrict__ d_mlp) {
-  static_assert(H1 == 64 && (H2 == 0 || H2 == 64) && IN % 16 == 0, "tiled shapes");
+size_t wgrad_smem_f32() {
   using A = MlpArch<IN, H1, H2>;
-  constexpr int HL = (H2 > 0) ? H2 : H1;
-  constexpr int R = wg::kR;
-  constexpr int PX = IN + 1, PH = 64 + 1;  // padded row strides
-  constexpr int PW1 = IN + 1, PW2 = H1 + 1;  // padded weight rows (no bank conflicts)
-  constexpr int kWs = H1 * PW1 + H2 * PW2 + 3 * HL;
-  extern __shared__ __align__(16) float sm[];
-  float* sW = sm;                       // weights, rows padded
-  float* sX = sW + kWs;                 // R x PX
-  float* sH1 = sX + R * PX;             // R x PH
-  float* sH2 = sH1 + R * PH;            // R x PH (two hidden layers)
-  float* sD3 = sH2 + R * PH;            // R x 4
-  float* sDL = sD3 + R * 4;             // R x PH: delta of the last hidden layer
-  float* sD1 = sDL + R * PH;            // R x PH: delta of h1 (two hidden layers)
-  for (int k = threadIdx.x; k < H1 * IN; k += blockDim.x) sW[(k / IN) * PW1 + k % IN] = w[k];
+  constexpr int kChunk = 32;
+  constexpr int H2s = H2 > 0 ? H2 : 1;
+  return sizeof(float) * (A::kWeights + kChunk * (IN + H1 + H2s + 4 + H2s + H1));
+}
+
+// ------------------------------------------- chunked forms for H1 = 64
+// The 16-64-3 and 32-64-64-3 MLPs run over chunks of 64 rows (RC = K
+// floor(64 / K) samples, whole pixels): the features (gathered, or read back
+// in a training step's backward) go to shared memory and every layer is a
+// register-tiled SIMT GEMM (wg::gemm).  The backward also forms the MLP
+// weight gradients (tiles in registers across all chunks of the CTA).
+namespace f32c {
+constexpr int kPH = 65;  // padded row stride of 64-wide activation tiles
+
+// Weights, rows padded: W1 [H1][IN + 1], W2 [H2][H1 + 1], W3 [3][HL].
+template <int IN, int H1, int H2>
+struct Ws {
+  static constexpr int HL = H2 > 0 ? H2 : H1;
+  static constexpr int P1 = IN + 1, P2 = H1 + 1;
+  static constexpr int o2 = H1 * P1, o3 = o2 + H2 * P2, total = o3 + 3 * HL;
+};
+template <int IN, int H1, int H2>
+__device__ __forceinline__ void load_weights(const float* __restrict__ w, float* sW) {
+  using W = Ws<IN, H1, H2>;
+  using A = MlpArch<IN, H1, H2>;
+  for (int k = threadIdx.x; k < H1 * IN; k += blockDim.x) sW[(k / IN) * W::P1 + k % IN] = w[k];
   for (int k = threadIdx.x; k < H2 * H1; k += blockDim.x)
-    sW[H1 * PW1 + (k / H1) * PW2 + k % H1] = w[H1 * IN + k];
-  for (int k = threadIdx.x; k < 3 * HL; k += blockDim.x)
-    sW[H1 * PW1 + H2 * PW2 + k] = w[A::kOffLast + k];
-  const float* W1 = sW;                          // [H1][PW1]
-  const float* W2 = sW + H1 * PW1;               // [H2][PW2]
-  const float* W3 = sW + H1 * PW1 + H2 * PW2;    // [3][HL]
-  const float* sHL = (H2 > 0) ? sH2 : sH1;
+    sW[W::o2 + (k / H1) * W::P2 + k % H1] = w[H1 * IN + k];
+  for (int k = threadIdx.x; k < 3 * W::HL; k += blockDim.x) sW[W::o3 + k] = w[A::kOffLast + k];
+}
+
+// Features of row `row` for the levels of quarter q (0..3) into sX.
+template <int IN, typename TT>
+__device__ __forceinline__ void gather_row(const DevCam& c, const FieldDev& f, float* sX, int row,
+                                           int q, bool valid, long long p, float D) {
+  constexpr int LQ = IN / 8;  // levels per quarter (F = 2)
+  float3 x = make_float3(0.f, 0.f, 0.f);
+  if (valid) {
+    const float3 d = pixel_dir(c, (int)(p % c.W), (int)(p / c.W));
+    x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
+  }
+  const TT* tab = reinterpret_cast<const TT*>(f.table);
+  const size_t T = (size_t)f.mask + 1;
+#pragma unroll
+  for (int lq = 0; lq < LQ; ++lq) {
+    const int l = q * LQ + lq;
+    float ax = 0.f, ay = 0.f, dw = 0.f;
+    if (valid) {
+      const float sl = f.s[l];
+      const float gx = sl * x.x, gy = sl * x.y, gz = sl * x.z;
+      const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
+      const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
+      const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
+      const TT* tl = tab + (size_t)l * T * 2;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        const float w = (dx ? rx : 1.f - rx) * (dy ? ry : 1.f - ry) * (dz ? rz : 1.f - rz);
+        const float2 e = load_entry<TT>(tl, hash3(cx + dx, cy + dy, cz + dz, f.mask));
+        ax = fmaf(w, e.x, ax);
+        ay = fmaf(w, e.y, ay);
+      }
+      dw = downweight(f.focal, sl, D);
+    }
+    sX[row * (IN + 1) + 2 * l] = dw * ax;
+    sX[row * (IN + 1) + 2 * l + 1] = dw * ay;
+  }
+}
+
+// h = relu(A W^T) for a 64-row tile A (stride pa) and W [NOUT][K] (stride pw).
+template <int NOUT, int K>
+__device__ __forceinline__ void dense_relu(const float* sA, int pa, const float* sWl, int pw,
+                                           float* sOut) {
+  float acc[4][NOUT / 16];
+  wg::zero<NOUT>(acc);
+  wg::gemm<NOUT, K>([&](int m, int k) { return sA[m * pa + k]; },
+                    [&](int n, int k) { return sWl[n * pw + k]; }, acc);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  // weight-gradient tiles: dW2 (or dW1 when one hidden layer) as 64 x 64,
-  // dW1 as 64 x IN (two hidden layers), dW3 entry per thread
-  float g2[4][64 / 16], g1[4][IN / 16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < NOUT / 16; ++j)
+      sOut[(4 * ty + i) * kPH + (NOUT / 16) * tx + j] = fmaxf(acc[i][j], 0.f);
+}
+}  // namespace f32c
+
+template <int IN, int H1, int H2, typename TT>
+__global__ void __launch_bounds__(256, 2) k_tex_fwd_f32c(
+    DevCam c, FieldDev f, int K, int RC, long long n_chunks, float bg0, float bg1, float bg2,
+    const float* __restrict__ notex, const float* __restrict__ weights,
+    const int* __restrict__ ids, const float* __restrict__ depths,
+    const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures) {
+  using W = f32c::Ws<IN, H1, H2>;
+  constexpr int HL = W::HL, PH = f32c::kPH;
+  extern __shared__ __align__(16) float sm[];
+  float* sW = sm;
+  float* sX = sW + W::total;            // 64 x (IN + 1)
+  float* sH1 = sX + 64 * (IN + 1);      // 64 x PH
+  float* sH2 = sH1 + 64 * PH;           // 64 x PH (two hidden layers)
+  float* sT = sH2 + (H2 > 0 ? 64 * PH : 0);  // 64 x 4: textures of the rows
+  f32c::load_weights<IN, H1, H2>(f.w, sW);
+  const long long P = (long long)c.W * c.H, S = P * K;
+  const int row = threadIdx.x & 63, q = threadIdx.x >> 6;
+  for (long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    const long long s0 = ch * RC;
+    __syncthreads();
+    {
+      const long long s = s0 + row;
+      const bool in_rows = row < RC && s < S;
+      const bool valid = in_rows && ids[s] >= 0;
+      const float D = valid ? depths[s] : 1.f;
+      f32c::gather_row<IN, TT>(c, f, sX, row, q, valid, s / K, D);
+      if (f.feat_mode == 1 && in_rows) {
+        float* fo = reinterpret_cast<float*>(f.feat) + s * IN + q * (IN / 4);
+#pragma unroll
+        for (int k = 0; k < IN / 4; ++k) fo[k] = sX[row * (IN + 1) + q * (IN / 4) + k];
+      }
+    }
+    __syncthreads();
+    f32c::dense_relu<H1, IN>(sX, IN + 1, sW, W::P1, sH1);
+    __syncthreads();
+    if constexpr (H2 > 0) {
+      f32c::dense_relu<H2, H1>(sH1, PH, sW + W::o2, W::P2, sH2);
+      __syncthreads();
+    }
+    const float* sHL = H2 > 0 ? sH2 : sH1;
+    if (threadIdx.x < 3 * 64) {  // textures T = W3 h_last
+      const int r = threadIdx.x / 3, ch3 = threadIdx.x % 3;
+      const float* w3 = sW + W::o3 + ch3 * HL;
+      float v = 0.f;
+#pragma unroll 8
+      for (int i = 0; i < HL; ++i) v = fmaf(w3[i], sHL[r * PH + i], v);
+      const long long s = s0 + r;
+      const bool valid = r < RC && s < S && ids[s] >= 0;
+      v = valid ? v : 0.f;
+      sT[4 * r + ch3] = v;
+      if (r < RC && s < S) textures[3 * s + ch3] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < RC / K) {  // composite (Eq. 6) per pixel of the chunk
+      const long long p = s0 / K + threadIdx.x;
+      if (p < P) {
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+        for (int j = 0; j < K; ++j) {
+          const int r = threadIdx.x * K + j;
+          const float wj = weights[p * K + j];
+          c0 = fmaf(wj, sT[4 * r], c0);
+          c1 = fmaf(wj, sT[4 * r + 1], c1);
+          c2 = fmaf(wj, sT[4 * r + 2], c2);
+        }
+        const float Tf = T_final[p];
+        image[3 * p] = notex[3 * p] + c0 + Tf * bg0;
+        image[3 * p + 1] = notex[3 * p + 1] + c1 + Tf * bg1;
+        image[3 * p + 2] = notex[3 * p + 2] + c2 + Tf * bg2;
+      }
+    }
+  }
+}
+
+template <int IN, int H1, int H2, typename TT>
+__global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
+    DevCam c, FieldDev f, int K, int KP, int RC, long long n_chunks,
+    const float* __restrict__ weights, const int* __restrict__ ids,
+    const float* __restrict__ depths, const float* __restrict__ d_image,
+    const float* __restrict__ d_weights, const float* __restrict__ d_textures,
+    float* __restrict__ dweff, float2* __restrict__ gin, float* __restrict__ d_mlp) {
+  using W = f32c::Ws<IN, H1, H2>;
+  using A = MlpArch<IN, H1, H2>;
+  constexpr int HL = W::HL, PH = f32c::kPH, PX = IN + 1;
+  extern __shared__ __align__(16) float sm[];
+  float* sW = sm;
+  float* sX = sW + W::total;                  // 64 x PX
+  float* sH1 = sX + 64 * PX;                  // 64 x PH
+  float* sH2 = sH1 + 64 * PH;                 // 64 x PH (two hidden layers)
+  float* sDL = sH2 + (H2 > 0 ? 64 * PH : 0);  // 64 x PH: delta of the last hidden layer
+  float* sD1 = sDL + 64 * PH;                 // 64 x PH: delta of h1 (two hidden layers)
+  float* sG = sD1 + (H2 > 0 ? 64 * PH : 0);   // 64 x 8: texture gradient, dL/dC, dL/dW
+  float* sGin = sH1;                          // 64 x PX: feature gradient (after h1 is used)
+  f32c::load_weights<IN, H1, H2>(f.w, sW);
+  const float* W1 = sW;
+  const float* W2 = sW + W::o2;
+  const float* W3 = sW + W::o3;
+  const long long P = (long long)c.W * c.H, S = P * K;
+  const long long R = gin_stride(P * KP);
+  const int row = threadIdx.x & 63, q = threadIdx.x >> 6;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float g2[4][4], g1[4][IN / 16];
   wg::zero<64>(g2);
   wg::zero<IN>(g1);
   float g3 = 0.f;
-  const long long n_chunks = (S + R - 1) / R;
+  const float* sHL = H2 > 0 ? sH2 : sH1;
   for (long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
-    const long long s0 = ch * R;
+    const long long s0 = ch * RC;
     __syncthreads();
-    for (int k = threadIdx.x; k < R * IN; k += 256) {
-      const int r = k / IN, i = k % IN;
-      sX[r * PX + i] = (s0 + r < S) ? feat[s0 * IN + k] : 0.f;
-    }
-    for (int r = threadIdx.x; r < R; r += 256) {
-      const float4 g = (s0 + r < S) ? gtex[s0 + r] : make_float4(0.f, 0.f, 0.f, 0.f);
-      sD3[4 * r] = g.x; sD3[4 * r + 1] = g.y; sD3[4 * r + 2] = g.z; sD3[4 * r + 3] = 0.f;
+    {
+      const long long s = s0 + row;
+      const bool in_rows = row < RC && s < S;
+      const bool valid = in_rows && ids[s] >= 0;
+      if (f.feat_mode == 2) {  // the forward of this step left the features
+        const float* fi = reinterpret_cast<const float*>(f.feat) + s * IN + q * (IN / 4);
+#pragma unroll
+        for (int k = 0; k < IN / 4; ++k) sX[row * PX + q * (IN / 4) + k] = in_rows ? fi[k] : 0.f;
+      } else {
+        const float D = valid ? depths[s] : 1.f;
+        f32c::gather_row<IN, TT>(c, f, sX, row, q, valid, s / K, D);
+      }
+      if (q == 0) {
+        float gT0 = 0.f, gT1 = 0.f, gT2 = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f, dwx = 0.f;
+        if (valid) {
+          const long long p = s / K;
+          const float wj = weights[s];
+          dc0 = d_image[3 * p]; dc1 = d_image[3 * p + 1]; dc2 = d_image[3 * p + 2];
+          gT0 = wj * dc0; gT1 = wj * dc1; gT2 = wj * dc2;
+          if (d_textures) {
+            gT0 += d_textures[3 * s]; gT1 += d_textures[3 * s + 1]; gT2 += d_textures[3 * s + 2];
+          }
+          if (d_weights) dwx = d_weights[s];
+        }
+        float* g = sG + 8 * row;
+        g[0] = gT0; g[1] = gT1; g[2] = gT2; g[3] = dc0; g[4] = dc1; g[5] = dc2; g[6] = dwx;
+        g[7] = valid ? 1.f : 0.f;
+      }
     }
     __syncthreads();
-    {  // h1 = relu(X W1^T)
-      float acc[4][64 / 16];
-      wg::zero<64>(acc);
-      wg::gemm<64, IN>([&](int m, int k) { return sX[m * PX + k]; },
-                       [&](int n, int k) { return W1[n * PW1 + k]; }, acc);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) sH1[(4 * ty + i) * PH + 4 * tx + j] = fmaxf(acc[i][j], 0.f);
-    }
+    f32c::dense_relu<H1, IN>(sX, PX, W1, W::P1, sH1);
     __syncthreads();
-    if constexpr (H2 > 0) {  // h2 = relu(h1 W2^T)
-      float acc[4][64 / 16];
-      wg::zero<64>(acc);
-      wg::gemm<64, H1>([&](int m, int k) { return sH1[m * PH + k]; },
-                       [&](int n, int k) { return W2[n * PW2 + k]; }, acc);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) sH2[(4 * ty + i) * PH + 4 * tx + j] = fmaxf(acc[i][j], 0.f);
+    if constexpr (H2 > 0) {
+      f32c::dense_relu<H2, H1>(sH1, PH, W2, W::P2, sH2);
       __syncthreads();
     }
-    // delta of the last hidden layer: (W3^T d3) * [h > 0]
-    for (int k = threadIdx.x; k < R * HL; k += 256) {
-      const int r = k / HL, c = k % HL;
-      const float v = W3[c] * sD3[4 * r] + W3[HL + c] * sD3[4 * r + 1] + W3[2 * HL + c] * sD3[4 * r + 2];
-      sDL[r * PH + c] = sHL[r * PH + c] > 0.f ? v : 0.f;
+    // dL/dW_j = T . dL/dC + dL/dW_j (upstream), T = W3 h_last
+    if (threadIdx.x < 64) {
+      const int r = threadIdx.x;
+      const long long s = s0 + r;
+      if (r < RC && s < S) {
+        const float* g = sG + 8 * r;
+        float T0 = 0.f, T1 = 0.f, T2 = 0.f;
+#pragma unroll 8
+        for (int i = 0; i < HL; ++i) {
+          const float h = sHL[r * PH + i];
+          T0 = fmaf(W3[i], h, T0);
+          T1 = fmaf(W3[HL + i], h, T1);
+          T2 = fmaf(W3[2 * HL + i], h, T2);
+        }
+        dweff[s] = g[7] != 0.f ? T0 * g[3] + T1 * g[4] + T2 * g[5] + g[6] : 0.f;
+      }
+    }
+    // delta of the last hidden layer: (W3^T gT) * [h > 0]
+    for (int k = threadIdx.x; k < 64 * HL; k += 256) {
+      const int r = k / HL, cc = k % HL;
+      const float* g = sG + 8 * r;
+      const float v = W3[cc] * g[0] + W3[HL + cc] * g[1] + W3[2 * HL + cc] * g[2];
+      sDL[r * PH + cc] = sHL[r * PH + cc] > 0.f ? v : 0.f;
     }
     __syncthreads();
     const float* sDH1 = sDL;  // delta of h1
     if constexpr (H2 > 0) {  // d1 = (d2 W2) * [h1 > 0]
-      float acc[4][64 / 16];
+      float acc[4][4];
       wg::zero<64>(acc);
       wg::gemm<64, H2>([&](int m, int k) { return sDL[m * PH + k]; },
-                       [&](int n, int k) { return W2[k * PW2 + n]; }, acc);
+                       [&](int n, int k) { return W2[k * W::P2 + n]; }, acc);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -391,27 +573,44 @@ __global__ void __launch_bounds__(256, 2) k_mlp_wgrad_f32_tiled(long long S,
       __syncthreads();
       sDH1 = sD1;
       // dW2[o][i] += sum_r d2[r][o] h1[r][i]
-      wg::gemm<64, R>([&](int m, int k) { return sDL[k * PH + m]; },
-                      [&](int n, int k) { return sH1[k * PH + n]; }, g2);
+      wg::gemm<64, 64>([&](int m, int k) { return sDL[k * PH + m]; },
+                       [&](int n, int k) { return sH1[k * PH + n]; }, g2);
     }
     // dW1[o][i] += sum_r d1[r][o] x[r][i]
-    if constexpr (H2 > 0) {
-      wg::gemm<IN, R>([&](int m, int k) { return sDH1[k * PH + m]; },
-                      [&](int n, int k) { return sX[k * PX + n]; }, g1);
-    } else {
-      wg::gemm<IN, R>([&](int m, int k) { return sDL[k * PH + m]; },
-                      [&](int n, int k) { return sX[k * PX + n]; }, g1);
-    }
-    // dW3[o][i] += sum_r d3[r][o] h_last[r][i]
+    wg::gemm<IN, 64>([&](int m, int k) { return sDH1[k * PH + m]; },
+                     [&](int n, int k) { return sX[k * PX + n]; }, g1);
+    // dW3[o][i] += sum_r gT[r][o] h_last[r][i]
     if (threadIdx.x < 3 * HL) {
       const int o = threadIdx.x / HL, i = threadIdx.x % HL;
       float v = g3;
 #pragma unroll 8
-      for (int r = 0; r < R; ++r) v = fmaf(sD3[4 * r + o], sHL[r * PH + i], v);
+      for (int r = 0; r < 64; ++r) v = fmaf(sG[8 * r + o], sHL[r * PH + i], v);
       g3 = v;
     }
+    // feature gradient d1 W1 -> sGin (h1 is no longer needed)
+    {
+      float acc[4][IN / 16];
+      wg::zero<IN>(acc);
+      wg::gemm<IN, H1>([&](int m, int k) { return sDH1[m * PH + k]; },
+                       [&](int n, int k) { return W1[k * W::P1 + n]; }, acc);
+      __syncthreads();  // every thread is done reading h1
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < IN / 16; ++j) sGin[(4 * ty + i) * PX + (IN / 16) * tx + j] = acc[i][j];
+    }
+    __syncthreads();
+    // level-major feature gradient, row p KP + j
+    for (int k = threadIdx.x; k < 64 * (IN / 2); k += 256) {
+      const int r = k % 64, l = k / 64;
+      const long long s = s0 + r;
+      if (r < RC && s < S) {
+        const long long rk = (s / K) * KP + s % K;
+        gin[(long long)l * R + rk] = make_float2(sGin[r * PX + 2 * l], sGin[r * PX + 2 * l + 1]);
+      }
+    }
   }
-  // one atomic per owned entry
+  if (!d_mlp) return;
   if constexpr (H2 > 0) {
     float* dW2 = d_mlp + H1 * IN;
 #pragma unroll
@@ -428,20 +627,14 @@ __global__ void __launch_bounds__(256, 2) k_mlp_wgrad_f32_tiled(long long S,
 }
 
 template <int IN, int H1, int H2>
-size_t wgrad_smem_f32_tiled() {
-  using A = MlpArch<IN, H1, H2>;
-  constexpr int R = wg::kR;
-  constexpr int HL = (H2 > 0) ? H2 : H1;
-  (void)sizeof(A);
-  return sizeof(float) * (H1 * (IN + 1) + H2 * (H1 + 1) + 3 * HL + R * (IN + 1) + 4 * R * 65 + R * 4);
+constexpr size_t f32c_fwd_smem() {
+  using W = f32c::Ws<IN, H1, H2>;
+  return sizeof(float) * (W::total + 64 * (IN + 1) + 64 * f32c::kPH * (H2 > 0 ? 2 : 1) + 64 * 4);
 }
-
 template <int IN, int H1, int H2>
-size_t wgrad_smem_f32() {
-  using A = MlpArch<IN, H1, H2>;
-  constexpr int kChunk = 32;
-  constexpr int H2s = H2 > 0 ? H2 : 1;
-  return sizeof(float) * (A::kWeights + kChunk * (IN + H1 + H2s + 4 + H2s + H1));
+constexpr size_t f32c_bwd_smem() {
+  using W = f32c::Ws<IN, H1, H2>;
+  return sizeof(float) * (W::total + 64 * (IN + 1) + 64 * f32c::kPH * (H2 > 0 ? 4 : 2) + 64 * 8);
 }
 
 // --------------------------------------------------------------- dispatch
@@ -450,6 +643,25 @@ cudaError_t tex_fwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
                                const float* notex, const float* weights, const int* ids,
                                const float* depths, const float* T_final, float* image,
                                float* textures, cudaStream_t st) {
+  if constexpr (H1 == 64) {
+    const long long S = (long long)c.W * c.H * s.K;
+    if (S == 0) return cudaSuccess;
+    const int RC = s.K * (64 / s.K);
+    const long long n_chunks = (S + RC - 1) / RC;
+    const size_t smem = f32c_fwd_smem<IN, H1, H2>();
+    cudaError_t e = cudaFuncSetAttribute(k_tex_fwd_f32c<IN, H1, H2, TT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min<long long>(n_chunks, 2LL * nsm);
+    NEXEL_PROF("texture_fwd_f32", st);
+    k_tex_fwd_f32c<IN, H1, H2, TT><<<grid, 256, smem, st>>>(c, fd, s.K, RC, n_chunks, s.bg[0],
+                                                           s.bg[1], s.bg[2], notex, weights, ids,
+                                                           depths, T_final, image, textures);
+    return cudaGetLastError();
+  }
   int KP = 1;
   while (KP < s.K) KP <<= 1;
   long long n = (long long)c.W * c.H * KP;
@@ -473,6 +685,28 @@ cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
   if (S == 0) return cudaSuccess;
   int KP = 1;
   while (KP < s.K) KP <<= 1;
+  if constexpr (H1 == 64) {
+    const int RC = s.K * (64 / s.K);
+    const long long n_chunks = (S + RC - 1) / RC;
+    const size_t smem = f32c_bwd_smem<IN, H1, H2>();
+    cudaError_t e = cudaFuncSetAttribute(k_tex_bwd_f32c<IN, H1, H2, TT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min<long long>(n_chunks, 2LL * nsm);
+    {
+      NEXEL_PROF("texture_bwd_f32", st);
+      k_tex_bwd_f32c<IN, H1, H2, TT><<<grid, 256, smem, st>>>(
+          c, fd, s.K, KP, RC, n_chunks, weights, ids, depths, d_image, d_weights, d_textures,
+          (float*)(bws + B.dweff), (float2*)(bws + B.gin), d_mlp);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_hash_bwd(c, fd, s.K, KP, (long long)c.W * c.H * KP, false, ids, depths,
+                           (const float2*)(bws + B.gin), (float*)(bws + B.ddepth), d_table, st);
+  }
   {
     NEXEL_PROF("texture_bwd_f32", st);
     k_tex_bwd_f32<IN, H1, H2, TT><<<(unsigned)((S + 255) / 256), 256, 0, st>>>(
@@ -486,21 +720,6 @@ cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
                       (const float2*)(bws + B.gin),
                       (float*)(bws + B.ddepth), d_table, st);
   if (e != cudaSuccess || !d_mlp) return e;
-  if constexpr (H1 == 64) {
-    const size_t smem = wgrad_smem_f32_tiled<IN, H1, H2>();
-    e = cudaFuncSetAttribute(k_mlp_wgrad_f32_tiled<IN, H1, H2>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int nsm = 152, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long chunks = (S + wg::kR - 1) / wg::kR;
-    const unsigned grid = (unsigned)std::min<long long>(chunks, 2LL * nsm);
-    NEXEL_PROF("mlp_wgrad_f32", st);
-    k_mlp_wgrad_f32_tiled<IN, H1, H2><<<grid, 256, smem, st>>>(
-        S, fd.w, (float*)(bws + B.feat), (float4*)(bws + B.gtex), d_mlp);
-    return cudaGetLastError();
-  }
   size_t smem = wgrad_smem_f32<IN, H1, H2>();
   e = cudaFuncSetAttribute(k_mlp_wgrad_f32<IN, H1, H2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
