@@ -252,6 +252,37 @@ def test_ragged_image_all_K(dev):
             compare_forward(fw, ref, K, TOL_F32)
 
 
+@pytest.mark.parametrize("mlp", ["f32", "bf16", "f16"])
+def test_ragged_image_all_K_64_wide(dev, mlp):
+    """The 16-64-3 MLP (chunked FP32 kernels, tcgen05 kernels) on an image
+    that is not a multiple of the tile, every K from 1 to 8 (so every padded
+    row count KP, and chunks of K floor(64 / K) samples): forward and
+    backward against the oracle."""
+    sc = synth.make_scene(400, 3, 22, gamma="var")
+    sc.scale *= 2.0
+    fld = synth.make_field(8, 12, 2, (64,), 22, table_std=0.3)
+    cam = synth.front_camera(37, 29)
+    grid = "f32" if mlp == "f32" else "f16"
+    tol = {"f32": TOL_F32, "bf16": TOL_BF16, "f16": TOL_F16}[mlp]
+    P = cam.width * cam.height
+    pix = np.arange(P)
+    for K in range(1, 9):
+        st = synth.Settings(K=K)
+        ref = oracle.render(sc, cam, st, fld, tie_tol=TIE, cell_tol=CELL, relu_tol=RELU)
+        ok = ref["tie"] == 0
+        dI, dW, dT = masked_upstream(P, P, K, pix, ok, seed=40 + K)
+        fw, gg, _ = run_gpu(sc, cam, st, fld, dev, grid=grid, mlp=mlp, d_image=dI, d_weights=dW,
+                            d_textures=dT, cache_features=(K % 2 == 0))
+        compare_forward(fw, ref, K, tol)
+        sel = pix[ok]
+        gr = oracle.render_bwd(sc, cam, st, fld, sel, dI[sel], dW[sel], dT[sel])
+        if mlp == "f32":
+            compare_grads(gg, gr, GRAD_RTOL)
+        else:
+            compare_grads(gg, gr, GRAD_RTOL_BF16 if mlp == "bf16" else GRAD_RTOL_F16,
+                          metric="l2")
+
+
 def test_empty_and_culled_scenes(dev):
     """N = 0, and surfels all behind the camera: image = T_final bg = bg."""
     cam = synth.front_camera(40, 24)
