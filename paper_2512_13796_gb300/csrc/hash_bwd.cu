@@ -13,12 +13,13 @@
 // coarse level would otherwise pile up on the same L2 lines).
 //
 // Atomics: at one level, neighbouring pixels of the same slot share cells
-// once a cell spans a couple of pixels.  Per corner, when that can happen
-// (cell of two pixels or more for some lane), the warp finds runs of
-// consecutive lanes with the same entry (shfl_up + ballot); when there are
-// at most 16 runs it sums each run with a segmented shuffle scan and lets
-// the run's last lane issue one vector atomic.  Otherwise every lane issues
-// its own.
+// once a cell spans a pixel or more.  Per level the warp finds the runs of
+// consecutive lanes in the same cell (shuffles + ballot); per corner it sums
+// each run with a segmented shuffle scan (as many steps as the longest run
+// needs, none when every lane has its own cell) and lets the run's last lane
+// issue one vector atomic per entry.  A run whose successor lies in the
+// x-adjacent cell hands its entries at x + 1 to the successor's entries at
+// x, so they are added once.
 #include "texture_common.cuh"
 
 namespace nexel {
@@ -107,12 +108,11 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     const bool same_prev = __shfl_up_sync(0xffffffffu, same_next, 1) && lane > 0;
     const bool adj_prev = __shfl_up_sync(0xffffffffu, adj_next, 1) && lane > 0;
     const unsigned heads = __ballot_sync(0xffffffffu, !same_prev);
-    // runs of one cell are summed with a segmented scan when there are few
-    // of them; otherwise every lane adds its own values
-    const bool scan = __popc(heads) <= 16;
+    // runs of one cell are summed with a segmented scan whose step count
+    // follows the longest run (no steps when every lane has its own cell)
     const int seg_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
     const int max_len = (int)__reduce_max_sync(0xffffffffu, (unsigned)(lane - seg_start)) + 1;
-    const bool tail = !scan || !same_next;
+    const bool tail = !same_next;
     const float gsx = dw * g.x, gsy = dw * g.y;
     float ax = 0.f, ay = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
 #pragma unroll
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
         const float wyz = wy[dy] * wz[dz];
         float v0x = wx[0] * wyz * gsx, v0y = wx[0] * wyz * gsy;
         float v1x = wx[1] * wyz * gsx, v1y = wx[1] * wyz * gsy;
-        if (scan) seg_scan2(v1x, v1y, lane, seg_start, max_len);
+        seg_scan2(v1x, v1y, lane, seg_start, max_len);
         // the run ending here hands its x + 1 sums to the next run's x entry
         const float px = __shfl_up_sync(0xffffffffu, (tail && adj_next) ? v1x : 0.f, 1);
         const float py = __shfl_up_sync(0xffffffffu, (tail && adj_next) ? v1y : 0.f, 1);
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
           v0x += px;
           v0y += py;
         }
-        if (scan) seg_scan2(v0x, v0y, lane, seg_start, max_len);
+        seg_scan2(v0x, v0y, lane, seg_start, max_len);
         if (valid && tail) {
           atomicAdd(dl + ((hx[0] ^ hyz) & f.mask), make_float2(v0x, v0y));
           if (!adj_next) atomicAdd(dl + ((hx[1] ^ hyz) & f.mask), make_float2(v1x, v1y));
