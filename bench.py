@@ -153,6 +153,50 @@ class Job:
         return out
 
 
+class BatchJob:
+    """The batched form: one training step over 8 views of uneven resolution
+    of a 600k-surfel scene (BF16 form), captured in one CUDA graph, beside
+    the same views through the single-view calls one after another."""
+    WORKLOAD = ("config3: 600k surfels, 8 views 640x480..1920x1080 (8.6 Mpix), K=4, "
+                "hash 16x2^19x2 FP16, MLP 32-64-64-3 BF16")
+
+    def __init__(self, dev):
+        import torch
+        from paper_2512_13796_gb300 import render as R
+        from paper_2512_13796_gb300 import synth
+        self.R = R
+        w = synth.workload(3)
+        self.w = w
+        self.p = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).to(dev)
+                  for k in ("mu", "quat", "scale", "opacity", "gamma", "color")}
+        self.field = R.DeviceField.from_synth(w.field, dev, "f16", "bf16")
+        self.step = R.BatchStep(w.cameras, w.settings, self.field, self.p)
+        g = torch.Generator(device="cpu").manual_seed(7)
+        for d in self.step.d_image:
+            d.copy_(torch.randn(d.shape, generator=g) * 1e-3)
+        self.step.capture()
+        self.pixels = self.step.pixels
+        # the single-view path
+        self.ts = self.field.storage_table()
+        self.ws = [R.Workspace(dev, cap_hint=n + 4096) for n in self.step.n_instances]
+        self.cam_s = [R.camera_struct(c) for c in w.cameras]
+        self.st_s = R.settings_struct(w.settings, "f16", "bf16", cache_features=True)
+        self.grads = None
+
+    def replay(self):
+        self.step.replay()
+
+    def sequential(self):
+        R, p = self.R, self.p
+        for v, cs in enumerate(self.cam_s):
+            out = R.forward(self.ws[v], cs, self.st_s, self.field, self.ts, self.field.weights,
+                            p["mu"], p["quat"], p["scale"], p["opacity"], p["gamma"], p["color"])
+            self.grads = R.backward(self.ws[v], cs, self.st_s, self.field, self.ts,
+                                    self.field.weights, p["mu"], p["quat"], p["scale"],
+                                    p["opacity"], p["gamma"], out, self.step.d_image[v],
+                                    accumulate=v > 0, grads=self.grads)
+
+
 def timed(fn, steps, flush, stream):
     """Per-step CUDA-event times (ms) with an L2 flush before each step."""
     import torch
@@ -276,6 +320,8 @@ def main():
     ap.add_argument("--impl", default="nexels", choices=["nexels", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default=None, help="write per-kernel times here")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched 8-view form (600k surfels)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2],
                     help="2: the headline workload; 1: the 50k-surfel 800x800 case (profiling)")
     args = ap.parse_args()
@@ -410,6 +456,23 @@ def main():
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     e2e_ms = agg([e2e_ms])
 
+    # the batched 8-view form, last (its 600k-surfel scene and 8 views'
+    # buffers are allocated only now), with its own clock samples
+    batch, clk_batch = None, None
+    if not args.no_batch:
+        batch = BatchJob(dev)
+        for _ in range(max(args.warmup, 3)):
+            batch.replay()
+            batch.sequential()
+        barrier()
+        cs = ClockSampler(local)
+        cs.start()
+        nb = max(3, min(args.steps, 10))
+        ms["batch_graph"] = agg(timed(batch.replay, nb, flush, stream))
+        ms["batch_sequential"] = agg(timed(batch.sequential, nb, flush, stream))
+        barrier()
+        clk_batch = cs.stop()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -440,6 +503,16 @@ def main():
                                     "render_fps": 1e3 / ms["f16_fwd"],
                                     "render_ms": ms["f16_fwd"]},
         },
+        "batched": None if batch is None else {
+            "workload": BatchJob.WORKLOAD, "pixels_per_step": batch.pixels,
+            "graph_train_mpix_s": world * batch.pixels / (ms["batch_graph"] * 1e-3) / 1e6,
+            "graph_train_ms": ms["batch_graph"],
+            "sequential_train_mpix_s": world * batch.pixels / (ms["batch_sequential"] * 1e-3) / 1e6,
+            "sequential_train_ms": ms["batch_sequential"],
+            "note": "graph: one CUDA graph per step (device-count preprocess, views as parallel "
+                    "branches, gradients summed); sequential: the single-view calls view after "
+                    "view, each preprocess reading its instance count back to the host",
+            "clocks": clk_batch},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items(),
                                                                         key=lambda kv: -kv[1][0])},
         "kernels_ms_per_step_f32": {k: v[0] / args.steps for k, v in

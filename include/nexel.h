@@ -32,7 +32,8 @@
  *     t equals view depth.
  *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
  *     legacy default stream) except nexel_preprocess, which synchronises the
- *     stream once to read the instance count back to the host.
+ *     stream once to read the instance count back to the host, and
+ *     nexel_read_status.
  *   - Return value: NEXEL_OK (0) or a negative NEXEL_ERR_* code; nothing is
  *     launched when an argument check fails.  nexel_status_string names it.
  */
@@ -183,6 +184,67 @@ int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
                      int accumulate, float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
                      float* d_gamma, float* d_color, float* d_table, float* d_mlp,
                      nexel_stream_t stream);
+
+/* Device-count preprocess: the same work as nexel_preprocess, but the
+ * instance count stays on the device, so nothing synchronises the stream and
+ * the call can be captured in a CUDA graph.  Launches are sized for the
+ * instance capacity ws_bytes gives (nexel_workspace_size); instances beyond
+ * it are dropped, which leaves a partial render and sets the capacity flag
+ * that nexel_read_status reports.  Returns only argument / launch errors. */
+int nexel_preprocess_async(const nexel_camera* cam, const nexel_settings* settings, int N,
+                           const float* mu, const float* quat, const float* scale,
+                           const float* opacity, const float* gamma, const float* color,
+                           void* ws, size_t ws_bytes, nexel_stream_t stream);
+
+/* Batched multi-view training step (a deployment form: the paper renders
+ * one view per call; each view follows the same passages as
+ * nexel_preprocess / nexel_render_fwd / nexel_render_bwd).  n_views cameras
+ * (cams: host array of n_views structs, resolutions may differ) of one
+ * scene.  Every per-view argument is a host array of n_views entries: view
+ * v has its own workspace ws[v] of ws_bytes[v] bytes, its own backward
+ * scratch bwd_ws[v] (bwd_ws_bytes[v]; either array may be NULL when no
+ * view needs scratch) and its own outputs, laid out as in
+ * nexel_render_fwd.  nexel_render_batch_fwd runs the device-count
+ * preprocess and the forward render of every view; nothing synchronises
+ * the stream, so the pair can be captured in one CUDA graph.  The views run
+ * as parallel branches: forked from `stream` onto streams the library owns
+ * (created on the device's first batched call; make that call before a
+ * capture) and joined back into it before the call returns, so later work
+ * on `stream` sees every view's results.  nexel_render_batch_bwd sums the
+ * gradients of all views into d_mu ... d_mlp (overwritten, or added to when
+ * accumulate != 0), with atomics, so their summation order varies between
+ * runs by rounding only.  d_weights and d_textures may be NULL arrays or
+ * hold NULL entries.  All views' arguments are checked before any launch.
+ * Capacity overflows and device timeouts are read per view with
+ * nexel_read_status. */
+int nexel_render_batch_fwd(int n_views, const nexel_camera* cams, const nexel_settings* settings,
+                           const nexel_field* field, int N, const float* mu, const float* quat,
+                           const float* scale, const float* opacity, const float* gamma,
+                           const float* color, void* const* ws, const size_t* ws_bytes,
+                           void* const* bwd_ws, const size_t* bwd_ws_bytes, float* const* image,
+                           float* const* notex, float* const* weights, int* const* ids,
+                           float* const* depths, float* const* textures, float* const* T_final,
+                           nexel_stream_t stream);
+int nexel_render_batch_bwd(int n_views, const nexel_camera* cams, const nexel_settings* settings,
+                           const nexel_field* field, int N, const float* mu, const float* quat,
+                           const float* scale, const float* opacity, const float* gamma,
+                           void* const* ws, const size_t* ws_bytes, void* const* bwd_ws,
+                           const size_t* bwd_ws_bytes, const float* const* weights,
+                           const int* const* ids, const float* const* depths,
+                           const float* const* T_final, const float* const* d_image,
+                           const float* const* d_weights, const float* const* d_textures,
+                           int accumulate, float* d_mu, float* d_quat, float* d_scale,
+                           float* d_opacity, float* d_gamma, float* d_color, float* d_table,
+                           float* d_mlp, nexel_stream_t stream);
+
+/* Reads and clears the device status words of one view's workspaces
+ * (bwd_ws may be NULL), synchronising the stream: NEXEL_ERR_CAPACITY if a
+ * device-count preprocess dropped instances, NEXEL_ERR_TIMEOUT if a bounded
+ * device wait of a tensor-core kernel ran out (that kernel's results are
+ * invalid), else NEXEL_OK. */
+int nexel_read_status(const nexel_camera* cam, const nexel_settings* settings,
+                      const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
+                      size_t bwd_ws_bytes, nexel_stream_t stream);
 
 /* Inspection of the binning done by the last nexel_preprocess on ws: the
  * n_instances (tile, surfel) pairs in the order the collection pass walks

@@ -31,7 +31,8 @@ MAX_LEVELS, MAX_LAYERS = 32, 4
 EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess",
            "nexel_render_fwd", "nexel_render_bwd", "nexel_instance_list", "nexel_status_string",
            "nexel_version", "nexel_launch_count", "nexel_profile_enable", "nexel_profile_read",
-           "nexel_render_fwd_static"]
+           "nexel_render_fwd_static", "nexel_preprocess_async", "nexel_render_batch_fwd",
+           "nexel_render_batch_bwd", "nexel_read_status"]
 
 
 def _nvcc() -> str:
@@ -130,6 +131,11 @@ def lib(auto_build: bool = False):
     L.nexel_instance_list.argtypes = [vp, i, vp, sz, ll, vp, vp, vp, vp]
     L.nexel_render_fwd_static.argtypes = [vp, vp, vp, i] + [vp] * 6 + [vp] * 7 + [
         C.POINTER(ll), vp]
+    L.nexel_preprocess_async.argtypes = [vp, vp, i] + [vp] * 7 + [sz, vp]
+    L.nexel_render_batch_fwd.argtypes = [i, vp, vp, vp, i] + [vp] * 6 + [vp] * 4 + [vp] * 7 + [vp]
+    L.nexel_render_batch_bwd.argtypes = ([i, vp, vp, vp, i] + [vp] * 5 + [vp] * 4 + [vp] * 4 +
+                                         [vp] * 3 + [i] + [vp] * 8 + [vp])
+    L.nexel_read_status.argtypes = [vp, vp, vp, i, vp, sz, vp, sz, vp]
     L.nexel_launch_count.restype = C.c_longlong
     L.nexel_launch_count.argtypes = []
     L.nexel_profile_enable.argtypes = [i]
@@ -216,6 +222,67 @@ def nexel_render_fwd_static(cam, st, field, N, mu, quat, scale, opacity, gamma, 
         scale, opacity, gamma, color, image, notex, weights, ids, depths, textures, T_final,
         C.byref(n), stream)
     return rc, n.value
+
+
+def nexel_preprocess_async(cam, st, N, mu, quat, scale, opacity, gamma, color, ws, ws_bytes,
+                           stream) -> int:
+    return check("nexel_preprocess_async", lib().nexel_preprocess_async(
+        C.byref(cam), C.byref(st), N, mu, quat, scale, opacity, gamma, color, ws, ws_bytes,
+        stream))
+
+
+def _cams(cams):
+    arr = (Camera * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k] = c
+    return arr
+
+
+def _ptrs(xs):
+    """Host array of device pointers (ints or None), or None for no array."""
+    if xs is None:
+        return None
+    return (C.c_void_p * len(xs))(*[x if x else None for x in xs])
+
+
+def _sizes(xs):
+    return None if xs is None else (C.c_size_t * len(xs))(*xs)
+
+
+def nexel_render_batch_fwd(cams, st, field, N, mu, quat, scale, opacity, gamma, color, ws,
+                           ws_bytes, bws, bws_bytes, image, notex, weights, ids, depths,
+                           textures, T_final, stream) -> int:
+    """Per-view arguments are Python lists with one entry per camera."""
+    n = len(cams)
+    return check("nexel_render_batch_fwd", lib().nexel_render_batch_fwd(
+        n, _cams(cams), C.byref(st), C.byref(field) if field is not None else None, N, mu, quat,
+        scale, opacity, gamma, color, _ptrs(ws), _sizes(ws_bytes), _ptrs(bws), _sizes(bws_bytes),
+        _ptrs(image), _ptrs(notex), _ptrs(weights), _ptrs(ids), _ptrs(depths), _ptrs(textures),
+        _ptrs(T_final), stream))
+
+
+def nexel_render_batch_bwd(cams, st, field, N, mu, quat, scale, opacity, gamma, ws, ws_bytes,
+                           bws, bws_bytes, weights, ids, depths, T_final, d_image, d_weights,
+                           d_textures, accumulate, d_mu, d_quat, d_scale, d_opacity, d_gamma,
+                           d_color, d_table, d_mlp, stream) -> int:
+    n = len(cams)
+    return check("nexel_render_batch_bwd", lib().nexel_render_batch_bwd(
+        n, _cams(cams), C.byref(st), C.byref(field) if field is not None else None, N, mu, quat,
+        scale, opacity, gamma, _ptrs(ws), _sizes(ws_bytes), _ptrs(bws), _sizes(bws_bytes),
+        _ptrs(weights), _ptrs(ids), _ptrs(depths), _ptrs(T_final), _ptrs(d_image),
+        _ptrs(d_weights), _ptrs(d_textures), int(accumulate), d_mu, d_quat, d_scale, d_opacity,
+        d_gamma, d_color, d_table, d_mlp, stream))
+
+
+def nexel_read_status(cam, st, field, N, ws, ws_bytes, bws, bws_bytes, stream) -> int:
+    """Returns the status (NEXEL_OK, NEXEL_ERR_CAPACITY or NEXEL_ERR_TIMEOUT)
+    without raising; argument errors raise."""
+    rc = lib().nexel_read_status(C.byref(cam), C.byref(st),
+                                 C.byref(field) if field is not None else None, N, ws, ws_bytes,
+                                 bws, bws_bytes, stream)
+    if rc not in (NEXEL_OK, -3, -5):
+        raise NexelError("nexel_read_status", rc)
+    return rc
 
 
 def nexel_launch_count() -> int:

@@ -205,6 +205,167 @@ __global__ void k_instance_list(long long n, int rank_bits, uint32_t rmask,
   if (depth_out) depth_out[i] = __uint_as_float(dkey[r]);
 }
 
+// ------------------------------------------------ per-view implementations
+// Shared by the single-view entry points and the batched ones (batch.cu).
+
+int check_fwd(const nexel_camera* cam, const nexel_settings* settings, const nexel_field* field,
+              int N, const void* ws, size_t ws_bytes, const void* bwd_ws, size_t bwd_ws_bytes,
+              const float* image, const float* notex, const float* weights, const int* ids,
+              const float* depths, const float* textures, const float* T_final) {
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !image || !notex || !T_final)
+    return NEXEL_ERR_INVALID_ARG;
+  const int K = settings->K;
+  if (K > 0 && (!weights || !ids || !depths || !textures)) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !field_ok(field)) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !texture_arch_supported(*settings, *field)) return NEXEL_ERR_UNSUPPORTED;
+  if (K > 0 && settings->cache_features != 0) {
+    BwdLayout B = bwd_layout(*cam, K, field->L * field->F, settings->recompute_buffers != 0);
+    if (!bwd_ws || bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
+  }
+  WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
+  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
+  return NEXEL_OK;
+}
+
+int check_bwd(const nexel_camera* cam, const nexel_settings* settings, const nexel_field* field,
+              int N, const float* mu, const float* quat, const float* scale, const float* opacity,
+              const float* gamma, const void* ws, size_t ws_bytes, const void* bwd_ws,
+              size_t bwd_ws_bytes, const float* weights, const int* ids, const float* depths,
+              const float* T_final, const float* d_image) {
+  const bool rc = settings && settings->recompute_buffers != 0;
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !d_image)
+    return NEXEL_ERR_INVALID_ARG;
+  if (!rc && !T_final) return NEXEL_ERR_INVALID_ARG;
+  if (!(settings->alpha_max < 1.f)) return NEXEL_ERR_INVALID_ARG;
+  if (N > 0 && (!mu || !quat || !scale || !opacity || !gamma)) return NEXEL_ERR_INVALID_ARG;
+  const int K = settings->K;
+  if (K > 0 && !rc && (!weights || !ids || !depths)) return NEXEL_ERR_INVALID_ARG;
+  if ((K > 0 || rc) && !bwd_ws) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !field_ok(field)) return NEXEL_ERR_INVALID_ARG;
+  if (K > 0 && !texture_arch_supported(*settings, *field)) return NEXEL_ERR_UNSUPPORTED;
+  WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
+  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
+  BwdLayout B = bwd_layout(*cam, K, K > 0 ? field->L * field->F : 0, rc);
+  if ((K > 0 || rc) && bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
+  return NEXEL_OK;
+}
+
+int preprocess_impl(const nexel_camera* cam, const nexel_settings* settings, int N,
+                    const float* mu, const float* quat, const float* scale, const float* opacity,
+                    const float* gamma, const float* color, void* ws, size_t ws_bytes,
+                    long long* n_instances_out, cudaStream_t st) {
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws) return NEXEL_ERR_INVALID_ARG;
+  if (N > 0 && (!mu || !quat || !scale || !opacity || !gamma || !color))
+    return NEXEL_ERR_INVALID_ARG;
+  WsLayout L = ws_layout_for_bytes(*cam, settings->K, N, ws_bytes);
+  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
+  DevCam c = make_devcam(*cam);
+  char* w = (char*)ws;
+  cudaError_t e = cudaMemsetAsync(w + L.counters, 0, 256, st);
+  if (e == cudaSuccess)
+    e = launch_preprocess(c, *settings, N, mu, quat, scale, opacity, gamma, color, w, L, st);
+  if (e == cudaSuccess) e = launch_depth_sort(N, w, L, st);
+  if (e == cudaSuccess) e = launch_count_scan(N, w, L, st);
+  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
+  if (!n_instances_out)  // device-count form: no host synchronisation
+    return cuda_status(launch_binning(c, N, -1, w, L, st));
+  uint32_t n_inst = 0;
+  e = cudaMemcpyAsync(&n_inst, w + L.counters + kCountersInst, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
+  *n_instances_out = (long long)n_inst;
+  if ((long long)n_inst > L.cap) return NEXEL_ERR_CAPACITY;
+  return cuda_status(launch_binning(c, N, (long long)n_inst, w, L, st));
+}
+
+int render_fwd_impl(const nexel_camera* cam, const nexel_settings* settings,
+                    const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
+                    float* image, float* notex, float* weights, int* ids, float* depths,
+                    float* textures, float* T_final, cudaStream_t st) {
+  const int K = settings->K;
+  void* feat_cache = nullptr;
+  if (K > 0 && settings->cache_features != 0) {
+    BwdLayout B = bwd_layout(*cam, K, field->L * field->F, settings->recompute_buffers != 0);
+    feat_cache = (char*)bwd_ws + B.feat;
+  }
+  WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
+  DevCam c = make_devcam(*cam);
+  char* w = (char*)ws;
+  cudaError_t e = launch_collect_fwd(c, *settings, w, L, notex, weights, ids, depths, T_final, st);
+  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
+  if (K == 0) {
+    long long P = (long long)cam->width * cam->height;
+    {
+      NEXEL_PROF("composite_notex", st);
+      k_composite_notex<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(
+          P, settings->bg[0], settings->bg[1], settings->bg[2], notex, T_final, image);
+    }
+    return cuda_status(cudaGetLastError());
+  }
+  e = launch_texture_fwd(c, *settings, *field, notex, weights, ids, depths, T_final, image,
+                         textures, feat_cache, (int*)(w + L.counters + kStatusOffset), st);
+  return cuda_status(e);
+}
+
+int zero_grads(const nexel_settings* settings, const nexel_field* field, int N, float* d_mu,
+               float* d_quat, float* d_scale, float* d_opacity, float* d_gamma, float* d_color,
+               float* d_table, float* d_mlp, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  const size_t n = (size_t)std::max(N, 0);
+  auto z = [&](float* p, size_t count) {
+    if (e == cudaSuccess && p && count) e = cudaMemsetAsync(p, 0, sizeof(float) * count, st);
+  };
+  z(d_mu, 3 * n);
+  z(d_quat, 4 * n);
+  z(d_scale, 2 * n);
+  z(d_opacity, n);
+  z(d_gamma, 2 * n);
+  z(d_color, 3 * n);
+  if (settings->K > 0 && field) {
+    z(d_table, (size_t)field->L * field->T * field->F);
+    size_t nw = 0;
+    for (int l = 0; l < field->n_layers; ++l) nw += (size_t)field->widths[l] * field->widths[l + 1];
+    z(d_mlp, nw);
+  }
+  return cuda_status(e);
+}
+
+int render_bwd_impl(const nexel_camera* cam, const nexel_settings* settings,
+                    const nexel_field* field, int N, const float* mu, const float* quat,
+                    const float* scale, const float* opacity, const float* gamma, void* ws,
+                    size_t ws_bytes, void* bwd_ws, const float* weights, const int* ids,
+                    const float* depths, const float* T_final, const float* d_image,
+                    const float* d_weights, const float* d_textures, float* d_mu, float* d_quat,
+                    float* d_scale, float* d_opacity, float* d_gamma, float* d_color,
+                    float* d_table, float* d_mlp, bool atomic_params, cudaStream_t st) {
+  const bool rc = settings->recompute_buffers != 0;
+  const int K = settings->K;
+  WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
+  BwdLayout B = bwd_layout(*cam, K, K > 0 ? field->L * field->F : 0, rc);
+  DevCam c = make_devcam(*cam);
+  char* w = (char*)ws;
+  char* bw = (char*)bwd_ws;
+  cudaError_t e = cudaSuccess;
+  if (rc) {
+    // recompute I, W, D, T_final with the collection pass (same kernel, same
+    // inputs, hence the same values the forward produced)
+    weights = (const float*)(bw + B.rc_weights);
+    ids = (const int*)(bw + B.rc_ids);
+    depths = (const float*)(bw + B.rc_depths);
+    T_final = (const float*)(bw + B.rc_T);
+    e = launch_collect_fwd(c, *settings, w, L, (float*)(bw + B.rc_notex), (float*)weights,
+                           (int*)ids, (float*)depths, (float*)T_final, st);
+  }
+  if (e == cudaSuccess && K > 0)
+    e = launch_texture_bwd(c, *settings, *field, bw, B, weights, ids, depths, d_image, d_weights,
+                           d_textures, d_table, d_mlp, settings->cache_features != 0, st);
+  if (e == cudaSuccess) e = launch_collect_bwd(c, *settings, w, L, bw, B, ids, T_final, d_image, st);
+  if (e == cudaSuccess)
+    e = launch_preprocess_bwd(c, *settings, N, mu, quat, scale, opacity, gamma, w, L, 1, d_mu,
+                              d_quat, d_scale, d_opacity, d_gamma, d_color, atomic_params, st);
+  return cuda_status(e);
+}
+
 }  // namespace nexel
 
 using namespace nexel;
@@ -246,66 +407,28 @@ int nexel_preprocess(const nexel_camera* cam, const nexel_settings* settings, in
                      const float* mu, const float* quat, const float* scale,
                      const float* opacity, const float* gamma, const float* color, void* ws,
                      size_t ws_bytes, long long* n_instances_out, nexel_stream_t stream) {
-  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !n_instances_out)
-    return NEXEL_ERR_INVALID_ARG;
-  if (N > 0 && (!mu || !quat || !scale || !opacity || !gamma || !color))
-    return NEXEL_ERR_INVALID_ARG;
-  WsLayout L = ws_layout_for_bytes(*cam, settings->K, N, ws_bytes);
-  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  DevCam c = make_devcam(*cam);
-  char* w = (char*)ws;
-  cudaError_t e = cudaMemsetAsync(w + L.counters, 0, 256, st);
-  if (e == cudaSuccess)
-    e = launch_preprocess(c, *settings, N, mu, quat, scale, opacity, gamma, color, w, L, st);
-  if (e == cudaSuccess) e = launch_depth_sort(N, w, L, st);
-  if (e == cudaSuccess) e = launch_count_scan(N, w, L, st);
-  uint32_t n_inst = 0;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&n_inst, w + L.counters + 4, 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
-  *n_instances_out = (long long)n_inst;
-  if ((long long)n_inst > L.cap) return NEXEL_ERR_CAPACITY;
-  return cuda_status(launch_binning(c, N, (long long)n_inst, w, L, st));
+  if (!n_instances_out) return NEXEL_ERR_INVALID_ARG;
+  return preprocess_impl(cam, settings, N, mu, quat, scale, opacity, gamma, color, ws, ws_bytes,
+                         n_instances_out, (cudaStream_t)stream);
+}
+
+int nexel_preprocess_async(const nexel_camera* cam, const nexel_settings* settings, int N,
+                           const float* mu, const float* quat, const float* scale,
+                           const float* opacity, const float* gamma, const float* color,
+                           void* ws, size_t ws_bytes, nexel_stream_t stream) {
+  return preprocess_impl(cam, settings, N, mu, quat, scale, opacity, gamma, color, ws, ws_bytes,
+                         nullptr, (cudaStream_t)stream);
 }
 
 int nexel_render_fwd(const nexel_camera* cam, const nexel_settings* settings,
                      const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
                      size_t bwd_ws_bytes, float* image, float* notex, float* weights, int* ids,
                      float* depths, float* textures, float* T_final, nexel_stream_t stream) {
-  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !image || !notex || !T_final)
-    return NEXEL_ERR_INVALID_ARG;
-  const int K = settings->K;
-  if (K > 0 && (!weights || !ids || !depths || !textures)) return NEXEL_ERR_INVALID_ARG;
-  if (K > 0 && !field_ok(field)) return NEXEL_ERR_INVALID_ARG;
-  if (K > 0 && !texture_arch_supported(*settings, *field)) return NEXEL_ERR_UNSUPPORTED;
-  const bool cache = K > 0 && settings->cache_features != 0;
-  void* feat_cache = nullptr;
-  if (cache) {
-    BwdLayout B = bwd_layout(*cam, K, field->L * field->F, settings->recompute_buffers != 0);
-    if (!bwd_ws || bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
-    feat_cache = (char*)bwd_ws + B.feat;
-  }
-  WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
-  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  DevCam c = make_devcam(*cam);
-  char* w = (char*)ws;
-  cudaError_t e = launch_collect_fwd(c, *settings, w, L, notex, weights, ids, depths, T_final, st);
-  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
-  if (K == 0) {
-    long long P = (long long)cam->width * cam->height;
-    {
-      NEXEL_PROF("composite_notex", st);
-      k_composite_notex<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(
-          P, settings->bg[0], settings->bg[1], settings->bg[2], notex, T_final, image);
-    }
-    return cuda_status(cudaGetLastError());
-  }
-  e = launch_texture_fwd(c, *settings, *field, notex, weights, ids, depths, T_final, image,
-                         textures, feat_cache, (int*)(w + L.counters + 32), st);
-  return cuda_status(e);
+  int rc = check_fwd(cam, settings, field, N, ws, ws_bytes, bwd_ws, bwd_ws_bytes, image, notex,
+                     weights, ids, depths, textures, T_final);
+  if (rc != NEXEL_OK) return rc;
+  return render_fwd_impl(cam, settings, field, N, ws, ws_bytes, bwd_ws, image, notex, weights,
+                         ids, depths, textures, T_final, (cudaStream_t)stream);
 }
 
 int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
@@ -317,53 +440,50 @@ int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
                      int accumulate, float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
                      float* d_gamma, float* d_color, float* d_table, float* d_mlp,
                      nexel_stream_t stream) {
-  const bool rc = settings && settings->recompute_buffers != 0;
-  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !d_image)
-    return NEXEL_ERR_INVALID_ARG;
-  if (!rc && !T_final) return NEXEL_ERR_INVALID_ARG;
-  if (!(settings->alpha_max < 1.f)) return NEXEL_ERR_INVALID_ARG;
-  if (N > 0 && (!mu || !quat || !scale || !opacity || !gamma)) return NEXEL_ERR_INVALID_ARG;
-  const int K = settings->K;
-  if (K > 0 && !rc && (!weights || !ids || !depths)) return NEXEL_ERR_INVALID_ARG;
-  if ((K > 0 || rc) && !bwd_ws) return NEXEL_ERR_INVALID_ARG;
-  if (K > 0 && !field_ok(field)) return NEXEL_ERR_INVALID_ARG;
-  if (K > 0 && !texture_arch_supported(*settings, *field)) return NEXEL_ERR_UNSUPPORTED;
-  WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
-  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
-  BwdLayout B = bwd_layout(*cam, K, K > 0 ? field->L * field->F : 0, rc);
-  if ((K > 0 || rc) && bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
+  int rc = check_bwd(cam, settings, field, N, mu, quat, scale, opacity, gamma, ws, ws_bytes,
+                     bwd_ws, bwd_ws_bytes, weights, ids, depths, T_final, d_image);
+  if (rc != NEXEL_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  DevCam c = make_devcam(*cam);
+  if (!accumulate) {
+    rc = zero_grads(settings, field, N, d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color,
+                    d_table, d_mlp, st);
+    if (rc != NEXEL_OK) return rc;
+  }
+  return render_bwd_impl(cam, settings, field, N, mu, quat, scale, opacity, gamma, ws, ws_bytes,
+                         bwd_ws, weights, ids, depths, T_final, d_image, d_weights, d_textures,
+                         d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color, d_table, d_mlp,
+                         false, st);
+}
+
+int nexel_read_status(const nexel_camera* cam, const nexel_settings* settings,
+                      const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
+                      size_t bwd_ws_bytes, nexel_stream_t stream) {
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws) return NEXEL_ERR_INVALID_ARG;
+  WsLayout L = ws_layout_for_bytes(*cam, settings->K, N, ws_bytes);
+  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int words[2] = {0, 0};
   char* w = (char*)ws;
-  char* bw = (char*)bwd_ws;
-  cudaError_t e = cudaSuccess;
-  if (rc) {
-    // recompute I, W, D, T_final with the collection pass (same kernel, same
-    // inputs, hence the same values the forward produced)
-    weights = (const float*)(bw + B.rc_weights);
-    ids = (const int*)(bw + B.rc_ids);
-    depths = (const float*)(bw + B.rc_depths);
-    T_final = (const float*)(bw + B.rc_T);
-    e = launch_collect_fwd(c, *settings, w, L, (float*)(bw + B.rc_notex), (float*)weights,
-                           (int*)ids, (float*)depths, (float*)T_final, st);
-  }
-  if (e == cudaSuccess && K > 0) {
-    if (!accumulate) {
-      if (d_table)
-        e = cudaMemsetAsync(d_table, 0, sizeof(float) * (size_t)field->L * field->T * field->F, st);
-      size_t nw = 0;
-      for (int l = 0; l < field->n_layers; ++l) nw += (size_t)field->widths[l] * field->widths[l + 1];
-      if (e == cudaSuccess && d_mlp) e = cudaMemsetAsync(d_mlp, 0, sizeof(float) * nw, st);
-    }
+  cudaError_t e = cudaMemcpyAsync(&words[0], w + L.counters + kStatusOffset, 4,
+                                  cudaMemcpyDeviceToHost, st);
+  char* bstat = nullptr;
+  if (bwd_ws) {
+    const int K = settings->K;
+    const int fd = (K > 0 && field_ok(field)) ? field->L * field->F : 0;
+    BwdLayout B = bwd_layout(*cam, K, fd, settings->recompute_buffers != 0);
+    if (bwd_ws_bytes < B.total) return NEXEL_ERR_INVALID_ARG;
+    bstat = (char*)bwd_ws + B.status;
     if (e == cudaSuccess)
-      e = launch_texture_bwd(c, *settings, *field, bw, B, weights, ids, depths, d_image, d_weights,
-                             d_textures, d_table, d_mlp, settings->cache_features != 0, st);
+      e = cudaMemcpyAsync(&words[1], bstat, 4, cudaMemcpyDeviceToHost, st);
   }
-  if (e == cudaSuccess) e = launch_collect_bwd(c, *settings, w, L, bw, B, ids, T_final, d_image, st);
-  if (e == cudaSuccess)
-    e = launch_preprocess_bwd(c, *settings, N, mu, quat, scale, opacity, gamma, w, L, accumulate,
-                              d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color, st);
-  return cuda_status(e);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w + L.counters + kStatusOffset, 0, 4, st);
+  if (e == cudaSuccess && bstat) e = cudaMemsetAsync(bstat, 0, 4, st);
+  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
+  const int f = words[0] | words[1];
+  if (f & kStatusCapacity) return NEXEL_ERR_CAPACITY;
+  if (f & kStatusTimeout) return NEXEL_ERR_TIMEOUT;
+  return NEXEL_OK;
 }
 
 int nexel_instance_list(const nexel_camera* cam, int N, const void* ws, size_t ws_bytes,

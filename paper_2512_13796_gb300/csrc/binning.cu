@@ -394,7 +394,11 @@ template <typename KeyT, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const KeyT* __restrict__ keys,
                                                              long long n, int shift, int bits,
                                                              uint32_t* __restrict__ hist,
-                                                             int nblocks) {
+                                                             int nblocks,
+                                                             const uint32_t* __restrict__ n_dev) {
+  // n is the key count, or, with n_dev, the capacity the grid was sized for
+  // and *n_dev (clamped to it) the count the device produced
+  if (n_dev) n = min(n, (long long)*n_dev);
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -413,7 +417,7 @@ template <typename KeyT, bool kVal, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const KeyT* __restrict__ kin, KeyT* __restrict__ kout, const uint32_t* __restrict__ vin,
     uint32_t* __restrict__ vout, long long n, int shift, int bits,
-    const uint32_t* __restrict__ offs, int nblocks) {
+    const uint32_t* __restrict__ offs, int nblocks, const uint32_t* __restrict__ n_dev) {
   // Warp w ranks the block's keys [512 w, 512 w + 512) in order (item k,
   // lane l -> key 512 w + 32 k + l) with warp-private digit counters (match
   // + leader update, no block barrier per item); one block-wide scan over
@@ -427,8 +431,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
   const int nbins = 1 << bits;
   const uint32_t mask = (uint32_t)nbins - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (n_dev) n = min(n, (long long)*n_dev);
   const long long base = (long long)blockIdx.x * (kSortThreads * ITEMS);
-  const int nloc = (int)min((long long)(kSortThreads * ITEMS), n - base);
+  const int nloc = (int)max(0LL, min((long long)(kSortThreads * ITEMS), n - base));
   for (int b = threadIdx.x; b < 256 * kW; b += kSortThreads) (&s_wc[0][0])[b] = 0;
   __syncthreads();
   KeyT key[ITEMS];
@@ -487,11 +492,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 }
 
 // Sorts n keys (and values when vin != nullptr) on bits [lo, lo + nbits).
-// Returns the index (0 or 1) of the buffer pair that holds the result.
+// Returns the index (0 or 1) of the buffer pair that holds the result.  With
+// n_dev the key count is read on the device (clamped to n, the capacity the
+// launches are sized for), so no host synchronisation is needed.
 template <typename KeyT, int ITEMS>
 static cudaError_t radix_sort(KeyT* k0, KeyT* k1, uint32_t* v0, uint32_t* v1, long long n, int lo,
                               int nbits, uint32_t* hist, uint32_t* sums, cudaStream_t st,
-                              int* which) {
+                              int* which, const uint32_t* n_dev = nullptr) {
   *which = 0;
   if (n <= 1 || nbits <= 0) return cudaSuccess;
   int nblocks = (int)((n + (kSortThreads * ITEMS) - 1) / (kSortThreads * ITEMS));
@@ -503,21 +510,22 @@ static cudaError_t radix_sort(KeyT* k0, KeyT* k1, uint32_t* v0, uint32_t* v1, lo
     int shift = lo + b;
     {
       NEXEL_PROF("radix_hist", st);
-      k_radix_hist<KeyT, ITEMS><<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, bits, hist, nblocks);
+      k_radix_hist<KeyT, ITEMS><<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, bits, hist, nblocks,
+                                                                   n_dev);
     }
     cudaError_t e = excl_scan(hist, (long long)(1 << bits) * nblocks, sums, nullptr, st);
     if (e != cudaSuccess) return e;
     if (v0) {
       {
         NEXEL_PROF("radix_scatter", st);
-        k_radix_scatter<KeyT, true, ITEMS><<<nblocks, kSortThreads, smem, st>>>(kin, kout, vin, vout, n,
-                                                                          shift, bits, hist, nblocks);
+        k_radix_scatter<KeyT, true, ITEMS><<<nblocks, kSortThreads, smem, st>>>(
+            kin, kout, vin, vout, n, shift, bits, hist, nblocks, n_dev);
       }
     } else {
       {
         NEXEL_PROF("radix_scatter", st);
         k_radix_scatter<KeyT, false, ITEMS><<<nblocks, kSortThreads, smem, st>>>(
-            kin, kout, nullptr, nullptr, n, shift, bits, hist, nblocks);
+            kin, kout, nullptr, nullptr, n, shift, bits, hist, nblocks, n_dev);
       }
     }
     std::swap(kin, kout);
@@ -562,11 +570,12 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
                                                    const uint4* __restrict__ tmask,
                                                    const uint32_t* __restrict__ offs,
                                                    const uint32_t* __restrict__ count,
-                                                   KeyT* __restrict__ keys) {
+                                                   KeyT* __restrict__ keys, uint32_t cap) {
   // one warp per surfel (rank order): the lanes take 32 tiles of the
   // rectangle at a time and the passing ones are written in tile order; the
   // decisions come from the counting pass's mask when the rectangle has at
-  // most 128 tiles, else the test runs again
+  // most 128 tiles, else the test runs again.  Instances at or beyond the
+  // key buffer's capacity are dropped (the device-count path flags that).
   const int lane = threadIdx.x & 31;
   const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (r >= N) return;
@@ -587,7 +596,8 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
       if ((m >> lane) & 1u) {
         const int2 t2 = rect_tile(32 * i + lane, nx, inv_nx);
         const KeyT tile = (KeyT)((ty0 + t2.y) * c.tiles_x + tx0 + t2.x);
-        keys[o + __popc(m & ((1u << lane) - 1u))] = (tile << rank_bits) | (KeyT)r;
+        const size_t at = o + __popc(m & ((1u << lane) - 1u));
+        if (at < cap) keys[at] = (tile << rank_bits) | (KeyT)r;
       }
       o += __popc(m);
     }
@@ -602,7 +612,8 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
     const unsigned m = __ballot_sync(0xffffffffu, hit);
     if (hit) {
       const KeyT tile = (KeyT)(ty * c.tiles_x + tx);
-      keys[o + __popc(m & ((1u << lane) - 1u))] = (tile << rank_bits) | (KeyT)r;
+      const size_t at = o + __popc(m & ((1u << lane) - 1u));
+      if (at < cap) keys[at] = (tile << rank_bits) | (KeyT)r;
     }
     o += __popc(m);
   }
@@ -652,8 +663,16 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
 
 template <typename KeyT>
 __global__ void k_ranges(long long n, int rank_bits, const KeyT* __restrict__ keys,
-                         uint2* __restrict__ ranges) {
+                         uint2* __restrict__ ranges, const uint32_t* __restrict__ n_dev,
+                         int* __restrict__ status) {
+  // with n_dev: n is the capacity and *n_dev the instance count; a count
+  // above the capacity (instances dropped by k_duplicate) is flagged
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n_dev) {
+    const long long want = (long long)*n_dev;
+    if (i == 0 && want > n && status) atomicOr(status, kStatusCapacity);
+    n = min(n, want);
+  }
   if (i >= n) return;
   uint32_t t = (uint32_t)(keys[i] >> rank_bits);
   if (i == 0 || (uint32_t)(keys[i - 1] >> rank_bits) != t) ranges[t].x = (uint32_t)i;
@@ -715,9 +734,14 @@ cudaError_t launch_count_scan(int N, char* ws, const WsLayout& L, cudaStream_t s
 template <typename KeyT>
 static cudaError_t binning_t(const DevCam& c, int N, long long n_inst, char* ws, const WsLayout& L,
                              cudaStream_t st) {
+  // n_inst < 0: the count stays on the device; every launch is sized for the
+  // capacity and reads the count the scan wrote.
+  const bool dev_count = n_inst < 0;
+  const uint32_t* n_dev = dev_count ? (const uint32_t*)(ws + L.counters + kCountersInst) : nullptr;
+  const long long n_launch = dev_count ? L.cap : n_inst;
   // The duplicate step writes into the buffer that makes the last sort pass
   // land in inst0, which is where the collection kernels read.
-  int passes = (n_inst > 1) ? L.tile_passes : 0;
+  int passes = (n_launch > 1 && L.tile_bits > 0) ? L.tile_passes : 0;
   KeyT* k0 = (KeyT*)(ws + ((passes & 1) ? L.inst1 : L.inst0));
   KeyT* k1 = (KeyT*)(ws + ((passes & 1) ? L.inst0 : L.inst1));
   int rb = L.key64 ? 32 : L.rank_bits;
@@ -725,22 +749,24 @@ static cudaError_t binning_t(const DevCam& c, int N, long long n_inst, char* ws,
     NEXEL_PROF("duplicate", st);
     k_duplicate<KeyT><<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, st>>>(
         c, N, rb, (uint32_t*)(ws + L.did0), (uint2*)(ws + L.rect), (float4*)(ws + L.conic),
-        (const uint4*)(ws + L.tmask), (uint32_t*)(ws + L.offs), (uint32_t*)(ws + L.count), k0);
+        (const uint4*)(ws + L.tmask), (uint32_t*)(ws + L.offs), (uint32_t*)(ws + L.count), k0,
+        (uint32_t)std::min<long long>(L.cap, 0xFFFFFFFFLL));
   }
   int which = 0;
-  cudaError_t e = radix_sort<KeyT, kSortItems>(k0, k1, nullptr, nullptr, n_inst, rb, L.tile_bits,
+  cudaError_t e = radix_sort<KeyT, kSortItems>(k0, k1, nullptr, nullptr, n_launch, rb, L.tile_bits,
                                    (uint32_t*)(ws + L.hist), (uint32_t*)(ws + L.scan_sums), st,
-                                   &which);
+                                   &which, n_dev);
   if (e != cudaSuccess) return e;
   KeyT* res = which ? k1 : k0;
   if ((char*)res != ws + L.inst0) return cudaErrorUnknown;
   e = cudaMemsetAsync(ws + L.ranges, 0, sizeof(uint2) * (size_t)L.n_tiles, st);
   if (e != cudaSuccess) return e;
-  if (n_inst > 0)
+  if (n_launch > 0)
     {
       NEXEL_PROF("tile_ranges", st);
-      k_ranges<KeyT><<<(unsigned)((n_inst + 255) / 256), 256, 0, st>>>(n_inst, rb, res,
-                                                                      (uint2*)(ws + L.ranges));
+      k_ranges<KeyT><<<(unsigned)((n_launch + 255) / 256), 256, 0, st>>>(
+          n_launch, rb, res, (uint2*)(ws + L.ranges), n_dev,
+          (int*)(ws + L.counters + kStatusOffset));
     }
   return cudaGetLastError();
 }
@@ -758,6 +784,14 @@ cudaError_t launch_binning(const DevCam& c, int N, long long n_inst, char* ws, c
 // space (x_c = R x + t, so dL/dx = R^T dL/dx_c) and the three frame columns
 // are taken through the rotation of the normalised quaternion and the
 // normalisation itself.
+template <bool kAtomic>
+__device__ __forceinline__ void acc(float* p, float v) {
+  if (kAtomic) atomicAdd(p, v);
+  else *p += v;
+}
+
+// kAtomic: views rendered concurrently add into the same gradients.
+template <bool kAtomic>
 __global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ quat,
                                  const uint32_t* __restrict__ did, const uint32_t* __restrict__ dkey,
                                  const float* __restrict__ gs, float* __restrict__ d_mu,
@@ -788,19 +822,29 @@ __global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ quat
              G[4] * (-4 * zq) + G[5] * (2 * y) + G[6] * (2 * x) + G[7] * (2 * y);
   float dot = w * gw + x * gx + y * gy + zq * gz;
   if (d_mu) {
-    d_mu[3 * i] += g_m.x; d_mu[3 * i + 1] += g_m.y; d_mu[3 * i + 2] += g_m.z;
+    acc<kAtomic>(d_mu + 3 * i, g_m.x);
+    acc<kAtomic>(d_mu + 3 * i + 1, g_m.y);
+    acc<kAtomic>(d_mu + 3 * i + 2, g_m.z);
   }
   if (d_quat) {
-    d_quat[4 * i] += (gw - w * dot) * qn;
-    d_quat[4 * i + 1] += (gx - x * dot) * qn;
-    d_quat[4 * i + 2] += (gy - y * dot) * qn;
-    d_quat[4 * i + 3] += (gz - zq * dot) * qn;
+    acc<kAtomic>(d_quat + 4 * i, (gw - w * dot) * qn);
+    acc<kAtomic>(d_quat + 4 * i + 1, (gx - x * dot) * qn);
+    acc<kAtomic>(d_quat + 4 * i + 2, (gy - y * dot) * qn);
+    acc<kAtomic>(d_quat + 4 * i + 3, (gz - zq * dot) * qn);
   }
-  if (d_scale) { d_scale[2 * i] += g[12]; d_scale[2 * i + 1] += g[13]; }
-  if (d_opac) d_opac[i] += g[14];
-  if (d_gamma) { d_gamma[2 * i] += g[15]; d_gamma[2 * i + 1] += g[16]; }
+  if (d_scale) {
+    acc<kAtomic>(d_scale + 2 * i, g[12]);
+    acc<kAtomic>(d_scale + 2 * i + 1, g[13]);
+  }
+  if (d_opac) acc<kAtomic>(d_opac + i, g[14]);
+  if (d_gamma) {
+    acc<kAtomic>(d_gamma + 2 * i, g[15]);
+    acc<kAtomic>(d_gamma + 2 * i + 1, g[16]);
+  }
   if (d_color) {
-    d_color[3 * i] += g[17]; d_color[3 * i + 1] += g[18]; d_color[3 * i + 2] += g[19];
+    acc<kAtomic>(d_color + 3 * i, g[17]);
+    acc<kAtomic>(d_color + 3 * i + 1, g[18]);
+    acc<kAtomic>(d_color + 3 * i + 2, g[19]);
   }
 }
 
@@ -808,7 +852,7 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
                                   const float* quat, const float* scale, const float* opacity,
                                   const float* gamma, char* ws, const WsLayout& L, int accumulate,
                                   float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
-                                  float* d_gamma, float* d_color, cudaStream_t st) {
+                                  float* d_gamma, float* d_color, bool atomic, cudaStream_t st) {
   (void)s;
   if (N <= 0) return cudaSuccess;
   if (!accumulate) {
@@ -823,7 +867,8 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
   }
   {
     NEXEL_PROF("preprocess_bwd", st);
-    k_preprocess_bwd<<<(N + 255) / 256, 256, 0, st>>>(
+    auto kern = atomic ? k_preprocess_bwd<true> : k_preprocess_bwd<false>;
+    kern<<<(N + 255) / 256, 256, 0, st>>>(
         c, N, quat, (uint32_t*)(ws + L.did0), (uint32_t*)(ws + L.dkey0),
         (float*)(ws + L.grad_sorted), d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color);
   }

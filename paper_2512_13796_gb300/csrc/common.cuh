@@ -114,6 +114,15 @@ __device__ __forceinline__ float downweight(float focal, float s, float t) {
   return -expm1f(-r * r * 0.15915494309189535f);
 }
 
+// Device status word bits (the word at kStatusOffset in the counters region
+// of the main workspace, and BwdLayout::status): a bounded device wait that
+// ran out, and instances dropped because the key buffers were full.
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusCapacity = 2;
+// counters region: [0] unused, [1] instance count, [8] status word
+constexpr size_t kCountersInst = 4;
+constexpr size_t kStatusOffset = 32;
+
 // ------------------------------------------------------------ workspace
 // Main workspace (binning results and per-pixel replay data).  Regions that
 // depend only on (camera, K, N) come first; the instance buffers and the
@@ -163,6 +172,9 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
                               const WsLayout& L, cudaStream_t st);
 cudaError_t launch_depth_sort(int N, char* ws, const WsLayout& L, cudaStream_t st);
 cudaError_t launch_count_scan(int N, char* ws, const WsLayout& L, cudaStream_t st);
+// n_inst: the instance count read back on the host, or < 0 for the
+// device-count form (capacity-sized launches that read the count written by
+// launch_count_scan and flag an overflow in the status word).
 cudaError_t launch_binning(const DevCam& c, int N, long long n_inst, char* ws, const WsLayout& L,
                            cudaStream_t st);
 cudaError_t launch_collect_fwd(const DevCam& c, const nexel_settings& s, char* ws,
@@ -176,7 +188,7 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
                                   const float* quat, const float* scale, const float* opacity,
                                   const float* gamma, char* ws, const WsLayout& L, int accumulate,
                                   float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
-                                  float* d_gamma, float* d_color, cudaStream_t st);
+                                  float* d_gamma, float* d_color, bool atomic, cudaStream_t st);
 // feat_cache (may be null): where a training forward leaves the per-sample
 // field features for the backward (the backward's feature buffer).
 cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
@@ -190,5 +202,41 @@ cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const n
                                const float* d_textures, float* d_table, float* d_mlp,
                                bool feat_cached, cudaStream_t st);
 bool texture_arch_supported(const nexel_settings& s, const nexel_field& f);
+
+// Per-view bodies of the C entry points (api.cu), shared with the batched
+// entry points (batch.cu).  check_* validate one view's arguments and launch
+// nothing; the *_impl functions assume a passed check.  preprocess_impl with
+// n_instances_out == nullptr is the device-count form.  render_bwd_impl
+// always adds into the gradients (zero_grads clears them first);
+// atomic_params makes the per-surfel additions atomic, for views that run
+// concurrently.
+int check_fwd(const nexel_camera* cam, const nexel_settings* settings, const nexel_field* field,
+              int N, const void* ws, size_t ws_bytes, const void* bwd_ws, size_t bwd_ws_bytes,
+              const float* image, const float* notex, const float* weights, const int* ids,
+              const float* depths, const float* textures, const float* T_final);
+int check_bwd(const nexel_camera* cam, const nexel_settings* settings, const nexel_field* field,
+              int N, const float* mu, const float* quat, const float* scale, const float* opacity,
+              const float* gamma, const void* ws, size_t ws_bytes, const void* bwd_ws,
+              size_t bwd_ws_bytes, const float* weights, const int* ids, const float* depths,
+              const float* T_final, const float* d_image);
+int preprocess_impl(const nexel_camera* cam, const nexel_settings* settings, int N,
+                    const float* mu, const float* quat, const float* scale, const float* opacity,
+                    const float* gamma, const float* color, void* ws, size_t ws_bytes,
+                    long long* n_instances_out, cudaStream_t st);
+int render_fwd_impl(const nexel_camera* cam, const nexel_settings* settings,
+                    const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
+                    float* image, float* notex, float* weights, int* ids, float* depths,
+                    float* textures, float* T_final, cudaStream_t st);
+int zero_grads(const nexel_settings* settings, const nexel_field* field, int N, float* d_mu,
+               float* d_quat, float* d_scale, float* d_opacity, float* d_gamma, float* d_color,
+               float* d_table, float* d_mlp, cudaStream_t st);
+int render_bwd_impl(const nexel_camera* cam, const nexel_settings* settings,
+                    const nexel_field* field, int N, const float* mu, const float* quat,
+                    const float* scale, const float* opacity, const float* gamma, void* ws,
+                    size_t ws_bytes, void* bwd_ws, const float* weights, const int* ids,
+                    const float* depths, const float* T_final, const float* d_image,
+                    const float* d_weights, const float* d_textures, float* d_mu, float* d_quat,
+                    float* d_scale, float* d_opacity, float* d_gamma, float* d_color,
+                    float* d_table, float* d_mlp, bool atomic_params, cudaStream_t st);
 
 }  // namespace nexel

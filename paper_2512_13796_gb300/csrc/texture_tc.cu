@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         if (tid < IN) atomicAdd(dW1 + (16 * c16 + i) * IN + tid, v[i] * (1.f / OP::kScale));  // dW1[o][i]
     }
   }
-  if (!ok && tid == 0 && status) atomicExch(status, 1);
+  if (!ok && tid == 0 && status) atomicOr(status, kStatusTimeout);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     ok = __syncthreads_and(ok) != 0;
   }
-  if (!ok && tid == 0 && status) atomicExch(status, 1);
+  if (!ok && tid == 0 && status) atomicOr(status, kStatusTimeout);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcFwdCols));

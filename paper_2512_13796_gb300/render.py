@@ -232,3 +232,143 @@ def render(params: dict, field: DeviceField | None, cam, settings, ws: Workspace
     w = field.weights if field is not None else None
     return NexelRender.apply(params["mu"], params["quat"], params["scale"], params["opacity"],
                              params["gamma"], params["color"], tab, w, cfg)
+
+
+class BatchStep:
+    """Multi-view training step of one scene (views of uneven resolutions)
+    through the batched entry points, with no host synchronisation inside
+    the step, so that the whole step can be captured in one CUDA graph.
+
+    Construction runs the synchronising preprocess once per view to size
+    each view's workspace (instance count x ``margin``); later steps use
+    the device-count preprocess, whose overflow (a scene that moved far)
+    ``status()`` reports.  ``d_image[v]`` are static upstream-gradient
+    buffers the caller fills (or computes inside the captured graph);
+    ``grads`` receives the gradients summed over the views.  Parameter,
+    table and weight tensors are read through their storage, so a captured
+    graph sees in-place updates of them; ``refresh_table()`` copies the FP32
+    master table into the storage copy in place."""
+
+    def __init__(self, cams, settings, field: DeviceField | None, params: dict,
+                 margin: float = 1.25, train: bool = True):
+        self.params = {k: params[k].detach().contiguous() for k in
+                       ("mu", "quat", "scale", "opacity", "gamma", "color")}
+        dev = self.params["mu"].device
+        self.dev = dev
+        self.N = int(self.params["mu"].shape[0])
+        self.field = field
+        self.cams = [camera_struct(c) for c in cams]
+        K = int(settings.K)
+        self.K = K
+        self.train = train
+        self.st = settings_struct(settings, field.grid_dtype if field else "f32",
+                                  field.mlp_dtype if field else "f32",
+                                  cache_features=train and K > 0)
+        self.ts = field.storage_table() if field is not None else None
+        self.w = field.weights if field is not None else None
+        self.fs = field.struct(self.ts, self.w) if (field is not None and K > 0) else None
+        p = [self.params[k] for k in ("mu", "quat", "scale", "opacity", "gamma", "color")]
+        self.ws, self.ws_bytes, self.bws, self.bws_bytes, self.out = [], [], [], [], []
+        self.n_instances = []
+        for cs in self.cams:
+            probe = Workspace(dev, cap_hint=1 << 20)
+            n = preprocess(probe, cs, self.st, *p)
+            self.n_instances.append(n)
+            cap = int(n * margin) + 4096
+            nbytes = N_.nexel_workspace_size(cs, self.N, cap)
+            self.ws.append(torch.empty(nbytes, dtype=torch.uint8, device=dev))
+            self.ws_bytes.append(nbytes)
+            bn = N_.nexel_bwd_workspace_size(cs, self.st, self.fs) if train else 0
+            self.bws.append(torch.empty(bn, dtype=torch.uint8, device=dev) if bn else None)
+            self.bws_bytes.append(bn)
+            H, W = cs.height, cs.width
+            self.out.append(dict(
+                image=torch.empty(H, W, 3, device=dev), notex=torch.empty(H, W, 3, device=dev),
+                weights=torch.empty(H, W, K, device=dev),
+                ids=torch.empty(H, W, K, dtype=torch.int32, device=dev),
+                depths=torch.empty(H, W, K, device=dev),
+                textures=torch.empty(H, W, K, 3, device=dev),
+                T_final=torch.empty(H, W, device=dev)))
+            del probe
+        self.d_image = [torch.zeros(cs.height, cs.width, 3, device=dev) for cs in self.cams]
+        N = self.N
+        self.grads = dict(mu=torch.zeros(N, 3, device=dev), quat=torch.zeros(N, 4, device=dev),
+                          scale=torch.zeros(N, 2, device=dev), opacity=torch.zeros(N, device=dev),
+                          gamma=torch.zeros(N, 2, device=dev), color=torch.zeros(N, 3, device=dev))
+        if self.fs is not None:
+            self.grads["table"] = torch.zeros_like(field.table)
+            self.grads["mlp"] = torch.zeros_like(field.weights)
+        self.graph = None
+
+    @property
+    def pixels(self) -> int:
+        return sum(c.width * c.height for c in self.cams)
+
+    def refresh_table(self):
+        if self.field is not None:
+            self.ts.copy_(self.field.table.detach().to(self.ts.dtype))
+
+    def _outs(self, key):
+        return [o[key].data_ptr() for o in self.out] if (self.K > 0 or key in
+                                                          ("image", "notex", "T_final")) else None
+
+    def forward(self):
+        p = self.params
+        N_.nexel_render_batch_fwd(
+            self.cams, self.st, self.fs, self.N, p["mu"].data_ptr(), p["quat"].data_ptr(),
+            p["scale"].data_ptr(), p["opacity"].data_ptr(), p["gamma"].data_ptr(),
+            p["color"].data_ptr(), [b.data_ptr() for b in self.ws], self.ws_bytes,
+            [_ptr(b) for b in self.bws], self.bws_bytes, self._outs("image"), self._outs("notex"),
+            self._outs("weights"), self._outs("ids"), self._outs("depths"),
+            self._outs("textures"), self._outs("T_final"), _stream())
+
+    def backward(self, accumulate: bool = False):
+        p, g = self.params, self.grads
+        N_.nexel_render_batch_bwd(
+            self.cams, self.st, self.fs, self.N, p["mu"].data_ptr(), p["quat"].data_ptr(),
+            p["scale"].data_ptr(), p["opacity"].data_ptr(), p["gamma"].data_ptr(),
+            [b.data_ptr() for b in self.ws], self.ws_bytes, [_ptr(b) for b in self.bws],
+            self.bws_bytes, self._outs("weights"), self._outs("ids"), self._outs("depths"),
+            self._outs("T_final"), [d.data_ptr() for d in self.d_image], None, None, accumulate,
+            g["mu"].data_ptr(), g["quat"].data_ptr(), g["scale"].data_ptr(),
+            g["opacity"].data_ptr(), g["gamma"].data_ptr(), g["color"].data_ptr(),
+            _ptr(g.get("table")), _ptr(g.get("mlp")), _stream())
+
+    def step(self):
+        self.forward()
+        if self.train:
+            self.backward()
+
+    def capture(self, extra=None):
+        """Captures forward (+ ``extra()``, e.g. a loss that writes d_image)
+        + backward into one CUDA graph, after one eager warm-up step on a
+        side stream (which also creates the library's branch streams)."""
+        s = torch.cuda.Stream(device=self.dev)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.forward()
+            if extra is not None:
+                extra()
+            if self.train:
+                self.backward()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize(self.dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.forward()
+            if extra is not None:
+                extra()
+            if self.train:
+                self.backward()
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def status(self) -> list[int]:
+        """Per-view device status (synchronises): 0, or the NEXEL_ERR_*
+        code of an instance-capacity overflow or a device timeout."""
+        return [N_.nexel_read_status(cs, self.st, self.fs, self.N, self.ws[v].data_ptr(),
+                                     self.ws_bytes[v], _ptr(self.bws[v]), self.bws_bytes[v],
+                                     _stream()) for v, cs in enumerate(self.cams)]

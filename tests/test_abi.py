@@ -67,3 +67,38 @@ def test_invalid_arguments_rejected_before_launch(lib):
     out = C.c_size_t(0)
     assert lib.nexel_workspace_size(C.byref(bad), 10, 10, C.byref(out)) == -1
     assert lib.nexel_workspace_size(C.byref(cam), -1, 10, C.byref(out)) == -1
+
+
+def test_batched_calls_check_every_view_before_launch(lib):
+    """The batched entry points validate all views' arguments first; a bad
+    view anywhere in the batch returns NEXEL_ERR_INVALID_ARG with nothing
+    launched (the fake device pointers below are never dereferenced)."""
+    cams = [R.camera_struct(synth.front_camera(64, 48)), R.camera_struct(synth.front_camera(32, 32))]
+    st = R.settings_struct(synth.Settings(K=0))
+    N = 16
+    fake = 1 << 20
+    sizes = [N_.nexel_workspace_size(c, N, 1000) for c in cams]
+    arr = (N_.Camera * 2)(*cams)
+    P = lambda xs: (C.c_void_p * len(xs))(*xs)
+    S = lambda xs: (C.c_size_t * len(xs))(*xs)
+    params = [fake] * 6
+
+    def fwd(n, cam_arr, ws_ptrs, ws_sizes):
+        return lib.nexel_render_batch_fwd(n, cam_arr, C.byref(st), None, N, *params, ws_ptrs,
+                                          ws_sizes, None, None, P([fake] * 2), P([fake] * 2),
+                                          None, None, None, None, P([fake] * 2), None)
+
+    assert fwd(0, arr, P([fake] * 2), S(sizes)) == -1
+    assert fwd(2, None, P([fake] * 2), S(sizes)) == -1
+    assert fwd(2, arr, P([fake, 0]), S(sizes)) == -1            # view 1 has no workspace
+    assert fwd(2, arr, P([fake] * 2), S([sizes[0], 64])) == -1  # view 1's is too small
+    bad = (N_.Camera * 2)(cams[0], cams[1])
+    bad[1].width = 0
+    assert fwd(2, bad, P([fake] * 2), S(sizes)) == -1
+    assert lib.nexel_render_batch_bwd(2, arr, C.byref(st), None, N, *params[:5], P([fake] * 2),
+                                      S(sizes), None, None, None, None, None, P([fake] * 2),
+                                      None, None, None, 0, *([None] * 8), None) == -1  # no d_image
+    assert lib.nexel_preprocess_async(C.byref(cams[0]), C.byref(st), N, *([None] * 6), fake,
+                                      sizes[0], None) == -1
+    assert lib.nexel_read_status(C.byref(cams[0]), C.byref(st), None, N, None, 0, None, 0,
+                                 None) == -1
