@@ -18,6 +18,10 @@ Functions and the passages they follow:
   depth_order           Sec. 3 (sorted by the depth of the centres)
   storage_bytes         supp. Sec. 7.1, last paragraph (2 B per Instant-NGP
                         parameter, 4 B otherwise)
+  objective (module)    Sec. 5, "Losses": L_1, D-SSIM, L_texture, L_alpha,
+                        L_opacity, L_grid, the weighted total, and the Adam
+                        step of the 3DGS scheme the paper follows (plain
+                        numpy, FP64; see its header for the readings)
 Parity unpinned: the shared conventions alpha_min / alpha_max / T_min, the
 near plane and the level scales s_l are parameters, not facts of the paper.
 """
