@@ -143,6 +143,34 @@ class Job:
                                       p["gamma"], p["color"])
         return self.fwd_out
 
+    def full_step(self):
+        """A whole training iteration: forward, the paper's objective
+        (nexel_loss_image / _params) against a fixed target, backward, and
+        the Adam step over every parameter (learning rates 0, so the timed
+        workload stays the same from step to step; the arithmetic is the
+        same), plus the FP16 refresh of the table's storage copy."""
+        R, p = self.R, self.p
+        if not hasattr(self, "objective"):
+            import torch
+            H, W = self.cam.height, self.cam.width
+            g = torch.Generator(device="cpu").manual_seed(321)
+            self.target = torch.rand(H, W, 3, generator=g).to(self.d_image.device)
+            self.objective = R.Objective(W, H, self.d_image.device)
+            ts = [p[k] for k in ("mu", "quat", "scale", "opacity", "gamma", "color")]
+            self.adam = R.Adam(ts + [self.field.table, self.field.weights], [0.0] * 8)
+        out = self.forward(self.st_train)
+        d_img, d_w, d_t = self.objective.image_terms(out["image"], self.target, out["weights"],
+                                                     out["textures"])
+        g = self.R.backward(self.ws, self.cam_s, self.st_train, self.field, self.ts, self.wts,
+                            p["mu"], p["quat"], p["scale"], p["opacity"], p["gamma"], out,
+                            d_img, d_w, d_t, grads=self.grads)
+        self.grads = g
+        self.objective.param_terms(p["opacity"], self.field, g["opacity"], g["table"])
+        self.adam.step([g[k] for k in ("mu", "quat", "scale", "opacity", "gamma", "color",
+                                       "table", "mlp")])
+        self.ts.copy_(self.field.table)
+        return out
+
     def step(self):
         out = self.forward(self.st_train)
         p = self.p
@@ -407,6 +435,9 @@ def main():
     results["f32_fwd"] = timed(jobs["f32"].forward, args.steps, flush, stream)
     results["f16_train"] = timed(jobs["f16"].step, args.steps, flush, stream)
     results["f16_fwd"] = timed(jobs["f16"].forward, args.steps, flush, stream)
+    for _ in range(3):
+        jobs["bf16"].full_step()
+    results["bf16_full"] = timed(jobs["bf16"].full_step, args.steps, flush, stream)
     barrier()
     clk = clocks.stop()  # samples over all four timed regions
     # per-kernel CUDA events on the launch stream, same steps again
@@ -503,6 +534,11 @@ def main():
                                     "render_fps": 1e3 / ms["f16_fwd"],
                                     "render_ms": ms["f16_fwd"]},
         },
+        "full_training_iteration": {
+            "train_mpix_s": mpix(ms["bf16_full"]), "train_ms": ms["bf16_full"],
+            "note": "BF16 form: forward + the paper's objective (L1, D-SSIM, texture, alpha, "
+                    "opacity, grid) + backward + Adam over all parameters + FP16 table "
+                    "refresh, all on the GPU"},
         "batched": None if batch is None else {
             "workload": BatchJob.WORKLOAD, "pixels_per_step": batch.pixels,
             "graph_train_mpix_s": world * batch.pixels / (ms["batch_graph"] * 1e-3) / 1e6,

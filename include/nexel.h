@@ -246,6 +246,59 @@ int nexel_read_status(const nexel_camera* cam, const nexel_settings* settings,
                       const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
                       size_t bwd_ws_bytes, nexel_stream_t stream);
 
+/* Training objective of Sec. 5 ("Losses"):
+ *   L = (1 - l_dssim) L_1 + l_dssim L_D-SSIM + l_alpha L_alpha
+ *       + l_texture L_texture + l_opacity L_opacity + l_grid L_grid
+ * with the paper's weights l_dssim 0.2, l_alpha 0.005, l_texture 0.5,
+ * l_opacity 0.01, l_grid 0.01.  L_D-SSIM = 1 - SSIM (3DGS's form: 11 x 11
+ * Gaussian window, sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2, mean
+ * over pixels and channels); L_texture averages |I_GT - sum_j W_j T_j /
+ * sum_j W_j| (pixels with sum_j W_j = 0 add nothing); L_alpha averages
+ * 1 - sum_j W_j; L_opacity averages the opacities; L_grid =
+ * sum_l s_l^-3 sum_{i,j} H_{l,i,j}^2 (the printed formula indexes s by the
+ * entry and leaves H unsquared; this is the reading).  |.| has derivative
+ * sign(.), sign(0) = 0. */
+typedef struct {
+  float dssim, alpha, texture, opacity, grid;
+} nexel_loss_weights;
+
+/* Bytes of device scratch for the objective on a width x height image. */
+int nexel_loss_workspace_size(int width, int height, size_t* bytes);
+
+/* Image-space terms.  image, target [H][W][3]; weights [H][W][K] and
+ * textures [H][W][K][3] are the forward's W and T (may be NULL when K = 0:
+ * the texture and alpha terms are then 0).  Writes (device, overwritten)
+ * d_image = dL/dimage, d_weights = dL/dW, d_textures = dL/dT -- the upstream
+ * gradients nexel_render_bwd takes -- and values[0..4] = L_1, L_D-SSIM,
+ * L_texture, L_alpha and the weighted sum of these four (device floats,
+ * summed in a fixed order, so repeated calls give identical values). */
+int nexel_loss_image(int width, int height, int K, const nexel_loss_weights* lw,
+                     const float* image, const float* target, const float* weights,
+                     const float* textures, void* ws, size_t ws_bytes, float* values,
+                     float* d_image, float* d_weights, float* d_textures, nexel_stream_t stream);
+
+/* Parameter-space terms, after nexel_loss_image and nexel_render_bwd on the
+ * same values array and ws (with the same width and height): ADDS
+ * l_opacity / N to every d_opacity[i] and l_grid 2 s_l^-3 H to every
+ * d_table entry (either pointer may be NULL), and writes values[5] =
+ * L_opacity, values[6] = L_grid, values[7] = the total L.  table is the
+ * FP32 master table [L][T][F] (field->table is not read); field may be NULL
+ * (no grid term). */
+int nexel_loss_params(int N, const float* opacity, const nexel_field* field, const float* table,
+                      const nexel_loss_weights* lw, void* ws, size_t ws_bytes, int width,
+                      int height, float* values, float* d_opacity, float* d_table,
+                      nexel_stream_t stream);
+
+/* One Adam step (Kingma and Ba; the optimiser of the 3DGS scheme the paper
+ * follows) over n_tensors FP32 tensors in one launch per 16 tensors:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr m / (1 - b1^step) / (sqrt(v / (1 - b2^step)) + eps).  Host arrays
+ * of device pointers params, grads, m, v (moments start at zero), host
+ * arrays sizes (elements) and lrs (per-tensor learning rate); step >= 1. */
+int nexel_adam_step(int n_tensors, float* const* params, const float* const* grads,
+                    float* const* m, float* const* v, const long long* sizes, const float* lrs,
+                    float beta1, float beta2, float eps, int step, nexel_stream_t stream);
+
 /* Inspection of the binning done by the last nexel_preprocess on ws: the
  * n_instances (tile, surfel) pairs in the order the collection pass walks
  * them, i.e. by tile, then by centre view depth (Sec. 3, "Preliminaries"),

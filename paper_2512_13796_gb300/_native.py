@@ -32,7 +32,8 @@ EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess
            "nexel_render_fwd", "nexel_render_bwd", "nexel_instance_list", "nexel_status_string",
            "nexel_version", "nexel_launch_count", "nexel_profile_enable", "nexel_profile_read",
            "nexel_render_fwd_static", "nexel_preprocess_async", "nexel_render_batch_fwd",
-           "nexel_render_batch_bwd", "nexel_read_status"]
+           "nexel_render_batch_bwd", "nexel_read_status", "nexel_loss_workspace_size",
+           "nexel_loss_image", "nexel_loss_params", "nexel_adam_step"]
 
 
 def _nvcc() -> str:
@@ -88,6 +89,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 # ------------------------------------------------------------- C structs
+class LossWeights(C.Structure):
+    _fields_ = [("dssim", C.c_float), ("alpha", C.c_float), ("texture", C.c_float),
+                ("opacity", C.c_float), ("grid", C.c_float)]
+
+
 class Camera(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("fx", C.c_float), ("fy", C.c_float),
                 ("cx", C.c_float), ("cy", C.c_float), ("world_to_cam", C.c_float * 12),
@@ -136,6 +142,11 @@ def lib(auto_build: bool = False):
     L.nexel_render_batch_bwd.argtypes = ([i, vp, vp, vp, i] + [vp] * 5 + [vp] * 4 + [vp] * 4 +
                                          [vp] * 3 + [i] + [vp] * 8 + [vp])
     L.nexel_read_status.argtypes = [vp, vp, vp, i, vp, sz, vp, sz, vp]
+    L.nexel_loss_workspace_size.argtypes = [i, i, C.POINTER(sz)]
+    L.nexel_loss_image.argtypes = [i, i, i, vp] + [vp] * 4 + [vp, sz, vp] + [vp] * 3 + [vp]
+    L.nexel_loss_params.argtypes = [i, vp, vp, vp, vp, vp, sz, i, i, vp, vp, vp, vp]
+    L.nexel_adam_step.argtypes = [i, vp, vp, vp, vp, vp, vp, C.c_float, C.c_float, C.c_float,
+                                  i, vp]
     L.nexel_launch_count.restype = C.c_longlong
     L.nexel_launch_count.argtypes = []
     L.nexel_profile_enable.argtypes = [i]
@@ -283,6 +294,34 @@ def nexel_read_status(cam, st, field, N, ws, ws_bytes, bws, bws_bytes, stream) -
     if rc not in (NEXEL_OK, -3, -5):
         raise NexelError("nexel_read_status", rc)
     return rc
+
+
+def nexel_loss_workspace_size(width: int, height: int) -> int:
+    out = C.c_size_t(0)
+    check("nexel_loss_workspace_size",
+          lib().nexel_loss_workspace_size(width, height, C.byref(out)))
+    return out.value
+
+
+def nexel_loss_image(width, height, K, lw, image, target, weights, textures, ws, ws_bytes,
+                     values, d_image, d_weights, d_textures, stream) -> int:
+    return check("nexel_loss_image", lib().nexel_loss_image(
+        width, height, K, C.byref(lw), image, target, weights, textures, ws, ws_bytes, values,
+        d_image, d_weights, d_textures, stream))
+
+
+def nexel_loss_params(N, opacity, field, table, lw, ws, ws_bytes, width, height, values,
+                      d_opacity, d_table, stream) -> int:
+    return check("nexel_loss_params", lib().nexel_loss_params(
+        N, opacity, C.byref(field) if field is not None else None, table, C.byref(lw), ws,
+        ws_bytes, width, height, values, d_opacity, d_table, stream))
+
+
+def nexel_adam_step(params, grads, m, v, sizes, lrs, beta1, beta2, eps, step, stream) -> int:
+    n = len(params)
+    return check("nexel_adam_step", lib().nexel_adam_step(
+        n, _ptrs(params), _ptrs(grads), _ptrs(m), _ptrs(v), (C.c_longlong * n)(*sizes),
+        (C.c_float * n)(*lrs), beta1, beta2, eps, step, stream))
 
 
 def nexel_launch_count() -> int:

@@ -372,3 +372,75 @@ class BatchStep:
         return [N_.nexel_read_status(cs, self.st, self.fs, self.N, self.ws[v].data_ptr(),
                                      self.ws_bytes[v], _ptr(self.bws[v]), self.bws_bytes[v],
                                      _stream()) for v, cs in enumerate(self.cams)]
+
+
+PAPER_LOSS_WEIGHTS = dict(dssim=0.2, alpha=0.005, texture=0.5, opacity=0.01, grid=0.01)
+
+
+class Objective:
+    """The training objective of the paper's Sec. 5 on the GPU
+    (nexel_loss_image / nexel_loss_params) for one image size.  ``values``
+    (device, 8 floats) holds L_1, L_D-SSIM, L_texture, L_alpha, their
+    weighted sum, L_opacity, L_grid and the total after both calls."""
+
+    NAMES = ("l1", "dssim", "texture", "alpha", "image_terms", "opacity", "grid", "total")
+
+    def __init__(self, width: int, height: int, device, weights: dict | None = None):
+        self.W, self.H = int(width), int(height)
+        w = dict(PAPER_LOSS_WEIGHTS, **(weights or {}))
+        self.lw = N_.LossWeights(**{k: float(w[k]) for k in ("dssim", "alpha", "texture",
+                                                               "opacity", "grid")})
+        nbytes = N_.nexel_loss_workspace_size(self.W, self.H)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.values = torch.zeros(8, device=device)
+
+    def image_terms(self, image, target, weights=None, textures=None):
+        """Returns (d_image, d_weights, d_textures) for nexel_render_bwd."""
+        K = 0 if weights is None else int(weights.shape[-1])
+        d_image = torch.empty_like(image)
+        d_w = torch.empty_like(weights) if K else None
+        d_t = torch.empty_like(textures) if K else None
+        N_.nexel_loss_image(self.W, self.H, K, self.lw, image.data_ptr(), target.data_ptr(),
+                            _ptr(weights) if K else None, _ptr(textures) if K else None,
+                            self.ws.data_ptr(), self.ws.numel(), self.values.data_ptr(),
+                            d_image.data_ptr(), _ptr(d_w), _ptr(d_t), _stream())
+        return d_image, d_w, d_t
+
+    def param_terms(self, opacity, field: DeviceField | None, d_opacity=None, d_table=None):
+        """Adds the opacity and grid regularisers' gradients (after the
+        render backward) and completes ``values``."""
+        fs = None
+        if field is not None:
+            fs = N_.Field()
+            fs.L, fs.T, fs.F = field.L, field.T, field.F
+            for l in range(field.L):
+                fs.level_scale[l] = float(field.level_scale[l])
+        N_.nexel_loss_params(int(opacity.shape[0]), opacity.data_ptr(), fs,
+                             field.table.data_ptr() if field is not None else None, self.lw,
+                             self.ws.data_ptr(), self.ws.numel(), self.W, self.H,
+                             self.values.data_ptr(), _ptr(d_opacity), _ptr(d_table), _stream())
+
+    def read(self) -> dict:
+        v = self.values.cpu().tolist()
+        return dict(zip(self.NAMES, v))
+
+
+class Adam:
+    """Adam over a list of FP32 tensors, one launch (nexel_adam_step) per
+    step for up to 16 tensors."""
+
+    def __init__(self, tensors: list, lrs: list, betas=(0.9, 0.999), eps: float = 1e-15):
+        self.p = list(tensors)
+        self.lrs = [float(x) for x in lrs]
+        self.m = [torch.zeros_like(t) for t in self.p]
+        self.v = [torch.zeros_like(t) for t in self.p]
+        self.b1, self.b2 = float(betas[0]), float(betas[1])
+        self.eps = float(eps)
+        self.t = 0
+
+    def step(self, grads: list):
+        self.t += 1
+        N_.nexel_adam_step([t.data_ptr() for t in self.p], [g.data_ptr() for g in grads],
+                           [t.data_ptr() for t in self.m], [t.data_ptr() for t in self.v],
+                           [t.numel() for t in self.p], self.lrs, self.b1, self.b2, self.eps,
+                           self.t, _stream())
