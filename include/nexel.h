@@ -101,6 +101,14 @@ typedef struct {
    * there instead.  Both calls must then get the same bwd_ws, with no other
    * call on it in between. */
   int cache_features;
+  /* Per-primitive colour (Sec. 3: channel-wise spherical-harmonics
+   * coefficients; Sec. 5: degree 3).  0: `color` is RGB [N][3], used as
+   * is.  3: `color` is [N][16][3] coefficients of the real SH of degree
+   * <= 3 (orthonormal, ordered by l then m = -l..l, Condon-Shortley phase),
+   * evaluated in the direction from the camera centre to the surfel centre:
+   * colour = 1/2 + sum_k Y_k(dir) c_k; d_color of nexel_render_bwd is then
+   * [N][16][3] and d_mu includes the path through the direction. */
+  int sh_degree;
 } nexel_settings;
 
 /* Neural field of Sec. 3 ("Instant-NGP") and Eq. 4: L hash tables of T

@@ -18,6 +18,9 @@ Functions and the passages they follow:
   depth_order           Sec. 3 (sorted by the depth of the centres)
   storage_bytes         supp. Sec. 7.1, last paragraph (2 B per Instant-NGP
                         parameter, 4 B otherwise)
+  render_sh, render_bwd_sh, sh (module)
+                        Sec. 3 (view-dependent radiance as channel-wise SH
+                        coefficients) with Sec. 5's degree 3 (S = 16)
   objective (module)    Sec. 5, "Losses": L_1, D-SSIM, L_texture, L_alpha,
                         L_opacity, L_grid, the weighted total, and the Adam
                         step of the 3DGS scheme the paper follows (plain
@@ -205,6 +208,35 @@ def render_bwd(scene, cam, settings, field, pixels, d_image, d_weights=None,
         offs = np.cumsum([0] + [w.size for w in field.weights])
         g["mlp_layers"] = [g["mlp"][offs[i]:offs[i + 1]].reshape(field.weights[i].shape)
                            for i in range(len(field.weights))]
+    return g
+
+
+def _with_colors(scene, rgb):
+    import types
+    return types.SimpleNamespace(mu=scene.mu, quat=scene.quat, scale=scene.scale,
+                                 opacity=scene.opacity, gamma=scene.gamma, color=rgb, n=scene.n)
+
+
+def render_sh(scene, coeffs, cam, settings, field=None, pixels=None, **kw) -> dict:
+    """render() with degree-3 SH per-primitive colours (coefficients
+    [N, 16, 3]), evaluated per surfel as oracle/sh.py states."""
+    from . import sh
+    rgb = sh.primitive_colors(scene.mu, coeffs, sh.camera_center(cam))
+    return render(_with_colors(scene, rgb), cam, settings, field, pixels, **kw)
+
+
+def render_bwd_sh(scene, coeffs, cam, settings, field, pixels, d_image, d_weights=None,
+                  d_textures=None, table=None) -> dict:
+    """render_bwd() for SH per-primitive colours: the colour gradient is
+    taken to the coefficients ([N, 16, 3]) and, through the direction, to mu."""
+    from . import sh
+    center = sh.camera_center(cam)
+    rgb = sh.primitive_colors(scene.mu, coeffs, center)
+    g = render_bwd(_with_colors(scene, rgb), cam, settings, field, pixels, d_image, d_weights,
+                   d_textures, table)
+    dc, dmu = sh.primitive_colors_bwd(scene.mu, coeffs, center, g["color"])
+    g["color"] = dc
+    g["mu"] = g["mu"] + dmu
     return g
 
 

@@ -104,7 +104,7 @@ class Settings(C.Structure):
     _fields_ = [("K", C.c_int), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("T_min", C.c_float), ("bg", C.c_float * 3), ("grid_dtype", C.c_int),
                 ("mlp_dtype", C.c_int), ("recompute_buffers", C.c_int),
-                ("cache_features", C.c_int)]
+                ("cache_features", C.c_int), ("sh_degree", C.c_int)]
 
 
 class Field(C.Structure):

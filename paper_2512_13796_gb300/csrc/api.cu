@@ -44,6 +44,7 @@ static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
   L.rect = take(n * 8);
   L.conic = take(n * 48);
   L.tmask = take(n * 16);
+  L.shj = take(n * 36);  // SH colour mode: d colour / d direction per surfel
   L.count = take(n * 4);
   L.offs = take((n + 1) * 4);
   L.ranges = take((size_t)L.n_tiles * 8);
@@ -176,7 +177,8 @@ static bool settings_ok(const nexel_settings* s) {
   return s && s->K >= 0 && s->K <= NEXEL_MAX_K && s->alpha_min > 0.f && s->alpha_max > 0.f &&
          s->alpha_max <= 1.f && s->alpha_min <= s->alpha_max && s->T_min >= 0.f &&
          s->T_min < 1.f && (s->grid_dtype == NEXEL_F32 || s->grid_dtype == NEXEL_F16) &&
-         (s->mlp_dtype == NEXEL_F32 || s->mlp_dtype == NEXEL_BF16 || s->mlp_dtype == NEXEL_F16);
+         (s->mlp_dtype == NEXEL_F32 || s->mlp_dtype == NEXEL_BF16 || s->mlp_dtype == NEXEL_F16) &&
+         (s->sh_degree == 0 || s->sh_degree == 3);
 }
 
 static bool field_ok(const nexel_field* f) {

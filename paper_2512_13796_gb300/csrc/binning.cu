@@ -138,13 +138,15 @@ __device__ __forceinline__ bool tile_may_hit(const TileConic& k, int tx, int ty,
   return !(q > 1e-3f);  // NaN keeps the tile
 }
 
-__global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __restrict__ mu,
+__global__ void k_preprocess(DevCam c, float alpha_min, int sh_degree, int N,
+                             const float* __restrict__ mu,
                              const float* __restrict__ quat, const float* __restrict__ scale,
                              const float* __restrict__ opac, const float* __restrict__ gam,
                              const float* __restrict__ color, float4* __restrict__ geom,
                              float4* __restrict__ aux, uint32_t* __restrict__ dkey,
                              uint32_t* __restrict__ did, uint2* __restrict__ rect,
-                             float4* __restrict__ conic, uint32_t* __restrict__ count) {
+                             float4* __restrict__ conic, uint32_t* __restrict__ count,
+                             float* __restrict__ shj) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   did[i] = (uint32_t)i;
@@ -276,7 +278,35 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int N, const float* __re
   g[1] = make_float4(z, o, g1, g2);
   g[2] = make_float4(nc.x / c.fx, nc.y / c.fy, Cux / c.fx, Cuy / c.fy);
   g[3] = make_float4(Cvx / c.fx, Cvy / c.fy, dn0, 0.f);
-  g[4] = make_float4(color[3 * i], color[3 * i + 1], color[3 * i + 2], __uint_as_float((uint32_t)i));
+  float3 rgb;
+  if (sh_degree == 3) {
+    // degree-3 SH coefficients [16][3], evaluated in the direction from the
+    // camera centre to the surfel centre, plus one half
+    float dx = m[0] - c.o[0], dy = m[1] - c.o[1], dz = m[2] - c.o[2];
+    const float inv = rsqrtf(fmaxf(dx * dx + dy * dy + dz * dz, 1e-30f));
+    const Sh3 Y = sh3_eval(dx * inv, dy * inv, dz * inv);
+    const float* cf = color + (size_t)48 * i;
+    rgb = make_float3(0.5f, 0.5f, 0.5f);
+    float w[3][16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      w[0][k] = cf[3 * k]; w[1][k] = cf[3 * k + 1]; w[2][k] = cf[3 * k + 2];
+      rgb.x = fmaf(Y.y[k], w[0][k], rgb.x);
+      rgb.y = fmaf(Y.y[k], w[1][k], rgb.y);
+      rgb.z = fmaf(Y.y[k], w[2][k], rgb.z);
+    }
+    // d colour_ch / d dir (for the backward, which has no coefficients)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const float3 gd = sh3_grad_dot(dx * inv, dy * inv, dz * inv, w[ch]);
+      shj[9 * (size_t)i + 3 * ch] = gd.x;
+      shj[9 * (size_t)i + 3 * ch + 1] = gd.y;
+      shj[9 * (size_t)i + 3 * ch + 2] = gd.z;
+    }
+  } else {
+    rgb = make_float3(color[3 * i], color[3 * i + 1], color[3 * i + 2]);
+  }
+  g[4] = make_float4(rgb.x, rgb.y, rgb.z, __uint_as_float((uint32_t)i));
   float4* a = aux + (size_t)i * kAuxF4;
   a[0] = make_float4(mx, my, z, s1);
   a[1] = make_float4(v1c.x, v1c.y, v1c.z, s2);
@@ -688,9 +718,11 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
   {
     NEXEL_PROF("preprocess", st);
     k_preprocess<<<(N + 255) / 256, 256, 0, st>>>(
-        c, s.alpha_min, N, mu, quat, scale, opacity, gamma, color, (float4*)(ws + L.geom_orig),
+        c, s.alpha_min, s.sh_degree, N, mu, quat, scale, opacity, gamma, color,
+        (float4*)(ws + L.geom_orig),
         (float4*)(ws + L.aux_orig), (uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.did0),
-        (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint32_t*)(ws + L.count));
+        (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint32_t*)(ws + L.count),
+        (float*)(ws + L.shj));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -792,7 +824,8 @@ __device__ __forceinline__ void acc(float* p, float v) {
 
 // kAtomic: views rendered concurrently add into the same gradients.
 template <bool kAtomic>
-__global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ quat,
+__global__ void k_preprocess_bwd(DevCam c, int N, int sh_degree, const float* __restrict__ mu,
+                                 const float* __restrict__ shj, const float* __restrict__ quat,
                                  const uint32_t* __restrict__ did, const uint32_t* __restrict__ dkey,
                                  const float* __restrict__ gs, float* __restrict__ d_mu,
                                  float* __restrict__ d_quat, float* __restrict__ d_scale,
@@ -821,10 +854,35 @@ __global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ quat
   float gz = G[0] * (-4 * zq) + G[1] * (-2 * w) + G[2] * (2 * x) + G[3] * (2 * w) +
              G[4] * (-4 * zq) + G[5] * (2 * y) + G[6] * (2 * x) + G[7] * (2 * y);
   float dot = w * gw + x * gx + y * gy + zq * gz;
+  float3 gm = g_m;
+  if (sh_degree == 3) {
+    // colour = 1/2 + sum_k Y_k(dir) c_k with dir = (mu - o) / |mu - o|:
+    // dL/dc_k = Y_k dL/dcolour; dL/dmu through the direction
+    const float vx = mu[3 * i] - c.o[0], vy = mu[3 * i + 1] - c.o[1], vz = mu[3 * i + 2] - c.o[2];
+    const float inv = rsqrtf(fmaxf(vx * vx + vy * vy + vz * vz, 1e-30f));
+    const float x = vx * inv, y = vy * inv, zd = vz * inv;
+    const float* J = shj + 9 * (size_t)i;  // d colour_ch / d dir, from the forward
+    const float3 q = make_float3(g[17] * J[0] + g[18] * J[3] + g[19] * J[6],
+                                 g[17] * J[1] + g[18] * J[4] + g[19] * J[7],
+                                 g[17] * J[2] + g[18] * J[5] + g[19] * J[8]);
+    const float qd = q.x * x + q.y * y + q.z * zd;
+    gm.x += (q.x - x * qd) * inv;
+    gm.y += (q.y - y * qd) * inv;
+    gm.z += (q.z - zd * qd) * inv;
+    if (d_color) {
+      const Sh3 Y = sh3_eval(x, y, zd);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        acc<kAtomic>(d_color + 48 * (size_t)i + 3 * k, Y.y[k] * g[17]);
+        acc<kAtomic>(d_color + 48 * (size_t)i + 3 * k + 1, Y.y[k] * g[18]);
+        acc<kAtomic>(d_color + 48 * (size_t)i + 3 * k + 2, Y.y[k] * g[19]);
+      }
+    }
+  }
   if (d_mu) {
-    acc<kAtomic>(d_mu + 3 * i, g_m.x);
-    acc<kAtomic>(d_mu + 3 * i + 1, g_m.y);
-    acc<kAtomic>(d_mu + 3 * i + 2, g_m.z);
+    acc<kAtomic>(d_mu + 3 * i, gm.x);
+    acc<kAtomic>(d_mu + 3 * i + 1, gm.y);
+    acc<kAtomic>(d_mu + 3 * i + 2, gm.z);
   }
   if (d_quat) {
     acc<kAtomic>(d_quat + 4 * i, (gw - w * dot) * qn);
@@ -841,7 +899,7 @@ __global__ void k_preprocess_bwd(DevCam c, int N, const float* __restrict__ quat
     acc<kAtomic>(d_gamma + 2 * i, g[15]);
     acc<kAtomic>(d_gamma + 2 * i + 1, g[16]);
   }
-  if (d_color) {
+  if (d_color && sh_degree != 3) {
     acc<kAtomic>(d_color + 3 * i, g[17]);
     acc<kAtomic>(d_color + 3 * i + 1, g[18]);
     acc<kAtomic>(d_color + 3 * i + 2, g[19]);
@@ -862,14 +920,16 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
     if (e == cudaSuccess && d_scale) e = cudaMemsetAsync(d_scale, 0, sizeof(float) * 2 * (size_t)N, st);
     if (e == cudaSuccess && d_opacity) e = cudaMemsetAsync(d_opacity, 0, sizeof(float) * (size_t)N, st);
     if (e == cudaSuccess && d_gamma) e = cudaMemsetAsync(d_gamma, 0, sizeof(float) * 2 * (size_t)N, st);
-    if (e == cudaSuccess && d_color) e = cudaMemsetAsync(d_color, 0, sizeof(float) * 3 * (size_t)N, st);
+    if (e == cudaSuccess && d_color)
+      e = cudaMemsetAsync(d_color, 0, sizeof(float) * (s.sh_degree == 3 ? 48 : 3) * (size_t)N, st);
     if (e != cudaSuccess) return e;
   }
   {
     NEXEL_PROF("preprocess_bwd", st);
     auto kern = atomic ? k_preprocess_bwd<true> : k_preprocess_bwd<false>;
     kern<<<(N + 255) / 256, 256, 0, st>>>(
-        c, N, quat, (uint32_t*)(ws + L.did0), (uint32_t*)(ws + L.dkey0),
+        c, N, s.sh_degree, mu, (const float*)(ws + L.shj), quat, (uint32_t*)(ws + L.did0),
+        (uint32_t*)(ws + L.dkey0),
         (float*)(ws + L.grad_sorted), d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color);
   }
   return cudaGetLastError();

@@ -35,6 +35,59 @@ struct DevCam {
   float near_;
 };
 
+// Real spherical harmonics of degree <= 3 at the unit direction (x, y, z)
+// (orthonormal on the sphere; ordered by degree l, then m = -l .. l; with
+// the Condon-Shortley phase): the per-primitive colour mode of Sec. 3 with
+// the degree of Sec. 5 (S = 16).
+struct Sh3 {
+  float y[16];
+};
+__host__ __device__ inline Sh3 sh3_eval(float x, float y, float z) {
+  // normalisation constants: sqrt((2l + 1) / (4 pi) (l - |m|)! / (l + |m|)!)
+  // times the factors of the Cartesian forms
+  const float k0 = 0.28209479177387814f, k1 = 0.48860251190291992f;
+  const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.54627421529603959f;
+  const float k3a = 0.59004358992664352f, k3b = 2.8906114426405538f, k3c = 0.45704579946446572f,
+              k3d = 0.37317633259011540f, k3e = 1.4453057213202769f;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Sh3 r;
+  r.y[0] = k0;
+  r.y[1] = -k1 * y; r.y[2] = k1 * z; r.y[3] = -k1 * x;
+  r.y[4] = k2a * x * y; r.y[5] = -k2a * y * z; r.y[6] = k2b * (2.f * zz - xx - yy);
+  r.y[7] = -k2a * x * z; r.y[8] = k2c * (xx - yy);
+  r.y[9] = -k3a * y * (3.f * xx - yy); r.y[10] = k3b * x * y * z;
+  r.y[11] = -k3c * y * (4.f * zz - xx - yy); r.y[12] = k3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  r.y[13] = -k3c * x * (4.f * zz - xx - yy); r.y[14] = k3e * z * (xx - yy);
+  r.y[15] = -k3a * x * (xx - 3.f * yy);
+  return r;
+}
+// sum_k w[k] dY_k/d(x, y, z) of the polynomials above
+__host__ __device__ inline float3 sh3_grad_dot(float x, float y, float z, const float* w) {
+  const float k1 = 0.48860251190291992f;
+  const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.54627421529603959f;
+  const float k3a = 0.59004358992664352f, k3b = 2.8906114426405538f, k3c = 0.45704579946446572f,
+              k3d = 0.37317633259011540f, k3e = 1.4453057213202769f;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  gy += -k1 * w[1]; gz += k1 * w[2]; gx += -k1 * w[3];
+  gx += k2a * y * w[4]; gy += k2a * x * w[4];
+  gy += -k2a * z * w[5]; gz += -k2a * y * w[5];
+  gx += -2.f * k2b * x * w[6]; gy += -2.f * k2b * y * w[6]; gz += 4.f * k2b * z * w[6];
+  gx += -k2a * z * w[7]; gz += -k2a * x * w[7];
+  gx += 2.f * k2c * x * w[8]; gy += -2.f * k2c * y * w[8];
+  gx += -6.f * k3a * x * y * w[9]; gy += -3.f * k3a * (xx - yy) * w[9];
+  gx += k3b * y * z * w[10]; gy += k3b * x * z * w[10]; gz += k3b * x * y * w[10];
+  gx += 2.f * k3c * x * y * w[11]; gy += -k3c * (4.f * zz - xx - 3.f * yy) * w[11];
+  gz += -8.f * k3c * y * z * w[11];
+  gx += -6.f * k3d * x * z * w[12]; gy += -6.f * k3d * y * z * w[12];
+  gz += k3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+  gx += -k3c * (4.f * zz - 3.f * xx - yy) * w[13]; gy += 2.f * k3c * x * y * w[13];
+  gz += -8.f * k3c * x * z * w[13];
+  gx += 2.f * k3e * x * z * w[14]; gy += -2.f * k3e * y * z * w[14]; gz += k3e * (xx - yy) * w[14];
+  gx += -3.f * k3a * (xx - yy) * w[15]; gy += 6.f * k3a * x * y * w[15];
+  return make_float3(gx, gy, gz);
+}
+
 // Packed per-surfel record (rank order), see the preprocess kernel:
 //  q0 = (cpx_hi, cpy_hi, cpx_lo, cpy_lo)  projected centre, pixels, as a
 //        float-float pair (hi + lo)
@@ -130,6 +183,7 @@ constexpr size_t kStatusOffset = 32;
 // every call re-derives the same layout from (camera, K, N, ws_bytes).
 struct WsLayout {
   size_t geom_orig, geom_sorted, aux_orig, aux_sorted, dkey0, dkey1, did0, did1, rect, conic, tmask, count,
+      shj,
       offs,
       ranges, n_contrib,
       grad_sorted, counters, fixed_end, inst0, inst1, hist, scan_sums, total;

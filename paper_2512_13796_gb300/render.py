@@ -26,7 +26,8 @@ def camera_struct(cam) -> N_.Camera:
 
 
 def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32",
-                    recompute: bool = False, cache_features: bool = False) -> N_.Settings:
+                    recompute: bool = False, cache_features: bool = False,
+                    sh_degree: int = 0) -> N_.Settings:
     s = N_.Settings()
     s.K = int(st.K)
     s.alpha_min, s.alpha_max, s.T_min = float(st.alpha_min), float(st.alpha_max), float(st.T_min)
@@ -36,6 +37,7 @@ def settings_struct(st, grid_dtype: str = "f32", mlp_dtype: str = "f32",
     s.mlp_dtype = {"f32": N_.F32, "bf16": N_.BF16, "f16": N_.F16}[mlp_dtype]
     s.recompute_buffers = 1 if recompute else 0
     s.cache_features = 1 if cache_features else 0
+    s.sh_degree = int(sh_degree)
     return s
 
 
@@ -158,8 +160,9 @@ def backward(ws: Workspace, cam_s, st_s, field, table_store, weights, mu, quat, 
     N = mu.shape[0]
     K = st_s.K
     g = grads if grads is not None else {}
+    cshape = (N, 16, 3) if st_s.sh_degree == 3 else (N, 3)
     for k, shape in (("mu", (N, 3)), ("quat", (N, 4)), ("scale", (N, 2)), ("opacity", (N,)),
-                     ("gamma", (N, 2)), ("color", (N, 3))):
+                     ("gamma", (N, 2)), ("color", cshape)):
         if k not in g:
             g[k] = torch.zeros(shape, device=dev)
     fs = None
@@ -294,7 +297,8 @@ class BatchStep:
         N = self.N
         self.grads = dict(mu=torch.zeros(N, 3, device=dev), quat=torch.zeros(N, 4, device=dev),
                           scale=torch.zeros(N, 2, device=dev), opacity=torch.zeros(N, device=dev),
-                          gamma=torch.zeros(N, 2, device=dev), color=torch.zeros(N, 3, device=dev))
+                          gamma=torch.zeros(N, 2, device=dev),
+                          color=torch.zeros_like(self.params["color"]))
         if self.fs is not None:
             self.grads["table"] = torch.zeros_like(field.table)
             self.grads["mlp"] = torch.zeros_like(field.weights)

@@ -247,6 +247,15 @@ def workload(idx: int, *, gamma: str | None = None, seed: int | None = None,
                     prec)
 
 
+def sh_coefficients(n: int, seed: int, rest_std: float = 0.2) -> np.ndarray:
+    """Seeded degree-3 SH colour coefficients [n, 16, 3] (float32): the
+    constant term U(-1, 1), the 15 higher ones N(0, rest_std)."""
+    rng = np.random.default_rng(seed + 71)
+    c = rng.normal(0.0, rest_std, size=(n, 16, 3))
+    c[:, 0, :] = rng.uniform(-1.0, 1.0, size=(n, 3))
+    return c.astype(np.float32)
+
+
 def pixel_sample(cam: Camera, n_random: int, n_tiles: int, seed: int,
                  tile: int = 16) -> np.ndarray:
     """Fixed pixel subsample: ``n_random`` pixels by seed plus every pixel of

@@ -1,0 +1,93 @@
+"""Degree-3 spherical-harmonics per-primitive colours (settings.sh_degree =
+3) against the FP64 oracle (oracle.render_sh / render_bwd_sh): images and
+the gradients of every parameter, the [N, 16, 3] coefficients included, on
+config 0 (every pixel, FP32 form) and on a config 1 pixel sample (FP32 and
+BF16 forms)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_13796_gb300 import synth
+
+from helpers import SURFEL_KEYS, compare_forward, compare_grads, masked_upstream
+
+pytestmark = pytest.mark.gpu
+
+TIE, CELL, RELU = 1e-5, 2e-6, 1e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    assert torch.cuda.is_available(), "GPU test without a CUDA device"
+    from paper_2512_13796_gb300 import _native
+    _native.build()
+    return torch.device("cuda:0")
+
+
+def _run(scene, coeffs, cam, st, field, dev, grid, mlp, dI=None, dW=None, dT=None):
+    import torch
+    from paper_2512_13796_gb300 import render as R
+    p = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k))).to(dev)
+         for k in SURFEL_KEYS}
+    p["color"] = torch.from_numpy(coeffs).to(dev)
+    fd = R.DeviceField.from_synth(field, dev, grid, mlp)
+    ws = R.Workspace(dev)
+    cam_s = R.camera_struct(cam)
+    st_s = R.settings_struct(st, grid, mlp, sh_degree=3)
+    ts = fd.storage_table()
+    out = R.forward(ws, cam_s, st_s, fd, ts, fd.weights, *[p[k] for k in SURFEL_KEYS])
+    g = None
+    if dI is not None:
+        t = lambda a: None if a is None else torch.from_numpy(a.astype(np.float32)).to(dev)
+        g = R.backward(ws, cam_s, st_s, fd, ts, fd.weights, *[p[k] for k in SURFEL_KEYS[:5]],
+                       out, t(dI), t(dW), t(dT))
+    torch.cuda.synchronize()
+    fw = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+    gg = None if g is None else {k: v.cpu().numpy() for k, v in g.items()}
+    return fw, gg
+
+
+def test_sh_config0_forward_backward(dev):
+    w = synth.workload(0, gamma="var")
+    cam, st = w.cameras[0], w.settings
+    coeffs = synth.sh_coefficients(w.scene.n, 0)
+    ref = oracle.render_sh(w.scene, coeffs, cam, st, w.field, tie_tol=TIE, cell_tol=CELL,
+                           relu_tol=RELU)
+    pix, ok = ref["pixels"], ref["tie"] == 0
+    P, K = cam.width * cam.height, st.K
+    dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=31)
+    fw, gg = _run(w.scene, coeffs, cam, st, w.field, dev, "f32", "f32", dI, dW, dT)
+    s = compare_forward(fw, ref, K, 1e-5)
+    assert s["n_tie"] < 0.25 * s["n_pix"]
+    sel = pix[ok]
+    gr = oracle.render_bwd_sh(w.scene, coeffs, cam, st, w.field, sel, dI[sel], dW[sel], dT[sel])
+    assert gg["color"].shape == (w.scene.n, 16, 3)
+    st_g = compare_grads(gg, gr, 1e-3)
+    print(f"\n[sh config0] fwd image err {s['image']:.2e} grads {st_g}")
+
+
+@pytest.mark.parametrize("form", ["f32", "bf16"])
+def test_sh_config1_sampled(dev, form):
+    w = synth.workload(1)
+    cam, st = w.cameras[0], w.settings
+    coeffs = synth.sh_coefficients(w.scene.n, 1)
+    pix = synth.pixel_sample(cam, 2048, 2, seed=7)
+    grid, mlp = ("f32", "f32") if form == "f32" else ("f16", "bf16")
+    ref = oracle.render_sh(w.scene, coeffs, cam, st, w.field, pix, tie_tol=TIE, cell_tol=CELL,
+                           relu_tol=RELU)
+    ok = ref["tie"] == 0
+    P, K = cam.width * cam.height, st.K
+    dI, _, _ = masked_upstream(pix.size, P, K, pix, ok, seed=32, with_wt=False)
+    fw, gg = _run(w.scene, coeffs, cam, st, w.field, dev, grid, mlp, dI)
+    # the per-primitive colour path is FP32 in both forms; the textures of the
+    # BF16 form carry its own tolerance
+    s = compare_forward(fw, ref, K, 1e-5 if form == "f32" else 2e-3)
+    assert s["n_tie"] < 0.25 * s["n_pix"]
+    sel = pix[ok]
+    gr = oracle.render_bwd_sh(w.scene, coeffs, cam, st, w.field, sel, dI[sel])
+    keys = ("mu", "quat", "scale", "opacity", "gamma", "color")
+    if form == "f32":
+        compare_grads(gg, gr, 1e-3, keys=keys + ("table", "mlp"))
+    else:
+        compare_grads(gg, gr, 0.1, keys=keys, metric="l2")
