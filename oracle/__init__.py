@@ -18,7 +18,7 @@ Functions and the passages they follow:
   depth_order           Sec. 3 (sorted by the depth of the centres)
   storage_bytes         supp. Sec. 7.1, last paragraph (2 B per Instant-NGP
                         parameter, 4 B otherwise)
-  render_sh, render_bwd_sh, sh (module)
+  render_sh, render_bwd_sh, sh (module), 48-output MLPs (SH textures)
                         Sec. 3 (view-dependent radiance as channel-wise SH
                         coefficients) with Sec. 5's degree 3 (S = 16)
   objective (module)    Sec. 5, "Losses": L_1, D-SSIM, L_texture, L_alpha,

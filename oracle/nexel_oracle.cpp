@@ -174,6 +174,63 @@ void mlp_backward(const OField& fd, const std::vector<std::vector<double>>& acts
   for (int i = 0; i < fd.widths[0]; ++i) g_in[i] = g[i];
 }
 
+// Real spherical harmonics of degree <= 3 at the unit direction (x, y, z):
+// orthonormal on the sphere, ordered by degree l and m = -l .. l, with the
+// Condon-Shortley phase.  An MLP with 48 outputs gives the texture as
+// channel-wise SH coefficients o[3k + ch] (Sec. 3: "a set of spherical
+// harmonics coefficients"; Sec. 5: degree 3), evaluated in the pixel's ray
+// direction: T_ch = sum_k Y_k(d / |d|) o[3k + ch].
+void sh3_basis(double x, double y, double z, double* Y) {
+  const double sp = std::sqrt(3.14159265358979323846);
+  const double k0 = 1.0 / (2.0 * sp), k1 = std::sqrt(3.0) / (2.0 * sp);
+  const double k2a = std::sqrt(15.0) / (2.0 * sp), k2b = std::sqrt(5.0) / (4.0 * sp),
+               k2c = std::sqrt(15.0) / (4.0 * sp);
+  const double k3a = std::sqrt(17.5) / (4.0 * sp), k3b = std::sqrt(105.0) / (2.0 * sp),
+               k3c = std::sqrt(10.5) / (4.0 * sp), k3d = std::sqrt(7.0) / (4.0 * sp),
+               k3e = std::sqrt(105.0) / (4.0 * sp);
+  const double xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = k0;
+  Y[1] = -k1 * y; Y[2] = k1 * z; Y[3] = -k1 * x;
+  Y[4] = k2a * x * y; Y[5] = -k2a * y * z; Y[6] = k2b * (2 * zz - xx - yy); Y[7] = -k2a * x * z;
+  Y[8] = k2c * (xx - yy);
+  Y[9] = -k3a * y * (3 * xx - yy); Y[10] = k3b * x * y * z; Y[11] = -k3c * y * (4 * zz - xx - yy);
+  Y[12] = k3d * z * (2 * zz - 3 * xx - 3 * yy); Y[13] = -k3c * x * (4 * zz - xx - yy);
+  Y[14] = k3e * z * (xx - yy); Y[15] = -k3a * x * (xx - 3 * yy);
+}
+
+// texture of one sample from the MLP output (3 outputs: RGB as is; 48: SH)
+void texture_from_output(const OField& fd, const std::vector<double>& out, const double d[3],
+                         double tex[3]) {
+  const int no = fd.widths[fd.n_layers];
+  if (no != 48) {
+    for (int ch = 0; ch < 3; ++ch) tex[ch] = out[ch];
+    return;
+  }
+  const double n = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  double Y[16];
+  sh3_basis(d[0] / n, d[1] / n, d[2] / n, Y);
+  for (int ch = 0; ch < 3; ++ch) {
+    tex[ch] = 0.0;
+    for (int k = 0; k < 16; ++k) tex[ch] += Y[k] * out[3 * k + ch];
+  }
+}
+
+// gradient with respect to the MLP output from the texture gradient gT
+std::vector<double> output_grad(const OField& fd, const double gT[3], const double d[3]) {
+  const int no = fd.widths[fd.n_layers];
+  std::vector<double> g(no, 0.0);
+  if (no != 48) {
+    for (int ch = 0; ch < 3; ++ch) g[ch] = gT[ch];
+    return g;
+  }
+  const double n = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  double Y[16];
+  sh3_basis(d[0] / n, d[1] / n, d[2] / n, Y);
+  for (int k = 0; k < 16; ++k)
+    for (int ch = 0; ch < 3; ++ch) g[3 * k + ch] = Y[k] * gT[ch];
+  return g;
+}
+
 // ------------------------------------------------------------- geometry
 void quat_to_rot(const double q[4], double R[9]) {
   double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
@@ -361,7 +418,7 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
     field_features(*fd, c.fx, x, e.t, feat.data(), keep ? &r.lev[j] : nullptr);
     std::vector<std::vector<double>> acts;
     mlp_forward(*fd, feat.data(), acts);
-    for (int ch = 0; ch < 3; ++ch) r.tex[j][ch] = acts[fd->n_layers][ch];
+    texture_from_output(*fd, acts[fd->n_layers], d, r.tex[j]);
     for (int ch = 0; ch < 3; ++ch) r.image[ch] += e.w * r.tex[j][ch];
     // a hidden pre-activation within relu_tol of zero (relative to the sum
     // of the magnitudes of its terms) is a ReLU decision that a
@@ -572,7 +629,9 @@ int oracle_render_bwd(const OCam* c, const OSet* st, const OField* fd, int N, co
       e[k] = dot3(r.tex[j], dC) + (d_weights ? d_weights[(size_t)p * K + j] : 0.0);
       if (!fd) continue;
       std::vector<double> gfeat(fd->widths[0]);
-      mlp_backward(*fd, r.acts[j], gT, gfeat.data(), n_mlp ? mlp_acc[tid].data() : nullptr);
+      const std::vector<double> gout = output_grad(*fd, gT, r.d);
+      mlp_backward(*fd, r.acts[j], gout.data(), gfeat.data(),
+                   n_mlp ? mlp_acc[tid].data() : nullptr);
       double x[3] = {r.o[0] + ce.t * r.d[0], r.o[1] + ce.t * r.d[1], r.o[2] + ce.t * r.d[2]};
       (void)x;
       double gx[3] = {0, 0, 0};

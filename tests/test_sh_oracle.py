@@ -92,3 +92,59 @@ def test_colour_gradient_matches_finite_differences():
         e = np.zeros_like(mu)
         e[i, j] = h
         assert abs((f(mu + e, c) - f(mu - e, c)) / (2 * h) - dmu[i, j]) < 1e-7
+
+
+def _field48_from_field3(f3):
+    """A 48-output field whose SH texture equals the RGB texture of f3: the
+    constant SH band carries W3 / Y_0, every other band is zero."""
+    import copy
+    f = copy.deepcopy(f3)
+    W3 = f3.weights[-1]
+    W48 = np.zeros((48, W3.shape[1]), np.float64)
+    for ch in range(3):
+        W48[ch] = W3[ch] / sh.K0
+    f.weights = list(f3.weights[:-1]) + [W48]
+    f.widths = tuple(f3.widths[:-1]) + (48,)
+    return f
+
+
+def test_sh_texture_with_only_the_constant_band_equals_rgb():
+    import oracle
+    from paper_2512_13796_gb300 import synth
+    w = synth.workload(0)
+    cam, st = w.cameras[0], w.settings
+    f48 = _field48_from_field3(w.field)
+    a = oracle.render(w.scene, cam, st, w.field)
+    b = oracle.render(w.scene, cam, st, f48)
+    np.testing.assert_allclose(b["textures"], a["textures"], atol=1e-12)
+    np.testing.assert_allclose(b["image"], a["image"], atol=1e-12)
+
+
+def test_sh_texture_gradient_matches_finite_differences():
+    """Central differences of <dI, image> against the oracle's backward for
+    weights of several SH bands of a 48-output field."""
+    import oracle
+    from paper_2512_13796_gb300 import synth
+    w = synth.workload(0)
+    cam, st = w.cameras[0], w.settings
+    rng = np.random.default_rng(12)
+    f48 = _field48_from_field3(w.field)
+    f48.weights[-1] = f48.weights[-1] + rng.normal(0, 0.3, f48.weights[-1].shape)
+    pix = np.arange(0, cam.width * cam.height, 7, dtype=np.int32)
+    ref = oracle.render(w.scene, cam, st, f48, pix, tie_tol=1e-5, cell_tol=1e-5, relu_tol=1e-4)
+    pix = pix[ref["tie"] == 0]
+    dI = rng.normal(size=(pix.size, 3))
+    g = oracle.render_bwd(w.scene, cam, st, f48, pix, dI)
+    f = lambda fld: float(np.sum(oracle.render(w.scene, cam, st, fld, pix)["image"] * dI))
+    h = 1e-6
+    n_last = f48.weights[-1].size
+    offs = sum(x.size for x in f48.weights[:-1])
+    import copy
+    for (o, i) in [(3 * 5 + 1, 2), (3 * 12 + 2, 7), (0, 0)]:
+        fp, fm = copy.deepcopy(f48), copy.deepcopy(f48)
+        fp.weights[-1][o, i] += h
+        fm.weights[-1][o, i] -= h
+        fd = (f(fp) - f(fm)) / (2 * h)
+        an = g["mlp"][offs + o * f48.weights[-1].shape[1] + i]
+        assert abs(fd - an) <= 1e-6 + 1e-4 * abs(fd), (o, i, fd, an)
+    assert n_last == 48 * f48.weights[-1].shape[1]
