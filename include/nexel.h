@@ -114,7 +114,10 @@ typedef struct {
 /* Neural field of Sec. 3 ("Instant-NGP") and Eq. 4: L hash tables of T
  * entries (T a power of two) with F features (F = 2), level scales s_l, and
  * an MLP without bias: widths[0] = L * F -> hidden ... -> widths[n_layers]
- * = 3, ReLU on hidden layers, linear output.  weights are float32 packed
+ * = 3 (RGB texture) or 48 (the texture's degree-3 SH coefficients o[3k + ch],
+ * Sec. 3 and Sec. 5, evaluated in the pixel's normalised ray direction:
+ * T_ch = sum_k Y_k(d / |d|) o[3k + ch]; FP32 form with 64-wide hidden
+ * layers only), ReLU on hidden layers, linear output.  weights are float32 packed
  * layer after layer, layer l row-major [widths[l+1]][widths[l]].  Hidden
  * widths must be multiples of 16 and at most 64; L * F a multiple of 8 and at
  * most 64. */

@@ -5,18 +5,22 @@
 
 namespace nexel {
 
+// (input, hidden 1, hidden 2, outputs): 3 outputs are RGB, 48 the degree-3
+// SH coefficients of the texture (FP32 form, chunked kernels only)
 #define NEXEL_ARCH_LIST(X) \
-  X(8, 16, 0)              \
-  X(16, 64, 0)             \
-  X(32, 64, 64)
+  X(8, 16, 0, 3)           \
+  X(16, 64, 0, 3)          \
+  X(32, 64, 64, 3)         \
+  X(16, 64, 0, 48)         \
+  X(32, 64, 64, 48)
 
 // Explicit instantiations live in one translation unit per architecture
 // (texture_f32_<in>_<h1>_<h2>.cu) so that they compile in parallel.
-#define X(a, b, cc)                                                                              \
-  extern template cudaError_t tex_fwd_f32<a, b, cc, float>(                                      \
+#define X(a, b, cc, o)                                                                           \
+  extern template cudaError_t tex_fwd_f32<a, b, cc, float, o>(                                   \
       const DevCam&, const nexel_settings&, const FieldDev&, const float*, const float*,         \
       const int*, const float*, const float*, float*, float*, cudaStream_t);                     \
-  extern template cudaError_t tex_bwd_f32<a, b, cc, float>(                                      \
+  extern template cudaError_t tex_bwd_f32<a, b, cc, float, o>(                                   \
       const DevCam&, const nexel_settings&, const FieldDev&, char*, const BwdLayout&,            \
       const float*, const int*, const float*, const float*, const float*, const float*, float*,  \
       float*, cudaStream_t);                                                                     \
@@ -24,10 +28,11 @@ namespace nexel {
 NEXEL_ARCH_LIST(X)
 #undef X
 
-static bool arch_match(const nexel_field& f, int in, int h1, int h2) {
-  if (h2 == 0) return f.n_layers == 2 && f.widths[0] == in && f.widths[1] == h1 && f.widths[2] == 3;
+static bool arch_match(const nexel_field& f, int in, int h1, int h2, int out) {
+  if (h2 == 0)
+    return f.n_layers == 2 && f.widths[0] == in && f.widths[1] == h1 && f.widths[2] == out;
   return f.n_layers == 3 && f.widths[0] == in && f.widths[1] == h1 && f.widths[2] == h2 &&
-         f.widths[3] == 3;
+         f.widths[3] == out;
 }
 
 bool texture_arch_supported(const nexel_settings& s, const nexel_field& f) {
@@ -37,7 +42,7 @@ bool texture_arch_supported(const nexel_settings& s, const nexel_field& f) {
     return f.widths[f.n_layers] == 3 && tc_arch_supported(f.widths[0], f.widths[1], h2);
   }
   if (s.grid_dtype != NEXEL_F32) return false;  // the FP32 form reads an FP32 table
-#define X(a, b, c) if (arch_match(f, a, b, c)) return true;
+#define X(a, b, c, o) if (arch_match(f, a, b, c, o)) return true;
   NEXEL_ARCH_LIST(X)
 #undef X
   return false;
@@ -53,10 +58,10 @@ cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const n
   if (s.mlp_dtype == NEXEL_BF16 || s.mlp_dtype == NEXEL_F16)
     return launch_texture_fwd_tc(c, s, f, fd, notex, weights, ids, depths, T_final, image,
                                  textures, status, st);
-#define X(a, b, cc)                                                                                \
-  if (arch_match(f, a, b, cc))                                                                     \
-    return tex_fwd_f32<a, b, cc, float>(c, s, fd, notex, weights, ids, depths, T_final, image, \
-                                        textures, st);
+#define X(a, b, cc, o)                                                                            \
+  if (arch_match(f, a, b, cc, o))                                                                  \
+    return tex_fwd_f32<a, b, cc, float, o>(c, s, fd, notex, weights, ids, depths, T_final, image, \
+                                           textures, st);
   NEXEL_ARCH_LIST(X)
 #undef X
   return cudaErrorInvalidValue;
@@ -90,10 +95,10 @@ cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const n
     return launch_hash_bwd(c, fd, s.K, KP, n_rows, s.grid_dtype == NEXEL_F16, ids, depths,
                            (const float2*)(bws + B.gin), (float*)(bws + B.ddepth), d_table, st);
   }
-#define X(a, b, cc)                                                                          \
-  if (arch_match(f, a, b, cc))                                                               \
-    return tex_bwd_f32<a, b, cc, float>(c, s, fd, bws, B, weights, ids, depths, d_image,      \
-                                        d_weights, d_textures, d_table, d_mlp, st);
+#define X(a, b, cc, o)                                                                       \
+  if (arch_match(f, a, b, cc, o))                                                            \
+    return tex_bwd_f32<a, b, cc, float, o>(c, s, fd, bws, B, weights, ids, depths, d_image,   \
+                                           d_weights, d_textures, d_table, d_mlp, st);
   NEXEL_ARCH_LIST(X)
 #undef X
   return cudaErrorInvalidValue;

@@ -40,18 +40,28 @@ inline FieldDev make_fielddev(const DevCam& c, const nexel_field& f) {
   return d;
 }
 
-template <int IN, int H1, int H2>
+// OUT = 3: RGB texture; OUT = 48: degree-3 SH coefficients of the texture
+// (o[3k + ch]), evaluated in the ray direction.
+template <int IN, int H1, int H2, int OUT = 3>
 struct MlpArch {
   static constexpr int HL = H2 > 0 ? H2 : H1;
   static constexpr int kOffLast = IN * H1 + (H2 > 0 ? H1 * H2 : 0);
-  static constexpr int kWeights = kOffLast + 3 * HL;
+  static constexpr int kWeights = kOffLast + OUT * HL;
 };
+
 
 // World-space direction of pixel (px, py), not normalised (z_cam = 1).
 __device__ __forceinline__ float3 pixel_dir(const DevCam& c, int px, int py) {
   float dx = (px + 0.5f - c.cx) / c.fx, dy = (py + 0.5f - c.cy) / c.fy;
   return make_float3(c.R[0] * dx + c.R[3] * dy + c.R[6], c.R[1] * dx + c.R[4] * dy + c.R[7],
                      c.R[2] * dx + c.R[5] * dy + c.R[8]);
+}
+
+// SH basis of degree <= 3 in the normalised ray direction of pixel p.
+__device__ __forceinline__ Sh3 pixel_sh3(const DevCam& c, long long p) {
+  const float3 d = pixel_dir(c, (int)(p % c.W), (int)(p / c.W));
+  const float inv = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+  return sh3_eval(d.x * inv, d.y * inv, d.z * inv);
 }
 
 // Raw table entry (the FP16 pair as its 32-bit pattern, or the FP32 pair)

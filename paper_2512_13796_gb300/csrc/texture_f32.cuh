@@ -316,21 +316,21 @@ size_t wgrad_smem_f32() {
 namespace f32c {
 constexpr int kPH = 65;  // padded row stride of 64-wide activation tiles
 
-// Weights, rows padded: W1 [H1][IN + 1], W2 [H2][H1 + 1], W3 [3][HL].
-template <int IN, int H1, int H2>
+// Weights, rows padded: W1 [H1][IN + 1], W2 [H2][H1 + 1], W3 [OUT][HL].
+template <int IN, int H1, int H2, int OUT = 3>
 struct Ws {
   static constexpr int HL = H2 > 0 ? H2 : H1;
   static constexpr int P1 = IN + 1, P2 = H1 + 1;
-  static constexpr int o2 = H1 * P1, o3 = o2 + H2 * P2, total = o3 + 3 * HL;
+  static constexpr int o2 = H1 * P1, o3 = o2 + H2 * P2, total = o3 + OUT * HL;
 };
-template <int IN, int H1, int H2>
+template <int IN, int H1, int H2, int OUT = 3>
 __device__ __forceinline__ void load_weights(const float* __restrict__ w, float* sW) {
-  using W = Ws<IN, H1, H2>;
-  using A = MlpArch<IN, H1, H2>;
+  using W = Ws<IN, H1, H2, OUT>;
+  using A = MlpArch<IN, H1, H2, OUT>;
   for (int k = threadIdx.x; k < H1 * IN; k += blockDim.x) sW[(k / IN) * W::P1 + k % IN] = w[k];
   for (int k = threadIdx.x; k < H2 * H1; k += blockDim.x)
     sW[W::o2 + (k / H1) * W::P2 + k % H1] = w[H1 * IN + k];
-  for (int k = threadIdx.x; k < 3 * W::HL; k += blockDim.x) sW[W::o3 + k] = w[A::kOffLast + k];
+  for (int k = threadIdx.x; k < OUT * W::HL; k += blockDim.x) sW[W::o3 + k] = w[A::kOffLast + k];
 }
 
 // Features of row `row` for the levels of quarter q (0..3) into sX.
@@ -388,13 +388,13 @@ __device__ __forceinline__ void dense_relu(const float* sA, int pa, const float*
 }
 }  // namespace f32c
 
-template <int IN, int H1, int H2, typename TT>
+template <int IN, int H1, int H2, typename TT, int OUT = 3>
 __global__ void __launch_bounds__(256, 2) k_tex_fwd_f32c(
     DevCam c, FieldDev f, int K, int RC, long long n_chunks, float bg0, float bg1, float bg2,
     const float* __restrict__ notex, const float* __restrict__ weights,
     const int* __restrict__ ids, const float* __restrict__ depths,
     const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures) {
-  using W = f32c::Ws<IN, H1, H2>;
+  using W = f32c::Ws<IN, H1, H2, OUT>;
   constexpr int HL = W::HL, PH = f32c::kPH;
   extern __shared__ __align__(16) float sm[];
   float* sW = sm;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(256, 2) k_tex_fwd_f32c(
   float* sH1 = sX + 64 * (IN + 1);      // 64 x PH
   float* sH2 = sH1 + 64 * PH;           // 64 x PH (two hidden layers)
   float* sT = sH2 + (H2 > 0 ? 64 * PH : 0);  // 64 x 4: textures of the rows
-  f32c::load_weights<IN, H1, H2>(f.w, sW);
+  f32c::load_weights<IN, H1, H2, OUT>(f.w, sW);
   const long long P = (long long)c.W * c.H, S = P * K;
   const int row = threadIdx.x & 63, q = threadIdx.x >> 6;
   for (long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
@@ -428,14 +428,25 @@ __global__ void __launch_bounds__(256, 2) k_tex_fwd_f32c(
       __syncthreads();
     }
     const float* sHL = H2 > 0 ? sH2 : sH1;
-    if (threadIdx.x < 3 * 64) {  // textures T = W3 h_last
+    if (threadIdx.x < 3 * 64) {  // textures T = W3 h_last (OUT = 48: SH in the ray direction)
       const int r = threadIdx.x / 3, ch3 = threadIdx.x % 3;
-      const float* w3 = sW + W::o3 + ch3 * HL;
-      float v = 0.f;
-#pragma unroll 8
-      for (int i = 0; i < HL; ++i) v = fmaf(w3[i], sHL[r * PH + i], v);
       const long long s = s0 + r;
       const bool valid = r < RC && s < S && ids[s] >= 0;
+      float v = 0.f;
+      if constexpr (OUT == 3) {
+        const float* w3 = sW + W::o3 + ch3 * HL;
+#pragma unroll 8
+        for (int i = 0; i < HL; ++i) v = fmaf(w3[i], sHL[r * PH + i], v);
+      } else if (valid) {
+        const Sh3 Y = pixel_sh3(c, s / K);
+        for (int k = 0; k < 16; ++k) {
+          const float* w3 = sW + W::o3 + (3 * k + ch3) * HL;
+          float o = 0.f;
+#pragma unroll 8
+          for (int i = 0; i < HL; ++i) o = fmaf(w3[i], sHL[r * PH + i], o);
+          v = fmaf(Y.y[k], o, v);
+        }
+      }
       v = valid ? v : 0.f;
       sT[4 * r + ch3] = v;
       if (r < RC && s < S) textures[3 * s + ch3] = v;
@@ -461,16 +472,17 @@ __global__ void __launch_bounds__(256, 2) k_tex_fwd_f32c(
   }
 }
 
-template <int IN, int H1, int H2, typename TT>
+template <int IN, int H1, int H2, typename TT, int OUT = 3>
 __global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
     DevCam c, FieldDev f, int K, int KP, int RC, long long n_chunks,
     const float* __restrict__ weights, const int* __restrict__ ids,
     const float* __restrict__ depths, const float* __restrict__ d_image,
     const float* __restrict__ d_weights, const float* __restrict__ d_textures,
     float* __restrict__ dweff, float2* __restrict__ gin, float* __restrict__ d_mlp) {
-  using W = f32c::Ws<IN, H1, H2>;
-  using A = MlpArch<IN, H1, H2>;
+  using W = f32c::Ws<IN, H1, H2, OUT>;
+  using A = MlpArch<IN, H1, H2, OUT>;
   constexpr int HL = W::HL, PH = f32c::kPH, PX = IN + 1;
+  constexpr int NG3 = OUT * HL / 256;  // last-layer weight gradients per thread (OUT = 48)
   extern __shared__ __align__(16) float sm[];
   float* sW = sm;
   float* sX = sW + W::total;                  // 64 x PX
@@ -480,7 +492,8 @@ __global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
   float* sD1 = sDL + 64 * PH;                 // 64 x PH: delta of h1 (two hidden layers)
   float* sG = sD1 + (H2 > 0 ? 64 * PH : 0);   // 64 x 8: texture gradient, dL/dC, dL/dW
   float* sGin = sH1;                          // 64 x PX: feature gradient (after h1 is used)
-  f32c::load_weights<IN, H1, H2>(f.w, sW);
+  float* sY = sG + 64 * 8;                    // 64 x 16: SH basis of the rows (OUT = 48)
+  f32c::load_weights<IN, H1, H2, OUT>(f.w, sW);
   const float* W1 = sW;
   const float* W2 = sW + W::o2;
   const float* W3 = sW + W::o3;
@@ -492,6 +505,9 @@ __global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
   wg::zero<64>(g2);
   wg::zero<IN>(g1);
   float g3 = 0.f;
+  float g3s[OUT == 48 ? NG3 : 1];
+#pragma unroll
+  for (int j = 0; j < (OUT == 48 ? NG3 : 1); ++j) g3s[j] = 0.f;
   const float* sHL = H2 > 0 ? sH2 : sH1;
   for (long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
     const long long s0 = ch * RC;
@@ -523,6 +539,11 @@ __global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
         float* g = sG + 8 * row;
         g[0] = gT0; g[1] = gT1; g[2] = gT2; g[3] = dc0; g[4] = dc1; g[5] = dc2; g[6] = dwx;
         g[7] = valid ? 1.f : 0.f;
+        if constexpr (OUT == 48) {
+          const Sh3 Y = pixel_sh3(c, valid ? s / K : 0);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) sY[16 * row + k] = valid ? Y.y[k] : 0.f;
+        }
       }
     }
     __syncthreads();
@@ -539,12 +560,30 @@ __global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
       if (r < RC && s < S) {
         const float* g = sG + 8 * r;
         float T0 = 0.f, T1 = 0.f, T2 = 0.f;
+        if constexpr (OUT == 3) {
 #pragma unroll 8
-        for (int i = 0; i < HL; ++i) {
-          const float h = sHL[r * PH + i];
-          T0 = fmaf(W3[i], h, T0);
-          T1 = fmaf(W3[HL + i], h, T1);
-          T2 = fmaf(W3[2 * HL + i], h, T2);
+          for (int i = 0; i < HL; ++i) {
+            const float h = sHL[r * PH + i];
+            T0 = fmaf(W3[i], h, T0);
+            T1 = fmaf(W3[HL + i], h, T1);
+            T2 = fmaf(W3[2 * HL + i], h, T2);
+          }
+        } else if (g[7] != 0.f) {
+          for (int k = 0; k < 16; ++k) {
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f;
+            const float* w3 = W3 + 3 * k * HL;
+#pragma unroll 8
+            for (int i = 0; i < HL; ++i) {
+              const float h = sHL[r * PH + i];
+              o0 = fmaf(w3[i], h, o0);
+              o1 = fmaf(w3[HL + i], h, o1);
+              o2 = fmaf(w3[2 * HL + i], h, o2);
+            }
+            const float y = sY[16 * r + k];
+            T0 = fmaf(y, o0, T0);
+            T1 = fmaf(y, o1, T1);
+            T2 = fmaf(y, o2, T2);
+          }
         }
         dweff[s] = g[7] != 0.f ? T0 * g[3] + T1 * g[4] + T2 * g[5] + g[6] : 0.f;
       }
@@ -553,7 +592,17 @@ __global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
     for (int k = threadIdx.x; k < 64 * HL; k += 256) {
       const int r = k / HL, cc = k % HL;
       const float* g = sG + 8 * r;
-      const float v = W3[cc] * g[0] + W3[HL + cc] * g[1] + W3[2 * HL + cc] * g[2];
+      float v;
+      if constexpr (OUT == 3) {
+        v = W3[cc] * g[0] + W3[HL + cc] * g[1] + W3[2 * HL + cc] * g[2];
+      } else {
+        // the output gradient is Y_k gT_ch at output 3k + ch
+        v = 0.f;
+        for (int kk = 0; kk < 16; ++kk) {
+          const float* w3 = W3 + 3 * kk * HL + cc;
+          v = fmaf(sY[16 * r + kk], w3[0] * g[0] + w3[HL] * g[1] + w3[2 * HL] * g[2], v);
+        }
+      }
       sDL[r * PH + cc] = sHL[r * PH + cc] > 0.f ? v : 0.f;
     }
     __syncthreads();
@@ -580,12 +629,25 @@ __global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
     wg::gemm<IN, 64>([&](int m, int k) { return sDH1[k * PH + m]; },
                      [&](int n, int k) { return sX[k * PX + n]; }, g1);
     // dW3[o][i] += sum_r gT[r][o] h_last[r][i]
-    if (threadIdx.x < 3 * HL) {
-      const int o = threadIdx.x / HL, i = threadIdx.x % HL;
-      float v = g3;
+    if constexpr (OUT == 3) {
+      if (threadIdx.x < 3 * HL) {
+        const int o = threadIdx.x / HL, i = threadIdx.x % HL;
+        float v = g3;
 #pragma unroll 8
-      for (int r = 0; r < 64; ++r) v = fmaf(sG[8 * r + o], sHL[r * PH + i], v);
-      g3 = v;
+        for (int r = 0; r < 64; ++r) v = fmaf(sG[8 * r + o], sHL[r * PH + i], v);
+        g3 = v;
+      }
+    } else {
+      // weight (3k + ch, i): sum_r Y_k[r] gT_ch[r] h_last[r][i]
+#pragma unroll
+      for (int j = 0; j < NG3; ++j) {
+        const int e = threadIdx.x + 256 * j, o = e / HL, i = e % HL;
+        const int kk = o / 3, chn = o % 3;
+        float v = g3s[j];
+        for (int r = 0; r < 64; ++r)
+          v = fmaf(sY[16 * r + kk] * sG[8 * r + chn], sHL[r * PH + i], v);
+        g3s[j] = v;
+      }
     }
     // feature gradient d1 W1 -> sGin (h1 is no longer needed)
     {
@@ -623,33 +685,40 @@ __global__ void __launch_bounds__(256, 2) k_tex_bwd_f32c(
 #pragma unroll
     for (int j = 0; j < IN / 16; ++j)
       atomicAdd(d_mlp + (4 * ty + i) * IN + (IN / 16) * tx + j, g1[i][j]);
-  if (threadIdx.x < 3 * HL) atomicAdd(d_mlp + A::kOffLast + threadIdx.x, g3);
+  if constexpr (OUT == 3) {
+    if (threadIdx.x < 3 * HL) atomicAdd(d_mlp + A::kOffLast + threadIdx.x, g3);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NG3; ++j) atomicAdd(d_mlp + A::kOffLast + threadIdx.x + 256 * j, g3s[j]);
+  }
 }
 
-template <int IN, int H1, int H2>
+template <int IN, int H1, int H2, int OUT = 3>
 constexpr size_t f32c_fwd_smem() {
-  using W = f32c::Ws<IN, H1, H2>;
+  using W = f32c::Ws<IN, H1, H2, OUT>;
   return sizeof(float) * (W::total + 64 * (IN + 1) + 64 * f32c::kPH * (H2 > 0 ? 2 : 1) + 64 * 4);
 }
-template <int IN, int H1, int H2>
+template <int IN, int H1, int H2, int OUT = 3>
 constexpr size_t f32c_bwd_smem() {
-  using W = f32c::Ws<IN, H1, H2>;
-  return sizeof(float) * (W::total + 64 * (IN + 1) + 64 * f32c::kPH * (H2 > 0 ? 4 : 2) + 64 * 8);
+  using W = f32c::Ws<IN, H1, H2, OUT>;
+  return sizeof(float) * (W::total + 64 * (IN + 1) + 64 * f32c::kPH * (H2 > 0 ? 4 : 2) + 64 * 8 +
+                          (OUT == 48 ? 64 * 16 : 0));
 }
 
 // --------------------------------------------------------------- dispatch
-template <int IN, int H1, int H2, typename TT>
+template <int IN, int H1, int H2, typename TT, int OUT = 3>
 cudaError_t tex_fwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev& fd,
                                const float* notex, const float* weights, const int* ids,
                                const float* depths, const float* T_final, float* image,
                                float* textures, cudaStream_t st) {
+  static_assert(OUT == 3 || H1 == 64, "SH outputs need the chunked kernels");
   if constexpr (H1 == 64) {
     const long long S = (long long)c.W * c.H * s.K;
     if (S == 0) return cudaSuccess;
     const int RC = s.K * (64 / s.K);
     const long long n_chunks = (S + RC - 1) / RC;
-    const size_t smem = f32c_fwd_smem<IN, H1, H2>();
-    cudaError_t e = cudaFuncSetAttribute(k_tex_fwd_f32c<IN, H1, H2, TT>,
+    const size_t smem = f32c_fwd_smem<IN, H1, H2, OUT>();
+    cudaError_t e = cudaFuncSetAttribute(k_tex_fwd_f32c<IN, H1, H2, TT, OUT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int nsm = 152, dev = 0;
@@ -657,7 +726,7 @@ cudaError_t tex_fwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const unsigned grid = (unsigned)std::min<long long>(n_chunks, 2LL * nsm);
     NEXEL_PROF("texture_fwd_f32", st);
-    k_tex_fwd_f32c<IN, H1, H2, TT><<<grid, 256, smem, st>>>(c, fd, s.K, RC, n_chunks, s.bg[0],
+    k_tex_fwd_f32c<IN, H1, H2, TT, OUT><<<grid, 256, smem, st>>>(c, fd, s.K, RC, n_chunks, s.bg[0],
                                                            s.bg[1], s.bg[2], notex, weights, ids,
                                                            depths, T_final, image, textures);
     return cudaGetLastError();
@@ -675,7 +744,7 @@ cudaError_t tex_fwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
   return cudaGetLastError();
 }
 
-template <int IN, int H1, int H2, typename TT>
+template <int IN, int H1, int H2, typename TT, int OUT = 3>
 cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev& fd,
                                char* bws, const BwdLayout& B, const float* weights, const int* ids,
                                const float* depths, const float* d_image, const float* d_weights,
@@ -685,11 +754,12 @@ cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
   if (S == 0) return cudaSuccess;
   int KP = 1;
   while (KP < s.K) KP <<= 1;
+  static_assert(OUT == 3 || H1 == 64, "SH outputs need the chunked kernels");
   if constexpr (H1 == 64) {
     const int RC = s.K * (64 / s.K);
     const long long n_chunks = (S + RC - 1) / RC;
-    const size_t smem = f32c_bwd_smem<IN, H1, H2>();
-    cudaError_t e = cudaFuncSetAttribute(k_tex_bwd_f32c<IN, H1, H2, TT>,
+    const size_t smem = f32c_bwd_smem<IN, H1, H2, OUT>();
+    cudaError_t e = cudaFuncSetAttribute(k_tex_bwd_f32c<IN, H1, H2, TT, OUT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int nsm = 152, dev = 0;
@@ -698,7 +768,7 @@ cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
     const unsigned grid = (unsigned)std::min<long long>(n_chunks, 2LL * nsm);
     {
       NEXEL_PROF("texture_bwd_f32", st);
-      k_tex_bwd_f32c<IN, H1, H2, TT><<<grid, 256, smem, st>>>(
+      k_tex_bwd_f32c<IN, H1, H2, TT, OUT><<<grid, 256, smem, st>>>(
           c, fd, s.K, KP, RC, n_chunks, weights, ids, depths, d_image, d_weights, d_textures,
           (float*)(bws + B.dweff), (float2*)(bws + B.gin), d_mlp);
     }
