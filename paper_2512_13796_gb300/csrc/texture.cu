@@ -39,7 +39,8 @@ bool texture_arch_supported(const nexel_settings& s, const nexel_field& f) {
   if (f.F != 2 || f.L * f.F != f.widths[0]) return false;
   if (s.mlp_dtype == NEXEL_BF16 || s.mlp_dtype == NEXEL_F16) {
     const int h2 = f.n_layers == 3 ? f.widths[2] : 0;
-    return f.widths[f.n_layers] == 3 && tc_arch_supported(f.widths[0], f.widths[1], h2);
+    return tc_arch_supported(f.widths[0], f.widths[1], h2, f.widths[f.n_layers],
+                             s.grid_dtype == NEXEL_F16);
   }
   if (s.grid_dtype != NEXEL_F32) return false;  // the FP32 form reads an FP32 table
 #define X(a, b, c, o) if (arch_match(f, a, b, c, o)) return true;
@@ -87,7 +88,7 @@ cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const n
     const int h2 = f.n_layers == 3 ? f.widths[2] : 0;
     if (e == cudaSuccess)
       e = launch_texture_bwd_tc(c, s.K, KP, n_rows, f.widths[0], f.widths[1], h2,
-                                s.mlp_dtype == NEXEL_F16, f.weights, (const uint32_t*)(bws + B.feat),
+                                f.widths[f.n_layers], s.mlp_dtype == NEXEL_F16, f.weights, (const uint32_t*)(bws + B.feat),
                                 weights, ids, d_image, d_weights, d_textures,
                                 (float*)(bws + B.dweff), (float2*)(bws + B.gin), d_mlp,
                                 (int*)(bws + B.status), st);

@@ -245,7 +245,8 @@ __device__ __forceinline__ void mlp_bwd_input_f32(const float* __restrict__ sW, 
 // fd.feat_mode == 1; the gather pass writes them for a backward without
 // cached features; the backward writes dweff and the level-major feature
 // gradient and adds the MLP weight gradients to d_mlp (may be null).
-bool tc_arch_supported(int in, int h1, int h2);
+// out: 3 (RGB texture) or 48 (degree-3 SH coefficients; FP16 table only)
+bool tc_arch_supported(int in, int h1, int h2, int out, bool half_table);
 cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                   const FieldDev& fd, const float* notex, const float* weights,
                                   const int* ids, const float* depths, const float* T_final,
@@ -254,7 +255,7 @@ cudaError_t launch_texture_gather_tc(const DevCam& c, const nexel_settings& s,
                                      const nexel_field& f, const FieldDev& fd, const int* ids,
                                      const float* depths, uint32_t* feat, cudaStream_t st);
 cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
-                                  int h2, bool f16, const float* w, const uint32_t* feat,
+                                  int h2, int out, bool f16, const float* w, const uint32_t* feat,
                                   const float* weights, const int* ids, const float* d_image,
                                   const float* d_weights, const float* d_textures, float* dweff,
                                   float2* gin, float* d_mlp, int* status, cudaStream_t st);

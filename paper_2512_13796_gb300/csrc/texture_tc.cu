@@ -219,13 +219,16 @@ __device__ __forceinline__ float2 level_feature_tc(const FieldDev& f, int l, flo
   return make_float2(dw * ax, dw * ay);
 }
 
-template <int IN, int H1, int H2>
+// OUT = 3 (RGB texture, output layer padded to ON = 16 MMA columns) or 48
+// (the texture's degree-3 SH coefficients, ON = 48).
+template <int IN, int H1, int H2, int OUT = 3>
 struct TcLayout {
   static constexpr int HL = H2 > 0 ? H2 : H1;
+  static constexpr int ON = OUT == 3 ? 16 : 48;            // output-layer MMA columns
   static constexpr int FA = IN + H1 + H2;                  // activation features per row
-  static constexpr int FD = HL + 16 + (H2 > 0 ? H1 : 0);  // delta features per row
+  static constexpr int FD = HL + ON + (H2 > 0 ? H1 : 0);  // delta features per row
   static constexpr int SA = FA / 8 * 128, SD = FD / 8 * 128;
-  static constexpr int D1 = H2 > 0 ? HL + 16 : 0;         // first feature of d1 in the delta tile
+  static constexpr int D1 = H2 > 0 ? HL + ON : 0;         // first feature of d1 in the delta tile
   // bytes
   static constexpr int act = 0;
   static constexpr int act_bytes = kTcRows / 8 * SA + 2048;  // MN-major reads run up to 128 features
@@ -235,13 +238,16 @@ struct TcLayout {
   static constexpr int w2 = w1 + H1 * IN * 2;                // [H2][H1]   B of R2
   static constexpr int w2t = w2 + H2 * H1 * 2;               // [H1][H2]   B of R3
   static constexpr int w1t = w2t + H2 * H1 * 2;              // [IN][H1]   B of the feature gradient
-  static constexpr int w3 = w1t + IN * H1 * 2;               // FP32 [3][HL]
-  static constexpr int total = w3 + 3 * HL * 4;
+  static constexpr int w3 = w1t + IN * H1 * 2;               // FP32 [OUT][HL]
+  static constexpr int total = w3 + OUT * HL * 4;
+  // TMEM columns: feature gradient / activations, then Da, then Db
+  static constexpr int t_da = 64, t_db = 64 + HL + ON;
+  static_assert(t_db + 64 <= 256, "TMEM columns");
   static_assert(IN % 16 == 0 && H1 == 64 && (H2 == 0 || H2 == 64), "supported MLP shapes");
-  static_assert(HL + 16 <= 256 && FA <= 256, "MMA N limits");
+  static_assert(HL + ON <= 256 && FA <= 256, "MMA N limits");
 };
 
-template <int IN, int H1, int H2, typename OP>
+template <int IN, int H1, int H2, typename OP, int OUT = 3>
 __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     DevCam c, int K, int log2KP, long long n_rows, long long n_tiles, const float* __restrict__ wts,
     const uint32_t* __restrict__ feat, const float* __restrict__ weights,
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     const float* __restrict__ d_weights, const float* __restrict__ d_textures,
     float* __restrict__ dweff, float2* __restrict__ gin, float* __restrict__ d_mlp,
     int* __restrict__ status) {
-  using Lt = TcLayout<IN, H1, H2>;
+  using Lt = TcLayout<IN, H1, H2, OUT>;
   constexpr int HL = Lt::HL;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ uint32_t s_tmem;
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       *reinterpret_cast<uint16_t*>(tc_smem + Lt::w2t + cm_off(k, o, (H2 > 0 ? H2 : 8) / 8 * 128)) =
           OP::cvt(W2[i]);
     }
-    for (int i = tid; i < 3 * HL; i += kTcThreads) w3s[i] = W3[i];
+    for (int i = tid; i < OUT * HL; i += kTcThreads) w3s[i] = W3[i];
     // zero the delta tile once: the padding columns of d3 stay zero
     for (int i = tid; i < Lt::del_bytes / 16; i += kTcThreads)
       reinterpret_cast<uint4*>(del)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   }
   sync_to_mma();
   const uint32_t tmem = s_tmem;
-  const uint32_t t0 = tmem, t_da = tmem + 64, t_db = tmem + 64 + 80;  // columns
+  const uint32_t t0 = tmem, t_da = tmem + Lt::t_da, t_db = tmem + Lt::t_db;  // columns
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   const uint32_t sb = smem_u32(tc_smem);
   uint32_t phase = 0;
@@ -353,9 +359,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
 #pragma unroll
     for (int c8 = 0; c8 < IN / 8; ++c8)
       *reinterpret_cast<uint4*>(act + cm_off(tid, 8 * c8, Lt::SA)) = cur.x[c8];
-    {
+    if constexpr (OUT == 3) {
       const float d3[8] = {OP::kScale * gT[0], OP::kScale * gT[1], OP::kScale * gT[2], 0.f, 0.f, 0.f, 0.f, 0.f};
       st8<OP>(del, tid, HL, Lt::SD, d3);
+    } else {
+      // output gradient of SH output 3k + ch: Y_k(ray) gT_ch
+      const Sh3 Y = pixel_sh3(c, valid ? (r >> log2KP) : 0);
+#pragma unroll
+      for (int c8 = 0; c8 < 6; ++c8) {
+        float d3[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int o = 8 * c8 + i;
+          d3[i] = valid ? OP::kScale * Y.y[o / 3] * gT[o % 3] : 0.f;
+        }
+        st8<OP>(del, tid, HL + 8 * c8, Lt::SD, d3);
+      }
     }
     sync_to_mma();
     // R1: h1 = X W1^T -> t0
@@ -414,14 +433,38 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       const uint64_t ml = H2 > 0 ? m2 : m1;
       const float4* w34 = reinterpret_cast<const float4*>(w3s);
       float T0 = 0.f, T1 = 0.f, T2 = 0.f;
+      Sh3 Y;
+      if constexpr (OUT == 48) Y = pixel_sh3(c, valid ? (r >> log2KP) : 0);
 #pragma unroll
       for (int c8 = 0; c8 < HL / 8; ++c8) {
+        // the (per-row, for SH) output-layer weights of hidden units 8 c8 ..
         float wr[3][8];
+        if constexpr (OUT == 3) {
 #pragma unroll
-        for (int o = 0; o < 3; ++o) {
-          const float4 a = w34[(o * HL + 8 * c8) / 4], b = w34[(o * HL + 8 * c8) / 4 + 1];
-          wr[o][0] = a.x; wr[o][1] = a.y; wr[o][2] = a.z; wr[o][3] = a.w;
-          wr[o][4] = b.x; wr[o][5] = b.y; wr[o][6] = b.z; wr[o][7] = b.w;
+          for (int o = 0; o < 3; ++o) {
+            const float4 a = w34[(o * HL + 8 * c8) / 4], b = w34[(o * HL + 8 * c8) / 4 + 1];
+            wr[o][0] = a.x; wr[o][1] = a.y; wr[o][2] = a.z; wr[o][3] = a.w;
+            wr[o][4] = b.x; wr[o][5] = b.y; wr[o][6] = b.z; wr[o][7] = b.w;
+          }
+        } else {
+          // SH: T_ch = sum_k Y_k (W3 h)_{3k + ch}, so the row's effective
+          // weight of channel ch is sum_k Y_k W3[3k + ch]
+#pragma unroll
+          for (int o = 0; o < 3; ++o)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) wr[o][i] = 0.f;
+#pragma unroll 4
+          for (int k = 0; k < 16; ++k)
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+              const float4 a = w34[((3 * k + o) * HL + 8 * c8) / 4];
+              const float4 b = w34[((3 * k + o) * HL + 8 * c8) / 4 + 1];
+              const float y = Y.y[k];
+              wr[o][0] = fmaf(y, a.x, wr[o][0]); wr[o][1] = fmaf(y, a.y, wr[o][1]);
+              wr[o][2] = fmaf(y, a.z, wr[o][2]); wr[o][3] = fmaf(y, a.w, wr[o][3]);
+              wr[o][4] = fmaf(y, b.x, wr[o][4]); wr[o][5] = fmaf(y, b.y, wr[o][5]);
+              wr[o][6] = fmaf(y, b.z, wr[o][6]); wr[o][7] = fmaf(y, b.w, wr[o][7]);
+            }
         }
         // the last hidden layer of this row, as stored (BF16)
         const uint4 hq = *reinterpret_cast<const uint4*>(act + cm_off(tid, IN + H1 + H2 - HL + 8 * c8, Lt::SA));
@@ -483,7 +526,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       for (int kk = 0; kk < kTcRows / 16; ++kk) {
         const bool acc = !(first && kk == 0);
         mma(t_da, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 2 * Lt::SA, Lt::SA, 128),
-            sdesc(sb + Lt::del + kk * 2 * Lt::SD, Lt::SD, 128), idesc(128, HL + 16, 1, 1, OP::kFmt), acc);
+            sdesc(sb + Lt::del + kk * 2 * Lt::SD, Lt::SD, 128), idesc(128, HL + Lt::ON, 1, 1, OP::kFmt), acc);
         mma(t_db, sdesc(sb + Lt::act + kk * 2 * Lt::SA, Lt::SA, 128),
             sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 2 * Lt::SD, Lt::SD, 128),
             idesc(128, H1, 1, 1, OP::kFmt), acc);
@@ -523,7 +566,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     float* dW1 = d_mlp;
     float* dW2 = d_mlp + H1 * IN;
     float* dW3 = dW2 + H2 * H1;
-    for (int c16 = 0; c16 < (HL + 16) / 16; ++c16) {
+    for (int c16 = 0; c16 < (HL + Lt::ON) / 16; ++c16) {
       float v[16];
       tmem_ld16(t_da + lane_base + 16 * c16, v);
 #pragma unroll
@@ -531,10 +574,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         const int n = 16 * c16 + i, m = tid;
         if (H2 > 0) {
           if (m < H1 && n < H2) atomicAdd(dW2 + n * H1 + m, v[i] * (1.f / OP::kScale));  // dW2[o=n][i=m]
-          if (m >= H1 && m < H1 + H2 && n >= HL && n < HL + 3)
+          if (m >= H1 && m < H1 + H2 && n >= HL && n < HL + OUT)
             atomicAdd(dW3 + (n - HL) * HL + (m - H1), v[i] * (1.f / OP::kScale));         // dW3[o][i]
         } else {
-          if (m < H1 && n >= HL && n < HL + 3)
+          if (m < H1 && n >= HL && n < HL + OUT)
             atomicAdd(dW3 + (n - HL) * HL + m, v[i] * (1.f / OP::kScale));
         }
       }
@@ -553,23 +596,25 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
-template <int IN, int H1, int H2, typename OP>
+template <int IN, int H1, int H2, typename OP, int OUT = 3>
 cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const float* w,
                        const uint32_t* feat, const float* weights, const int* ids,
                        const float* d_image, const float* d_weights, const float* d_textures,
                        float* dweff, float2* gin, float* d_mlp, int* status, cudaStream_t st) {
-  using Lt = TcLayout<IN, H1, H2>;
+  using Lt = TcLayout<IN, H1, H2, OUT>;
   int log2KP = 0;
   while ((1 << log2KP) < KP) ++log2KP;
   const long long n_tiles = (n_rows + kTcRows - 1) / kTcRows;
   if (n_tiles == 0) return cudaSuccess;
-  auto kern = k_tex_bwd_tc<IN, H1, H2, OP>;
+  auto kern = k_tex_bwd_tc<IN, H1, H2, OP, OUT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::total);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::min<long long>(n_tiles, 2LL * nsm);
+  // two CTAs per SM where their shared memory fits (227 KB per SM)
+  const long long per_sm = 2LL * (Lt::total + 1024) <= 227LL * 1024 ? 2 : 1;
+  const unsigned grid = (unsigned)std::min<long long>(n_tiles, per_sm * nsm);
   NEXEL_PROF("texture_bwd_tc", st);
   kern<<<grid, kTcThreads, Lt::total, st>>>(c, K, log2KP, n_rows, n_tiles, w, feat, weights, ids,
                                             d_image, d_weights, d_textures, dweff, gin, d_mlp,
@@ -588,30 +633,32 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
 // h1 W2^T, h_last W3^T) with ReLU epilogues, the last one writing the
 // textures and the composite.  Epilogues split the columns between warps w
 // and w + 4 (which share TMEM lanes).
-template <int IN, int H1, int H2>
+template <int IN, int H1, int H2, int OUT = 3>
 struct TcFwdLayout {
   static constexpr int HL = H2 > 0 ? H2 : H1;
+  static constexpr int ON = OUT == 3 ? 16 : 48;       // output-layer MMA columns
   // features X, then the hidden layer (h2 overwrites h1 once R2 has read it)
   static constexpr int FA = IN + (H1 > H2 ? H1 : H2);
   static constexpr int SA = FA / 8 * 128;
   static constexpr int act = 0;
   static constexpr int w1 = act + kTcRows / 8 * SA;   // [H1][IN]
   static constexpr int w2 = w1 + H1 * IN * 2;         // [H2][H1]
-  static constexpr int w3 = w2 + H2 * H1 * 2;         // [16][HL], rows 3.. zero
-  static constexpr int total = w3 + 16 * HL * 2;
+  static constexpr int w3 = w2 + H2 * H1 * 2;         // [ON][HL], rows OUT.. zero
+  static constexpr int total = w3 + ON * HL * 2;
+  static_assert(ON <= 64, "the output layer uses TMEM columns 64 .. 127");
 };
 
 constexpr int kTcFwdThreads = 256;
 constexpr int kTcFwdCols = 128;
 
-template <int IN, int H1, int H2, typename TT, typename OP>
+template <int IN, int H1, int H2, typename TT, typename OP, int OUT = 3>
 __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
     DevCam c, FieldDev f, int K, int log2KP, long long n_tiles, float bg0, float bg1, float bg2,
     const float* __restrict__ notex, const float* __restrict__ weights,
     const int* __restrict__ ids, const float* __restrict__ depths,
     const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures,
     uint32_t* __restrict__ feat_cache, int* __restrict__ status) {
-  using Lt = TcFwdLayout<IN, H1, H2>;
+  using Lt = TcFwdLayout<IN, H1, H2, OUT>;
   constexpr int HL = Lt::HL;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ uint32_t s_tmem;
@@ -628,10 +675,10 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
     for (int i = tid; i < H2 * H1; i += kTcFwdThreads)
       *reinterpret_cast<uint16_t*>(tc_smem + Lt::w2 + cm_off(i / H1, i % H1, H1 / 8 * 128)) =
           OP::cvt(W2[i]);
-    for (int i = tid; i < 16 * HL; i += kTcFwdThreads) {
+    for (int i = tid; i < Lt::ON * HL; i += kTcFwdThreads) {
       const int o = i / HL, k = i % HL;
       *reinterpret_cast<uint16_t*>(tc_smem + Lt::w3 + cm_off(o, k, HL / 8 * 128)) =
-          OP::cvt(o < 3 ? W3[o * HL + k] : 0.f);
+          OP::cvt(o < OUT ? W3[o * HL + k] : 0.f);
     }
   }
   if (tid == 0) {
@@ -734,24 +781,42 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
 #pragma unroll
       for (int kk = 0; kk < HL / 16; ++kk)
         mma(t1, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
-            sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, 16, 0, 0, OP::kFmt), kk > 0);
+            sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, Lt::ON, 0, 0, OP::kFmt), kk > 0);
       commit(&s_bar);
     }
     ok = ok && wait_bar(&s_bar, phase);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ehalf == 0) {
-      float v[16];
-      tmem_ld16(t1 + elane, v);
       const long long p = tile * PPT + erow / KP;
       const int j = erow & (KP - 1);
       const bool in_pix = p < P && j < K;
       const long long s = p * K + j;
+      float o3[3];
+      if constexpr (OUT == 3) {
+        float v[16];
+        tmem_ld16(t1 + elane, v);
+        o3[0] = v[0]; o3[1] = v[1]; o3[2] = v[2];
+      } else {
+        // SH coefficients o[3k + ch], evaluated in the ray direction
+        const Sh3 Y = pixel_sh3(c, in_pix ? p : 0);
+        o3[0] = o3[1] = o3[2] = 0.f;
+#pragma unroll
+        for (int c16 = 0; c16 < 3; ++c16) {
+          float v[16];
+          tmem_ld16(t1 + elane + 16 * c16, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int o = 16 * c16 + i;
+            o3[o % 3] = fmaf(Y.y[o / 3], v[i], o3[o % 3]);
+          }
+        }
+      }
       float wj = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
       if (in_pix) {
         if (ids[s] >= 0) {
           wj = weights[s];
-          T0 = v[0]; T1 = v[1]; T2 = v[2];
+          T0 = o3[0]; T1 = o3[1]; T2 = o3[2];
         }
         textures[3 * s] = T0; textures[3 * s + 1] = T1; textures[3 * s + 2] = T2;
       }
@@ -778,18 +843,18 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcFwdCols));
 }
 
-template <int IN, int H1, int H2, typename TT, typename OP>
+template <int IN, int H1, int H2, typename TT, typename OP, int OUT = 3>
 cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev& fd,
                        const float* notex, const float* weights, const int* ids,
                        const float* depths, const float* T_final, float* image, float* textures,
                        int* status, cudaStream_t st) {
-  using Lt = TcFwdLayout<IN, H1, H2>;
+  using Lt = TcFwdLayout<IN, H1, H2, OUT>;
   int log2KP = 0;
   while ((1 << log2KP) < s.K) ++log2KP;
   const long long rows = (long long)c.W * c.H << log2KP;
   const long long n_tiles = (rows + kTcRows - 1) / kTcRows;
   if (n_tiles == 0) return cudaSuccess;
-  auto kern = k_tex_fwd_tc<IN, H1, H2, TT, OP>;
+  auto kern = k_tex_fwd_tc<IN, H1, H2, TT, OP, OUT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::total);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 152;
@@ -855,26 +920,34 @@ cudaError_t gather_tc(const DevCam& c, const nexel_settings& s, const FieldDev& 
 
 }  // namespace
 
-bool tc_arch_supported(int in, int h1, int h2) {
-  return (in == 16 && h1 == 64 && h2 == 0) || (in == 32 && h1 == 64 && h2 == 64);
+bool tc_arch_supported(int in, int h1, int h2, int out, bool half_table) {
+  const bool hidden = (in == 16 && h1 == 64 && h2 == 0) || (in == 32 && h1 == 64 && h2 == 64);
+  // the 48-output (SH texture) kernels are built for the FP16 table
+  return hidden && (out == 3 || (out == 48 && half_table));
 }
 
 cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
-                                  int h2, bool f16, const float* w, const uint32_t* feat,
+                                  int h2, int out, bool f16, const float* w, const uint32_t* feat,
                                   const float* weights, const int* ids, const float* d_image,
                                   const float* d_weights, const float* d_textures, float* dweff,
                                   float2* gin, float* d_mlp, int* status, cudaStream_t st) {
-#define NEXEL_TCB(A, B, C, OPT)                                                                   \
-  return tex_bwd_tc<A, B, C, OPT>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights, \
-                                  d_textures, dweff, gin, d_mlp, status, st)
+#define NEXEL_TCB(A, B, C, OPT, O)                                                                \
+  return tex_bwd_tc<A, B, C, OPT, O>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights, \
+                                     d_textures, dweff, gin, d_mlp, status, st)
+#define NEXEL_TCB2(A, B, C, O)           \
+  if (out == O) {                        \
+    if (f16) NEXEL_TCB(A, B, C, OpF16, O); \
+    NEXEL_TCB(A, B, C, OpBf16, O);       \
+  }
   if (in == 16 && h1 == 64 && h2 == 0) {
-    if (f16) NEXEL_TCB(16, 64, 0, OpF16);
-    NEXEL_TCB(16, 64, 0, OpBf16);
+    NEXEL_TCB2(16, 64, 0, 3)
+    NEXEL_TCB2(16, 64, 0, 48)
   }
   if (in == 32 && h1 == 64 && h2 == 64) {
-    if (f16) NEXEL_TCB(32, 64, 64, OpF16);
-    NEXEL_TCB(32, 64, 64, OpBf16);
+    NEXEL_TCB2(32, 64, 64, 3)
+    NEXEL_TCB2(32, 64, 64, 48)
   }
+#undef NEXEL_TCB2
 #undef NEXEL_TCB
   return cudaErrorInvalidValue;
 }
@@ -885,16 +958,22 @@ cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, cons
                                   float* image, float* textures, int* status, cudaStream_t st) {
   const bool h = s.grid_dtype == NEXEL_F16, f16 = s.mlp_dtype == NEXEL_F16;
   const int in = f.widths[0], h1 = f.widths[1], h2 = f.n_layers == 3 ? f.widths[2] : 0;
-#define NEXEL_TCF(A, B, C, TT, OPT)                                                            \
-  return tex_fwd_tc<A, B, C, TT, OPT>(c, s, fd, notex, weights, ids, depths, T_final, image, \
-                                      textures, status, st)
+  const int out = f.widths[f.n_layers];
+#define NEXEL_TCF(A, B, C, TT, OPT, O)                                                            \
+  return tex_fwd_tc<A, B, C, TT, OPT, O>(c, s, fd, notex, weights, ids, depths, T_final, image, \
+                                         textures, status, st)
 #define NEXEL_TCF2(A, B, C)                                \
-  if (h) {                                                 \
-    if (f16) NEXEL_TCF(A, B, C, __half, OpF16);            \
-    NEXEL_TCF(A, B, C, __half, OpBf16);                    \
+  if (h && out == 48) {                                    \
+    if (f16) NEXEL_TCF(A, B, C, __half, OpF16, 48);        \
+    NEXEL_TCF(A, B, C, __half, OpBf16, 48);                \
   }                                                        \
-  if (f16) NEXEL_TCF(A, B, C, float, OpF16);               \
-  NEXEL_TCF(A, B, C, float, OpBf16);
+  if (out != 3) return cudaErrorInvalidValue;              \
+  if (h) {                                                 \
+    if (f16) NEXEL_TCF(A, B, C, __half, OpF16, 3);         \
+    NEXEL_TCF(A, B, C, __half, OpBf16, 3);                 \
+  }                                                        \
+  if (f16) NEXEL_TCF(A, B, C, float, OpF16, 3);            \
+  NEXEL_TCF(A, B, C, float, OpBf16, 3);
   if (in == 16 && h1 == 64 && h2 == 0) { NEXEL_TCF2(16, 64, 0) }
   if (in == 32 && h1 == 64 && h2 == 64) { NEXEL_TCF2(32, 64, 64) }
 #undef NEXEL_TCF2

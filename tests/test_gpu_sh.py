@@ -119,9 +119,36 @@ def test_sh_textures_fp32_both_modes(dev, hidden):
           f"{s['textures']:.2e} grads {st_g}")
 
 
-def test_sh_textures_rejected_by_tensor_core_forms(dev):
-    """The tcgen05 kernels have a 3-wide output layer: a 48-output MLP in the
-    BF16 form is refused (NEXEL_ERR_UNSUPPORTED) before any launch."""
+@pytest.mark.parametrize("mlp", ["bf16", "f16"])
+@pytest.mark.parametrize("hidden", [(64,), (64, 64)], ids=["16-64-48", "32-64-64-48"])
+def test_sh_textures_tensor_core_forms(dev, hidden, mlp):
+    """The tcgen05 kernels with the 48-wide output layer (FP16 table, BF16 or
+    FP16 MLP) against the FP64 oracle, both appearance modes in SH, with the
+    reduced-precision tolerances of the RGB forms (colours 2e-3 / 1e-3,
+    gradients in relative L2)."""
+    w = synth.workload(0, gamma="var")
+    cam, st = w.cameras[0], w.settings
+    L = 8 if len(hidden) == 1 else 16
+    field = synth.make_field(L, 12, 2, hidden, 5, out_dim=48)
+    coeffs = synth.sh_coefficients(w.scene.n, 4)
+    ref = oracle.render_sh(w.scene, coeffs, cam, st, field, tie_tol=TIE, cell_tol=CELL,
+                           relu_tol=RELU)
+    pix, ok = ref["pixels"], ref["tie"] == 0
+    P, K = cam.width * cam.height, st.K
+    dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=34)
+    fw, gg = _run(w.scene, coeffs, cam, st, field, dev, "f16", mlp, dI, dW, dT)
+    s = compare_forward(fw, ref, K, 2e-3 if mlp == "bf16" else 1e-3)
+    sel = pix[ok]
+    gr = oracle.render_bwd_sh(w.scene, coeffs, cam, st, field, sel, dI[sel], dW[sel], dT[sel])
+    st_g = compare_grads(gg, gr, 0.1 if mlp == "bf16" else 0.05, metric="l2")
+    print(f"\n[sh textures tc {hidden} {mlp}] image err {s['image']:.2e} tex err "
+          f"{s['textures']:.2e} grads {st_g}")
+
+
+def test_sh_textures_rejected_with_fp32_table_on_tensor_cores(dev):
+    """The 48-output tcgen05 kernels read the FP16 table: an FP32 table with
+    a tensor-core MLP and 48 outputs is refused (NEXEL_ERR_UNSUPPORTED)
+    before any launch."""
     import torch
     from paper_2512_13796_gb300 import _native as N_
     from paper_2512_13796_gb300 import render as R
@@ -129,9 +156,9 @@ def test_sh_textures_rejected_by_tensor_core_forms(dev):
     field = synth.make_field(16, 12, 2, (64, 64), 5, out_dim=48)
     p = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).to(dev)
          for k in SURFEL_KEYS}
-    fd = R.DeviceField.from_synth(field, dev, "f16", "bf16")
+    fd = R.DeviceField.from_synth(field, dev, "f32", "bf16")
     ws = R.Workspace(dev)
     with pytest.raises(N_.NexelError) as ei:
-        R.forward(ws, R.camera_struct(w.cameras[0]), R.settings_struct(w.settings, "f16", "bf16"),
+        R.forward(ws, R.camera_struct(w.cameras[0]), R.settings_struct(w.settings, "f32", "bf16"),
                   fd, fd.storage_table(), fd.weights, *[p[k] for k in SURFEL_KEYS])
     assert ei.value.code == -4
