@@ -111,21 +111,30 @@ class ClockSampler:
 class Job:
     """Device-resident inputs and workspaces of one form (bf16 or f32)."""
 
-    def __init__(self, w, dev, precision: str):
+    def __init__(self, w, dev, precision: str, sh: bool = False):
         import torch
         from paper_2512_13796_gb300 import render as R
+        from paper_2512_13796_gb300 import synth
         self.R = R
         self.precision = precision
         grid, mlp = {"bf16": ("f16", "bf16"), "f16": ("f16", "f16"),
                      "f32": ("f32", "f32")}[precision]
         self.cam, self.st = w.cameras[0], w.settings
         self.cam_s = R.camera_struct(self.cam)
-        self.st_s = R.settings_struct(self.st, grid, mlp)
+        shd = 3 if sh else 0
+        self.st_s = R.settings_struct(self.st, grid, mlp, sh_degree=shd)
         # a training step: the forward leaves the field features for the backward
-        self.st_train = R.settings_struct(self.st, grid, mlp, cache_features=True)
+        self.st_train = R.settings_struct(self.st, grid, mlp, cache_features=True, sh_degree=shd)
         self.p = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).to(dev)
                   for k in ("mu", "quat", "scale", "opacity", "gamma", "color")}
-        self.field = R.DeviceField.from_synth(w.field, dev, grid, mlp)
+        field = w.field
+        if sh:
+            # the paper's configuration: degree-3 SH for both appearance modes
+            # (48 colour coefficients per surfel, 48 MLP outputs)
+            self.p["color"] = torch.from_numpy(synth.sh_coefficients(w.scene.n, 2)).to(dev)
+            field = synth.make_field(w.field.L, int(np.log2(w.field.T)), w.field.F,
+                                     tuple(w.field.widths[1:-1]), 2, out_dim=48)
+        self.field = R.DeviceField.from_synth(field, dev, grid, mlp)
         self.ts = self.field.storage_table()
         self.wts = self.field.weights
         self.ws = R.Workspace(dev, cap_hint=32 << 20)
@@ -405,7 +414,8 @@ def main():
     stream = torch.cuda.current_stream()
     peaks, peak_kind = load_peaks()
     w = synth.workload(args.config)
-    jobs = {"bf16": Job(w, dev, "bf16"), "f32": Job(w, dev, "f32"), "f16": Job(w, dev, "f16")}
+    jobs = {"bf16": Job(w, dev, "bf16"), "f32": Job(w, dev, "f32"), "f16": Job(w, dev, "f16"),
+            "sh_f16": Job(w, dev, "f16", sh=True)}
     P = w.cameras[0].width * w.cameras[0].height
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -435,6 +445,8 @@ def main():
     results["f32_fwd"] = timed(jobs["f32"].forward, args.steps, flush, stream)
     results["f16_train"] = timed(jobs["f16"].step, args.steps, flush, stream)
     results["f16_fwd"] = timed(jobs["f16"].forward, args.steps, flush, stream)
+    results["sh_f16_train"] = timed(jobs["sh_f16"].step, args.steps, flush, stream)
+    results["sh_f16_fwd"] = timed(jobs["sh_f16"].forward, args.steps, flush, stream)
     for _ in range(3):
         jobs["bf16"].full_step()
     results["bf16_full"] = timed(jobs["bf16"].full_step, args.steps, flush, stream)
@@ -533,6 +545,13 @@ def main():
                                     "train_ms": ms["f16_train"],
                                     "render_fps": 1e3 / ms["f16_fwd"],
                                     "render_ms": ms["f16_fwd"]},
+            "paper_sh3_f16": {"train_mpix_s": mpix(ms["sh_f16_train"]),
+                              "train_ms": ms["sh_f16_train"],
+                              "render_fps": 1e3 / ms["sh_f16_fwd"],
+                              "render_ms": ms["sh_f16_fwd"],
+                              "note": "the paper's configuration: degree-3 SH for both "
+                                      "appearance modes (48 coefficients per surfel, MLP "
+                                      "32-64-64-48), FP16 table, FP16 MLP with loss scale 128"},
         },
         "full_training_iteration": {
             "train_mpix_s": mpix(ms["bf16_full"]), "train_ms": ms["bf16_full"],
