@@ -21,6 +21,10 @@ Functions and the passages they follow:
   render_sh, render_bwd_sh, sh (module), 48-output MLPs (SH textures)
                         Sec. 3 (view-dependent radiance as channel-wise SH
                         coefficients) with Sec. 5's degree 3 (S = 16)
+  blend_error, density (module)
+                        supp. Sec. 7.2 (adaptive density control: farthest
+                        point sampling initialisation, blended errors,
+                        stochastic split, prune)
   objective (module)    Sec. 5, "Losses": L_1, D-SSIM, L_texture, L_alpha,
                         L_opacity, L_grid, the weighted total, and the Adam
                         step of the 3DGS scheme the paper follows (plain
@@ -238,6 +242,21 @@ def render_bwd_sh(scene, coeffs, cam, settings, field, pixels, d_image, d_weight
     g["color"] = dc
     g["mu"] = g["mu"] + dmu
     return g
+
+
+def blend_error(scene, cam, settings, e_pix, pixels=None) -> np.ndarray:
+    """Per-surfel blended error sum_p w_ip e_p over the listed pixels
+    (supp. Sec. 7.2); e_pix [n_pix] the pixels' errors."""
+    pix = all_pixels(cam) if pixels is None else np.ascontiguousarray(pixels, np.int32)
+    e = _d(e_pix).reshape(pix.size)
+    out = np.zeros(scene.n)
+    sv = _surfels(scene)
+    c, s = _cam(cam), _set(settings, 0.0)
+    rc = lib().oracle_blend_error(C.byref(c), C.byref(s), C.c_int(scene.n), *[_p(a) for a in sv],
+                                  C.c_int(pix.size), _p(pix), _p(e), _p(out))
+    if rc != 0:
+        raise ValueError(f"oracle_blend_error failed ({rc})")
+    return out
 
 
 def render_procedural(scene, cam, settings, freq: float, pixels=None) -> np.ndarray:

@@ -582,6 +582,28 @@ int oracle_render_procedural(const OCam* c, const OSet* st, int N, const double*
 //   d_textures [n_pix][K][3] (each may be null).
 // Gradient outputs are OVERWRITTEN (zeroed first); any may be null.
 // d_table is [L][T][F], d_mlp is packed like the weights.
+// Blended L1 error of every surfel (supp. Sec. 7.2, "Densification": the
+// per-primitive error of Rota Bulo et al.): err[i] += sum over the listed
+// pixels of w_ip e_p, with w_ip = alpha T the compositing weight of surfel i
+// at pixel p (every composited surfel, textured or not) and e_p the pixel's
+// error, given.
+int oracle_blend_error(const OCam* c, const OSet* st, int N, const double* mu, const double* quat,
+                       const double* scale, const double* opac, const double* gamma,
+                       const double* color, int n_pix, const int* pix, const double* e_pix,
+                       double* err) {
+  Scene s = make_scene(*c, N, mu, quat, scale, opac, gamma, color);
+  std::vector<std::vector<std::pair<int, double>>> acc(n_pix);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int p = 0; p < n_pix; ++p) {
+    PixelResult r;
+    render_pixel(*c, *st, nullptr, s, pix[p], false, r);
+    for (const Contrib& e : r.list) acc[p].push_back({e.id, e.w * e_pix[p]});
+  }
+  for (int p = 0; p < n_pix; ++p)
+    for (auto& q : acc[p]) err[q.first] += q.second;
+  return 0;
+}
+
 int oracle_render_bwd(const OCam* c, const OSet* st, const OField* fd, int N, const double* mu,
                       const double* quat, const double* scale, const double* opac,
                       const double* gamma, const double* color, int n_pix, const int* pix,
