@@ -310,6 +310,58 @@ int nexel_adam_step(int n_tensors, float* const* params, const float* const* gra
                     float* const* m, float* const* v, const long long* sizes, const float* lrs,
                     float beta1, float beta2, float eps, int step, nexel_stream_t stream);
 
+/* Adaptive density control (supp. Sec. 7.2; Sec. 5, "Adaptive Density
+ * Control").
+ *
+ * nexel_fps: farthest point sampling of n points [n][3] (device): idx[0] =
+ * 0, then idx[i] = the unselected point farthest from the selected ones
+ * (ties: lowest index); d2sel[i] = its squared distance to them at
+ * selection (d2sel[0] = +inf), whose square root is the paper's initial
+ * scale of that point.  Squared distances are formed in FP32 with every
+ * operation rounded, ((dx dx + dy dy) + dz dz).  scratch: n floats.  One
+ * CTA, m iterations: an initialisation step, not a per-iteration one.
+ *
+ * nexel_blend_error: ADDS to err[i] (original order) the blended L1 error of
+ * Rota Bulo et al. that the paper accumulates across iterations:
+ * sum over pixels of w e_p, w = alpha T the compositing weight of surfel i
+ * at the pixel and e_p the mean over channels of |image - target|.  Runs on
+ * the workspace of the last nexel_preprocess of this view.
+ *
+ * nexel_densify_select: the n_select surfels to split, drawn without
+ * replacement with probabilities proportional to err (Efraimidis-Spirakis):
+ * the caller passes exponential random numbers expo[i] (mean 1), the call
+ * returns in sel the indices of the n_select smallest expo[i] / err[i]
+ * (FP32; err[i] = 0 never drawn; ties by index).  The paper draws 5 % of
+ * the surfels, capped so that the total stays within its budget P.
+ *
+ * nexel_densify_split: surfel sel[r] becomes two with scales halved along
+ * the longer axis (v1 if sigma1 >= sigma2, else v2) and centres
+ * mu -/+ (sigma_long / 2) v_long; the first stays at sel[r], the second
+ * goes to index N + r; every other property is copied.  The arrays hold
+ * N + n_select surfels; color has color_dim (3 or 48) floats per surfel.
+ *
+ * nexel_prune: copies the surfels with opacity >= threshold (the paper:
+ * 0.005), in order, to the output arrays and writes their count to n_out
+ * (device int).
+ *
+ * Scratch of the selection and the prune: nexel_density_workspace_size. */
+int nexel_fps(int n, const float* points, int m, float* scratch, int* idx, float* d2sel,
+              nexel_stream_t stream);
+int nexel_blend_error(const nexel_camera* cam, const nexel_settings* settings, int N, void* ws,
+                      size_t ws_bytes, const float* image, const float* target, float* err,
+                      nexel_stream_t stream);
+int nexel_density_workspace_size(int N, size_t* bytes);
+int nexel_densify_select(int N, const float* err, const float* expo, int n_select, void* ws,
+                         size_t ws_bytes, int* sel, nexel_stream_t stream);
+int nexel_densify_split(int N, int n_select, const int* sel, int color_dim, float* mu, float* quat,
+                        float* scale, float* opacity, float* gamma, float* color,
+                        nexel_stream_t stream);
+int nexel_prune(int N, float threshold, int color_dim, const float* mu, const float* quat,
+                const float* scale, const float* opacity, const float* gamma, const float* color,
+                void* ws, size_t ws_bytes, float* mu_out, float* quat_out, float* scale_out,
+                float* opacity_out, float* gamma_out, float* color_out, int* n_out,
+                nexel_stream_t stream);
+
 /* Inspection of the binning done by the last nexel_preprocess on ws: the
  * n_instances (tile, surfel) pairs in the order the collection pass walks
  * them, i.e. by tile, then by centre view depth (Sec. 3, "Preliminaries"),

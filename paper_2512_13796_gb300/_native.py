@@ -33,7 +33,9 @@ EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess
            "nexel_version", "nexel_launch_count", "nexel_profile_enable", "nexel_profile_read",
            "nexel_render_fwd_static", "nexel_preprocess_async", "nexel_render_batch_fwd",
            "nexel_render_batch_bwd", "nexel_read_status", "nexel_loss_workspace_size",
-           "nexel_loss_image", "nexel_loss_params", "nexel_adam_step"]
+           "nexel_loss_image", "nexel_loss_params", "nexel_adam_step", "nexel_fps",
+           "nexel_blend_error", "nexel_density_workspace_size", "nexel_densify_select",
+           "nexel_densify_split", "nexel_prune"]
 
 
 def _nvcc() -> str:
@@ -147,6 +149,12 @@ def lib(auto_build: bool = False):
     L.nexel_loss_params.argtypes = [i, vp, vp, vp, vp, vp, sz, i, i, vp, vp, vp, vp]
     L.nexel_adam_step.argtypes = [i, vp, vp, vp, vp, vp, vp, C.c_float, C.c_float, C.c_float,
                                   i, vp]
+    L.nexel_fps.argtypes = [i, vp, i, vp, vp, vp, vp]
+    L.nexel_blend_error.argtypes = [vp, vp, i, vp, sz, vp, vp, vp, vp]
+    L.nexel_density_workspace_size.argtypes = [i, C.POINTER(sz)]
+    L.nexel_densify_select.argtypes = [i, vp, vp, i, vp, sz, vp, vp]
+    L.nexel_densify_split.argtypes = [i, i, vp, i] + [vp] * 6 + [vp]
+    L.nexel_prune.argtypes = [i, C.c_float, i] + [vp] * 6 + [vp, sz] + [vp] * 7 + [vp]
     L.nexel_launch_count.restype = C.c_longlong
     L.nexel_launch_count.argtypes = []
     L.nexel_profile_enable.argtypes = [i]
@@ -322,6 +330,38 @@ def nexel_adam_step(params, grads, m, v, sizes, lrs, beta1, beta2, eps, step, st
     return check("nexel_adam_step", lib().nexel_adam_step(
         n, _ptrs(params), _ptrs(grads), _ptrs(m), _ptrs(v), (C.c_longlong * n)(*sizes),
         (C.c_float * n)(*lrs), beta1, beta2, eps, step, stream))
+
+
+def nexel_fps(n, points, m, scratch, idx, d2sel, stream) -> int:
+    return check("nexel_fps", lib().nexel_fps(n, points, m, scratch, idx, d2sel, stream))
+
+
+def nexel_blend_error(cam, st, N, ws, ws_bytes, image, target, err, stream) -> int:
+    return check("nexel_blend_error", lib().nexel_blend_error(
+        C.byref(cam), C.byref(st), N, ws, ws_bytes, image, target, err, stream))
+
+
+def nexel_density_workspace_size(N: int) -> int:
+    out = C.c_size_t(0)
+    check("nexel_density_workspace_size", lib().nexel_density_workspace_size(N, C.byref(out)))
+    return out.value
+
+
+def nexel_densify_select(N, err, expo, n_select, ws, ws_bytes, sel, stream) -> int:
+    return check("nexel_densify_select", lib().nexel_densify_select(
+        N, err, expo, n_select, ws, ws_bytes, sel, stream))
+
+
+def nexel_densify_split(N, n_select, sel, color_dim, mu, quat, scale, opacity, gamma, color,
+                        stream) -> int:
+    return check("nexel_densify_split", lib().nexel_densify_split(
+        N, n_select, sel, color_dim, mu, quat, scale, opacity, gamma, color, stream))
+
+
+def nexel_prune(N, threshold, color_dim, src, ws, ws_bytes, dst, n_out, stream) -> int:
+    """src, dst: (mu, quat, scale, opacity, gamma, color) device pointers."""
+    return check("nexel_prune", lib().nexel_prune(
+        N, threshold, color_dim, *src, ws, ws_bytes, *dst, n_out, stream))
 
 
 def nexel_launch_count() -> int:

@@ -48,14 +48,6 @@ __device__ __forceinline__ ff ff_div(ff a, ff b) {
   return fast_two_sum(q1, q2);
 }
 
-// Rotation of a (normalised) quaternion (w, x, y, z): columns v1, v2, n.
-__device__ __forceinline__ void quat_cols(float w, float x, float y, float z, float3& v1, float3& v2,
-                                          float3& n) {
-  v1 = make_float3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
-  v2 = make_float3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
-  n = make_float3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
-}
-
 __device__ __forceinline__ float3 rot(const float* R, float3 v) {
   return make_float3(R[0] * v.x + R[1] * v.y + R[2] * v.z, R[3] * v.x + R[4] * v.y + R[5] * v.z,
                      R[6] * v.x + R[7] * v.y + R[8] * v.z);
@@ -707,6 +699,17 @@ __global__ void k_ranges(long long n, int rank_bits, const KeyT* __restrict__ ke
   uint32_t t = (uint32_t)(keys[i] >> rank_bits);
   if (i == 0 || (uint32_t)(keys[i - 1] >> rank_bits) != t) ranges[t].x = (uint32_t)i;
   if (i == n - 1 || (uint32_t)(keys[i + 1] >> rank_bits) != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+// ------------------------------------------------------ shared primitives
+cudaError_t sort_pairs_u32(uint32_t* k0, uint32_t* k1, uint32_t* v0, uint32_t* v1, long long n,
+                           uint32_t* hist, uint32_t* sums, cudaStream_t st, int* which) {
+  return radix_sort<uint32_t, kSortItemsDepth>(k0, k1, v0, v1, n, 0, 32, hist, sums, st, which);
+}
+
+cudaError_t exclusive_scan_u32(uint32_t* a, long long n, uint32_t* sums, uint32_t* total,
+                               cudaStream_t st) {
+  return excl_scan(a, n, sums, total, st);
 }
 
 // ------------------------------------------------------------- launchers

@@ -378,4 +378,87 @@ cudaError_t launch_collect_bwd(const DevCam& c, const nexel_settings& s, char* w
   return collect_bwd_t<uint32_t>(c, s, ws, L, bws, B, ids, T_final, d_image, st);
 }
 
+
+// Blended error (supp. Sec. 7.2, after Rota Bulo et al.): err[id] += sum over
+// pixels of w e_p, w = alpha T the compositing weight of the surfel at the
+// pixel, e_p the pixel's L1 error (mean over channels of |image - target|).
+// The forward's walk without the top-K; per staged surfel the warp sums its
+// lanes' w e_p with shuffles and one lane adds it.
+template <typename KeyT>
+__global__ void __launch_bounds__(kTilePix) k_blend_error(
+    DevCam c, float alpha_min, float alpha_max, float T_min, uint32_t rmask,
+    const uint2* __restrict__ ranges, const KeyT* __restrict__ keys,
+    const float4* __restrict__ recs, const float* __restrict__ image,
+    const float* __restrict__ target, float* __restrict__ err) {
+  __shared__ float4 s_rec[kRecF4][kTilePix];
+  const int tile = blockIdx.x;
+  const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
+  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+  const int py = ty * kTile + (threadIdx.x / kTile);
+  const bool inside = px < c.W && py < c.H;
+  const float fpx = px + 0.5f, fpy = py + 0.5f;
+  const uint2 rg = ranges[tile];
+  float e = 0.f;
+  if (inside) {
+    const size_t p = (size_t)py * c.W + px;
+    e = (fabsf(image[3 * p] - target[3 * p]) + fabsf(image[3 * p + 1] - target[3 * p + 1]) +
+         fabsf(image[3 * p + 2] - target[3 * p + 2])) * (1.f / 3.f);
+  }
+  float T = 1.f;
+  bool done = !inside || e == 0.f;
+  for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kTilePix) {
+    if (__syncthreads_count(done) == kTilePix) break;
+    uint32_t i = b0 + threadIdx.x;
+    if (i < rg.y) {
+      const float4* src = recs + (size_t)rank_of(keys[i], rmask) * kRecF4;
+#pragma unroll
+      for (int k = 0; k < kRecF4; ++k) s_rec[k][threadIdx.x] = __ldg(src + k);
+    }
+    __syncthreads();
+    const int nb = (int)min((uint32_t)kTilePix, rg.y - b0);
+    for (int j = 0; j < nb; ++j) {
+      float we = 0.f;
+      if (!done) {
+        Hit h;
+        if (eval_surfel(s_rec[0][j], s_rec[1][j], s_rec[2][j], s_rec[3][j], fpx, fpy, c.near_,
+                        alpha_min, h)) {
+          const float a = fminf(h.alpha, alpha_max);
+          const float test = T * (1.f - a);
+          if (test < T_min) {
+            done = true;
+          } else {
+            we = a * T * e;
+            T = test;
+          }
+        }
+      }
+      if (__ballot_sync(0xffffffffu, we != 0.f) == 0u) continue;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) we += __shfl_xor_sync(0xffffffffu, we, d);
+      if ((threadIdx.x & 31) == 0 && we != 0.f)
+        atomicAdd(err + __float_as_uint(s_rec[4][j].w), we);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_blend_error(const DevCam& c, const nexel_settings& s, char* ws,
+                               const WsLayout& L, const float* image, const float* target,
+                               float* err, cudaStream_t st) {
+  const uint32_t rmask = L.key64 ? 0xFFFFFFFFu : ((1u << L.rank_bits) - 1u);
+  dim3 grid(L.n_tiles), block(kTilePix);
+  auto* rg = (const uint2*)(ws + L.ranges);
+  auto* recs = (const float4*)(ws + L.geom_sorted);
+  NEXEL_PROF("blend_error", st);
+  if (L.key64)
+    k_blend_error<unsigned long long><<<grid, block, 0, st>>>(
+        c, s.alpha_min, s.alpha_max, s.T_min, rmask, rg,
+        (const unsigned long long*)(ws + L.inst0), recs, image, target, err);
+  else
+    k_blend_error<uint32_t><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.T_min, rmask,
+                                                    rg, (const uint32_t*)(ws + L.inst0), recs,
+                                                    image, target, err);
+  return cudaGetLastError();
+}
+
 }  // namespace nexel

@@ -35,6 +35,14 @@ struct DevCam {
   float near_;
 };
 
+// Rotation of a (normalised) quaternion (w, x, y, z): columns v1, v2, n.
+__device__ __forceinline__ void quat_cols(float w, float x, float y, float z, float3& v1, float3& v2,
+                                          float3& n) {
+  v1 = make_float3(1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y));
+  v2 = make_float3(2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x));
+  n = make_float3(2.f * (x * z + w * y), 2.f * (y * z - w * x), 1.f - 2.f * (x * x + y * y));
+}
+
 // Real spherical harmonics of degree <= 3 at the unit direction (x, y, z)
 // (orthonormal on the sphere; ordered by degree l, then m = -l .. l; with
 // the Condon-Shortley phase): the per-primitive colour mode of Sec. 3 with
@@ -243,6 +251,10 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
                                   const float* gamma, char* ws, const WsLayout& L, int accumulate,
                                   float* d_mu, float* d_quat, float* d_scale, float* d_opacity,
                                   float* d_gamma, float* d_color, bool atomic, cudaStream_t st);
+// Blended error of every surfel (adds into err[N], original order).
+cudaError_t launch_blend_error(const DevCam& c, const nexel_settings& s, char* ws,
+                               const WsLayout& L, const float* image, const float* target,
+                               float* err, cudaStream_t st);
 // feat_cache (may be null): where a training forward leaves the per-sample
 // field features for the backward (the backward's feature buffer).
 cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
@@ -256,6 +268,15 @@ cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const n
                                const float* d_textures, float* d_table, float* d_mlp,
                                bool feat_cached, cudaStream_t st);
 bool texture_arch_supported(const nexel_settings& s, const nexel_field& f);
+
+// Stable LSD radix sort of n (uint32 key, uint32 value) pairs on all 32 key
+// bits (result in buffer pair *which), and an in-place exclusive scan with
+// the total; scratch: hist >= 256 ceil(n / 1024) words, sums >= that / 2048
+// + 2 words (binning.cu).
+cudaError_t sort_pairs_u32(uint32_t* k0, uint32_t* k1, uint32_t* v0, uint32_t* v1, long long n,
+                           uint32_t* hist, uint32_t* sums, cudaStream_t st, int* which);
+cudaError_t exclusive_scan_u32(uint32_t* a, long long n, uint32_t* sums, uint32_t* total,
+                               cudaStream_t st);
 
 // Per-view bodies of the C entry points (api.cu), shared with the batched
 // entry points (batch.cu).  check_* validate one view's arguments and launch

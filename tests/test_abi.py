@@ -102,3 +102,25 @@ def test_batched_calls_check_every_view_before_launch(lib):
                                       sizes[0], None) == -1
     assert lib.nexel_read_status(C.byref(cams[0]), C.byref(st), None, N, None, 0, None, 0,
                                  None) == -1
+
+
+def test_objective_and_density_calls_check_arguments_before_launch(lib):
+    """Argument errors of the objective, Adam and density entry points come
+    back before any launch."""
+    out = C.c_size_t(0)
+    assert lib.nexel_loss_workspace_size(0, 10, C.byref(out)) == -1
+    assert lib.nexel_density_workspace_size(-1, C.byref(out)) == -1
+    assert lib.nexel_density_workspace_size(100, C.byref(out)) == 0 and out.value > 800
+    fake = 1 << 20
+    assert lib.nexel_fps(10, None, 5, None, None, None, None) == -1
+    assert lib.nexel_fps(10, fake, 11, fake, fake, fake, None) == -1    # m > n
+    assert lib.nexel_densify_select(10, fake, fake, 11, fake, 1 << 20, fake, None) == -1
+    assert lib.nexel_densify_select(10, fake, fake, 2, fake, 16, fake, None) == -1  # small ws
+    assert lib.nexel_densify_split(10, 2, fake, 5, *([fake] * 6), None) == -1      # color_dim
+    assert lib.nexel_adam_step(1, None, None, None, None, None, None, C.c_float(0.9),
+                               C.c_float(0.999), C.c_float(1e-8), 1, None) == -1
+    sz = (C.c_longlong * 1)(10)
+    lr = (C.c_float * 1)(0.1)
+    ptrs = (C.c_void_p * 1)(fake)
+    assert lib.nexel_adam_step(1, ptrs, ptrs, ptrs, ptrs, sz, lr, C.c_float(0.9),
+                               C.c_float(0.999), C.c_float(1e-8), 0, None) == -1  # step 0
