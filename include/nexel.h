@@ -362,6 +362,35 @@ int nexel_prune(int N, float threshold, int color_dim, const float* mu, const fl
                 float* opacity_out, float* gamma_out, float* color_out, int* n_out,
                 nexel_stream_t stream);
 
+/* Launch-shape tuning (process-wide; no counterpart in the paper): CTAs
+ * per SM that the persistent texturing kernels keep in flight -- the tile
+ * pipeline depth of the tcgen05 forward (1..3, default 3), of the tcgen05
+ * backward (1..2, default 2; 1 where its shared memory allows one) and of
+ * the FP32 chunked kernels (1..2, default 2) -- and the CTA size of the
+ * hash backward (128 or 256, default 256).  Every choice computes the same
+ * values; the weight-gradient and table-gradient sums may differ by
+ * rounding (their atomic order).  nexel_autotune runs the caller's own
+ * training step (preprocess once, then forward + backward per candidate,
+ * `reps` timed steps after an untimed one, CUDA events on `stream`),
+ * tunes one knob after another keeping the fastest value, leaves the best
+ * tuning set and returns it (and its median step time in ms); it
+ * synchronises the stream.  Arguments as for nexel_render_fwd /
+ * nexel_render_bwd (gradients are overwritten). */
+typedef struct {
+  int tex_fwd_ctas_per_sm, tex_bwd_ctas_per_sm, f32_ctas_per_sm, hash_block;
+} nexel_tuning;
+int nexel_get_tuning(nexel_tuning* out);
+int nexel_set_tuning(const nexel_tuning* t);
+int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
+                   const nexel_field* field, int N, const float* mu, const float* quat,
+                   const float* scale, const float* opacity, const float* gamma,
+                   const float* color, void* ws, size_t ws_bytes, void* bwd_ws,
+                   size_t bwd_ws_bytes, float* image, float* notex, float* weights, int* ids,
+                   float* depths, float* textures, float* T_final, const float* d_image,
+                   float* d_mu, float* d_quat, float* d_scale, float* d_opacity, float* d_gamma,
+                   float* d_color, float* d_table, float* d_mlp, int reps, nexel_tuning* best,
+                   float* best_ms, nexel_stream_t stream);
+
 /* Inspection of the binning done by the last nexel_preprocess on ws: the
  * n_instances (tile, surfel) pairs in the order the collection pass walks
  * them, i.e. by tile, then by centre view depth (Sec. 3, "Preliminaries"),

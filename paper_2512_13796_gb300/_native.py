@@ -35,7 +35,8 @@ EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess
            "nexel_render_batch_bwd", "nexel_read_status", "nexel_loss_workspace_size",
            "nexel_loss_image", "nexel_loss_params", "nexel_adam_step", "nexel_fps",
            "nexel_blend_error", "nexel_density_workspace_size", "nexel_densify_select",
-           "nexel_densify_split", "nexel_prune"]
+           "nexel_densify_split", "nexel_prune", "nexel_get_tuning", "nexel_set_tuning",
+           "nexel_autotune"]
 
 
 def _nvcc() -> str:
@@ -91,6 +92,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 # ------------------------------------------------------------- C structs
+class Tuning(C.Structure):
+    _fields_ = [("tex_fwd_ctas_per_sm", C.c_int), ("tex_bwd_ctas_per_sm", C.c_int),
+                ("f32_ctas_per_sm", C.c_int), ("hash_block", C.c_int)]
+
+
 class LossWeights(C.Structure):
     _fields_ = [("dssim", C.c_float), ("alpha", C.c_float), ("texture", C.c_float),
                 ("opacity", C.c_float), ("grid", C.c_float)]
@@ -155,6 +161,10 @@ def lib(auto_build: bool = False):
     L.nexel_densify_select.argtypes = [i, vp, vp, i, vp, sz, vp, vp]
     L.nexel_densify_split.argtypes = [i, i, vp, i] + [vp] * 6 + [vp]
     L.nexel_prune.argtypes = [i, C.c_float, i] + [vp] * 6 + [vp, sz] + [vp] * 7 + [vp]
+    L.nexel_get_tuning.argtypes = [vp]
+    L.nexel_set_tuning.argtypes = [vp]
+    L.nexel_autotune.argtypes = ([vp, vp, vp, i] + [vp] * 6 + [vp, sz, vp, sz] + [vp] * 7 + [vp] +
+                                 [vp] * 8 + [i, vp, vp, vp])
     L.nexel_launch_count.restype = C.c_longlong
     L.nexel_launch_count.argtypes = []
     L.nexel_profile_enable.argtypes = [i]
@@ -362,6 +372,29 @@ def nexel_prune(N, threshold, color_dim, src, ws, ws_bytes, dst, n_out, stream) 
     """src, dst: (mu, quat, scale, opacity, gamma, color) device pointers."""
     return check("nexel_prune", lib().nexel_prune(
         N, threshold, color_dim, *src, ws, ws_bytes, *dst, n_out, stream))
+
+
+def nexel_get_tuning() -> Tuning:
+    t = Tuning()
+    check("nexel_get_tuning", lib().nexel_get_tuning(C.byref(t)))
+    return t
+
+
+def nexel_set_tuning(t: Tuning) -> int:
+    return check("nexel_set_tuning", lib().nexel_set_tuning(C.byref(t)))
+
+
+def nexel_autotune(cam, st, field, N, params, ws, ws_bytes, bws, bws_bytes, outs, d_image, grads,
+                   reps, stream) -> tuple:
+    """params: 6 device pointers (mu .. color); outs: 7 (image, notex,
+    weights, ids, depths, textures, T_final); grads: 8 (d_mu .. d_mlp).
+    Returns (Tuning, median ms)."""
+    t = Tuning()
+    ms = C.c_float(0.0)
+    check("nexel_autotune", lib().nexel_autotune(
+        C.byref(cam), C.byref(st), C.byref(field) if field is not None else None, N, *params, ws,
+        ws_bytes, bws, bws_bytes, *outs, d_image, *grads, reps, C.byref(t), C.byref(ms), stream))
+    return t, ms.value
 
 
 def nexel_launch_count() -> int:

@@ -278,6 +278,14 @@ cudaError_t sort_pairs_u32(uint32_t* k0, uint32_t* k1, uint32_t* v0, uint32_t* v
 cudaError_t exclusive_scan_u32(uint32_t* a, long long n, uint32_t* sums, uint32_t* total,
                                cudaStream_t st);
 
+// Launch shapes chosen by nexel_autotune / nexel_set_tuning (tuning.cu),
+// process-wide: CTAs per SM of the persistent texturing kernels and the CTA
+// size of the hash backward.
+struct Tuning {
+  int tex_fwd_ctas = 3, tex_bwd_ctas = 2, f32_ctas = 2, hash_block = 256;
+};
+Tuning current_tuning();
+
 // Per-view bodies of the C entry points (api.cu), shared with the batched
 // entry points (batch.cu).  check_* validate one view's arguments and launch
 // nothing; the *_impl functions assume a passed check.  preprocess_impl with

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     const int* __restrict__ ids, const float* __restrict__ depths,
     const float2* __restrict__ gin, float* __restrict__ ddepth, float* __restrict__ d_table) {
   const int lane = threadIdx.x & 31;
-  const uint32_t gw = blockIdx.x * (kHbThreads / 32) + (threadIdx.x >> 5);
+  const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   // warp gw: slot j = gw % KP of the 32 consecutive pixels 32 (gw / KP) ..
   const int KP = 1 << log2KP;
   const uint32_t r = ((gw >> log2KP) * 32u + (uint32_t)lane) * (uint32_t)KP + (gw & (KP - 1));
@@ -171,8 +171,10 @@ cudaError_t launch_hash_bwd(const DevCam& c, const FieldDev& fd, int K, int KP, 
       gin_stride(n_rows) >= (1LL << 32))
     return cudaErrorInvalidValue;
   const uint32_t R = (uint32_t)gin_stride(n_rows);
-  const unsigned grid = (unsigned)((n_rows + kHbThreads - 1) / kHbThreads);
-  const unsigned block = kHbThreads;
+  // CTA size: 256 threads, or 128 when the tuning asks (a multiple of the
+  // KP warps of a pixel group either way)
+  const unsigned block = current_tuning().hash_block == 128 ? 128u : (unsigned)kHbThreads;
+  const unsigned grid = (unsigned)((n_rows + block - 1) / block);
   NEXEL_PROF("hash_bwd", st);
   if (half_table)
     k_hash_bwd<__half><<<grid, block, 0, st>>>(c, fd, K, log2KP, (uint32_t)n_rows, R, ids, depths,

@@ -724,7 +724,8 @@ cudaError_t tex_fwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
     int nsm = 152, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned grid = (unsigned)std::min<long long>(n_chunks, 2LL * nsm);
+    const unsigned grid =
+        (unsigned)std::min<long long>(n_chunks, (long long)current_tuning().f32_ctas * nsm);
     NEXEL_PROF("texture_fwd_f32", st);
     k_tex_fwd_f32c<IN, H1, H2, TT, OUT><<<grid, 256, smem, st>>>(c, fd, s.K, RC, n_chunks, s.bg[0],
                                                            s.bg[1], s.bg[2], notex, weights, ids,
@@ -765,7 +766,8 @@ cudaError_t tex_bwd_f32(const DevCam& c, const nexel_settings& s, const FieldDev
     int nsm = 152, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned grid = (unsigned)std::min<long long>(n_chunks, 2LL * nsm);
+    const unsigned grid =
+        (unsigned)std::min<long long>(n_chunks, (long long)current_tuning().f32_ctas * nsm);
     {
       NEXEL_PROF("texture_bwd_f32", st);
       k_tex_bwd_f32c<IN, H1, H2, TT, OUT><<<grid, 256, smem, st>>>(

@@ -613,7 +613,8 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // two CTAs per SM where their shared memory fits (227 KB per SM)
-  const long long per_sm = 2LL * (Lt::total + 1024) <= 227LL * 1024 ? 2 : 1;
+  const long long per_sm = std::min<long long>(
+      current_tuning().tex_bwd_ctas, 2LL * (Lt::total + 1024) <= 227LL * 1024 ? 2 : 1);
   const unsigned grid = (unsigned)std::min<long long>(n_tiles, per_sm * nsm);
   NEXEL_PROF("texture_bwd_tc", st);
   kern<<<grid, kTcThreads, Lt::total, st>>>(c, K, log2KP, n_rows, n_tiles, w, feat, weights, ids,
@@ -860,7 +861,8 @@ cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev&
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::min<long long>(n_tiles, 3LL * nsm);
+  const unsigned grid =
+      (unsigned)std::min<long long>(n_tiles, (long long)current_tuning().tex_fwd_ctas * nsm);
   NEXEL_PROF("texture_fwd_tc", st);
   kern<<<grid, kTcFwdThreads, Lt::total, st>>>(
       c, fd, s.K, log2KP, n_tiles, s.bg[0], s.bg[1], s.bg[2], notex, weights, ids, depths, T_final,

@@ -124,3 +124,21 @@ def test_objective_and_density_calls_check_arguments_before_launch(lib):
     ptrs = (C.c_void_p * 1)(fake)
     assert lib.nexel_adam_step(1, ptrs, ptrs, ptrs, ptrs, sz, lr, C.c_float(0.9),
                                C.c_float(0.999), C.c_float(1e-8), 0, None) == -1  # step 0
+
+
+def test_tuning_round_trip_and_checks(lib):
+    t0 = N_.nexel_get_tuning()
+    assert (t0.tex_fwd_ctas_per_sm, t0.tex_bwd_ctas_per_sm, t0.f32_ctas_per_sm,
+            t0.hash_block) == (3, 2, 2, 256)
+    t = N_.Tuning(1, 1, 1, 128)
+    N_.nexel_set_tuning(t)
+    g = N_.nexel_get_tuning()
+    assert (g.tex_fwd_ctas_per_sm, g.tex_bwd_ctas_per_sm, g.f32_ctas_per_sm, g.hash_block) == \
+        (1, 1, 1, 128)
+    for bad in (N_.Tuning(0, 1, 1, 128), N_.Tuning(4, 1, 1, 128), N_.Tuning(1, 3, 1, 128),
+                N_.Tuning(1, 1, 1, 64)):
+        assert lib.nexel_set_tuning(C.byref(bad)) == -1
+    N_.nexel_set_tuning(t0)
+    best = N_.Tuning()
+    assert lib.nexel_autotune(None, None, None, 0, *([None] * 6), None, 0, None, 0, *([None] * 7),
+                              None, *([None] * 8), 0, C.byref(best), None, None) == -1

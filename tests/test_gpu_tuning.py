@@ -1,0 +1,83 @@
+"""Launch-shape tuning: nexel_autotune picks a valid tuning on a training
+step; every tuning renders the same image bit for bit (the tile pipeline
+depth changes only scheduling) and the same gradients up to the rounding
+of their atomic sums."""
+import numpy as np
+import pytest
+
+from paper_2512_13796_gb300 import synth
+
+from helpers import SURFEL_KEYS, gpu_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    assert torch.cuda.is_available(), "GPU test without a CUDA device"
+    from paper_2512_13796_gb300 import _native
+    _native.build()
+    return torch.device("cuda:0")
+
+
+def _step(dev, w, fd, p, dI):
+    import torch
+    from paper_2512_13796_gb300 import render as R
+    ws = R.Workspace(dev)
+    cam_s = R.camera_struct(w.cameras[0])
+    st_s = R.settings_struct(w.settings, "f16", "bf16", cache_features=True)
+    ts = fd.storage_table()
+    out = R.forward(ws, cam_s, st_s, fd, ts, fd.weights, *[p[k] for k in SURFEL_KEYS])
+    g = R.backward(ws, cam_s, st_s, fd, ts, fd.weights, *[p[k] for k in SURFEL_KEYS[:5]], out, dI)
+    torch.cuda.synchronize()
+    return out, g, ws, cam_s, st_s
+
+
+def test_autotune_and_tuning_invariance(dev):
+    import torch
+    from paper_2512_13796_gb300 import _native as N_
+    from paper_2512_13796_gb300 import render as R
+    w = synth.workload(1)
+    p = gpu_params(w.scene, dev)
+    fd = R.DeviceField.from_synth(w.field, dev, "f16", "bf16")
+    cam = w.cameras[0]
+    dI = torch.from_numpy(np.random.default_rng(1).normal(
+        size=(cam.height, cam.width, 3)).astype(np.float32) * 1e-3).to(dev)
+    t0 = N_.nexel_get_tuning()
+    results = []
+    try:
+        for t in (N_.Tuning(3, 2, 2, 256), N_.Tuning(1, 1, 1, 128)):
+            N_.nexel_set_tuning(t)
+            results.append(_step(dev, w, fd, p, dI))
+        (o1, g1, ws, cam_s, st_s), (o2, g2, _, _, _) = results
+        for k in ("image", "weights", "ids", "textures"):
+            assert torch.equal(o1[k], o2[k]), k
+        for k in g1:
+            a, b = g1[k].double(), g2[k].double()
+            assert float((a - b).norm() / b.norm()) < 1e-5, k
+        # the autotuner on the same step
+        g = {k: torch.zeros_like(v) for k, v in g1.items()}
+        bws = ws.bwd(cam_s, st_s, fd.struct(fd.storage_table(), fd.weights))
+        ts = fd.storage_table()
+        fs = fd.struct(ts, fd.weights)
+        best, ms = N_.nexel_autotune(
+            cam_s, st_s, fs, w.scene.n, [p[k].data_ptr() for k in SURFEL_KEYS], ws.ws.data_ptr(),
+            ws.ws.numel(), bws.data_ptr(), bws.numel(),
+            [o1[k].data_ptr() for k in ("image", "notex", "weights", "ids", "depths", "textures",
+                                        "T_final")], dI.data_ptr(),
+            [g[k].data_ptr() for k in ("mu", "quat", "scale", "opacity", "gamma", "color",
+                                       "table", "mlp")], 3,
+            torch.cuda.current_stream().cuda_stream)
+        print(f"\n[autotune] best {best.tex_fwd_ctas_per_sm} {best.tex_bwd_ctas_per_sm} "
+              f"{best.f32_ctas_per_sm} {best.hash_block} at {ms:.3f} ms")
+        assert ms > 0
+        cur = N_.nexel_get_tuning()
+        assert (cur.tex_fwd_ctas_per_sm, cur.hash_block) == (best.tex_fwd_ctas_per_sm,
+                                                             best.hash_block)
+        # the tuned step's gradients equal the untuned ones up to rounding
+        for k in g1:
+            a, b = g[k].double(), g1[k].double()
+            assert float((a - b).norm() / b.norm()) < 1e-5, k
+    finally:
+        N_.nexel_set_tuning(t0)
