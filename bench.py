@@ -180,6 +180,31 @@ class Job:
         self.ts.copy_(self.field.table)
         return out
 
+    def autotune(self) -> dict:
+        """nexel_autotune on this form's training step; the choice stays set
+        for the rest of the run (all forms)."""
+        import torch
+        R, p = self.R, self.p
+        out = self.forward(self.st_train)
+        N_ = R.N_
+        fs = self.field.struct(self.ts, self.wts)
+        bws = self.ws.bwd(self.cam_s, self.st_train, fs)
+        g = self.R.backward(self.ws, self.cam_s, self.st_train, self.field, self.ts, self.wts,
+                            p["mu"], p["quat"], p["scale"], p["opacity"], p["gamma"], out,
+                            self.d_image)
+        best, ms = N_.nexel_autotune(
+            self.cam_s, self.st_train, fs, self.N,
+            [p[k].data_ptr() for k in ("mu", "quat", "scale", "opacity", "gamma", "color")],
+            self.ws.ws.data_ptr(), self.ws.ws.numel(), bws.data_ptr(), bws.numel(),
+            [out[k].data_ptr() for k in ("image", "notex", "weights", "ids", "depths",
+                                         "textures", "T_final")], self.d_image.data_ptr(),
+            [g[k].data_ptr() for k in ("mu", "quat", "scale", "opacity", "gamma", "color",
+                                       "table", "mlp")], 5, torch.cuda.current_stream().cuda_stream)
+        return {"tex_fwd_ctas_per_sm": best.tex_fwd_ctas_per_sm,
+                "tex_bwd_ctas_per_sm": best.tex_bwd_ctas_per_sm,
+                "f32_ctas_per_sm": best.f32_ctas_per_sm, "hash_block": best.hash_block,
+                "tuned_step_ms": ms}
+
     def step(self):
         out = self.forward(self.st_train)
         p = self.p
@@ -357,6 +382,8 @@ def main():
     ap.add_argument("--impl", default="nexels", choices=["nexels", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-json", default=None, help="write per-kernel times here")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of nexel_autotune's choice")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched 8-view form (600k surfels)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2],
@@ -431,6 +458,9 @@ def main():
         for _ in range(max(args.warmup, 3)):
             j.step()
     barrier()
+    tuning = None
+    if not args.no_autotune:
+        tuning = jobs["bf16"].autotune()
 
     results = {}
     clocks = ClockSampler(local)
@@ -535,6 +565,7 @@ def main():
         "config": {"workload": WORKLOAD if args.config == 2 else "config1: 50k surfels, 800x800, K=4, hash 8x2^16x2, MLP 16-64-3", "surfels": w.scene.n, "width": W, "height": H,
                    "K": w.settings.K, "n_instances": int(n_inst),
                    "l2": "flushed (256 MB write) before every timed step",
+                   "launch_tuning": tuning,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "forms": {
             "bf16": {"train_mpix_s": mpix(ms["bf16_train"]), "train_ms": ms["bf16_train"],
