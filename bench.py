@@ -180,9 +180,10 @@ class Job:
         self.ts.copy_(self.field.table)
         return out
 
-    def autotune(self) -> dict:
-        """nexel_autotune on this form's training step; the choice stays set
-        for the rest of the run (all forms)."""
+    def autotune(self, flush_buf) -> dict:
+        """nexel_autotune on this form's training step, every timed step
+        after an L2 flush as in the timed regions; the choice stays set for
+        the rest of the run (all forms)."""
         import torch
         R, p = self.R, self.p
         out = self.forward(self.st_train)
@@ -199,7 +200,8 @@ class Job:
             [out[k].data_ptr() for k in ("image", "notex", "weights", "ids", "depths",
                                          "textures", "T_final")], self.d_image.data_ptr(),
             [g[k].data_ptr() for k in ("mu", "quat", "scale", "opacity", "gamma", "color",
-                                       "table", "mlp")], 5, torch.cuda.current_stream().cuda_stream)
+                                       "table", "mlp")], 5, torch.cuda.current_stream().cuda_stream,
+            flush_buf.data_ptr(), flush_buf.numel())
         return {"tex_fwd_ctas_per_sm": best.tex_fwd_ctas_per_sm,
                 "tex_bwd_ctas_per_sm": best.tex_bwd_ctas_per_sm,
                 "f32_ctas_per_sm": best.f32_ctas_per_sm, "hash_block": best.hash_block,
@@ -460,7 +462,7 @@ def main():
     barrier()
     tuning = None
     if not args.no_autotune:
-        tuning = jobs["bf16"].autotune()
+        tuning = jobs["bf16"].autotune(flush_buf)
 
     results = {}
     clocks = ClockSampler(local)

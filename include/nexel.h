@@ -371,7 +371,9 @@ int nexel_prune(int N, float threshold, int color_dim, const float* mu, const fl
  * values; the weight-gradient and table-gradient sums may differ by
  * rounding (their atomic order).  nexel_autotune runs the caller's own
  * training step (preprocess once, then forward + backward per candidate,
- * `reps` timed steps after an untimed one, CUDA events on `stream`),
+ * `reps` timed steps after an untimed one, CUDA events on `stream`; with a
+ * device buffer `flush` of flush_bytes > 0, larger than the L2, it is
+ * written before every timed step so that each starts from a cold L2),
  * tunes one knob after another keeping the fastest value, leaves the best
  * tuning set and returns it (and its median step time in ms); it
  * synchronises the stream.  Arguments as for nexel_render_fwd /
@@ -388,8 +390,9 @@ int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
                    size_t bwd_ws_bytes, float* image, float* notex, float* weights, int* ids,
                    float* depths, float* textures, float* T_final, const float* d_image,
                    float* d_mu, float* d_quat, float* d_scale, float* d_opacity, float* d_gamma,
-                   float* d_color, float* d_table, float* d_mlp, int reps, nexel_tuning* best,
-                   float* best_ms, nexel_stream_t stream);
+                   float* d_color, float* d_table, float* d_mlp, int reps, void* flush,
+                   size_t flush_bytes, nexel_tuning* best, float* best_ms,
+                   nexel_stream_t stream);
 
 /* Inspection of the binning done by the last nexel_preprocess on ws: the
  * n_instances (tile, surfel) pairs in the order the collection pass walks

@@ -164,7 +164,7 @@ def lib(auto_build: bool = False):
     L.nexel_get_tuning.argtypes = [vp]
     L.nexel_set_tuning.argtypes = [vp]
     L.nexel_autotune.argtypes = ([vp, vp, vp, i] + [vp] * 6 + [vp, sz, vp, sz] + [vp] * 7 + [vp] +
-                                 [vp] * 8 + [i, vp, vp, vp])
+                                 [vp] * 8 + [i, vp, sz, vp, vp, vp])
     L.nexel_launch_count.restype = C.c_longlong
     L.nexel_launch_count.argtypes = []
     L.nexel_profile_enable.argtypes = [i]
@@ -385,7 +385,7 @@ def nexel_set_tuning(t: Tuning) -> int:
 
 
 def nexel_autotune(cam, st, field, N, params, ws, ws_bytes, bws, bws_bytes, outs, d_image, grads,
-                   reps, stream) -> tuple:
+                   reps, stream, flush=None, flush_bytes=0) -> tuple:
     """params: 6 device pointers (mu .. color); outs: 7 (image, notex,
     weights, ids, depths, textures, T_final); grads: 8 (d_mu .. d_mlp).
     Returns (Tuning, median ms)."""
@@ -393,7 +393,8 @@ def nexel_autotune(cam, st, field, N, params, ws, ws_bytes, bws, bws_bytes, outs
     ms = C.c_float(0.0)
     check("nexel_autotune", lib().nexel_autotune(
         C.byref(cam), C.byref(st), C.byref(field) if field is not None else None, N, *params, ws,
-        ws_bytes, bws, bws_bytes, *outs, d_image, *grads, reps, C.byref(t), C.byref(ms), stream))
+        ws_bytes, bws, bws_bytes, *outs, d_image, *grads, reps, flush, flush_bytes, C.byref(t),
+        C.byref(ms), stream))
     return t, ms.value
 
 

@@ -73,9 +73,10 @@ int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
                    size_t bwd_ws_bytes, float* image, float* notex, float* weights, int* ids,
                    float* depths, float* textures, float* T_final, const float* d_image,
                    float* d_mu, float* d_quat, float* d_scale, float* d_opacity, float* d_gamma,
-                   float* d_color, float* d_table, float* d_mlp, int reps, nexel_tuning* best,
-                   float* best_ms, nexel_stream_t stream) {
-  if (reps < 1 || reps > 100 || !best) return NEXEL_ERR_INVALID_ARG;
+                   float* d_color, float* d_table, float* d_mlp, int reps, void* flush,
+                   size_t flush_bytes, nexel_tuning* best, float* best_ms,
+                   nexel_stream_t stream) {
+  if (reps < 1 || reps > 100 || !best || (flush_bytes > 0 && !flush)) return NEXEL_ERR_INVALID_ARG;
   int rc = check_fwd(cam, settings, field, N, ws, ws_bytes, bwd_ws, bwd_ws_bytes, image, notex,
                      weights, ids, depths, textures, T_final);
   if (rc != NEXEL_OK) return rc;
@@ -110,6 +111,9 @@ int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
     int r = step();
     std::vector<float> v;
     for (int i = 0; i < reps && r == NEXEL_OK; ++i) {
+      // the caller's buffer (larger than L2) written before each timed step
+      if (flush_bytes > 0 && cudaMemsetAsync(flush, i & 0xff, flush_bytes, st) != cudaSuccess)
+        return NEXEL_ERR_CUDA;
       if (cudaEventRecord(a, st) != cudaSuccess) return NEXEL_ERR_CUDA;
       r = step();
       if (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess)

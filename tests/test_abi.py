@@ -141,4 +141,4 @@ def test_tuning_round_trip_and_checks(lib):
     N_.nexel_set_tuning(t0)
     best = N_.Tuning()
     assert lib.nexel_autotune(None, None, None, 0, *([None] * 6), None, 0, None, 0, *([None] * 7),
-                              None, *([None] * 8), 0, C.byref(best), None, None) == -1
+                              None, *([None] * 8), 0, None, 0, C.byref(best), None, None) == -1
