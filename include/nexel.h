@@ -374,7 +374,8 @@ int nexel_prune(int N, float threshold, int color_dim, const float* mu, const fl
  * `reps` timed steps after an untimed one, CUDA events on `stream`; with a
  * device buffer `flush` of flush_bytes > 0, larger than the L2, it is
  * written before every timed step so that each starts from a cold L2),
- * tunes one knob after another keeping the fastest value, leaves the best
+ * tunes one knob after another keeping the fastest value (a value replaces
+ * the current one only when at least 1 % faster), leaves the best
  * tuning set and returns it (and its median step time in ms); it
  * synchronises the stream.  Arguments as for nexel_render_fwd /
  * nexel_render_bwd (gradients are overwritten). */

@@ -3,7 +3,7 @@
 // size of the hash backward.  The choice is process-wide; nexel_autotune
 // measures the candidates on the caller's own workload (one training step:
 // forward + backward, timed with CUDA events on the caller's stream) and
-// keeps the fastest, one knob after another.
+// keeps the fastest, one knob after another (a change must gain 1 %).
 #include "common.cuh"
 
 #include <algorithm>
@@ -146,7 +146,9 @@ int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
       float ms = 0.f;
       rc = measure(t, &ms);
       if (rc != NEXEL_OK) break;
-      if (ms < cur_ms) {
+      // a candidate replaces the current value only when it is at least 1 %
+      // faster (run-to-run noise of the median is below that)
+      if (ms < 0.99f * cur_ms) {
         cur = t;
         cur_ms = ms;
       }
