@@ -79,7 +79,9 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
   // together
   int l = (int)((gw >> log2KP) % (uint32_t)L);
   for (int it = 0; it < L; ++it, l = (l + 1 == L) ? 0 : l + 1) {
-    const float2 g = valid ? gin[(size_t)l * R + r] : make_float2(0.f, 0.f);
+    // the feature gradient is streamed once: evict-first, so that the table
+    // and its gradient keep their L2 lines
+    const float2 g = valid ? __ldcs(gin + (size_t)l * R + r) : make_float2(0.f, 0.f);
     const float sl = f.s[l];
     const float gx = sl * x.x, gy = sl * x.y, gz = sl * x.z;
     const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);

@@ -546,9 +546,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         tmem_ld16(t0 + lane_base + 16 * c16, v);
         if (r < n_rows) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            gin[(long long)(8 * c16 + i) * R + r] =
-                make_float2(v[2 * i] * (1.f / OP::kScale), v[2 * i + 1] * (1.f / OP::kScale));
+          for (int i = 0; i < 8; ++i)  // streamed to the hash backward: evict-first
+            __stcs(gin + (long long)(8 * c16 + i) * R + r,
+                   make_float2(v[2 * i] * (1.f / OP::kScale), v[2 * i + 1] * (1.f / OP::kScale)));
         }
       }
     }
