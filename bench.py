@@ -298,18 +298,38 @@ def measured_traffic(kernel: str, workload: str):
     return None
 
 
-def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, workload: str):
-    """Roofline entry of the dominant kernel from live per-kernel events."""
-    name, (ms_tot, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, workload: str,
+             kernel: str | None = None, as_name: str | None = None):
+    """Roofline entry of the dominant kernel (or of `kernel`) from live
+    per-kernel events; `as_name` selects the accounting (e.g. the tcgen05
+    backward counted in MMA FLOPs)."""
+    if kernel is None:
+        name, (ms_tot, launches) = max(prof.items(), key=lambda kv: kv[1][0])
+    else:
+        name, (ms_tot, launches) = kernel, prof[kernel]
+    label = name
+    name = as_name or name
     ms = ms_tot / max(launches, 1)
     w = job
     P = w.cam.width * w.cam.height
     K = w.st.K
     L, F = w.field.L, w.field.F
     b_entry = 2 if w.precision == "bf16" else 4
-    out = {"kernel": name, "ms_per_launch": ms, "launches": launches}
+    out = {"kernel": label, "ms_per_launch": ms, "launches": launches}
     samples = int((w.fwd_out["ids"] >= 0).sum().item()) if w.fwd_out is not None else P * K
-    if name.startswith("texture_fwd") or name.startswith("texture_bwd"):
+    if name == "texture_bwd_tc_flops":
+        # the tcgen05 MLP backward in algorithmic MMA FLOPs per sample row:
+        # forward recompute, input-side deltas and weight gradients
+        widths = w.field.widths
+        macs = sum(widths[i] * widths[i + 1] for i in range(len(widths) - 1))
+        rows = ((P * (1 << (K - 1).bit_length()) + 15) // 16) * 16
+        A = rows * 2 * macs * 3 / (ms * 1e-3) / 1e12
+        pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        out.update(bound="tensor", achieved=A, peak=pk, unit="TFLOP/s",
+                   peak_source=f"bf16_tflops_sustained ({peak_kind})", units_per_launch=rows,
+                   flop_per_unit=2 * macs * 3)
+        out["frac"] = A / pk
+    elif name.startswith("texture_fwd") or name.startswith("texture_bwd"):
         # algorithmic bytes: the table entries the gather reads (8 corners x
         # L levels x F features), plus, in the backward, an FP32 read-modify-
         # write of the same entries in the table gradient
@@ -344,7 +364,7 @@ def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, wo
         # sort / scan / collection kernels: report bytes moved per launch
         # against the HBM peak (algorithmic bytes set by the caller)
         out.update(bound="hbm", achieved=None, peak=peaks["hbm_gbs"], unit="GB/s", frac=None)
-    out["traffic"] = measured_traffic(name, workload)
+    out["traffic"] = measured_traffic(label, workload)
     return out
 
 
@@ -557,6 +577,14 @@ def main():
             json.dump({"bf16_train": prof, "f32_train": prof_f32, "steps": args.steps}, f, indent=1)
 
     rl = roofline(prof, jobs["bf16"], peaks, peak_kind, args.steps, f"config{args.config}")
+    # the other two kernels the measurement plan names: the hash gather (HBM
+    # bytes of the table reads, in the fused texturing forward) and the MLP
+    # backward on the tensor cores (MMA FLOPs against the sustained peak)
+    more = {}
+    for kname, acct in (("texture_fwd_tc", None), ("texture_bwd_tc", "texture_bwd_tc_flops")):
+        if kname in prof:
+            more[kname] = roofline(prof, jobs["bf16"], peaks, peak_kind, args.steps,
+                                   f"config{args.config}", kname, acct)
     n_inst = jobs["bf16"].fwd_out["n_instances"]
     mpix = lambda m: world * P / (m * 1e-3) / 1e6
     line = {
@@ -607,6 +635,7 @@ def main():
                                     sorted(prof_f32.items(), key=lambda kv: -kv[1][0])},
         "profiled_ms_per_step": {"bf16": ms["bf16_train_profiled"], "f32": ms["f32_train_profiled"]},
         "roofline": rl,
+        "rooflines_other": more,
         "cpu_baseline": cpu,
         "e2e": {"value": mpix(e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4},
