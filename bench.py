@@ -261,6 +261,23 @@ class BatchJob:
                                     accumulate=v > 0, grads=self.grads)
 
 
+def max_over_ranks(x: float, device, world: int) -> float:
+    """The slowest rank's value (the job's time): an all-reduce MAX over the
+    process group when there is more than one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix(pixels_per_rank: int, ms_max: float, world: int) -> float:
+    """Replicas (weak scaling): every rank renders its own view in the
+    slowest rank's time, so the job's throughput is world x pixels / time."""
+    return world * pixels_per_rank / (ms_max * 1e-3) / 1e6
+
+
 def timed(fn, steps, flush, stream):
     """Per-step CUDA-event times (ms) with an L2 flush before each step."""
     import torch
@@ -514,10 +531,7 @@ def main():
     _native.nexel_profile_enable(False)
 
     def agg(ts):
-        t = torch.tensor([float(np.mean(ts))], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(float(np.mean(ts)), dev, world)
 
     ms = {k: agg(v) for k, v in results.items()}
 
@@ -586,7 +600,7 @@ def main():
             more[kname] = roofline(prof, jobs["bf16"], peaks, peak_kind, args.steps,
                                    f"config{args.config}", kname, acct)
     n_inst = jobs["bf16"].fwd_out["n_instances"]
-    mpix = lambda m: world * P / (m * 1e-3) / 1e6
+    mpix = lambda m: whole_job_mpix(P, m, world)
     line = {
         "metric": METRIC, "value": mpix(ms["bf16_train"]), "unit": "Mpix/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
