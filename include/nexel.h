@@ -107,7 +107,8 @@ typedef struct {
    * <= 3 (orthonormal, ordered by l then m = -l..l, Condon-Shortley phase),
    * evaluated in the direction from the camera centre to the surfel centre:
    * colour = 1/2 + sum_k Y_k(dir) c_k; d_color of nexel_render_bwd is then
-   * [N][16][3] and d_mu includes the path through the direction. */
+   * [N][16][3] (16-byte aligned, else NEXEL_ERR_INVALID_ARG) and d_mu
+   * includes the path through the direction. */
   int sh_degree;
 } nexel_settings;
 

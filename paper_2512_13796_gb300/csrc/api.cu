@@ -445,6 +445,7 @@ int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
   int rc = check_bwd(cam, settings, field, N, mu, quat, scale, opacity, gamma, ws, ws_bytes,
                      bwd_ws, bwd_ws_bytes, weights, ids, depths, T_final, d_image);
   if (rc != NEXEL_OK) return rc;
+  if (settings->sh_degree == 3 && ((uintptr_t)d_color & 15)) return NEXEL_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   if (!accumulate) {
     rc = zero_grads(settings, field, N, d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color,

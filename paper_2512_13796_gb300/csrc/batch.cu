@@ -137,6 +137,7 @@ int nexel_render_batch_bwd(int n_views, const nexel_camera* cams, const nexel_se
                            float* d_mlp, nexel_stream_t stream) {
   if (n_views <= 0 || !cams || !settings || !ws || !ws_bytes || !d_image)
     return NEXEL_ERR_INVALID_ARG;
+  if (settings->sh_degree == 3 && ((uintptr_t)d_color & 15)) return NEXEL_ERR_INVALID_ARG;
   for (int v = 0; v < n_views; ++v) {
     int rc = check_bwd(&cams[v], settings, field, N, mu, quat, scale, opacity, gamma, ws[v],
                        ws_bytes[v], at(bwd_ws, v), bwd_ws_bytes ? bwd_ws_bytes[v] : 0,

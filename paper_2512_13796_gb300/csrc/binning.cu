@@ -874,11 +874,26 @@ __global__ void k_preprocess_bwd(DevCam c, int N, int sh_degree, const float* __
     gm.z += (q.z - zd * qd) * inv;
     if (d_color) {
       const Sh3 Y = sh3_eval(x, y, zd);
+      float dc[48];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        acc<kAtomic>(d_color + 48 * (size_t)i + 3 * k, Y.y[k] * g[17]);
-        acc<kAtomic>(d_color + 48 * (size_t)i + 3 * k + 1, Y.y[k] * g[18]);
-        acc<kAtomic>(d_color + 48 * (size_t)i + 3 * k + 2, Y.y[k] * g[19]);
+        dc[3 * k] = Y.y[k] * g[17];
+        dc[3 * k + 1] = Y.y[k] * g[18];
+        dc[3 * k + 2] = Y.y[k] * g[19];
+      }
+      if (kAtomic) {
+#pragma unroll
+        for (int k = 0; k < 48; ++k) atomicAdd(d_color + 48 * (size_t)i + k, dc[k]);
+      } else {
+        // the surfel's 48 coefficients are 192 contiguous bytes: 16-byte
+        // read-modify-writes
+        float4* dst = reinterpret_cast<float4*>(d_color + 48 * (size_t)i);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          float4 v = dst[q];
+          v.x += dc[4 * q]; v.y += dc[4 * q + 1]; v.z += dc[4 * q + 2]; v.w += dc[4 * q + 3];
+          dst[q] = v;
+        }
       }
     }
   }

@@ -100,6 +100,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Thread-to-MMA hand-over: generic-proxy shared stores and TMEM reads of all
 // threads happen before the MMAs thread 0 issues next.
 __device__ __forceinline__ void sync_to_mma() {
@@ -239,10 +251,18 @@ struct TcLayout {
   static constexpr int w2t = w2 + H2 * H1 * 2;               // [H1][H2]   B of R3
   static constexpr int w1t = w2t + H2 * H1 * 2;              // [IN][H1]   B of the feature gradient
   static constexpr int w3 = w1t + IN * H1 * 2;               // FP32 [OUT][HL]
-  static constexpr int total = w3 + OUT * HL * 4;
-  // TMEM columns: feature gradient / activations, then Da, then Db
+  // SH outputs: the rows' SH bases Y [128][16] (A of RE) and W3 regrouped
+  // as [3 HL][16] (B of RE: row ch HL + i, column k = W3[3k + ch][i])
+  static constexpr int ytile = w3 + OUT * HL * 4;
+  static constexpr int w3p = ytile + (OUT == 48 ? kTcRows * 16 * 2 : 0);
+  static constexpr int total = w3p + (OUT == 48 ? 3 * HL * 16 * 2 : 0);
+  // TMEM columns: feature gradient / activations, then Da, then Db; SH
+  // outputs add the rows' effective output weights E = Y W3' (3 HL columns)
   static constexpr int t_da = 64, t_db = 64 + HL + ON;
+  static constexpr int t_e = 256;
+  static constexpr int cols = OUT == 48 ? 512 : 256;
   static_assert(t_db + 64 <= 256, "TMEM columns");
+  static_assert(OUT == 3 || t_e + 3 * HL <= cols, "TMEM columns of E");
   static_assert(IN % 16 == 0 && H1 == 64 && (H2 == 0 || H2 == 64), "supported MLP shapes");
   static_assert(HL + ON <= 256 && FA <= 256, "MMA N limits");
 };
@@ -285,6 +305,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
           OP::cvt(W2[i]);
     }
     for (int i = tid; i < OUT * HL; i += kTcThreads) w3s[i] = W3[i];
+    if constexpr (OUT == 48) {
+      for (int i = tid; i < 3 * HL * 16; i += kTcThreads) {
+        const int n = i / 16, k = i % 16, ch = n / HL, h = n % HL;
+        *reinterpret_cast<uint16_t*>(tc_smem + Lt::w3p + cm_off(n, k, 256)) =
+            OP::cvt(W3[(3 * k + ch) * HL + h]);
+      }
+    }
     // zero the delta tile once: the padding columns of d3 stay zero
     for (int i = tid; i < Lt::del_bytes / 16; i += kTcThreads)
       reinterpret_cast<uint4*>(del)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -296,12 +323,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&s_tmem)),
-                 "r"(kTcCols));
+                 "r"(Lt::cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   sync_to_mma();
   const uint32_t tmem = s_tmem;
   const uint32_t t0 = tmem, t_da = tmem + Lt::t_da, t_db = tmem + Lt::t_db;  // columns
+  const uint32_t t_e = tmem + Lt::t_e;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   const uint32_t sb = smem_u32(tc_smem);
   uint32_t phase = 0;
@@ -363,7 +391,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       const float d3[8] = {OP::kScale * gT[0], OP::kScale * gT[1], OP::kScale * gT[2], 0.f, 0.f, 0.f, 0.f, 0.f};
       st8<OP>(del, tid, HL, Lt::SD, d3);
     } else {
-      // output gradient of SH output 3k + ch: Y_k(ray) gT_ch
+      // output gradient of SH output 3k + ch: Y_k(ray) gT_ch; and the row's
+      // SH basis, the A operand of RE
       const Sh3 Y = pixel_sh3(c, valid ? (r >> log2KP) : 0);
 #pragma unroll
       for (int c8 = 0; c8 < 6; ++c8) {
@@ -375,14 +404,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         }
         st8<OP>(del, tid, HL + 8 * c8, Lt::SD, d3);
       }
+      float yv[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) yv[k] = valid ? Y.y[k] : 0.f;
+      st8<OP>(tc_smem + Lt::ytile, tid, 0, 256, yv);
+      st8<OP>(tc_smem + Lt::ytile, tid, 8, 256, yv + 8);
     }
     sync_to_mma();
-    // R1: h1 = X W1^T -> t0
+    // R1: h1 = X W1^T -> t0 (SH outputs: with RE, E = Y W3'^T -> t_e)
     if (tid == 0) {
 #pragma unroll
       for (int kk = 0; kk < IN / 16; ++kk)
         mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
             sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
+      if constexpr (OUT == 48)
+        mma(t_e, sdesc(sb + Lt::ytile, 128, 256), sdesc(sb + Lt::w3p, 128, 256),
+            idesc(128, 3 * HL, 0, 0, OP::kFmt), false);
       commit(&s_bar);
     }
     load_row(tile + gridDim.x, nxt);
@@ -433,8 +470,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       const uint64_t ml = H2 > 0 ? m2 : m1;
       const float4* w34 = reinterpret_cast<const float4*>(w3s);
       float T0 = 0.f, T1 = 0.f, T2 = 0.f;
-      Sh3 Y;
-      if constexpr (OUT == 48) Y = pixel_sh3(c, valid ? (r >> log2KP) : 0);
 #pragma unroll
       for (int c8 = 0; c8 < HL / 8; ++c8) {
         // the (per-row, for SH) output-layer weights of hidden units 8 c8 ..
@@ -447,24 +482,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
             wr[o][4] = b.x; wr[o][5] = b.y; wr[o][6] = b.z; wr[o][7] = b.w;
           }
         } else {
-          // SH: T_ch = sum_k Y_k (W3 h)_{3k + ch}, so the row's effective
-          // weight of channel ch is sum_k Y_k W3[3k + ch]
+          // SH: T_ch = sum_k Y_k (W3 h)_{3k + ch}; the row's effective weight
+          // of channel ch, sum_k Y_k W3[3k + ch], came from RE (TMEM
+          // columns ch HL + i)
 #pragma unroll
-          for (int o = 0; o < 3; ++o)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) wr[o][i] = 0.f;
-#pragma unroll 4
-          for (int k = 0; k < 16; ++k)
-#pragma unroll
-            for (int o = 0; o < 3; ++o) {
-              const float4 a = w34[((3 * k + o) * HL + 8 * c8) / 4];
-              const float4 b = w34[((3 * k + o) * HL + 8 * c8) / 4 + 1];
-              const float y = Y.y[k];
-              wr[o][0] = fmaf(y, a.x, wr[o][0]); wr[o][1] = fmaf(y, a.y, wr[o][1]);
-              wr[o][2] = fmaf(y, a.z, wr[o][2]); wr[o][3] = fmaf(y, a.w, wr[o][3]);
-              wr[o][4] = fmaf(y, b.x, wr[o][4]); wr[o][5] = fmaf(y, b.y, wr[o][5]);
-              wr[o][6] = fmaf(y, b.z, wr[o][6]); wr[o][7] = fmaf(y, b.w, wr[o][7]);
-            }
+          for (int o = 0; o < 3; ++o) tmem_ld8(t_e + lane_base + o * HL + 8 * c8, wr[o]);
         }
         // the last hidden layer of this row, as stored (BF16)
         const uint4 hq = *reinterpret_cast<const uint4*>(act + cm_off(tid, IN + H1 + H2 - HL + 8 * c8, Lt::SA));
@@ -593,7 +615,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   if (!ok && tid == 0 && status) atomicOr(status, kStatusTimeout);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lt::cols));
 }
 
 template <int IN, int H1, int H2, typename OP, int OUT = 3>
