@@ -448,3 +448,74 @@ class Adam:
                            [t.data_ptr() for t in self.m], [t.data_ptr() for t in self.v],
                            [t.numel() for t in self.p], self.lrs, self.b1, self.b2, self.eps,
                            self.t, _stream())
+
+
+class DensityControl:
+    """Adaptive density control of supp. Sec. 7.2 around the library calls:
+    blended errors accumulated across iterations (nexel_blend_error), then a
+    density step that draws 5 % of the surfels (capped by the budget) in
+    proportion to their errors (nexel_densify_select, with exponential
+    random numbers drawn here from a seeded generator), splits them along
+    their long axis (nexel_densify_split) and prunes those with opacity
+    below 0.005 (nexel_prune).  Parameters are the activated surfel tensors
+    (mu, quat, scale, opacity, gamma, color); a density step returns new
+    tensors (the surfel count changes)."""
+
+    PRUNE_OPACITY = 0.005
+
+    def __init__(self, n: int, device, budget: int, seed: int = 0):
+        self.device = torch.device(device)
+        self.budget = int(budget)
+        self.err = torch.zeros(n, device=self.device)
+        self.gen = torch.Generator(device="cpu").manual_seed(seed)
+
+    def accumulate(self, ws: Workspace, cam_s, st_s, n: int, image, target):
+        """Adds this view's blended errors (after its forward on ws)."""
+        N_.nexel_blend_error(cam_s, st_s, n, ws.ws.data_ptr(), ws.ws.numel(), image.data_ptr(),
+                             target.data_ptr(), self.err.data_ptr(), _stream())
+
+    def step(self, params: dict) -> tuple[dict, int, int]:
+        """(new params, surfels split, surfels pruned); resets the errors."""
+        keys = ("mu", "quat", "scale", "opacity", "gamma", "color")
+        N = int(params["mu"].shape[0])
+        n_sel = max(0, min(-(-N * 5 // 100), self.budget - N))
+        color_dim = int(params["color"][0].numel())
+        ws = torch.empty(N_.nexel_density_workspace_size(N + n_sel), dtype=torch.uint8,
+                         device=self.device)
+        # room for the second children, then the split in place
+        grown = {k: torch.cat([params[k].detach(),
+                               torch.zeros((n_sel,) + tuple(params[k].shape[1:]),
+                                           device=self.device)]).contiguous() for k in keys}
+        if n_sel > 0:
+            expo = torch.empty(N).exponential_(generator=self.gen).to(self.device)
+            sel = torch.empty(n_sel, dtype=torch.int32, device=self.device)
+            N_.nexel_densify_select(N, self.err.data_ptr(), expo.data_ptr(), n_sel, ws.data_ptr(),
+                                    ws.numel(), sel.data_ptr(), _stream())
+            N_.nexel_densify_split(N, n_sel, sel.data_ptr(), color_dim,
+                                   *[grown[k].data_ptr() for k in keys], _stream())
+        M = N + n_sel
+        out = {k: torch.empty_like(v) for k, v in grown.items()}
+        n_out = torch.zeros(1, dtype=torch.int32, device=self.device)
+        N_.nexel_prune(M, self.PRUNE_OPACITY, color_dim, [grown[k].data_ptr() for k in keys],
+                       ws.data_ptr(), ws.numel(), [out[k].data_ptr() for k in keys],
+                       n_out.data_ptr(), _stream())
+        kept = int(n_out.item())
+        new = {k: v[:kept].clone() for k, v in out.items()}
+        self.err = torch.zeros(kept, device=self.device)
+        return new, n_sel, M - kept
+
+
+def fps_init(points, m: int) -> tuple:
+    """Farthest point sampling of a point cloud [n, 3] (device float32) to m
+    centres, and their initial scales: the distance at which each was
+    selected (supp. Sec. 7.2; the first takes the second's)."""
+    n = int(points.shape[0])
+    scratch = torch.empty(n, device=points.device)
+    idx = torch.empty(m, dtype=torch.int32, device=points.device)
+    d2 = torch.empty(m, device=points.device)
+    N_.nexel_fps(n, points.contiguous().data_ptr(), m, scratch.data_ptr(), idx.data_ptr(),
+                 d2.data_ptr(), _stream())
+    s = d2.sqrt()
+    if m > 1:
+        s[0] = s[1]
+    return points[idx.long()], s
