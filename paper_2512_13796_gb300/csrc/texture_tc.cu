@@ -21,6 +21,13 @@
 //         Db += [X | ...]^T d1             -> dW1 block
 //       (the row-major activation tiles are read MN-major, K = rows, so no
 //       transposed copies are made).
+// SH textures (OUT = 48: the MLP's outputs are the degree-3 SH coefficients
+// of the texture, evaluated in the pixel's ray direction, Sec. 3 / Sec. 5):
+// the output layer is 48 MMA columns wide; with R1 one more MMA forms each
+// row's effective output weights E = Y W3' (Y: the row's 16 SH basis values,
+// W3 regrouped per channel), read back in place of W3 by the CUDA-core step;
+// the delta tile's output block is Y_k gT_ch; the kernel then needs 512 TMEM
+// columns and more shared memory, so it runs one CTA per SM.
 // Shared-memory operands use the no-swizzle core-matrix layout (8 rows x
 // 16 bytes per core matrix); a descriptor's leading byte offset is the
 // stride between core matrices along K and its stride byte offset the stride
@@ -35,7 +42,6 @@ namespace {
 
 constexpr int kTcRows = 128;
 constexpr int kTcThreads = 128;
-constexpr int kTcCols = 256;  // TMEM columns per CTA (two CTAs per SM)
 constexpr int kTcWaitLimit = 1 << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
