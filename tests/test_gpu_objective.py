@@ -117,6 +117,41 @@ def test_loss_on_a_render_and_params_match_oracle(dev):
     _close(g_tab.cpu().numpy() - g_tab0, ref["d_table"], 1e-4, "d_table")
 
 
+def test_loss_image_full_size(dev):
+    """The headline image size (1280 x 720, K = 4): every term's value, and
+    d_image, d_weights, d_textures on every element, against the oracle."""
+    import torch
+    from paper_2512_13796_gb300 import render as R
+    H, W, K = 720, 1280, 4
+    rng = np.random.default_rng(41)
+    img = rng.uniform(0, 1, (H, W, 3)).astype(np.float32)
+    tgt = np.clip(img + rng.normal(0, 0.05, (H, W, 3)), 0, 1).astype(np.float32)
+    Wt = rng.uniform(0.0, 0.25, (H, W, K)).astype(np.float32)
+    T = rng.uniform(0, 1, (H, W, K, 3)).astype(np.float32)
+    ob = R.Objective(W, H, dev)
+    d_img, d_w, d_t = ob.image_terms(_t(img, dev), _t(tgt, dev), _t(Wt, dev), _t(T, dev))
+    torch.cuda.synchronize()
+    v = ob.read()
+    lam = O.LAMBDAS
+    assert abs(v["l1"] - O.l1(img, tgt)) <= 1e-5 * O.l1(img, tgt)
+    assert abs(v["dssim"] - O.dssim(img, tgt)) <= 1e-5
+    tv, tdW, tdT = O.texture_loss(tgt, Wt, T)
+    av, adW = O.alpha_loss(Wt)
+    assert abs(v["texture"] - tv) <= 1e-5 * tv and abs(v["alpha"] - av) <= 1e-5 * av
+    ref_img = (1 - lam["dssim"]) * O.l1_grad(img, tgt) + lam["dssim"] * O.dssim_grad(img, tgt)
+    _close(d_img.cpu().numpy(), ref_img, 1e-4, "d_image")
+    # |.| decides the sign of the texture residual: a pixel whose residual
+    # lies within FP32 rounding of zero may take the other sign (a tie);
+    # the comparison skips those pixels (a handful of the 921,600)
+    sw = Wt.astype(np.float64).sum(axis=2, keepdims=True)
+    tb = (Wt[..., None].astype(np.float64) * T).sum(axis=2) / sw
+    ok = np.all(np.abs(tb - tgt) > 1e-6, axis=2)
+    assert ok.mean() > 0.999
+    _close(d_w.cpu().numpy()[ok], (lam["texture"] * tdW + lam["alpha"] * adW)[ok], 1e-5,
+           "d_weights")
+    _close(d_t.cpu().numpy()[ok], (lam["texture"] * tdT)[ok], 1e-5, "d_textures")
+
+
 def test_adam_matches_oracle(dev):
     import torch
     from paper_2512_13796_gb300 import render as R

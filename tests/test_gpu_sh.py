@@ -162,3 +162,28 @@ def test_sh_textures_rejected_with_fp32_table_on_tensor_cores(dev):
         R.forward(ws, R.camera_struct(w.cameras[0]), R.settings_struct(w.settings, "f32", "bf16"),
                   fd, fd.storage_table(), fd.weights, *[p[k] for k in SURFEL_KEYS])
     assert ei.value.code == -4
+
+
+@pytest.mark.parametrize("mlp", ["f16", "bf16"])
+def test_sh_paper_configuration_config2_sampled(dev, mlp):
+    """The paper's configuration at the headline size: 300k surfels,
+    1280x720, K = 4, hash 16 x 2^19 x 2 (FP16 table), degree-3 SH in both
+    modes (48 colour coefficients, MLP 32-64-64-48) on the tensor cores,
+    on a pixel sample (random pixels and whole tiles)."""
+    w = synth.workload(2)
+    cam, st = w.cameras[0], w.settings
+    field = synth.make_field(16, 19, 2, (64, 64), 2, out_dim=48)
+    coeffs = synth.sh_coefficients(w.scene.n, 2)
+    pix = synth.pixel_sample(cam, 1024, 2, seed=22)
+    ref = oracle.render_sh(w.scene, coeffs, cam, st, field, pix, tie_tol=TIE, cell_tol=CELL,
+                           relu_tol=RELU)
+    ok = ref["tie"] == 0
+    P, K = cam.width * cam.height, st.K
+    dI, dW, dT = masked_upstream(pix.size, P, K, pix, ok, seed=35)
+    fw, gg = _run(w.scene, coeffs, cam, st, field, dev, "f16", mlp, dI, dW, dT)
+    s = compare_forward(fw, ref, K, 2e-3 if mlp == "bf16" else 1e-3)
+    sel = pix[ok]
+    gr = oracle.render_bwd_sh(w.scene, coeffs, cam, st, field, sel, dI[sel], dW[sel], dT[sel])
+    st_g = compare_grads(gg, gr, 0.1 if mlp == "bf16" else 0.05, metric="l2")
+    print(f"\n[sh config2 {mlp}] image err {s['image']:.2e} ties {s['n_tie']}/{s['n_pix']} "
+          f"grads {st_g}")
