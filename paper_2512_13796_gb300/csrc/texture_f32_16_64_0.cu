@@ -1,4 +1,4 @@
-// FP32 texturing kernels for the 16 -> 64 -> 3 MLP and its 48-output (SH) form.
+// FP32 texturing kernels for the 16 -> 64 -> 3 MLP.
 #include "texture_f32.cuh"
 
 namespace nexel {
@@ -6,13 +6,6 @@ template cudaError_t tex_fwd_f32<16, 64, 0, float>(
     const DevCam&, const nexel_settings&, const FieldDev&, const float*, const float*, const int*,
     const float*, const float*, float*, float*, cudaStream_t);
 template cudaError_t tex_bwd_f32<16, 64, 0, float>(
-    const DevCam&, const nexel_settings&, const FieldDev&, char*, const BwdLayout&, const float*,
-    const int*, const float*, const float*, const float*, const float*, float*, float*,
-    cudaStream_t);
-template cudaError_t tex_fwd_f32<16, 64, 0, float, 48>(
-    const DevCam&, const nexel_settings&, const FieldDev&, const float*, const float*, const int*,
-    const float*, const float*, float*, float*, cudaStream_t);
-template cudaError_t tex_bwd_f32<16, 64, 0, float, 48>(
     const DevCam&, const nexel_settings&, const FieldDev&, char*, const BwdLayout&, const float*,
     const int*, const float*, const float*, const float*, const float*, float*, float*,
     cudaStream_t);
