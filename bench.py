@@ -565,6 +565,36 @@ def main():
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     e2e_ms = agg([e2e_ms])
 
+    # the same step through the graph API (render.BatchStep with one view):
+    # target H2D, one CUDA graph (forward, L1 loss and its gradient in torch,
+    # backward), loss D2H
+    gstep = R.BatchStep([w.cameras[0]], w.settings, fld,
+                        {k: v.detach() for k, v in params.items()})
+    tgt_dev = torch.empty(H, W, 3, device=dev)
+    loss_dev = torch.zeros(1, device=dev)
+
+    def l1_and_grad():
+        diff = gstep.out[0]["image"] - tgt_dev
+        loss_dev.copy_(diff.abs().mean().reshape(1))
+        gstep.d_image[0].copy_(torch.sign(diff) / diff.numel())
+
+    tgt_dev.copy_(target_host.to(dev))
+    gstep.capture(l1_and_grad)
+
+    def e2e_graph_step():
+        tgt_dev.copy_(target_host, non_blocking=True)
+        gstep.replay()
+        loss_host.copy_(loss_dev, non_blocking=True)
+
+    for _ in range(3):
+        e2e_graph_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_graph_step()
+    torch.cuda.synchronize()
+    e2e_graph_ms = agg([(time.perf_counter() - t0) * 1e3 / args.steps])
+
     # the batched 8-view form, last (its 600k-surfel scene and 8 views'
     # buffers are allocated only now), with its own clock samples
     batch, clk_batch = None, None
@@ -652,7 +682,12 @@ def main():
         "rooflines_other": more,
         "cpu_baseline": cpu,
         "e2e": {"value": mpix(e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4},
+                "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4,
+                "path": "render() autograd API: H2D target, forward, L1 loss, backward, D2H loss"},
+        "e2e_graph": {"value": mpix(e2e_graph_ms), "unit": "Mpix/s", "ms_per_step": e2e_graph_ms,
+                      "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4,
+                      "path": "render.BatchStep graph API (one view): H2D target, one CUDA graph "
+                              "replay (forward, L1 loss, backward), D2H loss"},
         "gpu_launches": int(launches),
         "gpu_launches_note": "kernels of libnexel per timed step (library launch counter)",
         "clocks": clk,
