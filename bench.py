@@ -683,11 +683,13 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": mpix(e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4,
-                "path": "render() autograd API: H2D target, forward, L1 loss, backward, D2H loss"},
+                "path": "render() autograd API: H2D target, forward, L1 loss, backward, D2H loss; "
+                        "no L2 flush between steps"},
         "e2e_graph": {"value": mpix(e2e_graph_ms), "unit": "Mpix/s", "ms_per_step": e2e_graph_ms,
                       "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4,
                       "path": "render.BatchStep graph API (one view): H2D target, one CUDA graph "
-                              "replay (forward, L1 loss, backward), D2H loss"},
+                              "replay (forward, L1 loss, backward), D2H loss; no L2 flush between "
+                              "steps"},
         "gpu_launches": int(launches),
         "gpu_launches_note": "kernels of libnexel per timed step (library launch counter)",
         "clocks": clk,
