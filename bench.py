@@ -631,6 +631,26 @@ def main():
                                    f"config{args.config}", kname, acct)
     n_inst = jobs["bf16"].fwd_out["n_instances"]
     mpix = lambda m: whole_job_mpix(P, m, world)
+    # work counts of the collection pass (device reduction over the BF16
+    # job's last forward, outside the timed regions)
+    jb = jobs["bf16"]
+    stats = _native.nexel_render_stats(jb.cam_s, jb.st_train, jb.N, jb.ws.ws.data_ptr(),
+                                       jb.ws.ws.numel(), torch.cuda.current_stream().cuda_stream)
+    t_cf = prof["collect_fwd"][0] / args.steps if "collect_fwd" in prof else None
+    t_cb = prof["collect_bwd"][0] / args.steps if "collect_bwd" in prof else None
+    collection = {
+        "visible_surfels": stats["visible_surfels"],
+        "mean_tiles_per_visible_surfel": n_inst / max(stats["visible_surfels"], 1),
+        "longest_tile_list": stats["longest_list"], "tiles": stats["tiles"],
+        "pairs_to_last": stats["pairs_to_last"], "pairs_full_lists": stats["pairs_full_lists"],
+        "fwd_gpairs_per_s": stats["pairs_to_last"] / (t_cf * 1e-3) / 1e9 if t_cf else None,
+        "pairs_bwd_walk": stats["pairs_bwd_walk"],
+        "bwd_gpairs_per_s": stats["pairs_bwd_walk"] / (t_cb * 1e-3) / 1e9 if t_cb else None,
+        "note": "pairs_to_last = sum over pixels of the last list position composited (a "
+                "lower bound of the (pixel, surfel) pairs the forward evaluates); "
+                "pairs_bwd_walk = sum over tiles of the largest last position x tile pixels "
+                "(the pair evaluations the collection backward runs); pairs_full_lists = sum "
+                "over tiles of list length x tile pixels (no early termination)"}
     line = {
         "metric": METRIC, "value": mpix(ms["bf16_train"]), "unit": "Mpix/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -680,6 +700,7 @@ def main():
         "profiled_ms_per_step": {"bf16": ms["bf16_train_profiled"], "f32": ms["f32_train_profiled"]},
         "roofline": rl,
         "rooflines_other": more,
+        "collection": collection,
         "cpu_baseline": cpu,
         "e2e": {"value": mpix(e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4,

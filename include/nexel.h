@@ -406,6 +406,23 @@ int nexel_instance_list(const nexel_camera* cam, int N, const void* ws, size_t w
                         long long n_instances, int* tile_out, int* id_out, float* depth_out,
                         nexel_stream_t stream);
 
+/* Work statistics of the last nexel_render_fwd on ws (a device reduction;
+ * synchronises `stream`).  Writes out[7] (host):
+ *   out[0] (tile, surfel) instances of the binning (Sec. 3, "Preliminaries"),
+ *   out[1] surfels with at least one instance (not culled, on screen),
+ *   out[2] sum over pixels of the last list position the pixel composited
+ *          (Sec. 4.2): the (pixel, surfel) pairs the collection backward
+ *          evaluates, a lower bound of those the forward evaluates,
+ *   out[3] sum over tiles of list length x pixels of the tile: the pairs a
+ *          pass without early termination would evaluate,
+ *   out[4] the longest tile list, out[5] the number of 16 x 16 tiles,
+ *   out[6] sum over tiles of (largest last list position of its pixels) x
+ *          pixels of the tile: the pair evaluations the collection backward
+ *          runs (every thread of a tile walks back from the tile's largest).
+ * The counters block of ws holds the reduction; nothing else is changed. */
+int nexel_render_stats(const nexel_camera* cam, const nexel_settings* settings, int N,
+                       void* ws, size_t ws_bytes, long long* out, nexel_stream_t stream);
+
 /* Instrumentation (no counterpart in the paper).  nexel_launch_count: the
  * number of kernels this library has launched in the process.
  * nexel_profile_enable(1) starts recording a CUDA event pair on the launch

@@ -36,7 +36,7 @@ EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess
            "nexel_loss_image", "nexel_loss_params", "nexel_adam_step", "nexel_fps",
            "nexel_blend_error", "nexel_density_workspace_size", "nexel_densify_select",
            "nexel_densify_split", "nexel_prune", "nexel_get_tuning", "nexel_set_tuning",
-           "nexel_autotune"]
+           "nexel_autotune", "nexel_render_stats"]
 
 
 def _nvcc() -> str:
@@ -143,6 +143,7 @@ def lib(auto_build: bool = False):
     L.nexel_render_bwd.argtypes = ([vp, vp, vp, i] + [vp] * 5 + [vp, sz, vp, sz] + [vp] * 4 +
                                    [vp] * 3 + [i] + [vp] * 8 + [vp])
     L.nexel_instance_list.argtypes = [vp, i, vp, sz, ll, vp, vp, vp, vp]
+    L.nexel_render_stats.argtypes = [vp, vp, i, vp, sz, C.POINTER(ll), vp]
     L.nexel_render_fwd_static.argtypes = [vp, vp, vp, i] + [vp] * 6 + [vp] * 7 + [
         C.POINTER(ll), vp]
     L.nexel_preprocess_async.argtypes = [vp, vp, i] + [vp] * 7 + [sz, vp]
@@ -240,6 +241,18 @@ def nexel_instance_list(cam, N, ws, ws_bytes, n_instances, tile_out, id_out, dep
                         stream) -> int:
     return check("nexel_instance_list", lib().nexel_instance_list(
         C.byref(cam), N, ws, ws_bytes, n_instances, tile_out, id_out, depth_out, stream))
+
+
+RENDER_STATS = ("instances", "visible_surfels", "pairs_to_last", "pairs_full_lists",
+                "longest_list", "tiles", "pairs_bwd_walk")
+
+
+def nexel_render_stats(cam, st, N, ws, ws_bytes, stream) -> dict:
+    """Work statistics of the last forward on ws (synchronises the stream)."""
+    out = (C.c_longlong * 7)()
+    check("nexel_render_stats", lib().nexel_render_stats(C.byref(cam), C.byref(st), N, ws,
+                                                         ws_bytes, out, stream))
+    return dict(zip(RENDER_STATS, (int(v) for v in out)))
 
 
 def nexel_render_fwd_static(cam, st, field, N, mu, quat, scale, opacity, gamma, color, image,

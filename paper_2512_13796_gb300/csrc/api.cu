@@ -207,6 +207,53 @@ __global__ void k_instance_list(long long n, int rank_bits, uint32_t rmask,
   if (depth_out) depth_out[i] = __uint_as_float(dkey[r]);
 }
 
+// Work statistics of the last forward on a workspace, reduced on the device
+// into out[0..4] (64-bit counters in the counters block): Sigma_p last_p
+// (list positions up to each pixel's last composited surfel), Sigma_tiles
+// list length x pixels of the tile, the longest list, the surfels with at
+// least one instance, and Sigma_tiles (max_p in tile last_p) x pixels of the
+// tile (the lane iterations of the collection backward, which walks every
+// tile from its largest last position down).
+__global__ void __launch_bounds__(256) k_render_stats(int W, int H, int tiles_x, int n_tiles,
+                                                      int N, const int* __restrict__ n_contrib,
+                                                      const uint2* __restrict__ ranges,
+                                                      const uint32_t* __restrict__ count,
+                                                      unsigned long long* __restrict__ out) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long last = 0, walk = 0, vis = 0, longest = 0, bwalk = 0;
+  for (long long p = tid; p < (long long)W * H; p += stride) last += (unsigned)n_contrib[p];
+  for (long long t = tid; t < n_tiles; t += stride) {
+    const uint2 r = ranges[t];
+    const unsigned long long len = r.y > r.x ? r.y - r.x : 0;
+    const int tx = (int)(t % tiles_x), ty = (int)(t / tiles_x);
+    const int pw = min(kTile, W - tx * kTile), ph = min(kTile, H - ty * kTile);
+    walk += len * (unsigned long long)(pw * ph);
+    longest = max(longest, len);
+    int tmax = 0;
+    for (int y = 0; y < ph; ++y)
+      for (int x = 0; x < pw; ++x)
+        tmax = max(tmax, n_contrib[(size_t)(ty * kTile + y) * W + tx * kTile + x]);
+    bwalk += (unsigned long long)tmax * (unsigned long long)(pw * ph);
+  }
+  for (long long i = tid; i < N; i += stride) vis += count[i] > 0 ? 1 : 0;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    last += __shfl_xor_sync(0xffffffffu, last, d);
+    walk += __shfl_xor_sync(0xffffffffu, walk, d);
+    vis += __shfl_xor_sync(0xffffffffu, vis, d);
+    bwalk += __shfl_xor_sync(0xffffffffu, bwalk, d);
+    longest = max(longest, __shfl_xor_sync(0xffffffffu, longest, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (last) atomicAdd(out + 0, last);
+    if (walk) atomicAdd(out + 1, walk);
+    if (longest) atomicMax(out + 2, longest);
+    if (vis) atomicAdd(out + 3, vis);
+    if (bwalk) atomicAdd(out + 4, bwalk);
+  }
+}
+
 // ------------------------------------------------ per-view implementations
 // Shared by the single-view entry points and the batched ones (batch.cu).
 
@@ -517,6 +564,45 @@ int nexel_instance_list(const nexel_camera* cam, int N, const void* ws, size_t w
                                                       tile_out, id_out, depth_out);
     }
   return cuda_status(cudaGetLastError());
+}
+
+int nexel_render_stats(const nexel_camera* cam, const nexel_settings* settings, int N,
+                       void* ws, size_t ws_bytes, long long* out, nexel_stream_t stream) {
+  if (!cam_ok(cam) || !settings_ok(settings) || N < 0 || !ws || !out)
+    return NEXEL_ERR_INVALID_ARG;
+  WsLayout L = ws_layout_for_bytes(*cam, settings->K, N, ws_bytes);
+  if (L.cap < 0) return NEXEL_ERR_INVALID_ARG;
+  char* w = (char*)ws;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* acc = (unsigned long long*)(w + L.counters + kStatsOffset);
+  cudaError_t e = cudaMemsetAsync(acc, 0, 5 * sizeof(unsigned long long), st);
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    NEXEL_PROF("render_stats", st);
+    k_render_stats<<<2 * nsm, 256, 0, st>>>(cam->width, cam->height,
+                                            (cam->width + kTile - 1) / kTile, L.n_tiles, N,
+                                            (const int*)(w + L.n_contrib),
+                                            (const uint2*)(w + L.ranges),
+                                            (const uint32_t*)(w + L.count), acc);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[5] = {0, 0, 0, 0, 0};
+  uint32_t n_inst = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&n_inst, w + L.counters + kCountersInst, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return NEXEL_ERR_CUDA;
+  out[0] = (long long)n_inst;
+  out[1] = (long long)h[3];
+  out[2] = (long long)h[0];
+  out[3] = (long long)h[1];
+  out[4] = (long long)h[2];
+  out[5] = (long long)L.n_tiles;
+  out[6] = (long long)h[4];
+  return NEXEL_OK;
 }
 
 }  // extern "C"

@@ -183,6 +183,7 @@ constexpr int kStatusCapacity = 2;
 // counters region: [0] unused, [1] instance count, [8] status word
 constexpr size_t kCountersInst = 4;
 constexpr size_t kStatusOffset = 32;
+constexpr size_t kStatsOffset = 64;  // 5 x u64 of nexel_render_stats
 
 // ------------------------------------------------------------ workspace
 // Main workspace (binning results and per-pixel replay data).  Regions that

@@ -370,3 +370,42 @@ def test_cached_features_match_gathered(dev, mlp, recompute):
     else:
         s = compare_grads(g2, g1, 1e-2, metric="l2")
         _report(f"cached vs gathered bf16 recompute={recompute}", s)
+
+
+@pytest.mark.parametrize("idx", [0, 1])
+def test_render_stats(dev, idx):
+    """nexel_render_stats against the instance list (instances, visible
+    surfels, per-tile list lengths) and, on the 64x64 view, against the
+    oracle's composited counts: every pixel's last list position lies between
+    the number of surfels it composited and its tile's list length."""
+    import torch
+    from paper_2512_13796_gb300 import _native as N_
+    from paper_2512_13796_gb300 import render as R
+    w = synth.workload(idx, precision="f32")
+    cam = w.cameras[0]
+    fw, _, ws = run_gpu(w.scene, cam, w.settings, w.field, dev)
+    cam_s = R.camera_struct(cam)
+    st_s = R.settings_struct(w.settings)
+    stream = torch.cuda.current_stream().cuda_stream
+    s = N_.nexel_render_stats(cam_s, st_s, w.scene.n, ws.ws.data_ptr(), ws.ws.numel(), stream)
+    n = fw["n_instances"]
+    assert s["instances"] == n
+    tiles = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ids = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    N_.nexel_instance_list(cam_s, w.scene.n, ws.ws.data_ptr(), ws.ws.numel(), n,
+                           tiles.data_ptr(), ids.data_ptr(), None, stream)
+    torch.cuda.synchronize()
+    t, i = tiles.cpu().numpy()[:n], ids.cpu().numpy()[:n]
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    assert s["tiles"] == tx * ty
+    assert s["visible_surfels"] == np.unique(i).size
+    lens = np.bincount(t, minlength=tx * ty).astype(np.int64)
+    pw = np.minimum(16, cam.width - 16 * (np.arange(tx * ty) % tx))
+    ph = np.minimum(16, cam.height - 16 * (np.arange(tx * ty) // tx))
+    assert s["pairs_full_lists"] == int(np.sum(lens * pw * ph))
+    assert s["longest_list"] == int(lens.max())
+    assert 0 < s["pairs_to_last"] <= s["pairs_bwd_walk"] <= s["pairs_full_lists"]
+    if idx == 0:
+        ref = oracle.render(w.scene, cam, w.settings, w.field)
+        assert s["pairs_to_last"] >= int(ref["n_contrib"].sum())
+    print(f"\n[stats config{idx}] {s}")
