@@ -156,8 +156,10 @@ __device__ __forceinline__ void warp_sum20_add(const float (&g)[kGradStride], fl
   if (lo <= 2 && mid <= 4 && z != 0.f) atomicAdd(dst + 10 * (int)b4 + 5 * (int)b3 + mid, z);
 }
 
+// Four CTAs per SM (64 registers, no spills): the replay is issue-bound and
+// gains from the fourth tile in flight.
 template <int K, typename KeyT>
-__global__ void __launch_bounds__(kTilePix) k_collect_bwd(
+__global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
     DevCam c, float alpha_min, float alpha_max, float bg0, float bg1, float bg2, uint32_t rmask,
     const uint2* __restrict__ ranges, const KeyT* __restrict__ keys,
     const float4* __restrict__ recs, const int* __restrict__ ids, const float* __restrict__ T_final,
