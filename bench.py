@@ -631,6 +631,24 @@ def main():
                                    f"config{args.config}", kname, acct)
     n_inst = jobs["bf16"].fwd_out["n_instances"]
     mpix = lambda m: whole_job_mpix(P, m, world)
+    # the hash backward's real ceiling: L2 vector reductions.  Their rate is
+    # measured here (random float2 reductions into a 64 MiB table, the size
+    # of the FP32 gradient table, inside the flush buffer) and set against
+    # the reduction sectors ncu counted for one launch of the kernel.
+    red_peak = _native.nexel_peak_l2_reductions(flush_buf.data_ptr(), 64 << 20, 200_000_000, 3,
+                                                torch.cuda.current_stream().cuda_stream)
+    red_sectors = measured_traffic("hash_bwd_red_sectors", f"config{args.config}")
+    if "hash_bwd" in prof:
+        t_hb = prof["hash_bwd"][0] / prof["hash_bwd"][1]
+        ach = red_sectors / (t_hb * 1e-3) / 1e9 if red_sectors else None
+        more["hash_bwd_l2_reductions"] = {
+            "kernel": "hash_bwd", "ms_per_launch": t_hb, "bound": "l2_reductions",
+            "achieved": ach, "peak": red_peak, "unit": "G reduction sectors/s",
+            "frac": ach / red_peak if ach else None, "red_sectors_per_launch": red_sectors,
+            "peak_source": "nexel_peak_l2_reductions in this run: random float2 reductions "
+                           "into a 64 MiB L2-resident table (median of 3 x 2e8)",
+            "note": "red_sectors_per_launch = lts__t_sectors_op_red.sum of one ncu capture "
+                    "(profiles/l2_traffic_config2.md); null when hash_bwd.cu changed since"}
     # work counts of the collection pass (device reduction over the BF16
     # job's last forward, outside the timed regions)
     jb = jobs["bf16"]

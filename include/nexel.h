@@ -435,6 +435,18 @@ long long nexel_launch_count(void);
 int nexel_profile_enable(int on);
 int nexel_profile_read(int max_entries, char* names, float* total_ms, int* launches, int* n_out);
 
+/* Device measurement (no counterpart in the paper): the rate of random
+ * float2 reductions (red.global.add of two float32) into an L2-resident
+ * table, the resource that bounds the hash-grid backward's scatter (the
+ * adjoint of the trilinear lookup, Eq. 4).  buf (device, 8-byte aligned,
+ * buf_bytes >= 8) holds the table: its largest power-of-two count of float2
+ * entries that fits is zeroed, then each of `reps` launches adds (1, 1) at
+ * n_ops hashed indices; the table then holds 2 * n_ops * reps in total.
+ * Writes the median rate over the reps in 1e9 reductions per second to
+ * *gops_out (host).  Synchronises `stream`. */
+int nexel_peak_l2_reductions(void* buf, size_t buf_bytes, long long n_ops, int reps,
+                             float* gops_out, nexel_stream_t stream);
+
 /* Allocation-free forward render (the paper has no counterpart: this is a
  * deployment variant).  For callers that cannot allocate device memory --
  * e.g. a plugin inside a host application that owns all device

@@ -36,7 +36,7 @@ EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess
            "nexel_loss_image", "nexel_loss_params", "nexel_adam_step", "nexel_fps",
            "nexel_blend_error", "nexel_density_workspace_size", "nexel_densify_select",
            "nexel_densify_split", "nexel_prune", "nexel_get_tuning", "nexel_set_tuning",
-           "nexel_autotune", "nexel_render_stats"]
+           "nexel_autotune", "nexel_render_stats", "nexel_peak_l2_reductions"]
 
 
 def _nvcc() -> str:
@@ -144,6 +144,7 @@ def lib(auto_build: bool = False):
                                    [vp] * 3 + [i] + [vp] * 8 + [vp])
     L.nexel_instance_list.argtypes = [vp, i, vp, sz, ll, vp, vp, vp, vp]
     L.nexel_render_stats.argtypes = [vp, vp, i, vp, sz, C.POINTER(ll), vp]
+    L.nexel_peak_l2_reductions.argtypes = [vp, sz, ll, i, C.POINTER(C.c_float), vp]
     L.nexel_render_fwd_static.argtypes = [vp, vp, vp, i] + [vp] * 6 + [vp] * 7 + [
         C.POINTER(ll), vp]
     L.nexel_preprocess_async.argtypes = [vp, vp, i] + [vp] * 7 + [sz, vp]
@@ -253,6 +254,14 @@ def nexel_render_stats(cam, st, N, ws, ws_bytes, stream) -> dict:
     check("nexel_render_stats", lib().nexel_render_stats(C.byref(cam), C.byref(st), N, ws,
                                                          ws_bytes, out, stream))
     return dict(zip(RENDER_STATS, (int(v) for v in out)))
+
+
+def nexel_peak_l2_reductions(buf, buf_bytes, n_ops, reps, stream) -> float:
+    """Median rate of random float2 L2 reductions (1e9 per second)."""
+    g = C.c_float(0.0)
+    check("nexel_peak_l2_reductions", lib().nexel_peak_l2_reductions(buf, buf_bytes, n_ops, reps,
+                                                                     C.byref(g), stream))
+    return float(g.value)
 
 
 def nexel_render_fwd_static(cam, st, field, N, mu, quat, scale, opacity, gamma, color, image,

@@ -81,3 +81,21 @@ def test_autotune_and_tuning_invariance(dev):
             assert float((a - b).norm() / b.norm()) < 1e-5, k
     finally:
         N_.nexel_set_tuning(t0)
+
+
+def test_peak_l2_reductions_counts(dev):
+    """The reduction-rate probe adds (1, 1) n_ops x reps times into the
+    largest power-of-two float2 table that fits the buffer and leaves the
+    rest of the buffer alone."""
+    import torch
+    from paper_2512_13796_gb300 import _native as N_
+    buf = torch.full((((1 << 20) + 96) // 4,), -7.0, device=dev)  # 1 MiB table + 96 B tail
+    n, reps = 1_000_003, 2
+    g = N_.nexel_peak_l2_reductions(buf.data_ptr(), buf.numel() * 4, n, reps,
+                                    torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    tab = buf[: (1 << 20) // 4].double()
+    assert g > 0.0
+    assert float(tab.sum()) == 2.0 * n * reps
+    assert torch.all(tab >= 0) and torch.all(tab == tab.round())
+    assert torch.all(buf[(1 << 20) // 4:] == -7.0)
