@@ -51,6 +51,14 @@ static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
   L.n_contrib = take((size_t)std::max(L.P, 1) * 4);
   L.grad_sorted = take(n * kGradStride * 4);
   L.counters = take(256);
+  // direct placement by tile: [rank block][tile] counts and the tile starts
+  L.place_ok = (!L.key64 && L.n_tiles <= kPlaceMaxTiles) ? 1 : 0;
+  const size_t place_blocks = L.place_ok ? (n + kPlaceRanks - 1) / kPlaceRanks : 0;
+  L.place = take(place_blocks * (size_t)L.n_tiles * 4);
+  L.place_tiles = take(L.place_ok ? (size_t)L.n_tiles * 4 : 0);
+  L.mword_off = take(L.place_ok ? (n + 1) * 4 : 0);
+  L.mword_cap = L.place_ok ? (long long)n * kMaskWordsPerSurfel : 0;
+  L.mwords = take((size_t)L.mword_cap * 4);
   L.fixed_end = o;
 }
 
@@ -69,7 +77,8 @@ static void ws_cap(WsLayout& L, long long cap) {
   const size_t depth_tile = (size_t)kSortThreads * kSortItemsDepth;
   long long nb = std::max((c + kSortTile - 1) / kSortTile, ((size_t)L.N + depth_tile - 1) / depth_tile);
   L.hist = take((size_t)256 * nb * 4);
-  long long scan_n = std::max(256LL * nb, (long long)L.N + 1);
+  // the scans: radix histograms, the N + 1 surfel counts, the tile starts
+  long long scan_n = std::max(std::max(256LL * nb, (long long)L.N + 1), (long long)L.n_tiles);
   L.scan_sums = take(((size_t)(scan_n + kScanTile - 1) / kScanTile + 1) * 4);
   L.total = o;
 }

@@ -644,11 +644,17 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
 // Exact instance count of each surfel: the tiles of its rectangle that pass
 // tile_may_hit (one warp per surfel, original order), and, for rectangles of
 // at most 128 tiles, the pass/fail bits in rectangle order for k_duplicate.
+// With mwords, the pass/fail bits of every rectangle are also stored, one
+// word per 32 tiles of rectangle order, at the surfel's offset moff[i] (an
+// exclusive scan of the word counts), when they fit below cap_words.
 __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
                                                     const uint2* __restrict__ rect,
                                                     const float4* __restrict__ conic,
                                                     uint4* __restrict__ tmask,
-                                                    uint32_t* __restrict__ count) {
+                                                    uint32_t* __restrict__ count,
+                                                    const uint32_t* __restrict__ moff,
+                                                    uint32_t* __restrict__ mwords,
+                                                    uint32_t cap_words) {
   const int lane = threadIdx.x & 31;
   const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (i >= N || count[i] == 0) return;  // warp-uniform
@@ -657,6 +663,12 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
   const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
   const float inv_nx = 1.f / (float)nx;
   const TileConic kc = load_conic(conic, (uint32_t)i);
+  const uint32_t words = (uint32_t)(nt + 31) / 32;
+  uint32_t* mw_out = nullptr;
+  if (mwords) {
+    const uint32_t off = moff[i];
+    if (off <= cap_words && words <= cap_words - off) mw_out = mwords + off;
+  }
   uint32_t n = 0;
   if (nt <= 128) {
     uint32_t mw[4] = {0u, 0u, 0u, 0u};
@@ -672,15 +684,325 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
       tmask[i] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
       count[i] = n;
     }
+    if (mw_out && lane < (int)words)
+      mw_out[lane] = lane == 0 ? mw[0] : lane == 1 ? mw[1] : lane == 2 ? mw[2] : mw[3];
     return;
   }
-  for (int k = lane; k < nt; k += 32) {
+  for (int b = 0; b < nt; b += 32) {  // warp-uniform
+    const int k = b + lane;
     const int2 t2 = rect_tile(k, nx, inv_nx);
-    n += tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H) ? 1u : 0u;
+    const bool hit = k < nt && tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H);
+    const uint32_t m = __ballot_sync(0xffffffffu, hit);
+    n += __popc(m);
+    if (mw_out && lane == 0) mw_out[b >> 5] = m;
   }
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) n += __shfl_xor_sync(0xffffffffu, n, d);
   if (lane == 0) count[i] = n;
+}
+
+// Word count of each surfel's rectangle decisions (one per 32 tiles; none
+// for a culled surfel), to be scanned into the offsets of k_tile_count.
+__global__ void k_mask_words(int N, const uint2* __restrict__ rect,
+                             const uint32_t* __restrict__ count, uint32_t* __restrict__ words) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint2 rc = rect[i];
+  const uint32_t nt = ((rc.x >> 16) - (rc.x & 0xFFFF) + 1) * ((rc.y >> 16) - (rc.y & 0xFFFF) + 1);
+  words[i] = count[i] == 0 ? 0u : (nt + 31) / 32;
+}
+
+// ------------------------------------------------ direct placement by tile
+// The per-tile lists are the instances of the depth-rank-ordered surfels,
+// split by tile and kept in rank order.  Instead of sorting the rank-ordered
+// instance sequence on its tile bits, every instance is written straight to
+// its final slot:
+//   slot(r, t) = start(t) + #{instances of tile t from surfels of rank < r}.
+// Ranks come in blocks of kPlaceRanks: k_place_count counts each block's
+// instances per tile (shared-memory counters), k_place_colscan turns the
+// [block][tile] counts into per-tile exclusive prefixes over the blocks and
+// per-tile totals, whose exclusive scan gives start(t).  k_place_write then
+// walks its block in groups of 32 ranks: a 32-bit mask per tile records
+// which ranks of the group cover the tile, so an instance's place within
+// the group is a popcount of the lower bits, and the group's counts advance
+// the tile's running base.  The result is the same sequence as the stable
+// sort, bit for bit.
+
+// The block's kPlaceRanks ranks staged in shared memory (tile rectangle,
+// surfel id or ~0 when the surfel has no instance, offset of its decision
+// words), loaded with all threads at once so that the walks below read no
+// per-rank data from global memory.
+struct PlaceRanks {
+  uint2* rect;
+  uint32_t* id;
+  uint32_t* off;
+};
+constexpr size_t kPlaceStageBytes = (size_t)kPlaceRanks * (8 + 4 + 4);
+constexpr int kPlaceStageWords = 8192;  // decision words the write kernel stages
+static_assert(kPlaceThreads == kPlaceRanks, "the count kernel scans one rank per thread");
+
+__device__ __forceinline__ PlaceRanks stage_ranks(unsigned char* smem, long long r0, int N,
+                                                  const uint32_t* __restrict__ did,
+                                                  const uint2* __restrict__ rect,
+                                                  const uint32_t* __restrict__ count,
+                                                  const uint32_t* __restrict__ moff) {
+  PlaceRanks pr;
+  pr.rect = reinterpret_cast<uint2*>(smem);
+  pr.id = reinterpret_cast<uint32_t*>(smem + (size_t)kPlaceRanks * 8);
+  pr.off = reinterpret_cast<uint32_t*>(smem + (size_t)kPlaceRanks * 12);
+  for (int i = threadIdx.x; i < kPlaceRanks; i += blockDim.x) {
+    const long long r = r0 + i;
+    uint32_t id = ~0u;
+    if (r < N) {
+      id = did[r];
+      pr.rect[i] = rect[id];
+      pr.off[i] = moff[id];
+      if (count[id] == 0) id = ~0u;
+    }
+    pr.id[i] = id;
+  }
+  return pr;
+}
+
+__device__ __forceinline__ uint32_t rect_words(uint2 rc) {
+  const uint32_t nt = ((rc.x >> 16) - (rc.x & 0xFFFF) + 1) * ((rc.y >> 16) - (rc.y & 0xFFFF) + 1);
+  return (nt + 31) / 32;
+}
+
+// Decision word w (rectangle tiles 32 w .. 32 w + 31) of a staged surfel,
+// from one thread: stored by k_tile_count when it fitted, else the same
+// tests again.
+__device__ __forceinline__ uint32_t rect_word(const DevCam& c, uint32_t id, uint2 rc,
+                                              uint32_t off, const uint32_t* __restrict__ mwords,
+                                              uint32_t cap_words,
+                                              const float4* __restrict__ conic, int w) {
+  const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
+  const uint32_t words = (uint32_t)(nt + 31) / 32;
+  if (off <= cap_words && words <= cap_words - off) return mwords[off + w];
+  const float inv_nx = 1.f / (float)nx;
+  const TileConic kc = load_conic(conic, id);
+  uint32_t m = 0u;
+  for (int b = 0; b < 32; ++b) {
+    const int k = 32 * w + b;
+    if (k >= nt) break;
+    const int2 t2 = rect_tile(k, nx, inv_nx);
+    if (tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H)) m |= 1u << b;
+  }
+  return m;
+}
+
+// Calls f(t) for every passing tile of decision word w of a rectangle.
+template <typename F>
+__device__ __forceinline__ void for_word_tiles(const DevCam& c, uint2 rc, uint32_t m, int w,
+                                               F&& f) {
+  const int tx0 = rc.x & 0xFFFF, ty0 = rc.y & 0xFFFF;
+  const int nx = (rc.x >> 16) - tx0 + 1;
+  const float inv_nx = 1.f / (float)nx;
+  while (m) {
+    const int b = __ffs(m) - 1;
+    m &= m - 1u;
+    const int2 t2 = rect_tile(32 * w + b, nx, inv_nx);
+    f((ty0 + t2.y) * c.tiles_x + tx0 + t2.x);
+  }
+}
+
+// Block-wide exclusive prefix of the staged ranks' decision-word counts into
+// pre[0 .. kPlaceRanks] (one rank per thread; wsum: kPlaceThreads / 32 words).
+__device__ __forceinline__ void rank_word_prefix(const PlaceRanks& pr, uint32_t* pre,
+                                                 uint32_t* wsum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t v = pr.id[threadIdx.x] == ~0u ? 0u : rect_words(pr.rect[threadIdx.x]);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += o;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  uint32_t carry = 0;
+  for (int w = 0; w < warp; ++w) carry += wsum[w];
+  pre[threadIdx.x + 1] = carry + v;
+  if (threadIdx.x == 0) pre[0] = 0u;
+  __syncthreads();
+}
+
+// The rank i of word k of the block: pre[i] <= k < pre[i + 1].
+__device__ __forceinline__ int word_rank(const uint32_t* pre, uint32_t k) {
+  int i = 0;
+#pragma unroll
+  for (int step = kPlaceRanks / 2; step > 0; step >>= 1)
+    if (pre[i + step] <= k) i += step;
+  return i;
+}
+
+// Decision word w (rectangle tiles 32 w .. 32 w + 31) of a staged surfel,
+// called by a whole warp with the same arguments: the word k_tile_count
+// stored when it fitted, else the same tests again (lane b tests tile
+// 32 w + b).  Lane b also gets the index of its tile in *tile.
+__device__ __forceinline__ uint32_t rect_word_warp(const DevCam& c, uint32_t id, uint2 rc,
+                                                   uint32_t off,
+                                                   const uint32_t* __restrict__ mwords,
+                                                   uint32_t cap_words,
+                                                   const float4* __restrict__ conic, int w,
+                                                   int lane, int* tile) {
+  const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
+  const int k = 32 * w + lane;
+  const int2 t2 = rect_tile(k, nx, 1.f / (float)nx);
+  *tile = (ty0 + t2.y) * c.tiles_x + tx0 + t2.x;
+  const uint32_t words = (uint32_t)(nt + 31) / 32;
+  if (off <= cap_words && words <= cap_words - off) return mwords[off + w];
+  const bool hit = k < nt && tile_may_hit(load_conic(conic, id), tx0 + t2.x, ty0 + t2.y, c.W, c.H);
+  return __ballot_sync(0xffffffffu, hit);
+}
+
+__global__ void __launch_bounds__(kPlaceThreads) k_place_count(
+    const DevCam c, int N, int n_tiles, const uint32_t* __restrict__ did,
+    const uint2* __restrict__ rect, const float4* __restrict__ conic,
+    const uint32_t* __restrict__ count, const uint32_t* __restrict__ moff,
+    const uint32_t* __restrict__ mwords, uint32_t cap_words, uint32_t* __restrict__ M) {
+  extern __shared__ __align__(16) unsigned char s_count_smem[];
+  __shared__ uint32_t s_pre[kPlaceRanks + 1];  // decision words per rank, exclusive prefix
+  __shared__ uint32_t s_wsum[kPlaceThreads / 32];
+  const long long r0 = (long long)blockIdx.x * kPlaceRanks;
+  const PlaceRanks pr = stage_ranks(s_count_smem, r0, N, did, rect, count, moff);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_count_smem + kPlaceStageBytes);
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) s_cnt[t] = 0u;
+  __syncthreads();
+  rank_word_prefix(pr, s_pre, s_wsum);
+  // every (rank, decision word) pair of the block, spread over the threads
+  const uint32_t n_items = s_pre[kPlaceRanks];
+  for (uint32_t k = threadIdx.x; k < n_items; k += blockDim.x) {
+    const int i = word_rank(s_pre, k);
+    const int w = (int)(k - s_pre[i]);
+    const uint2 rc = pr.rect[i];
+    const uint32_t m = rect_word(c, pr.id[i], rc, pr.off[i], mwords, cap_words, conic, w);
+    for_word_tiles(c, rc, m, w, [&](int t) { atomicAdd(&s_cnt[t], 1u); });
+  }
+  __syncthreads();
+  uint32_t* row = M + (size_t)blockIdx.x * n_tiles;
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) row[t] = s_cnt[t];
+}
+
+// Per tile (one thread each): exclusive prefix of the counts over the rank
+// blocks, in place, and the tile's total.
+__global__ void __launch_bounds__(256) k_place_colscan(uint32_t* __restrict__ M, int nb,
+                                                       int n_tiles, uint32_t* __restrict__ tot) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  uint32_t run = 0;
+  int b = 0;
+  for (; b + 8 <= nb; b += 8) {  // eight independent loads in flight
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = M[(size_t)(b + k) * n_tiles + t];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      M[(size_t)(b + k) * n_tiles + t] = run;
+      run += v[k];
+    }
+  }
+  for (; b < nb; ++b) {
+    const uint32_t v = M[(size_t)b * n_tiles + t];
+    M[(size_t)b * n_tiles + t] = run;
+    run += v;
+  }
+  tot[t] = run;
+}
+
+// Tile ranges from the exclusive starts; a total above the key buffer's
+// capacity (instances dropped) is flagged and the ranges are clamped to it.
+__global__ void k_place_ranges(int n_tiles, const uint32_t* __restrict__ start,
+                               const uint32_t* __restrict__ total, uint32_t cap,
+                               uint2* __restrict__ ranges, int* __restrict__ status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  const uint32_t all = *total;
+  if (t == 0 && all > cap && status) atomicOr(status, kStatusCapacity);
+  const uint32_t a = start[t], e = t + 1 < n_tiles ? start[t + 1] : all;
+  ranges[t] = make_uint2(min(a, cap), min(e, cap));
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kPlaceThreads) k_place_write(
+    const DevCam c, int N, int n_tiles, int rank_bits, const uint32_t* __restrict__ did,
+    const uint2* __restrict__ rect, const float4* __restrict__ conic,
+    const uint32_t* __restrict__ count, const uint32_t* __restrict__ moff,
+    const uint32_t* __restrict__ mwords, uint32_t cap_words, const uint32_t* __restrict__ M,
+    const uint32_t* __restrict__ start, KeyT* __restrict__ keys, uint32_t cap) {
+  extern __shared__ __align__(16) unsigned char s_write_smem[];
+  __shared__ uint32_t s_pre[kPlaceRanks + 1];  // decision words per rank, exclusive prefix
+  __shared__ uint32_t s_wsum[kPlaceThreads / 32];
+  const long long r0 = (long long)blockIdx.x * kPlaceRanks;
+  const PlaceRanks pr = stage_ranks(s_write_smem, r0, N, did, rect, count, moff);
+  // the block's first kPlaceStageWords decision words and their ranks
+  uint32_t* s_word = reinterpret_cast<uint32_t*>(s_write_smem + kPlaceStageBytes);
+  uint16_t* s_wrank = reinterpret_cast<uint16_t*>(s_word + kPlaceStageWords);
+  // ranks 0-31 and 32-63 of the current group covering each tile, and each
+  // tile's next slot
+  uint32_t* s_lo = reinterpret_cast<uint32_t*>(s_wrank + kPlaceStageWords);
+  uint32_t* s_hi = s_lo + n_tiles;
+  uint32_t* s_base = s_hi + n_tiles;
+  const uint32_t* row = M + (size_t)blockIdx.x * n_tiles;
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    s_base[t] = start[t] + row[t];
+    s_lo[t] = 0u;
+    s_hi[t] = 0u;
+  }
+  __syncthreads();
+  rank_word_prefix(pr, s_pre, s_wsum);
+  const uint32_t n_items = s_pre[kPlaceRanks];
+  for (uint32_t k = threadIdx.x; k < min(n_items, (uint32_t)kPlaceStageWords); k += blockDim.x) {
+    const int i = word_rank(s_pre, k);
+    s_word[k] = rect_word(c, pr.id[i], pr.rect[i], pr.off[i], mwords, cap_words, conic,
+                          (int)(k - s_pre[i]));
+    s_wrank[k] = (uint16_t)i;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int g = 0; g < kPlaceRanks; g += 64) {
+    if (r0 + g >= N) break;  // block-uniform
+    // the group's decision words, one warp per word and one lane per tile:
+    // first which ranks cover each tile, then every instance's slot (the
+    // tile's base plus the group's lower ranks that cover it)
+    const uint32_t k0 = s_pre[g], k1 = s_pre[g + 64];
+    for (int pass = 0; pass < 2; ++pass) {
+      for (uint32_t k = k0 + warp; k < k1; k += kPlaceThreads / 32) {  // warp-uniform
+        int i, t;
+        uint32_t m;
+        if (k < (uint32_t)kPlaceStageWords) {
+          i = s_wrank[k];
+          const uint2 rc = pr.rect[i];
+          const int tx0 = rc.x & 0xFFFF, ty0 = rc.y & 0xFFFF, nx = (rc.x >> 16) - tx0 + 1;
+          const int2 t2 = rect_tile(32 * (int)(k - s_pre[i]) + lane, nx, 1.f / (float)nx);
+          t = (ty0 + t2.y) * c.tiles_x + tx0 + t2.x;
+          m = s_word[k];
+        } else {
+          i = word_rank(s_pre, k);
+          m = rect_word_warp(c, pr.id[i], pr.rect[i], pr.off[i], mwords, cap_words, conic,
+                             (int)(k - s_pre[i]), lane, &t);
+        }
+        if (((m >> lane) & 1u) == 0u) continue;
+        const int gi = i - g;  // rank within the group, 0 .. 63
+        if (pass == 0) {
+          if (gi < 32) atomicOr(&s_lo[t], 1u << gi);
+          else atomicOr(&s_hi[t], 1u << (gi - 32));
+        } else {
+          const uint32_t lower = gi < 32 ? (uint32_t)__popc(s_lo[t] & ((1u << gi) - 1u))
+                                         : (uint32_t)__popc(s_lo[t]) +
+                                               (uint32_t)__popc(s_hi[t] & ((1u << (gi - 32)) - 1u));
+          const uint32_t at = s_base[t] + lower;
+          if (at < cap) keys[at] = ((KeyT)t << rank_bits) | (KeyT)(r0 + i);
+        }
+      }
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+      s_base[t] += (uint32_t)(__popc(s_lo[t]) + __popc(s_hi[t]));
+      s_lo[t] = 0u;
+      s_hi[t] = 0u;
+    }
+    __syncthreads();
+  }
 }
 
 template <typename KeyT>
@@ -729,11 +1051,27 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  uint32_t* moff = nullptr;
+  if (L.place_ok) {
+    // offsets of the stored tile decisions (one word per 32 rectangle tiles)
+    moff = (uint32_t*)(ws + L.mword_off);
+    {
+      NEXEL_PROF("mask_words", st);
+      k_mask_words<<<(N + 255) / 256, 256, 0, st>>>(N, (const uint2*)(ws + L.rect),
+                                                    (const uint32_t*)(ws + L.count), moff);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = excl_scan(moff, N, (uint32_t*)(ws + L.scan_sums),
+                    (uint32_t*)(ws + L.counters + kCountersMaskWords), st);
+    if (e != cudaSuccess) return e;
+  }
   {
     NEXEL_PROF("tile_count", st);
     k_tile_count<<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, st>>>(
         c, N, (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint4*)(ws + L.tmask),
-        (uint32_t*)(ws + L.count));
+        (uint32_t*)(ws + L.count), moff, moff ? (uint32_t*)(ws + L.mwords) : nullptr,
+        (uint32_t)L.mword_cap);
   }
   return cudaGetLastError();
 }
@@ -764,6 +1102,63 @@ cudaError_t launch_count_scan(int N, char* ws, const WsLayout& L, cudaStream_t s
   }
   uint32_t* counters = (uint32_t*)(ws + L.counters);
   return excl_scan((uint32_t*)(ws + L.offs), N, (uint32_t*)(ws + L.scan_sums), counters + 1, st);
+}
+
+// Direct placement (32-bit keys, at most kPlaceMaxTiles tiles): the
+// instances land in inst0 in their final order; no sort passes.
+static cudaError_t binning_place(const DevCam& c, int N, char* ws, const WsLayout& L,
+                                 cudaStream_t st) {
+  const int n_tiles = L.n_tiles;
+  uint32_t* M = (uint32_t*)(ws + L.place);
+  uint32_t* tstart = (uint32_t*)(ws + L.place_tiles);
+  uint32_t* total = (uint32_t*)(ws + L.counters + kCountersPlaced);
+  const unsigned nb = (unsigned)((N + kPlaceRanks - 1) / kPlaceRanks);
+  const uint32_t cap = (uint32_t)std::min<long long>(L.cap, 0xFFFFFFFFLL);
+  const uint32_t* did = (const uint32_t*)(ws + L.did0);
+  const uint2* rect = (const uint2*)(ws + L.rect);
+  const float4* conic = (const float4*)(ws + L.conic);
+  const uint32_t* count = (const uint32_t*)(ws + L.count);
+  const uint32_t* moff = (const uint32_t*)(ws + L.mword_off);
+  const uint32_t* mwords = (const uint32_t*)(ws + L.mwords);
+  const uint32_t cap_words = (uint32_t)L.mword_cap;
+  cudaError_t e = cudaSuccess;
+  const size_t smem_count = kPlaceStageBytes + (size_t)n_tiles * 4;
+  const size_t smem_write =
+      kPlaceStageBytes + (size_t)kPlaceStageWords * 6 + (size_t)n_tiles * 12;
+  if (N > 0) e = cudaFuncSetAttribute(k_place_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_count);
+  if (e == cudaSuccess && N > 0) {
+    NEXEL_PROF("place_count", st);
+    k_place_count<<<nb, kPlaceThreads, smem_count, st>>>(c, N, n_tiles, did, rect, conic, count,
+                                                         moff, mwords, cap_words, M);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && N > 0) {
+    NEXEL_PROF("place_colscan", st);
+    k_place_colscan<<<(n_tiles + 255) / 256, 256, 0, st>>>(M, (int)nb, n_tiles, tstart);
+    e = cudaGetLastError();
+  } else if (e == cudaSuccess) {
+    e = cudaMemsetAsync(tstart, 0, (size_t)n_tiles * 4, st);
+  }
+  if (e == cudaSuccess) e = excl_scan(tstart, n_tiles, (uint32_t*)(ws + L.scan_sums), total, st);
+  if (e == cudaSuccess) {
+    NEXEL_PROF("tile_ranges", st);
+    k_place_ranges<<<(n_tiles + 255) / 256, 256, 0, st>>>(
+        n_tiles, tstart, total, cap, (uint2*)(ws + L.ranges),
+        (int*)(ws + L.counters + kStatusOffset));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && N > 0)
+    e = cudaFuncSetAttribute(k_place_write<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_write);
+  if (e == cudaSuccess && N > 0) {
+    NEXEL_PROF("place_write", st);
+    k_place_write<uint32_t><<<nb, kPlaceThreads, smem_write, st>>>(
+        c, N, n_tiles, L.rank_bits, did, rect, conic, count, moff, mwords, cap_words, M, tstart,
+        (uint32_t*)(ws + L.inst0), cap);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 template <typename KeyT>
@@ -808,6 +1203,7 @@ static cudaError_t binning_t(const DevCam& c, int N, long long n_inst, char* ws,
 
 cudaError_t launch_binning(const DevCam& c, int N, long long n_inst, char* ws, const WsLayout& L,
                            cudaStream_t st) {
+  if (L.place_ok) return binning_place(c, N, ws, L, st);
   if (L.key64) return binning_t<unsigned long long>(c, N, n_inst, ws, L, st);
   return binning_t<uint32_t>(c, N, n_inst, ws, L, st);
 }

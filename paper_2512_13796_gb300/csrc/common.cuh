@@ -22,6 +22,14 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;                        // instance (tile) sort
 constexpr int kSortItemsDepth = 4;                    // depth sort of the surfels
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per sort block
+// direct placement of the instances by tile (32-bit keys only): ranks per
+// block, and the largest tile count (two shared-memory words per tile)
+constexpr int kPlaceRanks = 1024;
+constexpr int kPlaceThreads = 1024;  // one rank per thread when staging
+constexpr int kPlaceMaxTiles = 8192;
+// stored tile decisions: room for this many words (32 rectangle tiles each)
+// per surfel on average; surfels past the room are tested again
+constexpr int kMaskWordsPerSurfel = 8;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = 256 * kScanItems;
 
@@ -182,6 +190,8 @@ constexpr int kStatusTimeout = 1;
 constexpr int kStatusCapacity = 2;
 // counters region: [0] unused, [1] instance count, [8] status word
 constexpr size_t kCountersInst = 4;
+constexpr size_t kCountersPlaced = 8;  // instances placed by the direct tile placement
+constexpr size_t kCountersMaskWords = 12;  // stored tile-decision words wanted
 constexpr size_t kStatusOffset = 32;
 constexpr size_t kStatsOffset = 64;  // 5 x u64 of nexel_render_stats
 
@@ -195,8 +205,11 @@ struct WsLayout {
       shj,
       offs,
       ranges, n_contrib,
-      grad_sorted, counters, fixed_end, inst0, inst1, hist, scan_sums, total;
+      grad_sorted, counters, place, place_tiles, mword_off, mwords, fixed_end, inst0, inst1, hist,
+      scan_sums, total;
+  long long mword_cap;  // words of room in mwords
   int N, P, K, n_tiles, tile_bits, rank_bits, key64, tile_passes;
+  int place_ok;  // the instances are placed by tile directly (no tile sort)
   long long cap;
 };
 // Backward scratch (per sample): dL/dW_j, dL/dD_j, the field features and
