@@ -1,15 +1,16 @@
-// Surfel preprocess, tile binning and the two stable radix sorts (centre
-// depth, then tile), plus the preprocess backward.
+// Surfel preprocess, tile binning (the stable radix sort of the centre
+// depths, then the per-tile lists), plus the preprocess backward.
 //
 // Ordering (Sec. 3, "Preliminaries"): surfels are sorted by the view depth of
 // their centres and composited per tile.  Instead of sorting 64-bit
 // (tile, depth) keys of every (tile, surfel) instance, the N surfels are
-// first sorted by depth (32-bit float keys, index order on ties), the
-// instances are then emitted in depth-rank order, and a stable sort on the
-// tile bits alone finishes the job.  The resulting per-tile lists are
-// identical, bit for bit, to a stable sort of (tile << 32 | depth bits) keys,
-// at a fraction of the key traffic: a key is (tile << rank_bits | rank) in
-// 32 bits whenever tile_bits + rank_bits <= 32.
+// first sorted by depth (32-bit float keys, index order on ties).  The
+// instances are then placed directly at their slots in the per-tile lists
+// (32-bit keys, at most kPlaceMaxTiles tiles), or emitted in depth-rank order
+// and stably sorted on the tile bits alone.  Either way the per-tile lists
+// are identical, bit for bit, to a stable sort of (tile << 32 | depth bits)
+// keys.  A key is (tile << rank_bits | rank), in 32 bits whenever
+// tile_bits + rank_bits <= 32.
 #include "common.cuh"
 
 #include <algorithm>
@@ -720,11 +721,12 @@ __global__ void k_mask_words(int N, const uint2* __restrict__ rect,
 // instances per tile (shared-memory counters), k_place_colscan turns the
 // [block][tile] counts into per-tile exclusive prefixes over the blocks and
 // per-tile totals, whose exclusive scan gives start(t).  k_place_write then
-// walks its block in groups of 32 ranks: a 32-bit mask per tile records
+// walks its block in groups of 64 ranks: two 32-bit masks per tile record
 // which ranks of the group cover the tile, so an instance's place within
 // the group is a popcount of the lower bits, and the group's counts advance
 // the tile's running base.  The result is the same sequence as the stable
-// sort, bit for bit.
+// sort, bit for bit.  Both kernels read the tile decisions k_tile_count
+// stored (one word per 32 rectangle tiles), so the tile test runs once.
 
 // The block's kPlaceRanks ranks staged in shared memory (tile rectangle,
 // surfel id or ~0 when the surfel has no instance, offset of its decision
