@@ -409,3 +409,61 @@ def test_render_stats(dev, idx):
         ref = oracle.render(w.scene, cam, w.settings, w.field)
         assert s["pairs_to_last"] >= int(ref["n_contrib"].sum())
     print(f"\n[stats config{idx}] {s}")
+
+
+def _instance_order_checked(dev, scene, cam, st, field):
+    """Forward through the C ABI, then the binned (tile, id, depth) sequence:
+    a stable (tile, centre depth, id) order with every surfel at most once
+    per tile.  Returns the forward outputs."""
+    import torch
+    from paper_2512_13796_gb300 import _native as N_
+    from paper_2512_13796_gb300 import render as R
+    fw, _, ws = run_gpu(scene, cam, st, field, dev)
+    n = fw["n_instances"]
+    assert n > 0
+    tiles = torch.empty(n, dtype=torch.int32, device=dev)
+    ids = torch.empty(n, dtype=torch.int32, device=dev)
+    dep = torch.empty(n, dtype=torch.float32, device=dev)
+    N_.nexel_instance_list(R.camera_struct(cam), scene.n, ws.ws.data_ptr(), ws.ws.numel(), n,
+                           tiles.data_ptr(), ids.data_ptr(), dep.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    t, i, d = tiles.cpu().numpy(), ids.cpu().numpy(), dep.cpu().numpy()
+    order = np.lexsort((i, d.view(np.uint32), t))
+    assert np.array_equal(order, np.arange(n)), "instance list is not (tile, depth, id) sorted"
+    key = t.astype(np.int64) * (scene.n + 1) + i
+    assert np.unique(key).size == n
+    return fw
+
+
+def test_tile_sort_path_beyond_placement_tiles(dev):
+    """An image of more than 8192 16x16 tiles (1600 x 1400: 8800 tiles) with
+    32-bit keys bins through the emit-and-sort path (the LSD tile sort): the
+    order is the stable one and the forward matches the oracle."""
+    scene = synth.make_scene(2000, 3, 41, gamma="var")
+    cam = synth.front_camera(1600, 1400)
+    st = synth.Settings(K=2)
+    field = synth.make_field(4, 12, 2, (16,), 3)
+    fw = _instance_order_checked(dev, scene, cam, st, field)
+    pix = synth.pixel_sample(cam, 2048, 2, seed=3)
+    ref = oracle.render(scene, cam, st, field, pix, tie_tol=TIE, cell_tol=CELL, relu_tol=RELU)
+    _report("tile-sort path fwd", compare_forward(fw, ref, st.K, TOL_F32))
+
+
+def test_placement_with_tile_decisions_tested_again(dev):
+    """Surfels so large on screen that their stored tile decisions overflow
+    the room of 8 words per surfel (up to 113 words each on a 1280 x 720
+    view): the later ones are tested again during the direct placement, and
+    the order and the forward still match."""
+    import dataclasses
+    base = synth.make_scene(300, 2, 43, gamma="one")
+    scene = dataclasses.replace(base, scale=(base.scale * 8.0).astype(np.float32))
+    cam = synth.front_camera(1280, 720)
+    st = synth.Settings(K=2)
+    field = synth.make_field(4, 12, 2, (16,), 3)
+    fw = _instance_order_checked(dev, scene, cam, st, field)
+    # far more decision words than the room holds: ~3600 tiles per surfel
+    assert fw["n_instances"] > 300 * 8 * 32
+    pix = synth.pixel_sample(cam, 2048, 2, seed=4)
+    ref = oracle.render(scene, cam, st, field, pix, tie_tol=TIE, cell_tol=CELL, relu_tol=RELU)
+    _report("placement with re-tested tiles fwd", compare_forward(fw, ref, st.K, TOL_F32))
