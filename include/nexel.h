@@ -150,8 +150,10 @@ int nexel_bwd_workspace_size(const nexel_camera* cam, const nexel_settings* sett
  * per surfel the camera-space frame, the exact screen footprint of the
  * region where alpha >= alpha_min, the tiles it touches; then a stable radix
  * sort of surfels by centre depth (culled: centre depth <= near or
- * opacity < alpha_min) and a stable radix sort of (tile, depth-rank)
- * instances by tile, bit-exact.  Results stay in `ws`.  Writes the number of
+ * opacity < alpha_min) and the per-tile lists of (tile, depth-rank)
+ * instances in rank order, bit-exact (each instance placed directly at its
+ * slot, or, for 64-bit keys or more than 8192 tiles, a stable radix sort of
+ * the instances by tile).  Results stay in `ws`.  Writes the number of
  * instances to *n_instances_out (host); returns NEXEL_ERR_CAPACITY, without
  * binning, if it exceeds the capacity `ws` was sized for. */
 int nexel_preprocess(const nexel_camera* cam, const nexel_settings* settings, int N,
