@@ -142,3 +142,21 @@ def test_tuning_round_trip_and_checks(lib):
     best = N_.Tuning()
     assert lib.nexel_autotune(None, None, None, 0, *([None] * 6), None, 0, None, 0, *([None] * 7),
                               None, *([None] * 8), 0, None, 0, C.byref(best), None, None) == -1
+
+
+def test_stats_and_reduction_probe_check_arguments(lib):
+    """nexel_render_stats and nexel_peak_l2_reductions reject bad arguments
+    before any CUDA call (the fake device pointers are never used)."""
+    cam = R.camera_struct(synth.front_camera(64, 64))
+    st = R.settings_struct(synth.Settings(K=2))
+    out = (C.c_longlong * 7)()
+    assert lib.nexel_render_stats(C.byref(cam), C.byref(st), 10, None, 1 << 20, out, None) == -1
+    assert lib.nexel_render_stats(C.byref(cam), C.byref(st), 10, 4096, 1 << 20, None, None) == -1
+    assert lib.nexel_render_stats(C.byref(cam), C.byref(st), -1, 4096, 1 << 20, out, None) == -1
+    g = C.c_float(0.0)
+    assert lib.nexel_peak_l2_reductions(None, 1 << 20, 1000, 1, C.byref(g), None) == -1
+    assert lib.nexel_peak_l2_reductions(4096, 1 << 20, 1000, 0, C.byref(g), None) == -1  # reps
+    assert lib.nexel_peak_l2_reductions(4096, 1 << 20, 0, 1, C.byref(g), None) == -1  # no ops
+    assert lib.nexel_peak_l2_reductions(4100, 1 << 20, 1000, 1, C.byref(g), None) == -1  # alignment
+    assert lib.nexel_peak_l2_reductions(4096, 4, 1000, 1, C.byref(g), None) == -1  # < one entry
+    assert lib.nexel_peak_l2_reductions(4096, 1 << 20, 1000, 1, None, None) == -1
