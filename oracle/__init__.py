@@ -67,7 +67,7 @@ class OSet(C.Structure):
     _fields_ = [("K", C.c_int), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
                 ("T_min", C.c_double), ("bg", C.c_double * 3), ("tie_tol", C.c_double),
                 ("order_tol", C.c_double), ("cell_tol", C.c_double),
-                ("relu_tol", C.c_double)]
+                ("relu_tol", C.c_double), ("edge_tol", C.c_double)]
 
 
 class OField(C.Structure):
@@ -107,7 +107,7 @@ def _cam(cam) -> OCam:
     return c
 
 
-def _set(st, tie_tol, order_tol=1e-6, cell_tol=0.0, relu_tol=0.0) -> OSet:
+def _set(st, tie_tol, order_tol=1e-6, cell_tol=0.0, relu_tol=0.0, edge_tol=0.0) -> OSet:
     s = OSet()
     s.K = int(st.K)
     s.alpha_min, s.alpha_max, s.T_min = float(st.alpha_min), float(st.alpha_max), float(st.T_min)
@@ -117,17 +117,19 @@ def _set(st, tie_tol, order_tol=1e-6, cell_tol=0.0, relu_tol=0.0) -> OSet:
     s.order_tol = float(min(order_tol, tie_tol)) if tie_tol > 0 else 0.0
     s.cell_tol = float(cell_tol)
     s.relu_tol = float(relu_tol)
+    s.edge_tol = float(edge_tol)
     return s
 
 
 class _FieldRef:
     """Keeps the float64 copies alive while the C struct points at them."""
 
-    def __init__(self, field, table=None):
+    def __init__(self, field, table=None, weights=None):
         self.scale = _d(field.level_scale)
         self.table = _d(field.table if table is None else table)
         self.widths = np.ascontiguousarray(np.asarray(field.widths, np.int32))
-        self.weights = _d(np.concatenate([np.asarray(w, np.float64).ravel() for w in field.weights]))
+        wl = field.weights if weights is None else weights
+        self.weights = _d(np.concatenate([np.asarray(w, np.float64).ravel() for w in wl]))
         self.n_mlp = self.weights.size
         self.s = OField()
         self.s.L, self.s.T, self.s.F = int(field.L), int(field.T), int(field.F)
@@ -147,14 +149,16 @@ def all_pixels(cam) -> np.ndarray:
     return np.arange(cam.width * cam.height, dtype=np.int32)
 
 
-TIE_BITS = {1: "topk", 2: "alpha", 4: "T_min", 8: "near", 16: "order", 32: "cell", 64: "relu"}
+TIE_BITS = {1: "topk", 2: "alpha", 4: "T_min", 8: "near", 16: "order", 32: "cell", 64: "relu",
+            128: "edge"}
 
 
 def render(scene, cam, settings, field=None, pixels=None, tie_tol: float = 1e-6,
            table=None, order_tol: float = 1e-6, cell_tol: float = 0.0,
-           relu_tol: float = 0.0) -> dict:
-    """Forward of the listed pixels.  ``table`` overrides field.table (e.g.
-    the fp16-rounded copy the reduced-precision path reads).  A pixel is
+           relu_tol: float = 0.0, weights=None, edge_tol: float = 1e-6) -> dict:
+    """Forward of the listed pixels.  ``table`` overrides field.table and
+    ``weights`` field.weights (e.g. the FP16-rounded table and the
+    BF16-rounded weights a reduced-precision path reads).  A pixel is
     flagged in ``tie`` when one of its discrete choices lies within tie_tol
     (relative) of flipping: top-K weight ties (bit 1), alpha at alpha_min or
     alpha_max (2), T(1 - alpha) at T_min (4), t* at the near plane (8), or,
@@ -163,21 +167,26 @@ def render(scene, cam, settings, field=None, pixels=None, tie_tol: float = 1e-6,
     cell_tol (world units) of a hash-cell face of some level (32), where the
     trilinear interpolation has a kink; and, when relu_tol > 0, a textured
     sample with a hidden MLP pre-activation within relu_tol (relative to the
-    sum of the magnitudes of its terms) of zero (64), a ReLU kink."""
+    sum of the magnitudes of its terms) of zero (64), a ReLU kink; and a
+    composited surfel whose edge-on measure |d_mu . n_c| lies within
+    edge_tol of the edge-on threshold (128).  ``tie_slot`` [n, K] holds the
+    kink bits (32, 64) of each slot's own sample."""
     L = lib()
     pix = all_pixels(cam) if pixels is None else np.ascontiguousarray(pixels, np.int32)
     n, K = pix.size, settings.K
     out = dict(image=np.zeros((n, 3)), notex=np.zeros((n, 3)), weights=np.zeros((n, K)),
                ids=np.zeros((n, K), np.int32), depths=np.zeros((n, K)),
                textures=np.zeros((n, K, 3)), T_final=np.zeros(n),
-               n_contrib=np.zeros(n, np.int32), tie=np.zeros(n, np.int32))
-    fr = _FieldRef(field, table) if field is not None else None
+               n_contrib=np.zeros(n, np.int32), tie=np.zeros(n, np.int32),
+               tie_slot=np.zeros((n, K), np.int32))
+    fr = _FieldRef(field, table, weights) if field is not None else None
     sv = _surfels(scene)
-    c, s = _cam(cam), _set(settings, tie_tol, order_tol, cell_tol, relu_tol)
+    c, s = _cam(cam), _set(settings, tie_tol, order_tol, cell_tol, relu_tol, edge_tol)
     rc = L.oracle_render(C.byref(c), C.byref(s), C.byref(fr.s) if fr else None,
                          C.c_int(scene.n), *[_p(a) for a in sv], C.c_int(n), _p(pix),
                          *[_p(out[k]) for k in ("image", "notex", "weights", "ids", "depths",
-                                                "textures", "T_final", "n_contrib", "tie")])
+                                                "textures", "T_final", "n_contrib", "tie",
+                                                "tie_slot")])
     if rc != 0:
         raise ValueError(f"oracle_render failed ({rc})")
     out["pixels"] = pix
@@ -185,11 +194,16 @@ def render(scene, cam, settings, field=None, pixels=None, tie_tol: float = 1e-6,
 
 
 def render_bwd(scene, cam, settings, field, pixels, d_image, d_weights=None,
-               d_textures=None, table=None) -> dict:
+               d_textures=None, table=None, weights=None, absolute: bool = False) -> dict:
+    """Analytic FP64 gradient of the listed pixels' outputs (discrete
+    choices held fixed) for upstream d_image, d_weights, d_textures.  With
+    ``absolute`` every entry instead holds the sum of the magnitudes of its
+    contributions (per pixel and surfel, per sample and table corner, per
+    sample and MLP weight)."""
     L = lib()
     pix = np.ascontiguousarray(pixels, np.int32)
     n, N = pix.size, scene.n
-    fr = _FieldRef(field, table) if field is not None else None
+    fr = _FieldRef(field, table, weights) if field is not None else None
     sv = _surfels(scene)
     g = dict(mu=np.zeros((N, 3)), quat=np.zeros((N, 4)), scale=np.zeros((N, 2)),
              opacity=np.zeros(N), gamma=np.zeros((N, 2)), color=np.zeros((N, 3)))
@@ -205,7 +219,7 @@ def render_bwd(scene, cam, settings, field, pixels, d_image, d_weights=None,
                              _p(dI), _p(dW), _p(dT),
                              *[_p(g[k]) for k in ("mu", "quat", "scale", "opacity", "gamma",
                                                   "color")],
-                             _p(g.get("table")), _p(g.get("mlp")))
+                             _p(g.get("table")), _p(g.get("mlp")), C.c_int(int(absolute)))
     if rc != 0:
         raise ValueError(f"oracle_render_bwd failed ({rc})")
     if fr:
@@ -230,14 +244,18 @@ def render_sh(scene, coeffs, cam, settings, field=None, pixels=None, **kw) -> di
 
 
 def render_bwd_sh(scene, coeffs, cam, settings, field, pixels, d_image, d_weights=None,
-                  d_textures=None, table=None) -> dict:
+                  d_textures=None, table=None, weights=None, absolute: bool = False) -> dict:
     """render_bwd() for SH per-primitive colours: the colour gradient is
-    taken to the coefficients ([N, 16, 3]) and, through the direction, to mu."""
+    taken to the coefficients ([N, 16, 3]) and, through the direction, to mu.
+    With ``absolute`` it returns render_bwd's magnitudes at the evaluated
+    per-primitive colours (the table and MLP entries are the ones of use)."""
     from . import sh
     center = sh.camera_center(cam)
     rgb = sh.primitive_colors(scene.mu, coeffs, center)
     g = render_bwd(_with_colors(scene, rgb), cam, settings, field, pixels, d_image, d_weights,
-                   d_textures, table)
+                   d_textures, table, weights, absolute)
+    if absolute:
+        return g
     dc, dmu = sh.primitive_colors_bwd(scene.mu, coeffs, center, g["color"])
     g["color"] = dc
     g["mu"] = g["mu"] + dmu
@@ -305,6 +323,23 @@ def map_positive(k: int) -> int:
 
 def hash_index(kx: int, ky: int, kz: int, T: int) -> int:
     return int(lib().oracle_hash(int(kx), int(ky), int(kz), int(T)))
+
+
+def centre_ray_cosine(cam, scene) -> np.ndarray:
+    """|cos| of the angle between each surfel's normal and its centre ray
+    (camera centre -> mu): 0 for a surfel seen exactly edge-on.  A pixel ray
+    meets such a plane at a grazing angle, where t*, u and v are the ratios
+    of nearly cancelling terms: their derivatives amplify any rounding by
+    ~1 / |cos| (FP64 throughout)."""
+    M = np.asarray(cam.world_to_cam, np.float64)
+    R, t = M[:, :3], M[:, 3]
+    o = -R.T @ t
+    q = np.asarray(scene.quat, np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    n = np.stack([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)], 1)
+    d = np.asarray(scene.mu, np.float64) - o
+    return np.abs(np.sum(d * n, 1)) / np.linalg.norm(d, axis=1)
 
 
 def depth_order(cam, mu) -> np.ndarray:

@@ -50,6 +50,7 @@ struct OSet {
   double order_tol;  // relative width used to flag centre-depth order ties
   double cell_tol;   // world-space distance to a hash-cell face flagged as a kink
   double relu_tol;   // relative width used to flag hidden pre-activations near 0
+  double edge_tol;   // width of the band above the edge-on threshold flagged as a tie
 };
 
 struct OField {
@@ -148,13 +149,19 @@ void mlp_forward(const OField& fd, const double* in, std::vector<std::vector<dou
   }
 }
 
-// Backward of the MLP: g_out -> g_in, accumulating weight gradients.
+// Backward of the MLP: g_out -> g_in, accumulating weight gradients.  With
+// `absolute` every product is replaced by the product of magnitudes (the
+// ReLU masks kept): g_in and the weight gradients then hold the sums of the
+// magnitudes of the terms along every path, the scale of the rounding error
+// of an evaluation that rounds each layer's operands.
 void mlp_backward(const OField& fd, const std::vector<std::vector<double>>& acts,
-                  const double* g_out, double* g_in, double* d_weights) {
+                  const double* g_out, double* g_in, double* d_weights, bool absolute = false) {
   std::vector<size_t> off(fd.n_layers + 1, 0);
   for (int l = 0; l < fd.n_layers; ++l)
     off[l + 1] = off[l] + (size_t)fd.widths[l] * fd.widths[l + 1];
   std::vector<double> g(g_out, g_out + fd.widths[fd.n_layers]);
+  if (absolute)
+    for (double& v : g) v = std::fabs(v);
   for (int l = fd.n_layers - 1; l >= 0; --l) {
     int ni = fd.widths[l], no = fd.widths[l + 1];
     bool last = (l == fd.n_layers - 1);
@@ -165,8 +172,12 @@ void mlp_backward(const OField& fd, const std::vector<std::vector<double>>& acts
     std::vector<double> gi(ni, 0.0);
     for (int o = 0; o < no; ++o) {
       for (int i = 0; i < ni; ++i) {
-        if (d_weights) d_weights[off[l] + (size_t)o * ni + i] += g[o] * acts[l][i];
-        gi[i] += W[(size_t)o * ni + i] * g[o];
+        if (d_weights) {
+          const double c = g[o] * acts[l][i];
+          d_weights[off[l] + (size_t)o * ni + i] += absolute ? std::fabs(c) : c;
+        }
+        const double wv = W[(size_t)o * ni + i];
+        gi[i] += (absolute ? std::fabs(wv) : wv) * g[o];
       }
     }
     g.swap(gi);
@@ -263,12 +274,21 @@ inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1]
 // |a|^(2g) with |0|^(2g) = 0
 inline double powabs(double a, double g) { return a == 0.0 ? 0.0 : std::pow(std::fabs(a), 2.0 * g); }
 
+// A surfel whose plane contains (to within kEdgeOn) its own centre ray is
+// seen edge-on: its footprint on screen degenerates to a line through the
+// projected centre.  The paper is silent on this case; the reading culls it.
+// The test is |d_mu . n_c| < kEdgeOn with d_mu = mu_c / z_mu the centre ray
+// scaled to unit depth and n_c the camera-space normal.
+constexpr double kEdgeOn = 1e-7;
+enum { EDGE_NONE = 0, EDGE_BAND = 1, EDGE_CULLED = 2 };
+
 struct Scene {
   int N;
   const double *mu, *quat, *scale, *opac, *gamma, *color;
   std::vector<std::array<double, 9>> R;  // per-surfel rotation
   std::vector<int> order;                // sorted by centre depth, culled removed
   std::vector<double> zc;                // centre view depth
+  std::vector<unsigned char> edge;       // EDGE_* bits of the edge-on reading
 };
 
 void ray_of(const OCam& c, int px, int py, double o[3], double d[3]) {
@@ -280,13 +300,28 @@ void ray_of(const OCam& c, int px, int py, double o[3], double d[3]) {
   }
 }
 
-void prepare_scene(const OCam& c, Scene& s) {
+void prepare_scene(const OCam& c, const OSet* st, Scene& s) {
   s.R.resize(s.N);
   s.zc.resize(s.N);
+  s.edge.assign(s.N, EDGE_NONE);
+  const double band = st ? st->edge_tol : 0.0;
   for (int i = 0; i < s.N; ++i) {
     quat_to_rot(s.quat + 4 * i, s.R[i].data());
     const double* m = s.mu + 3 * i;
-    s.zc[i] = c.Rt[8] * m[0] + c.Rt[9] * m[1] + c.Rt[10] * m[2] + c.Rt[11];
+    double mc[3];
+    for (int a = 0; a < 3; ++a)
+      mc[a] = c.Rt[4 * a] * m[0] + c.Rt[4 * a + 1] * m[1] + c.Rt[4 * a + 2] * m[2] + c.Rt[4 * a + 3];
+    s.zc[i] = mc[2];
+    if (mc[2] > c.near_) {
+      // edge-on test: camera-space normal n_c = R_cam n against mu_c / z_mu
+      const double* R = s.R[i].data();
+      double nc[3];
+      for (int a = 0; a < 3; ++a)
+        nc[a] = c.Rt[4 * a] * R[2] + c.Rt[4 * a + 1] * R[5] + c.Rt[4 * a + 2] * R[8];
+      const double dn0 = (mc[0] * nc[0] + mc[1] * nc[1] + mc[2] * nc[2]) / mc[2];
+      if (std::fabs(dn0) < kEdgeOn) s.edge[i] |= EDGE_CULLED;
+      if (std::fabs(std::fabs(dn0) - kEdgeOn) <= band) s.edge[i] |= EDGE_BAND;
+    }
   }
   s.order.clear();
   for (int i = 0; i < s.N; ++i)
@@ -308,6 +343,7 @@ struct PixelResult {
   std::vector<int> sel;  // indices into list, slot order
   double T_final;
   int tie;
+  int slot_tie[8];  // kink bits (TIE_CELL, TIE_RELU) of each slot's sample
   double notex[3], image[3];
   double tex[8][3];
   std::vector<std::vector<std::vector<double>>> acts;  // per slot MLP activations
@@ -316,7 +352,7 @@ struct PixelResult {
 
 enum {
   TIE_TOPK = 1, TIE_ALPHA = 2, TIE_TMIN = 4, TIE_NEAR = 8, TIE_ORDER = 16, TIE_CELL = 32,
-  TIE_RELU = 64
+  TIE_RELU = 64, TIE_EDGE = 128
 };
 
 inline bool near_rel(double a, double b, double tol) {
@@ -356,6 +392,10 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
     if (near_rel(t, c.near_, tol)) r.tie |= TIE_NEAR;
     if (near_rel(a, st.alpha_min, tol)) r.tie |= TIE_ALPHA;
     if (a < st.alpha_min || a == 0.0) continue;
+    // a surfel near the edge-on threshold would be composited here: a
+    // lower-precision test of the threshold may keep or cull it
+    if (s.edge[i] & EDGE_BAND) r.tie |= TIE_EDGE;
+    if (s.edge[i] & EDGE_CULLED) continue;
     if (near_rel(a, st.alpha_max, tol)) r.tie |= TIE_ALPHA;
     double ac = std::min(a, st.alpha_max);
     double test = T * (1.0 - ac);
@@ -399,6 +439,7 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
   for (int ch = 0; ch < 3; ++ch) r.image[ch] = r.notex[ch] + r.T_final * st.bg[ch];
   r.acts.assign(r.sel.size(), {});
   r.lev.assign(r.sel.size(), {});
+  for (int j = 0; j < 8; ++j) r.slot_tie[j] = 0;
   for (size_t j = 0; j < r.sel.size(); ++j) {
     const Contrib& e = r.list[r.sel[j]];
     for (int ch = 0; ch < 3; ++ch) r.tex[j][ch] = 0.0;
@@ -412,7 +453,7 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
       for (int l = 0; l < fd->L; ++l)
         for (int a = 0; a < 3; ++a) {
           double g = fd->scale[l] * x[a];
-          if (std::fabs(g - std::nearbyint(g)) < st.cell_tol * fd->scale[l]) r.tie |= TIE_CELL;
+          if (std::fabs(g - std::nearbyint(g)) < st.cell_tol * fd->scale[l]) r.slot_tie[j] |= TIE_CELL;
         }
     std::vector<double> feat(fd->L * fd->F);
     field_features(*fd, c.fx, x, e.t, feat.data(), keep ? &r.lev[j] : nullptr);
@@ -434,20 +475,22 @@ void render_pixel(const OCam& c, const OSet& st, const OField* fd, const Scene& 
             a += term;
             mag += std::fabs(term);
           }
-          if (std::fabs(a) <= st.relu_tol * mag && mag > 0.0) r.tie |= TIE_RELU;
+          if (std::fabs(a) <= st.relu_tol * mag && mag > 0.0) r.slot_tie[j] |= TIE_RELU;
         }
         W += (size_t)no * ni;
       }
     }
+    r.tie |= r.slot_tie[j];
     if (keep) r.acts[j] = std::move(acts);
   }
 }
 
-Scene make_scene(const OCam& c, int N, const double* mu, const double* quat, const double* scale,
-                 const double* opac, const double* gamma, const double* color) {
+Scene make_scene(const OCam& c, const OSet* st, int N, const double* mu, const double* quat,
+                 const double* scale, const double* opac, const double* gamma,
+                 const double* color) {
   Scene s;
   s.N = N; s.mu = mu; s.quat = quat; s.scale = scale; s.opac = opac; s.gamma = gamma; s.color = color;
-  prepare_scene(c, s);
+  prepare_scene(c, st, s);
   return s;
 }
 
@@ -519,9 +562,9 @@ int oracle_render(const OCam* c, const OSet* st, const OField* fd, int N, const 
                   const double* quat, const double* scale, const double* opac,
                   const double* gamma, const double* color, int n_pix, const int* pix,
                   double* image, double* notex, double* weights, int* ids, double* depths,
-                  double* textures, double* T_final, int* n_contrib, int* tie) {
+                  double* textures, double* T_final, int* n_contrib, int* tie, int* slot_tie) {
   if (st->K < 0 || st->K > 8) return -1;
-  Scene s = make_scene(*c, N, mu, quat, scale, opac, gamma, color);
+  Scene s = make_scene(*c, st, N, mu, quat, scale, opac, gamma, color);
   int K = st->K;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int p = 0; p < n_pix; ++p) {
@@ -537,6 +580,7 @@ int oracle_render(const OCam* c, const OSet* st, const OField* fd, int N, const 
       if (weights) weights[(size_t)p * K + j] = has ? e->w : 0.0;
       if (ids) ids[(size_t)p * K + j] = has ? e->id : -1;
       if (depths) depths[(size_t)p * K + j] = has ? e->t : 0.0;
+      if (slot_tie) slot_tie[(size_t)p * K + j] = has ? r.slot_tie[j] : 0;
       for (int ch = 0; ch < 3; ++ch)
         if (textures) textures[((size_t)p * K + j) * 3 + ch] = has ? r.tex[j][ch] : 0.0;
     }
@@ -557,7 +601,7 @@ int oracle_render_procedural(const OCam* c, const OSet* st, int N, const double*
                              const double* gamma, double freq, int n_pix, const int* pix,
                              double* image) {
   std::vector<double> dummy(3 * (size_t)std::max(N, 1), 0.0);
-  Scene s = make_scene(*c, N, mu, quat, scale, opac, gamma, dummy.data());
+  Scene s = make_scene(*c, st, N, mu, quat, scale, opac, gamma, dummy.data());
   OSet st0 = *st;
   st0.K = 0;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -577,11 +621,6 @@ int oracle_render_procedural(const OCam* c, const OSet* st, int N, const double*
   return 0;
 }
 
-// Backward of the listed pixels' outputs.  Upstream gradients:
-//   d_image [n_pix][3] (required), d_weights [n_pix][K] and
-//   d_textures [n_pix][K][3] (each may be null).
-// Gradient outputs are OVERWRITTEN (zeroed first); any may be null.
-// d_table is [L][T][F], d_mlp is packed like the weights.
 // Blended L1 error of every surfel (supp. Sec. 7.2, "Densification": the
 // per-primitive error of Rota Bulo et al.): err[i] += sum over the listed
 // pixels of w_ip e_p, with w_ip = alpha T the compositing weight of surfel i
@@ -591,7 +630,7 @@ int oracle_blend_error(const OCam* c, const OSet* st, int N, const double* mu, c
                        const double* scale, const double* opac, const double* gamma,
                        const double* color, int n_pix, const int* pix, const double* e_pix,
                        double* err) {
-  Scene s = make_scene(*c, N, mu, quat, scale, opac, gamma, color);
+  Scene s = make_scene(*c, st, N, mu, quat, scale, opac, gamma, color);
   std::vector<std::vector<std::pair<int, double>>> acc(n_pix);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int p = 0; p < n_pix; ++p) {
@@ -604,14 +643,30 @@ int oracle_blend_error(const OCam* c, const OSet* st, int N, const double* mu, c
   return 0;
 }
 
+// Backward of the listed pixels' outputs.  Upstream gradients:
+//   d_image [n_pix][3] (required), d_weights [n_pix][K] and
+//   d_textures [n_pix][K][3] (each may be null).
+// Gradient outputs are OVERWRITTEN (zeroed first); any may be null.
+// d_table is [L][T][F], d_mlp is packed like the weights.  With absolute
+// != 0 the texture path is evaluated on magnitudes -- every product through
+// the MLP backward, the trilinear weights and the positional gradient taken
+// as the product of magnitudes, every sum as a sum of magnitudes -- and every
+// contribution is added as its magnitude: each table and MLP entry then
+// holds the sum of the magnitudes of all the terms that reach it (and each
+// surfel entry the sum over pixels of |its per-pixel contribution|), the
+// scale against which the rounding error of an evaluation that rounds the
+// MLP's operands is bounded.
 int oracle_render_bwd(const OCam* c, const OSet* st, const OField* fd, int N, const double* mu,
                       const double* quat, const double* scale, const double* opac,
                       const double* gamma, const double* color, int n_pix, const int* pix,
                       const double* d_image, const double* d_weights, const double* d_textures,
                       double* d_mu, double* d_quat, double* d_scale, double* d_opac,
-                      double* d_gamma, double* d_color, double* d_table, double* d_mlp) {
+                      double* d_gamma, double* d_color, double* d_table, double* d_mlp,
+                      int absolute) {
   if (st->K < 0 || st->K > 8) return -1;
-  Scene s = make_scene(*c, N, mu, quat, scale, opac, gamma, color);
+  const bool ab = absolute != 0;
+  auto acc = [ab](double v) { return ab ? std::fabs(v) : v; };
+  Scene s = make_scene(*c, st, N, mu, quat, scale, opac, gamma, color);
   int K = st->K;
   size_t n_mlp = 0;
   if (fd)
@@ -635,7 +690,7 @@ int oracle_render_bwd(const OCam* c, const OSet* st, const OField* fd, int N, co
     render_pixel(*c, *st, fd, s, pix[p], true, r);
     const double* dC = d_image + 3 * p;
     size_t M = r.list.size();
-    std::vector<double> e(M, 0.0), dt(M, 0.0);
+    std::vector<double> e(M, 0.0), dt(M, 0.0), dt_mag(M, 0.0);
     std::vector<int> slot(M, -1);
     for (size_t j = 0; j < r.sel.size(); ++j) slot[r.sel[j]] = (int)j;
     PixGrad& G = pg[p];
@@ -650,47 +705,55 @@ int oracle_render_bwd(const OCam* c, const OSet* st, const OField* fd, int N, co
       }
       e[k] = dot3(r.tex[j], dC) + (d_weights ? d_weights[(size_t)p * K + j] : 0.0);
       if (!fd) continue;
-      std::vector<double> gfeat(fd->widths[0]);
-      const std::vector<double> gout = output_grad(*fd, gT, r.d);
-      mlp_backward(*fd, r.acts[j], gout.data(), gfeat.data(),
-                   n_mlp ? mlp_acc[tid].data() : nullptr);
-      double x[3] = {r.o[0] + ce.t * r.d[0], r.o[1] + ce.t * r.d[1], r.o[2] + ce.t * r.d[2]};
-      (void)x;
-      double gx[3] = {0, 0, 0};
-      double gt = 0.0;
-      for (int l = 0; l < fd->L; ++l) {
-        const LevelEval& le = r.lev[j][l];
-        double sl = fd->scale[l];
-        // d feature / d Delta
-        double gd = 0.0;
-        for (int f = 0; f < fd->F; ++f) gd += gfeat[l * fd->F + f] * le.acc[f];
-        gt += gd * downweight_dt(c->fx, sl, ce.t);
-        for (int corner = 0; corner < 8; ++corner) {
-          int dx = corner & 1, dy = (corner >> 1) & 1, dz = (corner >> 2) & 1;
-          int dl[3] = {dx, dy, dz};
-          double wa[3], dwa[3];
-          for (int a = 0; a < 3; ++a) {
-            wa[a] = dl[a] ? le.frac[a] : 1.0 - le.frac[a];
-            dwa[a] = dl[a] ? 1.0 : -1.0;
+      // the field's backward for this sample: MLP (weight gradients),
+      // table scatter and the positional gradient dt; evaluated signed, and
+      // in absolute mode once more on magnitudes for the table, the MLP and
+      // the scale of dt's rounding error
+      auto chain = [&](bool mag, double* dt_out) {
+        auto am = [mag](double v) { return mag ? std::fabs(v) : v; };
+        std::vector<double> gfeat(fd->widths[0]);
+        const std::vector<double> gout = output_grad(*fd, gT, r.d);
+        mlp_backward(*fd, r.acts[j], gout.data(), gfeat.data(),
+                     (n_mlp && mag == ab) ? mlp_acc[tid].data() : nullptr, mag);
+        double gx[3] = {0, 0, 0};
+        double gt = 0.0;
+        for (int l = 0; l < fd->L; ++l) {
+          const LevelEval& le = r.lev[j][l];
+          double sl = fd->scale[l];
+          // d feature / d Delta
+          double gd = 0.0;
+          for (int f = 0; f < fd->F; ++f) gd += am(gfeat[l * fd->F + f] * le.acc[f]);
+          gt += am(gd * downweight_dt(c->fx, sl, ce.t));
+          for (int corner = 0; corner < 8; ++corner) {
+            int dx = corner & 1, dy = (corner >> 1) & 1, dz = (corner >> 2) & 1;
+            int dl[3] = {dx, dy, dz};
+            double wa[3], dwa[3];
+            for (int a = 0; a < 3; ++a) {
+              wa[a] = dl[a] ? le.frac[a] : 1.0 - le.frac[a];
+              dwa[a] = dl[a] ? 1.0 : -1.0;
+            }
+            double w = wa[0] * wa[1] * wa[2];
+            uint32_t idx = spatial_hash(le.c0[0] + dx, le.c0[1] + dy, le.c0[2] + dz, (uint32_t)fd->T);
+            const double* ent = fd->table + ((size_t)l * fd->T + idx) * fd->F;
+            double ge = 0.0;
+            for (int f = 0; f < fd->F; ++f) {
+              double g = gfeat[l * fd->F + f];
+              if (d_table && mag == ab)
+                G.tab.push_back({((size_t)l * fd->T + idx) * fd->F + f, am(le.delta * w * g)});
+              ge += am(g * ent[f]);
+            }
+            // d/dx_a of w = dwa[a] * prod_{b != a} wa[b] * s_l
+            gx[0] += am(le.delta * ge * dwa[0] * wa[1] * wa[2] * sl);
+            gx[1] += am(le.delta * ge * wa[0] * dwa[1] * wa[2] * sl);
+            gx[2] += am(le.delta * ge * wa[0] * wa[1] * dwa[2] * sl);
           }
-          double w = wa[0] * wa[1] * wa[2];
-          uint32_t idx = spatial_hash(le.c0[0] + dx, le.c0[1] + dy, le.c0[2] + dz, (uint32_t)fd->T);
-          const double* ent = fd->table + ((size_t)l * fd->T + idx) * fd->F;
-          double ge = 0.0;
-          for (int f = 0; f < fd->F; ++f) {
-            double g = gfeat[l * fd->F + f];
-            if (d_table) G.tab.push_back({((size_t)l * fd->T + idx) * fd->F + f, le.delta * w * g});
-            ge += g * ent[f];
-          }
-          // d/dx_a of w = dwa[a] * prod_{b != a} wa[b] * s_l
-          gx[0] += le.delta * ge * dwa[0] * wa[1] * wa[2] * sl;
-          gx[1] += le.delta * ge * wa[0] * dwa[1] * wa[2] * sl;
-          gx[2] += le.delta * ge * wa[0] * wa[1] * dwa[2] * sl;
         }
-      }
-      // x = o + t d
-      gt += dot3(gx, r.d);
-      dt[k] += gt;
+        // x = o + t d
+        for (int a = 0; a < 3; ++a) gt += am(gx[a] * r.d[a]);
+        *dt_out += gt;
+      };
+      chain(false, &dt[k]);
+      if (ab) chain(true, &dt_mag[k]);
     }
     for (size_t k = 0; k < M; ++k)
       if (slot[k] < 0) e[k] = dot3(s.color + 3 * r.list[k].id, dC);
@@ -750,6 +813,19 @@ int oracle_render_bwd(const OCam* c, const OSet* st, const OField* fd, int N, co
       rot_backward(s.quat + 4 * i, GR, dq);
       for (int a = 0; a < 3; ++a) g[a] = gmu[a];
       for (int a = 0; a < 4; ++a) g[3 + a] = dq[a];
+      if (ab && dt_mag[k] != 0.0) {
+        // the record is linear in dt: add the magnitude of what the texture
+        // path's dt (taken on magnitudes) moves mu and q by
+        double gnx[3];
+        for (int a = 0; a < 3; ++a) {
+          g[a] = std::fabs(g[a]) + std::fabs(dt_mag[k] * n[a] / den);
+          gnx[a] = dt_mag[k] * (m[a] - ce.x[a]) / den;
+        }
+        double GX[9] = {0, 0, gnx[0], 0, 0, gnx[1], 0, 0, gnx[2]};
+        double dqx[4];
+        rot_backward(s.quat + 4 * i, GX, dqx);
+        for (int a = 0; a < 4; ++a) g[3 + a] = std::fabs(g[3 + a]) + std::fabs(dqx[a]);
+      }
       G.surf.push_back({i, g});
     }
   }
@@ -761,15 +837,15 @@ int oracle_render_bwd(const OCam* c, const OSet* st, const OField* fd, int N, co
     for (auto& sg : pg[p].surf) {
       int i = sg.first;
       const auto& g = sg.second;
-      if (d_mu) for (int a = 0; a < 3; ++a) d_mu[3 * i + a] += g[a];
-      if (d_quat) for (int a = 0; a < 4; ++a) d_quat[4 * i + a] += g[3 + a];
-      if (d_scale) for (int a = 0; a < 2; ++a) d_scale[2 * i + a] += g[7 + a];
-      if (d_opac) d_opac[i] += g[9];
-      if (d_gamma) for (int a = 0; a < 2; ++a) d_gamma[2 * i + a] += g[10 + a];
-      if (d_color) for (int a = 0; a < 3; ++a) d_color[3 * i + a] += g[12 + a];
+      if (d_mu) for (int a = 0; a < 3; ++a) d_mu[3 * i + a] += acc(g[a]);
+      if (d_quat) for (int a = 0; a < 4; ++a) d_quat[4 * i + a] += acc(g[3 + a]);
+      if (d_scale) for (int a = 0; a < 2; ++a) d_scale[2 * i + a] += acc(g[7 + a]);
+      if (d_opac) d_opac[i] += acc(g[9]);
+      if (d_gamma) for (int a = 0; a < 2; ++a) d_gamma[2 * i + a] += acc(g[10 + a]);
+      if (d_color) for (int a = 0; a < 3; ++a) d_color[3 * i + a] += acc(g[12 + a]);
     }
     if (d_table)
-      for (auto& tg : pg[p].tab) d_table[tg.first] += tg.second;
+      for (auto& tg : pg[p].tab) d_table[tg.first] += acc(tg.second);
   }
   if (d_mlp)
     for (int t = 0; t < n_threads; ++t)

@@ -4,6 +4,7 @@ definition and on a lattice with a known order, the blended-error
 identity sum_i err_i = sum_p e_p (1 - T_final_p), the sampling law of the
 selection, the split's geometry and the prune threshold."""
 import numpy as np
+import pytest
 
 import oracle
 from oracle import density as D
@@ -33,6 +34,52 @@ def test_fps_on_a_line_with_ties_to_the_lowest_index():
     idx, d2 = D.fps(x, 9)
     assert list(idx) == [0, 8, 4, 2, 6, 1, 3, 5, 7]
     np.testing.assert_allclose(D.fps_scales(d2), [8, 8, 4, 2, 2, 1, 1, 1, 1])
+
+
+def test_fps_check_accepts_the_definition_and_near_ties_only():
+    """fps_check walks another implementation's order: the FP64 order passes
+    with no tie; a swap of two well-separated choices fails; a choice within
+    the stated margin of the maximum passes and is counted."""
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(40, 3)).astype(np.float32)
+    idx, d2 = D.fps(x, 40)
+    c = D.fps_check(x, idx, d2, 1e-6)
+    assert c["ties"] == 0 and c["d2_rel"] == 0.0 and c["steps"] == 40
+    np.testing.assert_array_equal(c["d2"][1:], d2[1:])
+    bad = idx.copy()
+    bad[[1, 2]] = bad[[2, 1]]
+    with pytest.raises(AssertionError):
+        D.fps_check(x, bad, d2, 1e-6)
+    with pytest.raises(AssertionError):
+        D.fps_check(x, np.r_[idx[:5], idx[4]], d2[:6], 1e-6)  # a point twice
+    # two points at equal distance up to 1e-9 relative from point 0: either is valid
+    y = np.array([[0, 0, 0], [4, 0, 0], [0, 4 * (1 - 1e-9), 0], [1, 1, 0]], np.float64)
+    ri, rd = D.fps(y, 4)
+    assert ri[1] == 1
+    alt = np.array([0, 2, 1, 3])
+    c = D.fps_check(y, alt, rd, 1e-6)
+    assert c["ties"] == 1
+    with pytest.raises(AssertionError):
+        D.fps_check(y, alt, rd, 1e-10)
+
+
+def test_select_check_accepts_the_definition_and_near_ties_only():
+    rng = np.random.default_rng(6)
+    err = rng.exponential(size=50)
+    expo = rng.exponential(size=50)
+    sel = D.select(err, expo, 10)
+    assert D.select_check(err, expo, 10, sel, 1e-7)["ties"] == 0
+    with pytest.raises(AssertionError):
+        D.select_check(err, expo, 10, sel[::-1], 1e-7)
+    with pytest.raises(AssertionError):
+        D.select_check(err, expo, 10, np.r_[sel[:9], sel[0]], 1e-7)
+    # keys 1 and 1 + 1e-9: either order passes at 1e-7, and is counted
+    err2 = np.array([1.0, 1.0, 0.5, 0.0])
+    expo2 = np.array([1.0 + 1e-9, 1.0, 3.0, 1.0])
+    assert list(D.select(err2, expo2, 2)) == [1, 0]
+    assert D.select_check(err2, expo2, 2, [0, 1], 1e-7)["ties"] == 2
+    with pytest.raises(AssertionError):
+        D.select_check(err2, expo2, 2, [0, 1], 1e-10)
 
 
 def test_blend_error_sums_to_the_composited_weight():

@@ -199,6 +199,35 @@ def test_map_positive_is_bijection():
     assert oracle.map_positive(0) == 0
 
 
+def _golden_hash_rows():
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "spatial_hash.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                f = line.split()
+                rows.append(dict(k=tuple(int(v) for v in f[0:3]), log2T=int(f[3]),
+                                 m=tuple(int(v) for v in f[4:7]), h=int(f[10], 16),
+                                 index=int(f[11])))
+    return rows
+
+
+def test_spatial_hash_golden_values():
+    """The spatial hash (supp. Sec. 7.1: Instant-NGP's hash on MapPositive'd
+    cell coordinates) against values worked out by hand from its definition
+    (tests/golden/spatial_hash.txt): the MapPositive of every axis, the
+    table index at the listed T, and 31 of the 32 bits of the hash itself
+    (the index at T = 2^31).  A wrong prime, a '+' for the XOR, a swapped
+    axis or a dropped MapPositive changes some row."""
+    rows = _golden_hash_rows()
+    assert len(rows) >= 12
+    for r in rows:
+        assert tuple(oracle.map_positive(k) for k in r["k"]) == r["m"], r
+        assert oracle.hash_index(*r["k"], 1 << r["log2T"]) == r["index"], r
+        assert oracle.hash_index(*r["k"], 1 << 31) == r["h"] & 0x7FFFFFFF, r
+    # the axes are hashed with different primes: permuting a cell moves it
+    assert oracle.hash_index(0, 1, 0, 1 << 31) != oracle.hash_index(0, 0, 1, 1 << 31)
+
+
 def test_hash_without_collisions_is_dense_trilinear():
     """One level, T = 2^22: on a box of cells whose hashes are verified
     distinct, the hash grid equals dense trilinear interpolation, which
@@ -279,6 +308,46 @@ def test_depth_order_sorted_and_culled():
     assert np.all(np.diff(zs) >= 0)
     same = np.diff(zs) == 0
     assert np.all(np.diff(order)[same] > 0)  # index ascending on equal depth
+
+
+def _quat_of_columns(v1, v2, n):
+    """Unit quaternion (w, x, y, z) of the rotation with columns v1, v2, n."""
+    R = np.stack([v1, v2, n], axis=1)
+    w = math.sqrt(max(0.0, 1.0 + R[0, 0] + R[1, 1] + R[2, 2])) / 2
+    x = math.copysign(math.sqrt(max(0.0, 1.0 + R[0, 0] - R[1, 1] - R[2, 2])) / 2, R[2, 1] - R[1, 2])
+    y = math.copysign(math.sqrt(max(0.0, 1.0 - R[0, 0] + R[1, 1] - R[2, 2])) / 2, R[0, 2] - R[2, 0])
+    z = math.copysign(math.sqrt(max(0.0, 1.0 - R[0, 0] - R[1, 1] + R[2, 2])) / 2, R[1, 0] - R[0, 1])
+    return (w, x, y, z)
+
+
+@pytest.mark.parametrize("tilt", [0.0, 0.1])
+def test_edge_on_surfel(tilt):
+    """The edge-on reading: a surfel whose plane contains its own centre ray
+    (|d_mu . n_c| < 1e-7) is culled.  It would add nothing anyway: that plane
+    passes through the camera centre, so every pixel ray meets it at t = 0
+    (behind the near plane) or lies in it (grazing).  A surfel tilted away
+    from that renders a footprint, and no pixel is flagged near the
+    threshold."""
+    cam = facing_camera(48, 48)
+    eye = np.array([0.0, 0.0, -3.0])
+    mu = np.array([0.15, -0.1, 0.0])
+    ray = (mu - eye) / np.linalg.norm(mu - eye)
+    n0 = np.cross(ray, [0.0, 1.0, 0.0])
+    n0 /= np.linalg.norm(n0)
+    n = math.cos(tilt) * n0 + math.sin(tilt) * ray
+    v1 = np.cross([0.0, 1.0, 0.0], n)
+    v1 /= np.linalg.norm(v1)
+    v2 = np.cross(n, v1)
+    q = _quat_of_columns(v1, v2, n)
+    sc = one_surfel(mu, (0.5, 0.5), 0.95, (1.0, 1.0), (1.0, 1.0, 1.0), quat=q)
+    st = synth.Settings(K=0)
+    r = oracle.render(sc, cam, st, tie_tol=1e-5, edge_tol=1e-6)
+    drawn = int(np.count_nonzero(r["n_contrib"]))
+    if tilt == 0.0:
+        assert drawn == 0 and np.all(r["image"] == 0.0) and np.all(r["T_final"] == 1.0)
+    else:
+        assert drawn > 100 and r["image"].max() > 0.5
+    assert not np.any(r["tie"] & 128)
 
 
 # ------------------------------------------------------- storage accounting
@@ -420,3 +489,55 @@ def test_procedural_targets_reduce_to_constant_colour():
                       np.tile(tau, (sc.n, 1)))
     ref = oracle.render(sc2, cam, st, None)
     np.testing.assert_allclose(img, ref["image"], rtol=1e-12, atol=1e-14)
+
+
+def test_absolute_mode_bounds_the_gradient():
+    """render_bwd(absolute=True) sums the magnitudes of the contributions
+    (the texture path evaluated on magnitudes): it bounds |gradient| entry
+    by entry, equals it for the surfel parameters the texture path does not
+    reach when only one pixel contributes, and is linear in |upstream|."""
+    cam = synth.front_camera(24, 20)
+    sc = small_scene(13, n=40)
+    fld = synth.make_field(4, 10, 2, (16,), 3, table_std=0.3)
+    st = synth.Settings(K=2)
+    rng = np.random.default_rng(9)
+    P = cam.width * cam.height
+    pix = np.arange(P, dtype=np.int32)
+    dI, dW = rng.normal(size=(P, 3)), rng.normal(size=(P, 2))
+    g = oracle.render_bwd(sc, cam, st, fld, pix, dI, dW)
+    a = oracle.render_bwd(sc, cam, st, fld, pix, dI, dW, absolute=True)
+    for k in ("mu", "quat", "scale", "opacity", "gamma", "color", "table", "mlp"):
+        assert np.all(a[k] >= np.abs(g[k]) - 1e-12 * (np.abs(g[k]).max() + 1)), k
+        assert a[k].max() > 0, k
+    a2 = oracle.render_bwd(sc, cam, st, fld, pix, 2 * dI, 2 * dW, absolute=True)
+    np.testing.assert_allclose(a2["table"], 2 * a["table"], rtol=1e-12)
+    one = pix[[P // 2 + cam.width // 2]]
+    g1 = oracle.render_bwd(sc, cam, st, fld, one, dI[one], dW[one])
+    a1 = oracle.render_bwd(sc, cam, st, fld, one, dI[one], dW[one], absolute=True)
+    # one pixel: one contribution per surfel entry; the entries the texture
+    # path's dt does not reach equal the magnitude of the gradient, mu and q
+    # add the magnitude of what dt moves them by
+    for k in ("scale", "opacity", "color"):
+        np.testing.assert_allclose(a1[k], np.abs(g1[k]), rtol=1e-12, atol=1e-300)
+    for k in ("mu", "quat"):
+        assert np.all(a1[k] >= np.abs(g1[k]) * (1 - 1e-12)), k
+
+
+def test_centre_ray_cosine():
+    """|cos| between a surfel's normal and its centre ray: 1 for a surfel
+    facing the camera, ~0 for one whose plane holds the camera centre."""
+    cam = facing_camera(48, 48)
+    face = one_surfel((0.3, -0.2, 0.5), (0.1, 0.1), 0.5, (1, 1), (1, 1, 1))
+    c = oracle.centre_ray_cosine(cam, face)[0]
+    d = np.array([0.3, -0.2, 3.5])
+    assert abs(c - 3.5 / np.linalg.norm(d)) < 1e-6
+    eye = np.array([0.0, 0.0, -3.0])
+    mu = np.array([0.15, -0.1, 0.0])
+    ray = (mu - eye) / np.linalg.norm(mu - eye)
+    n = np.cross(ray, [0.0, 1.0, 0.0])
+    n /= np.linalg.norm(n)
+    v1 = np.cross([0.0, 1.0, 0.0], n)
+    v1 /= np.linalg.norm(v1)
+    edge = one_surfel(mu, (0.5, 0.5), 0.9, (1, 1), (1, 1, 1),
+                      quat=_quat_of_columns(v1, np.cross(n, v1), n))
+    assert oracle.centre_ray_cosine(cam, edge)[0] < 1e-6
