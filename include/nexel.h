@@ -84,7 +84,8 @@ typedef struct {
  * cores with FP32 accumulation; NEXEL_F16: FP16 operands with FP32
  * accumulation, the backward scaling the gradient that enters the MLP by
  * 128 and unscaling the results, as the paper trains).  The tensor-core
- * forms support the MLPs 16 -> 64 -> 3 and 32 -> 64 -> 64 -> 3. */
+ * forms support the MLPs 16 -> 64 -> OUT and 32 -> 64 -> 64 -> OUT with
+ * OUT = 3, and with OUT = 48 (SH textures) on the FP16 table. */
 typedef struct {
   int K;
   float alpha_min, alpha_max, T_min;
@@ -117,8 +118,9 @@ typedef struct {
  * an MLP without bias: widths[0] = L * F -> hidden ... -> widths[n_layers]
  * = 3 (RGB texture) or 48 (the texture's degree-3 SH coefficients o[3k + ch],
  * Sec. 3 and Sec. 5, evaluated in the pixel's normalised ray direction:
- * T_ch = sum_k Y_k(d / |d|) o[3k + ch]; FP32 form with 64-wide hidden
- * layers only), ReLU on hidden layers, linear output.  weights are float32 packed
+ * T_ch = sum_k Y_k(d / |d|) o[3k + ch]; the FP32 form with 64-wide hidden
+ * layers, the tensor-core forms with the FP16 table), ReLU on hidden
+ * layers, linear output.  weights are float32 packed
  * layer after layer, layer l row-major [widths[l+1]][widths[l]].  Hidden
  * widths must be multiples of 16 and at most 64; L * F a multiple of 8 and at
  * most 64. */
@@ -149,8 +151,11 @@ int nexel_bwd_workspace_size(const nexel_camera* cam, const nexel_settings* sett
  * the generalised-Gaussian kernel alpha = o exp(-|u|^(2 g1)/2) exp(-|v|^(2 g2)/2)):
  * per surfel the camera-space frame, the exact screen footprint of the
  * region where alpha >= alpha_min, the tiles it touches; then a stable radix
- * sort of surfels by centre depth (culled: centre depth <= near or
- * opacity < alpha_min) and the per-tile lists of (tile, depth-rank)
+ * sort of surfels by centre depth (culled: centre depth <= near,
+ * opacity < alpha_min, a surfel seen edge-on -- |d_mu . n| < 1e-7 for the
+ * centre ray d_mu at unit depth, whose plane then passes through the camera
+ * centre -- and a surfel with a NaN or infinite parameter, which is counted
+ * for nexel_render_stats and nexel_read_status) and the per-tile lists of (tile, depth-rank)
  * instances in rank order, bit-exact (each instance placed directly at its
  * slot, or, for 64-bit keys or more than 8192 tiles, a stable radix sort of
  * the instances by tile).  Results stay in `ws`.  Writes the number of
@@ -252,10 +257,15 @@ int nexel_render_batch_bwd(int n_views, const nexel_camera* cams, const nexel_se
                            float* d_mlp, nexel_stream_t stream);
 
 /* Reads and clears the device status words of one view's workspaces
- * (bwd_ws may be NULL), synchronising the stream: NEXEL_ERR_CAPACITY if a
- * device-count preprocess dropped instances, NEXEL_ERR_TIMEOUT if a bounded
- * device wait of a tensor-core kernel ran out (that kernel's results are
- * invalid), else NEXEL_OK. */
+ * (bwd_ws may be NULL), synchronising the stream: NEXEL_ERR_TIMEOUT if a
+ * bounded device wait of a tensor-core kernel ran out (that kernel's
+ * results are invalid; the words cover the last preprocess and forward on
+ * ws, which the preprocess resets, and the last backward on bwd_ws, which
+ * that backward resets), else NEXEL_ERR_CAPACITY if a device-count
+ * preprocess dropped instances, else NEXEL_ERR_NUMERIC if a preprocess
+ * culled a surfel with a NaN or infinite parameter (or a zero quaternion:
+ * such a surfel is skipped by the render and gets zero gradients;
+ * nexel_render_stats counts them), else NEXEL_OK. */
 int nexel_read_status(const nexel_camera* cam, const nexel_settings* settings,
                       const nexel_field* field, int N, void* ws, size_t ws_bytes, void* bwd_ws,
                       size_t bwd_ws_bytes, nexel_stream_t stream);
@@ -319,10 +329,13 @@ int nexel_adam_step(int n_tensors, float* const* params, const float* const* gra
  * nexel_fps: farthest point sampling of n points [n][3] (device): idx[0] =
  * 0, then idx[i] = the unselected point farthest from the selected ones
  * (ties: lowest index); d2sel[i] = its squared distance to them at
- * selection (d2sel[0] = +inf), whose square root is the paper's initial
- * scale of that point.  Squared distances are formed in FP32 with every
- * operation rounded, ((dx dx + dy dy) + dz dz).  scratch: n floats.  One
- * CTA, m iterations: an initialisation step, not a per-iteration one.
+ * selection (d2sel[0] = +inf).  scale (nullable) receives the paper's
+ * initial scale of each sampled point: the distance at which it was
+ * selected, sqrt(d2sel[i]) (its nearest neighbour among the points sampled
+ * before it), with scale[0] = scale[1] (the first point has no
+ * predecessor; 0 when m = 1).  Squared distances are formed in FP32 with
+ * every operation rounded, ((dx dx + dy dy) + dz dz).  scratch: n floats.
+ * One CTA, m iterations: an initialisation step, not a per-iteration one.
  *
  * nexel_blend_error: ADDS to err[i] (original order) the blended L1 error of
  * Rota Bulo et al. that the paper accumulates across iterations:
@@ -330,12 +343,18 @@ int nexel_adam_step(int n_tensors, float* const* params, const float* const* gra
  * at the pixel and e_p the mean over channels of |image - target|.  Runs on
  * the workspace of the last nexel_preprocess of this view.
  *
- * nexel_densify_select: the n_select surfels to split, drawn without
- * replacement with probabilities proportional to err (Efraimidis-Spirakis):
- * the caller passes exponential random numbers expo[i] (mean 1), the call
- * returns in sel the indices of the n_select smallest expo[i] / err[i]
- * (FP32; err[i] = 0 never drawn; ties by index).  The paper draws 5 % of
- * the surfels, capped so that the total stays within its budget P.
+ * nexel_densify_count: the number of surfels a density step splits: 5 %
+ * of the N current ones, rounded up, capped so that the total stays within
+ * the budget P (the paper's primitive budget): max(0, min(ceil(N / 20),
+ * budget - N)).  Host only; writes *n_select (host).
+ *
+ * nexel_densify_select: draws the surfels to split, nexel_densify_count(N,
+ * budget) of them, without replacement with probabilities proportional to
+ * err (Efraimidis-Spirakis): the caller passes exponential random numbers
+ * expo[i] (mean 1), the call returns in sel the indices of the n_select
+ * smallest expo[i] / err[i] (FP32; err[i] = 0 never drawn while a positive
+ * error remains; ties by index) in increasing key order, and n_select in
+ * *n_select_out (host).  sel (device) must hold ceil(N / 20) entries.
  *
  * nexel_densify_split: surfel sel[r] becomes two with scales halved along
  * the longer axis (v1 if sigma1 >= sigma2, else v2) and centres
@@ -349,13 +368,14 @@ int nexel_adam_step(int n_tensors, float* const* params, const float* const* gra
  *
  * Scratch of the selection and the prune: nexel_density_workspace_size. */
 int nexel_fps(int n, const float* points, int m, float* scratch, int* idx, float* d2sel,
-              nexel_stream_t stream);
+              float* scale, nexel_stream_t stream);
 int nexel_blend_error(const nexel_camera* cam, const nexel_settings* settings, int N, void* ws,
                       size_t ws_bytes, const float* image, const float* target, float* err,
                       nexel_stream_t stream);
 int nexel_density_workspace_size(int N, size_t* bytes);
-int nexel_densify_select(int N, const float* err, const float* expo, int n_select, void* ws,
-                         size_t ws_bytes, int* sel, nexel_stream_t stream);
+int nexel_densify_count(int N, long long budget, int* n_select);
+int nexel_densify_select(int N, const float* err, const float* expo, long long budget, void* ws,
+                         size_t ws_bytes, int* sel, int* n_select_out, nexel_stream_t stream);
 int nexel_densify_split(int N, int n_select, const int* sel, int color_dim, float* mu, float* quat,
                         float* scale, float* opacity, float* gamma, float* color,
                         nexel_stream_t stream);
@@ -386,6 +406,17 @@ typedef struct {
   int tex_fwd_ctas_per_sm, tex_bwd_ctas_per_sm, f32_ctas_per_sm, hash_block;
 } nexel_tuning;
 int nexel_get_tuning(nexel_tuning* out);
+
+/* Test hook of the failure path (no counterpart in the paper).  With
+ * polls in 1..65536 the tensor-core texturing kernels (forward and
+ * backward) launched afterwards issue no MMA and give up each wait for MMA
+ * completion after `polls` polls of its mbarrier, which nothing then
+ * arrives at: each CTA ends its tile loop, frees its TMEM, returns, and
+ * sets the timeout bit that nexel_read_status reports as
+ * NEXEL_ERR_TIMEOUT (the outputs of those launches are invalid).  No GPU
+ * fault and no unbounded wait is involved.  polls = 0 (the default)
+ * restores normal operation.  Process-wide. */
+int nexel_test_tc_wait_timeout(int polls);
 int nexel_set_tuning(const nexel_tuning* t);
 int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
                    const nexel_field* field, int N, const float* mu, const float* quat,
@@ -409,7 +440,7 @@ int nexel_instance_list(const nexel_camera* cam, int N, const void* ws, size_t w
                         nexel_stream_t stream);
 
 /* Work statistics of the last nexel_render_fwd on ws (a device reduction;
- * synchronises `stream`).  Writes out[7] (host):
+ * synchronises `stream`).  Writes out[8] (host):
  *   out[0] (tile, surfel) instances of the binning (Sec. 3, "Preliminaries"),
  *   out[1] surfels with at least one instance (not culled, on screen),
  *   out[2] sum over pixels of the last list position the pixel composited
@@ -420,7 +451,9 @@ int nexel_instance_list(const nexel_camera* cam, int N, const void* ws, size_t w
  *   out[4] the longest tile list, out[5] the number of 16 x 16 tiles,
  *   out[6] sum over tiles of (largest last list position of its pixels) x
  *          pixels of the tile: the pair evaluations the collection backward
- *          runs (every thread of a tile walks back from the tile's largest).
+ *          runs (every thread of a tile walks back from the tile's largest),
+ *   out[7] surfels the last preprocess culled for a NaN or infinite
+ *          parameter (or a zero quaternion).
  * The counters block of ws holds the reduction; nothing else is changed. */
 int nexel_render_stats(const nexel_camera* cam, const nexel_settings* settings, int N,
                        void* ws, size_t ws_bytes, long long* out, nexel_stream_t stream);
@@ -457,15 +490,20 @@ int nexel_peak_l2_reductions(void* buf, size_t buf_bytes, long long n_ops, int r
  * nexel_render_fwd with a workspace that is a file-scope device array of the
  * library (12 MiB on each device that uses it, held until the process
  * exits) instead of caller memory; it allocates nothing.  Inputs and outputs
- * are as for nexel_preprocess / nexel_render_fwd.  Limits: N <= 16384
- * surfels and width * height <= 65536 pixels (else NEXEL_ERR_INVALID_ARG,
- * nothing launched); more (tile, surfel) instances than the array holds
- * returns NEXEL_ERR_CAPACITY with the count in *n_instances_out.  The first
- * call on a device resolves the array's device address (once per device,
- * with that device current), so make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race,
- * so serialise them; it keeps the previous call's contents, and the
- * pipeline clears what must start at zero itself. */
+ * are as for nexel_preprocess / nexel_render_fwd; settings->cache_features
+ * must be 0 when K > 0 (no backward follows, so there is no scratch to
+ * cache features in; else NEXEL_ERR_INVALID_ARG, nothing launched).
+ * Limits: N <= 16384 surfels and width * height <= 65536 pixels (else
+ * NEXEL_ERR_INVALID_ARG, nothing launched); more (tile, surfel) instances
+ * than the array holds returns NEXEL_ERR_CAPACITY with the count in
+ * *n_instances_out.  Like nexel_preprocess, every call synchronises the
+ * stream once to read the instance count back.  The first call on a device
+ * resolves the array's device address (once per device, with that device
+ * current, kept for the life of the process: do not use the library across
+ * a cudaDeviceReset of that device), so make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the
+ * GPU race, so serialise them; it keeps the previous call's contents, and
+ * the pipeline clears what must start at zero itself. */
 int nexel_render_fwd_static(const nexel_camera* cam, const nexel_settings* settings,
                             const nexel_field* field, int N, const float* mu, const float* quat,
                             const float* scale, const float* opacity, const float* gamma,

@@ -34,9 +34,11 @@ EXPORTS = ["nexel_workspace_size", "nexel_bwd_workspace_size", "nexel_preprocess
            "nexel_render_fwd_static", "nexel_preprocess_async", "nexel_render_batch_fwd",
            "nexel_render_batch_bwd", "nexel_read_status", "nexel_loss_workspace_size",
            "nexel_loss_image", "nexel_loss_params", "nexel_adam_step", "nexel_fps",
-           "nexel_blend_error", "nexel_density_workspace_size", "nexel_densify_select",
+           "nexel_blend_error", "nexel_density_workspace_size", "nexel_densify_count",
+           "nexel_densify_select",
            "nexel_densify_split", "nexel_prune", "nexel_get_tuning", "nexel_set_tuning",
-           "nexel_autotune", "nexel_render_stats", "nexel_peak_l2_reductions"]
+           "nexel_autotune", "nexel_render_stats", "nexel_peak_l2_reductions",
+           "nexel_test_tc_wait_timeout"]
 
 
 def _nvcc() -> str:
@@ -157,12 +159,14 @@ def lib(auto_build: bool = False):
     L.nexel_loss_params.argtypes = [i, vp, vp, vp, vp, vp, sz, i, i, vp, vp, vp, vp]
     L.nexel_adam_step.argtypes = [i, vp, vp, vp, vp, vp, vp, C.c_float, C.c_float, C.c_float,
                                   i, vp]
-    L.nexel_fps.argtypes = [i, vp, i, vp, vp, vp, vp]
+    L.nexel_fps.argtypes = [i, vp, i, vp, vp, vp, vp, vp]
     L.nexel_blend_error.argtypes = [vp, vp, i, vp, sz, vp, vp, vp, vp]
     L.nexel_density_workspace_size.argtypes = [i, C.POINTER(sz)]
-    L.nexel_densify_select.argtypes = [i, vp, vp, i, vp, sz, vp, vp]
+    L.nexel_densify_count.argtypes = [i, ll, C.POINTER(i)]
+    L.nexel_densify_select.argtypes = [i, vp, vp, ll, vp, sz, vp, C.POINTER(i), vp]
     L.nexel_densify_split.argtypes = [i, i, vp, i] + [vp] * 6 + [vp]
     L.nexel_prune.argtypes = [i, C.c_float, i] + [vp] * 6 + [vp, sz] + [vp] * 7 + [vp]
+    L.nexel_test_tc_wait_timeout.argtypes = [i]
     L.nexel_get_tuning.argtypes = [vp]
     L.nexel_set_tuning.argtypes = [vp]
     L.nexel_autotune.argtypes = ([vp, vp, vp, i] + [vp] * 6 + [vp, sz, vp, sz] + [vp] * 7 + [vp] +
@@ -245,12 +249,12 @@ def nexel_instance_list(cam, N, ws, ws_bytes, n_instances, tile_out, id_out, dep
 
 
 RENDER_STATS = ("instances", "visible_surfels", "pairs_to_last", "pairs_full_lists",
-                "longest_list", "tiles", "pairs_bwd_walk")
+                "longest_list", "tiles", "pairs_bwd_walk", "nonfinite_surfels")
 
 
 def nexel_render_stats(cam, st, N, ws, ws_bytes, stream) -> dict:
     """Work statistics of the last forward on ws (synchronises the stream)."""
-    out = (C.c_longlong * 7)()
+    out = (C.c_longlong * len(RENDER_STATS))()
     check("nexel_render_stats", lib().nexel_render_stats(C.byref(cam), C.byref(st), N, ws,
                                                          ws_bytes, out, stream))
     return dict(zip(RENDER_STATS, (int(v) for v in out)))
@@ -326,12 +330,12 @@ def nexel_render_batch_bwd(cams, st, field, N, mu, quat, scale, opacity, gamma, 
 
 
 def nexel_read_status(cam, st, field, N, ws, ws_bytes, bws, bws_bytes, stream) -> int:
-    """Returns the status (NEXEL_OK, NEXEL_ERR_CAPACITY or NEXEL_ERR_TIMEOUT)
-    without raising; argument errors raise."""
+    """Returns the status (NEXEL_OK, NEXEL_ERR_CAPACITY, NEXEL_ERR_TIMEOUT or
+    NEXEL_ERR_NUMERIC) without raising; argument errors raise."""
     rc = lib().nexel_read_status(C.byref(cam), C.byref(st),
                                  C.byref(field) if field is not None else None, N, ws, ws_bytes,
                                  bws, bws_bytes, stream)
-    if rc not in (NEXEL_OK, -3, -5):
+    if rc not in (NEXEL_OK, -3, -5, -6):
         raise NexelError("nexel_read_status", rc)
     return rc
 
@@ -364,8 +368,8 @@ def nexel_adam_step(params, grads, m, v, sizes, lrs, beta1, beta2, eps, step, st
         (C.c_float * n)(*lrs), beta1, beta2, eps, step, stream))
 
 
-def nexel_fps(n, points, m, scratch, idx, d2sel, stream) -> int:
-    return check("nexel_fps", lib().nexel_fps(n, points, m, scratch, idx, d2sel, stream))
+def nexel_fps(n, points, m, scratch, idx, d2sel, scale, stream) -> int:
+    return check("nexel_fps", lib().nexel_fps(n, points, m, scratch, idx, d2sel, scale, stream))
 
 
 def nexel_blend_error(cam, st, N, ws, ws_bytes, image, target, err, stream) -> int:
@@ -379,9 +383,18 @@ def nexel_density_workspace_size(N: int) -> int:
     return out.value
 
 
-def nexel_densify_select(N, err, expo, n_select, ws, ws_bytes, sel, stream) -> int:
-    return check("nexel_densify_select", lib().nexel_densify_select(
-        N, err, expo, n_select, ws, ws_bytes, sel, stream))
+def nexel_densify_count(N: int, budget: int) -> int:
+    out = C.c_int(0)
+    check("nexel_densify_count", lib().nexel_densify_count(N, budget, C.byref(out)))
+    return out.value
+
+
+def nexel_densify_select(N, err, expo, budget, ws, ws_bytes, sel, stream) -> int:
+    """Returns the number of surfels drawn (nexel_densify_count)."""
+    out = C.c_int(0)
+    check("nexel_densify_select", lib().nexel_densify_select(
+        N, err, expo, budget, ws, ws_bytes, sel, C.byref(out), stream))
+    return out.value
 
 
 def nexel_densify_split(N, n_select, sel, color_dim, mu, quat, scale, opacity, gamma, color,
@@ -394,6 +407,12 @@ def nexel_prune(N, threshold, color_dim, src, ws, ws_bytes, dst, n_out, stream) 
     """src, dst: (mu, quat, scale, opacity, gamma, color) device pointers."""
     return check("nexel_prune", lib().nexel_prune(
         N, threshold, color_dim, *src, ws, ws_bytes, *dst, n_out, stream))
+
+
+def nexel_test_tc_wait_timeout(polls: int) -> int:
+    """Test hook: polls > 0 makes the tensor-core kernels issue no MMA and
+    give up each completion wait after that many polls; 0 turns it off."""
+    return check("nexel_test_tc_wait_timeout", lib().nexel_test_tc_wait_timeout(polls))
 
 
 def nexel_get_tuning() -> Tuning:

@@ -540,8 +540,9 @@ int nexel_read_status(const nexel_camera* cam, const nexel_settings* settings,
   if (e == cudaSuccess && bstat) e = cudaMemsetAsync(bstat, 0, 4, st);
   if (e != cudaSuccess) return NEXEL_ERR_CUDA;
   const int f = words[0] | words[1];
-  if (f & kStatusCapacity) return NEXEL_ERR_CAPACITY;
   if (f & kStatusTimeout) return NEXEL_ERR_TIMEOUT;
+  if (f & kStatusCapacity) return NEXEL_ERR_CAPACITY;
+  if (f & kStatusNumeric) return NEXEL_ERR_NUMERIC;
   return NEXEL_OK;
 }
 
@@ -598,10 +599,13 @@ int nexel_render_stats(const nexel_camera* cam, const nexel_settings* settings, 
     e = cudaGetLastError();
   }
   unsigned long long h[5] = {0, 0, 0, 0, 0};
-  uint32_t n_inst = 0;
+  uint32_t n_inst = 0, n_bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&n_inst, w + L.counters + kCountersInst, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&n_bad, w + L.counters + kCountersNonFinite, 4, cudaMemcpyDeviceToHost,
+                        st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return NEXEL_ERR_CUDA;
   out[0] = (long long)n_inst;
@@ -611,6 +615,7 @@ int nexel_render_stats(const nexel_camera* cam, const nexel_settings* settings, 
   out[4] = (long long)h[2];
   out[5] = (long long)L.n_tiles;
   out[6] = (long long)h[4];
+  out[7] = (long long)n_bad;
   return NEXEL_OK;
 }
 

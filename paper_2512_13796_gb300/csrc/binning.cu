@@ -139,13 +139,29 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int sh_degree, int N,
                              float4* __restrict__ aux, uint32_t* __restrict__ dkey,
                              uint32_t* __restrict__ did, uint2* __restrict__ rect,
                              float4* __restrict__ conic, uint32_t* __restrict__ count,
-                             float* __restrict__ shj) {
+                             float* __restrict__ shj, uint32_t* __restrict__ n_nonfinite,
+                             int* __restrict__ status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   did[i] = (uint32_t)i;
   float m[3] = {mu[3 * i], mu[3 * i + 1], mu[3 * i + 2]};
   float qw = quat[4 * i], qx = quat[4 * i + 1], qy = quat[4 * i + 2], qz = quat[4 * i + 3];
   float qn = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  // A surfel with a NaN or infinite parameter (or a zero quaternion) has no
+  // defined footprint: it is culled like one behind the camera, counted, and
+  // the status word reports it (NEXEL_ERR_NUMERIC from nexel_read_status).
+  bool finite = isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && isfinite(qn) &&
+                isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) &&
+                isfinite(scale[2 * i]) && isfinite(scale[2 * i + 1]) && isfinite(opac[i]) &&
+                isfinite(gam[2 * i]) && isfinite(gam[2 * i + 1]);
+  {
+    const int nc = sh_degree == 3 ? 48 : 3;
+    for (int k = 0; k < nc; ++k) finite = finite && isfinite(color[(size_t)nc * i + k]);
+  }
+  if (!finite) {
+    atomicAdd(n_nonfinite, 1u);
+    atomicOr(status, kStatusNumeric);
+  }
   qw *= qn; qx *= qn; qy *= qn; qz *= qn;
   float3 v1, v2, n;
   quat_cols(qw, qx, qy, qz, v1, v2, n);
@@ -163,8 +179,8 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int sh_degree, int N,
   }
   float z = mc[2].hi;
   float3 v1c = rot(c.R, v1), v2c = rot(c.R, v2), nc = rot(c.R, n);
-  bool ok = (z > c.near_) && (o >= alpha_min) && (s1 > 0.f) && (s2 > 0.f) && (g1 >= 1.f) &&
-            (g2 >= 1.f);
+  bool ok = finite && (z > c.near_) && (o >= alpha_min) && (s1 > 0.f) && (s2 > 0.f) &&
+            (g1 >= 1.f) && (g2 >= 1.f);
   float dmx = 0.f, dmy = 0.f, dn0 = 0.f;
   if (ok) {
     dmx = mc[0].hi / z;
@@ -1049,7 +1065,8 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
         (float4*)(ws + L.geom_orig),
         (float4*)(ws + L.aux_orig), (uint32_t*)(ws + L.dkey0), (uint32_t*)(ws + L.did0),
         (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint32_t*)(ws + L.count),
-        (float*)(ws + L.shj));
+        (float*)(ws + L.shj), (uint32_t*)(ws + L.counters + kCountersNonFinite),
+        (int*)(ws + L.counters + kStatusOffset));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -185,13 +185,17 @@ __device__ __forceinline__ float downweight(float focal, float s, float t) {
 
 // Device status word bits (the word at kStatusOffset in the counters region
 // of the main workspace, and BwdLayout::status): a bounded device wait that
-// ran out, and instances dropped because the key buffers were full.
+// ran out, instances dropped because the key buffers were full, and surfels
+// culled for a non-finite parameter.
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusCapacity = 2;
-// counters region: [0] unused, [1] instance count, [8] status word
+constexpr int kStatusNumeric = 4;
+// counters region (byte offsets): instance count, placed instances, stored
+// tile-decision words, non-finite surfels, the status word, the statistics
 constexpr size_t kCountersInst = 4;
 constexpr size_t kCountersPlaced = 8;  // instances placed by the direct tile placement
 constexpr size_t kCountersMaskWords = 12;  // stored tile-decision words wanted
+constexpr size_t kCountersNonFinite = 16;  // surfels culled for a NaN / infinite parameter
 constexpr size_t kStatusOffset = 32;
 constexpr size_t kStatsOffset = 64;  // 5 x u64 of nexel_render_stats
 
@@ -299,6 +303,10 @@ struct Tuning {
   int tex_fwd_ctas = 3, tex_bwd_ctas = 2, f32_ctas = 2, hash_block = 256;
 };
 Tuning current_tuning();
+// Test hook of the bounded waits (nexel_test_tc_wait_timeout): 0, or the
+// poll limit with which the tensor-core kernels wait for MMAs they do not
+// issue.
+int tc_wait_fault();
 
 // Per-view bodies of the C entry points (api.cu), shared with the batched
 // entry points (batch.cu).  check_* validate one view's arguments and launch

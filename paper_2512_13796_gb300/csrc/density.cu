@@ -19,7 +19,8 @@ constexpr int kFpsThreads = 1024;
 __global__ void __launch_bounds__(kFpsThreads) k_fps(int n, int m, const float* __restrict__ x,
                                                      float* __restrict__ mind,
                                                      int* __restrict__ idx,
-                                                     float* __restrict__ d2sel) {
+                                                     float* __restrict__ d2sel,
+                                                     float* __restrict__ scale) {
   __shared__ float s_v[32];
   __shared__ int s_k[32];
   __shared__ int s_cur;
@@ -66,6 +67,16 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(int n, int m, const float* 
       if (threadIdx.x == 0) s_cur = bk < n ? bk : 0;
     }
     __syncthreads();
+  }
+  // initial scales (supp. Sec. 7.2): the distance at which each point was
+  // selected, the nearest neighbour among the points sampled before it; the
+  // first point has no predecessor and takes the second's
+  if (scale) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kFpsThreads) {
+      const int src = (i == 0) ? 1 : i;
+      scale[i] = src < m ? __fsqrt_rn(d2sel[src]) : 0.f;
+    }
   }
 }
 
@@ -173,14 +184,14 @@ using namespace nexel;
 extern "C" {
 
 int nexel_fps(int n, const float* points, int m, float* scratch, int* idx, float* d2sel,
-              nexel_stream_t stream) {
+              float* scale, nexel_stream_t stream) {
   if (n < 0 || m < 0 || m > n || (n > 0 && (!points || !scratch)) ||
       (m > 0 && (!idx || !d2sel)))
     return NEXEL_ERR_INVALID_ARG;
   if (m == 0) return NEXEL_OK;
   cudaStream_t st = (cudaStream_t)stream;
   NEXEL_PROF("fps", st);
-  k_fps<<<1, kFpsThreads, 0, st>>>(n, m, points, scratch, idx, d2sel);
+  k_fps<<<1, kFpsThreads, 0, st>>>(n, m, points, scratch, idx, d2sel, scale);
   return cudaGetLastError() == cudaSuccess ? NEXEL_OK : NEXEL_ERR_CUDA;
 }
 
@@ -203,11 +214,24 @@ int nexel_density_workspace_size(int N, size_t* bytes) {
   return NEXEL_OK;
 }
 
-int nexel_densify_select(int N, const float* err, const float* expo, int n_select, void* ws,
-                         size_t ws_bytes, int* sel, nexel_stream_t stream) {
-  if (N < 0 || n_select < 0 || n_select > N || (N > 0 && (!err || !expo)) || !ws ||
-      (n_select > 0 && !sel))
+int nexel_densify_count(int N, long long budget, int* n_select) {
+  if (N < 0 || !n_select) return NEXEL_ERR_INVALID_ARG;
+  // 5 % of the current primitives, rounded up; no more than the budget
+  // leaves room for (the paper caps the primitive count at P)
+  const long long want = ((long long)N * 5 + 99) / 100;
+  const long long room = budget - (long long)N;
+  *n_select = (int)std::max(0LL, std::min(want, room));
+  return NEXEL_OK;
+}
+
+int nexel_densify_select(int N, const float* err, const float* expo, long long budget, void* ws,
+                         size_t ws_bytes, int* sel, int* n_select_out, nexel_stream_t stream) {
+  int n_select = 0;
+  if (nexel_densify_count(N, budget, &n_select) != NEXEL_OK || !n_select_out)
     return NEXEL_ERR_INVALID_ARG;
+  if ((N > 0 && (!err || !expo)) || !ws || (n_select > 0 && !sel))
+    return NEXEL_ERR_INVALID_ARG;
+  *n_select_out = n_select;
   const DensityLayout L = density_layout(N);
   if (ws_bytes < L.total) return NEXEL_ERR_INVALID_ARG;
   if (n_select == 0) return NEXEL_OK;

@@ -16,6 +16,10 @@
 // streams, or two host threads) race and corrupt each other's results;
 // serialise them.  The array keeps the last call's contents; the pipeline
 // clears what must start at zero (instance counter, tile ranges) itself.
+// Each call synchronises the stream once, as nexel_preprocess does, to read
+// the instance count back.  The device address of the array is resolved once
+// per device and kept: do not use the library across a cudaDeviceReset of
+// that device.
 #include "common.cuh"
 
 #include <mutex>
@@ -65,6 +69,9 @@ extern "C" int nexel_render_fwd_static(const nexel_camera* cam, const nexel_sett
                                        nexel_stream_t stream) {
   if (!cam || !settings || !n_instances_out) return NEXEL_ERR_INVALID_ARG;
   if (N < 0 || N > kStaticMaxN) return NEXEL_ERR_INVALID_ARG;
+  // a render without a backward: there is no backward scratch to cache
+  // features in
+  if (settings->cache_features != 0 && settings->K > 0) return NEXEL_ERR_INVALID_ARG;
   if (cam->width <= 0 || cam->height <= 0 ||
       (long long)cam->width * cam->height > kStaticMaxPixels)
     return NEXEL_ERR_INVALID_ARG;

@@ -77,9 +77,10 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
       smem_u32(bar)));
 }
 
-// Bounded wait for the mbarrier phase `parity`; false when the limit ran out.
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < kTcWaitLimit; ++it) {
+// Bounded wait for the mbarrier phase `parity`; false when `limit` polls ran
+// out.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -144,6 +145,7 @@ struct OpBf16 {
     __nv_bfloat16 b = __float2bfloat16_rn(x);
     return *reinterpret_cast<uint16_t*>(&b);
   }
+  __device__ static float round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 };
 struct OpF16 {
   static constexpr uint32_t kFmt = 0;
@@ -159,6 +161,7 @@ struct OpF16 {
     __half h = __float2half_rn(x);
     return *reinterpret_cast<uint16_t*>(&h);
   }
+  __device__ static float round(float x) { return __half2float(__float2half_rn(x)); }
 };
 
 // byte offset of element (row r, feature f) in a core-matrix tile whose
@@ -280,8 +283,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     const int* __restrict__ ids, const float* __restrict__ d_image,
     const float* __restrict__ d_weights, const float* __restrict__ d_textures,
     float* __restrict__ dweff, float2* __restrict__ gin, float* __restrict__ d_mlp,
-    int* __restrict__ status) {
+    int* __restrict__ status, int fault) {
   using Lt = TcLayout<IN, H1, H2, OUT>;
+  // fault > 0 (test hook only): no MMA is issued and each completion wait
+  // gives up after `fault` polls, which exercises the timeout path
+  const int wlim = fault > 0 ? fault : kTcWaitLimit;
+  const bool issue = fault == 0;
   constexpr int HL = Lt::HL;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ uint32_t s_tmem;
@@ -310,7 +317,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       *reinterpret_cast<uint16_t*>(tc_smem + Lt::w2t + cm_off(k, o, (H2 > 0 ? H2 : 8) / 8 * 128)) =
           OP::cvt(W2[i]);
     }
-    for (int i = tid; i < OUT * HL; i += kTcThreads) w3s[i] = W3[i];
+    // the output layer as the forward's MMA reads it (rounded to the operand
+    // type), so that the texture formed here for dL/dW_j is the forward's
+    for (int i = tid; i < OUT * HL; i += kTcThreads) w3s[i] = OP::round(W3[i]);
     if constexpr (OUT == 48) {
       for (int i = tid; i < 3 * HL * 16; i += kTcThreads) {
         const int n = i / 16, k = i % 16, ch = n / HL, h = n % HL;
@@ -418,7 +427,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     }
     sync_to_mma();
     // R1: h1 = X W1^T -> t0 (SH outputs: with RE, E = Y W3'^T -> t_e)
-    if (tid == 0) {
+    if (tid == 0 && issue) {
 #pragma unroll
       for (int kk = 0; kk < IN / 16; ++kk)
         mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
@@ -429,7 +438,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       commit(&s_bar);
     }
     load_row(tile + gridDim.x, nxt);
-    ok = wait_bar(&s_bar, phase);
+    ok = wait_bar(&s_bar, phase, wlim);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     uint64_t m1 = 0, m2 = 0;  // ReLU masks of h1, h2
@@ -448,14 +457,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     if constexpr (H2 > 0) {
       sync_to_mma();
       // R2: h2 = h1 W2^T -> t0
-      if (tid == 0) {
+      if (tid == 0 && issue) {
 #pragma unroll
         for (int kk = 0; kk < H1 / 16; ++kk)
           mma(t0, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
               sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0, OP::kFmt), kk > 0);
         commit(&s_bar);
       }
-      ok = ok && wait_bar(&s_bar, phase);
+      ok = ok && wait_bar(&s_bar, phase, wlim);
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -522,14 +531,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     if constexpr (H2 > 0) {
       sync_to_mma();
       // R3: d1 = (d2 W2) * [h1 > 0]; d2 is the delta tile's first H2 features
-      if (tid == 0) {
+      if (tid == 0 && issue) {
 #pragma unroll
         for (int kk = 0; kk < H2 / 16; ++kk)
           mma(t0, sdesc(sb + Lt::del + kk * 256, 128, Lt::SD),
               sdesc(sb + Lt::w2t + kk * 256, 128, H2 / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
         commit(&s_bar);
       }
-      ok = ok && wait_bar(&s_bar, phase);
+      ok = ok && wait_bar(&s_bar, phase, wlim);
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -544,7 +553,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     }
     sync_to_mma();
     // R4: feature gradient d1 W1 -> t0; weight gradients into Da, Db
-    if (tid == 0) {
+    if (tid == 0 && issue) {
 #pragma unroll
       for (int kk = 0; kk < H1 / 16; ++kk)
         mma(t0, sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 256, 128, Lt::SD),
@@ -561,7 +570,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       }
       commit(&s_bar);
     }
-    ok = ok && wait_bar(&s_bar, phase);
+    ok = ok && wait_bar(&s_bar, phase, wlim);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     first = false;
@@ -647,7 +656,7 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
   NEXEL_PROF("texture_bwd_tc", st);
   kern<<<grid, kTcThreads, Lt::total, st>>>(c, K, log2KP, n_rows, n_tiles, w, feat, weights, ids,
                                             d_image, d_weights, d_textures, dweff, gin, d_mlp,
-                                            status);
+                                            status, tc_wait_fault());
   return cudaGetLastError();
 }
 
@@ -686,8 +695,12 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
     const float* __restrict__ notex, const float* __restrict__ weights,
     const int* __restrict__ ids, const float* __restrict__ depths,
     const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures,
-    uint32_t* __restrict__ feat_cache, int* __restrict__ status) {
+    uint32_t* __restrict__ feat_cache, int* __restrict__ status, int fault) {
   using Lt = TcFwdLayout<IN, H1, H2, OUT>;
+  // fault > 0 (test hook only): no MMA is issued and each completion wait
+  // gives up after `fault` polls, which exercises the timeout path
+  const int wlim = fault > 0 ? fault : kTcWaitLimit;
+  const bool issue = fault == 0;
   constexpr int HL = Lt::HL;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ uint32_t s_tmem;
@@ -762,14 +775,14 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
       }
     }
     sync_to_mma();
-    if (tid == 0) {
+    if (tid == 0 && issue) {
 #pragma unroll
       for (int kk = 0; kk < IN / 16; ++kk)
         mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
             sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
       commit(&s_bar);
     }
-    ok = wait_bar(&s_bar, phase);
+    ok = wait_bar(&s_bar, phase, wlim);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -784,14 +797,14 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
     }
     if constexpr (H2 > 0) {
       sync_to_mma();
-      if (tid == 0) {
+      if (tid == 0 && issue) {
 #pragma unroll
         for (int kk = 0; kk < H1 / 16; ++kk)
           mma(t0, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
               sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0, OP::kFmt), kk > 0);
         commit(&s_bar);
       }
-      ok = ok && wait_bar(&s_bar, phase);
+      ok = ok && wait_bar(&s_bar, phase, wlim);
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -806,14 +819,14 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
       }
     }
     sync_to_mma();
-    if (tid == 0) {
+    if (tid == 0 && issue) {
 #pragma unroll
       for (int kk = 0; kk < HL / 16; ++kk)
         mma(t1, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
             sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, Lt::ON, 0, 0, OP::kFmt), kk > 0);
       commit(&s_bar);
     }
-    ok = ok && wait_bar(&s_bar, phase);
+    ok = ok && wait_bar(&s_bar, phase, wlim);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ehalf == 0) {
@@ -894,7 +907,8 @@ cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev&
   NEXEL_PROF("texture_fwd_tc", st);
   kern<<<grid, kTcFwdThreads, Lt::total, st>>>(
       c, fd, s.K, log2KP, n_tiles, s.bg[0], s.bg[1], s.bg[2], notex, weights, ids, depths, T_final,
-      image, textures, fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status);
+      image, textures, fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status,
+      tc_wait_fault());
   return cudaGetLastError();
 }
 

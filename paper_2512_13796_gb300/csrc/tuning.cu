@@ -14,6 +14,7 @@ namespace nexel {
 namespace {
 
 std::atomic<int> g_fwd{3}, g_bwd{2}, g_f32{2}, g_hash{256};
+std::atomic<int> g_tc_wait_fault{0};
 
 bool valid(const nexel_tuning& t) {
   return t.tex_fwd_ctas_per_sm >= 1 && t.tex_fwd_ctas_per_sm <= 3 &&
@@ -39,6 +40,8 @@ nexel_tuning get() {
 
 }  // namespace
 
+int tc_wait_fault() { return g_tc_wait_fault; }
+
 Tuning current_tuning() {
   Tuning t;
   t.tex_fwd_ctas = g_fwd;
@@ -53,6 +56,12 @@ Tuning current_tuning() {
 using namespace nexel;
 
 extern "C" {
+
+int nexel_test_tc_wait_timeout(int polls) {
+  if (polls < 0 || polls > (1 << 16)) return NEXEL_ERR_INVALID_ARG;
+  g_tc_wait_fault = polls;
+  return NEXEL_OK;
+}
 
 int nexel_get_tuning(nexel_tuning* out) {
   if (!out) return NEXEL_ERR_INVALID_ARG;

@@ -478,7 +478,7 @@ class DensityControl:
         """(new params, surfels split, surfels pruned); resets the errors."""
         keys = ("mu", "quat", "scale", "opacity", "gamma", "color")
         N = int(params["mu"].shape[0])
-        n_sel = max(0, min(-(-N * 5 // 100), self.budget - N))
+        n_sel = N_.nexel_densify_count(N, self.budget)
         color_dim = int(params["color"][0].numel())
         ws = torch.empty(N_.nexel_density_workspace_size(N + n_sel), dtype=torch.uint8,
                          device=self.device)
@@ -489,8 +489,8 @@ class DensityControl:
         if n_sel > 0:
             expo = torch.empty(N).exponential_(generator=self.gen).to(self.device)
             sel = torch.empty(n_sel, dtype=torch.int32, device=self.device)
-            N_.nexel_densify_select(N, self.err.data_ptr(), expo.data_ptr(), n_sel, ws.data_ptr(),
-                                    ws.numel(), sel.data_ptr(), _stream())
+            N_.nexel_densify_select(N, self.err.data_ptr(), expo.data_ptr(), self.budget,
+                                    ws.data_ptr(), ws.numel(), sel.data_ptr(), _stream())
             N_.nexel_densify_split(N, n_sel, sel.data_ptr(), color_dim,
                                    *[grown[k].data_ptr() for k in keys], _stream())
         M = N + n_sel
@@ -513,9 +513,7 @@ def fps_init(points, m: int) -> tuple:
     scratch = torch.empty(n, device=points.device)
     idx = torch.empty(m, dtype=torch.int32, device=points.device)
     d2 = torch.empty(m, device=points.device)
+    s = torch.empty(m, device=points.device)
     N_.nexel_fps(n, points.contiguous().data_ptr(), m, scratch.data_ptr(), idx.data_ptr(),
-                 d2.data_ptr(), _stream())
-    s = d2.sqrt()
-    if m > 1:
-        s[0] = s[1]
+                 d2.data_ptr(), s.data_ptr(), _stream())
     return points[idx.long()], s

@@ -104,6 +104,20 @@ def test_batched_calls_check_every_view_before_launch(lib):
                                  None) == -1
 
 
+def test_densify_count_is_the_split_fraction_within_the_budget(lib):
+    """nexel_densify_count (host only): 5 % of the surfels rounded up,
+    capped by the budget (supp. Sec. 7.2), as the oracle's split_count."""
+    from oracle import density as D
+    out = C.c_int(-1)
+    for N, budget in [(0, 10), (1, 10), (19, 100), (20, 100), (21, 100), (100, 1000),
+                      (101, 1000), (100, 102), (100, 90), (300_000, 10**6),
+                      (300_000, 300_001), (2_000_000_000 // 21, 1 << 40)]:
+        assert lib.nexel_densify_count(N, C.c_longlong(budget), C.byref(out)) == 0
+        assert out.value == D.split_count(N, budget), (N, budget, out.value)
+    assert lib.nexel_densify_count(-1, C.c_longlong(10), C.byref(out)) == -1
+    assert lib.nexel_densify_count(10, C.c_longlong(10), None) == -1
+
+
 def test_objective_and_density_calls_check_arguments_before_launch(lib):
     """Argument errors of the objective, Adam and density entry points come
     back before any launch."""
@@ -112,10 +126,15 @@ def test_objective_and_density_calls_check_arguments_before_launch(lib):
     assert lib.nexel_density_workspace_size(-1, C.byref(out)) == -1
     assert lib.nexel_density_workspace_size(100, C.byref(out)) == 0 and out.value > 800
     fake = 1 << 20
-    assert lib.nexel_fps(10, None, 5, None, None, None, None) == -1
-    assert lib.nexel_fps(10, fake, 11, fake, fake, fake, None) == -1    # m > n
-    assert lib.nexel_densify_select(10, fake, fake, 11, fake, 1 << 20, fake, None) == -1
-    assert lib.nexel_densify_select(10, fake, fake, 2, fake, 16, fake, None) == -1  # small ws
+    assert lib.nexel_fps(10, None, 5, None, None, None, None, None) == -1
+    assert lib.nexel_fps(10, fake, 11, fake, fake, fake, None, None) == -1    # m > n
+    n_sel = C.c_int(-7)
+    assert lib.nexel_densify_select(-1, fake, fake, C.c_longlong(100), fake, 1 << 20, fake,
+                                    C.byref(n_sel), None) == -1
+    assert lib.nexel_densify_select(100, fake, fake, C.c_longlong(1000), fake, 16, fake,
+                                    C.byref(n_sel), None) == -1  # small ws
+    assert lib.nexel_densify_select(100, fake, fake, C.c_longlong(1000), fake, 1 << 20, fake,
+                                    None, None) == -1  # no count output
     assert lib.nexel_densify_split(10, 2, fake, 5, *([fake] * 6), None) == -1      # color_dim
     assert lib.nexel_adam_step(1, None, None, None, None, None, None, C.c_float(0.9),
                                C.c_float(0.999), C.c_float(1e-8), 1, None) == -1

@@ -5,19 +5,25 @@ a radius-3 sphere, K = 4, BF16 form; the 8 views' backward passes
 accumulate into one set of gradients (accumulate = 1), compared with the
 sum of the oracle's per-view gradients.
 Config 4 (large-scene form): 1M surfels, 1920x1080, K = 8, BF16 form, with
-the top-K/depth buffers recomputed inside the backward."""
+the top-K/depth buffers recomputed inside the backward.
+Colours within 2e-3 of the oracle at the FP32 parameters; gradients per
+element against the oracle at the parameters the BF16 form reads, with the
+bound of test_gpu_parity.py (FP32 1e-3 relative plus 4 u of the summed
+contribution magnitudes, kinks cancelled, edge-on surfels' mu / quat left
+out)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2512_13796_gb300 import synth
 
-from helpers import compare_forward, compare_grads, gpu_params, SURFEL_KEYS
+from helpers import (SURFEL_KEYS, UNIT_ROUNDOFF, compare_forward, compare_grads, gpu_params,
+                     grad_stats, ill_conditioned, kink_cancelled_upstream, reference,
+                     reference_grads)
 
 pytestmark = pytest.mark.gpu
 
-TIE, CELL, RELU = 1e-5, 2e-6, 1e-4
-TOL_BF16, GRAD_L2_BF16 = 2e-3, 0.1  # see test_gpu_parity.py for the BF16 gradient bound
+TOL_BF16, GRAD_RTOL = 2e-3, 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -41,43 +47,41 @@ def _views(w, dev, recompute, n_pix, n_tiles, seed0):
     st = w.settings
     st_s = R.settings_struct(st, w.grid_dtype, w.mlp_dtype, recompute)
     grads = None
-    gr_sum = None
+    gr_sum, ga_sum = None, None
     stats = []
     for v, cam in enumerate(w.cameras):
         cam_s = R.camera_struct(cam)
         out = R.forward(ws, cam_s, st_s, fd, ts, fd.weights, *[p[k] for k in SURFEL_KEYS])
         pix = synth.pixel_sample(cam, n_pix, n_tiles, seed=seed0 + v)
-        ref = oracle.render(w.scene, cam, st, w.field, pix, tie_tol=TIE, cell_tol=CELL,
-                             relu_tol=RELU)
+        ref = reference(w.scene, cam, st, w.field, pix)
         fw = {k: (x.cpu().numpy() if hasattr(x, "cpu") else x) for k, x in out.items()}
         stats.append(compare_forward(fw, ref, st.K, TOL_BF16))
-        ok = ref["tie"] == 0
+        ref_b = reference(w.scene, cam, st, w.field, pix, mlp=w.mlp_dtype)
         P = cam.width * cam.height
-        rng = np.random.default_rng(seed0 + 100 + v)
-        dI = np.zeros((P, 3))
-        sel = pix[ok]
-        dI[sel] = rng.normal(size=(sel.size, 3))
+        dI, dW, dT, sel, _ = kink_cancelled_upstream(ref_b, P, st.K, seed0 + 100 + v)
+        t = lambda a: torch.from_numpy(a).to(dev)
         grads = R.backward(ws, cam_s, st_s, fd, ts, fd.weights, *[p[k] for k in SURFEL_KEYS[:5]],
-                           out, torch.from_numpy(dI.astype(np.float32)).to(dev),
-                           accumulate=grads is not None, grads=grads)
-        gr = oracle.render_bwd(w.scene, cam, st, w.field, sel, dI[sel])
+                           out, t(dI), t(dW), t(dT), accumulate=grads is not None, grads=grads)
+        gr, ga = reference_grads(w.scene, cam, st, w.field, sel, dI, dW, dT, w.mlp_dtype)
         gr_sum = gr if gr_sum is None else {k: gr_sum[k] + gr[k] for k in gr if k != "mlp_layers"}
+        ga_sum = ga if ga_sum is None else {k: ga_sum[k] + ga[k] for k in ga}
     torch.cuda.synchronize()
     gg = {k: x.cpu().numpy() for k, x in grads.items()}
-    return stats, gg, gr_sum
+    skip = np.unique(np.concatenate([ill_conditioned(w.scene, c) for c in w.cameras]))
+    s = compare_grads(gg, gr_sum, GRAD_RTOL, absolute=ga_sum, u=UNIT_ROUNDOFF[w.mlp_dtype],
+                      skip_surfels=skip)
+    return stats, s, skip.size
 
 
 def test_config3_batched_views_accumulate(dev):
     w = synth.workload(3)
-    stats, gg, gr = _views(w, dev, False, 256, 1, 300)
-    s = compare_grads(gg, gr, GRAD_L2_BF16, metric="l2")
+    stats, s, n_skip = _views(w, dev, False, 256, 1, 300)
     print(f"\n[config3 8 views] ties={[x['n_tie'] for x in stats]} "
-          f"image_err={max(x['image'] for x in stats):.2e} grads={s}")
+          f"image_err={max(x['image'] for x in stats):.2e} edge-on skipped={n_skip} grads={s}")
 
 
 def test_config4_large_scene_recompute(dev):
     w = synth.workload(4)
-    stats, gg, gr = _views(w, dev, True, 768, 1, 400)
-    s = compare_grads(gg, gr, GRAD_L2_BF16, metric="l2")
+    stats, s, n_skip = _views(w, dev, True, 768, 1, 400)
     print(f"\n[config4 1M 1080p K=8 recompute] ties={stats[0]['n_tie']}/{stats[0]['n_pix']} "
-          f"image_err={stats[0]['image']:.2e} grads={s}")
+          f"image_err={stats[0]['image']:.2e} edge-on skipped={n_skip} grads={s}")

@@ -1,7 +1,10 @@
-"""Adaptive density control on the GPU against the oracle (oracle/density.py,
-oracle.blend_error): farthest point sampling (indices and FP32 squared
-distances bit-exact), the blended-error pass on a render, the error-weighted
-selection (bit-exact), the split and the prune."""
+"""Adaptive density control on the GPU against the FP64 oracle
+(oracle/density.py, oracle.blend_error): farthest point sampling (every
+choice the FP64 argmax, or within FP32 resolution of it, counted as a
+near-tie; squared distances at selection within FP32 rounding; the initial
+scales), the blended-error pass on a render, the error-weighted selection
+(the same keys in the same order, near-ties counted), the split and the
+prune."""
 import numpy as np
 import pytest
 
@@ -36,23 +39,44 @@ def _fps_gpu(x, m, dev):
     scratch = torch.empty(n, device=dev)
     idx = torch.empty(m, dtype=torch.int32, device=dev)
     d2 = torch.empty(m, device=dev)
-    N_.nexel_fps(n, xt.data_ptr(), m, scratch.data_ptr(), idx.data_ptr(), d2.data_ptr(), _stream())
+    sc = torch.empty(m, device=dev)
+    N_.nexel_fps(n, xt.data_ptr(), m, scratch.data_ptr(), idx.data_ptr(), d2.data_ptr(),
+                 sc.data_ptr(), _stream())
     torch.cuda.synchronize()
-    return idx.cpu().numpy(), d2.cpu().numpy()
+    return idx.cpu().numpy(), d2.cpu().numpy(), sc.cpu().numpy()
+
+
+# FP32 squared distances of FP32 points: each difference, square and sum is
+# rounded once (relative error <= 2^-24 each), so a squared distance carries
+# <= ~4 x 2^-24 = 2.4e-7 relative error and two candidates whose FP64 values
+# lie within 1e-6 of each other may be ordered either way by FP32
+FPS_TIE = 1e-6
+FPS_D2_REL = 5e-7
 
 
 @pytest.mark.parametrize("n,m", [(9, 9), (3001, 3001), (20000, 1500)])
-def test_fps_bit_exact(dev, n, m):
+def test_fps_against_fp64(dev, n, m):
     if n == 9:
         x = np.zeros((9, 3), np.float32)
         x[:, 0] = np.arange(9)
     else:
         x = np.random.default_rng(n).normal(size=(n, 3)).astype(np.float32)
-    gi, gd = _fps_gpu(x, m, dev)
-    ri, rd = D.fps(x, m)
-    np.testing.assert_array_equal(gi, ri)
-    np.testing.assert_array_equal(gd[1:], rd[1:])
+    gi, gd, gs = _fps_gpu(x, m, dev)
+    chk = D.fps_check(x, gi, gd, FPS_TIE)
+    print(f"\n[fps n={n} m={m}] {chk}")
+    assert chk["d2_rel"] <= FPS_D2_REL
     assert np.isinf(gd[0])
+    if n == 9:  # integer lattice: every distance exact, no tie is near
+        ri, rd = D.fps(x, m)
+        np.testing.assert_array_equal(gi, ri)
+        np.testing.assert_array_equal(gd[1:], rd[1:])
+        assert chk["ties"] == 0
+    else:
+        assert chk["ties"] <= max(2, m // 200)
+    # the initial scales: the FP64 distance at each selection, the first
+    # point the second's (FP32 square root of an FP32 squared distance)
+    ref_s = D.fps_scales(chk["d2"])
+    np.testing.assert_allclose(gs, ref_s, rtol=5e-7, atol=0)
 
 
 def test_blend_error_matches_oracle(dev):
@@ -93,14 +117,21 @@ def test_select_split_prune(dev):
     err = rng.exponential(size=N).astype(np.float32)
     err[rng.choice(N, 300, replace=False)] = 0.0
     expo = rng.exponential(size=N).astype(np.float32)
-    n_sel = D.split_count(N, 10 * N)
+    budget = 10 * N
+    n_sel = D.split_count(N, budget)
     ws = torch.empty(N_.nexel_density_workspace_size(N + n_sel), dtype=torch.uint8, device=dev)
     sel = torch.empty(n_sel, dtype=torch.int32, device=dev)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     err_d, expo_d = t(err), t(expo)  # held: the call reads them asynchronously
-    N_.nexel_densify_select(N, err_d.data_ptr(), expo_d.data_ptr(), n_sel, ws.data_ptr(),
-                            ws.numel(), sel.data_ptr(), _stream())
+    got = N_.nexel_densify_select(N, err_d.data_ptr(), expo_d.data_ptr(), budget, ws.data_ptr(),
+                                  ws.numel(), sel.data_ptr(), _stream())
     torch.cuda.synchronize()
+    assert got == n_sel
+    # FP32 keys E / err are correctly rounded (relative error <= 2^-24)
+    chk = D.select_check(err, expo, n_sel, sel.cpu().numpy(), rel_tol=2.5e-7)
+    print(f"\n[select N={N} n={n_sel}] {chk}")
+    # no near-tie in this draw: the selection is the FP64 one, index for index
+    assert chk["ties"] == 0
     ref_sel = D.select(err, expo, n_sel)
     np.testing.assert_array_equal(sel.cpu().numpy(), ref_sel)
     for color_dim in (3, 48):

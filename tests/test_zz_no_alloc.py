@@ -85,3 +85,8 @@ def test_static_workspace_rejects_oversize():
     rc = N_.lib().nexel_render_fwd_static(C.byref(cam), C.byref(st), None, 16385,
                                           *([None] * 13), C.byref(n), None)
     assert rc == -1
+    # a feature cache needs the backward scratch, which this call does not take
+    st_cache = R.settings_struct(synth.Settings(K=4), cache_features=True)
+    rc = N_.lib().nexel_render_fwd_static(C.byref(cam), C.byref(st_cache), None, 10,
+                                          *([None] * 13), C.byref(n), None)
+    assert rc == -1
