@@ -210,10 +210,11 @@ class Job:
                 "f32_ctas_per_sm": best.f32_ctas_per_sm, "hash_block": best.hash_block,
                 "tuned_step_ms": ms}
 
-    def step(self):
-        out = self.forward(self.st_train)
+    def step(self, st_s=None):
+        st_s = st_s or self.st_train
+        out = self.forward(st_s)
         p = self.p
-        self.grads = self.R.backward(self.ws, self.cam_s, self.st_train, self.field, self.ts,
+        self.grads = self.R.backward(self.ws, self.cam_s, st_s, self.field, self.ts,
                                      self.wts,
                                      p["mu"], p["quat"], p["scale"], p["opacity"], p["gamma"], out,
                                      self.d_image, grads=self.grads)
@@ -388,6 +389,136 @@ def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, wo
     return out
 
 
+def key_layout(N: int, width: int, height: int) -> dict:
+    """The binning's key layout for N surfels on a width x height view (as
+    the library derives it): 16 x 16 tiles; 32-bit (tile, depth rank) keys
+    when tile and rank bits fit, else 64-bit; direct placement for 32-bit
+    keys and at most 8192 tiles, else the LSD tile sort."""
+    tiles = ((width + 15) // 16) * ((height + 15) // 16)
+    tile_bits = max(1, (tiles - 1).bit_length())
+    rank_bits = max(1, (N - 1).bit_length())
+    key64 = tile_bits + rank_bits > 32
+    return {"tiles": tiles, "tile_bits": tile_bits, "key64": key64,
+            "placement": (not key64) and tiles <= 8192, "tile_passes": (tile_bits + 7) // 8}
+
+
+def sort_rooflines(prof: dict, steps: int, N: int, n_inst: int, layout: dict, peaks: dict,
+                   peak_kind: str) -> dict:
+    """HBM roofline of the binning's sorts, from live per-kernel events.
+    The depth sort: N (key, value) pairs, 4 passes of 8 bits; per pair and
+    pass the histogram reads the 4 B key and the scatter reads and writes
+    key and value: 20 B.  The LSD tile sort (64-bit keys or more than 8192
+    tiles): n_inst keys, ceil(tile_bits / 8) passes, 3 key widths per key
+    and pass.  The direct placement's writer: 4 B key written per instance
+    and 16 B of rank data read per surfel (its stored tile decisions are
+    the library's own cache and not counted)."""
+    out = {}
+    hb = peaks["hbm_gbs"]
+    t_sort = sum(prof[k][0] for k in ("radix_hist", "radix_scatter") if k in prof) / steps
+    if t_sort > 0:
+        kb = 8 if layout["key64"] else 4
+        tile_b = 0 if layout["placement"] else n_inst * layout["tile_passes"] * 3 * kb
+        by = N * 4 * 20 + tile_b
+        A = by / (t_sort * 1e-3) / 1e9
+        out["radix_sort"] = {
+            "kernel": "radix_hist + radix_scatter", "ms_per_step": t_sort, "bound": "hbm",
+            "achieved": A, "peak": hb, "unit": "GB/s", "frac": A / hb,
+            "peak_source": f"hbm_gbs ({peak_kind})", "bytes_per_step": by,
+            "keys": {"depth_sort": N, "tile_sort": 0 if layout["placement"] else n_inst},
+            "passes": {"depth_sort": 4, "tile_sort": 0 if layout["placement"]
+                       else layout["tile_passes"]},
+            "mean_tiles_per_surfel": n_inst / max(N, 1)}
+    if "place_write" in prof:
+        t = prof["place_write"][0] / steps
+        by = n_inst * 4 + N * 16
+        A = by / (t * 1e-3) / 1e9
+        out["place_write"] = {
+            "kernel": "place_write", "ms_per_step": t, "bound": "hbm", "achieved": A,
+            "peak": hb, "unit": "GB/s", "frac": A / hb, "peak_source": f"hbm_gbs ({peak_kind})",
+            "bytes_per_step": by, "instances": n_inst,
+            "note": "the writer is bound by its shared-memory rank masks, not by HBM"}
+    return out
+
+
+def config1_leg(dev, steps, flush, stream, agg) -> dict:
+    """Config 1 (50k surfels, 800x800, K = 4, hash 8 x 2^16 x 2, MLP 16-64-3):
+    the BF16 and FP32 train steps and render FPS."""
+    from paper_2512_13796_gb300 import synth
+    w = synth.workload(1)
+    P = w.cameras[0].width * w.cameras[0].height
+    out = {"workload": "config1: 50k surfels (10 planes), 800x800, K=4, hash 8x2^16x2, "
+                       "MLP 16-64-3"}
+    for prec in ("bf16", "f32"):
+        j = Job(w, dev, prec)
+        for _ in range(3):
+            j.step()
+        t = agg(timed(j.step, steps, flush, stream))
+        f = agg(timed(j.forward, steps, flush, stream))
+        out[prec] = {"train_mpix_s": P / (t * 1e-3) / 1e6, "train_ms": t,
+                     "render_fps": 1e3 / f, "render_ms": f}
+        del j
+    return out
+
+
+def config4_leg(dev, steps, flush, stream, agg, peaks, peak_kind) -> dict:
+    """Config 4 (1M surfels, 1920x1080, K = 8, hash 16 x 2^20 x 2 FP16, BF16
+    MLP): the train step with the per-pixel buffers I, W, D, T_final stored
+    between forward and backward against the one that recomputes them in
+    the backward (time, and the memory each holds), and the inference-only
+    render FPS."""
+    import torch
+    from paper_2512_13796_gb300 import render as R
+    from paper_2512_13796_gb300 import synth
+    w = synth.workload(4)
+    cam = w.cameras[0]
+    P, K = cam.width * cam.height, w.settings.K
+    j = Job(w, dev, "bf16")
+    st_rc = R.settings_struct(w.settings, "f16", "bf16", recompute=True, cache_features=True)
+    res = {"workload": "config4: 1M surfels (box room + facades), 1920x1080, K=8, "
+                       "hash 16x2^20x2 FP16, MLP 32-64-64-3 BF16"}
+    fs = j.field.struct(j.ts, j.wts)
+    from paper_2512_13796_gb300 import _native as N_
+    bws_stored = N_.nexel_bwd_workspace_size(j.cam_s, j.st_train, fs)
+    bws_rc = N_.nexel_bwd_workspace_size(j.cam_s, st_rc, fs)
+    for name, st_s in (("stored", j.st_train), ("recompute", st_rc)):
+        for _ in range(3):
+            j.step(st_s)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats(dev)
+        base = torch.cuda.memory_allocated(dev)
+        t = agg(timed(lambda: j.step(st_s), steps, flush, stream))
+        peak = torch.cuda.max_memory_allocated(dev)
+        res[name] = {"train_ms": t, "train_mpix_s": P / (t * 1e-3) / 1e6,
+                     "peak_allocated_bytes": int(peak), "resident_before_step_bytes": int(base)}
+    res["stored"]["held_between_fwd_and_bwd_bytes"] = P * K * (4 + 4 + 4) + P * 4
+    res["recompute"]["held_between_fwd_and_bwd_bytes"] = 0
+    res["stored"]["bwd_scratch_bytes"] = bws_stored
+    res["recompute"]["bwd_scratch_bytes"] = bws_rc
+    res["memory_note"] = ("held_between_fwd_and_bwd: the weights W, ids I, depths D [H][W][K] "
+                          "and T_final the stored variant's backward reads; the recompute "
+                          "variant's backward rebuilds them in its own scratch (bwd_scratch "
+                          "grows by that much), so a caller may drop or reuse the forward's "
+                          "copies once the loss has read them")
+    for _ in range(3):
+        j.forward()
+    f = agg(timed(j.forward, steps, flush, stream))
+    res["render"] = {"fps": 1e3 / f, "ms": f, "mpix_s": P / (f * 1e-3) / 1e6,
+                     "note": "inference forward only (preprocess, binning, collection, texturing, "
+                             "composite), no feature cache"}
+    N_.nexel_profile_enable(True)
+    timed(lambda: j.step(j.st_train), 3, flush, stream)
+    prof = N_.nexel_profile_read()
+    N_.nexel_profile_enable(False)
+    n_inst = j.fwd_out["n_instances"]
+    lay = key_layout(w.scene.n, cam.width, cam.height)
+    res["binning"] = {"instances": int(n_inst), "key64": lay["key64"],
+                      "path": "direct placement" if lay["placement"] else "LSD tile sort"}
+    res["rooflines"] = sort_rooflines(prof, 3, w.scene.n, n_inst, lay, peaks, peak_kind)
+    del j
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline(w, seconds_target: float = 15.0) -> dict:
     """The FP64 oracle as it stands, forward + backward on a pixel sample of
     the same view, on this host's cores."""
@@ -430,6 +561,10 @@ def main():
                     help="skip the batched 8-view form (600k surfels)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2],
                     help="2: the headline workload; 1: the 50k-surfel 800x800 case (profiling)")
+    ap.add_argument("--no-config1", action="store_true",
+                    help="skip the 50k-surfel 800x800 (config 1) train-step line")
+    ap.add_argument("--no-config4", action="store_true",
+                    help="skip the 1M-surfel 1080p K=8 (config 4) leg")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -534,7 +669,9 @@ def main():
     _native.nexel_profile_enable(False)
 
     def agg(ts):
-        return max_over_ranks(float(np.mean(ts)), dev, world)
+        # the median of the timed steps (the measurement plan's statistic),
+        # the slowest rank's
+        return max_over_ranks(float(np.median(ts)), dev, world)
 
     ms = {k: agg(v) for k, v in results.items()}
 
@@ -615,6 +752,20 @@ def main():
         barrier()
         clk_batch = cs.stop()
 
+    # the other configurations the measurement plan names, after the
+    # headline ones (each allocates its own scene and buffers)
+    legs = {}
+    if not args.no_config1 and args.config == 2:
+        legs["config1"] = config1_leg(dev, max(5, min(args.steps, 20)), flush, stream, agg)
+        torch.cuda.empty_cache()
+    if not args.no_config4:
+        cs4 = ClockSampler(local)
+        cs4.start()
+        legs["config4"] = config4_leg(dev, max(5, min(args.steps, 10)), flush, stream, agg,
+                                      peaks, peak_kind)
+        legs["config4"]["clocks"] = cs4.stop()
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -633,6 +784,9 @@ def main():
             more[kname] = roofline(prof, jobs["bf16"], peaks, peak_kind, args.steps,
                                    f"config{args.config}", kname, acct)
     n_inst = jobs["bf16"].fwd_out["n_instances"]
+    more.update(sort_rooflines(prof, args.steps, w.scene.n, n_inst,
+                               key_layout(w.scene.n, w.cameras[0].width, w.cameras[0].height),
+                               peaks, peak_kind))
     mpix = lambda m: whole_job_mpix(P, m, world)
     # the hash backward's real ceiling: L2 vector reductions.  Their rate is
     # measured here (random float2 reductions into a 64 MiB table, the size
@@ -682,23 +836,6 @@ def main():
                    "l2": "flushed (256 MB write) before every timed step",
                    "launch_tuning": tuning,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "forms": {
-            "bf16": {"train_mpix_s": mpix(ms["bf16_train"]), "train_ms": ms["bf16_train"],
-                     "render_fps": 1e3 / ms["bf16_fwd"], "render_ms": ms["bf16_fwd"]},
-            "f32": {"train_mpix_s": mpix(ms["f32_train"]), "train_ms": ms["f32_train"],
-                    "render_fps": 1e3 / ms["f32_fwd"], "render_ms": ms["f32_fwd"]},
-            "f16_mlp_loss_scaled": {"train_mpix_s": mpix(ms["f16_train"]),
-                                    "train_ms": ms["f16_train"],
-                                    "render_fps": 1e3 / ms["f16_fwd"],
-                                    "render_ms": ms["f16_fwd"]},
-            "paper_sh3_f16": {"train_mpix_s": mpix(ms["sh_f16_train"]),
-                              "train_ms": ms["sh_f16_train"],
-                              "render_fps": 1e3 / ms["sh_f16_fwd"],
-                              "render_ms": ms["sh_f16_fwd"],
-                              "note": "the paper's configuration: degree-3 SH for both "
-                                      "appearance modes (48 coefficients per surfel, MLP "
-                                      "32-64-64-48), FP16 table, FP16 MLP with loss scale 128"},
-        },
         "full_training_iteration": {
             "train_mpix_s": mpix(ms["bf16_full"]), "train_ms": ms["bf16_full"],
             "note": "BF16 form: forward + the paper's objective (L1, D-SSIM, texture, alpha, "
@@ -726,7 +863,9 @@ def main():
         "e2e": {"value": mpix(e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4,
                 "path": "render() autograd API: H2D target, forward, L1 loss, backward, D2H loss; "
-                        "no L2 flush between steps"},
+                        "no L2 flush between steps; the surfel parameters, hash table and MLP "
+                        "stay resident on the device across steps, as in training (only the "
+                        "target image and the loss cross the bus)"},
         "e2e_graph": {"value": mpix(e2e_graph_ms), "unit": "Mpix/s", "ms_per_step": e2e_graph_ms,
                       "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4,
                       "path": "render.BatchStep graph API (one view): H2D target, one CUDA graph "
@@ -735,6 +874,25 @@ def main():
         "gpu_launches": int(launches),
         "gpu_launches_note": "kernels of libnexel per timed step (library launch counter)",
         "clocks": clk,
+        "statistic": "median of the timed steps (CUDA events), max over ranks",
+        "configs": legs,
+        "forms": {
+            "bf16": {"train_mpix_s": mpix(ms["bf16_train"]), "train_ms": ms["bf16_train"],
+                     "render_fps": 1e3 / ms["bf16_fwd"], "render_ms": ms["bf16_fwd"]},
+            "f32": {"train_mpix_s": mpix(ms["f32_train"]), "train_ms": ms["f32_train"],
+                    "render_fps": 1e3 / ms["f32_fwd"], "render_ms": ms["f32_fwd"]},
+            "f16_mlp_loss_scaled": {"train_mpix_s": mpix(ms["f16_train"]),
+                                    "train_ms": ms["f16_train"],
+                                    "render_fps": 1e3 / ms["f16_fwd"],
+                                    "render_ms": ms["f16_fwd"]},
+            "paper_sh3_f16": {"train_mpix_s": mpix(ms["sh_f16_train"]),
+                              "train_ms": ms["sh_f16_train"],
+                              "render_fps": 1e3 / ms["sh_f16_fwd"],
+                              "render_ms": ms["sh_f16_fwd"],
+                              "note": "the paper's configuration: degree-3 SH for both "
+                                      "appearance modes (48 coefficients per surfel, MLP "
+                                      "32-64-64-48), FP16 table, FP16 MLP with loss scale 128"},
+        },
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
