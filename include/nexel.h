@@ -387,7 +387,7 @@ int nexel_prune(int N, float threshold, int color_dim, const float* mu, const fl
 
 /* Launch-shape tuning (process-wide; no counterpart in the paper): CTAs
  * per SM that the persistent texturing kernels keep in flight -- the tile
- * pipeline depth of the tcgen05 forward (1..3, default 3), of the tcgen05
+ * pipeline depth of the tcgen05 forward (1..2, default 2), of the tcgen05
  * backward (1..2, default 2; 1 where its shared memory allows one) and of
  * the FP32 chunked kernels (1..2, default 2) -- and the CTA size of the
  * hash backward (128 or 256, default 256).  Every choice computes the same

@@ -300,7 +300,7 @@ cudaError_t exclusive_scan_u32(uint32_t* a, long long n, uint32_t* sums, uint32_
 // process-wide: CTAs per SM of the persistent texturing kernels and the CTA
 // size of the hash backward.
 struct Tuning {
-  int tex_fwd_ctas = 3, tex_bwd_ctas = 2, f32_ctas = 2, hash_block = 256;
+  int tex_fwd_ctas = 2, tex_bwd_ctas = 2, f32_ctas = 2, hash_block = 256;
 };
 Tuning current_tuning();
 // Test hook of the bounded waits (nexel_test_tc_wait_timeout): 0, or the

@@ -107,6 +107,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane (one wait)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
   asm volatile(
@@ -661,73 +678,125 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
 }
 
 // ------------------------------------------------------------- forward
-// Texturing forward on tcgen05 (Eqs. 3-4 and the composite of Eq. 6).  A
-// CTA of 256 threads owns 128-row tiles (128 / KP pixels x KP slots).
-// Gather: thread t handles half t / 128 of the levels of one row; within a
-// warp the lanes are consecutive pixels of one slot, so at coarse levels
-// neighbouring lanes read the same table entries.  The down-weighted
-// features go to shared memory as the BF16 A operand (and, in a training
-// step, to the feature cache); then up to three MMA rounds (X W1^T,
-// h1 W2^T, h_last W3^T) with ReLU epilogues, the last one writing the
-// textures and the composite.  Epilogues split the columns between warps w
-// and w + 4 (which share TMEM lanes).
+// Texturing forward on tcgen05 (Eqs. 3-4 and the composite of Eq. 6), warp
+// specialised.  A CTA of 12 warps walks a sequence of 128-row tiles (128 / KP
+// pixels x KP slots):
+//   warps 0-7 gather: thread t handles half t / 128 of the levels of one row;
+//     within a warp the lanes are consecutive pixels of one slot, so at
+//     coarse levels neighbouring lanes read the same table entries.  The
+//     down-weighted features go, as the A operand, into a ring of kFwStages
+//     shared-memory stages (and, in a training step, to the feature cache).
+//     A stage is handed to the MLP warps through an mbarrier (`full`) and
+//     handed back by the completion of the MMA that reads it (`empty`, a
+//     tcgen05 commit), so the gather runs up to kFwStages tiles ahead and
+//     never waits for the MLP's round trips.
+//   warps 8-11 MLP: warp 8 + q owns TMEM lanes 32 q .. 32 q + 31 (= rows); one
+//     thread issues X W1^T, h1 W2^T and h_last W3^T with FP32 accumulators in
+//     TMEM; the four warps run the ReLU epilogues (TMEM -> the hidden tile in
+//     shared memory, h2 overwriting h1) and the last epilogue writes the
+//     textures and the composite.
+// Every mbarrier wait is bounded: a wait that runs out sets the status word
+// and ends the CTA's loops (the TMEM is freed before the kernel returns).
+constexpr int kFwGatherWarps = 8;
+constexpr int kFwThreads = (kFwGatherWarps + 4) * 32;
+constexpr int kFwStages = 4;
+constexpr int kTcFwdCols = 128;
+
 template <int IN, int H1, int H2, int OUT = 3>
 struct TcFwdLayout {
   static constexpr int HL = H2 > 0 ? H2 : H1;
-  static constexpr int ON = OUT == 3 ? 16 : 48;       // output-layer MMA columns
-  // features X, then the hidden layer (h2 overwrites h1 once R2 has read it)
-  static constexpr int FA = IN + (H1 > H2 ? H1 : H2);
-  static constexpr int SA = FA / 8 * 128;
-  static constexpr int act = 0;
-  static constexpr int w1 = act + kTcRows / 8 * SA;   // [H1][IN]
+  static constexpr int ON = OUT == 3 ? 16 : 48;  // output-layer MMA columns
+  static constexpr int HM = H1 > H2 ? H1 : H2;   // hidden-tile features
+  static constexpr int SX = IN / 8 * 128;        // bytes per 8-row group of a stage
+  static constexpr int SHd = HM / 8 * 128;       // ... of the hidden tile
+  static constexpr int xstage = kTcRows / 8 * SX;
+  static constexpr int xring = 0;
+  static constexpr int hid = xring + kFwStages * xstage;
+  static constexpr int w1 = hid + kTcRows / 8 * SHd;  // [H1][IN]
   static constexpr int w2 = w1 + H1 * IN * 2;         // [H2][H1]
   static constexpr int w3 = w2 + H2 * H1 * 2;         // [ON][HL], rows OUT.. zero
   static constexpr int total = w3 + ON * HL * 2;
   static_assert(ON <= 64, "the output layer uses TMEM columns 64 .. 127");
+  static_assert(HM == 64, "hidden layers of 64 units");
 };
 
-constexpr int kTcFwdThreads = 256;
-constexpr int kTcFwdCols = 128;
+// Consumer-group (the four MLP warps) hand-over to the MMA-issuing thread:
+// their shared-memory stores and TMEM reads happen before the MMAs issued
+// next.
+__device__ __forceinline__ void mlp_warps_sync() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// AND of `v` over the four MLP warps (a named-barrier reduction).
+__device__ __forceinline__ bool mlp_warps_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, 1, 128, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <typename OP>
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  return make_uint4(OP::pack2(v[0], v[1]), OP::pack2(v[2], v[3]), OP::pack2(v[4], v[5]),
+                    OP::pack2(v[6], v[7]));
+}
 
 template <int IN, int H1, int H2, typename TT, typename OP, int OUT = 3>
-__global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
+__global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
     DevCam c, FieldDev f, int K, int log2KP, long long n_tiles, float bg0, float bg1, float bg2,
     const float* __restrict__ notex, const float* __restrict__ weights,
     const int* __restrict__ ids, const float* __restrict__ depths,
     const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures,
     uint32_t* __restrict__ feat_cache, int* __restrict__ status, int fault) {
   using Lt = TcFwdLayout<IN, H1, H2, OUT>;
+  constexpr int HL = Lt::HL;
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_full[kFwStages];
+  __shared__ __align__(8) uint64_t s_empty[kFwStages];
+  __shared__ __align__(8) uint64_t s_mma;
   // fault > 0 (test hook only): no MMA is issued and each completion wait
   // gives up after `fault` polls, which exercises the timeout path
   const int wlim = fault > 0 ? fault : kTcWaitLimit;
   const bool issue = fault == 0;
-  constexpr int HL = Lt::HL;
-  extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_bar;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  unsigned char* act = tc_smem + Lt::act;
   {
     const float* W1 = f.w;
     const float* W2 = f.w + H1 * IN;
     const float* W3 = W2 + H2 * H1;
-    for (int i = tid; i < H1 * IN; i += kTcFwdThreads)
+    for (int i = tid; i < H1 * IN; i += kFwThreads)
       *reinterpret_cast<uint16_t*>(tc_smem + Lt::w1 + cm_off(i / IN, i % IN, IN / 8 * 128)) =
           OP::cvt(W1[i]);
-    for (int i = tid; i < H2 * H1; i += kTcFwdThreads)
+    for (int i = tid; i < H2 * H1; i += kFwThreads)
       *reinterpret_cast<uint16_t*>(tc_smem + Lt::w2 + cm_off(i / H1, i % H1, H1 / 8 * 128)) =
           OP::cvt(W2[i]);
-    for (int i = tid; i < Lt::ON * HL; i += kTcFwdThreads) {
+    for (int i = tid; i < Lt::ON * HL; i += kFwThreads) {
       const int o = i / HL, k = i % HL;
       *reinterpret_cast<uint16_t*>(tc_smem + Lt::w3 + cm_off(o, k, HL / 8 * 128)) =
           OP::cvt(o < OUT ? W3[o * HL + k] : 0.f);
     }
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
+    for (int s = 0; s < kFwStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_full[s])),
+                   "r"(kFwGatherWarps * 32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mma)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == kFwGatherWarps) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&s_tmem)),
                  "r"(kTcFwdCols));
@@ -739,16 +808,20 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
   const uint32_t sb = smem_u32(tc_smem);
   const int KP = 1 << log2KP, PPT = kTcRows >> log2KP;
   const long long P = (long long)c.W * c.H;
-  // epilogue role: TMEM lanes 32 (warp % 4) .., column half warp / 4
-  const int erow = 32 * (warp & 3) + lane, ehalf = warp >> 2;
-  const uint32_t elane = (uint32_t)(32 * (warp & 3)) << 16;
-  // gather role: row (pixel tt % PPT, slot tt / PPT), levels of half gh
-  const int tt = tid & (kTcRows - 1), gh = tid >> 7;
-  const int grow = (tt % PPT) * KP + tt / PPT;
-  uint32_t phase = 0;
-  bool ok = true;
-  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    {
+
+  if (warp < kFwGatherWarps) {
+    // ------------------------------------------------------- gather warps
+    const int tt = tid & (kTcRows - 1), gh = tid >> 7;
+    const int grow = (tt % PPT) * KP + tt / PPT;
+    int i = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int st = i % kFwStages, use = i / kFwStages;
+      // the MMA that read this stage kFwStages tiles ago has completed
+      if (use > 0 && !wait_bar(&s_empty[st], (uint32_t)((use - 1) & 1), wlim)) {
+        if (tid == 0 && status) atomicOr(status, kStatusTimeout);
+        break;
+      }
+      unsigned char* xs = tc_smem + Lt::xring + st * Lt::xstage;
       const long long p = tile * PPT + tt % PPT;
       const int j = tt / PPT;
       const bool in_pix = p < P && j < K;
@@ -767,73 +840,108 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
         float v[8];
         gather4_tc<TT>(f, gh * LH + 4 * g8, x, D, valid, v);
         const int f0 = gh * (IN / 2) + 8 * g8;
-        st8<OP>(act, grow, f0, Lt::SA, v);
-        if (feat_cache && p < P) {
-          const uint4 q4 = *reinterpret_cast<const uint4*>(act + cm_off(grow, f0, Lt::SA));
+        const uint4 q4 = pack8<OP>(v);
+        *reinterpret_cast<uint4*>(xs + cm_off(grow, f0, Lt::SX)) = q4;
+        if (feat_cache && p < P)
           reinterpret_cast<uint4*>(feat_cache + (size_t)(tile * kTcRows + grow) * (IN / 2))[f0 / 8] = q4;
-        }
+      }
+      // the stage's generic stores become visible to the MMA (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_arrive(&s_full[st]);
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------- MLP warps
+  const int q = warp - kFwGatherWarps;  // TMEM lane quadrant (= warp % 4)
+  const int erow = 32 * q + lane;
+  const uint32_t elane = (uint32_t)(32 * q) << 16;
+  const bool leader = tid == kFwGatherWarps * 32;
+  uint32_t mph = 0;
+  bool ok = true;
+  int i = 0;
+  unsigned char* hid = tc_smem + Lt::hid;
+  for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
+    const int st = i % kFwStages, use = i / kFwStages;
+    // this row's composite inputs, fetched before the MMA waits
+    const long long p = tile * PPT + erow / KP;
+    const int j = erow & (KP - 1);
+    const bool in_pix = p < P && j < K;
+    const long long s = p * K + j;
+    int id = -1;
+    float wj = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f, Tf = 0.f;
+    if (in_pix) {
+      id = ids[s];
+      wj = weights[s];
+    }
+    if (j == 0 && p < P) {
+      n0 = notex[3 * p]; n1 = notex[3 * p + 1]; n2 = notex[3 * p + 2];
+      Tf = T_final[p];
+    }
+    // R1: h1 = X W1^T -> t0; its completion also frees the stage
+    if (leader) {
+      const bool got = wait_bar(&s_full[st], (uint32_t)(use & 1), wlim);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (got && issue) {
+        const uint32_t xa = sb + Lt::xring + st * Lt::xstage;
+#pragma unroll
+        for (int kk = 0; kk < IN / 16; ++kk)
+          mma(t0, sdesc(xa + kk * 256, 128, Lt::SX), sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128),
+              idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
+        commit(&s_mma);
+        commit(&s_empty[st]);
       }
     }
-    sync_to_mma();
-    if (tid == 0 && issue) {
-#pragma unroll
-      for (int kk = 0; kk < IN / 16; ++kk)
-        mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
-            sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
-      commit(&s_bar);
-    }
-    ok = wait_bar(&s_bar, phase, wlim);
-    phase ^= 1u;
+    ok = wait_bar(&s_mma, mph, wlim);
+    mph ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-    for (int c16 = 0; c16 < H1 / 32; ++c16) {
-      float v[16];
-      const int col = ehalf * (H1 / 2) + 16 * c16;
-      tmem_ld16(t0 + elane + col, v);
+    for (int c32 = 0; c32 < H1 / 32; ++c32) {
+      float v[32];
+      tmem_ld32(t0 + elane + 32 * c32, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-      st8<OP>(act, erow, IN + col, Lt::SA, v);
-      st8<OP>(act, erow, IN + col + 8, Lt::SA, v + 8);
+      for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k], 0.f);
+#pragma unroll
+      for (int k8 = 0; k8 < 4; ++k8)
+        *reinterpret_cast<uint4*>(hid + cm_off(erow, 32 * c32 + 8 * k8, Lt::SHd)) = pack8<OP>(v + 8 * k8);
     }
+    mlp_warps_sync();
     if constexpr (H2 > 0) {
-      sync_to_mma();
-      if (tid == 0 && issue) {
+      // R2: h2 = h1 W2^T -> t0 (h2 then overwrites h1 in the hidden tile)
+      if (leader && ok && issue) {
 #pragma unroll
         for (int kk = 0; kk < H1 / 16; ++kk)
-          mma(t0, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
+          mma(t0, sdesc(sb + Lt::hid + kk * 256, 128, Lt::SHd),
               sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0, OP::kFmt), kk > 0);
-        commit(&s_bar);
+        commit(&s_mma);
       }
-      ok = ok && wait_bar(&s_bar, phase, wlim);
-      phase ^= 1u;
+      ok = ok && wait_bar(&s_mma, mph, wlim);
+      mph ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int c16 = 0; c16 < H2 / 32; ++c16) {
-        float v[16];
-        const int col = ehalf * (H2 / 2) + 16 * c16;
-        tmem_ld16(t0 + elane + col, v);
+      for (int c32 = 0; c32 < H2 / 32; ++c32) {
+        float v[32];
+        tmem_ld32(t0 + elane + 32 * c32, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-        st8<OP>(act, erow, IN + col, Lt::SA, v);
-        st8<OP>(act, erow, IN + col + 8, Lt::SA, v + 8);
+        for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k], 0.f);
+#pragma unroll
+        for (int k8 = 0; k8 < 4; ++k8)
+          *reinterpret_cast<uint4*>(hid + cm_off(erow, 32 * c32 + 8 * k8, Lt::SHd)) = pack8<OP>(v + 8 * k8);
       }
+      mlp_warps_sync();
     }
-    sync_to_mma();
-    if (tid == 0 && issue) {
+    // R3: outputs h_last W3^T -> t1
+    if (leader && ok && issue) {
 #pragma unroll
       for (int kk = 0; kk < HL / 16; ++kk)
-        mma(t1, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
+        mma(t1, sdesc(sb + Lt::hid + kk * 256, 128, Lt::SHd),
             sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, Lt::ON, 0, 0, OP::kFmt), kk > 0);
-      commit(&s_bar);
+      commit(&s_mma);
     }
-    ok = ok && wait_bar(&s_bar, phase, wlim);
-    phase ^= 1u;
+    ok = ok && wait_bar(&s_mma, mph, wlim);
+    mph ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ehalf == 0) {
-      const long long p = tile * PPT + erow / KP;
-      const int j = erow & (KP - 1);
-      const bool in_pix = p < P && j < K;
-      const long long s = p * K + j;
+    {
       float o3[3];
       if constexpr (OUT == 3) {
         float v[16];
@@ -848,17 +956,18 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
           float v[16];
           tmem_ld16(t1 + elane + 16 * c16, v);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int o = 16 * c16 + i;
-            o3[o % 3] = fmaf(Y.y[o / 3], v[i], o3[o % 3]);
+          for (int k = 0; k < 16; ++k) {
+            const int o = 16 * c16 + k;
+            o3[o % 3] = fmaf(Y.y[o / 3], v[k], o3[o % 3]);
           }
         }
       }
-      float wj = 0.f, T0 = 0.f, T1 = 0.f, T2 = 0.f;
+      float T0 = 0.f, T1 = 0.f, T2 = 0.f;
       if (in_pix) {
-        if (ids[s] >= 0) {
-          wj = weights[s];
+        if (id >= 0) {
           T0 = o3[0]; T1 = o3[1]; T2 = o3[2];
+        } else {
+          wj = 0.f;
         }
         textures[3 * s] = T0; textures[3 * s + 1] = T1; textures[3 * s + 2] = T2;
       }
@@ -869,20 +978,19 @@ __global__ void __launch_bounds__(kTcFwdThreads, 3) k_tex_fwd_tc(
         c2 += __shfl_xor_sync(0xffffffffu, c2, dd);
       }
       if (j == 0 && p < P) {
-        const float Tf = T_final[p];
-        image[3 * p] = notex[3 * p] + c0 + Tf * bg0;
-        image[3 * p + 1] = notex[3 * p + 1] + c1 + Tf * bg1;
-        image[3 * p + 2] = notex[3 * p + 2] + c2 + Tf * bg2;
+        image[3 * p] = n0 + c0 + Tf * bg0;
+        image[3 * p + 1] = n1 + c1 + Tf * bg1;
+        image[3 * p + 2] = n2 + c2 + Tf * bg2;
       }
     }
-    // the next tile's gather overwrites the operand tile
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(ok) != 0;
+    // a wait that ran out on any MLP thread ends the loop for all four warps
+    ok = mlp_warps_and(ok);
   }
-  if (!ok && tid == 0 && status) atomicOr(status, kStatusTimeout);
+  if (!ok && q == 0 && lane == 0 && status) atomicOr(status, kStatusTimeout);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcFwdCols));
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+  if (warp == kFwGatherWarps)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcFwdCols));
 }
 
 template <int IN, int H1, int H2, typename TT, typename OP, int OUT = 3>
@@ -905,17 +1013,18 @@ cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev&
   const unsigned grid =
       (unsigned)std::min<long long>(n_tiles, (long long)current_tuning().tex_fwd_ctas * nsm);
   NEXEL_PROF("texture_fwd_tc", st);
-  kern<<<grid, kTcFwdThreads, Lt::total, st>>>(
+  kern<<<grid, kFwThreads, Lt::total, st>>>(
       c, fd, s.K, log2KP, n_tiles, s.bg[0], s.bg[1], s.bg[2], notex, weights, ids, depths, T_final,
-      image, textures, fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status,
-      tc_wait_fault());
+      image, textures, fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status, tc_wait_fault());
   return cudaGetLastError();
 }
+
+constexpr int kGatherThreads = 256;
 
 // Feature pass of a backward without cached features: the gather of the
 // forward (same lane layout and arithmetic), written to the feature buffer.
 template <int IN, typename TT, typename OP>
-__global__ void __launch_bounds__(kTcFwdThreads) k_gather_tc(DevCam c, FieldDev f, int K, int log2KP,
+__global__ void __launch_bounds__(kGatherThreads) k_gather_tc(DevCam c, FieldDev f, int K, int log2KP,
                                                            long long n_tiles, const int* __restrict__ ids,
                                                            const float* __restrict__ depths,
                                                            uint32_t* __restrict__ feat) {
@@ -957,7 +1066,7 @@ cudaError_t gather_tc(const DevCam& c, const nexel_settings& s, const FieldDev& 
   const long long n_tiles = (rows + kTcRows - 1) / kTcRows;
   if (n_tiles == 0) return cudaSuccess;
   NEXEL_PROF("texture_gather_tc", st);
-  k_gather_tc<IN, TT, OP><<<(unsigned)n_tiles, kTcFwdThreads, 0, st>>>(c, fd, s.K, log2KP, n_tiles,
+  k_gather_tc<IN, TT, OP><<<(unsigned)n_tiles, kGatherThreads, 0, st>>>(c, fd, s.K, log2KP, n_tiles,
                                                                       ids, depths, feat);
   return cudaGetLastError();
 }

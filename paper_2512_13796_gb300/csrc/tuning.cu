@@ -13,11 +13,11 @@
 namespace nexel {
 namespace {
 
-std::atomic<int> g_fwd{3}, g_bwd{2}, g_f32{2}, g_hash{256};
+std::atomic<int> g_fwd{2}, g_bwd{2}, g_f32{2}, g_hash{256};
 std::atomic<int> g_tc_wait_fault{0};
 
 bool valid(const nexel_tuning& t) {
-  return t.tex_fwd_ctas_per_sm >= 1 && t.tex_fwd_ctas_per_sm <= 3 &&
+  return t.tex_fwd_ctas_per_sm >= 1 && t.tex_fwd_ctas_per_sm <= 2 &&
          t.tex_bwd_ctas_per_sm >= 1 && t.tex_bwd_ctas_per_sm <= 2 && t.f32_ctas_per_sm >= 1 &&
          t.f32_ctas_per_sm <= 2 && (t.hash_block == 128 || t.hash_block == 256);
 }
@@ -142,7 +142,7 @@ int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
   // one knob after another, keeping the best value of each
   for (int knob = 0; knob < 4 && rc == NEXEL_OK; ++knob) {
     std::vector<int> vals;
-    if (knob == 0) vals = {1, 2, 3};
+    if (knob == 0) vals = {1, 2};
     else if (knob == 1) vals = {1, 2};
     else if (knob == 2) vals = {1, 2};
     else vals = {128, 256};

@@ -148,13 +148,13 @@ def test_objective_and_density_calls_check_arguments_before_launch(lib):
 def test_tuning_round_trip_and_checks(lib):
     t0 = N_.nexel_get_tuning()
     assert (t0.tex_fwd_ctas_per_sm, t0.tex_bwd_ctas_per_sm, t0.f32_ctas_per_sm,
-            t0.hash_block) == (3, 2, 2, 256)
+            t0.hash_block) == (2, 2, 2, 256)
     t = N_.Tuning(1, 1, 1, 128)
     N_.nexel_set_tuning(t)
     g = N_.nexel_get_tuning()
     assert (g.tex_fwd_ctas_per_sm, g.tex_bwd_ctas_per_sm, g.f32_ctas_per_sm, g.hash_block) == \
         (1, 1, 1, 128)
-    for bad in (N_.Tuning(0, 1, 1, 128), N_.Tuning(4, 1, 1, 128), N_.Tuning(1, 3, 1, 128),
+    for bad in (N_.Tuning(0, 1, 1, 128), N_.Tuning(3, 1, 1, 128), N_.Tuning(1, 3, 1, 128),
                 N_.Tuning(1, 1, 1, 64)):
         assert lib.nexel_set_tuning(C.byref(bad)) == -1
     N_.nexel_set_tuning(t0)

@@ -47,7 +47,7 @@ def test_autotune_and_tuning_invariance(dev):
     t0 = N_.nexel_get_tuning()
     results = []
     try:
-        for t in (N_.Tuning(3, 2, 2, 256), N_.Tuning(1, 1, 1, 128)):
+        for t in (N_.Tuning(2, 2, 2, 256), N_.Tuning(1, 1, 1, 128)):
             N_.nexel_set_tuning(t)
             results.append(_step(dev, w, fd, p, dI))
         (o1, g1, ws, cam_s, st_s), (o2, g2, _, _, _) = results
