@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
     const float rr = fD * f.inv_s[l];  // cell size in pixels at depth D
     // Eq. 3: Delta = 1 - exp(-r^2 / 2pi), r = f / (s D)
-    const float dw = -expm1f(-rr * rr * 0.15915494309189535f);
+    const float dw = one_minus_exp_neg(rr * rr * 0.15915494309189535f);
     // per-axis parts of the spatial hash (MapPositive, times the primes)
     const uint32_t hx[2] = {map_pos(cx), map_pos(cx + 1)};
     const uint32_t hy[2] = {map_pos(cy) * 2654435761u, map_pos(cy + 1) * 2654435761u};

@@ -196,65 +196,52 @@ __device__ __forceinline__ void st8(unsigned char* base, int r, int f0, int sg, 
 }
 
 // Features of levels l0 .. l0 + 3 at x (Eqs. 3-4): all 32 corner loads are
-// issued before any is used.
+// issued before any is used.  The spatial hash of a corner is the XOR of
+// per-axis parts (MapPositive, times the axis's prime), formed once per
+// axis value; a row that is not textured reads the entries around the
+// origin (valid addresses, harmless) and gets a zero down-weighting.
 template <typename TT>
 __device__ __forceinline__ void gather4_tc(const FieldDev& f, int l0, float3 x, float t, bool valid,
                                            float (&v)[8]) {
   using R = RawEntry<TT>;
   typename R::T e[4][8];
   float fr[4][3], dw[4];
+  const TT* tab = reinterpret_cast<const TT*>(f.table);
+  const uint32_t T2 = 2u * (f.mask + 1u);  // elements per level
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int l = l0 + q;
-    const TT* tl = reinterpret_cast<const TT*>(f.table) + (size_t)l * ((size_t)f.mask + 1) * 2;
+    const TT* tl = tab + (size_t)((uint32_t)l * T2);
     const float s = f.s[l];
     const float gx = s * x.x, gy = s * x.y, gz = s * x.z;
     const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
     const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
     fr[q][0] = gx - fx0; fr[q][1] = gy - fy0; fr[q][2] = gz - fz0;
-    dw[q] = downweight(f.focal, s, t);
+    dw[q] = valid ? downweight(f.focal, s, t) : 0.f;
+    const uint32_t hx0 = map_pos(cx), hx1 = map_pos(cx + 1);
+    const uint32_t hy0 = map_pos(cy) * 2654435761u, hy1 = map_pos(cy + 1) * 2654435761u;
+    const uint32_t hz0 = map_pos(cz) * 805459861u, hz1 = map_pos(cz + 1) * 805459861u;
+    const uint32_t yz[4] = {hy0 ^ hz0, hy1 ^ hz0, hy0 ^ hz1, hy1 ^ hz1};
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      e[q][k] = valid ? R::load(tl, hash3(cx + (k & 1), cy + ((k >> 1) & 1), cz + ((k >> 2) & 1), f.mask))
-                      : R::zero();
+      e[q][k] = R::load(tl, (((k & 1) ? hx1 : hx0) ^ yz[k >> 1]) & f.mask);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const float rx = fr[q][0], ry = fr[q][1], rz = fr[q][2];
+    const float wx[2] = {1.f - rx, rx};
+    const float wyz[4] = {(1.f - ry) * (1.f - rz), ry * (1.f - rz), (1.f - ry) * rz, ry * rz};
     float ax = 0.f, ay = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-      const float w = (dx ? rx : 1.f - rx) * (dy ? ry : 1.f - ry) * (dz ? rz : 1.f - rz);
+      const float w = wx[k & 1] * wyz[k >> 1];
       const float2 ee = R::to2(e[q][k]);
       ax = fmaf(w, ee.x, ax);
       ay = fmaf(w, ee.y, ay);
     }
-    v[2 * q] = valid ? dw[q] * ax : 0.f;
-    v[2 * q + 1] = valid ? dw[q] * ay : 0.f;
+    v[2 * q] = dw[q] * ax;
+    v[2 * q + 1] = dw[q] * ay;
   }
-}
-
-// Down-weighted trilinear hash-grid feature pair of level l at x (Eqs. 3-4).
-template <typename TT>
-__device__ __forceinline__ float2 level_feature_tc(const FieldDev& f, int l, float3 x, float t) {
-  const TT* tl = reinterpret_cast<const TT*>(f.table) + (size_t)l * ((size_t)f.mask + 1) * 2;
-  const float s = f.s[l];
-  const float gx = s * x.x, gy = s * x.y, gz = s * x.z;
-  const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
-  const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
-  const float rx = gx - fx0, ry = gy - fy0, rz = gz - fz0;
-  float ax = 0.f, ay = 0.f;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-    const float w = (dx ? rx : 1.f - rx) * (dy ? ry : 1.f - ry) * (dz ? rz : 1.f - rz);
-    const float2 e = load_entry<TT>(tl, hash3(cx + dx, cy + dy, cz + dz, f.mask));
-    ax = fmaf(w, e.x, ax);
-    ay = fmaf(w, e.y, ay);
-  }
-  const float dw = downweight(f.focal, s, t);
-  return make_float2(dw * ax, dw * ay);
 }
 
 // OUT = 3 (RGB texture, output layer padded to ON = 16 MMA columns) or 48
@@ -861,6 +848,17 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
   bool ok = true;
   int i = 0;
   unsigned char* hid = tc_smem + Lt::hid;
+  // Completion of the MMAs just issued: the issuing thread polls the
+  // mbarrier, a named-barrier reduction releases the other MLP threads (who
+  // sleep instead of polling) and tells them whether the wait ran out.
+  auto mma_done = [&]() -> bool {
+    bool got = true;
+    if (leader) got = ok && wait_bar(&s_mma, mph, wlim);
+    mph ^= 1u;
+    got = mlp_warps_and(got);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return got;
+  };
   for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
     const int st = i % kFwStages, use = i / kFwStages;
     // this row's composite inputs, fetched before the MMA waits
@@ -892,9 +890,7 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
         commit(&s_empty[st]);
       }
     }
-    ok = wait_bar(&s_mma, mph, wlim);
-    mph ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = mma_done();
 #pragma unroll
     for (int c32 = 0; c32 < H1 / 32; ++c32) {
       float v[32];
@@ -915,9 +911,7 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
               sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0, OP::kFmt), kk > 0);
         commit(&s_mma);
       }
-      ok = ok && wait_bar(&s_mma, mph, wlim);
-      mph ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      ok = mma_done() && ok;
 #pragma unroll
       for (int c32 = 0; c32 < H2 / 32; ++c32) {
         float v[32];
@@ -938,9 +932,7 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
             sdesc(sb + Lt::w3 + kk * 256, 128, HL / 8 * 128), idesc(128, Lt::ON, 0, 0, OP::kFmt), kk > 0);
       commit(&s_mma);
     }
-    ok = ok && wait_bar(&s_mma, mph, wlim);
-    mph ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = mma_done() && ok;
     {
       float o3[3];
       if constexpr (OUT == 3) {
