@@ -371,19 +371,26 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     const int j = (int)(r & (KP - 1));
     in.s = p * K + j;
     in.in_pix = tile < n_tiles && r < n_rows && p < P && j < K;
-    in.valid = in.in_pix && ids[in.s] >= 0;
-    in.gT[0] = in.gT[1] = in.gT[2] = in.dC[0] = in.dC[1] = in.dC[2] = in.dWx = 0.f;
-    if (in.valid) {
-      const float w = weights[in.s];
+    // every load of the row is issued at once (none waits for the id):
+    // an empty slot's weight is 0, and its values are dropped below
+    int id = -1;
+    float w = 0.f, t0v = 0.f, t1v = 0.f, t2v = 0.f, dwv = 0.f;
+    in.dC[0] = in.dC[1] = in.dC[2] = 0.f;
+    if (in.in_pix) {
+      id = ids[in.s];
+      w = weights[in.s];
       in.dC[0] = d_image[3 * p]; in.dC[1] = d_image[3 * p + 1]; in.dC[2] = d_image[3 * p + 2];
-      in.gT[0] = w * in.dC[0]; in.gT[1] = w * in.dC[1]; in.gT[2] = w * in.dC[2];
       if (d_textures) {
-        in.gT[0] += d_textures[3 * in.s];
-        in.gT[1] += d_textures[3 * in.s + 1];
-        in.gT[2] += d_textures[3 * in.s + 2];
+        t0v = d_textures[3 * in.s]; t1v = d_textures[3 * in.s + 1]; t2v = d_textures[3 * in.s + 2];
       }
-      if (d_weights) in.dWx = d_weights[in.s];
+      if (d_weights) dwv = d_weights[in.s];
     }
+    in.valid = in.in_pix && id >= 0;
+    in.gT[0] = in.valid ? fmaf(w, in.dC[0], t0v) : 0.f;
+    in.gT[1] = in.valid ? fmaf(w, in.dC[1], t1v) : 0.f;
+    in.gT[2] = in.valid ? fmaf(w, in.dC[2], t2v) : 0.f;
+    in.dWx = in.valid ? dwv : 0.f;
+    if (!in.valid) in.dC[0] = in.dC[1] = in.dC[2] = 0.f;
     // cached BF16 features of this row; zero beyond the pixels
 #pragma unroll
     for (int c8 = 0; c8 < IN / 8; ++c8) {
