@@ -208,6 +208,7 @@ class Job:
         return {"tex_fwd_ctas_per_sm": best.tex_fwd_ctas_per_sm,
                 "tex_bwd_ctas_per_sm": best.tex_bwd_ctas_per_sm,
                 "f32_ctas_per_sm": best.f32_ctas_per_sm, "hash_block": best.hash_block,
+                "collect_batch": best.collect_batch, "tex_fwd_stages": best.tex_fwd_stages,
                 "tuned_step_ms": ms}
 
     def step(self, st_s=None):

@@ -389,9 +389,13 @@ int nexel_prune(int N, float threshold, int color_dim, const float* mu, const fl
  * per SM that the persistent texturing kernels keep in flight -- the tile
  * pipeline depth of the tcgen05 forward (1..2, default 2), of the tcgen05
  * backward (1..2, default 2; 1 where its shared memory allows one) and of
- * the FP32 chunked kernels (1..2, default 2) -- and the CTA size of the
- * hash backward (128 or 256, default 256).  Every choice computes the same
- * values; the weight-gradient and table-gradient sums may differ by
+ * the FP32 chunked kernels (1..2, default 2) -- the CTA size of the hash
+ * backward (128 or 256, default 256), the number of surfel records the
+ * collection kernels stage in shared memory per batch (128, 256 or 512,
+ * default 256; Sec. 3's tile-based rasterizer walks each 16 x 16 tile's
+ * list in such batches) and the depth of the tcgen05 forward's ring of
+ * operand tiles (2..4, default 4: how many tiles its gather warps may run
+ * ahead of its MMAs).  Every choice computes the same values; the weight-gradient and table-gradient sums may differ by
  * rounding (their atomic order).  nexel_autotune runs the caller's own
  * training step (preprocess once, then forward + backward per candidate,
  * `reps` timed steps after an untimed one, CUDA events on `stream`; with a
@@ -404,6 +408,7 @@ int nexel_prune(int N, float threshold, int color_dim, const float* mu, const fl
  * nexel_render_bwd (gradients are overwritten). */
 typedef struct {
   int tex_fwd_ctas_per_sm, tex_bwd_ctas_per_sm, f32_ctas_per_sm, hash_block;
+  int collect_batch, tex_fwd_stages;
 } nexel_tuning;
 int nexel_get_tuning(nexel_tuning* out);
 

@@ -96,7 +96,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 # ------------------------------------------------------------- C structs
 class Tuning(C.Structure):
     _fields_ = [("tex_fwd_ctas_per_sm", C.c_int), ("tex_bwd_ctas_per_sm", C.c_int),
-                ("f32_ctas_per_sm", C.c_int), ("hash_block", C.c_int)]
+                ("f32_ctas_per_sm", C.c_int), ("hash_block", C.c_int),
+                ("collect_batch", C.c_int), ("tex_fwd_stages", C.c_int)]
 
 
 class LossWeights(C.Structure):

@@ -25,15 +25,18 @@ __device__ __forceinline__ uint32_t rank_of(KeyT k, uint32_t mask) {
   return (uint32_t)k & mask;
 }
 
-template <int K, typename KeyT>
+// BATCH: surfel records staged per batch (128, 256 or 512; a launch-shape
+// knob of the autotuner: smaller batches test for early termination more
+// often, larger ones synchronise less).
+template <int K, typename KeyT, int BATCH>
 __global__ void __launch_bounds__(kTilePix) k_collect_fwd(
     DevCam c, float alpha_min, float alpha_max, float T_min, uint32_t rmask,
     const uint2* __restrict__ ranges, const KeyT* __restrict__ keys,
     const float4* __restrict__ recs, float* __restrict__ notex, float* __restrict__ weights,
     int* __restrict__ ids, float* __restrict__ depths, float* __restrict__ T_final,
     int* __restrict__ n_contrib) {
-  __shared__ float4 s_rec[kRecF4][kTilePix];
-  __shared__ uint32_t s_rank[kTilePix];
+  __shared__ float4 s_rec[kRecF4][BATCH];
+  __shared__ uint32_t s_rank[BATCH];
   const int tile = blockIdx.x;
   const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
@@ -48,18 +51,21 @@ __global__ void __launch_bounds__(kTilePix) k_collect_fwd(
   for (int k = 0; k < K; ++k) { Wk[k] = 0.f; Dk[k] = 0.f; Rk[k] = -1; }
   int last = 0;
   bool done = !inside;
-  for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kTilePix) {
+  for (uint32_t b0 = rg.x; b0 < rg.y; b0 += BATCH) {
     if (__syncthreads_count(done) == kTilePix) break;
-    uint32_t i = b0 + threadIdx.x;
-    if (i < rg.y) {
-      uint32_t r = rank_of(keys[i], rmask);
-      s_rank[threadIdx.x] = r;
-      const float4* src = recs + (size_t)r * kRecF4;
 #pragma unroll
-      for (int k = 0; k < kRecF4; ++k) s_rec[k][threadIdx.x] = __ldg(src + k);
+    for (int t = threadIdx.x; t < BATCH; t += kTilePix) {
+      const uint32_t i = b0 + t;
+      if (i < rg.y) {
+        uint32_t r = rank_of(keys[i], rmask);
+        s_rank[t] = r;
+        const float4* src = recs + (size_t)r * kRecF4;
+#pragma unroll
+        for (int k = 0; k < kRecF4; ++k) s_rec[k][t] = __ldg(src + k);
+      }
     }
     __syncthreads();
-    const int nb = (int)min((uint32_t)kTilePix, rg.y - b0);
+    const int nb = (int)min((uint32_t)BATCH, rg.y - b0);
     if (!done) {
       for (int j = 0; j < nb; ++j) {
         const float4 q0 = s_rec[0][j], q1 = s_rec[1][j], q2 = s_rec[2][j], q3 = s_rec[3][j];
@@ -158,7 +164,7 @@ __device__ __forceinline__ void warp_sum20_add(const float (&g)[kGradStride], fl
 
 // Four CTAs per SM (64 registers, no spills): the replay is issue-bound and
 // gains from the fourth tile in flight.
-template <int K, typename KeyT>
+template <int K, typename KeyT, int BATCH>
 __global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
     DevCam c, float alpha_min, float alpha_max, float bg0, float bg1, float bg2, uint32_t rmask,
     const uint2* __restrict__ ranges, const KeyT* __restrict__ keys,
@@ -166,9 +172,9 @@ __global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
     const int* __restrict__ n_contrib, const float* __restrict__ d_image,
     const float* __restrict__ dweff, const float* __restrict__ ddepth,
     const float4* __restrict__ aux, float* __restrict__ grad) {
-  __shared__ float4 s_rec[kRecF4][kTilePix];
-  __shared__ float4 s_aux[kAuxF4][kTilePix];
-  __shared__ uint32_t s_rank[kTilePix];
+  __shared__ float4 s_rec[kRecF4][BATCH];
+  __shared__ float4 s_aux[kAuxF4][BATCH];
+  __shared__ uint32_t s_rank[BATCH];
   __shared__ int s_max;
   const int tile = blockIdx.x;
   const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
@@ -204,18 +210,21 @@ __global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
   __syncthreads();
   const uint32_t list_end = rg.x + (uint32_t)s_max;
   for (uint32_t bend = list_end; bend > rg.x;) {
-    const uint32_t bstart = (bend - rg.x > (uint32_t)kTilePix) ? bend - kTilePix : rg.x;
+    const uint32_t bstart = (bend - rg.x > (uint32_t)BATCH) ? bend - BATCH : rg.x;
     __syncthreads();
-    uint32_t i = bstart + threadIdx.x;
-    if (i < bend) {
-      uint32_t r = rank_of(keys[i], rmask);
-      s_rank[threadIdx.x] = r;
-      const float4* src = recs + (size_t)r * kRecF4;
 #pragma unroll
-      for (int k = 0; k < kRecF4; ++k) s_rec[k][threadIdx.x] = __ldg(src + k);
-      const float4* asrc = aux + (size_t)r * kAuxF4;
+    for (int t = threadIdx.x; t < BATCH; t += kTilePix) {
+      const uint32_t i = bstart + t;
+      if (i < bend) {
+        uint32_t r = rank_of(keys[i], rmask);
+        s_rank[t] = r;
+        const float4* src = recs + (size_t)r * kRecF4;
 #pragma unroll
-      for (int k = 0; k < kAuxF4; ++k) s_aux[k][threadIdx.x] = __ldg(asrc + k);
+        for (int k = 0; k < kRecF4; ++k) s_rec[k][t] = __ldg(src + k);
+        const float4* asrc = aux + (size_t)r * kAuxF4;
+#pragma unroll
+        for (int k = 0; k < kAuxF4; ++k) s_aux[k][t] = __ldg(asrc + k);
+      }
     }
     __syncthreads();
     for (int j = (int)(bend - bstart) - 1; j >= 0; --j) {
@@ -305,10 +314,17 @@ static cudaError_t collect_fwd_t(const DevCam& c, const nexel_settings& s, char*
   auto* recs = (const float4*)(ws + L.geom_sorted);
   int* nc = (int*)(ws + L.n_contrib);
   NEXEL_PROF("collect_fwd", st);
-#define NEXEL_CF(KK)                                                                              \
-  k_collect_fwd<KK, KeyT><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.T_min, rmask, rg, \
-                                                  keys, recs, notex, weights, ids, depths,       \
-                                                  T_final, nc)
+  const int batch = current_tuning().collect_batch;
+#define NEXEL_CF1(KK, BB)                                                                         \
+  k_collect_fwd<KK, KeyT, BB><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.T_min, rmask, \
+                                                      rg, keys, recs, notex, weights, ids, depths, \
+                                                      T_final, nc)
+#define NEXEL_CF(KK)                                          \
+  do {                                                        \
+    if (batch == 128) NEXEL_CF1(KK, 128);                     \
+    else if (batch == 512) NEXEL_CF1(KK, 512);                \
+    else NEXEL_CF1(KK, 256);                                  \
+  } while (0)
   switch (s.K) {
     case 0: NEXEL_CF(0); break;
     case 1: NEXEL_CF(1); break;
@@ -322,6 +338,7 @@ static cudaError_t collect_fwd_t(const DevCam& c, const nexel_settings& s, char*
     default: return cudaErrorInvalidValue;
   }
 #undef NEXEL_CF
+#undef NEXEL_CF1
   return cudaGetLastError();
 }
 
@@ -351,10 +368,18 @@ static cudaError_t collect_bwd_t(const DevCam& c, const nexel_settings& s, char*
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * kGradStride * (size_t)L.N, st);
   if (e != cudaSuccess) return e;
   NEXEL_PROF("collect_bwd", st);
-#define NEXEL_CB(KK)                                                                               \
-  k_collect_bwd<KK, KeyT><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.bg[0], s.bg[1],  \
-                                                  s.bg[2], rmask, rg, keys, recs, ids, T_final,  \
-                                                  nc, d_image, dwe, ddp, aux, grad)
+  const int batch = current_tuning().collect_batch;
+#define NEXEL_CB1(KK, BB)                                                                        \
+  k_collect_bwd<KK, KeyT, BB><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.bg[0],     \
+                                                      s.bg[1], s.bg[2], rmask, rg, keys, recs,   \
+                                                      ids, T_final, nc, d_image, dwe, ddp, aux,  \
+                                                      grad)
+#define NEXEL_CB(KK)                                          \
+  do {                                                        \
+    if (batch == 128) NEXEL_CB1(KK, 128);                     \
+    else if (batch == 512) NEXEL_CB1(KK, 512);                \
+    else NEXEL_CB1(KK, 256);                                  \
+  } while (0)
   switch (s.K) {
     case 0: NEXEL_CB(0); break;
     case 1: NEXEL_CB(1); break;
@@ -368,6 +393,7 @@ static cudaError_t collect_bwd_t(const DevCam& c, const nexel_settings& s, char*
     default: return cudaErrorInvalidValue;
   }
 #undef NEXEL_CB
+#undef NEXEL_CB1
   return cudaGetLastError();
 }
 

@@ -679,7 +679,8 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
 //     within a warp the lanes are consecutive pixels of one slot, so at
 //     coarse levels neighbouring lanes read the same table entries.  The
 //     down-weighted features go, as the A operand, into a ring of kFwStages
-//     shared-memory stages (and, in a training step, to the feature cache).
+//     shared-memory stages (2..kFwStages in use, a tuning knob; and, in a
+//     training step, to the feature cache).
 //     A stage is handed to the MLP warps through an mbarrier (`full`) and
 //     handed back by the completion of the MMA that reads it (`empty`, a
 //     tcgen05 commit), so the gather runs up to kFwStages tiles ahead and
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
     const float* __restrict__ notex, const float* __restrict__ weights,
     const int* __restrict__ ids, const float* __restrict__ depths,
     const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures,
-    uint32_t* __restrict__ feat_cache, int* __restrict__ status, int fault) {
+    uint32_t* __restrict__ feat_cache, int* __restrict__ status, int fault, int ns) {
   using Lt = TcFwdLayout<IN, H1, H2, OUT>;
   constexpr int HL = Lt::HL;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -809,7 +810,7 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
     const int grow = (tt % PPT) * KP + tt / PPT;
     int i = 0;
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
-      const int st = i % kFwStages, use = i / kFwStages;
+      const int st = i % ns, use = i / ns;  // ns <= kFwStages stages in use
       // the MMA that read this stage kFwStages tiles ago has completed
       if (use > 0 && !wait_bar(&s_empty[st], (uint32_t)((use - 1) & 1), wlim)) {
         if (tid == 0 && status) atomicOr(status, kStatusTimeout);
@@ -867,7 +868,7 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
     return got;
   };
   for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
-    const int st = i % kFwStages, use = i / kFwStages;
+    const int st = i % ns, use = i / ns;  // ns <= kFwStages stages in use
     // this row's composite inputs, fetched before the MMA waits
     const long long p = tile * PPT + erow / KP;
     const int j = erow & (KP - 1);
@@ -1014,7 +1015,8 @@ cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev&
   NEXEL_PROF("texture_fwd_tc", st);
   kern<<<grid, kFwThreads, Lt::total, st>>>(
       c, fd, s.K, log2KP, n_tiles, s.bg[0], s.bg[1], s.bg[2], notex, weights, ids, depths, T_final,
-      image, textures, fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status, tc_wait_fault());
+      image, textures, fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status, tc_wait_fault(),
+      std::min(std::max(current_tuning().tex_fwd_stages, 2), kFwStages));
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Launch-shape tuning: how many CTAs per SM the persistent texturing kernels
-// keep in flight (the tile pipeline depth of the MLP kernels), and the CTA
-// size of the hash backward.  The choice is process-wide; nexel_autotune
+// keep in flight (the tile pipeline depth of the MLP kernels), the CTA size
+// of the hash backward, the surfel staging batch of the collection kernels
+// and the depth of the texturing forward's operand ring.  The choice is process-wide; nexel_autotune
 // measures the candidates on the caller's own workload (one training step:
 // forward + backward, timed with CUDA events on the caller's stream) and
 // keeps the fastest, one knob after another (a change must gain 1 %).
@@ -13,13 +14,15 @@
 namespace nexel {
 namespace {
 
-std::atomic<int> g_fwd{2}, g_bwd{2}, g_f32{2}, g_hash{256};
+std::atomic<int> g_fwd{2}, g_bwd{2}, g_f32{2}, g_hash{256}, g_batch{256}, g_stages{4};
 std::atomic<int> g_tc_wait_fault{0};
 
 bool valid(const nexel_tuning& t) {
   return t.tex_fwd_ctas_per_sm >= 1 && t.tex_fwd_ctas_per_sm <= 2 &&
          t.tex_bwd_ctas_per_sm >= 1 && t.tex_bwd_ctas_per_sm <= 2 && t.f32_ctas_per_sm >= 1 &&
-         t.f32_ctas_per_sm <= 2 && (t.hash_block == 128 || t.hash_block == 256);
+         t.f32_ctas_per_sm <= 2 && (t.hash_block == 128 || t.hash_block == 256) &&
+         (t.collect_batch == 128 || t.collect_batch == 256 || t.collect_batch == 512) &&
+         t.tex_fwd_stages >= 2 && t.tex_fwd_stages <= 4;
 }
 
 void put(const nexel_tuning& t) {
@@ -27,6 +30,8 @@ void put(const nexel_tuning& t) {
   g_bwd = t.tex_bwd_ctas_per_sm;
   g_f32 = t.f32_ctas_per_sm;
   g_hash = t.hash_block;
+  g_batch = t.collect_batch;
+  g_stages = t.tex_fwd_stages;
 }
 
 nexel_tuning get() {
@@ -35,6 +40,8 @@ nexel_tuning get() {
   t.tex_bwd_ctas_per_sm = g_bwd;
   t.f32_ctas_per_sm = g_f32;
   t.hash_block = g_hash;
+  t.collect_batch = g_batch;
+  t.tex_fwd_stages = g_stages;
   return t;
 }
 
@@ -48,6 +55,8 @@ Tuning current_tuning() {
   t.tex_bwd_ctas = g_bwd;
   t.f32_ctas = g_f32;
   t.hash_block = g_hash;
+  t.collect_batch = g_batch;
+  t.tex_fwd_stages = g_stages;
   return t;
 }
 
@@ -140,16 +149,18 @@ int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
   float cur_ms = 0.f;
   rc = measure(cur, &cur_ms);
   // one knob after another, keeping the best value of each
-  for (int knob = 0; knob < 4 && rc == NEXEL_OK; ++knob) {
+  for (int knob = 0; knob < 6 && rc == NEXEL_OK; ++knob) {
     std::vector<int> vals;
     if (knob == 0) vals = {1, 2};
     else if (knob == 1) vals = {1, 2};
     else if (knob == 2) vals = {1, 2};
-    else vals = {128, 256};
+    else if (knob == 3) vals = {128, 256};
+    else if (knob == 4) vals = {128, 256, 512};
+    else vals = {2, 3, 4};
     for (int v : vals) {
       nexel_tuning t = cur;
-      int* field_of[4] = {&t.tex_fwd_ctas_per_sm, &t.tex_bwd_ctas_per_sm, &t.f32_ctas_per_sm,
-                          &t.hash_block};
+      int* field_of[6] = {&t.tex_fwd_ctas_per_sm, &t.tex_bwd_ctas_per_sm, &t.f32_ctas_per_sm,
+                          &t.hash_block, &t.collect_batch, &t.tex_fwd_stages};
       if (*field_of[knob] == v) continue;
       *field_of[knob] = v;
       float ms = 0.f;

@@ -146,16 +146,18 @@ def test_objective_and_density_calls_check_arguments_before_launch(lib):
 
 
 def test_tuning_round_trip_and_checks(lib):
+    fields = ("tex_fwd_ctas_per_sm", "tex_bwd_ctas_per_sm", "f32_ctas_per_sm", "hash_block",
+              "collect_batch", "tex_fwd_stages")
     t0 = N_.nexel_get_tuning()
-    assert (t0.tex_fwd_ctas_per_sm, t0.tex_bwd_ctas_per_sm, t0.f32_ctas_per_sm,
-            t0.hash_block) == (2, 2, 2, 256)
-    t = N_.Tuning(1, 1, 1, 128)
+    assert tuple(getattr(t0, f) for f in fields) == (2, 2, 2, 256, 256, 4)
+    t = N_.Tuning(1, 1, 1, 128, 512, 2)
     N_.nexel_set_tuning(t)
     g = N_.nexel_get_tuning()
-    assert (g.tex_fwd_ctas_per_sm, g.tex_bwd_ctas_per_sm, g.f32_ctas_per_sm, g.hash_block) == \
-        (1, 1, 1, 128)
-    for bad in (N_.Tuning(0, 1, 1, 128), N_.Tuning(3, 1, 1, 128), N_.Tuning(1, 3, 1, 128),
-                N_.Tuning(1, 1, 1, 64)):
+    assert tuple(getattr(g, f) for f in fields) == (1, 1, 1, 128, 512, 2)
+    for bad in (N_.Tuning(0, 1, 1, 128, 256, 4), N_.Tuning(3, 1, 1, 128, 256, 4),
+                N_.Tuning(1, 3, 1, 128, 256, 4), N_.Tuning(1, 1, 1, 64, 256, 4),
+                N_.Tuning(1, 1, 1, 128, 64, 4), N_.Tuning(1, 1, 1, 128, 256, 1),
+                N_.Tuning(1, 1, 1, 128, 256, 5)):
         assert lib.nexel_set_tuning(C.byref(bad)) == -1
     N_.nexel_set_tuning(t0)
     best = N_.Tuning()

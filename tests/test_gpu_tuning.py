@@ -47,15 +47,17 @@ def test_autotune_and_tuning_invariance(dev):
     t0 = N_.nexel_get_tuning()
     results = []
     try:
-        for t in (N_.Tuning(2, 2, 2, 256), N_.Tuning(1, 1, 1, 128)):
+        for t in (N_.Tuning(2, 2, 2, 256, 256, 4), N_.Tuning(1, 1, 1, 128, 128, 2),
+                  N_.Tuning(2, 1, 2, 256, 512, 3)):
             N_.nexel_set_tuning(t)
             results.append(_step(dev, w, fd, p, dI))
-        (o1, g1, ws, cam_s, st_s), (o2, g2, _, _, _) = results
-        for k in ("image", "weights", "ids", "textures"):
-            assert torch.equal(o1[k], o2[k]), k
-        for k in g1:
-            a, b = g1[k].double(), g2[k].double()
-            assert float((a - b).norm() / b.norm()) < 1e-5, k
+        (o1, g1, ws, cam_s, st_s) = results[0]
+        for (o2, g2, _, _, _) in results[1:]:
+            for k in ("image", "weights", "ids", "textures"):
+                assert torch.equal(o1[k], o2[k]), k
+            for k in g1:
+                a, b = g1[k].double(), g2[k].double()
+                assert float((a - b).norm() / b.norm()) < 1e-5, k
         # the autotuner on the same step
         g = {k: torch.zeros_like(v) for k, v in g1.items()}
         bws = ws.bwd(cam_s, st_s, fd.struct(fd.storage_table(), fd.weights))
@@ -70,7 +72,8 @@ def test_autotune_and_tuning_invariance(dev):
                                        "table", "mlp")], 3,
             torch.cuda.current_stream().cuda_stream)
         print(f"\n[autotune] best {best.tex_fwd_ctas_per_sm} {best.tex_bwd_ctas_per_sm} "
-              f"{best.f32_ctas_per_sm} {best.hash_block} at {ms:.3f} ms")
+              f"{best.f32_ctas_per_sm} {best.hash_block} {best.collect_batch} "
+              f"{best.tex_fwd_stages} at {ms:.3f} ms")
         assert ms > 0
         cur = N_.nexel_get_tuning()
         assert (cur.tex_fwd_ctas_per_sm, cur.hash_block) == (best.tex_fwd_ctas_per_sm,
