@@ -25,25 +25,42 @@ __device__ __forceinline__ uint32_t rank_of(KeyT k, uint32_t mask) {
   return (uint32_t)k & mask;
 }
 
-// BATCH: surfel records staged per batch (128, 256 or 512; a launch-shape
-// knob of the autotuner: smaller batches test for early termination more
-// often, larger ones synchronise less).
-template <int K, typename KeyT, int BATCH>
-__global__ void __launch_bounds__(kTilePix) k_collect_fwd(
-    DevCam c, float alpha_min, float alpha_max, float T_min, uint32_t rmask,
-    const uint2* __restrict__ ranges, const KeyT* __restrict__ keys,
-    const float4* __restrict__ recs, float* __restrict__ notex, float* __restrict__ weights,
-    int* __restrict__ ids, float* __restrict__ depths, float* __restrict__ T_final,
-    int* __restrict__ n_contrib) {
-  __shared__ float4 s_rec[kRecF4][BATCH];
-  __shared__ uint32_t s_rank[BATCH];
-  const int tile = blockIdx.x;
+// The tile's surfel list: instance i's depth rank, from a 32-bit (tile,
+// rank) key or a 64-bit key whose low 32 bits are the rank.
+__device__ __forceinline__ uint32_t key_rank(const KeySrc& k, uint32_t i) {
+  return k.key64 ? (uint32_t)reinterpret_cast<const unsigned long long*>(k.keys)[i]
+                 : reinterpret_cast<const uint32_t*>(k.keys)[i] & k.rmask;
+}
+
+// The work item a CTA takes next: with a queue, persistent CTAs pull items
+// (the tiles of every view of a batch, view after view) from a device
+// counter; without one, CTA b takes item b once.  Returns -1 when none is
+// left.  Every thread of the CTA calls it.
+__device__ __forceinline__ int next_item(unsigned* queue, int it, int total, int* s_item) {
+  if (!queue) return (it == 0 && (int)blockIdx.x < total) ? (int)blockIdx.x : -1;
+  __syncthreads();  // the previous item's shared-memory use is over
+  if (threadIdx.x == 0) *s_item = (int)atomicAdd(queue, 1u);
+  __syncthreads();
+  const int item = *s_item;
+  return item < total ? item : -1;
+}
+
+// One 16 x 16 tile of the collection forward.  BATCH: surfel records staged
+// per batch (128, 256 or 512; a launch-shape knob of the autotuner: smaller
+// batches test for early termination more often, larger ones synchronise
+// less).
+template <int K, int BATCH>
+__device__ __forceinline__ void collect_fwd_tile(const CollectFwdView& V, int tile,
+                                                 float alpha_min, float alpha_max, float T_min,
+                                                 float4 (*s_rec)[BATCH], uint32_t* s_rank) {
+  const DevCam& c = V.c;
+  const float4* __restrict__ recs = V.recs;
   const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
   const int py = ty * kTile + (threadIdx.x / kTile);
   const bool inside = px < c.W && py < c.H;
   const float fpx = px + 0.5f, fpy = py + 0.5f;
-  const uint2 rg = ranges[tile];
+  const uint2 rg = V.ranges[tile];
   float T = 1.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
   float Wk[K > 0 ? K : 1], Dk[K > 0 ? K : 1];
   int Rk[K > 0 ? K : 1];
@@ -57,7 +74,7 @@ __global__ void __launch_bounds__(kTilePix) k_collect_fwd(
     for (int t = threadIdx.x; t < BATCH; t += kTilePix) {
       const uint32_t i = b0 + t;
       if (i < rg.y) {
-        uint32_t r = rank_of(keys[i], rmask);
+        const uint32_t r = key_rank(V.keys, i);
         s_rank[t] = r;
         const float4* src = recs + (size_t)r * kRecF4;
 #pragma unroll
@@ -105,16 +122,36 @@ __global__ void __launch_bounds__(kTilePix) k_collect_fwd(
   }
   if (!inside) return;
   const size_t p = (size_t)py * c.W + px;
-  notex[3 * p] = n0; notex[3 * p + 1] = n1; notex[3 * p + 2] = n2;
-  T_final[p] = T;
-  n_contrib[p] = last;
+  V.notex[3 * p] = n0; V.notex[3 * p + 1] = n1; V.notex[3 * p + 2] = n2;
+  V.T_final[p] = T;
+  V.n_contrib[p] = last;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     int id = -1;
     if (Rk[k] >= 0) id = (int)__float_as_uint(__ldg(recs + (size_t)Rk[k] * kRecF4 + 4).w);
-    weights[p * K + k] = Wk[k];
-    ids[p * K + k] = id;
-    depths[p * K + k] = Dk[k];
+    V.weights[p * K + k] = Wk[k];
+    V.ids[p * K + k] = id;
+    V.depths[p * K + k] = Dk[k];
+  }
+}
+
+// Collection forward over the tiles of one view (one CTA per tile) or, with
+// a queue, of every view of a batch in one launch of persistent CTAs.
+template <int K, int BATCH, bool MV>
+__global__ void __launch_bounds__(kTilePix, 5) k_collect_fwd(
+    const __grid_constant__ ViewBatch<CollectFwdView> b, float alpha_min, float alpha_max,
+    float T_min, unsigned* queue) {
+  __shared__ float4 s_rec[kRecF4][BATCH];
+  __shared__ uint32_t s_rank[BATCH];
+  __shared__ int s_item;
+  const int total = b.item0[b.n];
+  for (int it = 0;; ++it) {
+    const int item = next_item(queue, it, total, &s_item);
+    if (item < 0) break;
+    // MV: a batch of views (else one view, at a fixed index)
+    const int v = MV ? view_of(b, item) : 0;
+    collect_fwd_tile<K, BATCH>(b.v[v], MV ? item - b.item0[v] : item, alpha_min, alpha_max,
+                               T_min, s_rec, s_rank);
   }
 }
 
@@ -162,21 +199,16 @@ __device__ __forceinline__ void warp_sum20_add(const float (&g)[kGradStride], fl
   if (lo <= 2 && mid <= 4 && z != 0.f) atomicAdd(dst + 10 * (int)b4 + 5 * (int)b3 + mid, z);
 }
 
-// Four CTAs per SM (64 registers, no spills): the replay is issue-bound and
-// gains from the fourth tile in flight.
-template <int K, typename KeyT, int BATCH>
-__global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
-    DevCam c, float alpha_min, float alpha_max, float bg0, float bg1, float bg2, uint32_t rmask,
-    const uint2* __restrict__ ranges, const KeyT* __restrict__ keys,
-    const float4* __restrict__ recs, const int* __restrict__ ids, const float* __restrict__ T_final,
-    const int* __restrict__ n_contrib, const float* __restrict__ d_image,
-    const float* __restrict__ dweff, const float* __restrict__ ddepth,
-    const float4* __restrict__ aux, float* __restrict__ grad) {
-  __shared__ float4 s_rec[kRecF4][BATCH];
-  __shared__ float4 s_aux[kAuxF4][BATCH];
-  __shared__ uint32_t s_rank[BATCH];
-  __shared__ int s_max;
-  const int tile = blockIdx.x;
+// One 16 x 16 tile of the collection backward (BATCH as in the forward).
+template <int K, int BATCH>
+__device__ __forceinline__ void collect_bwd_tile(const CollectBwdView& V, int tile,
+                                                 float alpha_min, float alpha_max, float bg0,
+                                                 float bg1, float bg2, float4 (*s_rec)[BATCH],
+                                                 float4 (*s_aux)[BATCH], uint32_t* s_rank,
+                                                 int* s_max) {
+  const DevCam& c = V.c;
+  const float4* __restrict__ recs = V.recs;
+  const float4* __restrict__ aux = V.aux;
   const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
   const int py = ty * kTile + (threadIdx.x / kTile);
@@ -184,7 +216,7 @@ __global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
   const float fpx = px + 0.5f, fpy = py + 0.5f;
   // camera-space ray direction of this pixel (z component 1)
   const float rdx = (fpx - c.cx) / c.fx, rdy = (fpy - c.cy) / c.fy;
-  const uint2 rg = ranges[tile];
+  const uint2 rg = V.ranges[tile];
   const size_t p = inside ? (size_t)py * c.W + px : 0;
   float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
   int last = 0;
@@ -193,22 +225,22 @@ __global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
 #pragma unroll
   for (int k = 0; k < K; ++k) { Ik[k] = -1; dWe[k] = 0.f; dDk[k] = 0.f; }
   if (inside) {
-    T = T_final[p];
-    last = n_contrib[p];
-    dC0 = d_image[3 * p]; dC1 = d_image[3 * p + 1]; dC2 = d_image[3 * p + 2];
+    T = V.T_final[p];
+    last = V.n_contrib[p];
+    dC0 = V.d_image[3 * p]; dC1 = V.d_image[3 * p + 1]; dC2 = V.d_image[3 * p + 2];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      Ik[k] = ids[p * K + k];
-      dWe[k] = dweff[p * K + k];
-      dDk[k] = ddepth[p * K + k];
+      Ik[k] = V.ids[p * K + k];
+      dWe[k] = V.dweff[p * K + k];
+      dDk[k] = V.ddepth[p * K + k];
     }
   }
   float R = bg0 * dC0 + bg1 * dC1 + bg2 * dC2;  // background behind everything
-  if (threadIdx.x == 0) s_max = 0;
+  if (threadIdx.x == 0) *s_max = 0;
   __syncthreads();
-  atomicMax(&s_max, last);
+  atomicMax(s_max, last);
   __syncthreads();
-  const uint32_t list_end = rg.x + (uint32_t)s_max;
+  const uint32_t list_end = rg.x + (uint32_t)*s_max;
   for (uint32_t bend = list_end; bend > rg.x;) {
     const uint32_t bstart = (bend - rg.x > (uint32_t)BATCH) ? bend - BATCH : rg.x;
     __syncthreads();
@@ -216,7 +248,7 @@ __global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
     for (int t = threadIdx.x; t < BATCH; t += kTilePix) {
       const uint32_t i = bstart + t;
       if (i < bend) {
-        uint32_t r = rank_of(keys[i], rmask);
+        const uint32_t r = key_rank(V.keys, i);
         s_rank[t] = r;
         const float4* src = recs + (size_t)r * kRecF4;
 #pragma unroll
@@ -297,28 +329,107 @@ __global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
         g[12] = -du1 * h.u;
         g[13] = -dv2 * h.v;
       }
-      warp_sum20_add(g, grad + (size_t)s_rank[j] * kGradStride);
+      warp_sum20_add(g, V.grad + (size_t)s_rank[j] * kGradStride);
     }
     bend = bstart;
   }
 }
 
-template <typename KeyT>
-static cudaError_t collect_fwd_t(const DevCam& c, const nexel_settings& s, char* ws,
-                                 const WsLayout& L, float* notex, float* weights, int* ids,
-                                 float* depths, float* T_final, cudaStream_t st) {
-  uint32_t rmask = L.key64 ? 0xFFFFFFFFu : ((1u << L.rank_bits) - 1u);
-  dim3 grid(L.n_tiles), block(kTilePix);
-  auto* rg = (const uint2*)(ws + L.ranges);
-  auto* keys = (const KeyT*)(ws + L.inst0);
-  auto* recs = (const float4*)(ws + L.geom_sorted);
-  int* nc = (int*)(ws + L.n_contrib);
-  NEXEL_PROF("collect_fwd", st);
+// Four CTAs per SM (64 registers, no spills): the replay is issue-bound and
+// gains from the fourth tile in flight.  One view (a CTA per tile) or, with
+// a queue, every view of a batch in one launch of persistent CTAs.
+template <int K, int BATCH, bool MV>
+__global__ void __launch_bounds__(kTilePix, 4) k_collect_bwd(
+    const __grid_constant__ ViewBatch<CollectBwdView> b, float alpha_min, float alpha_max,
+    float bg0, float bg1, float bg2, unsigned* queue) {
+  __shared__ float4 s_rec[kRecF4][BATCH];
+  __shared__ float4 s_aux[kAuxF4][BATCH];
+  __shared__ uint32_t s_rank[BATCH];
+  __shared__ int s_max;
+  __shared__ int s_item;
+  const int total = b.item0[b.n];
+  for (int it = 0;; ++it) {
+    const int item = next_item(queue, it, total, &s_item);
+    if (item < 0) break;
+    const int v = MV ? view_of(b, item) : 0;
+    collect_bwd_tile<K, BATCH>(b.v[v], MV ? item - b.item0[v] : item, alpha_min, alpha_max, bg0,
+                               bg1, bg2, s_rec, s_aux, s_rank, &s_max);
+  }
+}
+
+CollectFwdView collect_fwd_view(const DevCam& c, char* ws, const WsLayout& L, float* notex,
+                                float* weights, int* ids, float* depths, float* T_final) {
+  CollectFwdView v;
+  v.c = c;
+  v.ranges = (const uint2*)(ws + L.ranges);
+  v.keys.keys = ws + L.inst0;
+  v.keys.key64 = L.key64 ? 1 : 0;
+  v.keys.rmask = L.key64 ? 0xFFFFFFFFu : ((1u << L.rank_bits) - 1u);
+  v.recs = (const float4*)(ws + L.geom_sorted);
+  v.notex = notex;
+  v.weights = weights;
+  v.ids = ids;
+  v.depths = depths;
+  v.T_final = T_final;
+  v.n_contrib = (int*)(ws + L.n_contrib);
+  return v;
+}
+
+CollectBwdView collect_bwd_view(const DevCam& c, char* ws, const WsLayout& L, const char* bws,
+                                const BwdLayout& B, const int* ids, const float* T_final,
+                                const float* d_image) {
+  CollectBwdView v;
+  v.c = c;
+  v.ranges = (const uint2*)(ws + L.ranges);
+  v.keys.keys = ws + L.inst0;
+  v.keys.key64 = L.key64 ? 1 : 0;
+  v.keys.rmask = L.key64 ? 0xFFFFFFFFu : ((1u << L.rank_bits) - 1u);
+  v.recs = (const float4*)(ws + L.geom_sorted);
+  v.aux = (const float4*)(ws + L.aux_sorted);
+  v.ids = ids;
+  v.T_final = T_final;
+  v.n_contrib = (const int*)(ws + L.n_contrib);
+  v.d_image = d_image;
+  v.dweff = (const float*)(bws + B.dweff);
+  v.ddepth = (const float*)(bws + B.ddepth);
+  v.grad = (float*)(ws + L.grad_sorted);
+  return v;
+}
+
+namespace {
+
+// Grid of a launch: one CTA per item, or (with a queue) as many persistent
+// CTAs as fit on the GPU at once.
+template <typename Kern>
+unsigned batch_grid(Kern kern, int total, bool persistent) {
+  if (!persistent) return (unsigned)total;
+  int dev = 0, nsm = 152, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTilePix, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return (unsigned)std::min<long long>(total, (long long)per_sm * nsm);
+}
+
+}  // namespace
+
+cudaError_t launch_collect_fwd_batch(const nexel_settings& s, const ViewBatch<CollectFwdView>& b,
+                                     unsigned* queue, cudaStream_t st) {
+  const int total = b.item0[b.n];
+  if (total <= 0) return cudaSuccess;
+  if (queue) {
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
   const int batch = current_tuning().collect_batch;
-#define NEXEL_CF1(KK, BB)                                                                         \
-  k_collect_fwd<KK, KeyT, BB><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.T_min, rmask, \
-                                                      rg, keys, recs, notex, weights, ids, depths, \
-                                                      T_final, nc)
+  NEXEL_PROF("collect_fwd", st);
+#define NEXEL_CF1(KK, BB)                                                                   \
+  do {                                                                                      \
+    auto kern = queue ? k_collect_fwd<KK, BB, true> : k_collect_fwd<KK, BB, false>;          \
+    kern<<<batch_grid(kern, total, queue != nullptr), kTilePix, 0, st>>>(                   \
+        b, s.alpha_min, s.alpha_max, s.T_min, queue);                                       \
+  } while (0)
 #define NEXEL_CF(KK)                                          \
   do {                                                        \
     if (batch == 128) NEXEL_CF1(KK, 128);                     \
@@ -345,35 +456,30 @@ static cudaError_t collect_fwd_t(const DevCam& c, const nexel_settings& s, char*
 cudaError_t launch_collect_fwd(const DevCam& c, const nexel_settings& s, char* ws,
                                const WsLayout& L, float* notex, float* weights, int* ids,
                                float* depths, float* T_final, cudaStream_t st) {
-  if (L.key64)
-    return collect_fwd_t<unsigned long long>(c, s, ws, L, notex, weights, ids, depths, T_final, st);
-  return collect_fwd_t<uint32_t>(c, s, ws, L, notex, weights, ids, depths, T_final, st);
+  ViewBatch<CollectFwdView> b;
+  b.n = 1;
+  b.item0[0] = 0;
+  b.item0[1] = L.n_tiles;
+  b.v[0] = collect_fwd_view(c, ws, L, notex, weights, ids, depths, T_final);
+  return launch_collect_fwd_batch(s, b, nullptr, st);
 }
 
-template <typename KeyT>
-static cudaError_t collect_bwd_t(const DevCam& c, const nexel_settings& s, char* ws,
-                                 const WsLayout& L, const char* bws, const BwdLayout& B,
-                                 const int* ids, const float* T_final, const float* d_image,
-                                 cudaStream_t st) {
-  uint32_t rmask = L.key64 ? 0xFFFFFFFFu : ((1u << L.rank_bits) - 1u);
-  dim3 grid(L.n_tiles), block(kTilePix);
-  auto* rg = (const uint2*)(ws + L.ranges);
-  auto* keys = (const KeyT*)(ws + L.inst0);
-  auto* recs = (const float4*)(ws + L.geom_sorted);
-  auto* nc = (const int*)(ws + L.n_contrib);
-  auto* dwe = (const float*)(bws + B.dweff);
-  auto* ddp = (const float*)(bws + B.ddepth);
-  auto* aux = (const float4*)(ws + L.aux_sorted);
-  float* grad = (float*)(ws + L.grad_sorted);
-  cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * kGradStride * (size_t)L.N, st);
-  if (e != cudaSuccess) return e;
-  NEXEL_PROF("collect_bwd", st);
+cudaError_t launch_collect_bwd_batch(const nexel_settings& s, const ViewBatch<CollectBwdView>& b,
+                                     unsigned* queue, cudaStream_t st) {
+  const int total = b.item0[b.n];
+  if (total <= 0) return cudaSuccess;
+  if (queue) {
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
   const int batch = current_tuning().collect_batch;
-#define NEXEL_CB1(KK, BB)                                                                        \
-  k_collect_bwd<KK, KeyT, BB><<<grid, block, 0, st>>>(c, s.alpha_min, s.alpha_max, s.bg[0],     \
-                                                      s.bg[1], s.bg[2], rmask, rg, keys, recs,   \
-                                                      ids, T_final, nc, d_image, dwe, ddp, aux,  \
-                                                      grad)
+  NEXEL_PROF("collect_bwd", st);
+#define NEXEL_CB1(KK, BB)                                                                   \
+  do {                                                                                      \
+    auto kern = queue ? k_collect_bwd<KK, BB, true> : k_collect_bwd<KK, BB, false>;          \
+    kern<<<batch_grid(kern, total, queue != nullptr), kTilePix, 0, st>>>(                   \
+        b, s.alpha_min, s.alpha_max, s.bg[0], s.bg[1], s.bg[2], queue);                     \
+  } while (0)
 #define NEXEL_CB(KK)                                          \
   do {                                                        \
     if (batch == 128) NEXEL_CB1(KK, 128);                     \
@@ -401,9 +507,15 @@ cudaError_t launch_collect_bwd(const DevCam& c, const nexel_settings& s, char* w
                                const WsLayout& L, const char* bws, const BwdLayout& B,
                                const int* ids, const float* T_final, const float* d_image,
                                cudaStream_t st) {
-  if (L.key64)
-    return collect_bwd_t<unsigned long long>(c, s, ws, L, bws, B, ids, T_final, d_image, st);
-  return collect_bwd_t<uint32_t>(c, s, ws, L, bws, B, ids, T_final, d_image, st);
+  float* grad = (float*)(ws + L.grad_sorted);
+  cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * kGradStride * (size_t)L.N, st);
+  if (e != cudaSuccess) return e;
+  ViewBatch<CollectBwdView> b;
+  b.n = 1;
+  b.item0[0] = 0;
+  b.item0[1] = L.n_tiles;
+  b.v[0] = collect_bwd_view(c, ws, L, bws, B, ids, T_final, d_image);
+  return launch_collect_bwd_batch(s, b, nullptr, st);
 }
 
 

@@ -213,6 +213,7 @@ constexpr size_t kCountersInst = 4;
 constexpr size_t kCountersPlaced = 8;  // instances placed by the direct tile placement
 constexpr size_t kCountersMaskWords = 12;  // stored tile-decision words wanted
 constexpr size_t kCountersNonFinite = 16;  // surfels culled for a NaN / infinite parameter
+constexpr size_t kCountersBatchQueue = 20;  // work queue of a batched launch (first view's block)
 constexpr size_t kStatusOffset = 32;
 constexpr size_t kStatsOffset = 64;  // 5 x u64 of nexel_render_stats
 
@@ -274,6 +275,70 @@ cudaError_t launch_count_scan(int N, char* ws, const WsLayout& L, cudaStream_t s
 // launch_count_scan and flag an overflow in the status word).
 cudaError_t launch_binning(const DevCam& c, int N, long long n_inst, char* ws, const WsLayout& L,
                            cudaStream_t st);
+// ----------------------------------------------- views of one batched launch
+// A batched launch covers the work items of up to kMaxBatchViews views: item
+// i belongs to the view v with item0[v] <= i < item0[v + 1] (the views'
+// items one after another).
+constexpr int kMaxBatchViews = 16;
+template <typename V>
+struct ViewBatch {
+  int n;
+  int item0[kMaxBatchViews + 1];
+  V v[kMaxBatchViews];
+};
+
+// A view's binned instances: 32-bit (tile << rank_bits | rank) keys or
+// 64-bit keys whose low 32 bits are the depth rank.
+struct KeySrc {
+  const void* keys;
+  uint32_t rmask;
+  int key64;
+};
+
+// The view of work item `item` (the views' items lie one after another).
+template <typename V>
+__device__ __forceinline__ int view_of(const ViewBatch<V>& b, int item) {
+  int v = 0;
+  while (v + 1 < b.n && item >= b.item0[v + 1]) ++v;
+  return v;
+}
+
+// Per-view arguments of the collection forward and backward (items: tiles).
+struct CollectFwdView {
+  DevCam c;
+  const uint2* ranges;
+  KeySrc keys;
+  const float4* recs;
+  float *notex, *weights;
+  int* ids;
+  float *depths, *T_final;
+  int* n_contrib;
+};
+struct CollectBwdView {
+  DevCam c;
+  const uint2* ranges;
+  KeySrc keys;
+  const float4 *recs, *aux;
+  const int* ids;
+  const float* T_final;
+  const int* n_contrib;
+  const float *d_image, *dweff, *ddepth;
+  float* grad;
+};
+
+CollectFwdView collect_fwd_view(const DevCam& c, char* ws, const WsLayout& L, float* notex,
+                                float* weights, int* ids, float* depths, float* T_final);
+CollectBwdView collect_bwd_view(const DevCam& c, char* ws, const WsLayout& L, const char* bws,
+                                const BwdLayout& B, const int* ids, const float* T_final,
+                                const float* d_image);
+// queue: a device counter (reset by the launch) for persistent CTAs pulling
+// the items of every view; nullptr: one CTA per item.  The backward's
+// gradient records (grad of each view) must be zeroed by the caller.
+cudaError_t launch_collect_fwd_batch(const nexel_settings& s, const ViewBatch<CollectFwdView>& b,
+                                     unsigned* queue, cudaStream_t st);
+cudaError_t launch_collect_bwd_batch(const nexel_settings& s, const ViewBatch<CollectBwdView>& b,
+                                     unsigned* queue, cudaStream_t st);
+
 cudaError_t launch_collect_fwd(const DevCam& c, const nexel_settings& s, char* ws,
                                const WsLayout& L, float* notex, float* weights, int* ids,
                                float* depths, float* T_final, cudaStream_t st);

@@ -46,13 +46,22 @@ __device__ __forceinline__ void seg_scan2(float& vx, float& vy, int lane, int se
 
 }  // namespace
 
-template <typename TT>
+template <typename TT, bool MV>
 __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
-    DevCam c, FieldDev f, int K, int log2KP, uint32_t n_rows, uint32_t R,
-    const int* __restrict__ ids, const float* __restrict__ depths,
-    const float2* __restrict__ gin, float* __restrict__ ddepth, float* __restrict__ d_table) {
+    const __grid_constant__ ViewBatch<HashBwdView> b, FieldDev f, int K, int log2KP,
+    float* __restrict__ d_table) {
   const int lane = threadIdx.x & 31;
-  const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int item = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+  if (item >= b.item0[b.n]) return;  // whole warps
+  const int vi = MV ? view_of(b, item) : 0;  // MV: a batch of views
+  const HashBwdView& V = b.v[vi];
+  const DevCam& c = V.c;
+  const uint32_t n_rows = V.n_rows, R = V.R;
+  const int* __restrict__ ids = V.ids;
+  const float* __restrict__ depths = V.depths;
+  const float2* __restrict__ gin = V.gin;
+  // the view's own warp index
+  const uint32_t gw = (uint32_t)(MV ? item - b.item0[vi] : item);
   // warp gw: slot j = gw % KP of the 32 consecutive pixels 32 (gw / KP) ..
   const int KP = 1 << log2KP;
   const uint32_t r = ((gw >> log2KP) * 32u + (uint32_t)lane) * (uint32_t)KP + (gw & (KP - 1));
@@ -70,7 +79,7 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     D = depths[s];
     d = pixel_dir(c, (int)(p % (uint32_t)c.W), (int)(p / (uint32_t)c.W));
   }
-  const float iD = 1.f / D, fD = f.focal * iD;
+  const float iD = 1.f / D, fD = c.fx * iD;  // f of Eq. 3: the view's focal length
   const float3 x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
   const size_t T = (size_t)f.mask + 1;
   const int L = f.L;
@@ -160,31 +169,40 @@ __global__ void __launch_bounds__(kHbThreads, kHbMinBlocks) k_hash_bwd(
     const float ddw = -(1.f - dw) * rr * rr * 0.3183098861837907f * iD;
     dt += (g.x * ax + g.y * ay) * ddw + dw * sl * (qx * d.x + qy * d.y + qz * d.z);
   }
-  if (valid) ddepth[s] = dt;
+  if (valid) V.ddepth[s] = dt;
+}
+
+cudaError_t launch_hash_bwd_batch(const FieldDev& fd, int K, int KP, bool half_table,
+                                  const ViewBatch<HashBwdView>& b, float* d_table,
+                                  cudaStream_t st) {
+  int log2KP = 0;
+  while ((1 << log2KP) < KP) ++log2KP;
+  if ((1 << log2KP) != KP || KP > 32 || fd.L < 1 || fd.L > NEXEL_MAX_LEVELS || K <= 0)
+    return cudaErrorInvalidValue;
+  const long long warps = b.item0[b.n];
+  if (warps <= 0) return cudaSuccess;
+  // CTA size: 256 threads, or 128 when the tuning asks (a multiple of the
+  // KP warps of a pixel group either way)
+  const unsigned block = current_tuning().hash_block == 128 ? 128u : (unsigned)kHbThreads;
+  const unsigned grid = (unsigned)((warps * 32 + block - 1) / block);
+  NEXEL_PROF("hash_bwd", st);
+  auto kern = half_table ? (b.n > 1 ? k_hash_bwd<__half, true> : k_hash_bwd<__half, false>)
+                         : (b.n > 1 ? k_hash_bwd<float, true> : k_hash_bwd<float, false>);
+  kern<<<grid, block, 0, st>>>(b, fd, K, log2KP, d_table);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_hash_bwd(const DevCam& c, const FieldDev& fd, int K, int KP, long long n_rows,
                             bool half_table, const int* ids, const float* depths,
                             const float2* gin, float* ddepth, float* d_table, cudaStream_t st) {
   if (n_rows <= 0 || K <= 0) return cudaSuccess;
-  int log2KP = 0;
-  while ((1 << log2KP) < KP) ++log2KP;
-  if ((1 << log2KP) != KP || KP > 32 || fd.L < 1 || fd.L > NEXEL_MAX_LEVELS ||
-      gin_stride(n_rows) >= (1LL << 32))
-    return cudaErrorInvalidValue;
-  const uint32_t R = (uint32_t)gin_stride(n_rows);
-  // CTA size: 256 threads, or 128 when the tuning asks (a multiple of the
-  // KP warps of a pixel group either way)
-  const unsigned block = current_tuning().hash_block == 128 ? 128u : (unsigned)kHbThreads;
-  const unsigned grid = (unsigned)((n_rows + block - 1) / block);
-  NEXEL_PROF("hash_bwd", st);
-  if (half_table)
-    k_hash_bwd<__half><<<grid, block, 0, st>>>(c, fd, K, log2KP, (uint32_t)n_rows, R, ids, depths,
-                                               gin, ddepth, d_table);
-  else
-    k_hash_bwd<float><<<grid, block, 0, st>>>(c, fd, K, log2KP, (uint32_t)n_rows, R, ids, depths,
-                                              gin, ddepth, d_table);
-  return cudaGetLastError();
+  if (gin_stride(n_rows) >= (1LL << 32)) return cudaErrorInvalidValue;
+  ViewBatch<HashBwdView> b;
+  b.n = 1;
+  b.item0[0] = 0;
+  b.item0[1] = hash_bwd_items(n_rows, KP);
+  b.v[0] = HashBwdView{c, ids, depths, gin, ddepth, (uint32_t)n_rows, (uint32_t)gin_stride(n_rows)};
+  return launch_hash_bwd_batch(fd, K, KP, half_table, b, d_table, st);
 }
 
 }  // namespace nexel

@@ -128,6 +128,25 @@ cudaError_t launch_hash_bwd(const DevCam& c, const FieldDev& fd, int K, int KP, 
                             bool half_table, const int* ids, const float* depths,
                             const float2* gin, float* ddepth, float* d_table, cudaStream_t st);
 
+// Per-view arguments of the hash-grid backward (items: warps, each a slot
+// of 32 consecutive pixels; ceil(n_rows / (32 KP)) KP of them per view).
+struct HashBwdView {
+  DevCam c;
+  const int* ids;
+  const float* depths;
+  const float2* gin;
+  float* ddepth;
+  uint32_t n_rows, R;  // rows and the gin row stride (gin_stride(n_rows))
+};
+// One launch over every view of the batch; d_table is shared (summed).
+cudaError_t launch_hash_bwd_batch(const FieldDev& fd, int K, int KP, bool half_table,
+                                  const ViewBatch<HashBwdView>& b, float* d_table,
+                                  cudaStream_t st);
+// Warps (work items) of one view's hash-grid backward.
+inline int hash_bwd_items(long long n_rows, int KP) {
+  return (int)((n_rows + 32LL * KP - 1) / (32LL * KP)) * KP;
+}
+
 // FP32 MLP forward; keeps the hidden activations when asked.
 template <int IN, int H1, int H2>
 __device__ __forceinline__ void mlp_fwd_f32(const float* __restrict__ sW, const float* in,
@@ -247,6 +266,37 @@ __device__ __forceinline__ void mlp_bwd_input_f32(const float* __restrict__ sW, 
 // gradient and adds the MLP weight gradients to d_mlp (may be null).
 // out: 3 (RGB texture) or 48 (degree-3 SH coefficients; FP16 table only)
 bool tc_arch_supported(int in, int h1, int h2, int out, bool half_table);
+// Per-view arguments of the tcgen05 texturing forward (items: 128-row tiles
+// of the view's (pixel, slot) rows, pixel-major with KP rows per pixel).
+struct TexFwdView {
+  DevCam c;
+  const float *notex, *weights;
+  const int* ids;
+  const float *depths, *T_final;
+  float *image, *textures;
+  uint32_t* feat_cache;  // nullptr unless a training step caches the features
+  int* status;
+};
+// Per-view arguments of the tcgen05 texturing backward (items: 128-row
+// tiles; the rows' features cached by the forward in feat).
+struct TexBwdView {
+  DevCam c;
+  const uint32_t* feat;
+  const float* weights;
+  const int* ids;
+  const float *d_image, *d_weights, *d_textures;
+  float* dweff;
+  float2* gin;
+  long long n_rows;
+  int* status;
+};
+cudaError_t launch_texture_bwd_tc_batch(int K, int KP, int in, int h1, int h2, int out, bool f16,
+                                        const float* w, const ViewBatch<TexBwdView>& b,
+                                        float* d_mlp, cudaStream_t st);
+// One launch over every view of the batch (tile counts in b.item0).
+cudaError_t launch_texture_fwd_tc_batch(const nexel_settings& s, const nexel_field& f,
+                                        const FieldDev& fd, const ViewBatch<TexFwdView>& b,
+                                        cudaStream_t st);
 cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                   const FieldDev& fd, const float* notex, const float* weights,
                                   const int* ids, const float* depths, const float* T_final,

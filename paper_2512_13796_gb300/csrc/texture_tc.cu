@@ -201,8 +201,8 @@ __device__ __forceinline__ void st8(unsigned char* base, int r, int f0, int sg, 
 // axis value; a row that is not textured reads the entries around the
 // origin (valid addresses, harmless) and gets a zero down-weighting.
 template <typename TT>
-__device__ __forceinline__ void gather4_tc(const FieldDev& f, int l0, float3 x, float t, bool valid,
-                                           float (&v)[8]) {
+__device__ __forceinline__ void gather4_tc(const FieldDev& f, float focal, int l0, float3 x, float t,
+                                           bool valid, float (&v)[8]) {
   using R = RawEntry<TT>;
   typename R::T e[4][8];
   float fr[4][3], dw[4];
@@ -217,7 +217,7 @@ __device__ __forceinline__ void gather4_tc(const FieldDev& f, int l0, float3 x, 
     const float fx0 = floorf(gx), fy0 = floorf(gy), fz0 = floorf(gz);
     const int cx = (int)fx0, cy = (int)fy0, cz = (int)fz0;
     fr[q][0] = gx - fx0; fr[q][1] = gy - fy0; fr[q][2] = gz - fz0;
-    dw[q] = valid ? downweight(f.focal, s, t) : 0.f;
+    dw[q] = valid ? downweight(focal, s, t) : 0.f;
     const uint32_t hx0 = map_pos(cx), hx1 = map_pos(cx + 1);
     const uint32_t hy0 = map_pos(cy) * 2654435761u, hy1 = map_pos(cy + 1) * 2654435761u;
     const uint32_t hz0 = map_pos(cz) * 805459861u, hz1 = map_pos(cz + 1) * 805459861u;
@@ -280,15 +280,12 @@ struct TcLayout {
   static_assert(HL + ON <= 256 && FA <= 256, "MMA N limits");
 };
 
-template <int IN, int H1, int H2, typename OP, int OUT = 3>
+template <int IN, int H1, int H2, typename OP, int OUT, bool MV>
 __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
-    DevCam c, int K, int log2KP, long long n_rows, long long n_tiles, const float* __restrict__ wts,
-    const uint32_t* __restrict__ feat, const float* __restrict__ weights,
-    const int* __restrict__ ids, const float* __restrict__ d_image,
-    const float* __restrict__ d_weights, const float* __restrict__ d_textures,
-    float* __restrict__ dweff, float2* __restrict__ gin, float* __restrict__ d_mlp,
-    int* __restrict__ status, int fault) {
+    const __grid_constant__ ViewBatch<TexBwdView> b, int K, int log2KP,
+    const float* __restrict__ wts, float* __restrict__ d_mlp, int fault) {
   using Lt = TcLayout<IN, H1, H2, OUT>;
+  const long long n_tiles = b.item0[b.n];
   // fault > 0 (test hook only): no MMA is issued and each completion wait
   // gives up after `fault` polls, which exercises the timeout path
   const int wlim = fault > 0 ? fault : kTcWaitLimit;
@@ -354,7 +351,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   uint32_t phase = 0;
   bool ok = true;
   bool first = true;
-  const long long P = (long long)c.W * c.H;
   const int KP = 1 << log2KP;
 
   // per-row inputs of a tile; the next tile's are loaded while this one's
@@ -362,11 +358,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   struct RowIn {
     uint4 x[IN / 8];
     float gT[3], dC[3], dWx;
-    long long s;
+    long long s, r;  // sample and row within the tile's view
+    int vi;          // the tile's view
     bool valid, in_pix;
   };
   auto load_row = [&](long long tile, RowIn& in) {
-    const long long r = tile * kTcRows + tid;
+    // MV: a batch of views (else one view, at a fixed index)
+    in.vi = (MV && tile < n_tiles) ? view_of(b, (int)tile) : 0;
+    const TexBwdView& V = b.v[in.vi];
+    const long long n_rows = V.n_rows;
+    const long long P = (long long)V.c.W * V.c.H;
+    const float* __restrict__ weights = V.weights;
+    const int* __restrict__ ids = V.ids;
+    const float* __restrict__ d_image = V.d_image;
+    const float* __restrict__ d_textures = V.d_textures;
+    const float* __restrict__ d_weights = V.d_weights;
+    const uint32_t* __restrict__ feat = V.feat;
+    const long long r = (MV ? tile - b.item0[in.vi] : tile) * kTcRows + tid;
+    in.r = r;
     const long long p = r >> log2KP;
     const int j = (int)(r & (KP - 1));
     in.s = p * K + j;
@@ -402,8 +411,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   RowIn nxt;
   load_row(blockIdx.x, nxt);
   for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    const long long r = tile * kTcRows + tid;
     const RowIn cur = nxt;
+    const TexBwdView& V = b.v[MV ? cur.vi : 0];
+    const DevCam& c = V.c;
+    const long long r = cur.r, n_rows = V.n_rows;
     const long long s = cur.s;
     const bool in_pix = cur.in_pix, valid = cur.valid;
     const float gT[3] = {cur.gT[0], cur.gT[1], cur.gT[2]};
@@ -537,7 +548,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         }
         st8<OP>(del, tid, 8 * c8, Lt::SD, v);
       }
-      if (in_pix) dweff[s] = valid ? T0 * dC[0] + T1 * dC[1] + T2 * dC[2] + dWx : 0.f;
+      if (in_pix) V.dweff[s] = valid ? T0 * dC[0] + T1 * dC[1] + T2 * dC[2] + dWx : 0.f;
     }
     if constexpr (H2 > 0) {
       sync_to_mma();
@@ -595,7 +606,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         if (r < n_rows) {
 #pragma unroll
           for (int i = 0; i < 8; ++i)  // streamed to the hash backward: evict-first
-            __stcs(gin + (long long)(8 * c16 + i) * R + r,
+            __stcs(V.gin + (long long)(8 * c16 + i) * R + r,
                    make_float2(v[2 * i] * (1.f / OP::kScale), v[2 * i + 1] * (1.f / OP::kScale)));
         }
       }
@@ -638,23 +649,23 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
         if (tid < IN) atomicAdd(dW1 + (16 * c16 + i) * IN + tid, v[i] * (1.f / OP::kScale));  // dW1[o][i]
     }
   }
-  if (!ok && tid == 0 && status) atomicOr(status, kStatusTimeout);
+  if (!ok && tid == 0)  // a wait that ran out marks every view of the launch
+    for (int v = 0; v < b.n; ++v)
+      if (b.v[v].status) atomicOr(b.v[v].status, kStatusTimeout);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lt::cols));
 }
 
 template <int IN, int H1, int H2, typename OP, int OUT = 3>
-cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const float* w,
-                       const uint32_t* feat, const float* weights, const int* ids,
-                       const float* d_image, const float* d_weights, const float* d_textures,
-                       float* dweff, float2* gin, float* d_mlp, int* status, cudaStream_t st) {
+cudaError_t tex_bwd_tc(int K, int KP, const float* w, const ViewBatch<TexBwdView>& b, float* d_mlp,
+                       cudaStream_t st) {
   using Lt = TcLayout<IN, H1, H2, OUT>;
   int log2KP = 0;
   while ((1 << log2KP) < KP) ++log2KP;
-  const long long n_tiles = (n_rows + kTcRows - 1) / kTcRows;
+  const long long n_tiles = b.item0[b.n];
   if (n_tiles == 0) return cudaSuccess;
-  auto kern = k_tex_bwd_tc<IN, H1, H2, OP, OUT>;
+  auto kern = b.n > 1 ? k_tex_bwd_tc<IN, H1, H2, OP, OUT, true> : k_tex_bwd_tc<IN, H1, H2, OP, OUT, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::total);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 152;
@@ -665,9 +676,7 @@ cudaError_t tex_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, const f
       current_tuning().tex_bwd_ctas, 2LL * (Lt::total + 1024) <= 227LL * 1024 ? 2 : 1);
   const unsigned grid = (unsigned)std::min<long long>(n_tiles, per_sm * nsm);
   NEXEL_PROF("texture_bwd_tc", st);
-  kern<<<grid, kTcThreads, Lt::total, st>>>(c, K, log2KP, n_rows, n_tiles, w, feat, weights, ids,
-                                            d_image, d_weights, d_textures, dweff, gin, d_mlp,
-                                            status, tc_wait_fault());
+  kern<<<grid, kTcThreads, Lt::total, st>>>(b, K, log2KP, w, d_mlp, tc_wait_fault());
   return cudaGetLastError();
 }
 
@@ -747,13 +756,11 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
                     OP::pack2(v[6], v[7]));
 }
 
-template <int IN, int H1, int H2, typename TT, typename OP, int OUT = 3>
+template <int IN, int H1, int H2, typename TT, typename OP, int OUT, bool MV>
 __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
-    DevCam c, FieldDev f, int K, int log2KP, long long n_tiles, float bg0, float bg1, float bg2,
-    const float* __restrict__ notex, const float* __restrict__ weights,
-    const int* __restrict__ ids, const float* __restrict__ depths,
-    const float* __restrict__ T_final, float* __restrict__ image, float* __restrict__ textures,
-    uint32_t* __restrict__ feat_cache, int* __restrict__ status, int fault, int ns) {
+    const __grid_constant__ ViewBatch<TexFwdView> b, FieldDev f, int K, int log2KP, float bg0,
+    float bg1, float bg2, int fault, int ns) {
+  const long long n_tiles = b.item0[b.n];
   using Lt = TcFwdLayout<IN, H1, H2, OUT>;
   constexpr int HL = Lt::HL;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -802,7 +809,11 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
   const uint32_t t0 = tmem, t1 = tmem + 64;
   const uint32_t sb = smem_u32(tc_smem);
   const int KP = 1 << log2KP, PPT = kTcRows >> log2KP;
-  const long long P = (long long)c.W * c.H;
+  // a wait that ran out marks every view of the launch
+  auto mark_timeout = [&]() {
+    for (int v = 0; v < b.n; ++v)
+      if (b.v[v].status) atomicOr(b.v[v].status, kStatusTimeout);
+  };
 
   if (warp < kFwGatherWarps) {
     // ------------------------------------------------------- gather warps
@@ -813,19 +824,24 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
       const int st = i % ns, use = i / ns;  // ns <= kFwStages stages in use
       // the MMA that read this stage kFwStages tiles ago has completed
       if (use > 0 && !wait_bar(&s_empty[st], (uint32_t)((use - 1) & 1), wlim)) {
-        if (tid == 0 && status) atomicOr(status, kStatusTimeout);
+        if (tid == 0) mark_timeout();
         break;
       }
       unsigned char* xs = tc_smem + Lt::xring + st * Lt::xstage;
-      const long long p = tile * PPT + tt % PPT;
+      const int vi = MV ? view_of(b, (int)tile) : 0;  // MV: a batch of views
+      const TexFwdView& V = b.v[vi];
+      const DevCam& c = V.c;
+      const long long lt = MV ? tile - b.item0[vi] : tile;  // the view's own tile index
+      const long long P = (long long)c.W * c.H;
+      const long long p = lt * PPT + tt % PPT;
       const int j = tt / PPT;
       const bool in_pix = p < P && j < K;
       const long long s = p * K + j;
-      const bool valid = in_pix && ids[s] >= 0;
+      const bool valid = in_pix && V.ids[s] >= 0;
       float3 x = make_float3(0.f, 0.f, 0.f);
       float D = 1.f;
       if (valid) {
-        D = depths[s];
+        D = V.depths[s];
         const float3 d = pixel_dir(c, (int)(p % c.W), (int)(p / c.W));
         x = make_float3(c.o[0] + D * d.x, c.o[1] + D * d.y, c.o[2] + D * d.z);
       }
@@ -833,12 +849,12 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
 #pragma unroll
       for (int g8 = 0; g8 < LH / 4; ++g8) {  // 4 levels = 8 features per store
         float v[8];
-        gather4_tc<TT>(f, gh * LH + 4 * g8, x, D, valid, v);
+        gather4_tc<TT>(f, c.fx, gh * LH + 4 * g8, x, D, valid, v);
         const int f0 = gh * (IN / 2) + 8 * g8;
         const uint4 q4 = pack8<OP>(v);
         *reinterpret_cast<uint4*>(xs + cm_off(grow, f0, Lt::SX)) = q4;
-        if (feat_cache && p < P)
-          reinterpret_cast<uint4*>(feat_cache + (size_t)(tile * kTcRows + grow) * (IN / 2))[f0 / 8] = q4;
+        if (V.feat_cache && p < P)
+          reinterpret_cast<uint4*>(V.feat_cache + (size_t)(lt * kTcRows + grow) * (IN / 2))[f0 / 8] = q4;
       }
       // the stage's generic stores become visible to the MMA (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -869,20 +885,24 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
   };
   for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
     const int st = i % ns, use = i / ns;  // ns <= kFwStages stages in use
+    const int vi = MV ? view_of(b, (int)tile) : 0;
+    const TexFwdView& V = b.v[vi];
+    const DevCam& c = V.c;
+    const long long P = (long long)c.W * c.H;
     // this row's composite inputs, fetched before the MMA waits
-    const long long p = tile * PPT + erow / KP;
+    const long long p = (MV ? tile - b.item0[vi] : tile) * PPT + erow / KP;
     const int j = erow & (KP - 1);
     const bool in_pix = p < P && j < K;
     const long long s = p * K + j;
     int id = -1;
     float wj = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f, Tf = 0.f;
     if (in_pix) {
-      id = ids[s];
-      wj = weights[s];
+      id = V.ids[s];
+      wj = V.weights[s];
     }
     if (j == 0 && p < P) {
-      n0 = notex[3 * p]; n1 = notex[3 * p + 1]; n2 = notex[3 * p + 2];
-      Tf = T_final[p];
+      n0 = V.notex[3 * p]; n1 = V.notex[3 * p + 1]; n2 = V.notex[3 * p + 2];
+      Tf = V.T_final[p];
     }
     // R1: h1 = X W1^T -> t0; its completion also frees the stage
     if (leader) {
@@ -969,7 +989,7 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
         } else {
           wj = 0.f;
         }
-        textures[3 * s] = T0; textures[3 * s + 1] = T1; textures[3 * s + 2] = T2;
+        V.textures[3 * s] = T0; V.textures[3 * s + 1] = T1; V.textures[3 * s + 2] = T2;
       }
       float c0 = wj * T0, c1 = wj * T1, c2 = wj * T2;
       for (int dd = 1; dd < KP; dd <<= 1) {
@@ -978,15 +998,15 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
         c2 += __shfl_xor_sync(0xffffffffu, c2, dd);
       }
       if (j == 0 && p < P) {
-        image[3 * p] = n0 + c0 + Tf * bg0;
-        image[3 * p + 1] = n1 + c1 + Tf * bg1;
-        image[3 * p + 2] = n2 + c2 + Tf * bg2;
+        V.image[3 * p] = n0 + c0 + Tf * bg0;
+        V.image[3 * p + 1] = n1 + c1 + Tf * bg1;
+        V.image[3 * p + 2] = n2 + c2 + Tf * bg2;
       }
     }
     // a wait that ran out on any MLP thread ends the loop for all four warps
     ok = mlp_warps_and(ok);
   }
-  if (!ok && q == 0 && lane == 0 && status) atomicOr(status, kStatusTimeout);
+  if (!ok && q == 0 && lane == 0) mark_timeout();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   asm volatile("bar.sync 1, 128;" ::: "memory");
   if (warp == kFwGatherWarps)
@@ -994,17 +1014,15 @@ __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
 }
 
 template <int IN, int H1, int H2, typename TT, typename OP, int OUT = 3>
-cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev& fd,
-                       const float* notex, const float* weights, const int* ids,
-                       const float* depths, const float* T_final, float* image, float* textures,
-                       int* status, cudaStream_t st) {
+cudaError_t tex_fwd_tc(const nexel_settings& s, const FieldDev& fd, const ViewBatch<TexFwdView>& b,
+                       cudaStream_t st) {
   using Lt = TcFwdLayout<IN, H1, H2, OUT>;
   int log2KP = 0;
   while ((1 << log2KP) < s.K) ++log2KP;
-  const long long rows = (long long)c.W * c.H << log2KP;
-  const long long n_tiles = (rows + kTcRows - 1) / kTcRows;
+  const long long n_tiles = b.item0[b.n];
   if (n_tiles == 0) return cudaSuccess;
-  auto kern = k_tex_fwd_tc<IN, H1, H2, TT, OP, OUT>;
+  auto kern = b.n > 1 ? k_tex_fwd_tc<IN, H1, H2, TT, OP, OUT, true>
+                      : k_tex_fwd_tc<IN, H1, H2, TT, OP, OUT, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::total);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 152;
@@ -1014,8 +1032,7 @@ cudaError_t tex_fwd_tc(const DevCam& c, const nexel_settings& s, const FieldDev&
       (unsigned)std::min<long long>(n_tiles, (long long)current_tuning().tex_fwd_ctas * nsm);
   NEXEL_PROF("texture_fwd_tc", st);
   kern<<<grid, kFwThreads, Lt::total, st>>>(
-      c, fd, s.K, log2KP, n_tiles, s.bg[0], s.bg[1], s.bg[2], notex, weights, ids, depths, T_final,
-      image, textures, fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status, tc_wait_fault(),
+      b, fd, s.K, log2KP, s.bg[0], s.bg[1], s.bg[2], tc_wait_fault(),
       std::min(std::max(current_tuning().tex_fwd_stages, 2), kFwStages));
   return cudaGetLastError();
 }
@@ -1050,7 +1067,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather_tc(DevCam c, FieldDev
 #pragma unroll
   for (int g8 = 0; g8 < LH / 4; ++g8) {
     float v[8];
-    gather4_tc<TT>(f, gh * LH + 4 * g8, x, D, valid, v);
+    gather4_tc<TT>(f, f.focal, gh * LH + 4 * g8, x, D, valid, v);
     const int f0 = gh * (IN / 2) + 8 * g8;
     reinterpret_cast<uint4*>(feat + row * (IN / 2))[f0 / 8] =
         make_uint4(OP::pack2(v[0], v[1]), OP::pack2(v[2], v[3]), OP::pack2(v[4], v[5]),
@@ -1080,14 +1097,10 @@ bool tc_arch_supported(int in, int h1, int h2, int out, bool half_table) {
   return hidden && (out == 3 || (out == 48 && half_table));
 }
 
-cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
-                                  int h2, int out, bool f16, const float* w, const uint32_t* feat,
-                                  const float* weights, const int* ids, const float* d_image,
-                                  const float* d_weights, const float* d_textures, float* dweff,
-                                  float2* gin, float* d_mlp, int* status, cudaStream_t st) {
-#define NEXEL_TCB(A, B, C, OPT, O)                                                                \
-  return tex_bwd_tc<A, B, C, OPT, O>(c, K, KP, n_rows, w, feat, weights, ids, d_image, d_weights, \
-                                     d_textures, dweff, gin, d_mlp, status, st)
+cudaError_t launch_texture_bwd_tc_batch(int K, int KP, int in, int h1, int h2, int out, bool f16,
+                                        const float* w, const ViewBatch<TexBwdView>& b,
+                                        float* d_mlp, cudaStream_t st) {
+#define NEXEL_TCB(A, B, C, OPT, O) return tex_bwd_tc<A, B, C, OPT, O>(K, KP, w, b, d_mlp, st)
 #define NEXEL_TCB2(A, B, C, O)           \
   if (out == O) {                        \
     if (f16) NEXEL_TCB(A, B, C, OpF16, O); \
@@ -1106,16 +1119,27 @@ cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_ro
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, const nexel_field& f,
-                                  const FieldDev& fd, const float* notex, const float* weights,
-                                  const int* ids, const float* depths, const float* T_final,
-                                  float* image, float* textures, int* status, cudaStream_t st) {
+cudaError_t launch_texture_bwd_tc(const DevCam& c, int K, int KP, long long n_rows, int in, int h1,
+                                  int h2, int out, bool f16, const float* w, const uint32_t* feat,
+                                  const float* weights, const int* ids, const float* d_image,
+                                  const float* d_weights, const float* d_textures, float* dweff,
+                                  float2* gin, float* d_mlp, int* status, cudaStream_t st) {
+  ViewBatch<TexBwdView> b;
+  b.n = 1;
+  b.item0[0] = 0;
+  b.item0[1] = (int)((n_rows + kTcRows - 1) / kTcRows);
+  b.v[0] = TexBwdView{c, feat, weights, ids, d_image, d_weights, d_textures, dweff, gin, n_rows,
+                      status};
+  return launch_texture_bwd_tc_batch(K, KP, in, h1, h2, out, f16, w, b, d_mlp, st);
+}
+
+cudaError_t launch_texture_fwd_tc_batch(const nexel_settings& s, const nexel_field& f,
+                                        const FieldDev& fd, const ViewBatch<TexFwdView>& b,
+                                        cudaStream_t st) {
   const bool h = s.grid_dtype == NEXEL_F16, f16 = s.mlp_dtype == NEXEL_F16;
   const int in = f.widths[0], h1 = f.widths[1], h2 = f.n_layers == 3 ? f.widths[2] : 0;
   const int out = f.widths[f.n_layers];
-#define NEXEL_TCF(A, B, C, TT, OPT, O)                                                            \
-  return tex_fwd_tc<A, B, C, TT, OPT, O>(c, s, fd, notex, weights, ids, depths, T_final, image, \
-                                         textures, status, st)
+#define NEXEL_TCF(A, B, C, TT, OPT, O) return tex_fwd_tc<A, B, C, TT, OPT, O>(s, fd, b, st)
 #define NEXEL_TCF2(A, B, C)                                \
   if (h && out == 48) {                                    \
     if (f16) NEXEL_TCF(A, B, C, __half, OpF16, 48);        \
@@ -1133,6 +1157,22 @@ cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, cons
 #undef NEXEL_TCF2
 #undef NEXEL_TCF
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_texture_fwd_tc(const DevCam& c, const nexel_settings& s, const nexel_field& f,
+                                  const FieldDev& fd, const float* notex, const float* weights,
+                                  const int* ids, const float* depths, const float* T_final,
+                                  float* image, float* textures, int* status, cudaStream_t st) {
+  int log2KP = 0;
+  while ((1 << log2KP) < s.K) ++log2KP;
+  const long long rows = (long long)c.W * c.H << log2KP;
+  ViewBatch<TexFwdView> b;
+  b.n = 1;
+  b.item0[0] = 0;
+  b.item0[1] = (int)((rows + kTcRows - 1) / kTcRows);
+  b.v[0] = TexFwdView{c, notex, weights, ids, depths, T_final, image, textures,
+                      fd.feat_mode == 1 ? (uint32_t*)fd.feat : nullptr, status};
+  return launch_texture_fwd_tc_batch(s, f, fd, b, st);
 }
 
 cudaError_t launch_texture_gather_tc(const DevCam& c, const nexel_settings& s,

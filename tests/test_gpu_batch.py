@@ -16,14 +16,15 @@ import pytest
 import oracle
 from paper_2512_13796_gb300 import synth
 
-from helpers import (SURFEL_KEYS, compare_forward, compare_grads, gpu_params,
-                     masked_upstream)
+from helpers import (SURFEL_KEYS, UNIT_ROUNDOFF, compare_forward, compare_grads, gpu_params,
+                     ill_conditioned, masked_upstream, reference, reference_grads)
 
 pytestmark = pytest.mark.gpu
 
 TIE, CELL, RELU = 1e-5, 2e-6, 1e-4
 TOL_F32, GRAD_RTOL = 1e-5, 1e-3
 ATOMIC_ORDER_L2 = 1e-5  # same arithmetic, float atomics summed in another order
+MLP_ORDER_L2 = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -86,6 +87,53 @@ def test_batch_small_views_vs_oracle(dev, graph):
     compare_grads(gg, grs, GRAD_RTOL)
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_small_views_tensor_cores_vs_oracle(dev, graph):
+    """The batched step on the tensor-core path (FP16 table, BF16 MLP 16-64-3,
+    feature cache): every per-tile phase runs as one launch over the three
+    views (persistent collection CTAs pulling (view, tile) items, the
+    tcgen05 texturing kernels and the hash-grid backward over the views'
+    concatenated tiles).  Images against the FP64 oracle at the FP32
+    parameters (2e-3), gradients summed over the views per element against
+    the oracle at the parameters the form reads (upstream d_image on pixels
+    with no tie and no kink), with the reduced-precision bound."""
+    import torch
+    from paper_2512_13796_gb300 import render as R
+    scene = synth.make_scene(256, 3, 7, gamma="var")
+    cams = synth.sphere_cameras(np.random.default_rng(11), [(48, 40), (64, 64), (80, 56)])
+    field = synth.make_field(8, 12, 2, (64,), 7, table_std=0.3)
+    st = synth.Settings(K=2)
+    p = gpu_params(scene, dev)
+    fd = R.DeviceField.from_synth(field, dev, "f16", "bf16")
+    step = R.BatchStep(cams, st, fd, p)
+    grs, gas, refs = None, None, []
+    for v, cam in enumerate(cams):
+        ref = reference(scene, cam, st, field)
+        refs.append(ref)
+        ref_b = reference(scene, cam, st, field, mlp="bf16")
+        pix, ok = ref_b["pixels"], ref_b["tie"] == 0
+        P = cam.width * cam.height
+        dI, _, _ = masked_upstream(pix.size, P, st.K, pix, ok, seed=60 + v, with_wt=False)
+        sel = pix[ok]
+        gr, ga = reference_grads(scene, cam, st, field, sel, dI, None, None, "bf16")
+        grs = gr if grs is None else {k: grs[k] + gr[k] for k in gr if k != "mlp_layers"}
+        gas = ga if gas is None else {k: gas[k] + ga[k] for k in ga}
+        step.d_image[v].copy_(torch.from_numpy(dI.astype(np.float32)).view(cam.height,
+                                                                             cam.width, 3))
+    if graph:
+        step.capture()
+        step.replay()
+    else:
+        step.step()
+    torch.cuda.synchronize()
+    assert step.status() == [0, 0, 0]
+    for v, cam in enumerate(cams):
+        compare_forward(_numpy_out(step.out[v]), refs[v], st.K, 2e-3)
+    gg = {k: x.cpu().numpy() for k, x in step.grads.items()}
+    skip = np.unique(np.concatenate([ill_conditioned(scene, c) for c in cams]))
+    compare_grads(gg, grs, GRAD_RTOL, absolute=gas, u=UNIT_ROUNDOFF["bf16"], skip_surfels=skip)
+
+
 def test_batch_config3_matches_single_view_calls(dev):
     import torch
     from paper_2512_13796_gb300 import render as R
@@ -120,7 +168,13 @@ def test_batch_config3_matches_single_view_calls(dev):
     for k, g in grads.items():
         a, b = step.grads[k].double(), g.double()
         err = float((a - b).norm() / b.norm())
-        assert err <= ATOMIC_ORDER_L2, (k, err)
+        # the batched tcgen05 backward sums the MLP weight gradients of tiles
+        # of every view in one CTA's FP32 TMEM accumulators (not view by
+        # view): the same BF16 products added in another order.  The sums
+        # cancel strongly (8.6M rows of random-sign terms), so the rounding
+        # of a reordered FP32 sum is visible at ~1e-4 of the result.
+        bound = MLP_ORDER_L2 if k == "mlp" else ATOMIC_ORDER_L2
+        assert err <= bound, (k, err)
 
 
 def test_batch_capacity_overflow_is_flagged(dev):
