@@ -319,8 +319,8 @@ __global__ void k_preprocess(DevCam c, float alpha_min, int sh_degree, int N,
   float4* a = aux + (size_t)i * kAuxF4;
   a[0] = make_float4(mx, my, z, s1);
   a[1] = make_float4(v1c.x, v1c.y, v1c.z, s2);
-  a[2] = make_float4(v2c.x, v2c.y, v2c.z, 0.f);
-  a[3] = make_float4(nc.x, nc.y, nc.z, 0.f);
+  a[2] = make_float4(v2c.x, v2c.y, v2c.z, 1.f / s1);
+  a[3] = make_float4(nc.x, nc.y, nc.z, 1.f / s2);
 }
 
 // ------------------------------------------------------- scan (exclusive)

@@ -298,15 +298,19 @@ __device__ __forceinline__ void collect_bwd_tile(const CollectBwdView& V, int ti
         float du = 0.f, dv = 0.f;
         if (!clamped) {
           const float al = h.alpha;
-          g[14] = da * al / q1.y;
+          g[14] = da * h.e;            // d alpha / d opacity = e
           const float cpa = -da * al;  // dL/d(pu) * 2 = -dalpha * alpha
+          // d pu / d u = 2 g pu / u, d pu / d g = 2 pu ln|u| (|u| > 0: the
+          // quotient and the logarithm in fast form, a few ulp, well inside
+          // the gradients' tolerance)
+          constexpr float kLn2 = 0.6931471805599453f;
           if (h.u != 0.f) {
-            du = cpa * q1.z * h.pu / h.u;
-            g[15] = cpa * h.pu * logf(fabsf(h.u));
+            du = cpa * q1.z * __fdividef(h.pu, h.u);
+            g[15] = cpa * h.pu * (kLn2 * __log2f(fabsf(h.u)));
           }
           if (h.v != 0.f) {
-            dv = cpa * q1.w * h.pv / h.v;
-            g[16] = cpa * h.pv * logf(fabsf(h.v));
+            dv = cpa * q1.w * __fdividef(h.pv, h.v);
+            g[16] = cpa * h.pv * (kLn2 * __log2f(fabsf(h.v)));
           }
         }
         // camera-space chain (the hit x = t d lies on the plane, so
@@ -317,11 +321,11 @@ __device__ __forceinline__ void collect_bwd_tile(const CollectBwdView& V, int ti
         const float us = h.u * s1, vs = h.v * s2;
         const float rx = us * a1.x + vs * a2.x, ry = us * a1.y + vs * a2.y,
                     rz = us * a1.z + vs * a2.z;
-        const float du1 = du / s1, dv2 = dv / s2;
+        const float du1 = du * a2.w, dv2 = dv * a3.w;  // du / s1, dv / s2
         const float grx = du1 * a1.x + dv2 * a2.x, gry = du1 * a1.y + dv2 * a2.y,
                     grz = du1 * a1.z + dv2 * a2.z;
         const float gtt = dt + grx * rdx + gry * rdy + grz;
-        const float gd = gtt / h.den;
+        const float gd = gtt * h.inv;
         g[0] = -grx + gd * a3.x; g[1] = -gry + gd * a3.y; g[2] = -grz + gd * a3.z;
         g[3] = du1 * rx; g[4] = du1 * ry; g[5] = du1 * rz;
         g[6] = dv2 * rx; g[7] = dv2 * ry; g[8] = dv2 * rz;

@@ -122,10 +122,11 @@ __host__ __device__ inline float3 sh3_grad_dot(float x, float y, float z, const 
 // components are stored divided by fx and fy, so delta is in pixels.
 //
 // Auxiliary camera-space record for the backward (rank order):
-//  a0 = (mu_c, sigma1), a1 = (v1_c, sigma2), a2 = (v2_c, 0), a3 = (n_c, 0).
+//  a0 = (mu_c, sigma1), a1 = (v1_c, sigma2), a2 = (v2_c, 1 / sigma1),
+//  a3 = (n_c, 1 / sigma2).
 
 struct Hit {
-  float dx, dy, den, t, u, v, pu, pv, alpha;  // alpha before clamping
+  float dx, dy, inv, t, u, v, pu, pv, e, alpha;  // inv = 1 / den; alpha = opacity e, unclamped
 };
 
 // |a|^(2 g); exact square for g == 1.
@@ -142,15 +143,17 @@ __device__ __forceinline__ bool eval_surfel(const float4& q0, const float4& q1, 
                                             float alpha_min, Hit& h) {
   h.dx = (fpx - q0.x) - q0.z;
   h.dy = (fpy - q0.y) - q0.w;
-  h.den = fmaf(h.dx, q2.x, fmaf(h.dy, q2.y, q3.z));
-  const float inv = 1.0f / h.den;
+  const float den = fmaf(h.dx, q2.x, fmaf(h.dy, q2.y, q3.z));
+  const float inv = 1.0f / den;
+  h.inv = inv;
   h.t = q1.x * q3.z * inv;  // z dn0 / den: exactly z on the centre ray
   if (!(h.t > near_)) return false;
   h.u = fmaf(h.dx, q2.z, h.dy * q2.w) * inv;
   h.v = fmaf(h.dx, q3.x, h.dy * q3.y) * inv;
   h.pu = pow2g(h.u, q1.z);
   h.pv = pow2g(h.v, q1.w);
-  h.alpha = q1.y * expf(-0.5f * (h.pu + h.pv));
+  h.e = expf(-0.5f * (h.pu + h.pv));
+  h.alpha = q1.y * h.e;
   if (!(h.alpha >= alpha_min) || h.alpha == 0.0f) return false;
   return true;
 }
