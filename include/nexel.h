@@ -193,7 +193,11 @@ int nexel_render_fwd(const nexel_camera* cam, const nexel_settings* settings,
  * accumulate != 0.  Any gradient pointer may be NULL to skip it.  bwd_ws is
  * scratch of nexel_bwd_workspace_size bytes.  Requires alpha_max < 1 (the
  * replay divides by 1 - alpha).  The colour gradient flows only to surfels
- * composited untextured (Eq. 5). */
+ * composited untextured (Eq. 5).  The gradient outputs belong to the call
+ * until it completes on `stream`: no other work may read or write them
+ * meanwhile (d_table is held in a reordered form while the hash-grid
+ * backward runs -- entries 1 and 2 of each 4-entry group swapped -- and
+ * restored before the call's last kernel ends). */
 int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
                      const nexel_field* field, int N, const float* mu, const float* quat,
                      const float* scale, const float* opacity, const float* gamma, void* ws,

@@ -416,7 +416,8 @@ int render_bwd_impl(const nexel_camera* cam, const nexel_settings* settings,
   }
   if (e == cudaSuccess && K > 0)
     e = launch_texture_bwd(c, *settings, *field, bw, B, weights, ids, depths, d_image, d_weights,
-                           d_textures, d_table, d_mlp, settings->cache_features != 0, st);
+                           d_textures, d_table, d_mlp, settings->cache_features != 0,
+                           !atomic_params, st);
   if (e == cudaSuccess) e = launch_collect_bwd(c, *settings, w, L, bw, B, ids, T_final, d_image, st);
   if (e == cudaSuccess)
     e = launch_preprocess_bwd(c, *settings, N, mu, quat, scale, opacity, gamma, w, L, 1, d_mu,

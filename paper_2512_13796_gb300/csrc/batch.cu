@@ -157,6 +157,8 @@ int fused_bwd(int n_views, const nexel_camera* cams, const nexel_settings& s,
                                 ws_layout_for_bytes(cams[0], s.K, N, ws_bytes[0]).counters +
                                 kCountersBatchQueue);
   FieldDev fd = make_fielddev(make_devcam(cams[0]), f);
+  // the hash backward launches run one after another on this stream
+  fd.grad_exclusive = 1;
   const int h2 = f.n_layers == 3 ? f.widths[2] : 0;
   cudaError_t e = cudaSuccess;
   for (int v0 = 0; v0 < n_views && e == cudaSuccess; v0 += kMaxBatchViews) {

@@ -365,11 +365,12 @@ cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const n
                                const float* depths, const float* T_final, float* image,
                                float* textures, void* feat_cache, int* status, cudaStream_t st);
 // feat_cached: the forward left the features in bws (no gather here).
+// grad_exclusive: no other stream accumulates into d_table meanwhile
 cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                char* bws, const BwdLayout& B, const float* weights, const int* ids,
                                const float* depths, const float* d_image, const float* d_weights,
                                const float* d_textures, float* d_table, float* d_mlp,
-                               bool feat_cached, cudaStream_t st);
+                               bool feat_cached, bool grad_exclusive, cudaStream_t st);
 bool texture_arch_supported(const nexel_settings& s, const nexel_field& f);
 
 // Stable LSD radix sort of n (uint32 key, uint32 value) pairs on all 32 key

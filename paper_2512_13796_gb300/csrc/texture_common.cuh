@@ -22,12 +22,17 @@ struct FieldDev {
   // gathering, 0 = unused
   void* feat;
   int feat_mode;
+  // 1: no other work writes the table gradient while this call's hash
+  // backward runs (it may then reorder it temporarily, see hash_bwd.cu);
+  // 0: other streams may accumulate into it concurrently
+  int grad_exclusive;
 };
 
 inline FieldDev make_fielddev(const DevCam& c, const nexel_field& f) {
   FieldDev d;
   d.feat = nullptr;
   d.feat_mode = 0;
+  d.grad_exclusive = 0;
   d.L = f.L;
   d.mask = (uint32_t)f.T - 1u;
   d.focal = c.fx;
