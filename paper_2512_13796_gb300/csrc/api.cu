@@ -395,7 +395,8 @@ int render_bwd_impl(const nexel_camera* cam, const nexel_settings* settings,
                     const float* depths, const float* T_final, const float* d_image,
                     const float* d_weights, const float* d_textures, float* d_mu, float* d_quat,
                     float* d_scale, float* d_opacity, float* d_gamma, float* d_color,
-                    float* d_table, float* d_mlp, bool atomic_params, cudaStream_t st) {
+                    float* d_table, float* d_mlp, int grad_mode, cudaStream_t st) {
+  const bool atomic_params = grad_mode == kGradShared;
   const bool rc = settings->recompute_buffers != 0;
   const int K = settings->K;
   WsLayout L = ws_layout_for_bytes(*cam, K, N, ws_bytes);
@@ -417,7 +418,7 @@ int render_bwd_impl(const nexel_camera* cam, const nexel_settings* settings,
   if (e == cudaSuccess && K > 0)
     e = launch_texture_bwd(c, *settings, *field, bw, B, weights, ids, depths, d_image, d_weights,
                            d_textures, d_table, d_mlp, settings->cache_features != 0,
-                           !atomic_params, st);
+                           grad_mode, st);
   if (e == cudaSuccess) e = launch_collect_bwd(c, *settings, w, L, bw, B, ids, T_final, d_image, st);
   if (e == cudaSuccess)
     e = launch_preprocess_bwd(c, *settings, N, mu, quat, scale, opacity, gamma, w, L, 1, d_mu,
@@ -512,7 +513,7 @@ int nexel_render_bwd(const nexel_camera* cam, const nexel_settings* settings,
   return render_bwd_impl(cam, settings, field, N, mu, quat, scale, opacity, gamma, ws, ws_bytes,
                          bwd_ws, weights, ids, depths, T_final, d_image, d_weights, d_textures,
                          d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color, d_table, d_mlp,
-                         false, st);
+                         accumulate ? kGradExclusive : kGradZeroed, st);
 }
 
 int nexel_read_status(const nexel_camera* cam, const nexel_settings* settings,

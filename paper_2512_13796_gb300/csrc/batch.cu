@@ -150,15 +150,16 @@ int fused_bwd(int n_views, const nexel_camera* cams, const nexel_settings& s,
               const float* const* d_image, const float* const* d_weights,
               const float* const* d_textures, float* d_mu, float* d_quat, float* d_scale,
               float* d_opacity, float* d_gamma, float* d_color, float* d_table, float* d_mlp,
-              cudaStream_t st) {
+              bool zeroed, cudaStream_t st) {
   int KP = 1;
   while (KP < s.K) KP <<= 1;
   unsigned* queue = (unsigned*)((char*)ws[0] +
                                 ws_layout_for_bytes(cams[0], s.K, N, ws_bytes[0]).counters +
                                 kCountersBatchQueue);
   FieldDev fd = make_fielddev(make_devcam(cams[0]), f);
-  // the hash backward launches run one after another on this stream
-  fd.grad_exclusive = 1;
+  // the hash backward launches run one after another on this stream; the
+  // first finds the table gradient zero unless the call accumulates
+  fd.grad_mode = zeroed ? kGradZeroed : kGradExclusive;
   const int h2 = f.n_layers == 3 ? f.widths[2] : 0;
   cudaError_t e = cudaSuccess;
   for (int v0 = 0; v0 < n_views && e == cudaSuccess; v0 += kMaxBatchViews) {
@@ -199,6 +200,7 @@ int fused_bwd(int n_views, const nexel_camera* cams, const nexel_settings& s,
                                       tb, d_mlp, st);
     if (e == cudaSuccess)
       e = launch_hash_bwd_batch(fd, s.K, KP, s.grid_dtype == NEXEL_F16, hb, d_table, st);
+    fd.grad_mode = kGradExclusive;  // later view groups add to what this one left
     if (e == cudaSuccess) e = launch_collect_bwd_batch(s, cb, queue, st);
   }
   for (int v = 0; v < n_views && e == cudaSuccess; ++v) {
@@ -292,7 +294,7 @@ int nexel_render_batch_bwd(int n_views, const nexel_camera* cams, const nexel_se
     return fused_bwd(n_views, cams, *settings, *field, N, mu, quat, scale, opacity, gamma, ws,
                      ws_bytes, bwd_ws, weights, ids, depths, T_final, d_image, d_weights,
                      d_textures, d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color, d_table,
-                     d_mlp, st);
+                     d_mlp, !accumulate, st);
   const int nb = n_views < kBranches ? n_views : kBranches;
   rc = fork_branches(p, nb, st);
   if (rc != NEXEL_OK) return rc;
@@ -301,7 +303,8 @@ int nexel_render_batch_bwd(int n_views, const nexel_camera* cams, const nexel_se
     rc = render_bwd_impl(&cams[v], settings, field, N, mu, quat, scale, opacity, gamma, ws[v],
                          ws_bytes[v], at(bwd_ws, v), at(weights, v), at(ids, v), at(depths, v),
                          at(T_final, v), d_image[v], at(d_weights, v), at(d_textures, v), d_mu,
-                         d_quat, d_scale, d_opacity, d_gamma, d_color, d_table, d_mlp, true, sv);
+                         d_quat, d_scale, d_opacity, d_gamma, d_color, d_table, d_mlp,
+                         kGradShared, sv);
   }
   const int jr = join_branches(p, nb, st);
   return rc != NEXEL_OK ? rc : jr;

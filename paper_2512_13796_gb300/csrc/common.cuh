@@ -365,12 +365,12 @@ cudaError_t launch_texture_fwd(const DevCam& c, const nexel_settings& s, const n
                                const float* depths, const float* T_final, float* image,
                                float* textures, void* feat_cache, int* status, cudaStream_t st);
 // feat_cached: the forward left the features in bws (no gather here).
-// grad_exclusive: no other stream accumulates into d_table meanwhile
+// grad_mode: kGradShared / kGradExclusive / kGradZeroed (d_table)
 cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const nexel_field& f,
                                char* bws, const BwdLayout& B, const float* weights, const int* ids,
                                const float* depths, const float* d_image, const float* d_weights,
                                const float* d_textures, float* d_table, float* d_mlp,
-                               bool feat_cached, bool grad_exclusive, cudaStream_t st);
+                               bool feat_cached, int grad_mode, cudaStream_t st);
 bool texture_arch_supported(const nexel_settings& s, const nexel_field& f);
 
 // Stable LSD radix sort of n (uint32 key, uint32 value) pairs on all 32 key
@@ -423,6 +423,10 @@ int render_fwd_impl(const nexel_camera* cam, const nexel_settings* settings,
 int zero_grads(const nexel_settings* settings, const nexel_field* field, int N, float* d_mu,
                float* d_quat, float* d_scale, float* d_opacity, float* d_gamma, float* d_color,
                float* d_table, float* d_mlp, cudaStream_t st);
+// How a backward call holds its gradient outputs
+constexpr int kGradShared = 0;     // other calls accumulate into them concurrently (atomics)
+constexpr int kGradExclusive = 1;  // this call alone writes them until it completes
+constexpr int kGradZeroed = 2;     // ... and they were zeroed just before it
 int render_bwd_impl(const nexel_camera* cam, const nexel_settings* settings,
                     const nexel_field* field, int N, const float* mu, const float* quat,
                     const float* scale, const float* opacity, const float* gamma, void* ws,
@@ -430,6 +434,6 @@ int render_bwd_impl(const nexel_camera* cam, const nexel_settings* settings,
                     const float* depths, const float* T_final, const float* d_image,
                     const float* d_weights, const float* d_textures, float* d_mu, float* d_quat,
                     float* d_scale, float* d_opacity, float* d_gamma, float* d_color,
-                    float* d_table, float* d_mlp, bool atomic_params, cudaStream_t st);
+                    float* d_table, float* d_mlp, int grad_mode, cudaStream_t st);
 
 }  // namespace nexel

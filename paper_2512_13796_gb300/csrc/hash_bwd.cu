@@ -229,10 +229,10 @@ cudaError_t launch_hash_bwd_batch(const FieldDev& fd, int K, int KP, bool half_t
   // other work writes it meanwhile, T >= 4 and it is 16-byte aligned; else
   // natural order)
   const bool paired =
-      fd.grad_exclusive && d_table && fd.mask >= 3u && ((uintptr_t)d_table & 15u) == 0;
+      fd.grad_mode != kGradShared && d_table && fd.mask >= 3u && ((uintptr_t)d_table & 15u) == 0;
   const long long groups = paired ? (long long)fd.L * ((long long)fd.mask + 1) / 4 : 0;
   const unsigned sgrid = (unsigned)((groups + 255) / 256);
-  if (paired) {
+  if (paired && fd.grad_mode != kGradZeroed) {  // zeros need no reordering
     NEXEL_PROF("hash_bwd_order", st);
     k_swap_pairs<<<sgrid, 256, 0, st>>>(reinterpret_cast<float4*>(d_table), groups);
   }

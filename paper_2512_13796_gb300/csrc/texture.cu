@@ -73,9 +73,9 @@ cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const n
                                char* bws, const BwdLayout& B, const float* weights, const int* ids,
                                const float* depths, const float* d_image, const float* d_weights,
                                const float* d_textures, float* d_table, float* d_mlp,
-                               bool feat_cached, bool grad_exclusive, cudaStream_t st) {
+                               bool feat_cached, int grad_mode, cudaStream_t st) {
   FieldDev fd = make_fielddev(c, f);
-  fd.grad_exclusive = grad_exclusive ? 1 : 0;
+  fd.grad_mode = grad_mode;
   fd.feat = bws + B.feat;
   fd.feat_mode = feat_cached ? 2 : 0;
   if (s.mlp_dtype == NEXEL_BF16 || s.mlp_dtype == NEXEL_F16) {

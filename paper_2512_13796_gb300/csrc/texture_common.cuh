@@ -22,17 +22,18 @@ struct FieldDev {
   // gathering, 0 = unused
   void* feat;
   int feat_mode;
-  // 1: no other work writes the table gradient while this call's hash
-  // backward runs (it may then reorder it temporarily, see hash_bwd.cu);
-  // 0: other streams may accumulate into it concurrently
-  int grad_exclusive;
+  // how the call holds the table gradient (kGradShared: other streams may
+  // accumulate into it concurrently; kGradExclusive: no other work writes it
+  // while the hash backward runs, which may then reorder it temporarily, see
+  // hash_bwd.cu; kGradZeroed: exclusive and all zero on entry)
+  int grad_mode;
 };
 
 inline FieldDev make_fielddev(const DevCam& c, const nexel_field& f) {
   FieldDev d;
   d.feat = nullptr;
   d.feat_mode = 0;
-  d.grad_exclusive = 0;
+  d.grad_mode = 0;
   d.L = f.L;
   d.mask = (uint32_t)f.T - 1u;
   d.focal = c.fx;

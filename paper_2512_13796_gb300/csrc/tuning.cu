@@ -120,7 +120,8 @@ int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
     if (r == NEXEL_OK)
       r = render_bwd_impl(cam, settings, field, N, mu, quat, scale, opacity, gamma, ws, ws_bytes,
                           bwd_ws, weights, ids, depths, T_final, d_image, nullptr, nullptr, d_mu,
-                          d_quat, d_scale, d_opacity, d_gamma, d_color, d_table, d_mlp, false, st);
+                          d_quat, d_scale, d_opacity, d_gamma, d_color, d_table, d_mlp,
+                          kGradZeroed, st);
     return r;
   };
   // median time of reps steps after one untimed step
