@@ -805,8 +805,8 @@ def main():
             "frac": ach / red_peak if ach else None, "red_sectors_per_launch": red_sectors,
             "peak_source": "nexel_peak_l2_reductions in this run: random float2 reductions "
                            "into a 64 MiB L2-resident table (median of 3 x 2e8)",
-            "note": "red_sectors_per_launch = lts__t_sectors_op_red.sum of one ncu capture "
-                    "(profiles/l2_traffic_config2.md); null when hash_bwd.cu changed since"}
+            "note": "red_sectors_per_launch = lts__t_sectors_srcunit_tex_op_red.sum of one ncu "
+                    "capture (profiles/hash_bwd_config2.md); null when hash_bwd.cu changed since"}
     # work counts of the collection pass (device reduction over the BF16
     # job's last forward, outside the timed regions)
     jb = jobs["bf16"]
