@@ -392,7 +392,10 @@ int nexel_prune(int N, float threshold, int color_dim, const float* mu, const fl
 /* Launch-shape tuning (process-wide; no counterpart in the paper): CTAs
  * per SM that the persistent texturing kernels keep in flight -- the tile
  * pipeline depth of the tcgen05 forward (1..2, default 2), of the tcgen05
- * backward (1..2, default 2; 1 where its shared memory allows one) and of
+ * backward (1..3, default 3: tiles in flight per SM; 3 is one CTA of three
+ * tile groups with a dedicated MMA warp, for RGB textures with two hidden
+ * layers of 64 units and up to 32 inputs, and means 2 for other shapes; 1
+ * where the shared memory of the other shapes allows one) and of
  * the FP32 chunked kernels (1..2, default 2) -- the CTA size of the hash
  * backward (128 or 256, default 256), the number of surfel records the
  * collection kernels stage in shared memory per batch (128, 256 or 512,

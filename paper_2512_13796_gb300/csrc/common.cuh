@@ -387,7 +387,7 @@ cudaError_t exclusive_scan_u32(uint32_t* a, long long n, uint32_t* sums, uint32_
 // size of the hash backward, the surfel staging batch of the collection
 // kernels and the depth of the texturing forward's operand ring.
 struct Tuning {
-  int tex_fwd_ctas = 2, tex_bwd_ctas = 2, f32_ctas = 2, hash_block = 256;
+  int tex_fwd_ctas = 2, tex_bwd_ctas = 3, f32_ctas = 2, hash_block = 256;
   int collect_batch = 256, tex_fwd_stages = 4;
 };
 Tuning current_tuning();

@@ -296,6 +296,11 @@ struct TexBwdView {
   long long n_rows;
   int* status;
 };
+// The tcgen05 backward with three tile groups per CTA (texture_tc_bwd3.cu):
+// the shapes it takes, and its launch.
+bool tex_bwd_tc3_supported(int in, int h1, int h2, int out);
+cudaError_t launch_texture_bwd_tc3(int K, int KP, int in, bool f16, const float* w,
+                                   const ViewBatch<TexBwdView>& b, float* d_mlp, cudaStream_t st);
 cudaError_t launch_texture_bwd_tc_batch(int K, int KP, int in, int h1, int h2, int out, bool f16,
                                         const float* w, const ViewBatch<TexBwdView>& b,
                                         float* d_mlp, cudaStream_t st);

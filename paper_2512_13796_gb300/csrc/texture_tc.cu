@@ -32,7 +32,7 @@
 // 16 bytes per core matrix); a descriptor's leading byte offset is the
 // stride between core matrices along K and its stride byte offset the stride
 // along M/N, for K-major and MN-major operands alike.
-#include "texture_common.cuh"
+#include "tc_common.cuh"
 
 #include <algorithm>
 
@@ -40,160 +40,7 @@ namespace nexel {
 
 namespace {
 
-constexpr int kTcRows = 128;
-constexpr int kTcThreads = 128;
-constexpr int kTcWaitLimit = 1 << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// shared-memory matrix descriptor, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// instruction descriptor, kind::f16: A and B of format fmt (0 = F16,
-// 1 = BF16), F32 accumulator, M x N
-__host__ __device__ constexpr uint32_t idesc(int m, int n, int a_mn, int b_mn, uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
-         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
-                                    bool acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(id), "r"((uint32_t)acc));
-}
-
-__device__ __forceinline__ void commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-      smem_u32(bar)));
-}
-
-// Bounded wait for the mbarrier phase `parity`; false when `limit` polls ran
-// out.
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int limit) {
-  for (int it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity));
-    if (done) return true;
-  }
-  return false;
-}
-
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane (one wait)
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Thread-to-MMA hand-over: generic-proxy shared stores and TMEM reads of all
-// threads happen before the MMAs thread 0 issues next.
-__device__ __forceinline__ void sync_to_mma() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// MMA operand type.  BF16; or FP16, where the backward scales the gradient
-// entering the MLP by 128 and unscales the feature and weight gradients (the
-// paper trains the MLP in FP16 with a loss scale of 128).
-struct OpBf16 {
-  static constexpr uint32_t kFmt = 1;
-  static constexpr float kScale = 1.f;
-  __device__ static uint32_t pack2(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-  }
-  __device__ static float2 unpack2(uint32_t w) {
-    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
-  }
-  __device__ static uint16_t cvt(float x) {
-    __nv_bfloat16 b = __float2bfloat16_rn(x);
-    return *reinterpret_cast<uint16_t*>(&b);
-  }
-  __device__ static float round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-};
-struct OpF16 {
-  static constexpr uint32_t kFmt = 0;
-  static constexpr float kScale = 128.f;
-  __device__ static uint32_t pack2(float lo, float hi) {
-    __half2 v = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-  }
-  __device__ static float2 unpack2(uint32_t w) {
-    return __half22float2(*reinterpret_cast<const __half2*>(&w));
-  }
-  __device__ static uint16_t cvt(float x) {
-    __half h = __float2half_rn(x);
-    return *reinterpret_cast<uint16_t*>(&h);
-  }
-  __device__ static float round(float x) { return __half2float(__float2half_rn(x)); }
-};
-
-// byte offset of element (row r, feature f) in a core-matrix tile whose
-// 8-row groups are sg bytes apart
-__host__ __device__ constexpr uint32_t cm_off(int r, int f, int sg) {
-  return (uint32_t)((r >> 3) * sg + (f >> 3) * 128 + (r & 7) * 16 + (f & 7) * 2);
-}
-
-// Stores 8 consecutive features f0..f0+7 (f0 % 8 == 0) of row r.
-template <typename OP>
-__device__ __forceinline__ void st8(unsigned char* base, int r, int f0, int sg, const float* v) {
-  uint4 q = make_uint4(OP::pack2(v[0], v[1]), OP::pack2(v[2], v[3]), OP::pack2(v[4], v[5]),
-                       OP::pack2(v[6], v[7]));
-  *reinterpret_cast<uint4*>(base + cm_off(r, f0, sg)) = q;
-}
+using namespace tcb;
 
 // Features of levels l0 .. l0 + 3 at x (Eqs. 3-4): all 32 corner loads are
 // issued before any is used.  The spatial hash of a corner is the XOR of
@@ -452,8 +299,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     if (tid == 0 && issue) {
 #pragma unroll
       for (int kk = 0; kk < IN / 16; ++kk)
-        mma(t0, sdesc(sb + Lt::act + kk * 256, 128, Lt::SA),
-            sdesc(sb + Lt::w1 + kk * 256, 128, IN / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
+        mma(t0, dadv(sdesc(sb + Lt::act, 128, Lt::SA), kk * 256),
+            dadv(sdesc(sb + Lt::w1, 128, IN / 8 * 128), kk * 256), idesc(128, H1, 0, 0, OP::kFmt),
+            kk > 0);
       if constexpr (OUT == 48)
         mma(t_e, sdesc(sb + Lt::ytile, 128, 256), sdesc(sb + Lt::w3p, 128, 256),
             idesc(128, 3 * HL, 0, 0, OP::kFmt), false);
@@ -482,8 +330,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       if (tid == 0 && issue) {
 #pragma unroll
         for (int kk = 0; kk < H1 / 16; ++kk)
-          mma(t0, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 256, 128, Lt::SA),
-              sdesc(sb + Lt::w2 + kk * 256, 128, H1 / 8 * 128), idesc(128, H2, 0, 0, OP::kFmt), kk > 0);
+          mma(t0, dadv(sdesc(sb + Lt::act, 128, Lt::SA), (IN / 8) * 128 + kk * 256),
+              dadv(sdesc(sb + Lt::w2, 128, H1 / 8 * 128), kk * 256),
+              idesc(128, H2, 0, 0, OP::kFmt), kk > 0);
         commit(&s_bar);
       }
       ok = ok && wait_bar(&s_bar, phase, wlim);
@@ -556,8 +405,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
       if (tid == 0 && issue) {
 #pragma unroll
         for (int kk = 0; kk < H2 / 16; ++kk)
-          mma(t0, sdesc(sb + Lt::del + kk * 256, 128, Lt::SD),
-              sdesc(sb + Lt::w2t + kk * 256, 128, H2 / 8 * 128), idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
+          mma(t0, dadv(sdesc(sb + Lt::del, 128, Lt::SD), kk * 256),
+              dadv(sdesc(sb + Lt::w2t, 128, H2 / 8 * 128), kk * 256),
+              idesc(128, H1, 0, 0, OP::kFmt), kk > 0);
         commit(&s_bar);
       }
       ok = ok && wait_bar(&s_bar, phase, wlim);
@@ -578,16 +428,17 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     if (tid == 0 && issue) {
 #pragma unroll
       for (int kk = 0; kk < H1 / 16; ++kk)
-        mma(t0, sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 256, 128, Lt::SD),
-            sdesc(sb + Lt::w1t + kk * 256, 128, H1 / 8 * 128), idesc(128, IN, 0, 0, OP::kFmt), kk > 0);
+        mma(t0, dadv(sdesc(sb + Lt::del, 128, Lt::SD), (Lt::D1 / 8) * 128 + kk * 256),
+            dadv(sdesc(sb + Lt::w1t, 128, H1 / 8 * 128), kk * 256),
+            idesc(128, IN, 0, 0, OP::kFmt), kk > 0);
       // K = rows: 16 rows = two 8-row groups per MMA
+      const uint64_t aM = sdesc(sb + Lt::act, Lt::SA, 128), dM = sdesc(sb + Lt::del, Lt::SD, 128);
 #pragma unroll 1
       for (int kk = 0; kk < kTcRows / 16; ++kk) {
         const bool acc = !(first && kk == 0);
-        mma(t_da, sdesc(sb + Lt::act + (IN / 8) * 128 + kk * 2 * Lt::SA, Lt::SA, 128),
-            sdesc(sb + Lt::del + kk * 2 * Lt::SD, Lt::SD, 128), idesc(128, HL + Lt::ON, 1, 1, OP::kFmt), acc);
-        mma(t_db, sdesc(sb + Lt::act + kk * 2 * Lt::SA, Lt::SA, 128),
-            sdesc(sb + Lt::del + (Lt::D1 / 8) * 128 + kk * 2 * Lt::SD, Lt::SD, 128),
+        mma(t_da, dadv(aM, (IN / 8) * 128 + kk * 2 * Lt::SA), dadv(dM, kk * 2 * Lt::SD),
+            idesc(128, HL + Lt::ON, 1, 1, OP::kFmt), acc);
+        mma(t_db, dadv(aM, kk * 2 * Lt::SA), dadv(dM, (Lt::D1 / 8) * 128 + kk * 2 * Lt::SD),
             idesc(128, H1, 1, 1, OP::kFmt), acc);
       }
       commit(&s_bar);
@@ -750,11 +601,6 @@ __device__ __forceinline__ void bar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <typename OP>
-__device__ __forceinline__ uint4 pack8(const float* v) {
-  return make_uint4(OP::pack2(v[0], v[1]), OP::pack2(v[2], v[3]), OP::pack2(v[4], v[5]),
-                    OP::pack2(v[6], v[7]));
-}
 
 template <int IN, int H1, int H2, typename TT, typename OP, int OUT, bool MV>
 __global__ void __launch_bounds__(kFwThreads, 2) k_tex_fwd_tc(
@@ -1100,6 +946,9 @@ bool tc_arch_supported(int in, int h1, int h2, int out, bool half_table) {
 cudaError_t launch_texture_bwd_tc_batch(int K, int KP, int in, int h1, int h2, int out, bool f16,
                                         const float* w, const ViewBatch<TexBwdView>& b,
                                         float* d_mlp, cudaStream_t st) {
+  // three tiles in flight per SM where the shape allows (texture_tc_bwd3.cu)
+  if (current_tuning().tex_bwd_ctas >= 3 && tex_bwd_tc3_supported(in, h1, h2, out))
+    return launch_texture_bwd_tc3(K, KP, in, f16, w, b, d_mlp, st);
 #define NEXEL_TCB(A, B, C, OPT, O) return tex_bwd_tc<A, B, C, OPT, O>(K, KP, w, b, d_mlp, st)
 #define NEXEL_TCB2(A, B, C, O)           \
   if (out == O) {                        \

@@ -14,12 +14,12 @@
 namespace nexel {
 namespace {
 
-std::atomic<int> g_fwd{2}, g_bwd{2}, g_f32{2}, g_hash{256}, g_batch{256}, g_stages{4};
+std::atomic<int> g_fwd{2}, g_bwd{3}, g_f32{2}, g_hash{256}, g_batch{256}, g_stages{4};
 std::atomic<int> g_tc_wait_fault{0};
 
 bool valid(const nexel_tuning& t) {
   return t.tex_fwd_ctas_per_sm >= 1 && t.tex_fwd_ctas_per_sm <= 2 &&
-         t.tex_bwd_ctas_per_sm >= 1 && t.tex_bwd_ctas_per_sm <= 2 && t.f32_ctas_per_sm >= 1 &&
+         t.tex_bwd_ctas_per_sm >= 1 && t.tex_bwd_ctas_per_sm <= 3 && t.f32_ctas_per_sm >= 1 &&
          t.f32_ctas_per_sm <= 2 && (t.hash_block == 128 || t.hash_block == 256) &&
          (t.collect_batch == 128 || t.collect_batch == 256 || t.collect_batch == 512) &&
          t.tex_fwd_stages >= 2 && t.tex_fwd_stages <= 4;
@@ -153,7 +153,7 @@ int nexel_autotune(const nexel_camera* cam, const nexel_settings* settings,
   for (int knob = 0; knob < 6 && rc == NEXEL_OK; ++knob) {
     std::vector<int> vals;
     if (knob == 0) vals = {1, 2};
-    else if (knob == 1) vals = {1, 2};
+    else if (knob == 1) vals = {1, 2, 3};
     else if (knob == 2) vals = {1, 2};
     else if (knob == 3) vals = {128, 256};
     else if (knob == 4) vals = {128, 256, 512};

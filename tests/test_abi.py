@@ -149,13 +149,13 @@ def test_tuning_round_trip_and_checks(lib):
     fields = ("tex_fwd_ctas_per_sm", "tex_bwd_ctas_per_sm", "f32_ctas_per_sm", "hash_block",
               "collect_batch", "tex_fwd_stages")
     t0 = N_.nexel_get_tuning()
-    assert tuple(getattr(t0, f) for f in fields) == (2, 2, 2, 256, 256, 4)
+    assert tuple(getattr(t0, f) for f in fields) == (2, 3, 2, 256, 256, 4)
     t = N_.Tuning(1, 1, 1, 128, 512, 2)
     N_.nexel_set_tuning(t)
     g = N_.nexel_get_tuning()
     assert tuple(getattr(g, f) for f in fields) == (1, 1, 1, 128, 512, 2)
     for bad in (N_.Tuning(0, 1, 1, 128, 256, 4), N_.Tuning(3, 1, 1, 128, 256, 4),
-                N_.Tuning(1, 3, 1, 128, 256, 4), N_.Tuning(1, 1, 1, 64, 256, 4),
+                N_.Tuning(1, 4, 1, 128, 256, 4), N_.Tuning(1, 1, 1, 64, 256, 4),
                 N_.Tuning(1, 1, 1, 128, 64, 4), N_.Tuning(1, 1, 1, 128, 256, 1),
                 N_.Tuning(1, 1, 1, 128, 256, 5)):
         assert lib.nexel_set_tuning(C.byref(bad)) == -1

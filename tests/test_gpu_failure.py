@@ -82,18 +82,20 @@ def test_nonfinite_surfels_are_culled_and_counted(dev):
 
 
 @pytest.mark.parametrize("mlp", ["bf16", "f16"])
-def test_tc_wait_timeout_reported_and_recovered(dev, mlp):
+@pytest.mark.parametrize("levels,hidden", [(8, (64,)), (16, (64, 64))])
+def test_tc_wait_timeout_reported_and_recovered(dev, mlp, levels, hidden):
     """The test hook makes every tensor-core kernel wait, with a short
     bound, for MMAs it never issued: the forward and the backward return,
     nexel_read_status reports NEXEL_ERR_TIMEOUT, and with the hook off the
     same calls run normally again (each CTA freed its TMEM) and match a
-    fresh run."""
+    fresh run.  Two hidden layers with 32 inputs take the backward with
+    three tile groups per CTA and a dedicated MMA thread."""
     import torch
     from paper_2512_13796_gb300 import _native as N_
     from paper_2512_13796_gb300 import render as R
     w = synth.workload(0)
     sc, cam, st = w.scene, synth.front_camera(96, 80), w.settings
-    fld = synth.make_field(8, 12, 2, (64,), 0)
+    fld = synth.make_field(levels, 12, 2, hidden, 0)
     P, K = cam.width * cam.height, st.K
     dI = np.random.default_rng(3).normal(size=(P, 3)).astype(np.float32)
     good, g_good, _ = run_gpu(sc, cam, st, fld, dev, grid="f16", mlp=mlp, d_image=dI,
