@@ -204,10 +204,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
   // MMA rounds run
   struct RowIn {
     uint4 x[IN / 8];
-    float gT[3], dC[3], dWx;
+    float w, dC[3], dT[3], dWx;
     long long s, r;  // sample and row within the tile's view
-    int vi;          // the tile's view
-    bool valid, in_pix;
+    int vi, id;      // the tile's view, the slot's surfel
+    bool in_pix;
   };
   auto load_row = [&](long long tile, RowIn& in) {
     // MV: a batch of views (else one view, at a fixed index)
@@ -227,26 +227,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     const int j = (int)(r & (KP - 1));
     in.s = p * K + j;
     in.in_pix = tile < n_tiles && r < n_rows && p < P && j < K;
-    // every load of the row is issued at once (none waits for the id):
-    // an empty slot's weight is 0, and its values are dropped below
-    int id = -1;
-    float w = 0.f, t0v = 0.f, t1v = 0.f, t2v = 0.f, dwv = 0.f;
+    // every load of the row is issued at once and nothing here waits for
+    // them: the values are first used when the tile is staged, a tile later
+    in.id = -1;
+    in.w = in.dWx = 0.f;
     in.dC[0] = in.dC[1] = in.dC[2] = 0.f;
+    in.dT[0] = in.dT[1] = in.dT[2] = 0.f;
     if (in.in_pix) {
-      id = ids[in.s];
-      w = weights[in.s];
+      in.id = ids[in.s];
+      in.w = weights[in.s];
       in.dC[0] = d_image[3 * p]; in.dC[1] = d_image[3 * p + 1]; in.dC[2] = d_image[3 * p + 2];
       if (d_textures) {
-        t0v = d_textures[3 * in.s]; t1v = d_textures[3 * in.s + 1]; t2v = d_textures[3 * in.s + 2];
+        in.dT[0] = d_textures[3 * in.s]; in.dT[1] = d_textures[3 * in.s + 1];
+        in.dT[2] = d_textures[3 * in.s + 2];
       }
-      if (d_weights) dwv = d_weights[in.s];
+      if (d_weights) in.dWx = d_weights[in.s];
     }
-    in.valid = in.in_pix && id >= 0;
-    in.gT[0] = in.valid ? fmaf(w, in.dC[0], t0v) : 0.f;
-    in.gT[1] = in.valid ? fmaf(w, in.dC[1], t1v) : 0.f;
-    in.gT[2] = in.valid ? fmaf(w, in.dC[2], t2v) : 0.f;
-    in.dWx = in.valid ? dwv : 0.f;
-    if (!in.valid) in.dC[0] = in.dC[1] = in.dC[2] = 0.f;
     // cached BF16 features of this row; zero beyond the pixels
 #pragma unroll
     for (int c8 = 0; c8 < IN / 8; ++c8) {
@@ -263,10 +259,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tex_bwd_tc(
     const DevCam& c = V.c;
     const long long r = cur.r, n_rows = V.n_rows;
     const long long s = cur.s;
-    const bool in_pix = cur.in_pix, valid = cur.valid;
-    const float gT[3] = {cur.gT[0], cur.gT[1], cur.gT[2]};
-    const float dC[3] = {cur.dC[0], cur.dC[1], cur.dC[2]};
-    const float dWx = cur.dWx;
+    // the row's texture gradient gT = w dL/dC + dL/dT (Eq. 6); nothing for
+    // an empty slot or a row beyond the pixels
+    const bool in_pix = cur.in_pix, valid = cur.in_pix && cur.id >= 0;
+    const float gT[3] = {valid ? fmaf(cur.w, cur.dC[0], cur.dT[0]) : 0.f,
+                         valid ? fmaf(cur.w, cur.dC[1], cur.dT[1]) : 0.f,
+                         valid ? fmaf(cur.w, cur.dC[2], cur.dT[2]) : 0.f};
+    const float dC[3] = {valid ? cur.dC[0] : 0.f, valid ? cur.dC[1] : 0.f, valid ? cur.dC[2] : 0.f};
+    const float dWx = valid ? cur.dWx : 0.f;
     // stage X and d3
 #pragma unroll
     for (int c8 = 0; c8 < IN / 8; ++c8)

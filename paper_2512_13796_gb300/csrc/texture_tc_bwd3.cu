@@ -9,17 +9,22 @@
 //   warps 4 g .. 4 g + 3 (g = 0, 1, 2): tile group g.  Thread t of the group
 //     owns row t of the group's current 128-row tile (TMEM lane t; the warp
 //     index modulo 4 is the TMEM lane quadrant).  Per tile the group stages
-//     X and d3, then runs four epilogues, each after one MMA round:
+//     X and d3, then runs four MMA rounds, each followed by an epilogue:
 //       R1  h1 = X W1^T
 //       R2  h2 = h1 W2^T;  then on CUDA cores T = W3 h2, dL/dW_j and
 //           d2 = (W3^T d3) * [h2 > 0]
 //       R3  d1 = (d2 W2) * [h1 > 0];  with it Da += [h1 | h2]^T [d2 | d3]
 //       R4  feature gradient d1 W1;  with it Db += [X | ...]^T d1
-//     handing each round to the MMA warp through its `ready` mbarrier and
-//     waiting for the round's tcgen05 commit on its `done` mbarrier.
-//   warp 12: one thread issues every MMA of the CTA, serving the groups in
-//     the order their rounds become ready, so all MMAs come from one thread
-//     (the weight-gradient accumulators Da, Db are shared by the groups).
+//     The group's thread 0 issues its own rounds once the group's named
+//     barrier shows all 128 rows in place, and the group waits for the
+//     round's tcgen05 commit on its `done` mbarrier.  A single thread issues
+//     about one MMA per 44 cycles whatever its width up to N = 128, so one
+//     issuer for the CTA would serialise the groups.
+//   warp 12: one thread issues the weight-gradient products Da and Db, which
+//     the groups share (one issuer per accumulator), in the order the groups
+//     hand their tiles over (`wready` / `wdone` mbarriers).
+// A row's inputs for the next tile are loaded while the current tile runs
+// and used only when it is staged.
 // Shared memory per group: the activation tile [X | h1 | h2] and the delta
 // tile [d2 | d3]; d1 overwrites d2 once R3 and Da (the only readers of d2)
 // have completed, which keeps a group at 60 KB and three groups plus the
@@ -40,7 +45,7 @@ using namespace tcb;
 
 constexpr int kB3Groups = 3;
 constexpr int kB3Threads = (4 * kB3Groups + 1) * 32;
-constexpr int kB3MmaWarp = 4 * kB3Groups;
+constexpr int kB3MmaWarp = 4 * kB3Groups;  // the weight-gradient MMA warp
 
 template <int IN, int H1, int H2>
 struct TcBwd3Layout {
@@ -76,12 +81,10 @@ __device__ __forceinline__ bool bar_test(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// A group's hand-over of a round to the MMA thread: its shared-memory stores
-// (generic proxy) and TMEM reads are ordered before the MMAs issued next.
-__device__ __forceinline__ void hand_over(uint64_t* ready) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(ready)) : "memory");
+// A plain arrival on a hand-over barrier (the caller has ordered its
+// shared-memory writes for the async proxy before).
+__device__ __forceinline__ void bar_arrive_only(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // AND of `v` over the 128 threads of group g (named barrier 1 + g).
@@ -108,9 +111,10 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
   const bool issue = fault == 0;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_ready[kB3Groups];
-  __shared__ __align__(8) uint64_t s_done[kB3Groups];
-  __shared__ __align__(8) uint64_t s_fin;
+  __shared__ __align__(8) uint64_t s_done[kB3Groups];    // a group's own rounds complete
+  __shared__ __align__(8) uint64_t s_wready[kB3Groups];  // group -> weight-gradient issuer
+  __shared__ __align__(8) uint64_t s_wdone[kB3Groups];   // weight-gradient issuer -> group
+  __shared__ __align__(8) uint64_t s_fin[kB3Groups + 1];  // all MMAs of an issuer complete
   __shared__ int s_bad, s_acc;
   const int tid = threadIdx.x, warp = tid >> 5;
   float* w3s = reinterpret_cast<float*>(tc_smem + Lt::w3);
@@ -143,10 +147,12 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
   }
   if (tid == 0) {
     for (int g = 0; g < kB3Groups; ++g) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&s_ready[g])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_done[g])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&s_wready[g])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_wdone[g])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_fin)));
+    for (int r = 0; r <= kB3Groups; ++r)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_fin[r])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_bad = 0;
     s_acc = 0;
@@ -171,17 +177,19 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
     unsigned char* del = act + Lt::act_bytes;
     const int KP = 1 << log2KP;
     bool ok = true;
-    uint32_t dph = 0;  // phase of the group's `done` barrier
+    uint32_t dph = 0, wph = 0;  // phases of the group's `done` and `wdone` barriers
 
     // per-row inputs of a tile; the group's next tile's are loaded while
     // this one's rounds run
     struct RowIn {
       uint4 x[IN / 8];
-      float gT[3], dC[3], dWx;
+      float w, dC[3], dT[3], dWx;
       long long s, r;  // sample and row within the tile's view
-      int vi;          // the tile's view
-      bool valid, in_pix;
+      int vi, id;      // the tile's view, the slot's surfel
+      bool in_pix;
     };
+    // issues the loads of a row's inputs and nothing that waits for them:
+    // the values are first used when the tile is staged, a tile later
     auto load_row = [&](long long tile, RowIn& in) {
       in.vi = (MV && tile < n_tiles) ? view_of(b, (int)tile) : 0;
       const TexBwdView& V = b.v[in.vi];
@@ -193,28 +201,23 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
       const int j = (int)(r & (KP - 1));
       in.s = p * K + j;
       in.in_pix = tile < n_tiles && r < n_rows && p < P && j < K;
-      int id = -1;
-      float w = 0.f, t0v = 0.f, t1v = 0.f, t2v = 0.f, dwv = 0.f;
+      in.id = -1;
+      in.w = in.dWx = 0.f;
       in.dC[0] = in.dC[1] = in.dC[2] = 0.f;
+      in.dT[0] = in.dT[1] = in.dT[2] = 0.f;
       if (in.in_pix) {
-        id = V.ids[in.s];
-        w = V.weights[in.s];
+        in.id = V.ids[in.s];
+        in.w = V.weights[in.s];
         in.dC[0] = V.d_image[3 * p];
         in.dC[1] = V.d_image[3 * p + 1];
         in.dC[2] = V.d_image[3 * p + 2];
         if (V.d_textures) {
-          t0v = V.d_textures[3 * in.s];
-          t1v = V.d_textures[3 * in.s + 1];
-          t2v = V.d_textures[3 * in.s + 2];
+          in.dT[0] = V.d_textures[3 * in.s];
+          in.dT[1] = V.d_textures[3 * in.s + 1];
+          in.dT[2] = V.d_textures[3 * in.s + 2];
         }
-        if (V.d_weights) dwv = V.d_weights[in.s];
+        if (V.d_weights) in.dWx = V.d_weights[in.s];
       }
-      in.valid = in.in_pix && id >= 0;
-      in.gT[0] = in.valid ? fmaf(w, in.dC[0], t0v) : 0.f;
-      in.gT[1] = in.valid ? fmaf(w, in.dC[1], t1v) : 0.f;
-      in.gT[2] = in.valid ? fmaf(w, in.dC[2], t2v) : 0.f;
-      in.dWx = in.valid ? dwv : 0.f;
-      if (!in.valid) in.dC[0] = in.dC[1] = in.dC[2] = 0.f;
 #pragma unroll
       for (int c8 = 0; c8 < IN / 8; ++c8) {
         in.x[c8] = make_uint4(0u, 0u, 0u, 0u);
@@ -245,6 +248,48 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
       }
       return make_uint2(m[0], m[1]);
     };
+    // round r of the group's tile, issued by the group's own thread 0 once
+    // all 128 rows are in place (rounds 2, 3 also go to the weight-gradient
+    // thread, for Da and Db)
+    const uint32_t sgrp = sb + g * Lt::group_bytes;
+    auto issue_round = [&](int r) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if (r >= 2) bar_arrive_only(&s_wready[g]);
+      asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (gt == 0 && issue) {
+        constexpr uint32_t fmt = OP::kFmt;
+        const uint64_t aK = sdesc(sgrp, 128, Lt::SA), dK = sdesc(sgrp + Lt::act_bytes, 128, Lt::SD);
+        if (r == 0) {  // R1: h1 = X W1^T
+          const uint64_t wd = sdesc(sb + Lt::w1, 128, IN / 8 * 128);
+#pragma unroll
+          for (int kk = 0; kk < IN / 16; ++kk)
+            mma(tg, dadv(aK, kk * 256), dadv(wd, kk * 256), idesc(128, H1, 0, 0, fmt), kk > 0);
+        } else if (r == 1) {  // R2: h2 = h1 W2^T
+          const uint64_t wd = sdesc(sb + Lt::w2, 128, H1 / 8 * 128);
+#pragma unroll
+          for (int kk = 0; kk < H1 / 16; ++kk)
+            mma(tg, dadv(aK, (IN / 8) * 128 + kk * 256), dadv(wd, kk * 256),
+                idesc(128, H2, 0, 0, fmt), kk > 0);
+        } else if (r == 2) {  // R3: d2 W2
+          const uint64_t wd = sdesc(sb + Lt::w2t, 128, H2 / 8 * 128);
+#pragma unroll
+          for (int kk = 0; kk < H2 / 16; ++kk)
+            mma(tg, dadv(dK, kk * 256), dadv(wd, kk * 256), idesc(128, H1, 0, 0, fmt), kk > 0);
+        } else {  // R4: feature gradient d1 W1
+          const uint64_t wd = sdesc(sb + Lt::w1t, 128, H1 / 8 * 128);
+#pragma unroll
+          for (int kk = 0; kk < H1 / 16; ++kk)
+            mma(tg, dadv(dK, kk * 256), dadv(wd, kk * 256), idesc(128, IN, 0, 0, fmt), kk > 0);
+        }
+        commit(&s_done[g]);
+      }
+    };
+    auto weights_done = [&]() {
+      ok = ok && wait_bar(&s_wdone[g], wph, wlim);
+      wph ^= 1u;
+    };
     auto round_done = [&]() {
       ok = ok && wait_bar(&s_done[g], dph, wlim);
       dph ^= 1u;
@@ -257,20 +302,26 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
     for (; tile < n_tiles && ok; tile += stride) {
       const RowIn cur = nxt;
       const TexBwdView& V = b.v[MV ? cur.vi : 0];
+      // the row's texture gradient gT = w dL/dC + dL/dT (Eq. 6); nothing
+      // for an empty slot or a row beyond the pixels
+      const bool valid = cur.in_pix && cur.id >= 0;
+      const float gT[3] = {valid ? fmaf(cur.w, cur.dC[0], cur.dT[0]) : 0.f,
+                           valid ? fmaf(cur.w, cur.dC[1], cur.dT[1]) : 0.f,
+                           valid ? fmaf(cur.w, cur.dC[2], cur.dT[2]) : 0.f};
       // stage X and d3 (the previous tile's R4 and Db have completed)
 #pragma unroll
       for (int c8 = 0; c8 < IN / 8; ++c8)
         *reinterpret_cast<uint4*>(act + cm_off(gt, 8 * c8, Lt::SA)) = cur.x[c8];
       {
-        const float d3[8] = {OP::kScale * cur.gT[0], OP::kScale * cur.gT[1],
-                             OP::kScale * cur.gT[2], 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float d3[8] = {OP::kScale * gT[0], OP::kScale * gT[1],
+                             OP::kScale * gT[2], 0.f, 0.f, 0.f, 0.f, 0.f};
         st8<OP>(del, gt, H2, Lt::SD, d3);
       }
-      hand_over(&s_ready[g]);  // R1
+      issue_round(0);
       load_row(tile + stride, nxt);
       round_done();
       const uint2 m1 = relu_h1();
-      hand_over(&s_ready[g]);  // R2
+      issue_round(1);
       round_done();
       // h2 = ReLU of the round's accumulator, and with it (CUDA cores) the
       // texture T = W3 h2 (h2 as stored, the operand type), dL/dW_j, and
@@ -297,8 +348,8 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
               T0 = fmaf(wr[0][e], hv, T0);
               T1 = fmaf(wr[1][e], hv, T1);
               T2 = fmaf(wr[2][e], hv, T2);
-              const float gsum = OP::kScale * fmaf(cur.gT[0], wr[0][e],
-                                                   fmaf(cur.gT[1], wr[1][e], cur.gT[2] * wr[2][e]));
+              const float gsum = OP::kScale * fmaf(gT[0], wr[0][e],
+                                                   fmaf(gT[1], wr[1][e], gT[2] * wr[2][e]));
               d2[i] = pos ? gsum : 0.f;
             }
           }
@@ -309,10 +360,11 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
         }
         if (cur.in_pix)
           V.dweff[cur.s] =
-              cur.valid ? T0 * cur.dC[0] + T1 * cur.dC[1] + T2 * cur.dC[2] + cur.dWx : 0.f;
+              valid ? T0 * cur.dC[0] + T1 * cur.dC[1] + T2 * cur.dC[2] + cur.dWx : 0.f;
       }
-      hand_over(&s_ready[g]);  // R3 and Da
+      issue_round(2);  // and Da
       round_done();
+      weights_done();  // Da has read d2
       // d1 = (d2 W2) * [h1 > 0], over d2 (R3 and Da, its readers, are done)
 #pragma unroll
       for (int c16 = 0; c16 < H1 / 16; ++c16) {
@@ -338,7 +390,7 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
           st8<OP>(del, gt, 16 * c16 + 8, Lt::SD, v + 8);
         }
       }
-      hand_over(&s_ready[g]);  // R4 and Db
+      issue_round(3);  // and Db
       round_done();
       {
         // feature gradient, level-major float2 per level, streamed to the
@@ -356,97 +408,79 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
           }
         }
       }
+      // Db has read X, h1 and d1 before the next tile overwrites them
+      weights_done();
       // the next R1 overwrites the group's accumulator: these TMEM reads
       // come first; a wait that ran out on any thread ends the group's loop
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       ok = group_and(g, ok);
     }
+    // the group's MMAs have completed before the TMEM is read or freed
+    if (gt == 0 && issue) {
+      commit(&s_fin[g]);
+      if (!wait_bar(&s_fin[g], 0, kTcWaitLimit)) ok = false;
+    }
     if (!ok) s_bad = 1;
   } else if (tid == kB3MmaWarp * 32) {
-    // ------------------------------------------------------ MMA thread
+    // ------------------------------------------- weight-gradient MMA thread
+    // Da and Db, shared by the groups, have this one issuer; it serves the
+    // groups in the order they hand their tiles over (two events per tile).
     constexpr uint32_t fmt = OP::kFmt;
-    int left[kB3Groups], rnd[kB3Groups];
+    int left[kB3Groups], ev[kB3Groups];
     uint32_t rph[kB3Groups];
+    uint64_t aM[kB3Groups], dM[kB3Groups];  // MN-major base descriptors
     for (int g = 0; g < kB3Groups; ++g) {
       const long long t0 = (long long)blockIdx.x * kB3Groups + g;
       left[g] = t0 < n_tiles ? (int)((n_tiles - 1 - t0) / stride + 1) : 0;
-      rnd[g] = 0;
+      ev[g] = 0;
       rph[g] = 0;
-    }
-    // base descriptors, built once: the group tiles read K-major (rows = M)
-    // and MN-major (rows = K), and the weight tiles
-    uint64_t aK[kB3Groups], dK[kB3Groups], aM[kB3Groups], dM[kB3Groups];
-#pragma unroll
-    for (int g = 0; g < kB3Groups; ++g) {
-      const uint32_t act = sb + g * Lt::group_bytes, del = act + Lt::act_bytes;
-      aK[g] = sdesc(act, 128, Lt::SA);
-      dK[g] = sdesc(del, 128, Lt::SD);
+      const uint32_t act = sb + g * Lt::group_bytes;
       aM[g] = sdesc(act, Lt::SA, 128);
-      dM[g] = sdesc(del, Lt::SD, 128);
+      dM[g] = sdesc(act + Lt::act_bytes, Lt::SD, 128);
     }
-    const uint64_t w1d = sdesc(sb + Lt::w1, 128, IN / 8 * 128);
-    const uint64_t w2d = sdesc(sb + Lt::w2, 128, H1 / 8 * 128);
-    const uint64_t w2td = sdesc(sb + Lt::w2t, 128, H2 / 8 * 128);
-    const uint64_t w1td = sdesc(sb + Lt::w1t, 128, H1 / 8 * 128);
     bool da_acc = false, db_acc = false, ok = true;
     int idle = 0;
     while (left[0] + left[1] + left[2] > 0) {
       bool any = false;
 #pragma unroll
       for (int g = 0; g < kB3Groups; ++g) {
-        if (left[g] == 0 || !bar_test(&s_ready[g], rph[g])) continue;
+        if (left[g] == 0 || !bar_test(&s_wready[g], rph[g])) continue;
         rph[g] ^= 1u;
         any = true;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t tg = tmem + 64 * g;
         if (issue) {
-          if (rnd[g] == 0) {  // R1: h1 = X W1^T
-#pragma unroll
-            for (int kk = 0; kk < IN / 16; ++kk)
-              mma(tg, dadv(aK[g], kk * 256), dadv(w1d, kk * 256), idesc(128, H1, 0, 0, fmt), kk > 0);
-          } else if (rnd[g] == 1) {  // R2: h2 = h1 W2^T
-#pragma unroll
-            for (int kk = 0; kk < H1 / 16; ++kk)
-              mma(tg, dadv(aK[g], (IN / 8) * 128 + kk * 256), dadv(w2d, kk * 256),
-                  idesc(128, H2, 0, 0, fmt), kk > 0);
-          } else if (rnd[g] == 2) {  // R3: d2 W2; Da += [h1 | h2]^T [d2 | d3]
-#pragma unroll
-            for (int kk = 0; kk < H2 / 16; ++kk)
-              mma(tg, dadv(dK[g], kk * 256), dadv(w2td, kk * 256), idesc(128, H1, 0, 0, fmt), kk > 0);
-            // K = rows: 16 rows = two 8-row groups per MMA, operands MN-major
+          // K = rows: 16 rows = two 8-row groups per MMA, operands MN-major
+          if (ev[g] == 0) {  // Da += [h1 | h2]^T [d2 | d3]
 #pragma unroll
             for (int kk = 0; kk < kTcRows / 16; ++kk)
               mma(tmem + Lt::t_da, dadv(aM[g], (IN / 8) * 128 + kk * 2 * Lt::SA),
                   dadv(dM[g], kk * 2 * Lt::SD), idesc(128, H2 + 16, 1, 1, fmt), da_acc || kk > 0);
             da_acc = true;
-          } else {  // R4: feature gradient d1 W1; Db += [X | ...]^T d1
-#pragma unroll
-            for (int kk = 0; kk < H1 / 16; ++kk)
-              mma(tg, dadv(dK[g], kk * 256), dadv(w1td, kk * 256), idesc(128, IN, 0, 0, fmt), kk > 0);
+          } else {  // Db += [X | ...]^T d1
 #pragma unroll
             for (int kk = 0; kk < kTcRows / 16; ++kk)
               mma(tmem + Lt::t_db, dadv(aM[g], kk * 2 * Lt::SA), dadv(dM[g], kk * 2 * Lt::SD),
                   idesc(128, H1, 1, 1, fmt), db_acc || kk > 0);
             db_acc = true;
           }
-          commit(&s_done[g]);
+          commit(&s_wdone[g]);
         }
-        if (++rnd[g] == 4) {
-          rnd[g] = 0;
+        if (++ev[g] == 2) {
+          ev[g] = 0;
           --left[g];
         }
       }
       if (any) {
         idle = 0;
-      } else if (++idle > wlim) {  // a group stopped handing rounds over
+      } else if (++idle > wlim) {  // a group stopped handing tiles over
         ok = false;
         break;
       }
     }
     // every MMA issued here has completed before the TMEM is read or freed
     if (issue) {
-      commit(&s_fin);
-      if (!wait_bar(&s_fin, 0, kTcWaitLimit)) ok = false;
+      commit(&s_fin[kB3Groups]);
+      if (!wait_bar(&s_fin[kB3Groups], 0, kTcWaitLimit)) ok = false;
     }
     if (!ok) s_bad = 1;
     s_acc = (da_acc && db_acc) ? 1 : 0;
