@@ -59,10 +59,14 @@ struct TcBwd3Layout {
   static constexpr int w2 = w1 + H1 * IN * 2;         // [H2][H1]  B of R2
   static constexpr int w2t = w2 + H2 * H1 * 2;        // [H1][H2]  B of R3
   static constexpr int w1t = w2t + H2 * H1 * 2;       // [IN][H1]  B of R4
-  static constexpr int w3 = w1t + IN * H1 * 2;        // FP32 [3][H2]
+  static constexpr int w3b = w1t + IN * H1 * 2;       // [16][H2]  B of T (rows 3.. zero)
+  static constexpr int w3 = w3b + 16 * H2 * 2;        // FP32 [3][H2]
   static constexpr int total = w3 + 3 * H2 * 4;
   // TMEM columns
-  static constexpr int t_da = 64 * kB3Groups, t_db = t_da + H2 + 16;
+  // TMEM columns: per group its round accumulator (64) and T (16), 96
+  // apart; then Da and Db
+  static constexpr int t_grp = 96, t_T = 64;
+  static constexpr int t_da = t_grp * kB3Groups, t_db = t_da + H2 + 16;
   static constexpr int cols = 512;
   static_assert(IN % 16 == 0 && IN <= 32 && H1 == 64 && H2 == 64, "supported MLP shapes");
   static_assert(FA >= IN + 128, "Da reads 128 activation features from IN");
@@ -138,6 +142,11 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
       *reinterpret_cast<uint16_t*>(tc_smem + Lt::w2t + cm_off(k, o, H2 / 8 * 128)) = v;
     }
     for (int i = tid; i < 3 * H2; i += kB3Threads) w3s[i] = OP::round(W3[i]);
+    for (int i = tid; i < 16 * H2; i += kB3Threads) {
+      const int o = i / H2, k = i % H2;
+      *reinterpret_cast<uint16_t*>(tc_smem + Lt::w3b + cm_off(o, k, H2 / 8 * 128)) =
+          OP::cvt(o < 3 ? W3[o * H2 + k] : 0.f);
+    }
     // the delta tiles start at zero: the padding of d3 (features H2 + 8 ..)
     // stays zero
     for (int g = 0; g < kB3Groups; ++g)
@@ -172,7 +181,7 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
     // ------------------------------------------------------ tile group g
     const int g = warp >> 2, gt = tid & 127;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-    const uint32_t tg = tmem + 64 * g;  // the group's round accumulator
+    const uint32_t tg = tmem + Lt::t_grp * g;  // the group's round accumulator
     unsigned char* act = tc_smem + g * Lt::group_bytes;
     unsigned char* del = act + Lt::act_bytes;
     const int KP = 1 << log2KP;
@@ -272,11 +281,16 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
           for (int kk = 0; kk < H1 / 16; ++kk)
             mma(tg, dadv(aK, (IN / 8) * 128 + kk * 256), dadv(wd, kk * 256),
                 idesc(128, H2, 0, 0, fmt), kk > 0);
-        } else if (r == 2) {  // R3: d2 W2
+        } else if (r == 2) {  // R3: d2 W2; and the texture T = h2 W3^T (N = 16)
           const uint64_t wd = sdesc(sb + Lt::w2t, 128, H2 / 8 * 128);
 #pragma unroll
           for (int kk = 0; kk < H2 / 16; ++kk)
             mma(tg, dadv(dK, kk * 256), dadv(wd, kk * 256), idesc(128, H1, 0, 0, fmt), kk > 0);
+          const uint64_t w3d = sdesc(sb + Lt::w3b, 128, H2 / 8 * 128);
+#pragma unroll
+          for (int kk = 0; kk < H2 / 16; ++kk)
+            mma(tg + Lt::t_T, dadv(aK, ((IN + H1) / 8) * 128 + kk * 256), dadv(w3d, kk * 256),
+                idesc(128, 16, 0, 0, fmt), kk > 0);
         } else {  // R4: feature gradient d1 W1
           const uint64_t wd = sdesc(sb + Lt::w1t, 128, H1 / 8 * 128);
 #pragma unroll
@@ -323,12 +337,10 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
       const uint2 m1 = relu_h1();
       issue_round(1);
       round_done();
-      // h2 = ReLU of the round's accumulator, and with it (CUDA cores) the
-      // texture T = W3 h2 (h2 as stored, the operand type), dL/dW_j, and
+      // h2 = ReLU of the round's accumulator, and with it (CUDA cores)
       // d2 = (W3^T d3) * [h2 > 0]
       {
         const float4* w34 = reinterpret_cast<const float4*>(w3s);
-        float T0 = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
         for (int c16 = 0; c16 < H2 / 16; ++c16) {
           float v[16], d2[16];
@@ -344,10 +356,6 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
               const int i = 4 * c4 + e;
               const bool pos = v[i] > 0.f;
               v[i] = fmaxf(v[i], 0.f);
-              const float hv = OP::round(v[i]);
-              T0 = fmaf(wr[0][e], hv, T0);
-              T1 = fmaf(wr[1][e], hv, T1);
-              T2 = fmaf(wr[2][e], hv, T2);
               const float gsum = OP::kScale * fmaf(gT[0], wr[0][e],
                                                    fmaf(gT[1], wr[1][e], gT[2] * wr[2][e]));
               d2[i] = pos ? gsum : 0.f;
@@ -358,12 +366,17 @@ __global__ void __launch_bounds__(kB3Threads, 1) k_tex_bwd_tc3(
           st8<OP>(del, gt, 16 * c16, Lt::SD, d2);
           st8<OP>(del, gt, 16 * c16 + 8, Lt::SD, d2 + 8);
         }
-        if (cur.in_pix)
-          V.dweff[cur.s] =
-              valid ? T0 * cur.dC[0] + T1 * cur.dC[1] + T2 * cur.dC[2] + cur.dWx : 0.f;
       }
       issue_round(2);  // and Da
       round_done();
+      {
+        // dL/dW_j = T . dL/dC + dL/dW_j (upstream), T from the R3 round
+        float T[8];
+        tmem_ld8(tg + Lt::t_T + lane_base, T);
+        if (cur.in_pix)
+          V.dweff[cur.s] =
+              valid ? T[0] * cur.dC[0] + T[1] * cur.dC[1] + T[2] * cur.dC[2] + cur.dWx : 0.f;
+      }
       weights_done();  // Da has read d2
       // d1 = (d2 W2) * [h1 > 0], over d2 (R3 and Da, its readers, are done)
 #pragma unroll
