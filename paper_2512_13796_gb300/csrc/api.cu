@@ -404,8 +404,11 @@ int render_bwd_impl(const nexel_camera* cam, const nexel_settings* settings,
   DevCam c = make_devcam(*cam);
   char* w = (char*)ws;
   char* bw = (char*)bwd_ws;
-  cudaError_t e = cudaSuccess;
-  if (rc) {
+  // the scratch is the caller's uninitialised memory: the backward's status
+  // word (read by nexel_read_status) starts at zero on every backward that
+  // has a scratch (K > 0 or recompute), in every form
+  cudaError_t e = (bw && (K > 0 || rc)) ? cudaMemsetAsync(bw + B.status, 0, 4, st) : cudaSuccess;
+  if (e == cudaSuccess && rc) {
     // recompute I, W, D, T_final with the collection pass (same kernel, same
     // inputs, hence the same values the forward produced)
     weights = (const float*)(bw + B.rc_weights);
@@ -528,7 +531,9 @@ int nexel_read_status(const nexel_camera* cam, const nexel_settings* settings,
   cudaError_t e = cudaMemcpyAsync(&words[0], w + L.counters + kStatusOffset, 4,
                                   cudaMemcpyDeviceToHost, st);
   char* bstat = nullptr;
-  if (bwd_ws) {
+  // the backward's status word exists where it has a scratch (K > 0 or
+  // recompute)
+  if (bwd_ws && (settings->K > 0 || settings->recompute_buffers != 0)) {
     const int K = settings->K;
     const int fd = (K > 0 && field_ok(field)) ? field->L * field->F : 0;
     BwdLayout B = bwd_layout(*cam, K, fd, settings->recompute_buffers != 0);

@@ -84,10 +84,8 @@ cudaError_t launch_texture_bwd(const DevCam& c, const nexel_settings& s, const n
     int KP = 1;
     while (KP < s.K) KP <<= 1;
     const long long n_rows = ((long long)c.W * c.H * KP + 15) / 16 * 16;
-    // the scratch is the caller's uninitialised memory: the status word the
-    // kernel may set starts at zero on every backward
-    cudaError_t e = cudaMemsetAsync(bws + B.status, 0, 4, st);
-    if (e == cudaSuccess && !feat_cached)
+    cudaError_t e = cudaSuccess;
+    if (!feat_cached)
       e = launch_texture_gather_tc(c, s, f, fd, ids, depths, (uint32_t*)(bws + B.feat), st);
     const int h2 = f.n_layers == 3 ? f.widths[2] : 0;
     if (e == cudaSuccess)
