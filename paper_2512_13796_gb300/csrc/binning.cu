@@ -1245,7 +1245,8 @@ template <bool kAtomic>
 __global__ void k_preprocess_bwd(DevCam c, int N, int sh_degree, const float* __restrict__ mu,
                                  const float* __restrict__ shj, const float* __restrict__ quat,
                                  const uint32_t* __restrict__ did, const uint32_t* __restrict__ dkey,
-                                 const float* __restrict__ gs, float* __restrict__ d_mu,
+                                 const float* __restrict__ gs, const float4* __restrict__ aux,
+                                 float* __restrict__ d_mu,
                                  float* __restrict__ d_quat, float* __restrict__ d_scale,
                                  float* __restrict__ d_opac, float* __restrict__ d_gamma,
                                  float* __restrict__ d_color) {
@@ -1253,11 +1254,23 @@ __global__ void k_preprocess_bwd(DevCam c, int N, int sh_degree, const float* __
   if (r >= N) return;
   if (dkey[r] == 0xFFFFFFFFu) return;  // culled: no gradient
   uint32_t i = did[r];
+  // the collection backward's sums over the surfel's pixels, turned into
+  // camera-space gradients with the surfel's frame (aux: v1, v2, n and the
+  // reciprocal scales; the hit offset in the plane is u s1 v1 + v s2 v2)
   const float* g = gs + (size_t)r * kGradStride;
-  const float3 g_m = rotT(c.R, make_float3(g[0], g[1], g[2]));
-  const float3 g_v1 = rotT(c.R, make_float3(g[3], g[4], g[5]));
-  const float3 g_v2 = rotT(c.R, make_float3(g[6], g[7], g[8]));
-  const float3 g_n = rotT(c.R, make_float3(g[9], g[10], g[11]));
+  const float4 a1 = aux[(size_t)r * kAuxF4 + 1], a2 = aux[(size_t)r * kAuxF4 + 2],
+               a3 = aux[(size_t)r * kAuxF4 + 3];
+  const float3 v1 = make_float3(a1.x, a1.y, a1.z), v2 = make_float3(a2.x, a2.y, a2.z),
+               nc = make_float3(a3.x, a3.y, a3.z);
+  auto comb = [](float3 p, float a, float3 q, float b) {
+    return make_float3(fmaf(p.x, a, q.x * b), fmaf(p.y, a, q.y * b), fmaf(p.z, a, q.z * b));
+  };
+  const float3 gmc = comb(v1, -g[0], v2, -g[1]);
+  const float3 g_m = rotT(c.R, make_float3(fmaf(nc.x, g[2], gmc.x), fmaf(nc.y, g[2], gmc.y),
+                                           fmaf(nc.z, g[2], gmc.z)));
+  const float3 g_v1 = rotT(c.R, comb(v1, g[3], v2, g[4]));
+  const float3 g_v2 = rotT(c.R, comb(v1, g[5], v2, g[6]));
+  const float3 g_n = rotT(c.R, comb(v1, -g[7], v2, -g[8]));
   float q0 = quat[4 * i], q1 = quat[4 * i + 1], q2 = quat[4 * i + 2], q3 = quat[4 * i + 3];
   float qn = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
   float w = q0 * qn, x = q1 * qn, y = q2 * qn, zq = q3 * qn;
@@ -1280,9 +1293,9 @@ __global__ void k_preprocess_bwd(DevCam c, int N, int sh_degree, const float* __
     const float inv = rsqrtf(fmaxf(vx * vx + vy * vy + vz * vz, 1e-30f));
     const float x = vx * inv, y = vy * inv, zd = vz * inv;
     const float* J = shj + 9 * (size_t)i;  // d colour_ch / d dir, from the forward
-    const float3 q = make_float3(g[17] * J[0] + g[18] * J[3] + g[19] * J[6],
-                                 g[17] * J[1] + g[18] * J[4] + g[19] * J[7],
-                                 g[17] * J[2] + g[18] * J[5] + g[19] * J[8]);
+    const float3 q = make_float3(g[12] * J[0] + g[13] * J[3] + g[14] * J[6],
+                                 g[12] * J[1] + g[13] * J[4] + g[14] * J[7],
+                                 g[12] * J[2] + g[13] * J[5] + g[14] * J[8]);
     const float qd = q.x * x + q.y * y + q.z * zd;
     gm.x += (q.x - x * qd) * inv;
     gm.y += (q.y - y * qd) * inv;
@@ -1292,9 +1305,9 @@ __global__ void k_preprocess_bwd(DevCam c, int N, int sh_degree, const float* __
       float dc[48];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        dc[3 * k] = Y.y[k] * g[17];
-        dc[3 * k + 1] = Y.y[k] * g[18];
-        dc[3 * k + 2] = Y.y[k] * g[19];
+        dc[3 * k] = Y.y[k] * g[12];
+        dc[3 * k + 1] = Y.y[k] * g[13];
+        dc[3 * k + 2] = Y.y[k] * g[14];
       }
       if (kAtomic) {
 #pragma unroll
@@ -1323,19 +1336,19 @@ __global__ void k_preprocess_bwd(DevCam c, int N, int sh_degree, const float* __
     acc<kAtomic>(d_quat + 4 * i + 2, (gy - y * dot) * qn);
     acc<kAtomic>(d_quat + 4 * i + 3, (gz - zq * dot) * qn);
   }
-  if (d_scale) {
-    acc<kAtomic>(d_scale + 2 * i, g[12]);
-    acc<kAtomic>(d_scale + 2 * i + 1, g[13]);
+  if (d_scale) {  // sigma1 = -sum(du / s1 . u s1) / s1, sigma2 likewise
+    acc<kAtomic>(d_scale + 2 * i, -g[3] * a2.w);
+    acc<kAtomic>(d_scale + 2 * i + 1, -g[6] * a3.w);
   }
-  if (d_opac) acc<kAtomic>(d_opac + i, g[14]);
+  if (d_opac) acc<kAtomic>(d_opac + i, g[9]);
   if (d_gamma) {
-    acc<kAtomic>(d_gamma + 2 * i, g[15]);
-    acc<kAtomic>(d_gamma + 2 * i + 1, g[16]);
+    acc<kAtomic>(d_gamma + 2 * i, g[10]);
+    acc<kAtomic>(d_gamma + 2 * i + 1, g[11]);
   }
   if (d_color && sh_degree != 3) {
-    acc<kAtomic>(d_color + 3 * i, g[17]);
-    acc<kAtomic>(d_color + 3 * i + 1, g[18]);
-    acc<kAtomic>(d_color + 3 * i + 2, g[19]);
+    acc<kAtomic>(d_color + 3 * i, g[12]);
+    acc<kAtomic>(d_color + 3 * i + 1, g[13]);
+    acc<kAtomic>(d_color + 3 * i + 2, g[14]);
   }
 }
 
@@ -1363,7 +1376,8 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
     kern<<<(N + 255) / 256, 256, 0, st>>>(
         c, N, s.sh_degree, mu, (const float*)(ws + L.shj), quat, (uint32_t*)(ws + L.did0),
         (uint32_t*)(ws + L.dkey0),
-        (float*)(ws + L.grad_sorted), d_mu, d_quat, d_scale, d_opacity, d_gamma, d_color);
+        (float*)(ws + L.grad_sorted), (const float4*)(ws + L.aux_sorted), d_mu, d_quat, d_scale,
+        d_opacity, d_gamma, d_color);
   }
   return cudaGetLastError();
 }

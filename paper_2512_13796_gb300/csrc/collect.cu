@@ -155,48 +155,39 @@ __global__ void __launch_bounds__(kTilePix, 5) k_collect_fwd(
   }
 }
 
-// Warp sum of the 20 per-lane gradient values, added to dst[0..19] with one
-// atomic per value.  A transposing butterfly: at each xor step a lane keeps
-// one half of its partial sums and sends the other half to its partner
-// (20 -> 10 -> 5 -> 3 -> 2 -> 1 values, 21 shuffles instead of 5 x 20), so
-// that in the end 20 distinct lanes each hold the total of one value, at
-// index 10 b4 + 5 b3 + 3 b2 + 2 b1 + b0 (b = lane bits), and issue their
+// Warp sum of the 16 per-lane gradient values, added to dst[0..15] with one
+// atomic per nonzero total.  A transposing butterfly: at each xor step a lane
+// keeps one half of its partial sums and sends the other half to its
+// partner (16 -> 8 -> 4 -> 2 -> 1 values, then the last pair: 16 shuffles
+// instead of 5 x 16), so that in the end each total sits in two lanes, at
+// index 8 b4 + 4 b3 + 2 b2 + b1 (b = lane bits); the even lanes issue the
 // atomics in the same instruction.
-__device__ __forceinline__ void warp_sum20_add(const float (&g)[kGradStride], float* dst) {
-  static_assert(kGradStride == 20, "the butterfly below is laid out for 20 values");
+__device__ __forceinline__ void warp_sum16_add(const float (&g)[kGradStride], float* dst) {
+  static_assert(kGradStride == 16, "the butterfly below is laid out for 16 values");
   const int lane = threadIdx.x & 31;
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
-  float u[10];
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float u[8];
 #pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    const float keep = b4 ? g[10 + i] : g[i], send = b4 ? g[i] : g[10 + i];
+  for (int i = 0; i < 8; ++i) {
+    const float keep = b4 ? g[8 + i] : g[i], send = b4 ? g[i] : g[8 + i];
     u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
-  float w[6];
+  float w[4];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const float keep = b3 ? u[5 + i] : u[i], send = b3 ? u[i] : u[5 + i];
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b3 ? u[4 + i] : u[i], send = b3 ? u[i] : u[4 + i];
     w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
-  w[5] = 0.f;
-  float x[4];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float keep = b2 ? w[3 + i] : w[i], send = b2 ? w[i] : w[3 + i];
-    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  x[3] = 0.f;
-  float y[2];
+  float x[2];
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    const float keep = b1 ? x[2 + i] : x[i], send = b1 ? x[i] : x[2 + i];
-    y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    const float keep = b2 ? w[2 + i] : w[i], send = b2 ? w[i] : w[2 + i];
+    x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
-  const float keep = b0 ? y[1] : y[0], send = b0 ? y[0] : y[1];
-  const float z = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-  const int lo = 2 * (int)b1 + (int)b0;      // index within the 3-value group
-  const int mid = 3 * (int)b2 + lo;          // index within the 5-value group
-  if (lo <= 2 && mid <= 4 && z != 0.f) atomicAdd(dst + 10 * (int)b4 + 5 * (int)b3 + mid, z);
+  const float keep = b1 ? x[1] : x[0], send = b1 ? x[0] : x[1];
+  const float y = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  const float z = y + __shfl_xor_sync(0xffffffffu, y, 1);
+  if (!(lane & 1) && z != 0.f) atomicAdd(dst + 8 * (int)b4 + 4 * (int)b3 + 2 * (int)b2 + (int)b1, z);
 }
 
 // One 16 x 16 tile of the collection backward (BATCH as in the forward).
@@ -265,8 +256,15 @@ __device__ __forceinline__ void collect_bwd_tile(const CollectBwdView& V, int ti
       Hit h;
       bool ok = pos < last && eval_surfel(q0, q1, q2, q3, fpx, fpy, c.near_, alpha_min, h);
       if (!__any_sync(0xffffffffu, ok)) continue;
-      // per-surfel gradient record: mu_c (0-2), v1_c (3-5), v2_c (6-8),
-      // n_c (9-11), sigma (12-13), opacity (14), gamma (15-16), colour (17-19)
+      // per-surfel gradient record (sums over the surfel's pixels), from
+      // which the preprocess backward forms the camera-space gradients with
+      // the surfel's own frame v1, v2, n and scales s1, s2 (the hit offset
+      // in the plane is r = u s1 v1 + v s2 v2):
+      //   0 du1, 1 dv2, 2 gd          (mu_c = -v1 S0 - v2 S1 + n S2)
+      //   3 du1 u s1, 4 du1 v s2      (v1_c = v1 S3 + v2 S4; sigma1 = -S3 / s1)
+      //   5 dv2 u s1, 6 dv2 v s2      (v2_c = v1 S5 + v2 S6; sigma2 = -S6 / s2)
+      //   7 gd u s1, 8 gd v s2        (n_c = -v1 S7 - v2 S8)
+      //   9 opacity, 10-11 gamma, 12-14 colour, 15 unused
       float g[kGradStride];
 #pragma unroll
       for (int k = 0; k < kGradStride; ++k) g[k] = 0.f;
@@ -291,14 +289,14 @@ __device__ __forceinline__ void collect_bwd_tile(const CollectBwdView& V, int ti
         } else {
           e = q4.x * dC0 + q4.y * dC1 + q4.z * dC2;
           const float w = a * T;
-          g[17] = w * dC0; g[18] = w * dC1; g[19] = w * dC2;
+          g[12] = w * dC0; g[13] = w * dC1; g[14] = w * dC2;
         }
         const float da = T * (e - R);
         R = a * e + (1.f - a) * R;
         float du = 0.f, dv = 0.f;
         if (!clamped) {
           const float al = h.alpha;
-          g[14] = da * h.e;            // d alpha / d opacity = e
+          g[9] = da * h.e;             // d alpha / d opacity = e
           const float cpa = -da * al;  // dL/d(pu) * 2 = -dalpha * alpha
           // d pu / d u = 2 g pu / u, d pu / d g = 2 pu ln|u| (|u| > 0: the
           // quotient and the logarithm in fast form, a few ulp, well inside
@@ -306,34 +304,30 @@ __device__ __forceinline__ void collect_bwd_tile(const CollectBwdView& V, int ti
           constexpr float kLn2 = 0.6931471805599453f;
           if (h.u != 0.f) {
             du = cpa * q1.z * __fdividef(h.pu, h.u);
-            g[15] = cpa * h.pu * (kLn2 * __log2f(fabsf(h.u)));
+            g[10] = cpa * h.pu * (kLn2 * __log2f(fabsf(h.u)));
           }
           if (h.v != 0.f) {
             dv = cpa * q1.w * __fdividef(h.pv, h.v);
-            g[16] = cpa * h.pv * (kLn2 * __log2f(fabsf(h.v)));
+            g[11] = cpa * h.pv * (kLn2 * __log2f(fabsf(h.v)));
           }
         }
         // camera-space chain (the hit x = t d lies on the plane, so
         // x - mu = u s1 v1 + v s2 v2 exactly): u = (x - mu) . v1 / s1 with
-        // t = (mu . n) / (d . n)
+        // t = (mu . n) / (d . n); the per-surfel vectors v1, v2, n multiply
+        // the sums in the preprocess backward
         const float4 a0 = s_aux[0][j], a1 = s_aux[1][j], a2 = s_aux[2][j], a3 = s_aux[3][j];
-        const float s1 = a0.w, s2 = a1.w;
-        const float us = h.u * s1, vs = h.v * s2;
-        const float rx = us * a1.x + vs * a2.x, ry = us * a1.y + vs * a2.y,
-                    rz = us * a1.z + vs * a2.z;
+        const float us = h.u * a0.w, vs = h.v * a1.w;   // u s1, v s2
         const float du1 = du * a2.w, dv2 = dv * a3.w;  // du / s1, dv / s2
-        const float grx = du1 * a1.x + dv2 * a2.x, gry = du1 * a1.y + dv2 * a2.y,
-                    grz = du1 * a1.z + dv2 * a2.z;
-        const float gtt = dt + grx * rdx + gry * rdy + grz;
-        const float gd = gtt * h.inv;
-        g[0] = -grx + gd * a3.x; g[1] = -gry + gd * a3.y; g[2] = -grz + gd * a3.z;
-        g[3] = du1 * rx; g[4] = du1 * ry; g[5] = du1 * rz;
-        g[6] = dv2 * rx; g[7] = dv2 * ry; g[8] = dv2 * rz;
-        g[9] = -gd * rx; g[10] = -gd * ry; g[11] = -gd * rz;
-        g[12] = -du1 * h.u;
-        g[13] = -dv2 * h.v;
+        // dL/dt through u and v: (du1 v1 + dv2 v2) . d, d = (rdx, rdy, 1)
+        const float v1d = fmaf(a1.x, rdx, fmaf(a1.y, rdy, a1.z));
+        const float v2d = fmaf(a2.x, rdx, fmaf(a2.y, rdy, a2.z));
+        const float gd = fmaf(du1, v1d, fmaf(dv2, v2d, dt)) * h.inv;
+        g[0] = du1; g[1] = dv2; g[2] = gd;
+        g[3] = du1 * us; g[4] = du1 * vs;
+        g[5] = dv2 * us; g[6] = dv2 * vs;
+        g[7] = gd * us; g[8] = gd * vs;
       }
-      warp_sum20_add(g, V.grad + (size_t)s_rank[j] * kGradStride);
+      warp_sum16_add(g, V.grad + (size_t)s_rank[j] * kGradStride);
     }
     bend = bstart;
   }

@@ -17,7 +17,7 @@ constexpr int kTile = NEXEL_TILE;            // 16 x 16 pixel tiles
 constexpr int kTilePix = kTile * kTile;      // one thread per pixel
 constexpr int kRecF4 = 5;                    // packed surfel record: 5 float4
 constexpr int kAuxF4 = 4;                    // camera-space frame for the backward
-constexpr int kGradStride = 20;              // per-surfel gradient record (floats)
+constexpr int kGradStride = 16;              // per-surfel gradient record (floats)
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;                        // instance (tile) sort
 constexpr int kSortItemsDepth = 4;                    // depth sort of the surfels
