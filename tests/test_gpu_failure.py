@@ -121,3 +121,27 @@ def test_tc_wait_timeout_reported_and_recovered(dev, mlp, levels, hidden):
         np.testing.assert_allclose(g_again[k], g_good[k], rtol=1e-4,
                                    atol=1e-6 * float(np.abs(g_good[k]).max() + 1e-30),
                                    err_msg=k)
+
+
+@pytest.mark.parametrize("mlp", ["f32", "bf16"])
+def test_status_clean_after_backward_on_dirty_scratch(dev, mlp):
+    """The backward scratch is the caller's memory, uninitialised: filled
+    with 0xFF bytes before the call, a normal forward + backward still
+    reads back NEXEL_OK (the backward clears its status word on entry in
+    every form)."""
+    import torch
+    from paper_2512_13796_gb300 import render as R
+    w = synth.workload(0)
+    sc, cam, st = w.scene, synth.front_camera(96, 80), w.settings
+    grid = "f32" if mlp == "f32" else "f16"
+    fld = synth.make_field(8, 12, 2, (64,), 0)
+    P = cam.width * cam.height
+    dI = np.random.default_rng(5).normal(size=(P, 3)).astype(np.float32)
+    ws = R.Workspace(dev, cap_hint=1 << 16)
+    cam_s = R.camera_struct(cam)
+    st_s = R.settings_struct(st, grid, mlp)
+    fs = R.DeviceField.from_synth(fld, dev, grid, mlp)
+    fstruct = fs.struct(fs.storage_table(), fs.weights)
+    ws.bwd(cam_s, st_s, fstruct).fill_(255)
+    run_gpu(sc, cam, st, fld, dev, grid=grid, mlp=mlp, d_image=dI, ws=ws)
+    assert _status(ws, cam_s, st_s, fstruct, sc.n, ws.bws) == NEXEL_OK
