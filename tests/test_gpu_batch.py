@@ -88,8 +88,10 @@ def test_batch_small_views_vs_oracle(dev, graph):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-def test_batch_small_views_tensor_cores_vs_oracle(dev, graph):
+@pytest.mark.parametrize("levels,hidden", [(8, (64,)), (16, (64, 64))])
+def test_batch_small_views_tensor_cores_vs_oracle(dev, graph, levels, hidden):
     """The batched step on the tensor-core path (FP16 table, BF16 MLP 16-64-3,
+    or 32-64-64-3, which takes the backward with three tile groups per CTA;
     feature cache): every per-tile phase runs as one launch over the three
     views (persistent collection CTAs pulling (view, tile) items, the
     tcgen05 texturing kernels and the hash-grid backward over the views'
@@ -101,7 +103,7 @@ def test_batch_small_views_tensor_cores_vs_oracle(dev, graph):
     from paper_2512_13796_gb300 import render as R
     scene = synth.make_scene(256, 3, 7, gamma="var")
     cams = synth.sphere_cameras(np.random.default_rng(11), [(48, 40), (64, 64), (80, 56)])
-    field = synth.make_field(8, 12, 2, (64,), 7, table_std=0.3)
+    field = synth.make_field(levels, 12, 2, hidden, 7, table_std=0.3)
     st = synth.Settings(K=2)
     p = gpu_params(scene, dev)
     fd = R.DeviceField.from_synth(field, dev, "f16", "bf16")
