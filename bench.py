@@ -392,15 +392,18 @@ def roofline(prof: dict, job: Job, peaks: dict, peak_kind: str, n_steps: int, wo
 
 def key_layout(N: int, width: int, height: int) -> dict:
     """The binning's key layout for N surfels on a width x height view (as
-    the library derives it): 16 x 16 tiles; 32-bit (tile, depth rank) keys
-    when tile and rank bits fit, else 64-bit; direct placement for 32-bit
-    keys and at most 8192 tiles, else the LSD tile sort."""
+    the library derives it): 16 x 16 tiles; direct placement for at most
+    8192 tiles, with 32-bit (tile, depth rank) keys when tile and rank bits
+    fit and keys holding the rank alone otherwise; beyond 8192 tiles the LSD
+    tile sort, with 64-bit keys when the bits do not fit."""
     tiles = ((width + 15) // 16) * ((height + 15) // 16)
     tile_bits = max(1, (tiles - 1).bit_length())
     rank_bits = max(1, (N - 1).bit_length())
-    key64 = tile_bits + rank_bits > 32
-    return {"tiles": tiles, "tile_bits": tile_bits, "key64": key64,
-            "placement": (not key64) and tiles <= 8192, "tile_passes": (tile_bits + 7) // 8}
+    placement = tiles <= 8192
+    fits32 = tile_bits + rank_bits <= 32
+    return {"tiles": tiles, "tile_bits": tile_bits, "key64": (not placement) and not fits32,
+            "rank_only": placement and not fits32, "placement": placement,
+            "tile_passes": (tile_bits + 7) // 8}
 
 
 def sort_rooflines(prof: dict, steps: int, N: int, n_inst: int, layout: dict, peaks: dict,

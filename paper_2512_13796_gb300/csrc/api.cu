@@ -24,7 +24,14 @@ static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
   L.n_tiles = tx * ty;
   L.tile_bits = ceil_log2(L.n_tiles);
   L.rank_bits = std::max(1, ceil_log2(std::max(N, 2)));
-  L.key64 = (L.tile_bits + L.rank_bits > 32) ? 1 : 0;
+  // direct placement by tile up to kPlaceMaxTiles tiles, whatever the key
+  // width: a placed key needs no tile field (its slot gives the tile), so
+  // when tile and rank bits exceed 32 it holds the rank alone; the tile sort
+  // (more tiles) keeps (tile, rank) keys, 64-bit where they do not fit
+  const bool fits32 = L.tile_bits + L.rank_bits <= 32;
+  L.place_ok = L.n_tiles <= kPlaceMaxTiles ? 1 : 0;
+  L.key64 = (!L.place_ok && !fits32) ? 1 : 0;
+  L.rank_only = (L.place_ok && !fits32) ? 1 : 0;
   L.tile_passes = (L.tile_bits + 7) / 8;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -52,7 +59,6 @@ static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
   L.grad_sorted = take(n * kGradStride * 4);
   L.counters = take(256);
   // direct placement by tile: [rank block][tile] counts and the tile starts
-  L.place_ok = (!L.key64 && L.n_tiles <= kPlaceMaxTiles) ? 1 : 0;
   const size_t place_blocks = L.place_ok ? (n + kPlaceRanks - 1) / kPlaceRanks : 0;
   L.place = take(place_blocks * (size_t)L.n_tiles * 4);
   L.place_tiles = take(L.place_ok ? (size_t)L.n_tiles * 4 : 0);
@@ -212,6 +218,31 @@ __global__ void k_instance_list(long long n, int rank_bits, uint32_t rmask,
   KeyT k = keys[i];
   uint32_t r = (uint32_t)k & rmask;
   if (tile_out) tile_out[i] = (int)(k >> rank_bits);
+  if (id_out) id_out[i] = (int)did[r];
+  if (depth_out) depth_out[i] = __uint_as_float(dkey[r]);
+}
+
+// Rank-only keys (placed instances whose tile and rank bits exceed 32): the
+// tile of instance i is the last tile whose list starts at or before i (the
+// lists are consecutive, in tile order; empty ones start where the next
+// begins).
+__global__ void k_instance_list_placed(long long n, int n_tiles, const uint2* __restrict__ ranges,
+                                       const uint32_t* __restrict__ keys,
+                                       const uint32_t* __restrict__ did,
+                                       const uint32_t* __restrict__ dkey, int* __restrict__ tile_out,
+                                       int* __restrict__ id_out, float* __restrict__ depth_out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t r = keys[i];
+  if (tile_out) {
+    int lo = 0, hi = n_tiles;  // first tile whose list starts after i
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((long long)ranges[mid].x <= i) lo = mid + 1;
+      else hi = mid;
+    }
+    tile_out[i] = lo - 1;
+  }
   if (id_out) id_out[i] = (int)did[r];
   if (depth_out) depth_out[i] = __uint_as_float(dkey[r]);
 }
@@ -565,7 +596,15 @@ int nexel_instance_list(const nexel_camera* cam, int N, const void* ws, size_t w
   unsigned grid = (unsigned)((n_instances + 255) / 256);
   const uint32_t* did = (const uint32_t*)(w + L.did0);
   const uint32_t* dk = (const uint32_t*)(w + L.dkey0);
-  if (L.key64)
+  if (L.rank_only)
+    {
+      NEXEL_PROF("instance_list", st);
+      k_instance_list_placed<<<grid, 256, 0, st>>>(n_instances, L.n_tiles,
+                                                   (const uint2*)(w + L.ranges),
+                                                   (const uint32_t*)(w + L.inst0), did, dk,
+                                                   tile_out, id_out, depth_out);
+    }
+  else if (L.key64)
     {
       NEXEL_PROF("instance_list", st);
       k_instance_list<unsigned long long><<<grid, 256, 0, st>>>(

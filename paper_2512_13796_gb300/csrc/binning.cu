@@ -6,11 +6,12 @@
 // (tile, depth) keys of every (tile, surfel) instance, the N surfels are
 // first sorted by depth (32-bit float keys, index order on ties).  The
 // instances are then placed directly at their slots in the per-tile lists
-// (32-bit keys, at most kPlaceMaxTiles tiles), or emitted in depth-rank order
-// and stably sorted on the tile bits alone.  Either way the per-tile lists
-// are identical, bit for bit, to a stable sort of (tile << 32 | depth bits)
+// (at most kPlaceMaxTiles tiles), or emitted in depth-rank order and stably
+// sorted on the tile bits alone.  Either way the per-tile lists are
+// identical, bit for bit, to a stable sort of (tile << 32 | depth bits)
 // keys.  A key is (tile << rank_bits | rank), in 32 bits whenever
-// tile_bits + rank_bits <= 32.
+// tile_bits + rank_bits <= 32; otherwise a placed key holds the rank alone
+// (32 bits; its slot gives the tile) and a sorted one is 64-bit.
 #include "common.cuh"
 
 #include <algorithm>
@@ -942,7 +943,7 @@ __global__ void k_place_ranges(int n_tiles, const uint32_t* __restrict__ start,
 
 template <typename KeyT>
 __global__ void __launch_bounds__(kPlaceThreads) k_place_write(
-    const DevCam c, int N, int n_tiles, int rank_bits, const uint32_t* __restrict__ did,
+    const DevCam c, int N, int n_tiles, int tile_shift, const uint32_t* __restrict__ did,
     const uint2* __restrict__ rect, const float4* __restrict__ conic,
     const uint32_t* __restrict__ count, const uint32_t* __restrict__ moff,
     const uint32_t* __restrict__ mwords, uint32_t cap_words, const uint32_t* __restrict__ M,
@@ -1009,7 +1010,9 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place_write(
                                          : (uint32_t)__popc(s_lo[t]) +
                                                (uint32_t)__popc(s_hi[t] & ((1u << (gi - 32)) - 1u));
           const uint32_t at = s_base[t] + lower;
-          if (at < cap) keys[at] = ((KeyT)t << rank_bits) | (KeyT)(r0 + i);
+          // (tile << rank bits | rank), or the rank alone (tile_shift 32)
+          if (at < cap)
+            keys[at] = (tile_shift < 32 ? (KeyT)t << tile_shift : (KeyT)0) | (KeyT)(r0 + i);
         }
       }
       __syncthreads();
@@ -1173,8 +1176,8 @@ static cudaError_t binning_place(const DevCam& c, int N, char* ws, const WsLayou
   if (e == cudaSuccess && N > 0) {
     NEXEL_PROF("place_write", st);
     k_place_write<uint32_t><<<nb, kPlaceThreads, smem_write, st>>>(
-        c, N, n_tiles, L.rank_bits, did, rect, conic, count, moff, mwords, cap_words, M, tstart,
-        (uint32_t*)(ws + L.inst0), cap);
+        c, N, n_tiles, L.rank_only ? 32 : L.rank_bits, did, rect, conic, count, moff, mwords,
+        cap_words, M, tstart, (uint32_t*)(ws + L.inst0), cap);
     e = cudaGetLastError();
   }
   return e;

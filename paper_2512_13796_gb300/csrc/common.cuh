@@ -234,7 +234,8 @@ struct WsLayout {
       scan_sums, total;
   long long mword_cap;  // words of room in mwords
   int N, P, K, n_tiles, tile_bits, rank_bits, key64, tile_passes;
-  int place_ok;  // the instances are placed by tile directly (no tile sort)
+  int place_ok;   // the instances are placed by tile directly (no tile sort)
+  int rank_only;  // placed keys hold the depth rank alone (tile + rank bits > 32)
   long long cap;
 };
 // Backward scratch (per sample): dL/dW_j, dL/dD_j, the field features and

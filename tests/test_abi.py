@@ -48,6 +48,13 @@ def test_workspace_sizes_are_host_only(lib):
     a = N_.nexel_workspace_size(cam, 300_000, 10_000_000)
     b = N_.nexel_workspace_size(cam, 300_000, 20_000_000)
     assert b > a > 300_000 * 80
+    # 1920 x 1080 (13 tile bits) and 600k surfels (20 rank bits): the
+    # instances are placed by tile with 32-bit keys holding the rank alone,
+    # two 4-byte key buffers per instance (64-bit keys would take 16 B)
+    big = R.camera_struct(synth.front_camera(1920, 1080))
+    per_inst = (N_.nexel_workspace_size(big, 600_000, 20_000_000) -
+                N_.nexel_workspace_size(big, 600_000, 10_000_000)) / 10_000_000
+    assert 8 <= per_inst < 9, per_inst
     st = R.settings_struct(synth.Settings(K=4))
     f = N_.Field()
     f.L, f.T, f.F = 16, 1 << 19, 2

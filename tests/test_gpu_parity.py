@@ -400,6 +400,36 @@ def test_tile_sort_path_beyond_placement_tiles(dev):
     _report("tile-sort path fwd", compare_forward(fw, ref, st.K, TOL_F32))
 
 
+def test_placement_with_rank_only_keys(dev):
+    """530k surfels on a 1920 x 1080 view (8160 tiles: 13 tile bits and 20
+    rank bits, more than 32): the instances are still placed by tile, with
+    keys that hold the depth rank alone (the slot gives the tile); the
+    binned order is the stable (tile, depth, id) one, every surfel appears
+    once per tile, and the forward matches the oracle."""
+    scene = synth.make_scene(530_000, 12, 47, room=True, gamma="var")
+    cam = synth.front_camera(1920, 1080)
+    st = synth.Settings(K=2)
+    field = synth.make_field(4, 12, 2, (16,), 7)
+    fw = _instance_order_checked(dev, scene, cam, st, field)
+    pix = synth.pixel_sample(cam, 384, 1, seed=8)
+    ref = reference(scene, cam, st, field, pix)
+    _report("rank-only placed keys fwd", compare_forward(fw, ref, st.K, TOL_F32))
+
+
+def test_tile_sort_with_64_bit_keys(dev):
+    """More than 8192 tiles (1600 x 1400: 8800 tiles, 14 bits) and 270k
+    surfels (19 rank bits): the emit-and-sort path with 64-bit (tile, rank)
+    keys; the order is the stable one and the forward matches the oracle."""
+    scene = synth.make_scene(270_000, 12, 49, room=True, gamma="var")
+    cam = synth.front_camera(1600, 1400)
+    st = synth.Settings(K=2)
+    field = synth.make_field(4, 12, 2, (16,), 9)
+    fw = _instance_order_checked(dev, scene, cam, st, field)
+    pix = synth.pixel_sample(cam, 384, 1, seed=10)
+    ref = reference(scene, cam, st, field, pix)
+    _report("64-bit tile sort fwd", compare_forward(fw, ref, st.K, TOL_F32))
+
+
 def test_placement_with_tile_decisions_tested_again(dev):
     """Surfels so large on screen that their stored tile decisions overflow
     the room of 8 words per surfel (up to 113 words each on a 1280 x 720
