@@ -11,9 +11,9 @@
 //     index modulo 4 is the TMEM lane quadrant).  Per tile the group stages
 //     X and d3, then runs four MMA rounds, each followed by an epilogue:
 //       R1  h1 = X W1^T
-//       R2  h2 = h1 W2^T;  then on CUDA cores T = W3 h2, dL/dW_j and
-//           d2 = (W3^T d3) * [h2 > 0]
-//       R3  d1 = (d2 W2) * [h1 > 0];  with it Da += [h1 | h2]^T [d2 | d3]
+//       R2  h2 = h1 W2^T;  then on CUDA cores d2 = (W3^T d3) * [h2 > 0]
+//       R3  d1 = (d2 W2) * [h1 > 0] and the texture T = h2 W3^T (N = 16),
+//           then dL/dW_j = T . dL/dC; with R3, Da += [h1 | h2]^T [d2 | d3]
 //       R4  feature gradient d1 W1;  with it Db += [X | ...]^T d1
 //     The group's thread 0 issues its own rounds once the group's named
 //     barrier shows all 128 rows in place, and the group waits for the
@@ -28,8 +28,8 @@
 // Shared memory per group: the activation tile [X | h1 | h2] and the delta
 // tile [d2 | d3]; d1 overwrites d2 once R3 and Da (the only readers of d2)
 // have completed, which keeps a group at 60 KB and three groups plus the
-// weights under the 227 KB of an SM.  TMEM: 64 columns per group for its
-// round accumulator, then Da (80 columns) and Db (64).
+// weights under the 227 KB of an SM.  TMEM: 96 columns per group (its round
+// accumulator and T), then Da (80 columns) and Db (64).
 // Every wait is bounded; a wait that runs out ends the CTA's loops, the MMA
 // thread waits (bounded) for the MMAs it issued, the TMEM is freed and the
 // status word of every view of the launch gets NEXEL_ERR_TIMEOUT.
