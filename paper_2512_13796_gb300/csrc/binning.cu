@@ -660,11 +660,16 @@ __global__ void __launch_bounds__(256) k_duplicate(const DevCam c, int N, int ra
 }
 
 // Exact instance count of each surfel: the tiles of its rectangle that pass
-// tile_may_hit (one warp per surfel, original order), and, for rectangles of
-// at most 128 tiles, the pass/fail bits in rectangle order for k_duplicate.
-// With mwords, the pass/fail bits of every rectangle are also stored, one
-// word per 32 tiles of rectangle order, at the surfel's offset moff[i] (an
-// exclusive scan of the word counts), when they fit below cap_words.
+// tile_may_hit (original order), and, for rectangles of at most 128 tiles,
+// the pass/fail bits in rectangle order for k_duplicate.  With mwords, the
+// pass/fail bits of every rectangle are also stored, one word per 32 tiles
+// of rectangle order, at the surfel's offset moff[i] (an exclusive scan of
+// the word counts), when they fit below cap_words.
+// One warp per 32 consecutive surfels: lane i loads surfel i's visibility,
+// rectangle, support conic and word offset (coalesced, all at once), then
+// the warp walks its visible surfels one by one (their data broadcast by
+// shuffles), lane b testing tile b of each 32-tile word; the surfel's own
+// lane keeps its count and mask for one coalesced store at the end.
 __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
                                                     const uint2* __restrict__ rect,
                                                     const float4* __restrict__ conic,
@@ -674,47 +679,74 @@ __global__ void __launch_bounds__(256) k_tile_count(const DevCam c, int N,
                                                     uint32_t* __restrict__ mwords,
                                                     uint32_t cap_words) {
   const int lane = threadIdx.x & 31;
-  const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (i >= N || count[i] == 0) return;  // warp-uniform
-  const uint2 rc = rect[i];
-  const int tx0 = rc.x & 0xFFFF, tx1 = rc.x >> 16, ty0 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
-  const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
-  const float inv_nx = 1.f / (float)nx;
-  const TileConic kc = load_conic(conic, (uint32_t)i);
-  const uint32_t words = (uint32_t)(nt + 31) / 32;
-  uint32_t* mw_out = nullptr;
-  if (mwords) {
-    const uint32_t off = moff[i];
-    if (off <= cap_words && words <= cap_words - off) mw_out = mwords + off;
+  const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL;
+  if (i0 >= N) return;  // warp-uniform
+  const long long i = i0 + lane;
+  const bool vis = i < N && count[i] != 0;
+  uint2 rc_own = make_uint2(0u, 0u);
+  uint32_t off_own = 0u;
+  float4 ka = make_float4(0.f, 0.f, 0.f, 0.f), kb = ka, kcc = ka;
+  if (vis) {
+    rc_own = rect[i];
+    ka = conic[3 * i];
+    kb = conic[3 * i + 1];
+    kcc = conic[3 * i + 2];
+    if (mwords) off_own = moff[i];
   }
-  uint32_t n = 0;
-  if (nt <= 128) {
-    uint32_t mw[4] = {0u, 0u, 0u, 0u};
+  uint32_t my_n = 0u;
+  uint4 my_mask = make_uint4(0u, 0u, 0u, 0u);
+  for (unsigned todo = __ballot_sync(0xffffffffu, vis); todo; todo &= todo - 1u) {
+    const int sl = __ffs(todo) - 1;  // the surfel's lane (warp-uniform)
+    const uint32_t rx = __shfl_sync(0xffffffffu, rc_own.x, sl);
+    const uint32_t ry = __shfl_sync(0xffffffffu, rc_own.y, sl);
+    const TileConic kc = {__shfl_sync(0xffffffffu, ka.x, sl),  __shfl_sync(0xffffffffu, ka.y, sl),
+                          __shfl_sync(0xffffffffu, ka.z, sl),  __shfl_sync(0xffffffffu, ka.w, sl),
+                          __shfl_sync(0xffffffffu, kb.x, sl),  __shfl_sync(0xffffffffu, kb.y, sl),
+                          __shfl_sync(0xffffffffu, kb.z, sl),  __shfl_sync(0xffffffffu, kb.w, sl),
+                          __shfl_sync(0xffffffffu, kcc.x, sl), __shfl_sync(0xffffffffu, kcc.y, sl),
+                          __shfl_sync(0xffffffffu, kcc.z, sl), __shfl_sync(0xffffffffu, kcc.w, sl)};
+    const int tx0 = rx & 0xFFFF, tx1 = rx >> 16, ty0 = ry & 0xFFFF, ty1 = ry >> 16;
+    const int nx = tx1 - tx0 + 1, nt = nx * (ty1 - ty0 + 1);
+    const float inv_nx = 1.f / (float)nx;
+    const uint32_t words = (uint32_t)(nt + 31) / 32;
+    uint32_t* mw_out = nullptr;
+    if (mwords) {
+      const uint32_t off = __shfl_sync(0xffffffffu, off_own, sl);
+      if (off <= cap_words && words <= cap_words - off) mw_out = mwords + off;
+    }
+    uint32_t n = 0;
+    if (nt <= 128) {
+      uint32_t mw[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const int k = 32 * w + lane;
-      const int2 t2 = rect_tile(k, nx, inv_nx);
-      const bool hit = k < nt && tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H);
-      mw[w] = __ballot_sync(0xffffffffu, hit);
-      n += __popc(mw[w]);
+      for (int w = 0; w < 4; ++w) {
+        if (32 * w >= nt) break;  // warp-uniform
+        const int k = 32 * w + lane;
+        const int2 t2 = rect_tile(k, nx, inv_nx);
+        const bool hit = k < nt && tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H);
+        mw[w] = __ballot_sync(0xffffffffu, hit);
+        n += __popc(mw[w]);
+      }
+      if (lane == sl) my_mask = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+      if (mw_out && lane < (int)words)
+        mw_out[lane] = lane == 0 ? mw[0] : lane == 1 ? mw[1] : lane == 2 ? mw[2] : mw[3];
+    } else {
+      for (int b = 0; b < nt; b += 32) {  // warp-uniform
+        const int k = b + lane;
+        const int2 t2 = rect_tile(k, nx, inv_nx);
+        const bool hit = k < nt && tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H);
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        n += __popc(m);
+        if (mw_out && lane == 0) mw_out[b >> 5] = m;
+      }
     }
-    if (lane == 0) {
-      tmask[i] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
-      count[i] = n;
-    }
-    if (mw_out && lane < (int)words)
-      mw_out[lane] = lane == 0 ? mw[0] : lane == 1 ? mw[1] : lane == 2 ? mw[2] : mw[3];
-    return;
+    if (lane == sl) my_n = n;
   }
-  for (int b = 0; b < nt; b += 32) {  // warp-uniform
-    const int k = b + lane;
-    const int2 t2 = rect_tile(k, nx, inv_nx);
-    const bool hit = k < nt && tile_may_hit(kc, tx0 + t2.x, ty0 + t2.y, c.W, c.H);
-    const uint32_t m = __ballot_sync(0xffffffffu, hit);
-    n += __popc(m);
-    if (mw_out && lane == 0) mw_out[b >> 5] = m;
+  if (vis) {
+    const uint32_t nt = ((rc_own.x >> 16) - (rc_own.x & 0xFFFF) + 1) *
+                        ((rc_own.y >> 16) - (rc_own.y & 0xFFFF) + 1);
+    if (nt <= 128) tmask[i] = my_mask;
+    count[i] = my_n;
   }
-  if (lane == 0) count[i] = n;
 }
 
 // Word count of each surfel's rectangle decisions (one per 32 tiles; none
@@ -902,15 +934,40 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place_count(
   for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) row[t] = s_cnt[t];
 }
 
-// Per tile (one thread each): exclusive prefix of the counts over the rank
-// blocks, in place, and the tile's total.
-__global__ void __launch_bounds__(256) k_place_colscan(uint32_t* __restrict__ M, int nb,
-                                                       int n_tiles, uint32_t* __restrict__ tot) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// Per tile: exclusive prefix of the counts over the rank blocks, in place,
+// and the tile's total.  A CTA takes 32 tiles (lane = tile, so every load
+// is one 128-byte row piece) and splits the rank blocks into 32 chunks, one
+// per warp: each warp sums its chunk, the chunk sums are scanned through
+// shared memory, and each warp then rewrites its chunk from its own base.
+constexpr int kColscanWarps = 32;
+__global__ void __launch_bounds__(kColscanWarps * 32) k_place_colscan(uint32_t* __restrict__ M,
+                                                                     int nb, int n_tiles,
+                                                                     uint32_t* __restrict__ tot) {
+  __shared__ uint32_t s_part[kColscanWarps][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
+  const int chunk = (nb + kColscanWarps - 1) / kColscanWarps;
+  const int b0 = min(nb, warp * chunk), b1 = min(nb, b0 + chunk);
+  uint32_t sum = 0;
+  if (t < n_tiles) {
+    int b = b0;
+    for (; b + 8 <= b1; b += 8) {  // eight independent loads in flight
+      uint32_t v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = M[(size_t)(b + k) * n_tiles + t];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sum += v[k];
+    }
+    for (; b < b1; ++b) sum += M[(size_t)b * n_tiles + t];
+  }
+  s_part[warp][lane] = sum;
+  __syncthreads();
   if (t >= n_tiles) return;
   uint32_t run = 0;
-  int b = 0;
-  for (; b + 8 <= nb; b += 8) {  // eight independent loads in flight
+  for (int w = 0; w < warp; ++w) run += s_part[w][lane];
+  if (warp == kColscanWarps - 1) tot[t] = run + sum;
+  int b = b0;
+  for (; b + 8 <= b1; b += 8) {
     uint32_t v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = M[(size_t)(b + k) * n_tiles + t];
@@ -920,12 +977,11 @@ __global__ void __launch_bounds__(256) k_place_colscan(uint32_t* __restrict__ M,
       run += v[k];
     }
   }
-  for (; b < nb; ++b) {
+  for (; b < b1; ++b) {
     const uint32_t v = M[(size_t)b * n_tiles + t];
     M[(size_t)b * n_tiles + t] = run;
     run += v;
   }
-  tot[t] = run;
 }
 
 // Tile ranges from the exclusive starts; a total above the key buffer's
@@ -1090,7 +1146,7 @@ cudaError_t launch_preprocess(const DevCam& c, const nexel_settings& s, int N, c
   }
   {
     NEXEL_PROF("tile_count", st);
-    k_tile_count<<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, st>>>(
+    k_tile_count<<<(unsigned)(((long long)N + 255) / 256), 256, 0, st>>>(
         c, N, (uint2*)(ws + L.rect), (float4*)(ws + L.conic), (uint4*)(ws + L.tmask),
         (uint32_t*)(ws + L.count), moff, moff ? (uint32_t*)(ws + L.mwords) : nullptr,
         (uint32_t)L.mword_cap);
@@ -1157,7 +1213,8 @@ static cudaError_t binning_place(const DevCam& c, int N, char* ws, const WsLayou
   }
   if (e == cudaSuccess && N > 0) {
     NEXEL_PROF("place_colscan", st);
-    k_place_colscan<<<(n_tiles + 255) / 256, 256, 0, st>>>(M, (int)nb, n_tiles, tstart);
+    k_place_colscan<<<(n_tiles + 31) / 32, kColscanWarps * 32, 0, st>>>(M, (int)nb, n_tiles,
+                                                                        tstart);
     e = cudaGetLastError();
   } else if (e == cudaSuccess) {
     e = cudaMemsetAsync(tstart, 0, (size_t)n_tiles * 4, st);
