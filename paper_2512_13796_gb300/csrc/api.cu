@@ -47,7 +47,7 @@ static void ws_fixed(const nexel_camera& cam, int N, WsLayout& L) {
   L.dkey0 = take(n * 4);
   L.dkey1 = take(n * 4);
   L.did0 = take(n * 4);
-  L.did1 = take(n * 4);
+  L.did1 = take(n * 4);  // after the depth sort: each surfel's rank (inverse permutation)
   L.rect = take(n * 8);
   L.conic = take(n * 48);
   L.tmask = take(n * 16);

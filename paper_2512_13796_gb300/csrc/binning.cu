@@ -579,10 +579,11 @@ static cudaError_t radix_sort(KeyT* k0, KeyT* k1, uint32_t* v0, uint32_t* v1, lo
 __global__ void k_permute(int N, const uint32_t* __restrict__ did, const float4* __restrict__ geom,
                           float4* __restrict__ geom_sorted, const float4* __restrict__ aux,
                           float4* __restrict__ aux_sorted, const uint32_t* __restrict__ count,
-                          uint32_t* __restrict__ offs) {
+                          uint32_t* __restrict__ offs, uint32_t* __restrict__ rank_of) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= N) return;
   uint32_t id = did[r];
+  rank_of[id] = (uint32_t)r;  // the inverse permutation, for the backward
   const float4* s = geom + (size_t)id * kRecF4;
   float4* d = geom_sorted + (size_t)r * kRecF4;
 #pragma unroll
@@ -1176,7 +1177,8 @@ cudaError_t launch_count_scan(int N, char* ws, const WsLayout& L, cudaStream_t s
                                                (float4*)(ws + L.geom_sorted),
                                                (float4*)(ws + L.aux_orig),
                                                (float4*)(ws + L.aux_sorted),
-                                               (uint32_t*)(ws + L.count), (uint32_t*)(ws + L.offs));
+                                               (uint32_t*)(ws + L.count), (uint32_t*)(ws + L.offs),
+                                               (uint32_t*)(ws + L.did1));
   }
   uint32_t* counters = (uint32_t*)(ws + L.counters);
   return excl_scan((uint32_t*)(ws + L.offs), N, (uint32_t*)(ws + L.scan_sums), counters + 1, st);
@@ -1300,24 +1302,31 @@ __device__ __forceinline__ void acc(float* p, float v) {
   else *p += v;
 }
 
+// One thread per surfel in original order (its parameters and gradients
+// are read and written coalesced); its rank, from the inverse permutation
+// the forward left, locates its 64-byte gradient record and frame record.
 // kAtomic: views rendered concurrently add into the same gradients.
 template <bool kAtomic>
 __global__ void k_preprocess_bwd(DevCam c, int N, int sh_degree, const float* __restrict__ mu,
                                  const float* __restrict__ shj, const float* __restrict__ quat,
-                                 const uint32_t* __restrict__ did, const uint32_t* __restrict__ dkey,
+                                 const uint32_t* __restrict__ rank_of,
+                                 const uint32_t* __restrict__ dkey,
                                  const float* __restrict__ gs, const float4* __restrict__ aux,
                                  float* __restrict__ d_mu,
                                  float* __restrict__ d_quat, float* __restrict__ d_scale,
                                  float* __restrict__ d_opac, float* __restrict__ d_gamma,
                                  float* __restrict__ d_color) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= N) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint32_t r = rank_of[i];
   if (dkey[r] == 0xFFFFFFFFu) return;  // culled: no gradient
-  uint32_t i = did[r];
   // the collection backward's sums over the surfel's pixels, turned into
   // camera-space gradients with the surfel's frame (aux: v1, v2, n and the
   // reciprocal scales; the hit offset in the plane is u s1 v1 + v s2 v2)
-  const float* g = gs + (size_t)r * kGradStride;
+  const float4* g4 = reinterpret_cast<const float4*>(gs + (size_t)r * kGradStride);
+  const float4 ga = g4[0], gb = g4[1], gc = g4[2], gd = g4[3];
+  const float g[15] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w,
+                       gc.x, gc.y, gc.z, gc.w, gd.x, gd.y, gd.z};
   const float4 a1 = aux[(size_t)r * kAuxF4 + 1], a2 = aux[(size_t)r * kAuxF4 + 2],
                a3 = aux[(size_t)r * kAuxF4 + 3];
   const float3 v1 = make_float3(a1.x, a1.y, a1.z), v2 = make_float3(a2.x, a2.y, a2.z),
@@ -1434,7 +1443,7 @@ cudaError_t launch_preprocess_bwd(const DevCam& c, const nexel_settings& s, int 
     NEXEL_PROF("preprocess_bwd", st);
     auto kern = atomic ? k_preprocess_bwd<true> : k_preprocess_bwd<false>;
     kern<<<(N + 255) / 256, 256, 0, st>>>(
-        c, N, s.sh_degree, mu, (const float*)(ws + L.shj), quat, (uint32_t*)(ws + L.did0),
+        c, N, s.sh_degree, mu, (const float*)(ws + L.shj), quat, (uint32_t*)(ws + L.did1),
         (uint32_t*)(ws + L.dkey0),
         (float*)(ws + L.grad_sorted), (const float4*)(ws + L.aux_sorted), d_mu, d_quat, d_scale,
         d_opacity, d_gamma, d_color);
