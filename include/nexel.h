@@ -509,11 +509,11 @@ int nexel_peak_l2_reductions(void* buf, size_t buf_bytes, long long n_ops, int r
  * NEXEL_ERR_INVALID_ARG, nothing launched); more (tile, surfel) instances
  * than the array holds returns NEXEL_ERR_CAPACITY with the count in
  * *n_instances_out.  Like nexel_preprocess, every call synchronises the
- * stream once to read the instance count back.  The first call on a device
- * resolves the array's device address (once per device, with that device
- * current, kept for the life of the process: do not use the library across
- * a cudaDeviceReset of that device), so make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the
+ * stream once to read the instance count back, so no call can be captured
+ * into a CUDA graph.  The first call on a device resolves the array's device
+ * address (once per device, with that device current, kept for the life of
+ * the process: do not use the library across a cudaDeviceReset of that
+ * device).  All calls share the array: calls that overlap on the
  * GPU race, so serialise them; it keeps the previous call's contents, and
  * the pipeline clears what must start at zero itself. */
 int nexel_render_fwd_static(const nexel_camera* cam, const nexel_settings* settings,
