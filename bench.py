@@ -692,7 +692,11 @@ def main():
     loss_host = torch.empty(1).pin_memory()
     ws_e2e = R.Workspace(dev, cap_hint=32 << 20)
 
+    grad_leaves = list(params.values()) + [fld.table, fld.weights]
+
     def e2e_step():
+        for t in grad_leaves:  # a training step starts with no gradients
+            t.grad = None
         tgt = target_host.to(dev, non_blocking=True)
         img, _, _ = R.render(params, fld, w.cameras[0], w.settings, ws_e2e)
         loss = (img - tgt).abs().mean()
@@ -866,7 +870,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": mpix(e2e_ms), "unit": "Mpix/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": H * W * 3 * 4, "d2h_bytes_per_step": 4,
-                "path": "render() autograd API: H2D target, forward, L1 loss, backward, D2H loss; "
+                "path": "render() autograd API: gradients set to None, H2D target, forward, L1 loss, backward, D2H loss; "
                         "no L2 flush between steps; the surfel parameters, hash table and MLP "
                         "stay resident on the device across steps, as in training (only the "
                         "target image and the loss cross the bus)"},

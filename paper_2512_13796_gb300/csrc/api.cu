@@ -409,7 +409,7 @@ int zero_grads(const nexel_settings* settings, const nexel_field* field, int N, 
   z(d_scale, 2 * n);
   z(d_opacity, n);
   z(d_gamma, 2 * n);
-  z(d_color, 3 * n);
+  z(d_color, (settings->sh_degree == 3 ? 48 : 3) * n);  // RGB, or 16 SH coefficients x 3
   if (settings->K > 0 && field) {
     z(d_table, (size_t)field->L * field->T * field->F);
     size_t nw = 0;

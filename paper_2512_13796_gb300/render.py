@@ -160,18 +160,21 @@ def backward(ws: Workspace, cam_s, st_s, field, table_store, weights, mu, quat, 
     N = mu.shape[0]
     K = st_s.K
     g = grads if grads is not None else {}
+    # new gradient buffers: without accumulate the library overwrites them
+    # (it zeroes every gradient output itself), so they need no fill here
+    new = torch.zeros if accumulate else torch.empty
     cshape = (N, 16, 3) if st_s.sh_degree == 3 else (N, 3)
     for k, shape in (("mu", (N, 3)), ("quat", (N, 4)), ("scale", (N, 2)), ("opacity", (N,)),
                      ("gamma", (N, 2)), ("color", cshape)):
         if k not in g:
-            g[k] = torch.zeros(shape, device=dev)
+            g[k] = new(shape, device=dev)
     fs = None
     if field is not None and K > 0:
         fs = field.struct(table_store, weights)
         if "table" not in g:
-            g["table"] = torch.zeros_like(field.table)
+            g["table"] = new(field.table.shape, device=dev)
         if "mlp" not in g:
-            g["mlp"] = torch.zeros_like(field.weights)
+            g["mlp"] = new(field.weights.shape, device=dev)
     bws = ws.bwd(cam_s, st_s, fs)
     buf = ws.ws
     N_.nexel_render_bwd(cam_s, st_s, fs, N, mu.data_ptr(), quat.data_ptr(), scale.data_ptr(),

@@ -86,6 +86,40 @@ def test_sh_config0_forward_backward(dev):
     print(f"\n[sh config0] fwd image err {s['image']:.2e} grads {st_g}")
 
 
+def test_sh_backward_overwrites_dirty_gradients(dev):
+    """Without accumulate, the backward overwrites every gradient output,
+    all 48 SH coefficients per surfel included: into buffers full of NaN
+    it gives exactly what it gives into zeroed ones."""
+    import torch
+    from paper_2512_13796_gb300 import render as R
+    w = synth.workload(0, gamma="var")
+    cam, st = w.cameras[0], w.settings
+    coeffs = synth.sh_coefficients(w.scene.n, 0)
+    p = {k: torch.from_numpy(np.ascontiguousarray(getattr(w.scene, k))).to(dev)
+         for k in SURFEL_KEYS}
+    p["color"] = torch.from_numpy(coeffs).to(dev)
+    fd = R.DeviceField.from_synth(w.field, dev, "f32", "f32")
+    ws = R.Workspace(dev)
+    cam_s = R.camera_struct(cam)
+    st_s = R.settings_struct(st, "f32", "f32", sh_degree=3)
+    ts = fd.storage_table()
+    out = R.forward(ws, cam_s, st_s, fd, ts, fd.weights, *[p[k] for k in SURFEL_KEYS])
+    dI = torch.from_numpy(np.random.default_rng(3).normal(
+        size=(cam.height, cam.width, 3)).astype(np.float32)).to(dev)
+    args = (ws, cam_s, st_s, fd, ts, fd.weights, *[p[k] for k in SURFEL_KEYS[:5]], out, dI)
+    clean = R.backward(*args)
+    shapes = {k: v.shape for k, v in clean.items()}
+    dirty = {k: torch.full(sh, float("nan"), device=dev) for k, sh in shapes.items()}
+    again = R.backward(*args, accumulate=False, grads=dirty)
+    torch.cuda.synchronize()
+    assert clean["color"].shape == (w.scene.n, 16, 3)
+    for k in shapes:
+        a, b = clean[k].cpu().numpy(), again[k].cpu().numpy()
+        assert np.isfinite(b).all(), k
+        # float atomics may sum in another order: equal up to their rounding
+        assert np.allclose(a, b, rtol=1e-5, atol=1e-6 * max(1.0, float(np.abs(a).max()))), k
+
+
 @pytest.mark.parametrize("form", ["f32", "bf16"])
 def test_sh_config1_sampled(dev, form):
     w = synth.workload(1)
